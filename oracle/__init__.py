@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the financial Monte Carlo method of Belletti et al.,
+"Tensor Processing Units for Financial Monte Carlo" (2019).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never imports, links or falls back to it, and this package imports nothing
+from the library: the two share no code.  Inputs come from the seeded
+generators in ``workloads.py``, which hold none of the method's arithmetic.
+
+Contents
+  oracle.c   plain C, IEEE double, one path at a time (compiled by ``build()``
+             with gcc -O2 -ffp-contract=off, no fast-math; OpenMP only over
+             independent paths, each writing its own output slot, so results do
+             not depend on the thread count):
+             Philox4x32-10 (Sec. IV.A), Box-Muller (Sec. VI.D), Cholesky
+             (Sec. II.A.3), correlated GBM Euler / log-Euler steps (Sec. II.A.1,
+             II.A.2), Heston full-truncation Euler, European / Asian / barrier
+             payoffs (Sec. I.A.2), forward-mode pathwise Greeks (Sec. I.A.3),
+             the estimator of Eq. 3 with its standard error.
+  mlp.py     FP64 numpy forward / backward of the pricing surrogate.
+  risk.py    VaR / CVaR of Sec. VI.B and nested revaluation.
+
+Pins (tests/test_oracle_*.py, all ``-m "not gpu"``): Philox against PyTorch's
+independent header-only Philox engine; uniform-map exactness; normal moments;
+Black-Scholes closed form incl. the paper's vanilla-call value (Sec. VI.A.1);
+martingale and put-call parity; discrete geometric-Asian closed form and the
+AM >= GM invariant; one-step barrier closed form and in + out = vanilla;
+Cholesky against numpy; d = 1 basket = scalar GBM; geometric-basket closed
+form; Heston xi = 0 reduction to Black-Scholes; Greeks against Black-Scholes
+closed forms and common-random-number finite differences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Payoff vocabulary shared by name with the library's binding; the integer
+# codes below are this file's own.
+PAYOFF_CODES = {
+    "call": 0, "put": 1, "asian_call": 2, "asian_put": 3,
+    "uo_call": 4, "ui_call": 5, "uo_put": 6, "ui_put": 7,
+    "do_call": 8, "di_call": 9, "do_put": 10, "di_put": 11,
+}
+HESTON_GREEKS = ("delta", "vega_v0", "rho", "d_kappa", "d_theta", "d_xi", "d_rho")
+HESTON_PARAM_ORDER = ("s0", "v0", "r", "kappa", "theta", "xi", "rho")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain gcc, no CUDA)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.POINTER
+    d_p, i_p, u32_p = P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint32)
+    i64, u64, i32, dbl = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    lib.orc_philox4x32_10.argtypes = [u32_p, u32_p, u32_p]
+    lib.orc_uniform.argtypes = [ctypes.c_uint32]
+    lib.orc_uniform.restype = dbl
+    lib.orc_normals.argtypes = [u64, u64, u64, i64, d_p]
+    lib.orc_cholesky.argtypes = [i32, d_p, d_p]
+    lib.orc_cholesky.restype = i32
+    gbm_common = [i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, i32, u64, i64, i64]
+    lib.orc_gbm_payoffs.argtypes = gbm_common + [i32, i_p, d_p, d_p, d_p]
+    lib.orc_gbm_payoffs.restype = i32
+    lib.orc_gbm_paths.argtypes = gbm_common + [i32, d_p]
+    lib.orc_gbm_paths.restype = i32
+    lib.orc_gbm_greeks.argtypes = gbm_common + [i32, i_p, d_p, d_p]
+    lib.orc_gbm_greeks.restype = i32
+    hes_common = [dbl] * 8 + [i32, u64, i64, i64]
+    lib.orc_heston_payoffs.argtypes = hes_common + [i32, i_p, d_p, d_p, d_p]
+    lib.orc_heston_payoffs.restype = i32
+    lib.orc_heston_paths.argtypes = hes_common + [i32, d_p]
+    lib.orc_heston_paths.restype = i32
+    lib.orc_heston_greeks.argtypes = hes_common + [i32, i_p, d_p, d_p]
+    lib.orc_heston_greeks.restype = i32
+    lib.orc_mean_se.argtypes = [d_p, i64, d_p, d_p]
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+# --------------------------------------------------------------------------
+# Random stream (Sec. IV.A keyed counter-based generation; Sec. VI.D Box-Muller)
+# --------------------------------------------------------------------------
+def philox(counter, key):
+    """One Philox4x32-10 block: counter = 4 words, key = 2 words -> 4 words."""
+    lib = _load()
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    u32_p = ctypes.POINTER(ctypes.c_uint32)
+    lib.orc_philox4x32_10(c.ctypes.data_as(u32_p), k.ctypes.data_as(u32_p), out.ctypes.data_as(u32_p))
+    return out
+
+
+def uniform(x: int) -> float:
+    return _load().orc_uniform(int(x) & 0xFFFFFFFF)
+
+
+def normals(seed: int, stream: int, j0: int, count: int) -> np.ndarray:
+    """Normals j0 .. j0+count-1 of stream `stream` (path index) under `seed`."""
+    z = np.empty(count, dtype=np.float64)
+    _load().orc_normals(seed, stream, j0, count, _dptr(z))
+    return z
+
+
+def cholesky(A) -> np.ndarray:
+    A = _f64(A)
+    d = A.shape[0]
+    L = np.empty_like(A)
+    rc = _load().orc_cholesky(d, _dptr(A), _dptr(L))
+    if rc != 0:
+        raise OracleError("matrix is not positive definite")
+    return L
+
+
+def mean_se(f) -> tuple[float, float]:
+    """Eq. 3 estimator and its standard error, compensated sums in index order."""
+    f = _f64(f).ravel()
+    m, s = ctypes.c_double(), ctypes.c_double()
+    _load().orc_mean_se(_dptr(f), f.size, ctypes.byref(m), ctypes.byref(s))
+    return m.value, s.value
+
+
+# --------------------------------------------------------------------------
+# Payoff list helpers
+# --------------------------------------------------------------------------
+def _payoff_arrays(payoffs):
+    kinds = np.array([PAYOFF_CODES[p["kind"]] for p in payoffs], dtype=np.int32)
+    K = np.array([float(p.get("strike", 0.0)) for p in payoffs], dtype=np.float64)
+    H = np.array([float(p.get("barrier", np.inf)) for p in payoffs], dtype=np.float64)
+    return kinds, K, H
+
+
+def _gbm_args(s0, sigma, corr, weights):
+    s0 = _f64(np.atleast_1d(s0))
+    sigma = _f64(np.atleast_1d(sigma))
+    d = s0.size
+    corr = None if corr is None else _f64(corr).reshape(d, d)
+    w = np.full(d, 1.0 / d) if weights is None else _f64(weights)
+    return d, s0, sigma, corr, w
+
+
+# --------------------------------------------------------------------------
+# Correlated GBM (Sec. II.A.1 scalar and II.A.2 multivariate Euler-Maruyama)
+# --------------------------------------------------------------------------
+def gbm_payoffs(s0, sigma, r, T, steps, paths, payoffs, corr=None, weights=None,
+                scheme="log_euler", seed=42, path_offset=0) -> np.ndarray:
+    """Discounted per-path payoffs, shape [len(payoffs), paths]."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    kinds, K, H = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), paths), dtype=np.float64)
+    ip = kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    rc = _load().orc_gbm_payoffs(d, _dptr(s0), _dptr(sigma), _dptr(corr), _dptr(w), r, T, steps,
+                                 0 if scheme == "log_euler" else 1, seed, path_offset, paths,
+                                 len(payoffs), ip, _dptr(K), _dptr(H), _dptr(out))
+    _check(rc, "orc_gbm_payoffs")
+    return out
+
+
+def gbm_paths(s0, sigma, r, T, steps, paths, corr=None, weights=None, scheme="log_euler",
+              seed=42, path_offset=0, save_every=1) -> np.ndarray:
+    """Asset prices at steps 0, k, 2k, ..., M: shape [M/k + 1, d, paths]."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    nsave = steps // save_every + 1
+    out = np.empty((nsave, d, paths), dtype=np.float64)
+    rc = _load().orc_gbm_paths(d, _dptr(s0), _dptr(sigma), _dptr(corr), _dptr(w), r, T, steps,
+                               0 if scheme == "log_euler" else 1, seed, path_offset, paths,
+                               save_every, _dptr(out))
+    _check(rc, "orc_gbm_paths")
+    return out
+
+
+def gbm_greeks(s0, sigma, r, T, steps, paths, payoffs, corr=None, weights=None,
+               scheme="log_euler", seed=42, path_offset=0) -> np.ndarray:
+    """Per-path discounted pathwise Greeks, shape [len(payoffs), 2d+1, paths]:
+    d/dS0_a (a < d), d/dsigma_a (d <= k < 2d), d/dr (k = 2d)."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    kinds, K, _ = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), 2 * d + 1, paths), dtype=np.float64)
+    ip = kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    rc = _load().orc_gbm_greeks(d, _dptr(s0), _dptr(sigma), _dptr(corr), _dptr(w), r, T, steps,
+                                0 if scheme == "log_euler" else 1, seed, path_offset, paths,
+                                len(payoffs), ip, _dptr(K), _dptr(out))
+    _check(rc, "orc_gbm_greeks")
+    return out
+
+
+# --------------------------------------------------------------------------
+# Heston, full-truncation Euler
+# --------------------------------------------------------------------------
+def _hes(h):
+    return (float(h["s0"]), float(h["v0"]), float(h["r"]), float(h["kappa"]), float(h["theta"]),
+            float(h["xi"]), float(h["rho"]))
+
+
+def heston_payoffs(h, T, steps, paths, payoffs, seed=42, path_offset=0) -> np.ndarray:
+    kinds, K, H = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), paths), dtype=np.float64)
+    ip = kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    rc = _load().orc_heston_payoffs(*_hes(h), T, steps, seed, path_offset, paths, len(payoffs), ip,
+                                    _dptr(K), _dptr(H), _dptr(out))
+    _check(rc, "orc_heston_payoffs")
+    return out
+
+
+def heston_paths(h, T, steps, paths, seed=42, path_offset=0, save_every=1) -> np.ndarray:
+    """[M/k + 1, 2, paths]: component 0 price, 1 variance."""
+    out = np.empty((steps // save_every + 1, 2, paths), dtype=np.float64)
+    rc = _load().orc_heston_paths(*_hes(h), T, steps, seed, path_offset, paths, save_every, _dptr(out))
+    _check(rc, "orc_heston_paths")
+    return out
+
+
+def heston_greeks(h, T, steps, paths, payoffs, seed=42, path_offset=0) -> np.ndarray:
+    """[len(payoffs), 7, paths] in the order of HESTON_GREEKS."""
+    kinds, K, _ = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), 7, paths), dtype=np.float64)
+    ip = kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    rc = _load().orc_heston_greeks(*_hes(h), T, steps, seed, path_offset, paths, len(payoffs), ip,
+                                   _dptr(K), _dptr(out))
+    _check(rc, "orc_heston_greeks")
+    return out
+
+
+def price(per_path: np.ndarray):
+    """Mean and standard error of each row of a [n_payoff, paths] array."""
+    return [mean_se(row) for row in np.atleast_2d(per_path)]

@@ -1,0 +1,575 @@
+/*
+ * FP64 CPU oracle for the Monte Carlo method of "Tensor Processing Units for
+ * Financial Monte Carlo" (Belletti et al., 2019).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * restatement of the method that the CUDA library is checked against.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it;
+ * the library never links, calls or falls back to it, and it includes no header
+ * of the library.  Every floating-point quantity is IEEE double; no blocking,
+ * fusion or reordering beyond what each cited passage states.
+ *
+ * Parity status: every function below is pinned by the tests listed in the
+ * oracle package docstring, except orc_heston_* whose pins are the xi = 0
+ * Black-Scholes reduction and finite differences (no closed form at xi > 0).
+ *
+ * Random stream (the paper fixes the generator family, Sec. IV.A, not the
+ * layout; the layout below is this library's convention):
+ *   key     = (seed mod 2^32, seed div 2^32)
+ *   normal j of stream s is produced from Philox4x32-10 block q = j div 4 at
+ *   counter (q mod 2^32, q div 2^32, s mod 2^32, s div 2^32), lane j mod 4;
+ *   lanes (0,1) and (2,3) form Box-Muller pairs.
+ *   Uniform map U(x) = (floor(x / 2^9) + 1/2) * 2^-23, which is exact in both
+ *   binary32 and binary64 and lies in [2^-24, 1 - 2^-24].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: the keyed, multi-stream generator named for GPUs in       */
+/* Sec. IV.A (Salmon et al., SC'11, whose published round function this is). */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u; /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u; /* Weyl key increments */
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1) from one 32-bit word, exact in binary32 and binary64. */
+double orc_uniform(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); /* 2^-23 */
+}
+
+/* Normal number j of stream `stream` under key `seed` (Box-Muller on the pair of
+ * uniforms that shares j's block; the transform the paper uses in Sec. VI.D). */
+typedef struct {
+    uint64_t seed, stream;
+    uint64_t cached_q;
+    int have;
+    double z[4];
+} orc_stream;
+
+static void stream_init(orc_stream *s, uint64_t seed, uint64_t stream)
+{
+    s->seed = seed; s->stream = stream; s->have = 0; s->cached_q = 0;
+}
+
+static double stream_normal(orc_stream *s, uint64_t j)
+{
+    uint64_t q = j >> 2;
+    if (!s->have || s->cached_q != q) {
+        uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)s->stream, (uint32_t)(s->stream >> 32)};
+        uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        for (int pair = 0; pair < 2; ++pair) {
+            double u1 = orc_uniform(x[2 * pair]);
+            double u2 = orc_uniform(x[2 * pair + 1]);
+            double rad = sqrt(-2.0 * log(u1));
+            s->z[2 * pair] = rad * cos(2.0 * M_PI * u2);
+            s->z[2 * pair + 1] = rad * sin(2.0 * M_PI * u2);
+        }
+        s->cached_q = q; s->have = 1;
+    }
+    return s->z[j & 3];
+}
+
+void orc_normals(uint64_t seed, uint64_t stream, uint64_t j0, int64_t count, double *z)
+{
+    orc_stream s;
+    stream_init(&s, seed, stream);
+    for (int64_t k = 0; k < count; ++k) z[k] = stream_normal(&s, j0 + (uint64_t)k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cholesky factor L with L L^T = A (Sec. II.A.3 uses it for the Grammian;   */
+/* here it factors the asset correlation so that L z has covariance A).      */
+/* Plain Cholesky-Banachiewicz; returns 0, or -1 if A is not positive        */
+/* definite.  A and L are row-major d x d; the upper triangle of L is zero.  */
+/* ------------------------------------------------------------------------ */
+int orc_cholesky(int d, const double *A, double *L)
+{
+    memset(L, 0, sizeof(double) * (size_t)d * (size_t)d);
+    for (int i = 0; i < d; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[(size_t)i * d + j];
+            for (int k = 0; k < j; ++k) s -= L[(size_t)i * d + k] * L[(size_t)j * d + k];
+            if (i == j) {
+                if (!(s > 0.0)) return -1;
+                L[(size_t)i * d + i] = sqrt(s);
+            } else {
+                L[(size_t)i * d + j] = s / L[(size_t)j * d + j];
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Payoffs on the monitored underlying U(t_i), i = 1..M (Sec. I.A.2: path-   */
+/* dependent outcomes f(X_{0:T}); barrier and Asian options).                */
+/* ------------------------------------------------------------------------ */
+enum {
+    ORC_CALL = 0, ORC_PUT = 1, ORC_ASIAN_CALL = 2, ORC_ASIAN_PUT = 3,
+    ORC_UO_CALL = 4, ORC_UI_CALL = 5, ORC_UO_PUT = 6, ORC_UI_PUT = 7,
+    ORC_DO_CALL = 8, ORC_DI_CALL = 9, ORC_DO_PUT = 10, ORC_DI_PUT = 11
+};
+
+typedef struct {
+    double u_T;   /* U(t_M) */
+    double avg;   /* (1/M) sum_{i=1..M} U(t_i) */
+    double umax;  /* max_{i=1..M} U(t_i) */
+    double umin;  /* min_{i=1..M} U(t_i) */
+} orc_pathstats;
+
+static double payoff_value(int kind, double K, double H, const orc_pathstats *p)
+{
+    double call = p->u_T > K ? p->u_T - K : 0.0;
+    double put = K > p->u_T ? K - p->u_T : 0.0;
+    int up_hit = p->umax >= H, down_hit = p->umin <= H;
+    switch (kind) {
+    case ORC_CALL: return call;
+    case ORC_PUT: return put;
+    case ORC_ASIAN_CALL: return p->avg > K ? p->avg - K : 0.0;
+    case ORC_ASIAN_PUT: return K > p->avg ? K - p->avg : 0.0;
+    case ORC_UO_CALL: return up_hit ? 0.0 : call;
+    case ORC_UI_CALL: return up_hit ? call : 0.0;
+    case ORC_UO_PUT: return up_hit ? 0.0 : put;
+    case ORC_UI_PUT: return up_hit ? put : 0.0;
+    case ORC_DO_CALL: return down_hit ? 0.0 : call;
+    case ORC_DI_CALL: return down_hit ? call : 0.0;
+    case ORC_DO_PUT: return down_hit ? 0.0 : put;
+    case ORC_DI_PUT: return down_hit ? put : 0.0;
+    default: return NAN;
+    }
+}
+
+/* Derivative of the undiscounted payoff with respect to the quantity it is
+ * written on (u_T for European kinds, avg for Asian kinds); the indicator
+ * convention d/dx (x-K)^+ = 1{x > K}.  Barrier kinds have no pathwise
+ * derivative (the knock indicator is discontinuous): returns NAN. */
+static double payoff_slope(int kind, double K, const orc_pathstats *p)
+{
+    switch (kind) {
+    case ORC_CALL: return p->u_T > K ? 1.0 : 0.0;
+    case ORC_PUT: return K > p->u_T ? -1.0 : 0.0;
+    case ORC_ASIAN_CALL: return p->avg > K ? 1.0 : 0.0;
+    case ORC_ASIAN_PUT: return K > p->avg ? -1.0 : 0.0;
+    default: return NAN;
+    }
+}
+
+static int payoff_is_asian(int kind) { return kind == ORC_ASIAN_CALL || kind == ORC_ASIAN_PUT; }
+
+/* ------------------------------------------------------------------------ */
+/* Correlated geometric Brownian motion, d >= 1 assets (Eq. 1 with           */
+/* mu(X) = r X and sigma(X) = diag(X) diag(sig) Lrho; the multivariate       */
+/* Euler-Maruyama step of Sec. II.A.2, which for d = 1 is the scalar step of  */
+/* Sec. II.A.1).  scheme 0: log-Euler on log S; scheme 1: Euler on S.         */
+/*   dW_a = sqrt(Delta) * sig_a * sum_{k<=a} Lrho[a][k] z_k,  z = normals     */
+/*          i*d .. i*d+d-1 of stream path0+n.                                */
+/*   log-Euler: x_a += (r - sig_a^2/2) Delta + dW_a                          */
+/*   Euler:     S_a += S_a (r Delta + dW_a)                                   */
+/* U(t) = sum_a w_a S_a(t).                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int d;
+    const double *s0, *sig, *w;
+    double *Lrho; /* d x d */
+    double r, T;
+    int steps, scheme;
+    uint64_t seed;
+} orc_gbm;
+
+static int gbm_setup(orc_gbm *m, int d, const double *s0, const double *sig, const double *corr,
+                     const double *w, double r, double T, int steps, int scheme, uint64_t seed)
+{
+    m->d = d; m->s0 = s0; m->sig = sig; m->w = w; m->r = r; m->T = T;
+    m->steps = steps; m->scheme = scheme; m->seed = seed;
+    m->Lrho = (double *)malloc(sizeof(double) * (size_t)d * (size_t)d);
+    if (!m->Lrho) return -3;
+    if (corr) {
+        if (orc_cholesky(d, corr, m->Lrho) != 0) { free(m->Lrho); return -2; }
+    } else {
+        memset(m->Lrho, 0, sizeof(double) * (size_t)d * (size_t)d);
+        for (int a = 0; a < d; ++a) m->Lrho[(size_t)a * d + a] = 1.0;
+    }
+    return 0;
+}
+
+/* Simulate one path.  Optional outputs:
+ *   save: [n_saved][d][ld] prices at steps 0, save_every, 2 save_every, ..., M
+ *   S_T:  [d] terminal prices;  stats: monitored statistics of U.
+ *   tangents (Greeks, forward mode): per asset a, dS_a/dS0_a, dS_a/dsig_a,
+ *   dS_a/dr at the end (tS0, tsig, tr) and their (1/M) sum over i = 1..M of
+ *   w_a * tangent (aS0, asig, ar) for the Asian average. */
+typedef struct {
+    double *tS0, *tsig, *tr;   /* [d] terminal tangents of S_a */
+    double *aS0, *asig, *ar;   /* [d] tangents of the Asian average */
+} orc_tangents;
+
+static void gbm_path(const orc_gbm *m, int64_t n, double *save, int64_t col, int save_every, int64_t ld,
+                     double *S_T, orc_pathstats *stats, orc_tangents *tg,
+                     double *work /* 3*d */)
+{
+    const int d = m->d, M = m->steps;
+    const double dt = m->T / M, sdt = sqrt(dt);
+    double *x = work, *z = work + d, *y = work + 2 * d; /* state, normals, Lrho z */
+    orc_stream st;
+    stream_init(&st, m->seed, (uint64_t)n);
+    for (int a = 0; a < d; ++a) x[a] = (m->scheme == 0) ? log(m->s0[a]) : m->s0[a];
+    if (tg) {
+        for (int a = 0; a < d; ++a) {
+            /* log-Euler tangents are of x = log S; Euler tangents are of S. */
+            tg->tS0[a] = (m->scheme == 0) ? 1.0 / m->s0[a] : 1.0;
+            tg->tsig[a] = 0.0; tg->tr[a] = 0.0;
+            tg->aS0[a] = 0.0; tg->asig[a] = 0.0; tg->ar[a] = 0.0;
+        }
+    }
+    if (save) {
+        for (int a = 0; a < d; ++a) save[(size_t)a * ld + col] = m->s0[a];
+    }
+    double sum = 0.0, umax = -INFINITY, umin = INFINITY, u = 0.0;
+    for (int i = 0; i < M; ++i) {
+        for (int a = 0; a < d; ++a) z[a] = stream_normal(&st, (uint64_t)i * d + a);
+        for (int a = 0; a < d; ++a) {
+            double s = 0.0;
+            for (int k = 0; k <= a; ++k) s += m->Lrho[(size_t)a * d + k] * z[k];
+            y[a] = s;
+        }
+        for (int a = 0; a < d; ++a) {
+            double dW = sdt * m->sig[a] * y[a];
+            if (m->scheme == 0) {
+                x[a] += (m->r - 0.5 * m->sig[a] * m->sig[a]) * dt + dW;
+                if (tg) {
+                    tg->tsig[a] += -m->sig[a] * dt + sdt * y[a];
+                    tg->tr[a] += dt;
+                }
+            } else {
+                double g = 1.0 + m->r * dt + dW;
+                if (tg) {
+                    tg->tS0[a] = tg->tS0[a] * g;
+                    tg->tsig[a] = tg->tsig[a] * g + x[a] * sdt * y[a];
+                    tg->tr[a] = tg->tr[a] * g + x[a] * dt;
+                }
+                x[a] = x[a] * g;
+            }
+        }
+        u = 0.0;
+        for (int a = 0; a < d; ++a) {
+            double Sa = (m->scheme == 0) ? exp(x[a]) : x[a];
+            u += m->w[a] * Sa;
+            if (tg) {
+                /* dS_a/dp = S_a dx_a/dp for log-Euler, the tangent itself for Euler */
+                double f = (m->scheme == 0) ? Sa : 1.0;
+                tg->aS0[a] += m->w[a] * f * tg->tS0[a] / M;
+                tg->asig[a] += m->w[a] * f * tg->tsig[a] / M;
+                tg->ar[a] += m->w[a] * f * tg->tr[a] / M;
+            }
+        }
+        sum += u;
+        if (u > umax) umax = u;
+        if (u < umin) umin = u;
+        if (save && save_every > 0 && (i + 1) % save_every == 0) {
+            int slot = (i + 1) / save_every;
+            for (int a = 0; a < d; ++a)
+                save[((size_t)slot * d + a) * ld + col] = (m->scheme == 0) ? exp(x[a]) : x[a];
+        }
+    }
+    for (int a = 0; a < d; ++a) {
+        double Sa = (m->scheme == 0) ? exp(x[a]) : x[a];
+        if (S_T) S_T[a] = Sa;
+        if (tg && m->scheme == 0) {
+            tg->tS0[a] *= Sa; tg->tsig[a] *= Sa; tg->tr[a] *= Sa;
+        }
+    }
+    if (stats) {
+        stats->u_T = u; stats->avg = sum / M; stats->umax = umax; stats->umin = umin;
+    }
+}
+
+/* Discounted payoffs of every path: out[p * npaths + n], path index path0 + n.
+ * Returns 0, -1 on bad arguments, -2 if corr is not positive definite. */
+int orc_gbm_payoffs(int d, const double *s0, const double *sig, const double *corr, const double *w,
+                    double r, double T, int steps, int scheme, uint64_t seed,
+                    int64_t path0, int64_t npaths,
+                    int npay, const int *kind, const double *strike, const double *barrier,
+                    double *out)
+{
+    if (d < 1 || steps < 1 || npaths < 0 || !(T > 0.0) || (scheme != 0 && scheme != 1)) return -1;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, w, r, T, steps, scheme, seed);
+    if (rc) return rc;
+    const double disc = exp(-r * T);
+#pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            orc_pathstats ps;
+            gbm_path(&m, path0 + n, NULL, 0, 0, 0, NULL, &ps, NULL, work);
+            for (int p = 0; p < npay; ++p)
+                out[(size_t)p * npaths + n] = disc * payoff_value(kind[p], strike[p], barrier[p], &ps);
+        }
+        free(work);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
+/* Materialised paths: save[(slot*d + a)*npaths + n] = S_a at step slot*save_every
+ * (slot 0 is t_0), for n in [0, npaths), path index path0 + n. */
+int orc_gbm_paths(int d, const double *s0, const double *sig, const double *corr, const double *w,
+                  double r, double T, int steps, int scheme, uint64_t seed,
+                  int64_t path0, int64_t npaths, int save_every, double *save)
+{
+    if (d < 1 || steps < 1 || npaths < 0 || !(T > 0.0) || save_every < 1 || steps % save_every) return -1;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, w, r, T, steps, scheme, seed);
+    if (rc) return rc;
+#pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            gbm_path(&m, path0 + n, save, n, save_every, npaths, NULL, NULL, NULL, work);
+        }
+        free(work);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
+/* Pathwise (infinitesimal perturbation) Greeks in forward mode (Sec. I.A.3,
+ * Sec. VI.A.2 "Basket European option Delta"), per path, discounted:
+ *   g[((p*(2d+1)) + k) * npaths + n],  k = 0..d-1: d/dS0_k,  k = d..2d-1:
+ *   d/dsig_{k-d},  k = 2d: d/dr (includes the -T * discounted payoff term).
+ * European and Asian kinds only; returns -4 for a barrier kind. */
+int orc_gbm_greeks(int d, const double *s0, const double *sig, const double *corr, const double *w,
+                   double r, double T, int steps, int scheme, uint64_t seed,
+                   int64_t path0, int64_t npaths,
+                   int npay, const int *kind, const double *strike,
+                   double *g)
+{
+    if (d < 1 || steps < 1 || npaths < 0 || !(T > 0.0) || (scheme != 0 && scheme != 1)) return -1;
+    for (int p = 0; p < npay; ++p)
+        if (kind[p] > ORC_ASIAN_PUT || kind[p] < 0) return -4;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, w, r, T, steps, scheme, seed);
+    if (rc) return rc;
+    const double disc = exp(-r * T);
+    const int ng = 2 * d + 1;
+#pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * 9 * (size_t)d);
+        orc_tangents tg = {work + 3 * d, work + 4 * d, work + 5 * d, work + 6 * d, work + 7 * d, work + 8 * d};
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            orc_pathstats ps;
+            gbm_path(&m, path0 + n, NULL, 0, 0, 0, NULL, &ps, &tg, work);
+            for (int p = 0; p < npay; ++p) {
+                double slope = payoff_slope(kind[p], strike[p], &ps);
+                double f = payoff_value(kind[p], strike[p], 0.0, &ps);
+                int asian = payoff_is_asian(kind[p]);
+                double dr = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double dS0 = asian ? tg.aS0[a] : m.w[a] * tg.tS0[a];
+                    double dsg = asian ? tg.asig[a] : m.w[a] * tg.tsig[a];
+                    dr += asian ? tg.ar[a] : m.w[a] * tg.tr[a];
+                    g[((size_t)p * ng + a) * npaths + n] = disc * slope * dS0;
+                    g[((size_t)p * ng + d + a) * npaths + n] = disc * slope * dsg;
+                }
+                g[((size_t)p * ng + 2 * d) * npaths + n] = disc * (slope * dr - T * f);
+            }
+        }
+        free(work);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Heston stochastic volatility (Sec. II.A.1 names stochastic-volatility     */
+/* extensions of the scalar Euler scheme), full-truncation Euler on          */
+/* (x = log S, v), two normals per step: z1 = normal 2i, z2 = normal 2i+1.   */
+/*   v+ = max(v, 0)                                                          */
+/*   x <- x + (r - v+/2) Delta + sqrt(v+ Delta) (rho z1 + sqrt(1-rho^2) z2)  */
+/*   v <- v + kappa (theta - v+) Delta + xi sqrt(v+ Delta) z1                */
+/* both right-hand sides use the state before the step.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double s0, v0, r, kappa, theta, xi, rho, T;
+    int steps;
+    uint64_t seed;
+} orc_heston;
+
+/* tangent index order: 0 S0, 1 v0, 2 r, 3 kappa, 4 theta, 5 xi, 6 rho */
+#define ORC_HN 7
+
+static void heston_path(const orc_heston *h, int64_t n, double *save, int64_t col, int save_every, int64_t ld,
+                        orc_pathstats *stats, double *dST /* [7] or NULL */, double *dAvg /* [7] */)
+{
+    const int M = h->steps;
+    const double dt = h->T / M;
+    const double rc = sqrt(1.0 - h->rho * h->rho);
+    orc_stream st;
+    stream_init(&st, h->seed, (uint64_t)n);
+    double x = log(h->s0), v = h->v0;
+    double tx[ORC_HN] = {0}, tv[ORC_HN] = {0}, ta[ORC_HN] = {0};
+    tx[0] = 1.0 / h->s0;
+    tv[1] = 1.0;
+    if (save) { save[col] = h->s0; save[ld + col] = h->v0; }
+    double sum = 0.0, umax = -INFINITY, umin = INFINITY, S = h->s0;
+    for (int i = 0; i < M; ++i) {
+        double z1 = stream_normal(&st, 2 * (uint64_t)i);
+        double z2 = stream_normal(&st, 2 * (uint64_t)i + 1);
+        double vp = v > 0.0 ? v : 0.0;
+        double sq = sqrt(vp * dt);
+        double c = h->rho * z1 + rc * z2;
+        double xn = x + (h->r - 0.5 * vp) * dt + sq * c;
+        double vn = v + h->kappa * (h->theta - vp) * dt + h->xi * sq * z1;
+        if (dST) {
+            for (int k = 0; k < ORC_HN; ++k) {
+                double dvp = v > 0.0 ? tv[k] : 0.0;
+                /* d sqrt(v+ dt) = dt dv+ / (2 sqrt(v+ dt)) for v+ > 0, 0 otherwise */
+                double dsq = vp > 0.0 ? dt * dvp / (2.0 * sq) : 0.0;
+                double dc = (k == 6) ? (z1 - h->rho / rc * z2) : 0.0;
+                double dr = (k == 2) ? 1.0 : 0.0;
+                double dkap = (k == 3) ? 1.0 : 0.0, dth = (k == 4) ? 1.0 : 0.0, dxi = (k == 5) ? 1.0 : 0.0;
+                double ntx = tx[k] + (dr - 0.5 * dvp) * dt + dsq * c + sq * dc;
+                double ntv = tv[k] + (dkap * (h->theta - vp) + h->kappa * (dth - dvp)) * dt
+                             + (dxi * sq + h->xi * dsq) * z1;
+                tx[k] = ntx; tv[k] = ntv;
+            }
+        }
+        x = xn; v = vn;
+        S = exp(x);
+        sum += S;
+        if (S > umax) umax = S;
+        if (S < umin) umin = S;
+        if (dST) for (int k = 0; k < ORC_HN; ++k) ta[k] += S * tx[k] / M;
+        if (save && save_every > 0 && (i + 1) % save_every == 0) {
+            int slot = (i + 1) / save_every;
+            save[((size_t)slot * 2) * ld + col] = S;
+            save[((size_t)slot * 2 + 1) * ld + col] = v;
+        }
+    }
+    if (stats) { stats->u_T = S; stats->avg = sum / M; stats->umax = umax; stats->umin = umin; }
+    if (dST) for (int k = 0; k < ORC_HN; ++k) { dST[k] = S * tx[k]; dAvg[k] = ta[k]; }
+}
+
+static int heston_check(double v0, double kappa, double theta, double xi, double rho, double T, int steps)
+{
+    if (steps < 1 || !(T > 0.0) || !(rho > -1.0 && rho < 1.0) || v0 < 0.0 || kappa < 0.0 || theta < 0.0 || xi < 0.0)
+        return -1;
+    return 0;
+}
+
+int orc_heston_payoffs(double s0, double v0, double r, double kappa, double theta, double xi, double rho,
+                       double T, int steps, uint64_t seed, int64_t path0, int64_t npaths,
+                       int npay, const int *kind, const double *strike, const double *barrier, double *out)
+{
+    if (heston_check(v0, kappa, theta, xi, rho, T, steps) || npaths < 0) return -1;
+    orc_heston h = {s0, v0, r, kappa, theta, xi, rho, T, steps, seed};
+    const double disc = exp(-r * T);
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < npaths; ++n) {
+        orc_pathstats ps;
+        heston_path(&h, path0 + n, NULL, 0, 0, 0, &ps, NULL, NULL);
+        for (int p = 0; p < npay; ++p)
+            out[(size_t)p * npaths + n] = disc * payoff_value(kind[p], strike[p], barrier[p], &ps);
+    }
+    return 0;
+}
+
+/* save[(slot*2 + c)*npaths + n]: c = 0 price S, c = 1 variance v (before truncation). */
+int orc_heston_paths(double s0, double v0, double r, double kappa, double theta, double xi, double rho,
+                     double T, int steps, uint64_t seed, int64_t path0, int64_t npaths,
+                     int save_every, double *save)
+{
+    if (heston_check(v0, kappa, theta, xi, rho, T, steps) || npaths < 0 || save_every < 1 || steps % save_every)
+        return -1;
+    orc_heston h = {s0, v0, r, kappa, theta, xi, rho, T, steps, seed};
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < npaths; ++n)
+        heston_path(&h, path0 + n, save, n, save_every, npaths, NULL, NULL, NULL);
+    return 0;
+}
+
+/* Forward-mode pathwise Greeks of the Heston pricer, discounted, per path:
+ * g[(p*7 + k)*npaths + n], k: 0 d/dS0, 1 d/dv0, 2 d/dr (with the -T P term),
+ * 3 d/dkappa, 4 d/dtheta, 5 d/dxi, 6 d/drho.  European and Asian kinds only. */
+int orc_heston_greeks(double s0, double v0, double r, double kappa, double theta, double xi, double rho,
+                      double T, int steps, uint64_t seed, int64_t path0, int64_t npaths,
+                      int npay, const int *kind, const double *strike, double *g)
+{
+    if (heston_check(v0, kappa, theta, xi, rho, T, steps) || npaths < 0) return -1;
+    for (int p = 0; p < npay; ++p)
+        if (kind[p] > ORC_ASIAN_PUT || kind[p] < 0) return -4;
+    orc_heston h = {s0, v0, r, kappa, theta, xi, rho, T, steps, seed};
+    const double disc = exp(-r * T);
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < npaths; ++n) {
+        orc_pathstats ps;
+        double dST[ORC_HN], dAvg[ORC_HN];
+        heston_path(&h, path0 + n, NULL, 0, 0, 0, &ps, dST, dAvg);
+        for (int p = 0; p < npay; ++p) {
+            double slope = payoff_slope(kind[p], strike[p], &ps);
+            double f = payoff_value(kind[p], strike[p], 0.0, &ps);
+            const double *dU = payoff_is_asian(kind[p]) ? dAvg : dST;
+            for (int k = 0; k < ORC_HN; ++k) {
+                double v = disc * slope * dU[k];
+                if (k == 2) v -= T * disc * f;
+                g[((size_t)p * ORC_HN + k) * npaths + n] = v;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Estimator (Eq. 3): mean of N samples and its standard error             */
+/*   se = sqrt((sum f^2 / N - mean^2) / (N - 1)),                           */
+/* with Neumaier-compensated sums taken in index order.                      */
+/* ------------------------------------------------------------------------ */
+static void neumaier_add(double *sum, double *comp, double b)
+{
+    double a = *sum, t = a + b;
+    *comp += (fabs(a) >= fabs(b)) ? (a - t) + b : (b - t) + a;
+    *sum = t;
+}
+
+void orc_mean_se(const double *f, int64_t n, double *mean, double *se)
+{
+    double s = 0.0, cs = 0.0, q = 0.0, cq = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        neumaier_add(&s, &cs, f[i]);
+        neumaier_add(&q, &cq, f[i] * f[i]);
+    }
+    double m = (s + cs) / (double)n;
+    double m2 = (q + cq) / (double)n;
+    *mean = m;
+    *se = n > 1 ? sqrt(fmax(m2 - m * m, 0.0) / (double)(n - 1)) : 0.0;
+}

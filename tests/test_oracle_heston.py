@@ -1,0 +1,97 @@
+"""Pins of the oracle's Heston full-truncation Euler pricer."""
+import cmath
+from math import exp, log, pi
+
+import numpy as np
+import pytest
+
+import closed_forms as cf
+
+BASE = dict(s0=100.0, v0=0.04, r=0.05, kappa=2.0, theta=0.04, xi=0.5, rho=-0.7)
+
+
+def heston_call_semi_closed(S, K, r, T, v0, kappa, theta, xi, rho):
+    """Heston (1993) call via the characteristic function of log S_T in the
+    rotation-free ("little trap") form, integrated numerically."""
+    from scipy.integrate import quad
+
+    def phi(u):
+        iu = 1j * u
+        b = kappa - rho * xi * iu
+        d = cmath.sqrt(b * b + xi * xi * (iu + u * u))
+        g = (b - d) / (b + d)
+        e = cmath.exp(-d * T)
+        C = kappa * theta / xi ** 2 * ((b - d) * T - 2.0 * cmath.log((1 - g * e) / (1 - g)))
+        D = (b - d) / xi ** 2 * (1 - e) / (1 - g * e)
+        return cmath.exp(iu * (log(S) + r * T) + C + D * v0)
+
+    lnK = log(K)
+    f0 = phi(-1j)
+
+    def p1(u):
+        return (cmath.exp(-1j * u * lnK) * phi(u - 1j) / (1j * u * f0)).real
+
+    def p2(u):
+        return (cmath.exp(-1j * u * lnK) * phi(u) / (1j * u)).real
+
+    P1 = 0.5 + quad(p1, 1e-10, 200.0, limit=400)[0] / pi
+    P2 = 0.5 + quad(p2, 1e-10, 200.0, limit=400)[0] / pi
+    return S * P1 - K * exp(-r * T) * P2
+
+
+def test_xi_zero_reduces_to_black_scholes(orc):
+    h = dict(BASE, xi=0.0)  # v stays at theta = v0 = 0.04: GBM with sigma = 0.2
+    pays = [dict(kind="call", strike=K) for K in (90.0, 100.0, 110.0)]
+    f = orc.heston_payoffs(h, 1.0, 32, 1 << 17, pays)
+    for row, p in zip(f, pays):
+        m, se = orc.mean_se(row)
+        assert abs(m - cf.bs_call(100.0, p["strike"], 0.05, 0.2, 1.0)) <= 3 * se, (p, m, se)
+    P = orc.heston_paths(h, 1.0, 32, 256, save_every=32)
+    assert np.all(P[:, 1] == 0.04)
+
+
+def test_discounted_price_is_martingale(orc):
+    """Given the state, the log increment is normal with mean (r - v+/2) D and
+    variance v+ D, so e^{-rT} E[S_T] = S0 holds exactly for the scheme."""
+    N = 1 << 17
+    P = orc.heston_paths(BASE, 1.0, 64, N, save_every=64)
+    x = np.exp(-0.05) * P[-1, 0]
+    assert abs(x.mean() - 100.0) <= 3 * x.std(ddof=1) / np.sqrt(N)
+
+
+def test_variance_mean_reverts(orc):
+    """With the Feller condition comfortably met (2 kappa theta >> xi^2) the
+    truncation is never active and E[v_i] = theta when v0 = theta."""
+    h = dict(BASE, xi=0.1)
+    N = 1 << 16
+    P = orc.heston_paths(h, 1.0, 64, N, save_every=16)
+    for i in range(P.shape[0]):
+        v = P[i, 1]
+        assert abs(v.mean() - 0.04) <= 3 * v.std(ddof=1) / np.sqrt(N) + 1e-15
+    # v0 != theta: E[v] follows v_{i+1} = v_i + kappa (theta - v_i) D exactly
+    h2 = dict(h, v0=0.09)
+    P2 = orc.heston_paths(h2, 1.0, 64, N, save_every=64)
+    want = 0.04 + (0.09 - 0.04) * (1 - 2.0 / 64) ** 64
+    v = P2[-1, 1]
+    assert abs(v.mean() - want) <= 3 * v.std(ddof=1) / np.sqrt(N)
+
+
+def test_leverage_sign(orc):
+    """rho < 0 skews log returns to the left; rho > 0 to the right."""
+    N = 1 << 15
+    for rho, sign in [(-0.7, -1), (0.7, 1)]:
+        P = orc.heston_paths(dict(BASE, rho=rho), 1.0, 64, N, save_every=64)
+        x = np.log(P[-1, 0])
+        skew = np.mean((x - x.mean()) ** 3) / x.std() ** 3
+        assert np.sign(skew) == sign
+
+
+@pytest.mark.parametrize("K", [80.0, 100.0, 120.0])
+def test_semi_closed_form_within_bias(orc, K):
+    """Euler bias of full truncation at 256 steps is small but not zero: the
+    oracle must land within 3 SE plus a stated 0.5 % of the price (a dropped
+    term or a sign error on rho moves the price by several percent)."""
+    f = orc.heston_payoffs(BASE, 1.0, 256, 1 << 16, [dict(kind="call", strike=K)])
+    m, se = orc.mean_se(f[0])
+    exact = heston_call_semi_closed(100.0, K, 0.05, 1.0, 0.04, 2.0, 0.04, 0.5, -0.7)
+    assert abs(m - exact) <= 3 * se + 0.005 * exact, (m, se, exact)
