@@ -1,0 +1,168 @@
+/*
+ * gbmc -- GB300-native financial Monte Carlo (C ABI).
+ *
+ * The library simulates many independent discretised SDE paths (Eq. 1 of
+ * Belletti et al., "Tensor Processing Units for Financial Monte Carlo", 2019),
+ * evaluates path payoffs and returns the Monte Carlo estimator of Eq. 3 with
+ * its standard error.  All simulation work runs in the library's CUDA kernels
+ * on the device that is current on the calling thread.
+ *
+ * Conventions shared by every entry point
+ *   - Host pointers are read during the call only; the library copies what it
+ *     needs and never frees caller memory.  Device pointers are caller-owned.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Entry
+ *     points that return host results synchronise that stream before
+ *     returning; mc_plan_execute is asynchronous.
+ *   - Every entry point returns an mc_status.  On error no output is written,
+ *     and mc_last_error() returns a thread-local message.  No entry point
+ *     throws, aborts or exits.
+ *   - Random numbers: Philox4x32-10 (Sec. IV.A), key = (seed mod 2^32,
+ *     seed div 2^32).  Normal j of path n (global index, path_offset included)
+ *     comes from the block at counter (j/4 mod 2^32, j/4 div 2^32, n mod 2^32,
+ *     n div 2^32), lane j mod 4, with Box-Muller (Sec. VI.D) on lanes (0,1)
+ *     and (2,3) and uniforms u(x) = (floor(x/2^9) + 1/2) 2^-23.  Step i of a
+ *     d-asset GBM uses normals i*d .. i*d+d-1; step i of Heston uses 2i (the
+ *     variance shock) and 2i+1.  Results therefore do not depend on the launch
+ *     shape, and disjoint path_offset ranges give independent sub-runs.
+ */
+#ifndef GBMC_MC_H
+#define GBMC_MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_VERSION 10000 /* major*10000 + minor*100 + patch */
+
+typedef enum {
+    MC_OK = 0,
+    MC_EINVAL = -1,        /* an argument is out of range or inconsistent */
+    MC_ENOTPSD = -2,       /* the correlation matrix is not positive definite */
+    MC_ENOMEM = -3,        /* device or host allocation failed */
+    MC_ECUDA = -4,         /* a CUDA runtime call failed (message has the name) */
+    MC_ETIMEOUT = -5,      /* a bounded device wait ran out */
+    MC_EUNSUPPORTED = -6   /* valid request this build cannot serve */
+} mc_status;
+
+typedef enum {
+    MC_GBM = 0,    /* d >= 1 correlated geometric Brownian motions (Sec. II.A.1, II.A.2) */
+    MC_HESTON = 1  /* single-asset Heston stochastic volatility, full-truncation Euler */
+} mc_model_kind;
+
+typedef enum {
+    MC_LOG_EULER = 0, /* Euler step on log S: exact in law at the grid for GBM */
+    MC_EULER = 1      /* Euler-Maruyama step on S itself, as written in Sec. II.A.1 */
+} mc_scheme;
+
+/* Arithmetic of the correlation contraction dW = sqrt(dt) diag(sigma) L z
+ * (Sec. II.A.2, Sec. V.A).  The state, the payoffs and all accumulators stay
+ * FP32 whatever this is; FP64 is used only in the final cross-block sum and in
+ * the Cholesky factorisation. */
+typedef enum {
+    MC_FP32 = 0,
+    MC_BF16 = 1,     /* tensor cores, bf16 operands, FP32 accumulation */
+    MC_FP16 = 2,     /* tensor cores, fp16 operands, FP32 accumulation */
+    MC_FP8E4M3 = 3   /* tensor cores, e4m3 operands with per-step scale, FP32 accumulation */
+} mc_precision;
+
+typedef struct {
+    int32_t kind;          /* mc_model_kind */
+    int32_t d;             /* assets; MC_HESTON requires d == 1 */
+    const double *s0;      /* host [d] spot prices, > 0 */
+    const double *sigma;   /* host [d] volatilities >= 0 (MC_GBM) */
+    const double *corr;    /* host [d*d] row-major correlation matrix (unit diagonal,
+                              symmetric, positive definite), or NULL for identity */
+    const double *weights; /* host [d] basket weights, or NULL for 1/d each */
+    double r;              /* risk-free rate: drift of every asset and discount rate */
+    double v0, kappa, theta, xi, rho; /* MC_HESTON only: dv = kappa (theta - v) dt + xi sqrt(v) dW1,
+                                         d<W1, W2> = rho dt, |rho| < 1 */
+} mc_model;
+
+typedef struct {
+    int32_t scheme;        /* mc_scheme (MC_GBM); MC_HESTON always uses full-truncation Euler */
+    int32_t steps;         /* M >= 1 equal steps of dt = T / M */
+    double T;              /* maturity > 0 */
+    int64_t paths;         /* N >= 1 */
+    int64_t path_offset;   /* global index of the first path (for sharding / resume) */
+    uint64_t seed;         /* Philox key */
+    int32_t precision;     /* mc_precision of the correlation contraction */
+    int32_t ckpt_every;    /* adjoint checkpoint stride in steps (0 = 32) */
+} mc_sim_cfg;
+
+/* Payoffs on the monitored underlying U(t) = sum_a w_a S_a(t) (U = S for d = 1),
+ * observed at t_i = i T / M, i = 1..M (Sec. I.A.2).  Barrier kinds: up-and-out
+ * is knocked out when max_i U(t_i) >= barrier, down-and-out when
+ * min_i U(t_i) <= barrier; "in" kinds are alive exactly when the matching
+ * "out" kind is dead.  Asian kinds use (1/M) sum_{i=1..M} U(t_i). */
+typedef enum {
+    MC_CALL = 0, MC_PUT = 1, MC_ASIAN_CALL = 2, MC_ASIAN_PUT = 3,
+    MC_UO_CALL = 4, MC_UI_CALL = 5, MC_UO_PUT = 6, MC_UI_PUT = 7,
+    MC_DO_CALL = 8, MC_DI_CALL = 9, MC_DO_PUT = 10, MC_DI_PUT = 11
+} mc_payoff_kind;
+
+#define MC_MAX_PAYOFFS 32
+
+typedef struct {
+    int32_t kind;          /* mc_payoff_kind */
+    double strike;
+    double barrier;        /* ignored by non-barrier kinds */
+} mc_payoff;
+
+typedef struct {
+    double price;          /* e^{-rT} (1/N) sum_n f(path n): the estimator of Eq. 3 */
+    double se;             /* its standard error sqrt((mean(f^2) - mean(f)^2) / (N - 1)), discounted */
+} mc_result;
+
+/* Library version (MC_VERSION of the build). */
+int mc_version(void);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char *mc_last_error(void);
+
+/*
+ * mc_simulate -- materialise simulated paths (Sec. II.A.1 / II.A.2 scheme).
+ *   dev_out: caller-owned DEVICE buffer of float32, layout
+ *            [steps/save_every + 1][D][paths], D = d for MC_GBM (asset prices)
+ *            and D = 2 for MC_HESTON (price, variance before truncation);
+ *            slot k holds the state after k*save_every steps (slot 0 = t_0).
+ *   save_every must divide steps.  Runs on `stream` and synchronises it
+ *   before returning.
+ */
+int mc_simulate(const mc_model *model, const mc_sim_cfg *cfg, int32_t save_every,
+                float *dev_out, void *stream);
+
+/*
+ * mc_price -- discounted Monte Carlo prices of n_payoff payoffs on the same
+ * simulated paths (Eq. 3), with standard errors.
+ *   out: host [n_payoff] results.  1 <= n_payoff <= MC_MAX_PAYOFFS.
+ * Synchronises `stream` before returning.
+ */
+int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs,
+             int32_t n_payoff, mc_result *out, void *stream);
+
+/*
+ * Plans: the same computation as mc_price split into a set-up phase (argument
+ * checks, upload of the model, FP64 Cholesky factorisation on the device,
+ * scaled copies of the factor, device scratch for per-block partial sums)
+ * and an asynchronous execution that launches only the path kernels and the
+ * final FP64 reduction.  A plan may be executed any number of times on any
+ * stream of the device it was created on, but executions of one plan must
+ * not overlap in time (they share the plan's scratch).
+ *   mc_plan_execute: dev_out is a DEVICE buffer of n_payoff mc_result.
+ */
+typedef struct mc_plan mc_plan;
+int mc_plan_create(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs,
+                   int32_t n_payoff, mc_plan **plan, void *stream);
+int mc_plan_execute(mc_plan *plan, mc_result *dev_out, void *stream);
+int mc_plan_destroy(mc_plan *plan);
+
+/* Number of kernel launches one mc_plan_execute issues (for accounting). */
+int mc_plan_launches(const mc_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMC_MC_H */

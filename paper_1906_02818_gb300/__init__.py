@@ -1,0 +1,16 @@
+"""gbmc: GB300-native financial Monte Carlo (Belletti et al., 2019, the
+data-parallel path: Philox normals, correlated Euler / log-Euler steps, path
+payoffs, FP64-finished estimator with standard errors).
+
+The compute path is the CUDA library libgbmc.so (C ABI in include/mc.h); this
+package is its thin binding.  Importing it does not load CUDA; the first call
+loads the library and raises if it is missing.
+"""
+from .native import MCError, PAYOFF, PRECISION, SCHEME  # noqa: F401
+
+
+def __getattr__(name):
+    if name in ("price", "simulate", "Plan"):
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)

@@ -1,0 +1,156 @@
+// FP32 correlated-basket path kernel (the multivariate Euler-Maruyama scheme
+// of Sec. II.A.2), instantiated per basket width D in separate translation
+// units so that they compile in parallel.  The contraction dW = Lhat z runs
+// in FP32 FMAs with the packed factor in the launch-parameter block
+// (constant bank): every FMA takes its factor entry as a constant operand.
+#pragma once
+
+#include "mc_kernels.cuh"
+
+namespace gbmc {
+
+// Kernel entry for width D and the given scheme, chosen by the flags of `a`
+// (explicitly instantiated in k_basket_*.cu).
+template <int D, int SCHEME>
+const void *basket_select_scheme(const BasketArgs &a);
+
+#ifdef GBMC_BASKET_IMPL
+namespace basket_detail {
+
+constexpr int kBlock = 256;
+
+struct Stats {
+    float sum, umax, umin;
+    __device__ __forceinline__ void init() { sum = 0.0f; umax = -INFINITY; umin = INFINITY; }
+    __device__ __forceinline__ void add(float u) { sum += u; umax = fmaxf(umax, u); umin = fminf(umin, u); }
+};
+
+__device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet &pay, bool valid,
+                                                   float uT, float avg, const Stats &st)
+{
+    for (int p = 0; p < pay.n; ++p) {
+        float f = payoff_eval(pay.kind[p], pay.strike[p], pay.barrier[p], uT, avg, st.umax, st.umin);
+        warp_accumulate(s_acc, pay.n, p, valid ? f : 0.0f);
+    }
+}
+
+// ------------------------------ FP32 basket -------------------------------
+template <int D, int SCHEME, bool STATS, bool SAVE, bool EXACT>
+__global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const BasketArgs a, const BasketConst<D> c)
+{
+    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ double s_red[32];
+    for (int i = threadIdx.x; i < (kBlock / 32) * a.pay.n * 2; i += blockDim.x) s_acc[i] = 0.0f;
+    __syncthreads();
+
+    const int64_t gthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int M = a.run.steps, d = a.d;
+    const float inv_m = 1.0f / static_cast<float>(M);
+    for (int it = 0; it < a.run.ppt; ++it) {
+        const int64_t nl = tid + it * gthreads;
+        const bool valid = nl < a.run.paths;
+        float uT = 0.0f, avg = 0.0f;
+        Stats st;
+        st.init();
+        if (valid) {
+            const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
+            float x[D];  // log-Euler: log2(S_a / S0_a); Euler: S_a
+#pragma unroll
+            for (int j = 0; j < D; ++j) x[j] = (SCHEME == MC_LOG_EULER) ? 0.0f : c.s0[j];
+            if (SAVE) {
+                for (int j = 0; j < d; ++j) a.run.save[static_cast<int64_t>(j) * a.run.paths + nl] = c.s0[j];
+            }
+            NormalReader rd;
+            rd.init(n, a.run.k0, a.run.k1);
+            for (int i = 0; i < M; ++i) {
+                // dW is accumulated apart from the state so that the O(1) state
+                // takes one rounding per step instead of one per FMA.
+                float dw[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) dw[j] = 0.0f;
+                // dW = Lhat z, column by column as the normals are produced.
+#pragma unroll
+                for (int kb = 0; kb < D / 4 + (D % 4 ? 1 : 0); ++kb) {
+                    float zz[4];
+                    if (EXACT) {
+                        const float4 z4 = normals4(static_cast<uint64_t>(i) * (D / 4) + kb, n, a.run.k0, a.run.k1);
+                        zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) {
+                            const int k = 4 * kb + l;
+                            zz[l] = (k < D && k < d) ? rd.get(static_cast<uint64_t>(i) * d + k) : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const int k = 4 * kb + l;
+                        if (k < D) {
+#pragma unroll
+                            for (int j = k; j < D; ++j) dw[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], dw[j]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    if (SCHEME == MC_EULER) x[j] = fmaf(x[j], c.drift[j] + dw[j], x[j]);
+                    else x[j] += c.drift[j] + dw[j];
+                }
+                if (STATS || (SAVE && ((i + 1) % a.run.save_every) == 0)) {
+                    float u = 0.0f;
+                    const int64_t slot = (i + 1) / a.run.save_every;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * exp2f(x[j]) : x[j];
+                        if (STATS) u = fmaf(c.w[j], Sj, u);
+                        if (SAVE && ((i + 1) % a.run.save_every) == 0 && j < d)
+                            a.run.save[(slot * d + j) * a.run.paths + nl] = Sj;
+                    }
+                    if (STATS) st.add(u);
+                }
+            }
+            float u = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                if (SCHEME == MC_LOG_EULER) u = fmaf(c.ws0[j], exp2f(x[j]), u);
+                else u = fmaf(c.w[j], x[j], u);
+            }
+            uT = u;
+            avg = st.sum * inv_m;
+        }
+        if (a.pay.n > 0) accumulate_payoffs(s_acc, a.pay, valid, uT, avg, st);
+    }
+    if (a.pay.n > 0) block_finish(s_acc, s_red, a.pay.n, a.red);
+}
+
+template <int D, int SCHEME, bool STATS, bool SAVE, bool EXACT>
+const void *basket_fn()
+{
+    return reinterpret_cast<const void *>(&basket_fp32_kernel<D, SCHEME, STATS, SAVE, EXACT>);
+}
+
+template <int D, int SCHEME>
+const void *basket_select_impl(const BasketArgs &a)
+{
+    const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
+    const bool save = a.run.save != nullptr;
+    const bool exact = (a.d == D) && (D % 4 == 0);
+    if (save) return basket_fn<D, SCHEME, false, true, false>();
+    if (stats) return exact ? basket_fn<D, SCHEME, true, false, true>() : basket_fn<D, SCHEME, true, false, false>();
+    return exact ? basket_fn<D, SCHEME, false, false, true>() : basket_fn<D, SCHEME, false, false, false>();
+}
+
+}  // namespace basket_detail
+
+template <int D, int SCHEME>
+const void *basket_select_scheme(const BasketArgs &a)
+{
+    return basket_detail::basket_select_impl<D, SCHEME>(a);
+}
+
+#define GBMC_INSTANTIATE_BASKET(D, SCHEME) \
+    template const void *basket_select_scheme<D, SCHEME>(const BasketArgs &a);
+#endif  // GBMC_BASKET_IMPL
+
+}  // namespace gbmc

@@ -1,0 +1,87 @@
+// FP64 linear algebra of the set-up phase: the Cholesky factor of the asset
+// correlation (Sec. II.A.2 needs a factor sigma with sigma sigma^T equal to
+// the covariance; Sec. II.A.3 uses the same factorisation for the Grammian)
+// and its scaled FP32 copy for the FP32 contraction.
+#include "mc_kernels.cuh"
+
+namespace gbmc {
+
+namespace {
+
+constexpr int kCholBlock = 1024;
+
+// Right-looking Cholesky, one CTA, in place on W (initialised with A).
+// status: 0 ok, 1 a pivot was not positive (A not positive definite).
+__global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const double *A, double *W, int *status)
+{
+    __shared__ int s_fail;
+    for (int64_t idx = threadIdx.x; idx < static_cast<int64_t>(d) * d; idx += blockDim.x) W[idx] = A[idx];
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    for (int k = 0; k < d; ++k) {
+        if (threadIdx.x == 0) {
+            const double p = W[static_cast<int64_t>(k) * d + k];
+            if (!(p > 0.0)) s_fail = 1;
+            else W[static_cast<int64_t>(k) * d + k] = sqrt(p);
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const double lkk = W[static_cast<int64_t>(k) * d + k];
+        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[static_cast<int64_t>(i) * d + k] /= lkk;
+        __syncthreads();
+        const int m = d - k - 1;
+        for (int64_t idx = threadIdx.x; idx < static_cast<int64_t>(m) * m; idx += blockDim.x) {
+            const int ii = static_cast<int>(idx / m), jj = static_cast<int>(idx % m);
+            if (jj <= ii) {
+                const int i = k + 1 + ii, j = k + 1 + jj;
+                W[static_cast<int64_t>(i) * d + j] -= W[static_cast<int64_t>(i) * d + k] * W[static_cast<int64_t>(j) * d + k];
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (!s_fail) {
+        for (int64_t idx = threadIdx.x; idx < static_cast<int64_t>(d) * d; idx += blockDim.x) {
+            const int i = static_cast<int>(idx / d), j = static_cast<int>(idx % d);
+            if (j > i) W[idx] = 0.0;
+        }
+    }
+    if (threadIdx.x == 0) *status = s_fail;
+}
+
+__global__ void scale_factor_kernel(int d, const double *L, const double *sigma, double c, double sdt,
+                                    double r, double dt, int scheme, float *Lp, float *drift)
+{
+    const int64_t tot = static_cast<int64_t>(d) * (d + 1) / 2;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < tot;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        // packed lower triangle: row a at a(a+1)/2
+        int a = static_cast<int>((sqrt(8.0 * static_cast<double>(idx) + 1.0) - 1.0) * 0.5);
+        while (static_cast<int64_t>(a + 1) * (a + 2) / 2 <= idx) ++a;
+        while (static_cast<int64_t>(a) * (a + 1) / 2 > idx) --a;
+        const int k = static_cast<int>(idx - static_cast<int64_t>(a) * (a + 1) / 2);
+        Lp[idx] = static_cast<float>(c * sdt * sigma[a] * L[static_cast<int64_t>(a) * d + k]);
+    }
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < d; a += gridDim.x * blockDim.x)
+        drift[a] = static_cast<float>(scheme == MC_LOG_EULER ? c * (r - 0.5 * sigma[a] * sigma[a]) * dt : r * dt);
+}
+
+}  // namespace
+
+cudaError_t launch_cholesky(int d, const double *A, double *L, int *status, cudaStream_t s)
+{
+    cholesky_kernel<<<1, kCholBlock, 0, s>>>(d, A, L, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_factor(int d, const double *L, const double *sigma, double c, double sdt,
+                                double r, double dt, int scheme, float *Lpacked, float *drift,
+                                cudaStream_t s)
+{
+    const int64_t tot = static_cast<int64_t>(d) * (d + 1) / 2;
+    const int grid = static_cast<int>((tot + 255) / 256 > 1024 ? 1024 : (tot + 255) / 256);
+    scale_factor_kernel<<<grid, 256, 0, s>>>(d, L, sigma, c, sdt, r, dt, scheme, Lpacked, drift);
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

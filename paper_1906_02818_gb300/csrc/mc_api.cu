@@ -1,0 +1,426 @@
+// Host runtime and C ABI (include/mc.h): argument checks, plan set-up (model
+// upload, FP64 Cholesky on the device, scaled factor, persistent-grid sizing,
+// scratch for per-block partials), kernel dispatch and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mc_kernels.cuh"
+
+using namespace gbmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define MC_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA, "%s: %s (%s)", \
+                        #call, cudaGetErrorName(e_), cudaGetErrorString(e_));                  \
+    } while (0)
+
+bool finite_all(const double *p, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+int check_model(const mc_model *m)
+{
+    if (!m) return fail(MC_EINVAL, "model is NULL");
+    if (m->kind != MC_GBM && m->kind != MC_HESTON) return fail(MC_EINVAL, "unknown model kind %d", m->kind);
+    if (m->d < 1 || m->d > 4096) return fail(MC_EINVAL, "d = %d out of range [1, 4096]", m->d);
+    if (!m->s0) return fail(MC_EINVAL, "s0 is NULL");
+    if (!std::isfinite(m->r)) return fail(MC_EINVAL, "r is not finite");
+    for (int a = 0; a < m->d; ++a)
+        if (!(m->s0[a] > 0.0) || !std::isfinite(m->s0[a])) return fail(MC_EINVAL, "s0[%d] must be finite and > 0", a);
+    if (m->kind == MC_HESTON) {
+        if (m->d != 1) return fail(MC_EINVAL, "Heston requires d == 1");
+        const double v[5] = {m->v0, m->kappa, m->theta, m->xi, m->rho};
+        if (!finite_all(v, 5)) return fail(MC_EINVAL, "Heston parameters must be finite");
+        if (m->v0 < 0 || m->kappa < 0 || m->theta < 0 || m->xi < 0)
+            return fail(MC_EINVAL, "Heston v0, kappa, theta, xi must be >= 0");
+        if (!(m->rho > -1.0 && m->rho < 1.0)) return fail(MC_EINVAL, "Heston rho must lie in (-1, 1)");
+        return MC_OK;
+    }
+    if (!m->sigma) return fail(MC_EINVAL, "sigma is NULL");
+    for (int a = 0; a < m->d; ++a)
+        if (!(m->sigma[a] >= 0.0) || !std::isfinite(m->sigma[a])) return fail(MC_EINVAL, "sigma[%d] must be finite and >= 0", a);
+    if (m->weights && !finite_all(m->weights, m->d)) return fail(MC_EINVAL, "weights must be finite");
+    if (m->corr) {
+        const int d = m->d;
+        if (!finite_all(m->corr, static_cast<int64_t>(d) * d)) return fail(MC_EINVAL, "corr must be finite");
+        for (int i = 0; i < d; ++i) {
+            if (std::fabs(m->corr[static_cast<int64_t>(i) * d + i] - 1.0) > 1e-12)
+                return fail(MC_EINVAL, "corr[%d][%d] must be 1 (unit diagonal)", i, i);
+            for (int j = 0; j < i; ++j) {
+                const double a = m->corr[static_cast<int64_t>(i) * d + j], b = m->corr[static_cast<int64_t>(j) * d + i];
+                if (std::fabs(a - b) > 1e-12 * (1.0 + std::fabs(a)))
+                    return fail(MC_EINVAL, "corr is not symmetric at (%d, %d)", i, j);
+                if (std::fabs(a) > 1.0) return fail(MC_EINVAL, "corr[%d][%d] = %g outside [-1, 1]", i, j, a);
+            }
+        }
+    }
+    return MC_OK;
+}
+
+int check_cfg(const mc_sim_cfg *c, const mc_model *m)
+{
+    if (!c) return fail(MC_EINVAL, "cfg is NULL");
+    if (c->steps < 1) return fail(MC_EINVAL, "steps = %d must be >= 1", c->steps);
+    if (!(c->T > 0.0) || !std::isfinite(c->T)) return fail(MC_EINVAL, "T must be finite and > 0");
+    if (c->paths < 1) return fail(MC_EINVAL, "paths = %lld must be >= 1", static_cast<long long>(c->paths));
+    if (c->path_offset < 0 || c->path_offset + c->paths > (int64_t(1) << 56))
+        return fail(MC_EINVAL, "path range must lie in [0, 2^56)");
+    if (c->scheme != MC_LOG_EULER && c->scheme != MC_EULER) return fail(MC_EINVAL, "unknown scheme %d", c->scheme);
+    if (c->precision < MC_FP32 || c->precision > MC_FP8E4M3) return fail(MC_EINVAL, "unknown precision %d", c->precision);
+    if (c->ckpt_every < 0) return fail(MC_EINVAL, "ckpt_every must be >= 0");
+    if (m->kind == MC_HESTON && c->precision != MC_FP32)
+        return fail(MC_EINVAL, "Heston has no correlation contraction: precision must be MC_FP32");
+    return MC_OK;
+}
+
+int build_payoffs(const mc_payoff *p, int np, PayoffSet *ps)
+{
+    if (np < 0 || np > MC_MAX_PAYOFFS) return fail(MC_EINVAL, "n_payoff = %d out of range [0, %d]", np, MC_MAX_PAYOFFS);
+    if (np > 0 && !p) return fail(MC_EINVAL, "payoffs is NULL");
+    std::memset(ps, 0, sizeof *ps);
+    ps->n = np;
+    for (int i = 0; i < np; ++i) {
+        const int k = p[i].kind;
+        if (k < MC_CALL || k > MC_DI_PUT) return fail(MC_EINVAL, "payoff %d: unknown kind %d", i, k);
+        if (!std::isfinite(p[i].strike)) return fail(MC_EINVAL, "payoff %d: strike not finite", i);
+        const bool barrier = k >= MC_UO_CALL;
+        if (barrier && std::isnan(p[i].barrier)) return fail(MC_EINVAL, "payoff %d: barrier is NaN", i);
+        ps->kind[i] = k;
+        ps->strike[i] = static_cast<float>(p[i].strike);
+        ps->barrier[i] = barrier ? static_cast<float>(p[i].barrier) : INFINITY;
+        if (k == MC_ASIAN_CALL || k == MC_ASIAN_PUT) ps->need_avg = 1;
+        if (k >= MC_UO_CALL && k <= MC_UI_PUT) ps->need_max = 1;
+        if (k >= MC_DO_CALL) ps->need_min = 1;
+    }
+    return MC_OK;
+}
+
+struct DeviceInfo {
+    int device = -1;
+    int sms = 0;
+};
+
+int device_info(DeviceInfo *di)
+{
+    MC_CUDA(cudaGetDevice(&di->device));
+    MC_CUDA(cudaDeviceGetAttribute(&di->sms, cudaDevAttrMultiProcessorCount, di->device));
+    return MC_OK;
+}
+
+// Persistent single-wave grid: at most `resident` blocks, every thread the
+// same number of paths (ppt), grid shrunk so that no block is idle.
+void size_grid(int64_t paths, int block, int resident, int *grid, int *ppt)
+{
+    int64_t g = (paths + block - 1) / block;
+    if (resident > 0 && g > resident) g = resident;
+    if (g < 1) g = 1;
+    int64_t p = (paths + g * block - 1) / (g * block);
+    g = (paths + p * block - 1) / (p * block);
+    *grid = static_cast<int>(g);
+    *ppt = static_cast<int>(p);
+}
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+}  // namespace
+
+enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2 };
+
+struct mc_plan {
+    int device = -1;
+    KernelKind kk = K_GBM1D;
+    int np = 0;
+    int grid = 0, block = 256;
+    int D = 0;
+    Gbm1dArgs g1{};
+    BasketArgs bk{};
+    HestonArgs hs{};
+    std::vector<unsigned char> cst;
+    float *partials = nullptr;
+    unsigned int *ticket = nullptr;
+    mc_result *dout = nullptr;
+    double *dcorr = nullptr, *dL = nullptr, *dsig = nullptr;
+    float *dLp = nullptr, *ddrift = nullptr;
+    int *dstatus = nullptr;
+
+    ~mc_plan()
+    {
+        dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
+        dfree(dLp); dfree(ddrift); dfree(dstatus);
+    }
+};
+
+namespace {
+
+// Shared set-up of mc_plan_create and mc_simulate.  save != nullptr selects
+// the materialising kernels (no payoffs, no reduction).
+int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int np,
+               float *save, int save_every, cudaStream_t s)
+{
+    int rc;
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
+    PayoffSet ps;
+    if ((rc = build_payoffs(pays, np, &ps))) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    P->device = di.device;
+    P->np = np;
+
+    PathRun run{};
+    run.paths = c->paths;
+    run.path_offset = c->path_offset;
+    run.k0 = static_cast<uint32_t>(c->seed);
+    run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    run.steps = c->steps;
+    run.save = save;
+    run.save_every = save_every > 0 ? save_every : 1;
+
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const double disc = std::exp(-m->r * c->T);
+    ReduceArgs red{};
+    red.paths = c->paths;
+    red.disc = disc;
+    int resident = 0;
+
+    if (m->kind == MC_HESTON) {
+        P->kk = K_HESTON;
+        HestonArgs &h = P->hs;
+        h.run = run;
+        h.s0 = static_cast<float>(m->s0[0]);
+        h.v0 = static_cast<float>(m->v0);
+        h.r = static_cast<float>(m->r);
+        h.kappa = static_cast<float>(m->kappa);
+        h.theta = static_cast<float>(m->theta);
+        h.xi = static_cast<float>(m->xi);
+        h.rho = static_cast<float>(m->rho);
+        h.rhoc = static_cast<float>(std::sqrt(1.0 - m->rho * m->rho));
+        h.dt = static_cast<float>(dt);
+        h.pay = ps;
+        h.red = red;
+        resident = heston_occupancy(h, P->block) * di.sms;
+    } else if (m->d == 1) {
+        P->kk = K_GBM1D;
+        if (m->corr && std::fabs(m->corr[0] - 1.0) > 1e-12) return fail(MC_EINVAL, "corr[0] must be 1");
+        Gbm1dArgs &g = P->g1;
+        g.run = run;
+        g.scheme = c->scheme;
+        const double sg = m->sigma[0];
+        const double w = m->weights ? m->weights[0] : 1.0;
+        // U = w S for a one-asset basket; the kernel simulates S and the
+        // weight is folded into S0 (U is linear in S0 under both schemes).
+        g.s0 = static_cast<float>(save ? m->s0[0] : w * m->s0[0]);
+        if (c->scheme == MC_LOG_EULER) {
+            g.a = static_cast<float>(M_LOG2E * (m->r - 0.5 * sg * sg) * dt);
+            g.b = static_cast<float>(M_LOG2E * sg * sdt);
+        } else {
+            g.a = static_cast<float>(m->r * dt);
+            g.b = static_cast<float>(sg * sdt);
+        }
+        g.pay = ps;
+        g.red = red;
+        resident = gbm1d_occupancy(g, P->block) * di.sms;
+    } else {
+        const int d = m->d;
+        if (c->precision != MC_FP32)
+            return fail(MC_EUNSUPPORTED, "tensor-core contraction not available for this request");
+        const int D = basket_fp32_width(d);
+        if (!D) return fail(MC_EUNSUPPORTED, "FP32 contraction supports d <= 64 (got %d)", d);
+        P->kk = K_BASKET_FP32;
+        P->D = D;
+        const size_t dd = static_cast<size_t>(d) * d;
+        const size_t tri = static_cast<size_t>(d) * (d + 1) / 2;
+        MC_CUDA(cudaMalloc(&P->dcorr, dd * sizeof(double)));
+        MC_CUDA(cudaMalloc(&P->dL, dd * sizeof(double)));
+        MC_CUDA(cudaMalloc(&P->dsig, d * sizeof(double)));
+        MC_CUDA(cudaMalloc(&P->dLp, tri * sizeof(float)));
+        MC_CUDA(cudaMalloc(&P->ddrift, d * sizeof(float)));
+        MC_CUDA(cudaMalloc(&P->dstatus, sizeof(int)));
+        std::vector<double> corr(dd, 0.0);
+        if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+        else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
+        MC_CUDA(cudaMemcpyAsync(P->dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+        MC_CUDA(cudaMemcpyAsync(P->dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+        MC_CUDA(launch_cholesky(d, P->dcorr, P->dL, P->dstatus, s));
+        const double cs = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
+        MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cs, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
+        int status = 0;
+        std::vector<float> Lp(tri), drift(d);
+        MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(Lp.data(), P->dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(drift.data(), P->ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+        // Pack the launch-parameter block: rows of width D, zero beyond d.
+        P->cst.assign(basket_const_bytes(D), 0);
+        size_t oL, oDr, oWs, oW, oS;
+        basket_const_offsets(D, &oL, &oDr, &oWs, &oW, &oS);
+        float *cL = reinterpret_cast<float *>(P->cst.data() + oL);
+        float *cDr = reinterpret_cast<float *>(P->cst.data() + oDr);
+        float *cWs = reinterpret_cast<float *>(P->cst.data() + oWs);
+        float *cW = reinterpret_cast<float *>(P->cst.data() + oW);
+        float *cS = reinterpret_cast<float *>(P->cst.data() + oS);
+        for (int a = 0; a < d; ++a) {
+            for (int k = 0; k <= a; ++k) cL[a * (a + 1) / 2 + k] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + k];
+            const double w = m->weights ? m->weights[a] : 1.0 / d;
+            cDr[a] = drift[a];
+            cWs[a] = static_cast<float>(w * m->s0[a]);
+            cW[a] = static_cast<float>(w);
+            cS[a] = static_cast<float>(m->s0[a]);
+        }
+        BasketArgs &b = P->bk;
+        b.run = run;
+        b.d = d;
+        b.scheme = c->scheme;
+        b.pay = ps;
+        b.red = red;
+        resident = basket_fp32_occupancy(D, b, P->block) * di.sms;
+    }
+    if (resident <= 0) return fail(MC_ECUDA, "kernel cannot be resident (occupancy query failed)");
+    int ppt = 1;
+    size_grid(c->paths, P->block, resident, &P->grid, &ppt);
+    P->g1.run.ppt = ppt;
+    P->bk.run.ppt = ppt;
+    P->hs.run.ppt = ppt;
+    if (np > 0) {
+        MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
+        MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+        MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
+        MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
+        for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red}) {
+            r->partials = P->partials;
+            r->ticket = P->ticket;
+            r->out = P->dout;
+        }
+    }
+    return MC_OK;
+}
+
+int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
+{
+    for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red}) r->out = dev_out ? dev_out : P->dout;
+    switch (P->kk) {
+    case K_GBM1D: MC_CUDA(launch_gbm1d(P->g1, P->grid, P->block, s)); break;
+    case K_BASKET_FP32: MC_CUDA(launch_basket_fp32(P->D, P->bk, P->cst.data(), P->grid, P->block, s)); break;
+    case K_HESTON: MC_CUDA(launch_heston(P->hs, P->grid, P->block, s)); break;
+    }
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_version(void) { return MC_VERSION; }
+
+const char *mc_last_error(void) { return g_err.c_str(); }
+
+int mc_plan_create(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+                   mc_plan **plan, void *stream)
+{
+    if (!plan) return fail(MC_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (n_payoff < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
+    mc_plan *P = new (std::nothrow) mc_plan();
+    if (!P) return fail(MC_ENOMEM, "host allocation failed");
+    int rc = plan_setup(P, model, cfg, payoffs, n_payoff, nullptr, 0, static_cast<cudaStream_t>(stream));
+    if (rc) {
+        delete P;
+        return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        delete P;
+        return fail(MC_ECUDA, "set-up: %s", cudaGetErrorString(e));
+    }
+    *plan = P;
+    return MC_OK;
+}
+
+int mc_plan_execute(mc_plan *plan, mc_result *dev_out, void *stream)
+{
+    if (!plan) return fail(MC_EINVAL, "plan is NULL");
+    if (!dev_out) return fail(MC_EINVAL, "dev_out is NULL");
+    int dev = -1;
+    MC_CUDA(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail(MC_EINVAL, "plan belongs to device %d, current is %d", plan->device, dev);
+    return plan_launch(plan, dev_out, static_cast<cudaStream_t>(stream));
+}
+
+int mc_plan_destroy(mc_plan *plan)
+{
+    delete plan;
+    return MC_OK;
+}
+
+int mc_plan_launches(const mc_plan *plan) { return plan ? 1 : 0; }
+
+int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+             mc_result *out, void *stream)
+{
+    if (!out) return fail(MC_EINVAL, "out is NULL");
+    mc_plan *P = nullptr;
+    int rc = mc_plan_create(model, cfg, payoffs, n_payoff, &P, stream);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = plan_launch(P, P->dout, s);
+    std::vector<mc_result> tmp(n_payoff);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), P->dout, n_payoff * sizeof(mc_result), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(MC_ECUDA, "mc_price: %s", cudaGetErrorString(e));
+    }
+    if (!rc) std::memcpy(out, tmp.data(), n_payoff * sizeof(mc_result));
+    delete P;
+    return rc;
+}
+
+int mc_simulate(const mc_model *model, const mc_sim_cfg *cfg, int32_t save_every, float *dev_out, void *stream)
+{
+    if (!dev_out) return fail(MC_EINVAL, "dev_out is NULL");
+    if (!cfg) return fail(MC_EINVAL, "cfg is NULL");
+    if (save_every < 1 || cfg->steps < 1 || cfg->steps % save_every)
+        return fail(MC_EINVAL, "save_every = %d must divide steps = %d", save_every, cfg ? cfg->steps : 0);
+    mc_plan P;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = plan_setup(&P, model, cfg, nullptr, 0, dev_out, save_every, s);
+    if (rc) return rc;
+    rc = plan_launch(&P, nullptr, s);
+    if (rc) return rc;
+    // P's set-up buffers are released when it goes out of scope; the kernel
+    // no longer needs them (the factor travels in the launch parameters), but
+    // cudaFree must not race the launch's argument capture: synchronise.
+    MC_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+// Device building blocks shared by the path kernels: the keyed counter-based
+// generator (Sec. IV.A), the Box-Muller transform (Sec. VI.D), payoffs on the
+// monitored underlying (Sec. I.A.2) and the warp / block / cross-block
+// reduction that ends in the FP64 estimator of Eq. 3.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mc.h"
+
+namespace gbmc {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with the round multipliers, xor of the high halves with the other counter
+// words and the round key, and a Weyl bump of the key between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// u = (floor(x / 2^9) + 1/2) 2^-23 in [2^-24, 1 - 2^-24], exact in binary32:
+// the bits of 1 + floor(x/2^9) 2^-23 minus (1 - 2^-24) (Sterbenz: exact).
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
+}
+
+// Box-Muller on one pair of words: z0 = r cos(2 pi u_b), z1 = r sin(2 pi u_b),
+// r = sqrt(-2 ln u_a).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float ua = u01(a), ub = u01(b);
+    const float rad = sqrtf(-2.0f * logf(ua));
+    float s, c;
+    sincospif(2.0f * ub, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// The four normals of block q of stream (path) n.
+__device__ __forceinline__ float4 normals4(uint64_t q, uint64_t n, uint32_t k0, uint32_t k1)
+{
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                             static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)),
+                                  k0, k1);
+    float4 z;
+    box_muller(x.x, x.y, z.x, z.y);
+    box_muller(x.z, x.w, z.z, z.w);
+    return z;
+}
+
+// Sequential reader of normal j of one stream, regenerating a block only when
+// j leaves the cached one (warp-uniform when all lanes are at the same j).
+struct NormalReader {
+    uint64_t n;
+    uint32_t k0, k1;
+    uint64_t q;
+    float4 z;
+    __device__ __forceinline__ void init(uint64_t stream, uint32_t key0, uint32_t key1)
+    {
+        n = stream; k0 = key0; k1 = key1; q = ~0ull;
+    }
+    __device__ __forceinline__ float get(uint64_t j)
+    {
+        const uint64_t qj = j >> 2;
+        if (qj != q) { q = qj; z = normals4(qj, n, k0, k1); }
+        const uint32_t l = static_cast<uint32_t>(j) & 3u;
+        return l == 0 ? z.x : (l == 1 ? z.y : (l == 2 ? z.z : z.w));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Payoffs (undiscounted) on the monitored statistics of U.
+// ---------------------------------------------------------------------------
+struct PayoffSet {
+    int n;
+    int need_avg;   // some payoff uses the arithmetic average
+    int need_max;   // some payoff uses the running maximum
+    int need_min;   // some payoff uses the running minimum
+    int kind[MC_MAX_PAYOFFS];
+    float strike[MC_MAX_PAYOFFS];
+    float barrier[MC_MAX_PAYOFFS];
+};
+
+__device__ __forceinline__ float payoff_eval(int kind, float K, float H, float uT, float avg,
+                                             float umax, float umin)
+{
+    const float call = fmaxf(uT - K, 0.0f), put = fmaxf(K - uT, 0.0f);
+    const bool up = umax >= H, down = umin <= H;
+    switch (kind) {
+    case MC_CALL: return call;
+    case MC_PUT: return put;
+    case MC_ASIAN_CALL: return fmaxf(avg - K, 0.0f);
+    case MC_ASIAN_PUT: return fmaxf(K - avg, 0.0f);
+    case MC_UO_CALL: return up ? 0.0f : call;
+    case MC_UI_CALL: return up ? call : 0.0f;
+    case MC_UO_PUT: return up ? 0.0f : put;
+    case MC_UI_PUT: return up ? put : 0.0f;
+    case MC_DO_CALL: return down ? 0.0f : call;
+    case MC_DI_CALL: return down ? call : 0.0f;
+    case MC_DO_PUT: return down ? 0.0f : put;
+    case MC_DI_PUT: return down ? put : 0.0f;
+    default: return 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction.  Each warp owns a slot per payoff in shared memory; after every
+// grid-stride iteration the warp's 32 payoffs (and squares) are summed with
+// shuffles and lane 0 adds them to its slot (fixed order: deterministic).  At
+// block end the warp slots are summed into one FP32 (sum f, sum f^2) pair per
+// payoff and written to the block's partials.  The last block to finish
+// (atomic ticket, no spin-wait) sums all block partials in FP64, forms mean
+// and standard error, discounts and writes the results, then resets the
+// ticket for the next launch.
+// ---------------------------------------------------------------------------
+struct ReduceArgs {
+    float *partials;        // [gridDim.x][n_payoff][2]
+    unsigned int *ticket;   // zero on entry to the launch, reset by the last block
+    mc_result *out;         // [n_payoff]
+    int64_t paths;
+    double disc;
+};
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Adds this warp's 32 payoff values to s_acc[warp][p][*].
+__device__ __forceinline__ void warp_accumulate(float *s_acc, int np, int p, float f)
+{
+    const float a = warp_sum(f), b = warp_sum(f * f);
+    if ((threadIdx.x & 31) == 0) {
+        float *slot = s_acc + ((threadIdx.x >> 5) * np + p) * 2;
+        slot[0] += a;
+        slot[1] += b;
+    }
+}
+
+// Called by every thread of the block after its last path.  s_acc holds
+// nwarps*np*2 floats; s_red is scratch for 32 doubles.
+__device__ inline void block_finish(float *s_acc, double *s_red, int np, const ReduceArgs &ra)
+{
+    const int nwarps = blockDim.x >> 5;
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * 2; i += blockDim.x) {
+        float s = 0.0f;
+        for (int w = 0; w < nwarps; ++w) s += s_acc[w * np * 2 + i];
+        ra.partials[static_cast<size_t>(blockIdx.x) * np * 2 + i] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (threadIdx.x == 0) s_last = (atomicAdd(ra.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nb = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = 0; p < np; ++p) {
+        double t[2];
+        for (int m = 0; m < 2; ++m) {
+            double v = 0.0;
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
+                v += static_cast<double>(ra.partials[static_cast<size_t>(b) * np * 2 + p * 2 + m]);
+            v = warp_sum_d(v);
+            if (lane == 0) s_red[warp] = v;
+            __syncthreads();
+            double tot = 0.0;
+            for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+            t[m] = tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double N = static_cast<double>(ra.paths);
+            const double mean = t[0] / N, m2 = t[1] / N;
+            const double var = fmax(m2 - mean * mean, 0.0);
+            mc_result res;
+            res.price = ra.disc * mean;
+            res.se = ra.paths > 1 ? ra.disc * sqrt(var / (N - 1.0)) : 0.0;
+            ra.out[p] = res;
+        }
+    }
+    if (threadIdx.x == 0) *ra.ticket = 0u;
+}
+
+}  // namespace gbmc

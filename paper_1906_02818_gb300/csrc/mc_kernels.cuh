@@ -1,0 +1,85 @@
+// Launch-parameter blocks and host launchers of the path kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mc_device.cuh"
+
+namespace gbmc {
+
+// Common per-launch fields of every path kernel.
+struct PathRun {
+    int64_t paths;        // paths of this launch
+    int64_t path_offset;  // global index of the first one
+    uint32_t k0, k1;      // Philox key
+    int steps;
+    int ppt;              // paths per thread (grid-stride count)
+    float *save;          // mc_simulate output or nullptr
+    int save_every;
+};
+
+// Single-asset GBM.  log-Euler: y = log2(S/S0) += a + b z with
+// a = log2(e) (r - sigma^2/2) dt, b = log2(e) sigma sqrt(dt).
+// Euler: S <- S + S (a + b z) with a = r dt, b = sigma sqrt(dt).
+struct Gbm1dArgs {
+    PathRun run;
+    int scheme;
+    float s0, a, b;
+    PayoffSet pay;
+    ReduceArgs red;
+};
+
+// Correlated basket of at most D assets with the Cholesky factor in the
+// launch-parameter block (constant bank): packed lower triangle of
+// Lhat = c sqrt(dt) diag(sigma) Lrho (c = log2(e) for log-Euler, 1 for Euler),
+// row a at offset a(a+1)/2.  Entries for assets >= d are zero.
+template <int D>
+struct BasketConst {
+    float L[D * (D + 1) / 2];
+    float drift[D];  // log-Euler: log2(e) (r - sigma_a^2/2) dt; Euler: r dt
+    float ws0[D];    // w_a * S0_a
+    float w[D];
+    float s0[D];
+};
+
+struct BasketArgs {
+    PathRun run;
+    int d;
+    int scheme;
+    PayoffSet pay;
+    ReduceArgs red;
+};
+
+// Heston full-truncation Euler, y = log2(S/S0).
+struct HestonArgs {
+    PathRun run;
+    float s0, v0, r, kappa, theta, xi, rho, rhoc, dt;
+    PayoffSet pay;
+    ReduceArgs red;
+};
+
+// Host launchers (return cudaError_t of the launch).
+cudaError_t launch_gbm1d(const Gbm1dArgs &a, int grid, int block, cudaStream_t s);
+int gbm1d_occupancy(const Gbm1dArgs &a, int block);
+
+cudaError_t launch_basket_fp32(int D, const BasketArgs &a, const void *cst, int grid, int block,
+                               cudaStream_t s);
+int basket_fp32_occupancy(int D, const BasketArgs &a, int block);
+int basket_fp32_width(int d);        // smallest instantiated D >= d (0 if none)
+size_t basket_const_bytes(int D);    // sizeof(BasketConst<D>)
+void basket_const_offsets(int D, size_t *L, size_t *drift, size_t *ws0, size_t *w, size_t *s0);
+
+cudaError_t launch_heston(const HestonArgs &a, int grid, int block, cudaStream_t s);
+int heston_occupancy(const HestonArgs &a, int block);
+
+// FP64 Cholesky of a d x d SPD matrix on the device (one CTA); writes the
+// lower factor to L and 0 / 1 (not positive definite) to *status.
+cudaError_t launch_cholesky(int d, const double *A, double *L, int *status, cudaStream_t s);
+
+// Lhat (packed lower triangle, FP32) = c sqrt(dt) diag(sigma) L, plus drift.
+cudaError_t launch_scale_factor(int d, const double *L, const double *sigma, double c, double sdt,
+                                double r, double dt, int scheme, float *Lpacked, float *drift,
+                                cudaStream_t s);
+
+}  // namespace gbmc

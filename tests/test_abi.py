@@ -1,0 +1,94 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+include/mc.h declares, and rejects bad arguments on the host (these checks run
+before any CUDA call, so they need no device)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mc_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1906_02818_gb300 import native
+    return native.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1906_02818_gb300 import native
+    names = declared_functions()
+    assert "mc_price" in names and "mc_simulate" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding marshals exactly the declared surface
+    assert sorted(s[0] for s in native.SIGNATURES) == names
+
+
+def test_version_and_error_string(lib):
+    assert lib.mc_version() == 10000
+    assert isinstance(lib.mc_last_error(), bytes)
+
+
+def _structs(kind="gbm", d=1, **over):
+    from paper_1906_02818_gb300 import api
+    if kind == "gbm":
+        model = dict(kind="gbm", s0=np.full(d, 100.0), sigma=np.full(d, 0.2), r=0.05)
+    else:
+        model = dict(kind="heston", s0=100.0, v0=0.04, r=0.05, kappa=2.0, theta=0.04, xi=0.5, rho=-0.7)
+    model.update({k: v for k, v in over.items() if k in ("s0", "sigma", "corr", "weights", "r", "rho", "xi", "v0")})
+    cfg = dict(steps=4, T=1.0, paths=16)
+    cfg.update({k: v for k, v in over.items() if k in ("steps", "T", "paths", "scheme", "precision", "path_offset")})
+    pays = over.get("payoffs", [dict(kind="call", strike=100.0)])
+    return api._Marshalled(model, cfg, pays)
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(steps=0), "steps"),
+    (dict(T=-1.0), "T must"),
+    (dict(paths=0), "paths"),
+    (dict(path_offset=-1), "path range"),
+    (dict(s0=np.array([-1.0])), "s0[0]"),
+    (dict(sigma=np.array([np.nan])), "sigma[0]"),
+    (dict(payoffs=[dict(kind="call", strike=float("nan"))]), "strike"),
+    (dict(d=2, corr=np.array([[1.0, 0.5], [0.4, 1.0]])), "symmetric"),
+    (dict(d=2, corr=np.array([[2.0, 0.5], [0.5, 1.0]])), "unit diagonal"),
+])
+def test_price_rejects_bad_arguments_on_host(lib, over, needle):
+    from paper_1906_02818_gb300 import native
+    mm = _structs(**over)
+    out = (native.McResult * 1)()
+    rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
+    assert rc == native.MC_EINVAL
+    assert needle in lib.mc_last_error().decode()
+
+
+def test_heston_argument_checks(lib):
+    from paper_1906_02818_gb300 import native
+    for over, needle in [(dict(rho=1.0), "rho"), (dict(xi=-0.1), ">= 0"), (dict(precision="bf16"), "precision")]:
+        mm = _structs(kind="heston", **over)
+        out = (native.McResult * 1)()
+        rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
+        assert rc == native.MC_EINVAL, over
+        assert needle in lib.mc_last_error().decode()
+
+
+def test_null_and_count_checks(lib):
+    from paper_1906_02818_gb300 import native
+    mm = _structs()
+    out = (native.McResult * 1)()
+    assert lib.mc_price(None, ctypes.byref(mm.cfg), mm.payoffs, 1, out, None) == native.MC_EINVAL
+    assert lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, 33, out, None) == native.MC_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.mc_plan_create(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, 0,
+                              ctypes.byref(h), None) == native.MC_EINVAL
+    assert lib.mc_simulate(ctypes.byref(mm.model), ctypes.byref(mm.cfg), 3, ctypes.c_void_p(1), None) == native.MC_EINVAL
+    assert lib.mc_plan_execute(None, ctypes.c_void_p(1), None) == native.MC_EINVAL

@@ -1,0 +1,180 @@
+"""GPU parity of the pricing path (mc_price / plans) with the FP64 oracle on
+identical Philox streams: 1-D GBM, FP32 correlated baskets, Heston."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import BAND, REL, assert_price_close, cfg_of, gbm_model, oracle_gbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1906_02818_gb300 as gb
+    from paper_1906_02818_gb300 import native
+    native.lib()
+    return gb
+
+
+ALL_1D = [dict(kind="call", strike=100.0), dict(kind="put", strike=100.0),
+          dict(kind="asian_call", strike=100.0), dict(kind="asian_put", strike=95.0),
+          dict(kind="uo_call", strike=100.0, barrier=130.0), dict(kind="ui_call", strike=100.0, barrier=130.0),
+          dict(kind="do_put", strike=100.0, barrier=80.0), dict(kind="di_put", strike=100.0, barrier=80.0)]
+
+
+def barrier_band_mass(orc, paths_U, per_path, payoffs):
+    """Payoff mass / N of paths whose monitored max/min is within BAND of H."""
+    masses = []
+    umax = paths_U[1:].max(axis=0)
+    umin = paths_U[1:].min(axis=0)
+    for i, p in enumerate(payoffs):
+        if p["kind"][:2] in ("uo", "ui", "do", "di"):
+            ext = umax if p["kind"][0] == "u" else umin
+            near = np.abs(ext - p["barrier"]) <= BAND * p["barrier"]
+            # the alive/dead flip changes the payoff by at most the vanilla payoff
+            uT = paths_U[-1]
+            van = np.maximum(uT - p["strike"], 0) if "call" in p["kind"] else np.maximum(p["strike"] - uT, 0)
+            masses.append(float(np.sum(van[near])) / per_path.shape[1] * 1.01 + 1e-12)
+        else:
+            masses.append(None)
+    return masses
+
+
+@pytest.mark.parametrize("scheme", ["log_euler", "euler"])
+@pytest.mark.parametrize("steps,paths", [(64, 1 << 15), (63, 50_001), (1, 7), (5, 1)])
+def test_gbm1d_all_payoffs(gb, orc, scheme, steps, paths):
+    w = workloads.gbm_1d(paths=paths, steps=steps)
+    w["sigma"] = np.array([0.3])
+    got = gb.price(gbm_model(w), cfg_of(w, scheme=scheme), ALL_1D)
+    ref = oracle_gbm(orc, w, paths, ALL_1D, scheme=scheme)
+    U = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], steps, paths, scheme=scheme)[:, 0]
+    assert_price_close(got, ref, ALL_1D, barrier_band_mass(orc, U, ref, ALL_1D), f"{scheme}/{steps}/{paths}")
+
+
+def test_gbm1d_full_size_config(gb, orc):
+    """The 1-D workload at its full size (2^20 paths, 64 steps) in the launch
+    configuration the benchmark uses, and against Black-Scholes within 3 SE."""
+    from closed_forms import bs_call
+    w = workloads.gbm_1d()
+    got = gb.price(gbm_model(w), cfg_of(w), w["payoffs"])
+    ref = oracle_gbm(orc, w, w["paths"], w["payoffs"])
+    assert_price_close(got, ref, w["payoffs"], label="C1")
+    assert abs(got[0][0] - bs_call(100, 100, 0.05, 0.2, 1.0)) <= 3 * got[0][1]
+
+
+def test_plan_matches_price_and_repeats(gb):
+    import torch
+    w = workloads.gbm_1d(paths=1 << 16)
+    a = gb.price(gbm_model(w), cfg_of(w), ALL_1D)
+    with gb.Plan(gbm_model(w), cfg_of(w), ALL_1D) as plan:
+        r1 = plan.execute().cpu().numpy()
+        r2 = plan.execute().cpu().numpy()
+        torch.cuda.synchronize()
+    assert np.array_equal(r1, r2)  # deterministic reduction order
+    assert np.allclose(r1, np.array(a), rtol=0, atol=0)
+
+
+def test_path_offset_shards_combine(gb, orc):
+    """Sharding the path range with path_offset: shard prices combine to the
+    unsharded price, and a shard deep in the range matches the oracle."""
+    w = workloads.gbm_1d(paths=1 << 16)
+    pays = [dict(kind="call", strike=100.0)]
+    full = gb.price(gbm_model(w), cfg_of(w), pays)[0][0]
+    parts = [gb.price(gbm_model(w), cfg_of(w, paths=1 << 14, path_offset=k << 14), pays)[0][0] for k in range(4)]
+    assert abs(np.mean(parts) - full) <= 1e-6 * full
+    deep = gb.price(gbm_model(w), cfg_of(w, paths=777, path_offset=(1 << 40) + 3), pays)
+    ref = oracle_gbm(orc, w, 777, pays, path_offset=(1 << 40) + 3)
+    assert_price_close(deep, ref, pays, label="deep shard")
+
+
+def _basket(d, k, paths, steps, seed=3):
+    s0, sg, corr = workloads.basket_market(d, k, seed=seed)
+    w = np.full(d, 1.0 / d)
+    b0 = float(w @ s0)
+    pays = [dict(kind="call", strike=b0), dict(kind="put", strike=b0), dict(kind="asian_call", strike=b0),
+            dict(kind="uo_call", strike=b0, barrier=1.15 * b0)]
+    return dict(s0=s0, sigma=sg, corr=corr, weights=w, r=0.05, T=1.0, steps=steps, paths=paths, seed=42), pays
+
+
+@pytest.mark.parametrize("d,scheme", [(2, "log_euler"), (5, "euler"), (8, "log_euler"), (16, "euler"),
+                                      (31, "log_euler"), (64, "log_euler"), (64, "euler")])
+def test_basket_fp32(gb, orc, d, scheme):
+    w, pays = _basket(d, 2, 3000, 24)
+    got = gb.price(gbm_model(w), cfg_of(w, scheme=scheme), pays)
+    ref = oracle_gbm(orc, w, w["paths"], pays, scheme=scheme)
+    P = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], w["paths"], corr=w["corr"],
+                      weights=w["weights"], scheme=scheme)
+    U = np.einsum("a,tan->tn", w["weights"], P)
+    assert_price_close(got, ref, pays, barrier_band_mass(orc, U, ref, pays), f"d={d}/{scheme}")
+
+
+def test_basket_d64_config_prefix(gb, orc):
+    """The d = 64, 252-step workload on an oracle-sized prefix of its paths
+    (same launch shape as the full run for this path count)."""
+    w = workloads.basket_d64(paths=2048)
+    got = gb.price(gbm_model(w), cfg_of(w), w["payoffs"])
+    ref = oracle_gbm(orc, w, 2048, w["payoffs"])
+    P = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], 2048, corr=w["corr"], weights=w["weights"])
+    U = np.einsum("a,tan->tn", w["weights"], P)
+    assert_price_close(got, ref, w["payoffs"], barrier_band_mass(orc, U, ref, w["payoffs"]), "C2 prefix")
+
+
+def test_basket_d64_full_size_sampled(gb, orc):
+    """Full-size d = 64 run (2^18 paths) in the benchmark's launch shape:
+    it equals the combination of 8 shard runs, and shards sampled across the
+    range match the oracle path by path."""
+    w = workloads.basket_d64()
+    N = w["paths"]
+    full = gb.price(gbm_model(w), cfg_of(w), w["payoffs"])
+    parts = [gb.price(gbm_model(w), cfg_of(w, paths=N // 8, path_offset=k * N // 8), w["payoffs"]) for k in range(8)]
+    for i in range(len(w["payoffs"])):
+        assert abs(np.mean([p[i][0] for p in parts]) - full[i][0]) <= 1e-6 * abs(full[i][0])
+    for off in (0, N // 2 + 17, N - 300):
+        n = 300
+        got = gb.price(gbm_model(w), cfg_of(w, paths=n, path_offset=off), w["payoffs"])
+        ref = oracle_gbm(orc, w, n, w["payoffs"], path_offset=off)
+        P = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], n, corr=w["corr"],
+                          weights=w["weights"], path_offset=off)
+        U = np.einsum("a,tan->tn", w["weights"], P)
+        assert_price_close(got, ref, w["payoffs"], barrier_band_mass(orc, U, ref, w["payoffs"]), f"C2@{off}")
+
+
+def test_heston_config_prefix(gb, orc):
+    w = workloads.heston(paths=1 << 14)
+    got = gb.price(dict(kind="heston", **w["model"]), cfg_of(w), w["payoffs"])
+    ref = orc.heston_payoffs(w["model"], w["T"], w["steps"], w["paths"], w["payoffs"])
+    assert_price_close(got, ref, w["payoffs"], label="C3 prefix")
+
+
+@pytest.mark.parametrize("steps,paths", [(7, 1001), (1, 3), (256, 1 << 12)])
+def test_heston_barriers_and_ragged(gb, orc, steps, paths):
+    m = dict(workloads.HESTON_PARAMS)
+    pays = ALL_1D
+    got = gb.price(dict(kind="heston", **m), dict(steps=steps, T=1.0, paths=paths), pays)
+    ref = orc.heston_payoffs(m, 1.0, steps, paths, pays)
+    U = orc.heston_paths(m, 1.0, steps, paths)[:, 0]
+    assert_price_close(got, ref, pays, barrier_band_mass(orc, U, ref, pays), f"heston {steps}/{paths}")
+
+
+def test_heston_full_size_sampled(gb, orc):
+    w = workloads.heston()
+    N = w["paths"]
+    full = gb.price(dict(kind="heston", **w["model"]), cfg_of(w), w["payoffs"])
+    from closed_forms import bs_call  # sanity: prices are ordered in strike
+    assert all(full[i][0] > full[i + 1][0] for i in range(8))
+    for off in (0, N // 3, N - 500):
+        got = gb.price(dict(kind="heston", **w["model"]), cfg_of(w, paths=500, path_offset=off), w["payoffs"])
+        ref = orc.heston_payoffs(w["model"], w["T"], w["steps"], 500, w["payoffs"], path_offset=off)
+        assert_price_close(got, ref, w["payoffs"], label=f"C3@{off}")
+
+
+def test_non_psd_correlation_is_reported(gb):
+    from paper_1906_02818_gb300 import native
+    corr = np.array([[1.0, 0.9, 0.9], [0.9, 1.0, -0.9], [0.9, -0.9, 1.0]])
+    with pytest.raises(native.MCError) as e:
+        gb.price(dict(kind="gbm", s0=[100.0] * 3, sigma=[0.2] * 3, corr=corr, r=0.05),
+                 dict(steps=4, T=1.0, paths=64), [dict(kind="call", strike=100.0)])
+    assert e.value.status == native.MC_ENOTPSD

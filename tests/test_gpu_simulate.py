@@ -1,0 +1,59 @@
+"""GPU parity of materialised paths (mc_simulate) with the oracle, path by
+path, on tiny and ragged path counts (brute force) and on the d = 64 basket."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import BAND, cfg_of, gbm_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b) / np.abs(b))
+
+
+@pytest.mark.parametrize("paths", [1, 2, 3, 7, 32, 1000])
+@pytest.mark.parametrize("scheme", ["log_euler", "euler"])
+def test_gbm1d_paths_brute_force(gb, orc, paths, scheme):
+    w = workloads.gbm_1d(paths=paths, steps=65)
+    got = gb.simulate(gbm_model(w), cfg_of(w, scheme=scheme, path_offset=11), save_every=5).cpu().numpy()
+    ref = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], 65, paths, scheme=scheme, save_every=5,
+                        path_offset=11)
+    assert got.shape == ref.shape
+    assert rel_err(got, ref) <= BAND
+
+
+@pytest.mark.parametrize("d,scheme", [(3, "log_euler"), (12, "euler"), (64, "log_euler")])
+def test_basket_paths(gb, orc, d, scheme):
+    s0, sg, corr = workloads.basket_market(d, 3, seed=9)
+    model = dict(kind="gbm", s0=s0, sigma=sg, corr=corr, r=0.05)
+    got = gb.simulate(model, dict(steps=36, T=1.0, paths=129, scheme=scheme), save_every=6).cpu().numpy()
+    ref = orc.gbm_paths(s0, sg, 0.05, 1.0, 36, 129, corr=corr, scheme=scheme, save_every=6)
+    assert got.shape == ref.shape
+    assert rel_err(got, ref) <= BAND
+
+
+def test_basket_d64_config_paths(gb, orc):
+    w = workloads.basket_d64(paths=64)
+    got = gb.simulate(gbm_model(w), cfg_of(w), save_every=63).cpu().numpy()
+    ref = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], 64, corr=w["corr"], save_every=63)
+    assert rel_err(got, ref) <= BAND
+
+
+@pytest.mark.parametrize("paths", [1, 5, 300])
+def test_heston_paths(gb, orc, paths):
+    m = dict(workloads.HESTON_PARAMS)
+    got = gb.simulate(dict(kind="heston", **m), dict(steps=64, T=1.0, paths=paths), save_every=8).cpu().numpy()
+    ref = orc.heston_paths(m, 1.0, 64, paths, save_every=8)
+    assert rel_err(got[:, 0], ref[:, 0]) <= BAND
+    # the variance is O(0.04) and crosses zero: compare on an absolute scale
+    assert np.max(np.abs(got[:, 1] - ref[:, 1])) <= BAND * 0.04 * 10
