@@ -64,11 +64,17 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const BasketArgs a,
             NormalReader rd;
             rd.init(n, a.run.k0, a.run.k1);
             for (int i = 0; i < M; ++i) {
-                // dW is accumulated apart from the state so that the O(1) state
-                // takes one rounding per step instead of one per FMA.
-                float dw[D];
+                // log-Euler accumulates L z straight into the state (|y| = O(1):
+                // ~65 roundings of <= 3e-8 per step, ~2e-6 rms over 252 steps);
+                // Euler needs dW apart because the step is multiplicative.
+                float dw[SCHEME == MC_EULER ? D : 1];
+                if (SCHEME == MC_EULER) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) dw[j] = 0.0f;
+                    for (int j = 0; j < D; ++j) dw[j] = 0.0f;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) x[j] += c.drift[j];
+                }
                 // dW = Lhat z, column by column as the normals are produced.
 #pragma unroll
                 for (int kb = 0; kb < D / 4 + (D % 4 ? 1 : 0); ++kb) {
@@ -88,14 +94,16 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const BasketArgs a,
                         const int k = 4 * kb + l;
                         if (k < D) {
 #pragma unroll
-                            for (int j = k; j < D; ++j) dw[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], dw[j]);
+                            for (int j = k; j < D; ++j) {
+                                if (SCHEME == MC_EULER) dw[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], dw[j]);
+                                else x[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], x[j]);
+                            }
                         }
                     }
                 }
+                if (SCHEME == MC_EULER) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    if (SCHEME == MC_EULER) x[j] = fmaf(x[j], c.drift[j] + dw[j], x[j]);
-                    else x[j] += c.drift[j] + dw[j];
+                    for (int j = 0; j < D; ++j) x[j] = fmaf(x[j], c.drift[j] + dw[j], x[j]);
                 }
                 if (STATS || (SAVE && ((i + 1) % a.run.save_every) == 0)) {
                     float u = 0.0f;

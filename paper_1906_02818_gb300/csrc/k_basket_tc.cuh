@@ -1,0 +1,373 @@
+// Correlated-basket path kernel with the correlation contraction on the
+// 5th-generation tensor cores (Sec. II.A.2: dW = sigma(X) Z for N stacked
+// scenarios is a (paths x d) x (d x d) product; Sec. V.A: low-precision
+// multiplies with FP32 accumulation).
+//
+// One CTA = 128 paths = 128 threads; thread t owns path row t of every tile
+// and TMEM lane t.  Per step i:
+//   1. each thread draws its row of Z_i (Philox4x32-10 + Box-Muller, fused in
+//      registers), rounds it to BF16 / FP16 / E4M3 (E4M3 with a per-path,
+//      per-step amax scale) and stores it in the 128B- (64B- for E4M3)
+//      swizzled K-major shared-memory tile the MMA reads;
+//   2. one thread issues tcgen05.mma: D[128 x 64] (TMEM, FP32) = Z_i Lq^T,
+//      where Lq is the quantised Cholesky factor of the correlation (rows
+//      scaled to the operand range), resident in shared memory;
+//   3. every thread reads its row of D back (tcgen05.ld) and applies the
+//      FP32 step: y_n += drift_n + cs_n D_n (log-Euler on log2(S_n/S0_n)), or
+//      S_n <- S_n (1 + r dt + cs_n D_n) (Euler), with cs_n folding
+//      sqrt(dt) sigma_n and the operand scales.
+// Z tiles are double-buffered so that drawing Z_{i+1} overlaps MMA_i.  All
+// waits on the MMA's mbarrier are bounded; on expiry the CTA records an error
+// word, stops simulating, frees its TMEM and still takes part in the
+// reduction (the final block then reports NaN prices).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mc_kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace gbmc {
+
+namespace tcb {
+
+constexpr int kRows = 128;   // paths per tile = UMMA M
+constexpr int kN = 64;       // assets (padded) = UMMA N = K
+constexpr int kThreads = 128;
+
+template <int PREC>
+struct Layout {
+    static constexpr int kElemBytes = PREC == MC_FP8E4M3 ? 1 : 2;
+    static constexpr int kRowBytes = kN * kElemBytes;              // 128 or 64
+    static constexpr int kTileBytes = kRows * kRowBytes;           // Z tile
+    static constexpr int kBBytes = kN * kRowBytes;                 // factor tile
+    static constexpr int kGroupBytes = 8 * kRowBytes;              // SBO
+    static constexpr int kChunks = kRowBytes / 16;                 // 16-B chunks per row
+    static constexpr int kPerChunk = 16 / kElemBytes;              // elements per chunk
+    static constexpr int kKStep = PREC == MC_FP8E4M3 ? 32 : 16;    // UMMA K
+    static constexpr int kMmas = kN / kKStep;
+    static constexpr tc::Swizzle kSw = PREC == MC_FP8E4M3 ? tc::SW_64B : tc::SW_128B;
+    // shared memory: [pad to 1024] Z0 | Z1 | B | mbarrier | tmem slot
+    static constexpr int kSmem = 1024 + 2 * kTileBytes + kBBytes + 64;
+    // byte offset of (row, chunk) inside a swizzled tile
+    __device__ static __forceinline__ uint32_t chunk_off(int row, int chunk)
+    {
+        const int phys = PREC == MC_FP8E4M3 ? (chunk ^ ((row >> 1) & 3)) : (chunk ^ (row & 7));
+        return static_cast<uint32_t>((row >> 3) * kGroupBytes + (row & 7) * kRowBytes + phys * 16);
+    }
+};
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    if (PREC == MC_BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack4_e4m3(float a, float b, float c, float d)
+{
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+struct Stats {
+    float sum, umax, umin;
+};
+
+// Draws Z_i of path n (row `row`) into the tile at `tile`; returns the
+// dequantisation factor of the row (1 unless E4M3).
+template <int PREC, bool EXACT>
+__device__ __forceinline__ float draw_row(uint32_t tile, int row, int i, int d, uint64_t n, uint32_t k0,
+                                          uint32_t k1, NormalReader &rd, bool valid)
+{
+    using Ly = Layout<PREC>;
+    auto normal8 = [&](int c0, float (&z)[8]) {
+        if (!valid) {
+#pragma unroll
+            for (int l = 0; l < 8; ++l) z[l] = 0.0f;
+        } else if (EXACT) {
+            const uint64_t q = static_cast<uint64_t>(i) * (kN / 4) + c0 / 4;
+            const float4 a = normals4(q, n, k0, k1), b = normals4(q + 1, n, k0, k1);
+            z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+        } else {
+#pragma unroll
+            for (int l = 0; l < 8; ++l)
+                z[l] = (c0 + l < d) ? rd.get(static_cast<uint64_t>(i) * d + c0 + l) : 0.0f;
+        }
+    };
+    if (PREC != MC_FP8E4M3) {
+#pragma unroll
+        for (int cb = 0; cb < Ly::kChunks; ++cb) {
+            float z[8];
+            normal8(cb * 8, z);
+            st_shared_v4(tile + Ly::chunk_off(row, cb), pack2<PREC>(z[0], z[1]), pack2<PREC>(z[2], z[3]),
+                         pack2<PREC>(z[4], z[5]), pack2<PREC>(z[6], z[7]));
+        }
+        return 1.0f;
+    } else {
+        float z[kN];
+#pragma unroll
+        for (int cb = 0; cb < kN / 8; ++cb) {
+            float t[8];
+            normal8(cb * 8, t);
+#pragma unroll
+            for (int l = 0; l < 8; ++l) z[cb * 8 + l] = t[l];
+        }
+        float amax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kN; ++j) amax = fmaxf(amax, fabsf(z[j]));
+        const float s = amax > 0.0f ? 448.0f / amax : 1.0f;
+#pragma unroll
+        for (int cb = 0; cb < Ly::kChunks; ++cb) {
+            const float *q = z + cb * 16;
+            st_shared_v4(tile + Ly::chunk_off(row, cb), pack4_e4m3(q[0] * s, q[1] * s, q[2] * s, q[3] * s),
+                         pack4_e4m3(q[4] * s, q[5] * s, q[6] * s, q[7] * s),
+                         pack4_e4m3(q[8] * s, q[9] * s, q[10] * s, q[11] * s),
+                         pack4_e4m3(q[12] * s, q[13] * s, q[14] * s, q[15] * s));
+        }
+        return amax > 0.0f ? amax / 448.0f : 1.0f;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void issue_mmas(uint32_t tmem_d, uint32_t ztile, uint32_t btile)
+{
+    using Ly = Layout<PREC>;
+#pragma unroll
+    for (int kk = 0; kk < Ly::kMmas; ++kk) {
+        const uint64_t ad = tc::smem_desc(ztile + kk * 32, Ly::kGroupBytes, Ly::kSw);
+        const uint64_t bd = tc::smem_desc(btile + kk * 32, Ly::kGroupBytes, Ly::kSw);
+        if (PREC == MC_FP8E4M3) tc::mma_f8(tmem_d, ad, bd, tc::idesc_e4m3(kRows, kN), kk > 0 ? 1u : 0u);
+        else tc::mma_f16(tmem_d, ad, bd, tc::idesc_f16(kRows, kN, PREC == MC_BF16), kk > 0 ? 1u : 0u);
+    }
+}
+
+template <int PREC, int SCHEME, bool STATS, bool EXACT>
+__global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, const TcConst c)
+{
+    using Ly = Layout<PREC>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ float s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ double s_red[32];
+
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t zt[2] = {base, base + Ly::kTileBytes};
+    const uint32_t bt = base + 2 * Ly::kTileBytes;
+    const uint32_t mbar = bt + Ly::kBBytes;
+    const uint32_t tslot = mbar + 16;
+    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
+
+    for (int i = t; i < (kThreads / 32) * a.pay.n * 2; i += kThreads) s_acc[i] = 0.0f;
+    if (t == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_init(mbar + 8, 1);  // factor-tile load barrier
+    }
+    __syncthreads();
+    // factor tile: one bulk (TMA) copy of the pre-swizzled image
+    if (t == 0) {
+        tc::mbar_arrive_expect_tx(mbar + 8, Ly::kBBytes);
+        tc::bulk_g2s(bt, a.bimg, Ly::kBBytes, mbar + 8);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, kN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot_ptr;
+    // CTA-uniform: every change goes through __syncthreads_or.
+    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8, 0, a.wait_cap) ? 0 : 1) != 0;
+
+    uint32_t phase = 0;
+    const int M = a.run.steps, d = a.d;
+    const float inv_m = 1.0f / static_cast<float>(M);
+    const int64_t ntiles = (a.run.paths + kRows - 1) / kRows;
+    const uint32_t row_taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t nl = tile * kRows + t;
+        const bool valid = nl < a.run.paths;
+        const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
+        NormalReader rd;
+        rd.init(n, a.run.k0, a.run.k1);
+        float x[kN];
+#pragma unroll
+        for (int j = 0; j < kN; ++j) x[j] = (SCHEME == MC_LOG_EULER) ? 0.0f : c.s0[j];
+        Stats st{0.0f, -INFINITY, INFINITY};
+
+        float deq_cur = 1.0f, deq_next = 1.0f;
+        if (!aborted) {
+            deq_cur = draw_row<PREC, EXACT>(zt[0], t, 0, d, n, a.run.k0, a.run.k1, rd, valid);
+            tc::fence_proxy_async();
+        }
+        __syncthreads();
+        if (t == 0 && !aborted) {
+            tc::fence_after_sync();
+            issue_mmas<PREC>(tmem, zt[0], bt);
+            tc::mma_commit(mbar);
+        }
+        for (int i = 0; i < M && !aborted; ++i) {
+            if (i + 1 < M) {
+                deq_next = draw_row<PREC, EXACT>(zt[(i + 1) & 1], t, i + 1, d, n, a.run.k0, a.run.k1, rd, valid);
+                tc::fence_proxy_async();
+            }
+            const bool ok = tc::mbar_wait_bounded(mbar, phase & 1u, a.wait_cap);
+            ++phase;
+            tc::fence_after_sync();
+            float v[kN];
+            {
+                float part[16];
+#pragma unroll
+                for (int cc = 0; cc < kN / 16; ++cc) {
+                    tc::tmem_ld16(row_taddr + cc * 16, part);
+#pragma unroll
+                    for (int l = 0; l < 16; ++l) v[cc * 16 + l] = part[l];
+                }
+            }
+            tc::tmem_wait_ld();
+            tc::fence_before_sync();
+            if (__syncthreads_or(ok ? 0 : 1)) aborted = true;
+            if (t == 0 && i + 1 < M && !aborted) {
+                tc::fence_after_sync();
+                issue_mmas<PREC>(tmem, zt[(i + 1) & 1], bt);
+                tc::mma_commit(mbar);
+            }
+            // FP32 state update of step i
+            float u = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kN; ++j) {
+                const float dw = c.cs[j] * (v[j] * deq_cur);
+                if (SCHEME == MC_LOG_EULER) {
+                    x[j] += c.drift[j] + dw;
+                    if (STATS) u = fmaf(c.ws0[j], exp2f(x[j]), u);
+                } else {
+                    x[j] = fmaf(x[j], c.drift[j] + dw, x[j]);
+                    if (STATS) u = fmaf(c.w[j], x[j], u);
+                }
+            }
+            if (STATS) {
+                st.sum += u;
+                st.umax = fmaxf(st.umax, u);
+                st.umin = fminf(st.umin, u);
+            }
+            deq_cur = deq_next;
+        }
+        float uT = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kN; ++j) {
+            if (SCHEME == MC_LOG_EULER) uT = fmaf(c.ws0[j], exp2f(x[j]), uT);
+            else uT = fmaf(c.w[j], x[j], uT);
+        }
+        const float avg = st.sum * inv_m;
+        const bool use = valid && !aborted;
+        for (int p = 0; p < a.pay.n; ++p) {
+            const float f = payoff_eval(a.pay.kind[p], a.pay.strike[p], a.pay.barrier[p], uT, avg, st.umax, st.umin);
+            warp_accumulate(s_acc, a.pay.n, p, use ? f : 0.0f);
+        }
+        __syncthreads();
+    }
+    if (aborted && t == 0) atomicExch(a.err, 1u);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kN);
+    }
+    block_finish(s_acc, s_red, a.pay.n, a.red);
+}
+
+// Factor tile for the MMA's B operand: row n = Lrho[n][0..63] (zero above
+// the diagonal and beyond d), scaled by s_n (E4M3: 448 / max_k |Lrho[n][k]|,
+// else 1), rounded to the operand type, at its swizzled position.  Also the
+// FP32 per-column scale cs_n = c sqrt(dt) sigma_n / s_n and the drift.
+template <int PREC>
+__global__ void tc_prep_kernel(int d, const double *L, const double *sigma, double cfac, double sdt, double r,
+                               double dt, int scheme, uint8_t *bimg, float *cs, float *drift)
+{
+    using Ly = Layout<PREC>;
+    const int nrow = threadIdx.x;
+    if (nrow >= kN) return;
+    double amax = 0.0;
+    for (int k = 0; k < kN; ++k) {
+        const double v = (nrow < d && k <= nrow) ? L[static_cast<int64_t>(nrow) * d + k] : 0.0;
+        amax = fmax(amax, fabs(v));
+    }
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : 1.0;
+    for (int k = 0; k < kN; ++k) {
+        const double v = (nrow < d && k <= nrow) ? L[static_cast<int64_t>(nrow) * d + k] * s : 0.0;
+        const uint32_t off = Ly::chunk_off(nrow, k / Ly::kPerChunk) + (k % Ly::kPerChunk) * Ly::kElemBytes;
+        // rounded through binary32, like the normals (one rule for both operands)
+        const float fv = static_cast<float>(v);
+        if (PREC == MC_BF16) {
+            *reinterpret_cast<__nv_bfloat16 *>(bimg + off) = __float2bfloat16_rn(fv);
+        } else if (PREC == MC_FP16) {
+            *reinterpret_cast<__half *>(bimg + off) = __float2half_rn(fv);
+        } else {
+            uint16_t pr;
+            asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(pr) : "f"(0.0f), "f"(fv));
+            bimg[off] = static_cast<uint8_t>(pr & 0xFFu);
+        }
+    }
+    if (nrow < d) {
+        cs[nrow] = static_cast<float>(cfac * sdt * sigma[nrow] / s);
+        drift[nrow] = static_cast<float>(scheme == MC_LOG_EULER ? cfac * (r - 0.5 * sigma[nrow] * sigma[nrow]) * dt
+                                                                : r * dt);
+    } else {
+        cs[nrow] = 0.0f;
+        drift[nrow] = 0.0f;
+    }
+}
+
+}  // namespace tcb
+
+template <int PREC, int SCHEME>
+const void *basket_tc_select(const TcArgs &a)
+{
+    const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
+    const bool exact = a.d == tcb::kN;
+    if (stats)
+        return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, true, true>)
+                     : reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, true, false>);
+    return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, false, true>)
+                 : reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, false, false>);
+}
+
+template <int PREC>
+int basket_tc_smem()
+{
+    return tcb::Layout<PREC>::kSmem;
+}
+
+template <int PREC>
+cudaError_t tc_prep(int d, const double *L, const double *sigma, double cfac, double sdt, double r, double dt,
+                    int scheme, uint8_t *bimg, float *cs, float *drift, cudaStream_t s)
+{
+    tcb::tc_prep_kernel<PREC><<<1, tcb::kN, 0, s>>>(d, L, sigma, cfac, sdt, r, dt, scheme, bimg, cs, drift);
+    return cudaGetLastError();
+}
+
+#define GBMC_INSTANTIATE_TC(PREC)                                                                         \
+    template const void *basket_tc_select<PREC, MC_LOG_EULER>(const TcArgs &a);                           \
+    template const void *basket_tc_select<PREC, MC_EULER>(const TcArgs &a);                               \
+    template int basket_tc_smem<PREC>();                                                                  \
+    template cudaError_t tc_prep<PREC>(int, const double *, const double *, double, double, double, double, \
+                                       int, uint8_t *, float *, float *, cudaStream_t);
+
+}  // namespace gbmc

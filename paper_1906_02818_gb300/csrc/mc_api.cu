@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -145,6 +146,18 @@ void size_grid(int64_t paths, int block, int resident, int *grid, int *ppt)
     *ppt = static_cast<int>(p);
 }
 
+// Polls of a bounded mbarrier wait before a kernel gives up (GBMC_WAIT_CAP
+// overrides; each poll suspends for at most a few microseconds).
+uint32_t wait_cap()
+{
+    const char *e = std::getenv("GBMC_WAIT_CAP");
+    if (e && *e) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v > 0) return static_cast<uint32_t>(v);
+    }
+    return 1u << 22;
+}
+
 template <class T>
 void dfree(T *&p)
 {
@@ -154,7 +167,7 @@ void dfree(T *&p)
 
 }  // namespace
 
-enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2 };
+enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3 };
 
 struct mc_plan {
     int device = -1;
@@ -165,6 +178,11 @@ struct mc_plan {
     Gbm1dArgs g1{};
     BasketArgs bk{};
     HestonArgs hs{};
+    TcArgs tc{};
+    TcConst tcc{};
+    int prec = MC_FP32;
+    uint8_t *bimg = nullptr;
+    unsigned int *err = nullptr;
     std::vector<unsigned char> cst;
     float *partials = nullptr;
     unsigned int *ticket = nullptr;
@@ -176,7 +194,7 @@ struct mc_plan {
     ~mc_plan()
     {
         dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
-        dfree(dLp); dfree(ddrift); dfree(dstatus);
+        dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err);
     }
 };
 
@@ -251,19 +269,21 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         resident = gbm1d_occupancy(g, P->block) * di.sms;
     } else {
         const int d = m->d;
-        if (c->precision != MC_FP32)
-            return fail(MC_EUNSUPPORTED, "tensor-core contraction not available for this request");
-        const int D = basket_fp32_width(d);
+        const bool tcpath = c->precision != MC_FP32;
+        if (tcpath && d > 64)
+            return fail(MC_EUNSUPPORTED, "tensor-core contraction supports d <= 64 (got %d)", d);
+        if (tcpath && save)
+            return fail(MC_EUNSUPPORTED, "paths are materialised by the FP32 contraction only");
+        const int D = tcpath ? 64 : basket_fp32_width(d);
         if (!D) return fail(MC_EUNSUPPORTED, "FP32 contraction supports d <= 64 (got %d)", d);
-        P->kk = K_BASKET_FP32;
         P->D = D;
         const size_t dd = static_cast<size_t>(d) * d;
         const size_t tri = static_cast<size_t>(d) * (d + 1) / 2;
         MC_CUDA(cudaMalloc(&P->dcorr, dd * sizeof(double)));
         MC_CUDA(cudaMalloc(&P->dL, dd * sizeof(double)));
         MC_CUDA(cudaMalloc(&P->dsig, d * sizeof(double)));
-        MC_CUDA(cudaMalloc(&P->dLp, tri * sizeof(float)));
-        MC_CUDA(cudaMalloc(&P->ddrift, d * sizeof(float)));
+        MC_CUDA(cudaMalloc(&P->dLp, (tcpath ? 64 : tri) * sizeof(float)));
+        MC_CUDA(cudaMalloc(&P->ddrift, (tcpath ? 64 : d) * sizeof(float)));
         MC_CUDA(cudaMalloc(&P->dstatus, sizeof(int)));
         std::vector<double> corr(dd, 0.0);
         if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
@@ -271,43 +291,92 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         MC_CUDA(cudaMemcpyAsync(P->dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
         MC_CUDA(cudaMemcpyAsync(P->dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
         MC_CUDA(launch_cholesky(d, P->dcorr, P->dL, P->dstatus, s));
-        const double cs = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
-        MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cs, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
+        const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
         int status = 0;
-        std::vector<float> Lp(tri), drift(d);
-        MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
-        MC_CUDA(cudaMemcpyAsync(Lp.data(), P->dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
-        MC_CUDA(cudaMemcpyAsync(drift.data(), P->ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
-        MC_CUDA(cudaStreamSynchronize(s));
-        if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
-        // Pack the launch-parameter block: rows of width D, zero beyond d.
-        P->cst.assign(basket_const_bytes(D), 0);
-        size_t oL, oDr, oWs, oW, oS;
-        basket_const_offsets(D, &oL, &oDr, &oWs, &oW, &oS);
-        float *cL = reinterpret_cast<float *>(P->cst.data() + oL);
-        float *cDr = reinterpret_cast<float *>(P->cst.data() + oDr);
-        float *cWs = reinterpret_cast<float *>(P->cst.data() + oWs);
-        float *cW = reinterpret_cast<float *>(P->cst.data() + oW);
-        float *cS = reinterpret_cast<float *>(P->cst.data() + oS);
-        for (int a = 0; a < d; ++a) {
-            for (int k = 0; k <= a; ++k) cL[a * (a + 1) / 2 + k] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + k];
-            const double w = m->weights ? m->weights[a] : 1.0 / d;
-            cDr[a] = drift[a];
-            cWs[a] = static_cast<float>(w * m->s0[a]);
-            cW[a] = static_cast<float>(w);
-            cS[a] = static_cast<float>(m->s0[a]);
+        if (tcpath) {
+            // Quantised, swizzled factor tile + per-column scales (FP64 -> operand type).
+            P->kk = K_BASKET_TC;
+            P->prec = c->precision;
+            MC_CUDA(cudaMalloc(&P->bimg, tc_bimg_bytes(P->prec)));
+            MC_CUDA(cudaMalloc(&P->err, sizeof(unsigned int)));
+            MC_CUDA(cudaMemsetAsync(P->err, 0, sizeof(unsigned int), s));
+            MC_CUDA(launch_tc_prep(P->prec, d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->bimg, P->dLp,
+                                   P->ddrift, s));
+            std::vector<float> cs(64), drift(64);
+            MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(cs.data(), P->dLp, 64 * sizeof(float), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(drift.data(), P->ddrift, 64 * sizeof(float), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+            TcConst &k = P->tcc;
+            std::memset(&k, 0, sizeof k);
+            for (int a = 0; a < 64; ++a) {
+                k.cs[a] = cs[a];
+                k.drift[a] = drift[a];
+                if (a < d) {
+                    const double w = m->weights ? m->weights[a] : 1.0 / d;
+                    k.ws0[a] = static_cast<float>(w * m->s0[a]);
+                    k.w[a] = static_cast<float>(w);
+                    k.s0[a] = static_cast<float>(m->s0[a]);
+                } else {
+                    k.s0[a] = 1.0f;  // padded columns: zero weight, inert state
+                }
+            }
+            TcArgs &ta = P->tc;
+            ta.run = run;
+            ta.d = d;
+            ta.scheme = c->scheme;
+            ta.bimg = P->bimg;
+            ta.pay = ps;
+            ta.red = red;
+            ta.red.err = P->err;
+            ta.err = P->err;
+            ta.wait_cap = wait_cap();
+            P->block = 128;
+            resident = basket_tc_occupancy(P->prec, ta) * di.sms;
+        } else {
+            P->kk = K_BASKET_FP32;
+            MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
+            std::vector<float> Lp(tri), drift(d);
+            MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(Lp.data(), P->dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(drift.data(), P->ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+            // Pack the launch-parameter block: rows of width D, zero beyond d.
+            P->cst.assign(basket_const_bytes(D), 0);
+            size_t oL, oDr, oWs, oW, oS;
+            basket_const_offsets(D, &oL, &oDr, &oWs, &oW, &oS);
+            float *cL = reinterpret_cast<float *>(P->cst.data() + oL);
+            float *cDr = reinterpret_cast<float *>(P->cst.data() + oDr);
+            float *cWs = reinterpret_cast<float *>(P->cst.data() + oWs);
+            float *cW = reinterpret_cast<float *>(P->cst.data() + oW);
+            float *cS = reinterpret_cast<float *>(P->cst.data() + oS);
+            for (int a = 0; a < d; ++a) {
+                for (int k = 0; k <= a; ++k) cL[a * (a + 1) / 2 + k] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + k];
+                const double w = m->weights ? m->weights[a] : 1.0 / d;
+                cDr[a] = drift[a];
+                cWs[a] = static_cast<float>(w * m->s0[a]);
+                cW[a] = static_cast<float>(w);
+                cS[a] = static_cast<float>(m->s0[a]);
+            }
+            BasketArgs &b = P->bk;
+            b.run = run;
+            b.d = d;
+            b.scheme = c->scheme;
+            b.pay = ps;
+            b.red = red;
+            resident = basket_fp32_occupancy(D, b, P->block) * di.sms;
         }
-        BasketArgs &b = P->bk;
-        b.run = run;
-        b.d = d;
-        b.scheme = c->scheme;
-        b.pay = ps;
-        b.red = red;
-        resident = basket_fp32_occupancy(D, b, P->block) * di.sms;
     }
     if (resident <= 0) return fail(MC_ECUDA, "kernel cannot be resident (occupancy query failed)");
     int ppt = 1;
-    size_grid(c->paths, P->block, resident, &P->grid, &ppt);
+    if (P->kk == K_BASKET_TC) {
+        const int64_t tiles = (c->paths + 127) / 128;
+        P->grid = static_cast<int>(tiles < resident ? tiles : resident);
+    } else {
+        size_grid(c->paths, P->block, resident, &P->grid, &ppt);
+    }
     P->g1.run.ppt = ppt;
     P->bk.run.ppt = ppt;
     P->hs.run.ppt = ppt;
@@ -316,7 +385,7 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
         MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
         MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
-        for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red}) {
+        for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red, &P->tc.red}) {
             r->partials = P->partials;
             r->ticket = P->ticket;
             r->out = P->dout;
@@ -327,11 +396,12 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
 
 int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
 {
-    for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red}) r->out = dev_out ? dev_out : P->dout;
+    for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red, &P->tc.red}) r->out = dev_out ? dev_out : P->dout;
     switch (P->kk) {
     case K_GBM1D: MC_CUDA(launch_gbm1d(P->g1, P->grid, P->block, s)); break;
     case K_BASKET_FP32: MC_CUDA(launch_basket_fp32(P->D, P->bk, P->cst.data(), P->grid, P->block, s)); break;
     case K_HESTON: MC_CUDA(launch_heston(P->hs, P->grid, P->block, s)); break;
+    case K_BASKET_TC: MC_CUDA(launch_basket_tc(P->prec, P->tc, P->tcc, P->grid, s)); break;
     }
     return MC_OK;
 }
@@ -398,6 +468,13 @@ int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payo
         cudaError_t e = cudaMemcpyAsync(tmp.data(), P->dout, n_payoff * sizeof(mc_result), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(MC_ECUDA, "mc_price: %s", cudaGetErrorString(e));
+    }
+    if (!rc && P->err) {
+        unsigned int e = 0;
+        if (cudaMemcpy(&e, P->err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = fail(MC_ECUDA, "mc_price: reading the wait status failed");
+        else if (e)
+            rc = fail(MC_ETIMEOUT, "a bounded wait on the tensor-core pipeline gave up");
     }
     if (!rc) std::memcpy(out, tmp.data(), n_payoff * sizeof(mc_result));
     delete P;

@@ -135,6 +135,7 @@ struct ReduceArgs {
     mc_result *out;         // [n_payoff]
     int64_t paths;
     double disc;
+    const unsigned int *err;  // optional: non-zero means a CTA gave up; results become NaN
 };
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -197,12 +198,13 @@ __device__ inline void block_finish(float *s_acc, double *s_red, int np, const R
             __syncthreads();
         }
         if (threadIdx.x == 0) {
+            const bool bad = ra.err && *reinterpret_cast<const volatile unsigned int *>(ra.err) != 0u;
             const double N = static_cast<double>(ra.paths);
             const double mean = t[0] / N, m2 = t[1] / N;
             const double var = fmax(m2 - mean * mean, 0.0);
             mc_result res;
-            res.price = ra.disc * mean;
-            res.se = ra.paths > 1 ? ra.disc * sqrt(var / (N - 1.0)) : 0.0;
+            res.price = bad ? __longlong_as_double(0x7ff8000000000000ll) : ra.disc * mean;
+            res.se = bad ? res.price : (ra.paths > 1 ? ra.disc * sqrt(var / (N - 1.0)) : 0.0);
             ra.out[p] = res;
         }
     }

@@ -59,6 +59,27 @@ struct HestonArgs {
     ReduceArgs red;
 };
 
+// Tensor-core basket (d <= 64, padded to 64): launch-parameter constants per
+// asset column n and the per-launch arguments.
+struct TcConst {
+    float drift[64];  // log-Euler: log2(e) (r - sigma_n^2/2) dt; Euler: r dt
+    float cs[64];     // scale of column n of the MMA result: c sqrt(dt) sigma_n / s_n
+    float ws0[64];    // w_n S0_n
+    float w[64];
+    float s0[64];
+};
+
+struct TcArgs {
+    PathRun run;
+    int d;
+    int scheme;
+    const uint8_t *bimg;   // pre-swizzled quantised factor tile (device)
+    PayoffSet pay;
+    ReduceArgs red;
+    unsigned int *err;     // set to 1 when a bounded wait gave up
+    uint32_t wait_cap;     // polls per mbarrier wait before giving up
+};
+
 // Host launchers (return cudaError_t of the launch).
 cudaError_t launch_gbm1d(const Gbm1dArgs &a, int grid, int block, cudaStream_t s);
 int gbm1d_occupancy(const Gbm1dArgs &a, int block);
@@ -72,6 +93,15 @@ void basket_const_offsets(int D, size_t *L, size_t *drift, size_t *ws0, size_t *
 
 cudaError_t launch_heston(const HestonArgs &a, int grid, int block, cudaStream_t s);
 int heston_occupancy(const HestonArgs &a, int block);
+
+// Tensor-core basket: launch, occupancy, dynamic shared memory, factor prep.
+cudaError_t launch_basket_tc(int prec, const TcArgs &a, const TcConst &c, int grid, cudaStream_t s);
+int basket_tc_occupancy(int prec, const TcArgs &a);
+// Quantised, swizzled factor image (bimg), per-column cs and drift (device).
+cudaError_t launch_tc_prep(int prec, int d, const double *L, const double *sigma, double c, double sdt,
+                           double r, double dt, int scheme, uint8_t *bimg, float *cs, float *drift,
+                           cudaStream_t s);
+int tc_bimg_bytes(int prec);
 
 // FP64 Cholesky of a d x d SPD matrix on the device (one CTA); writes the
 // lower factor to L and 0 / 1 (not positive definite) to *status.

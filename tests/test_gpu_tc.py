@@ -1,0 +1,157 @@
+"""GPU parity of the tensor-core contraction (BF16 / FP16 / E4M3 operands,
+FP32 accumulation and state).
+
+Two checks per case:
+  1. exact pipeline check: the expected price is rebuilt from the oracle's
+     FP64 normals with the operands rounded exactly as the kernel rounds them
+     (tests/quant.py) and the rest of the step in FP64; the kernel must match
+     it to 1e-5 relative (+ the barrier band), so any layout, swizzle or
+     descriptor error fails;
+  2. reduced-precision error: the relative error against the unrounded FP64
+     oracle on the same stream is reported and must stay within 3 standard
+     errors (Sec. V.A: low-precision multiplies add no significant bias).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import BAND, REL, cfg_of, gbm_model, oracle_gbm
+from quant import quantize
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0):
+    """Per-path discounted payoffs and monitored U of the quantised-operand
+    scheme: dW_n = sqrt(dt) sigma_n sum_k Lq[n,k] zq[k] / (s_n s_z)."""
+    d = len(w["s0"])
+    L = orc.cholesky(w["corr"]) if w.get("corr") is not None else np.eye(d)
+    s_n = np.ones(d)
+    if prec == "fp8":
+        s_n = np.where(np.abs(L).max(axis=1) > 0, 448.0 / np.abs(L).max(axis=1), 1.0)
+    Lq = quantize((L * s_n[:, None]).astype(np.float32), prec) / s_n[:, None]
+    dt = w["T"] / steps
+    Z = np.stack([orc.normals(w["seed"], path_offset + n, 0, steps * d) for n in range(paths)]).reshape(paths, steps, d)
+    Z32 = Z.astype(np.float32)
+    if prec == "fp8":
+        amax = np.abs(Z32).max(axis=2, keepdims=True)
+        s = (np.float32(448.0) / amax).astype(np.float32)
+        # the kernel multiplies by amax/448 computed in binary32
+        Zq = quantize((Z32 * s).astype(np.float32), "fp8") * (amax / np.float32(448.0)).astype(np.float32)
+    else:
+        Zq = quantize(Z32, prec)
+    sig, s0, wt = w["sigma"], w["s0"], w["weights"]
+    x = np.log(s0)[None, :].repeat(paths, 0) if scheme == "log_euler" else s0[None, :].repeat(paths, 0).copy()
+    U = np.empty((steps + 1, paths))
+    U[0] = wt @ s0
+    for i in range(steps):
+        dW = np.sqrt(dt) * sig[None, :] * (Zq[:, i, :] @ Lq.T)
+        if scheme == "log_euler":
+            x = x + (w["r"] - 0.5 * sig ** 2) * dt + dW
+            S = np.exp(x)
+        else:
+            x = x * (1.0 + w["r"] * dt + dW)
+            S = x
+        U[i + 1] = S @ wt
+    return U
+
+
+def payoffs_from_U(U, pays, r, T):
+    disc = np.exp(-r * T)
+    uT, avg, mx, mn = U[-1], U[1:].mean(axis=0), U[1:].max(axis=0), U[1:].min(axis=0)
+    out = []
+    for p in pays:
+        K, H, k = p["strike"], p.get("barrier", np.inf), p["kind"]
+        call, put = np.maximum(uT - K, 0), np.maximum(K - uT, 0)
+        v = {"call": call, "put": put, "asian_call": np.maximum(avg - K, 0),
+             "uo_call": np.where(mx >= H, 0, call), "ui_call": np.where(mx >= H, call, 0)}[k]
+        out.append(disc * v)
+    return np.array(out)
+
+
+def band(U, pays, per_path):
+    m = []
+    for i, p in enumerate(pays):
+        if p["kind"].startswith("u") and "barrier" in p:
+            near = np.abs(U[1:].max(axis=0) - p["barrier"]) <= BAND * p["barrier"]
+            m.append(float(np.sum(np.maximum(U[-1][near] - p["strike"], 0))) / U.shape[1] * 1.01 + 1e-12)
+        else:
+            m.append(0.0)
+    return m
+
+
+def _case(d, k, paths, steps, seed=5):
+    s0, sg, corr = workloads.basket_market(d, k, seed=seed)
+    w = np.full(d, 1.0 / d)
+    b0 = float(w @ s0)
+    pays = [dict(kind="call", strike=b0), dict(kind="put", strike=b0), dict(kind="asian_call", strike=b0),
+            dict(kind="uo_call", strike=b0, barrier=1.1 * b0), dict(kind="ui_call", strike=b0, barrier=1.1 * b0)]
+    return dict(s0=s0, sigma=sg, corr=corr, weights=w, r=0.05, T=1.0, steps=steps, paths=paths, seed=42), pays
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp8"])
+@pytest.mark.parametrize("d,scheme", [(64, "log_euler"), (40, "log_euler"), (64, "euler"), (7, "log_euler")])
+def test_tc_matches_quantised_emulation(gb, orc, prec, d, scheme):
+    w, pays = _case(d, 3, 1000, 12)
+    got = gb.price(gbm_model(w), cfg_of(w, precision=prec, scheme=scheme), pays)
+    U = emulate(orc, w, prec, w["paths"], w["steps"], scheme)
+    want = payoffs_from_U(U, pays, w["r"], w["T"])
+    bm = band(U, pays, want)
+    for i, p in enumerate(pays):
+        m = want[i].mean()
+        tol = REL * max(abs(m), 1e-6) + bm[i]
+        assert abs(got[i][0] - m) <= tol, (prec, d, scheme, p, got[i][0], m, tol)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp8"])
+def test_tc_reduced_precision_error_vs_fp64(gb, orc, prec):
+    """The d = 64 workload on 4096 paths: error of the reduced-precision
+    contraction against the FP64 oracle (same stream) within 3 SE."""
+    w = workloads.basket_d64(paths=4096)
+    got = gb.price(gbm_model(w), cfg_of(w, precision=prec), w["payoffs"])
+    ref = oracle_gbm(orc, w, w["paths"], w["payoffs"])
+    for i, p in enumerate(w["payoffs"]):
+        m, se = orc.mean_se(ref[i])
+        rel = abs(got[i][0] - m) / abs(m)
+        print(f"{prec} {p['kind']}: {got[i][0]:.6f} vs FP64 {m:.6f}  rel err {rel:.2e}  (SE {se:.4f})")
+        assert abs(got[i][0] - m) <= 3 * se
+
+
+def test_tc_full_size_bf16_vs_fp32(gb):
+    """Full d = 64 workload (2^18 paths x 252 steps) in the benchmark's launch
+    shape: BF16 and FP32 contractions agree within 3 SE of each other, and
+    the BF16 run equals the combination of its 4 path shards."""
+    w = workloads.basket_d64()
+    bf = gb.price(gbm_model(w), cfg_of(w, precision="bf16"), w["payoffs"])
+    fp = gb.price(gbm_model(w), cfg_of(w), w["payoffs"])
+    for i in range(len(w["payoffs"])):
+        assert abs(bf[i][0] - fp[i][0]) <= 3 * fp[i][1]
+    N = w["paths"]
+    parts = [gb.price(gbm_model(w), cfg_of(w, paths=N // 4, path_offset=k * N // 4, precision="bf16"), w["payoffs"])
+             for k in range(4)]
+    for i in range(len(w["payoffs"])):
+        assert abs(np.mean([p[i][0] for p in parts]) - bf[i][0]) <= 1e-6 * abs(bf[i][0])
+
+
+def test_tc_sampled_windows_full_range(gb, orc):
+    """Windows sampled across the full 2^18-path range match the quantised
+    emulation exactly (the counter-based stream makes any window reproducible)."""
+    w = workloads.basket_d64()
+    pays = w["payoffs"]
+    steps = 20
+    for off in (0, 131_101, (1 << 18) - 200):
+        got = gb.price(gbm_model(w), cfg_of(w, paths=200, path_offset=off, steps=steps, precision="bf16"), pays)
+        U = emulate(orc, w, "bf16", 200, steps, path_offset=off)
+        want = payoffs_from_U(U, pays, w["r"], w["T"])
+        bm = band(U, pays, want)
+        for i in range(len(pays)):
+            m = want[i].mean()
+            assert abs(got[i][0] - m) <= REL * abs(m) + bm[i], (off, pays[i], got[i][0], m)
