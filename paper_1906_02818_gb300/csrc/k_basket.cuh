@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const BasketArgs a,
                     const int64_t slot = (i + 1) / a.run.save_every;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * exp2f(x[j]) : x[j];
+                        const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * ex2_approx(x[j]) : x[j];
                         if (STATS) u = fmaf(c.w[j], Sj, u);
                         if (SAVE && ((i + 1) % a.run.save_every) == 0 && j < d)
                             a.run.save[(slot * d + j) * a.run.paths + nl] = Sj;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const BasketArgs a,
             float u = 0.0f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                if (SCHEME == MC_LOG_EULER) u = fmaf(c.ws0[j], exp2f(x[j]), u);
+                if (SCHEME == MC_LOG_EULER) u = fmaf(c.ws0[j], ex2_approx(x[j]), u);
                 else u = fmaf(c.w[j], x[j], u);
             }
             uT = u;

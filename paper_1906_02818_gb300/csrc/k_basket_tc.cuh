@@ -12,8 +12,8 @@
 //   2. one thread issues tcgen05.mma: D[128 x 64] (TMEM, FP32) = Z_i Lq^T,
 //      where Lq is the quantised Cholesky factor of the correlation (rows
 //      scaled to the operand range), resident in shared memory;
-//   3. every thread reads its row of D back (tcgen05.ld) and applies the
-//      FP32 step: y_n += drift_n + cs_n D_n (log-Euler on log2(S_n/S0_n)), or
+//   3. every thread reads its row of D back (tcgen05.ld, 16 columns at a
+//      time) and applies the FP32 step: y_n += drift_n + cs_n D_n (log-Euler on log2(S_n/S0_n)), or
 //      S_n <- S_n (1 + r dt + cs_n D_n) (Euler), with cs_n folding
 //      sqrt(dt) sigma_n and the operand scales.
 // Z tiles are double-buffered so that drawing Z_{i+1} overlaps MMA_i.  All
@@ -231,36 +231,32 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
             const bool ok = tc::mbar_wait_bounded(mbar, phase & 1u, a.wait_cap);
             ++phase;
             tc::fence_after_sync();
-            float v[kN];
-            {
-                float part[16];
+            // FP32 state update of step i, 16 accumulator columns at a time
+            float u = 0.0f;
 #pragma unroll
-                for (int cc = 0; cc < kN / 16; ++cc) {
-                    tc::tmem_ld16(row_taddr + cc * 16, part);
+            for (int cc = 0; cc < kN / 16; ++cc) {
+                float v[16];
+                tc::tmem_ld16(row_taddr + cc * 16, v);
+                tc::tmem_wait_ld();
 #pragma unroll
-                    for (int l = 0; l < 16; ++l) v[cc * 16 + l] = part[l];
+                for (int l = 0; l < 16; ++l) {
+                    const int j = cc * 16 + l;
+                    const float dw = c.cs[j] * (v[l] * deq_cur);
+                    if (SCHEME == MC_LOG_EULER) {
+                        x[j] += c.drift[j] + dw;
+                        if (STATS) u = fmaf(c.ws0[j], ex2_approx(x[j]), u);
+                    } else {
+                        x[j] = fmaf(x[j], c.drift[j] + dw, x[j]);
+                        if (STATS) u = fmaf(c.w[j], x[j], u);
+                    }
                 }
             }
-            tc::tmem_wait_ld();
             tc::fence_before_sync();
             if (__syncthreads_or(ok ? 0 : 1)) aborted = true;
             if (t == 0 && i + 1 < M && !aborted) {
                 tc::fence_after_sync();
                 issue_mmas<PREC>(tmem, zt[(i + 1) & 1], bt);
                 tc::mma_commit(mbar);
-            }
-            // FP32 state update of step i
-            float u = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kN; ++j) {
-                const float dw = c.cs[j] * (v[j] * deq_cur);
-                if (SCHEME == MC_LOG_EULER) {
-                    x[j] += c.drift[j] + dw;
-                    if (STATS) u = fmaf(c.ws0[j], exp2f(x[j]), u);
-                } else {
-                    x[j] = fmaf(x[j], c.drift[j] + dw, x[j]);
-                    if (STATS) u = fmaf(c.w[j], x[j], u);
-                }
             }
             if (STATS) {
                 st.sum += u;
@@ -272,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
         float uT = 0.0f;
 #pragma unroll
         for (int j = 0; j < kN; ++j) {
-            if (SCHEME == MC_LOG_EULER) uT = fmaf(c.ws0[j], exp2f(x[j]), uT);
+            if (SCHEME == MC_LOG_EULER) uT = fmaf(c.ws0[j], ex2_approx(x[j]), uT);
             else uT = fmaf(c.w[j], x[j], uT);
         }
         const float avg = st.sum * inv_m;

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
                         if (SCHEME == MC_LOG_EULER) y += fmaf(a.b, zz[l], a.a);
                         else y = fmaf(y, fmaf(a.b, zz[l], a.a), y);
                         if (STATS || SAVE) {
-                            const float S = (SCHEME == MC_LOG_EULER) ? a.s0 * exp2f(y) : y;
+                            const float S = (SCHEME == MC_LOG_EULER) ? a.s0 * ex2_approx(y) : y;
                             if (STATS) st.add(S);
                             if (SAVE && ((i + 1) % a.run.save_every) == 0)
                                 a.run.save[static_cast<int64_t>((i + 1) / a.run.save_every) * a.run.paths + nl] = S;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
                     }
                 }
             }
-            uT = (SCHEME == MC_LOG_EULER) ? a.s0 * exp2f(y) : y;
+            uT = (SCHEME == MC_LOG_EULER) ? a.s0 * ex2_approx(y) : y;
             avg = st.sum * inv_m;
         }
         if (a.pay.n > 0) accumulate_payoffs(s_acc, a.pay, valid, uT, avg, st);

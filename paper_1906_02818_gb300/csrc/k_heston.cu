@@ -45,12 +45,12 @@ __global__ void __launch_bounds__(kBlock) heston_kernel(const HestonArgs a)
                     const int i = 2 * q + l;
                     if (i < M) {
                         const float vp = fmaxf(v, 0.0f);
-                        const float sq = sqrtf(vp * dt);
+                        const float sq = sqrt_approx(vp * dt);
                         const float c = fmaf(a.rho, z1s[l], a.rhoc * z2s[l]);
                         y = fmaf(kLog2e, fmaf(sq, c, (a.r - 0.5f * vp) * dt), y);
                         v = v + fmaf(a.xi * sq, z1s[l], kdt * (a.theta - vp));
                         if (STATS || SAVE) {
-                            S = a.s0 * exp2f(y);
+                            S = a.s0 * ex2_approx(y);
                             sum += S;
                             umax = fmaxf(umax, S);
                             umin = fminf(umin, S);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBlock) heston_kernel(const HestonArgs a)
                     }
                 }
             }
-            uT = a.s0 * exp2f(y);
+            uT = a.s0 * ex2_approx(y);
             avg = sum * inv_m;
         }
         for (int p = 0; p < a.pay.n; ++p) {

@@ -41,15 +41,53 @@ __device__ __forceinline__ float u01(uint32_t x)
 }
 
 // Box-Muller on one pair of words: z0 = r cos(2 pi u_b), z1 = r sin(2 pi u_b),
-// r = sqrt(-2 ln u_a).
+// r = sqrt(-2 ln u_a), evaluated with the SFU's approximate instructions
+// (lg2, sqrt, sin, cos: one issue slot each).  The angle is taken as
+// theta = 2 pi (u_b - 1/2) in (-pi, pi), the range where sin/cos.approx are
+// most accurate, and the sign flip (cos(theta) = -cos(2 pi u_b), likewise
+// sin) is folded into r.  -2 ln u_a is clamped at 0: lg2.approx has an
+// absolute error near 2^-22 close to u = 1.  Per-normal absolute error is a
+// few 1e-6 at worst.
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
 {
     const float ua = u01(a), ub = u01(b);
-    const float rad = sqrtf(-2.0f * logf(ua));
-    float s, c;
-    sincospif(2.0f * ub, &s, &c);
-    z0 = rad * c;
-    z1 = rad * s;
+    // -2 ln u = -2 ln(2) log2(u)
+    const float r2 = fmaxf(-1.3862943611198906f * lg2_approx(ua), 0.0f);
+    const float nrad = -sqrt_approx(r2);
+    const float theta = 6.2831853071795865f * (ub - 0.5f);
+    z0 = nrad * cos_approx(theta);
+    z1 = nrad * sin_approx(theta);
 }
 
 // The four normals of block q of stream (path) n.
