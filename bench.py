@@ -30,10 +30,13 @@ METRIC = "path-steps/s and prices/s at stated std err vs FP64 oracle; roofline f
 UNIT = "path-steps/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Lane-level instructions the basket kernel executes per path-step, from
-# `ncu --metrics smsp__thread_inst_executed.sum` on the same build (profiles/).
-# None until measured for a precision.
-INST_PER_PATH_STEP = {"fp32": None, "bf16": None, "fp16": None, "fp8": None}
+# Warp instructions the basket kernel issues per path-step (smsp__inst_executed.sum
+# divided by paths x steps) from the ncu capture of the same kernel build,
+# recorded in profiles/.  None where no capture of the current build exists.
+INST_PER_PATH_STEP = {"fp32": None, "bf16": 52.89, "fp16": None, "fp8": None}
+# DRAM bytes (read + write) of one launch of that kernel in the same capture:
+# only the factor tile and launch constants are read, whatever the path count.
+DRAM_BYTES_PER_LAUNCH = {"bf16": 86528}
 
 
 def peaks():
@@ -47,6 +50,14 @@ def peaks():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
 
 
 class ClockSampler:
@@ -160,8 +171,6 @@ def run_gbmc(args):
     cfg = dict(steps=w["steps"], T=w["T"], paths=P, seed=w["seed"], path_offset=rank * P,
                precision=args.prec)
     stream = torch.cuda.Stream()
-    plan = gb.Plan(model, cfg, w["payoffs"], stream=stream)
-    out = torch.empty((len(w["payoffs"]), 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -169,31 +178,39 @@ def run_gbmc(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            plan.execute(out, stream=stream)
-    barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        barrier()
+    def timed(prec, clock_sampler=None):
+        c = dict(cfg, precision=prec)
+        plan = gb.Plan(model, c, w["payoffs"], stream=stream)
+        out = torch.empty((len(w["payoffs"]), 2), dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
-            for s, e in evs:
-                flush.fill_(1.0)  # L2 flush between timed iterations (outside the events)
-                s.record(stream)
+            for _ in range(args.warmup):
                 plan.execute(out, stream=stream)
-                e.record(stream)
         barrier()
-    step_ms = [s.elapsed_time(e) for s, e in evs]
-    tot_ms = float(sum(step_ms))
-    t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_ms = float(t.item())
-    ms_step = tot_ms / args.steps
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with (clock_sampler or _Null()):
+            barrier()
+            with torch.cuda.stream(stream):
+                for s, e in evs:
+                    flush.fill_(1.0)  # L2 flush between timed iterations (outside the events)
+                    s.record(stream)
+                    plan.execute(out, stream=stream)
+                    e.record(stream)
+            barrier()
+        step_ms = [s.elapsed_time(e) for s, e in evs]
+        t = torch.tensor([float(sum(step_ms))], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        launches = plan.launches * args.steps
+        res = out.cpu().numpy()
+        plan.close()
+        return float(t.item()) / args.steps, step_ms, res, launches
+
+    clk = ClockSampler(local)
+    ms_step, step_ms, res, launches = timed(args.prec, clk)
+    fp32 = timed("fp32") if args.prec != "fp32" else None
     path_steps = P * w["steps"] * world
     value = path_steps / (ms_step * 1e-3)
-    res = out.cpu().numpy()
-    launches = plan.launches * args.steps
 
     # End to end through the public C-ABI call with host buffers: model
     # upload, Cholesky, kernels, results back to the host, every step.
@@ -213,15 +230,17 @@ def run_gbmc(args):
     pk, pk_kind = peaks()
     clocks = clk.summary()
     inst = INST_PER_PATH_STEP.get(args.prec)
-    issue_peak = 152 * 4 * 32 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # T lane-instr/s
+    issue_peak = 152 * 4 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # T warp-inst/s
     if inst is not None:
         achieved = inst * P * w["steps"] / (ms_step * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": issue_peak, "unit": "Tinst/s",
-                "frac": achieved / issue_peak, "traffic": None,
-                "basis": f"lane instructions per path-step {inst} (ncu) x path-steps / event time; "
-                         f"peak = 152 SMs x 4 issue x 32 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz ({pk_kind})"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": issue_peak, "unit": "Twarp-inst/s",
+                "frac": achieved / issue_peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(args.prec),
+                "kernel": "basket_tc_kernel" if args.prec != "fp32" else "basket_fp32_kernel",
+                "basis": f"{inst} warp instructions per path-step (ncu, profiles/) x path-steps / CUDA-event "
+                         f"time; peak = 152 SMs x 4 issue slots x {pk.get('sm_max_mhz', 2070.0)} MHz "
+                         f"(issue rate; sm_max_mhz from MEASURED_PEAKS.json, {pk_kind})"}
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": issue_peak, "unit": "Tinst/s", "frac": None,
+        roof = {"bound": "alu", "achieved": None, "peak": issue_peak, "unit": "Twarp-inst/s", "frac": None,
                 "traffic": None, "basis": "instruction count per path-step not yet measured for this precision"}
     # the contraction's own FP32 FMA-pipe fraction (algorithmic: d(d+1) flop per path-step)
     fma_peak = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -253,11 +272,16 @@ def run_gbmc(args):
             "contraction_fp32_tflops": {"achieved": contraction_tflops, "peak": fma_peak,
                                         "frac": contraction_tflops / fma_peak},
             "clocks": clocks,
+            "fp32_contraction": None if fp32 is None else {
+                "value": path_steps / (fp32[0] * 1e-3), "ms_per_step": fp32[0],
+                "results": [{"payoff": p["kind"], "price": float(fp32[2][i, 0]), "std_err": float(fp32[2][i, 1])}
+                            for i, p in enumerate(w["payoffs"])],
+                "diff_vs_headline_in_se": [float(abs(res[i, 0] - fp32[2][i, 0]) / fp32[2][i, 1])
+                                           for i in range(len(w["payoffs"]))]},
             "cpu_baseline": cpu,
             "step_ms_min_max": [min(step_ms), max(step_ms)],
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -265,10 +289,10 @@ def run_gbmc(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16", "fp8"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -1,5 +1,8 @@
 // Dispatch of the tensor-core basket kernels (instantiated per operand type
 // in k_basket_tc_{bf16,fp16,fp8}.cu).
+#include <cstdio>
+#include <cstdlib>
+
 #include "mc_kernels.cuh"
 
 namespace gbmc {
@@ -55,8 +58,29 @@ int basket_tc_occupancy(int prec, const TcArgs &a)
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kTcThreads, smem) != cudaSuccess) return 0;
-    // every resident CTA holds 64 TMEM columns of the SM's 512
-    return nb > 8 ? 8 : nb;
+    // The same bound computed from the kernel's resources: registers (per-warp
+    // allocation in units of 256), shared memory (static + dynamic + the
+    // per-block reservation), threads, and TMEM (64 of 512 columns per CTA).
+    cudaFuncAttributes fa;
+    int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0, thr_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return nb > 8 ? 8 : nb;
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int m = regs_sm / (warp_regs * (kTcThreads / 32));
+    const int per_block_smem = static_cast<int>(fa.sharedSizeBytes) + smem + smem_res;
+    m = per_block_smem > 0 && smem_sm / per_block_smem < m ? smem_sm / per_block_smem : m;
+    m = thr_sm / kTcThreads < m ? thr_sm / kTcThreads : m;
+    m = m > 8 ? 8 : m;
+    if (std::getenv("GBMC_DEBUG"))
+        std::fprintf(stderr, "[gbmc] tc occupancy: runtime %d, resources %d (regs %d, smem %d)\n", nb, m,
+                     fa.numRegs, per_block_smem);
+    // The runtime's answer can be lower than the resource bound for kernels
+    // that use tensor memory; more CTAs than fit simply wait for a slot.
+    return nb > m ? nb : m;
 }
 
 cudaError_t launch_tc_prep(int prec, int d, const double *L, const double *sigma, double c, double sdt,
