@@ -161,6 +161,36 @@ int mc_plan_destroy(mc_plan *plan);
 /* Number of kernel launches one mc_plan_execute issues (for accounting). */
 int mc_plan_launches(const mc_plan *plan);
 
+/*
+ * mc_price_gbm1d_noalloc -- single-asset GBM pricing that allocates nothing.
+ * (The paper has no counterpart: this is a deployment variant of mc_price.)
+ *
+ * For callers that must not call cudaMalloc or any allocating routine: code
+ * that runs under another framework's memory pool or allocator hooks, or
+ * inside a latency-critical loop where a device allocation (which can
+ * synchronise the device) is not allowed.  The caller passes the inputs
+ * (host structs, as for mc_price) and the output; the kernel's scratch
+ * (per-block FP32 partial sums and the last-block ticket) is a fixed device
+ * array inside the library, MC_NOALLOC_PARTIALS floats (512 KiB) plus 256
+ * bytes, which every GPU that loads the library holds until the process
+ * exits.
+ *   model: kind MC_GBM with d == 1; cfg, payoffs as for mc_price
+ *          (1 <= n_payoff <= MC_MAX_PAYOFFS; larger counts are rejected with
+ *          MC_EINVAL).  The grid is limited to the blocks whose partial sums
+ *          fit the array; any path count is accepted.
+ *   dev_out: DEVICE buffer of n_payoff mc_result, written asynchronously on
+ *          `stream`; nothing is synchronised.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind;
+ * the ticket that must start at zero is cleared at each call.  Calls whose
+ * executions overlap on the GPU (other streams, other threads) race on the
+ * array: serialise them.
+ */
+#define MC_NOALLOC_PARTIALS 131072
+int mc_price_gbm1d_noalloc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs,
+                           int32_t n_payoff, mc_result *dev_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

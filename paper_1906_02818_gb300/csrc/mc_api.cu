@@ -167,6 +167,12 @@ void dfree(T *&p)
 
 }  // namespace
 
+int gbmc::set_last_error(int code, const char *msg)
+{
+    g_err = msg ? msg : "";
+    return code;
+}
+
 enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3 };
 
 struct mc_plan {

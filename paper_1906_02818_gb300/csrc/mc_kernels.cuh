@@ -80,6 +80,9 @@ struct TcArgs {
     uint32_t wait_cap;     // polls per mbarrier wait before giving up
 };
 
+// Records the thread-local message returned by mc_last_error(); returns code.
+int set_last_error(int code, const char *msg);
+
 // Host launchers (return cudaError_t of the launch).
 cudaError_t launch_gbm1d(const Gbm1dArgs &a, int grid, int block, cudaStream_t s);
 int gbm1d_occupancy(const Gbm1dArgs &a, int block);

@@ -62,6 +62,9 @@ SIGNATURES = [
     ("mc_plan_execute", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_plan_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("mc_plan_launches", ctypes.c_int, [ctypes.c_void_p]),
+    ("mc_price_gbm1d_noalloc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg),
+                                              ctypes.POINTER(McPayoff), ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
 ]
 
 _lib = None
