@@ -143,6 +143,32 @@ int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payo
              int32_t n_payoff, mc_result *out, void *stream);
 
 /*
+ * mc_greek_count -- number of Greeks mc_greeks returns per payoff:
+ *   MC_GBM: 2d + 1 (d/dS0_a, a < d; d/dsigma_a; d/dr), MC_HESTON: 7
+ *   (d/dS0, d/dv0, d/dr, d/dkappa, d/dtheta, d/dxi, d/drho).  -1 on NULL.
+ */
+int32_t mc_greek_count(const mc_model *model);
+
+/*
+ * mc_greeks -- pathwise (infinitesimal perturbation) Greeks of the discounted
+ * prices (Sec. I.A.3; the paper obtains them by back-propagation through the
+ * simulation, Sec. VI.A.2), with their standard errors, on the same paths as
+ * the prices.  d/dr includes the -T * price term of the discount factor.
+ *   MC_HESTON: reverse-mode adjoint kernel; the path state is checkpointed
+ *     every cfg->ckpt_every steps (0 = 32, at most 64) in device scratch and
+ *     each segment is recomputed from its checkpoint during the backward
+ *     sweep.  d sqrt(v+)/dv is taken as 0 where v <= 0.
+ *   MC_GBM: d == 1 and MC_LOG_EULER (the adjoint of log S is constant along
+ *     the path and the sweep reduces to closed forms per path).
+ * Payoffs: European and Asian kinds only (a barrier's knock indicator has no
+ * pathwise derivative: MC_EUNSUPPORTED).
+ *   prices: host [n_payoff] or NULL; greeks: host [n_payoff][mc_greek_count].
+ * Synchronises `stream` before returning.
+ */
+int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+              mc_result *prices, mc_result *greeks, void *stream);
+
+/*
  * Plans: the same computation as mc_price split into a set-up phase (argument
  * checks, upload of the model, FP64 Cholesky factorisation on the device,
  * scaled copies of the factor, device scratch for per-block partial sums)

@@ -10,7 +10,10 @@ from .native import MCError, PAYOFF, PRECISION, SCHEME  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("price", "simulate", "Plan"):
+    if name in ("price", "simulate", "greeks", "Plan"):
         from . import api
         return getattr(api, name)
+    if name in ("HestonPricer", "GbmPricer"):
+        from . import autograd
+        return getattr(autograd, name)
     raise AttributeError(name)

@@ -90,6 +90,21 @@ def price(model: dict, cfg: dict, payoffs, stream=None):
     return [(r.price, r.se) for r in out]
 
 
+def greeks(model: dict, cfg: dict, payoffs, stream=None):
+    """Pathwise Greeks: (prices, greeks) with prices a list of (price, se) and
+    greeks an array [n_payoff, G, 2] of (mean, se); G = 7 for Heston
+    (S0, v0, r, kappa, theta, xi, rho), 3 for single-asset GBM (S0, sigma, r)."""
+    L = native.lib()
+    mm = _Marshalled(model, cfg, payoffs)
+    G = L.mc_greek_count(ctypes.byref(mm.model))
+    pr = (McResult * mm.n_payoff)()
+    gr = (McResult * (mm.n_payoff * G))()
+    check(L.mc_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, pr, gr,
+                      _stream_handle(stream)))
+    g = np.array([[r.price, r.se] for r in gr]).reshape(mm.n_payoff, G, 2)
+    return [(r.price, r.se) for r in pr], g
+
+
 def simulate(model: dict, cfg: dict, save_every: int = 1, stream=None):
     """Simulated paths as a CUDA float32 tensor [steps/save_every + 1, D, paths]."""
     import torch

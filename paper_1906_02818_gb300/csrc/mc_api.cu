@@ -196,11 +196,12 @@ struct mc_plan {
     double *dcorr = nullptr, *dL = nullptr, *dsig = nullptr;
     float *dLp = nullptr, *ddrift = nullptr;
     int *dstatus = nullptr;
+    float *ckpt = nullptr;
 
     ~mc_plan()
     {
         dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
-        dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err);
+        dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err); dfree(ckpt);
     }
 };
 
@@ -485,6 +486,103 @@ int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payo
     if (!rc) std::memcpy(out, tmp.data(), n_payoff * sizeof(mc_result));
     delete P;
     return rc;
+}
+
+int32_t mc_greek_count(const mc_model *model)
+{
+    if (!model) return fail(MC_EINVAL, "model is NULL");
+    return model->kind == MC_HESTON ? 7 : 2 * model->d + 1;
+}
+
+int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, mc_result *prices,
+              mc_result *greeks, void *stream)
+{
+    int rc;
+    if (!greeks) return fail(MC_EINVAL, "greeks is NULL");
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
+    if (np < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
+    PayoffSet ps;
+    if ((rc = build_payoffs(pays, np, &ps))) return rc;
+    for (int i = 0; i < np; ++i)
+        if (ps.kind[i] > MC_ASIAN_PUT)
+            return fail(MC_EUNSUPPORTED, "payoff %d: barrier payoffs have no pathwise Greek", i);
+    if (m->kind == MC_GBM && m->d != 1)
+        return fail(MC_EUNSUPPORTED, "pathwise Greeks for d > 1 are not available in this build");
+    if (m->kind == MC_GBM && c->scheme != MC_LOG_EULER)
+        return fail(MC_EUNSUPPORTED, "GBM Greeks are computed for the log-Euler scheme");
+    const int K = c->ckpt_every ? c->ckpt_every : 32;
+    if (m->kind == MC_HESTON && (K < 1 || K > 64)) return fail(MC_EINVAL, "ckpt_every = %d outside [1, 64]", K);
+    const int G = mc_greek_count(m);
+    const int nv = np * (G + 1);
+    if (nv * 2 * 4 * 4 > 48 * 1024) return fail(MC_EINVAL, "too many payoffs for one Greeks launch");
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const double w = m->weights ? m->weights[0] : 1.0;
+    GreeksArgs a{};
+    a.run.paths = c->paths;
+    a.run.path_offset = c->path_offset;
+    a.run.k0 = static_cast<uint32_t>(c->seed);
+    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    a.run.steps = c->steps;
+    a.run.save_every = 1;
+    a.model = m->kind;
+    a.s0 = static_cast<float>(m->s0[0]);
+    a.s0w = static_cast<float>(w * m->s0[0]);
+    a.r = static_cast<float>(m->r);
+    a.dt = static_cast<float>(dt);
+    a.sdt = static_cast<float>(sdt);
+    a.T = static_cast<float>(c->T);
+    if (m->kind == MC_GBM) {
+        const double sg = m->sigma[0];
+        a.sigma = static_cast<float>(sg);
+        a.a2 = static_cast<float>(M_LOG2E * (m->r - 0.5 * sg * sg) * dt);
+        a.b2 = static_cast<float>(M_LOG2E * sg * sdt);
+    } else {
+        a.v0 = static_cast<float>(m->v0);
+        a.kappa = static_cast<float>(m->kappa);
+        a.theta = static_cast<float>(m->theta);
+        a.xi = static_cast<float>(m->xi);
+        a.rho = static_cast<float>(m->rho);
+        a.rhoc = static_cast<float>(std::sqrt(1.0 - m->rho * m->rho));
+        a.K = K;
+    }
+    a.pay = ps;
+    const int block = greeks_block();
+    const int occ = greeks_occupancy(a.model, np);
+    if (occ <= 0) return fail(MC_ECUDA, "Greeks kernel cannot be resident");
+    int grid = 0, ppt = 1;
+    size_grid(c->paths, block, occ * di.sms, &grid, &ppt);
+    a.run.ppt = ppt;
+
+    mc_plan P;  // owns the scratch buffers (freed on return)
+    P.np = nv;
+    MC_CUDA(cudaMalloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned int)));
+    MC_CUDA(cudaMemsetAsync(P.ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMalloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
+    if (m->kind == MC_HESTON) {
+        const size_t nseg = (c->steps + K - 1) / K;
+        MC_CUDA(cudaMalloc(&P.ckpt, nseg * 2 * static_cast<size_t>(grid) * block * sizeof(float)));
+    }
+    a.ckpt = P.ckpt;
+    a.red.partials = P.partials;
+    a.red.ticket = P.ticket;
+    a.red.out = P.dout;
+    a.red.paths = c->paths;
+    a.red.disc = std::exp(-m->r * c->T);
+    a.red.err = nullptr;
+    MC_CUDA(launch_greeks(a, grid, s));
+    std::vector<mc_result> tmp(nv);
+    MC_CUDA(cudaMemcpyAsync(tmp.data(), P.dout, nv * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    for (int p = 0; p < np; ++p) {
+        if (prices) prices[p] = tmp[static_cast<size_t>(p) * (G + 1)];
+        for (int k = 0; k < G; ++k) greeks[static_cast<size_t>(p) * G + k] = tmp[static_cast<size_t>(p) * (G + 1) + 1 + k];
+    }
+    return MC_OK;
 }
 
 int mc_simulate(const mc_model *model, const mc_sim_cfg *cfg, int32_t save_every, float *dev_out, void *stream)

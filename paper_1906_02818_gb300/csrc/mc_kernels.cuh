@@ -80,6 +80,25 @@ struct TcArgs {
     uint32_t wait_cap;     // polls per mbarrier wait before giving up
 };
 
+// Pathwise Greeks (k_greeks.cu): single-asset GBM (log-Euler, closed forms)
+// and Heston (reverse-mode adjoint with checkpoints every K steps).
+struct GreeksArgs {
+    PathRun run;
+    int model;          // MC_GBM (d = 1) or MC_HESTON
+    float s0;           // S0 (denominator of delta)
+    float s0w;          // w * S0: the monitored underlying is U = w S
+    float sigma, r, dt, sdt, T;
+    float a2, b2;       // GBM: log2(S/S0) += a2 + b2 z
+    float v0, kappa, theta, xi, rho, rhoc;
+    int K;              // Heston checkpoint stride (1..64)
+    float *ckpt;        // Heston: [ceil(M/K)][2][grid * block] checkpoint buffer
+    PayoffSet pay;      // European / Asian kinds only
+    ReduceArgs red;     // n_payoff * (1 + G) values per path
+};
+cudaError_t launch_greeks(const GreeksArgs &a, int grid, cudaStream_t s);
+int greeks_occupancy(int model, int n_payoff);
+int greeks_block();
+
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
 
