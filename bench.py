@@ -211,6 +211,11 @@ def run_gbmc(args):
     fp32 = timed("fp32") if args.prec != "fp32" else None
     path_steps = P * w["steps"] * world
     value = path_steps / (ms_step * 1e-3)
+    combined = None
+    if world > 1:  # the one exchange of the sharded path: all-reduce of the moments
+        from paper_1906_02818_gb300 import shard
+        combined = shard.allreduce_results([(float(res[i, 0]), float(res[i, 1])) for i in range(len(w["payoffs"]))],
+                                           P, device=torch.device("cuda", local))
 
     # End to end through the public C-ABI call with host buffers: model
     # upload, Cholesky, kernels, results back to the host, every step.
@@ -265,6 +270,9 @@ def run_gbmc(args):
             "prices_per_s": len(w["payoffs"]) * world / (ms_step * 1e-3),
             "results": [{"payoff": p["kind"], "price": float(res[i, 0]), "std_err": float(res[i, 1])}
                         for i, p in enumerate(w["payoffs"])],
+            "results_all_ranks": None if combined is None else [
+                {"payoff": p["kind"], "price": combined[i][0], "std_err": combined[i][1]}
+                for i, p in enumerate(w["payoffs"])],
             "e2e": {"value": P * w["steps"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
             "gpu_launches": launches,
