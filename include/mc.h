@@ -169,6 +169,100 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
               mc_result *prices, mc_result *greeks, void *stream);
 
 /*
+ * Surrogate pricing network (mc_mlp): n_in -> width x hidden (SiLU) -> 1
+ * (linear), the network that revalues the risk portfolio.  Parameters are
+ * one packed FP32 vector: for each layer l, W_l [in x out] row-major, then
+ * b_l [out].  All x / y / t buffers are DEVICE pointers, row-major [n x n_in]
+ * and [n]; host pointers are noted.  The network lives on the device that
+ * was current at creation.
+ *   mc_mlp_create: init = host packed parameters (mc_mlp_param_count floats).
+ *   mc_mlp_forward: y = net(x); precision MC_FP32 (FP32 SIMT GEMMs) or
+ *     MC_BF16 (tensor cores, BF16 weights and activations, FP32 accumulation).
+ *   mc_mlp_loss_grad: MSE (1/n) sum (y - t)^2 and its gradient (host, packed;
+ *     may be NULL) by back-propagation; synchronises `stream`.
+ *   mc_mlp_train: `epochs` passes of mini-batch Adam (lr; beta 0.9, 0.999;
+ *     eps 1e-8) over the n samples in whole batches; last_epoch_loss = mean
+ *     batch loss of the final epoch; synchronises `stream`.
+ */
+typedef struct mc_mlp mc_mlp;
+int mc_mlp_create(int32_t n_in, int32_t width, int32_t hidden, const float *init, mc_mlp **net);
+int64_t mc_mlp_param_count(const mc_mlp *net);
+int mc_mlp_get_params(const mc_mlp *net, float *host);
+int mc_mlp_set_params(mc_mlp *net, const float *host);
+int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int32_t precision, void *stream);
+int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, double *loss,
+                     float *host_grad, void *stream);
+int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, int32_t epochs, int32_t batch,
+                 float lr, double *last_epoch_loss, void *stream);
+int mc_mlp_destroy(mc_mlp *net);
+
+/*
+ * Portfolio risk (Sec. VI.B): VaR and CVaR of the one-period PnL of a
+ * portfolio of options on correlated GBM underlyings.
+ *   Scenarios: S'_u = S0_u exp((mu - sigma_u^2/2) h + sqrt(h) sigma_u (Lrho z)_u),
+ *   z = normals of scenario stream s (a stream domain of its own).
+ *   Revaluation of every option at (S', T_o - h): MC_RISK_NESTED runs
+ *   inner_paths Monte Carlo paths per (scenario, underlying) with steps of
+ *   1 / steps_per_year (up-and-out calls monitored at every step, and
+ *   worthless when S' is already at or above the barrier); base values at
+ *   (S0, T_o) use base_paths paths.  MC_RISK_SURROGATE evaluates the network
+ *   v(S/K, sigma, tau, r, K/H) = V_call / K (K/H = 0 for European), puts by
+ *   put-call parity, at the scenario states and at the base date.
+ *   PnL_s = sum_o position_o (V_o(scenario s) - V_o(base)); losses l = -PnL;
+ *   VaR_alpha = the k-th largest loss, k = ceil((1 - alpha) n_scen);
+ *   CVaR_alpha = the mean of the losses strictly above VaR_alpha (VaR_alpha
+ *   itself if none is).  Maturities and the horizon are whole steps.
+ *   Limits: n_under <= 64, 32 options per underlying, n_scen <= 2^24;
+ *   option kinds MC_CALL, MC_PUT, MC_UO_CALL.
+ *   host_pnl: host [n_scen] or NULL.  Synchronises `stream`.
+ */
+typedef struct {
+    int32_t n_under;
+    const double *s0, *sigma, *corr; /* [n_under], [n_under], [n_under^2] or NULL */
+    double r;                        /* risk-free rate (revaluation, discounting) */
+    double mu;                       /* drift of the scenario move */
+    int32_t n_opt;
+    const int32_t *under;            /* [n_opt] underlying index */
+    const int32_t *kind;             /* [n_opt] MC_CALL, MC_PUT or MC_UO_CALL */
+    const double *strike, *barrier, *maturity, *position; /* [n_opt]; barrier may be NULL without barriers */
+} mc_portfolio;
+
+typedef enum { MC_RISK_NESTED = 0, MC_RISK_SURROGATE = 1 } mc_risk_method;
+
+typedef struct {
+    double alpha;            /* e.g. 0.99 */
+    double horizon;          /* h in years, a whole number of steps */
+    int64_t n_scen;
+    int32_t steps_per_year;  /* time step of the revaluation, e.g. 252 (daily) */
+    int32_t method;          /* mc_risk_method */
+    int32_t inner_paths;     /* nested: paths per (scenario, underlying) */
+    int32_t base_paths;      /* nested: paths per underlying at the base date */
+    uint64_t seed;
+    mc_mlp *surrogate;       /* surrogate: the trained network */
+    int32_t surrogate_precision; /* MC_FP32 or MC_BF16 */
+} mc_risk_cfg;
+
+typedef struct {
+    double var, cvar;        /* of the loss -PnL */
+    double base_value;       /* sum_o position_o V_o(base) */
+    int64_t n_tail;          /* losses strictly above VaR */
+} mc_risk_result;
+
+int mc_risk(const mc_portfolio *portfolio, const mc_risk_cfg *cfg, mc_risk_result *result, double *host_pnl,
+            void *stream);
+
+/*
+ * mc_surrogate_labels -- training labels of the surrogate: for each point p
+ * of dev_points [n][5] = (S/K, sigma, tau, r, K/H), the discounted Monte Carlo
+ * price / K of a call on S with strike K and maturity tau (an up-and-out call
+ * with barrier H monitored at every step when K/H > 0; 0 when S >= H), with
+ * `paths` paths and round(tau * steps_per_year) log-Euler steps on a stream
+ * domain of its own.  dev_labels [n].  Asynchronous on `stream`.
+ */
+int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
+                        uint64_t seed, float *dev_labels, void *stream);
+
+/*
  * Plans: the same computation as mc_price split into a set-up phase (argument
  * checks, upload of the model, FP64 Cholesky factorisation on the device,
  * scaled copies of the factor, device scratch for per-block partial sums)

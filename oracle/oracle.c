@@ -573,3 +573,102 @@ void orc_mean_se(const double *f, int64_t n, double *mean, double *se)
     *mean = m;
     *se = n > 1 ? sqrt(fmax(m2 - m * m, 0.0) / (double)(n - 1)) : 0.0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Portfolio risk (Sec. VI.B) and surrogate labels.  Stream indices carry a  */
+/* domain tag in the top byte: 2 scenarios, 3 inner paths, 4 labels, 5 base  */
+/* values.                                                                   */
+/* ------------------------------------------------------------------------ */
+static uint64_t domain_tag(uint64_t domain, uint64_t idx) { return (domain << 56) | idx; }
+
+/* Scenario s: S'_u = S0_u exp((mu - sig_u^2/2) h + sqrt(h) sig_u (Lrho z)_u),
+ * z_u = normal u of stream tag(2, s). */
+int orc_risk_scenarios(int d, const double *s0, const double *sig, const double *corr, double mu, double h,
+                       int64_t nscen, uint64_t seed, double *Sp)
+{
+    double *L = (double *)malloc(sizeof(double) * (size_t)d * (size_t)d);
+    if (!L) return -3;
+    if (orc_cholesky(d, corr, L) != 0) { free(L); return -2; }
+#pragma omp parallel
+    {
+        double *z = (double *)malloc(sizeof(double) * (size_t)d);
+#pragma omp for schedule(static)
+        for (int64_t s = 0; s < nscen; ++s) {
+            orc_stream st;
+            stream_init(&st, seed, domain_tag(2, (uint64_t)s));
+            for (int u = 0; u < d; ++u) z[u] = stream_normal(&st, (uint64_t)u);
+            for (int u = 0; u < d; ++u) {
+                double w = 0.0;
+                for (int k = 0; k <= u; ++k) w += L[(size_t)u * d + k] * z[k];
+                Sp[(size_t)s * d + u] = s0[u] * exp((mu - 0.5 * sig[u] * sig[u]) * h + sqrt(h) * sig[u] * w);
+            }
+        }
+        free(z);
+    }
+    free(L);
+    return 0;
+}
+
+/* Monte Carlo value of option o of underlying u at state S (log-Euler steps
+ * of dt, `steps` of them to maturity, up-and-out monitored at every step and
+ * worthless if S already >= H), with `inner` paths of streams tag(domain,
+ * base | path).  kind: 0 call, 1 put, 4 up-and-out call (the payoff codes). */
+static double nested_value(double S, double sig, double r, double dt, int kind, double K, double H, int steps,
+                           int inner, uint64_t seed, uint64_t domain, uint64_t base)
+{
+    if (kind == ORC_UO_CALL && S >= H) return 0.0;
+    double sum = 0.0;
+    for (int p = 0; p < inner; ++p) {
+        orc_stream st;
+        stream_init(&st, seed, domain_tag(domain, base | (uint64_t)p));
+        double x = log(S), mx = -INFINITY;
+        for (int i = 0; i < steps; ++i) {
+            x += (r - 0.5 * sig * sig) * dt + sig * sqrt(dt) * stream_normal(&st, (uint64_t)i);
+            if (x > mx) mx = x;
+        }
+        double ST = exp(x), f;
+        if (kind == ORC_PUT) f = K > ST ? K - ST : 0.0;
+        else f = ST > K ? ST - K : 0.0;
+        if (kind == ORC_UO_CALL && exp(mx) >= H) f = 0.0;
+        sum += f;
+    }
+    return exp(-r * steps * dt) * sum / inner;
+}
+
+/* Revaluation of every option: base values (scen < 0: state s0, steps =
+ * rem + hsteps, streams tag(5, (u << 24) | path)) or scenario `scen` (state
+ * Sp[scen], steps = rem, streams tag(3, ((scen d + u) << 16) | path)). */
+int orc_risk_values(int d, const double *state, const double *sig, double r, double dt, int hsteps, int64_t scen,
+                    int nopt, const int *under, const int *kind, const double *K, const double *H, const int *rem,
+                    int inner, uint64_t seed, double *V)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int o = 0; o < nopt; ++o) {
+        const int u = under[o];
+        if (scen < 0)
+            V[o] = nested_value(state[u], sig[u], r, dt, kind[o], K[o], H[o], rem[o] + hsteps, inner, seed, 5,
+                                (uint64_t)u << 24);
+        else
+            V[o] = nested_value(state[u], sig[u], r, dt, kind[o], K[o], H[o], rem[o], inner, seed, 3,
+                                ((uint64_t)scen * (uint64_t)d + (uint64_t)u) << 16);
+    }
+    return 0;
+}
+
+/* Surrogate label of point p = (S/K, sig, tau, r, K/H): discounted Monte Carlo
+ * call price / K (up-and-out with H = K / (K/H) when K/H > 0), `paths` paths
+ * of streams tag(4, (p << 16) | path), round(tau * spy) steps. */
+int orc_surrogate_labels(int64_t npts, const double *pts, int paths, int spy, uint64_t seed, double *labels)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t p = 0; p < npts; ++p) {
+        const double *q = pts + 5 * p;
+        int M = (int)lround(q[2] * spy);
+        if (M < 1) M = 1;
+        const double dt = q[2] / M;
+        const double H = q[4] > 0.0 ? 1.0 / q[4] : INFINITY;
+        labels[p] = nested_value(q[0], q[1], q[3], dt, q[4] > 0.0 ? ORC_UO_CALL : ORC_CALL, 1.0, H, M, paths, seed,
+                                 4, (uint64_t)p << 16);
+    }
+    return 0;
+}

@@ -159,3 +159,124 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Mlp:
+    """The surrogate network (mc_mlp_*): parameters on the device, forward in
+    FP32 or BF16, loss/gradient and native Adam training."""
+
+    def __init__(self, n_in: int, width: int, hidden: int, init):
+        self._lib = native.lib()
+        init = np.ascontiguousarray(init, dtype=np.float32)
+        h = ctypes.c_void_p()
+        check(self._lib.mc_mlp_create(n_in, width, hidden, init.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self._h = h
+        self.n_in = n_in
+        self.count = self._lib.mc_mlp_param_count(h)
+        if self.count != init.size:
+            self.close()
+            raise ValueError(f"init has {init.size} values, the network {self.count}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.count, dtype=np.float32)
+        check(self._lib.mc_mlp_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(self._lib.mc_mlp_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, x, precision="fp32", stream=None):
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        check(self._lib.mc_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), x.shape[0], ctypes.c_void_p(y.data_ptr()),
+                                       native.PRECISION[precision], _stream_handle(stream)))
+        return y
+
+    def loss_grad(self, x, t, stream=None):
+        x, t = x.contiguous(), t.contiguous()
+        g = np.empty(self.count, dtype=np.float32)
+        loss = ctypes.c_double()
+        check(self._lib.mc_mlp_loss_grad(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         x.shape[0], ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p),
+                                         _stream_handle(stream)))
+        return loss.value, g
+
+    def train(self, x, t, epochs, batch, lr, stream=None):
+        x, t = x.contiguous(), t.contiguous()
+        loss = ctypes.c_double()
+        check(self._lib.mc_mlp_train(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                     x.shape[0], epochs, batch, ctypes.c_float(lr), ctypes.byref(loss),
+                                     _stream_handle(stream)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PORTFOLIO_KIND = {0: 0, 1: 1, 4: 4}  # call, put, up-and-out call (mc_payoff_kind codes)
+
+
+def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None):
+    """Monte Carlo training labels V_call / K at CUDA float32 points [n, 5]."""
+    import torch
+    pts = points.contiguous()
+    out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    check(native.lib().mc_surrogate_labels(pts.shape[0], ctypes.c_void_p(pts.data_ptr()), paths, steps_per_year, seed,
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
+def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_paths=1 << 12, base_paths=1 << 16,
+         seed=42, surrogate=None, surrogate_precision="fp32", want_pnl=False, stream=None):
+    """VaR / CVaR of the portfolio (see mc_risk); returns a dict."""
+    L = native.lib()
+    keep = []
+
+    def dp(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(native.c_double_p)
+
+    def ip(x):
+        a = np.ascontiguousarray(x, dtype=np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+    pf = native.McPortfolio()
+    pf.n_under = len(portfolio["s0"])
+    pf.s0, pf.sigma = dp(portfolio["s0"]), dp(portfolio["sigma"])
+    pf.corr = dp(portfolio["corr"]) if portfolio.get("corr") is not None else None
+    pf.r, pf.mu = float(portfolio["r"]), float(portfolio["mu"])
+    pf.n_opt = len(portfolio["strike"])
+    pf.under, pf.kind = ip(portfolio["under"]), ip([PORTFOLIO_KIND[int(k)] for k in portfolio["kind"]])
+    pf.strike, pf.barrier = dp(portfolio["strike"]), dp(portfolio["barrier"])
+    pf.maturity, pf.position = dp(portfolio["maturity"]), dp(portfolio["position"])
+    cf = native.McRiskCfg()
+    cf.alpha, cf.horizon, cf.n_scen = alpha, float(portfolio["horizon"]), int(n_scen)
+    cf.steps_per_year = int(portfolio.get("steps_per_year", 252))
+    cf.method = native.RISK_METHOD[method]
+    cf.inner_paths, cf.base_paths, cf.seed = int(inner_paths), int(base_paths), int(seed)
+    cf.surrogate = surrogate.handle if surrogate is not None else None
+    cf.surrogate_precision = native.PRECISION[surrogate_precision]
+    res = native.McRiskResult()
+    pnl = np.empty(int(n_scen)) if want_pnl else None
+    check(L.mc_risk(ctypes.byref(pf), ctypes.byref(cf), ctypes.byref(res),
+                    pnl.ctypes.data_as(ctypes.c_void_p) if want_pnl else None, _stream_handle(stream)))
+    out = dict(var=res.var, cvar=res.cvar, base_value=res.base_value, n_tail=res.n_tail)
+    if want_pnl:
+        out["pnl"] = pnl
+    return out

@@ -1,0 +1,199 @@
+// C ABI of the surrogate network (mc_mlp_* in include/mc.h): parameter
+// storage, forward evaluation, loss/gradient, and the native training loop
+// (mini-batch Adam) that drives the kernels of k_mlp.cu.
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "mc_kernels.cuh"
+#include "mlp.cuh"
+
+using namespace gbmc;
+
+struct mc_mlp {
+    MlpLayout L;
+    int device = -1;
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float *work = nullptr;
+    size_t work_floats = 0;
+    double *partial = nullptr;
+    int step = 0;
+    ~mc_mlp()
+    {
+        for (float *p : {params, grad, m, v, work})
+            if (p) cudaFree(p);
+        if (partial) cudaFree(partial);
+    }
+};
+
+namespace {
+
+constexpr int kPartials = 512;
+
+#define MLP_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            char b_[256];                                                                     \
+            std::snprintf(b_, sizeof b_, "%s: %s", #call, cudaGetErrorString(e_));           \
+            return set_last_error(e_ == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA, b_); \
+        }                                                                                     \
+    } while (0)
+
+int ensure_work(mc_mlp *N, size_t floats)
+{
+    if (N->work_floats >= floats) return MC_OK;
+    if (N->work) cudaFree(N->work);
+    N->work = nullptr;
+    N->work_floats = 0;
+    MLP_CUDA(cudaMalloc(&N->work, floats * sizeof(float)));
+    N->work_floats = floats;
+    return MC_OK;
+}
+
+int check_net(const mc_mlp *N)
+{
+    if (!N) return set_last_error(MC_EINVAL, "network is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != N->device)
+        return set_last_error(MC_EINVAL, "network belongs to another device");
+    return MC_OK;
+}
+
+}  // namespace
+
+namespace gbmc {
+const MlpLayout &mlp_layout_of(const mc_mlp *net) { return net->L; }
+
+// Forward evaluation used by mc_risk (x, y device, n rows) on `s`.
+int mlp_forward_any(mc_mlp *net, const float *x, int64_t n, float *y, int precision, cudaStream_t s)
+{
+    return mc_mlp_forward(net, x, n, y, precision, s);
+}
+}  // namespace gbmc
+
+extern "C" {
+
+int mc_mlp_create(int32_t n_in, int32_t width, int32_t hidden, const float *init, mc_mlp **out)
+{
+    if (!out) return set_last_error(MC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_in < 1 || n_in > 64 || width < 1 || width > 1024 || hidden < 1 || hidden > 16)
+        return set_last_error(MC_EINVAL, "n_in in [1,64], width in [1,1024], hidden in [1,16]");
+    if (!init) return set_last_error(MC_EINVAL, "init is NULL");
+    mc_mlp *N = new (std::nothrow) mc_mlp();
+    if (!N) return set_last_error(MC_ENOMEM, "host allocation failed");
+    N->L = MlpLayout(n_in, width, hidden);
+    const size_t bytes = static_cast<size_t>(N->L.count) * sizeof(float);
+    int rc = MC_OK;
+    auto fail_free = [&](int code) { delete N; return code; };
+    if (cudaGetDevice(&N->device) != cudaSuccess) return fail_free(set_last_error(MC_ECUDA, "no device"));
+    for (float **p : {&N->params, &N->grad, &N->m, &N->v})
+        if (cudaMalloc(p, bytes) != cudaSuccess) return fail_free(set_last_error(MC_ENOMEM, "device allocation failed"));
+    if (cudaMalloc(&N->partial, kPartials * sizeof(double)) != cudaSuccess)
+        return fail_free(set_last_error(MC_ENOMEM, "device allocation failed"));
+    if (cudaMemcpy(N->params, init, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(N->m, 0, bytes) != cudaSuccess || cudaMemset(N->v, 0, bytes) != cudaSuccess)
+        return fail_free(set_last_error(MC_ECUDA, "initialisation copy failed"));
+    (void)rc;
+    *out = N;
+    return MC_OK;
+}
+
+int64_t mc_mlp_param_count(const mc_mlp *net) { return net ? net->L.count : -1; }
+
+int mc_mlp_get_params(const mc_mlp *net, float *host)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!host) return set_last_error(MC_EINVAL, "host is NULL");
+    MLP_CUDA(cudaMemcpy(host, net->params, net->L.count * sizeof(float), cudaMemcpyDeviceToHost));
+    return MC_OK;
+}
+
+int mc_mlp_set_params(mc_mlp *net, const float *host)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!host) return set_last_error(MC_EINVAL, "host is NULL");
+    MLP_CUDA(cudaMemcpy(net->params, host, net->L.count * sizeof(float), cudaMemcpyHostToDevice));
+    net->step = 0;
+    MLP_CUDA(cudaMemset(net->m, 0, net->L.count * sizeof(float)));
+    MLP_CUDA(cudaMemset(net->v, 0, net->L.count * sizeof(float)));
+    return MC_OK;
+}
+
+int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int32_t precision, void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!dev_x || !dev_y || n < 1) return set_last_error(MC_EINVAL, "x, y must be set and n >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision != MC_FP32) return set_last_error(MC_EUNSUPPORTED, "this build evaluates the network in FP32 here");
+    int maxw = 0;
+    for (int v : net->L.sizes) maxw = v > maxw ? v : maxw;
+    if ((rc = ensure_work(net, 2 * static_cast<size_t>(n) * maxw))) return rc;
+    MLP_CUDA(mlp_forward_fp32(net->L, net->params, dev_x, n, net->work, dev_y, s));
+    return MC_OK;
+}
+
+int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, double *loss, float *host_grad,
+                     void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!dev_x || !dev_t || n < 1) return set_last_error(MC_EINVAL, "x, t must be set and n >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_work(net, mlp_train_floats(net->L, n)))) return rc;
+    MLP_CUDA(mlp_loss_grad(net->L, net->params, dev_x, dev_t, n, net->work, net->grad, net->partial, kPartials, s));
+    std::vector<double> part(kPartials);
+    MLP_CUDA(cudaMemcpyAsync(part.data(), net->partial, kPartials * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (host_grad)
+        MLP_CUDA(cudaMemcpyAsync(host_grad, net->grad, net->L.count * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MLP_CUDA(cudaStreamSynchronize(s));
+    double tot = 0.0;
+    for (double p : part) tot += p;
+    if (loss) *loss = tot / static_cast<double>(n);
+    return MC_OK;
+}
+
+int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, int32_t epochs, int32_t batch,
+                 float lr, double *last_epoch_loss, void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!dev_x || !dev_t || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
+        return set_last_error(MC_EINVAL, "x, t set; n, epochs, batch >= 1; lr > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t B = batch < n ? batch : n;
+    if ((rc = ensure_work(net, mlp_train_floats(net->L, B)))) return rc;
+    const int n_in = net->L.sizes[0];
+    std::vector<double> part(kPartials);
+    double epoch_loss = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        epoch_loss = 0.0;
+        const bool last = ep == epochs - 1;
+        for (int64_t b0 = 0; b0 + B <= n; b0 += B) {  // whole batches; the samples are i.i.d.
+            MLP_CUDA(mlp_loss_grad(net->L, net->params, dev_x + b0 * n_in, dev_t + b0, B, net->work, net->grad,
+                                   net->partial, kPartials, s));
+            MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
+            if (last) {
+                MLP_CUDA(cudaMemcpyAsync(part.data(), net->partial, kPartials * sizeof(double), cudaMemcpyDeviceToHost, s));
+                MLP_CUDA(cudaStreamSynchronize(s));
+                for (double p : part) epoch_loss += p;
+            }
+        }
+    }
+    MLP_CUDA(cudaStreamSynchronize(s));
+    if (last_epoch_loss) *last_epoch_loss = epoch_loss / static_cast<double>((n / B) * B);
+    return MC_OK;
+}
+
+int mc_mlp_destroy(mc_mlp *net)
+{
+    delete net;
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// Surrogate network: packed FP32 parameter layout and the device routines of
+// k_mlp.cu / k_mlp_tc.cu used by the mc_mlp_* entry points and mc_risk.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace gbmc {
+
+// Layer sizes n_in, width x hidden, 1; layer l's W_l [in x out] (row-major)
+// at w_off[l], b_l [out] at b_off[l] in one packed FP32 vector.
+struct MlpLayout {
+    std::vector<int> sizes;
+    std::vector<int64_t> w_off, b_off;
+    int64_t count = 0;
+    MlpLayout() = default;
+    MlpLayout(int n_in, int width, int hidden);
+};
+
+// y[n] = net(x[n x n_in]) in FP32; work holds 2 n max_width floats.
+cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const float *x, int64_t n, float *work,
+                             float *y, cudaStream_t s);
+// Loss partials (npartial doubles, sum / n = MSE) and the packed gradient of
+// the MSE of one batch; acts holds mlp_train_floats(L, n) floats.
+cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
+                          float *acts, float *grad, double *partial, int npartial, cudaStream_t s);
+size_t mlp_train_floats(const MlpLayout &L, int64_t n);
+cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
+
+}  // namespace gbmc

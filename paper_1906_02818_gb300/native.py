@@ -48,6 +48,28 @@ class McResult(ctypes.Structure):
     _fields_ = [("price", ctypes.c_double), ("se", ctypes.c_double)]
 
 
+class McPortfolio(ctypes.Structure):
+    _fields_ = [("n_under", ctypes.c_int32), ("s0", c_double_p), ("sigma", c_double_p), ("corr", c_double_p),
+                ("r", ctypes.c_double), ("mu", ctypes.c_double), ("n_opt", ctypes.c_int32),
+                ("under", ctypes.POINTER(ctypes.c_int32)), ("kind", ctypes.POINTER(ctypes.c_int32)),
+                ("strike", c_double_p), ("barrier", c_double_p), ("maturity", c_double_p),
+                ("position", c_double_p)]
+
+
+class McRiskCfg(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("horizon", ctypes.c_double), ("n_scen", ctypes.c_int64),
+                ("steps_per_year", ctypes.c_int32), ("method", ctypes.c_int32), ("inner_paths", ctypes.c_int32),
+                ("base_paths", ctypes.c_int32), ("seed", ctypes.c_uint64), ("surrogate", ctypes.c_void_p),
+                ("surrogate_precision", ctypes.c_int32)]
+
+
+class McRiskResult(ctypes.Structure):
+    _fields_ = [("var", ctypes.c_double), ("cvar", ctypes.c_double), ("base_value", ctypes.c_double),
+                ("n_tail", ctypes.c_int64)]
+
+
+RISK_METHOD = {"nested": 0, "surrogate": 1}
+
 # name, restype, argtypes  (the complete exported surface of mc.h)
 SIGNATURES = [
     ("mc_version", ctypes.c_int, []),
@@ -66,6 +88,23 @@ SIGNATURES = [
     ("mc_plan_execute", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_plan_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("mc_plan_launches", ctypes.c_int, [ctypes.c_void_p]),
+    ("mc_mlp_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    ("mc_mlp_param_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("mc_mlp_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_mlp_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_mlp_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_void_p]),
+    ("mc_mlp_loss_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("mc_mlp_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("mc_risk", ctypes.c_int, [ctypes.POINTER(McPortfolio), ctypes.POINTER(McRiskCfg),
+                               ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_surrogate_labels", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_price_gbm1d_noalloc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg),
                                               ctypes.POINTER(McPayoff), ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p]),

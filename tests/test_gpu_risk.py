@@ -1,0 +1,118 @@
+"""GPU parity of portfolio risk (mc_risk) and of the surrogate's labels with
+the FP64 oracle on identical streams; exactness of the VaR / CVaR selection;
+the trained surrogate judged by nested Monte Carlo, and what it gains."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import risk as orisk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def test_labels_match_oracle(gb, orc):
+    import torch
+    pts = workloads.surrogate_points(96, seed=11)
+    pts[:48, 4] = 0.0  # European half
+    got = gb.surrogate_labels(torch.from_numpy(pts).cuda(), 1024).cpu().numpy()
+    want = orisk.labels(pts.astype(np.float64), 1024)
+    euro = pts[:, 4] == 0
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-3)
+    print("label rel err: european max %.2e, barrier max %.2e" % (rel[euro].max(), rel[~euro].max()))
+    assert np.all(rel[euro] <= 2e-5)
+    # barrier labels: a path whose running maximum lies within FP32 rounding of
+    # H may knock out on one side only; one flip moves a label by <= 1/1024 * (S_max - K)
+    assert np.all(np.abs(got - want)[~euro] <= 2e-5 * np.abs(want[~euro]) + 2.0 / 1024)
+
+
+def _small_portfolio():
+    return workloads.risk_portfolio(n_under=4, per_under=8, seed=7)
+
+
+def _oracle_pnl(pf, nscen, inner, base_paths):
+    S = orisk.scenarios(pf["s0"], pf["sigma"], pf["corr"], pf["mu"], pf["horizon"], nscen)
+    steps = np.rint(pf["maturity"] * 252).astype(np.int32)
+    rem = steps - 1
+    base = orisk.option_values(pf["s0"], pf["sigma"], pf["r"], 1 / 252, 1, -1, pf["under"], pf["kind"],
+                               pf["strike"], pf["barrier"], rem, base_paths)
+    pnl = np.empty(nscen)
+    vals = []
+    for s in range(nscen):
+        V = orisk.option_values(S[s], pf["sigma"], pf["r"], 1 / 252, 1, s, pf["under"], pf["kind"], pf["strike"],
+                                pf["barrier"], rem, inner)
+        vals.append(V)
+        pnl[s] = pf["position"] @ (V - base)
+    return pnl, np.array(vals), base
+
+
+def test_nested_pnl_matches_oracle(gb, orc):
+    pf = _small_portfolio()
+    ns, inner, bp = 24, 1024, 4096
+    got = gb.risk(pf, alpha=0.9, n_scen=ns, method="nested", inner_paths=inner, base_paths=bp, want_pnl=True)
+    pnl, vals, base = _oracle_pnl(pf, ns, inner, bp)
+    scale = np.abs(pf["position"]) @ np.abs(vals).max(axis=0)  # sum of |V| over the options
+    err = np.abs(got["pnl"] - pnl)
+    print("nested PnL max abs err %.3e, scale %.3e" % (err.max(), scale))
+    # FP32 inner paths vs FP64: <= 2e-5 of the book's gross value, plus barrier flips
+    # (a knock decision within rounding of H moves one option by <= (H - K) / inner)
+    flip = np.max(np.where(pf["kind"] == 4, pf["barrier"] - pf["strike"], 0)) / inner
+    assert np.all(err <= 2e-5 * scale + 4 * flip)
+    assert abs(got["base_value"] - pf["position"] @ base) <= 2e-5 * (np.abs(pf["position"]) @ np.abs(base)) + 4 * flip
+
+
+def test_var_cvar_selection_is_exact(gb):
+    pf = _small_portfolio()
+    for alpha, ns in [(0.99, 1000), (0.95, 4096), (0.5, 3)]:
+        got = gb.risk(pf, alpha=alpha, n_scen=ns, method="nested", inner_paths=256, base_paths=1024, want_pnl=True)
+        var, cvar, nt = orisk.var_cvar(got["pnl"], alpha)
+        assert got["var"] == var and got["n_tail"] == nt
+        assert abs(got["cvar"] - cvar) <= 1e-12 * abs(cvar)
+
+
+@pytest.fixture(scope="module")
+def trained(gb):
+    """A surrogate trained on GPU Monte Carlo labels (2^17 points, 2^11 paths
+    each: a reduced version of the 2^20-label training)."""
+    import torch
+    pts = torch.from_numpy(workloads.surrogate_points(1 << 17)).cuda()
+    lab = gb.surrogate_labels(pts, 2048)
+    net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+    loss = net.train(pts, lab, epochs=40, batch=2048, lr=1e-3)
+    print("surrogate final epoch loss %.3e" % loss)
+    return net, loss
+
+
+def test_surrogate_judged_by_nested(gb, trained):
+    """The trained surrogate's VaR / CVaR against nested Monte Carlo (the
+    judge) on the same 2048 scenarios of the full 1024-option book, and the
+    time each revaluation takes."""
+    import torch
+    net, loss = trained
+    pf = workloads.risk_portfolio()
+    ns = 2048
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nested = gb.risk(pf, n_scen=ns, method="nested", inner_paths=1 << 12, base_paths=1 << 16, want_pnl=True)
+    t1 = time.perf_counter()
+    sur = gb.risk(pf, n_scen=ns, method="surrogate", surrogate=net, want_pnl=True)
+    t2 = time.perf_counter()
+    rv = abs(sur["var"] - nested["var"]) / abs(nested["var"])
+    rc = abs(sur["cvar"] - nested["cvar"]) / abs(nested["cvar"])
+    corr = np.corrcoef(sur["pnl"], nested["pnl"])[0, 1]
+    print(f"VaR nested {nested['var']:.3f} surrogate {sur['var']:.3f} (rel {rv:.3%}); "
+          f"CVaR nested {nested['cvar']:.3f} surrogate {sur['cvar']:.3f} (rel {rc:.3%}); "
+          f"PnL corr {corr:.4f}; time nested {t1 - t0:.3f}s surrogate {t2 - t1:.3f}s")
+    assert corr > 0.95
+    assert rv < 0.10 and rc < 0.10
+    assert t2 - t1 < t1 - t0  # the network revalues faster than the inner simulation

@@ -1,0 +1,93 @@
+"""Pins of the risk oracle (oracle/risk.py and the risk functions of
+oracle.c): VaR / CVaR against their definitions and the normal closed forms,
+scenario moments, nested values and labels against Black-Scholes."""
+import math
+
+import numpy as np
+import pytest
+
+import closed_forms as cf
+import workloads
+from oracle import risk
+
+
+def test_var_cvar_definition_brute_force():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 10, 101, 1000):
+        pnl = rng.standard_normal(n)
+        for alpha in (0.5, 0.9, 0.99):
+            var, cvar, nt = risk.var_cvar(pnl, alpha)
+            losses = sorted(-pnl, reverse=True)
+            k = max(1, math.ceil((1 - alpha) * n - 1e-9))
+            assert var == losses[k - 1]
+            above = [l for l in losses if l > var]
+            assert nt == len(above)
+            assert cvar == (np.mean(above) if above else var)
+            assert cvar >= var
+
+
+def test_var_cvar_normal_closed_form():
+    rng = np.random.default_rng(1)
+    n, alpha = 1 << 20, 0.99
+    pnl = 2.0 + 3.0 * rng.standard_normal(n)
+    var, cvar, _ = risk.var_cvar(pnl, alpha)
+    from scipy.stats import norm
+    z = norm.ppf(alpha)
+    assert abs(var - (-2.0 + 3.0 * z)) < 0.03
+    assert abs(cvar - (-2.0 + 3.0 * norm.pdf(z) / (1 - alpha))) < 0.03
+
+
+def test_scenario_moments(orc):
+    s0, sg, corr = workloads.basket_market(6, 2, seed=5)
+    h, mu, n = 1 / 252, 0.05, 1 << 17
+    S = risk.scenarios(s0, sg, corr, mu, h, n)
+    X = np.log(S / s0)
+    Sigma = np.diag(sg) @ corr @ np.diag(sg) * h
+    se = np.sqrt((np.outer(np.diag(Sigma), np.diag(Sigma)) + Sigma ** 2) / n)
+    assert np.all(np.abs(np.cov(X.T) - Sigma) < 5 * se)
+    assert np.all(np.abs(X.mean(axis=0) - (mu - 0.5 * sg ** 2) * h) < 5 * np.sqrt(np.diag(Sigma) / n))
+
+
+def test_nested_value_is_black_scholes(orc):
+    # European call and put from the same state within 3 SE of Black-Scholes
+    V = risk.option_values([100.0], [0.25], 0.05, 1 / 252, 1, 0, [0, 0], [0, 1], [105.0, 95.0], [np.inf, np.inf],
+                           [251, 251], 1 << 16)
+    tau = 251 / 252
+    for v, want in zip(V, [cf.bs_call(100, 105, 0.05, 0.25, tau), cf.bs_put(100, 95, 0.05, 0.25, tau)]):
+        assert abs(v - want) < 3 * 0.06  # SE of the 2^16-path estimate is below 0.06 here
+    # up-and-out <= vanilla, and 0 at or above the barrier
+    U = risk.option_values([100.0], [0.25], 0.05, 1 / 252, 1, 0, [0, 0], [4, 4], [100.0, 100.0], [130.0, 99.0],
+                           [60, 60], 4096)
+    van = risk.option_values([100.0], [0.25], 0.05, 1 / 252, 1, 0, [0], [0], [100.0], [np.inf], [60], 4096)
+    assert 0 < U[0] < van[0] and U[1] == 0.0
+
+
+def test_labels_european_are_black_scholes(orc):
+    pts = np.array([[1.0, 0.2, 1.0, 0.05, 0.0], [1.2, 0.3, 0.5, 0.02, 0.0], [0.8, 0.15, 2.0, 0.07, 0.0]])
+    lab = risk.labels(pts, 1 << 15)
+    for p, l in zip(pts, lab):
+        want = cf.bs_call(p[0], 1.0, p[3], p[1], p[2])
+        assert abs(l - want) < 4 * p[0] * p[1] * math.sqrt(p[2]) / math.sqrt(1 << 15) + 1e-4
+    b = risk.labels(np.array([[1.0, 0.2, 1.0, 0.05, 0.8], [1.3, 0.2, 1.0, 0.05, 0.8]]), 4096)
+    assert 0 < b[0] < lab[0] and b[1] == 0.0
+
+
+def test_european_portfolio_nested_matches_exact_revaluation(orc):
+    """European-only portfolio: nested Monte Carlo PnL (oracle, 2^12 inner
+    paths) against the exact Black-Scholes revaluation on the same scenarios:
+    agreement within the inner-noise standard error."""
+    pf = workloads.risk_portfolio(n_under=4, per_under=8, barriers=False)
+    S = risk.scenarios(pf["s0"], pf["sigma"], pf["corr"], pf["mu"], pf["horizon"], 8)
+    steps = np.rint(pf["maturity"] * 252).astype(int)
+    rem = steps - 1
+    kind = pf["kind"]
+    def exact(state, taus):
+        return np.array([(cf.bs_call if k == 0 else cf.bs_put)(state[u], K, pf["r"], pf["sigma"][u], t)
+                         for u, k, K, t in zip(pf["under"], kind, pf["strike"], taus)])
+    base_x = exact(pf["s0"], steps / 252)
+    for s in range(8):
+        V = risk.option_values(S[s], pf["sigma"], pf["r"], 1 / 252, 1, s, pf["under"], kind, pf["strike"],
+                               pf["barrier"], rem, 1 << 12)
+        Vx = exact(S[s], rem / 252)
+        # inner SE of each value <= 0.6 here; positions +-1, 32 options
+        assert abs(pf["position"] @ (V - Vx)) < 3 * 0.6 * math.sqrt(32)

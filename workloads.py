@@ -78,3 +78,65 @@ def heston(paths: int = 1 << 22, steps: int = 256):
     pays = [dict(kind="call", strike=K) for K in HESTON_STRIKES]
     pays += [dict(kind="asian_call", strike=K) for K in HESTON_STRIKES]
     return dict(model=dict(HESTON_PARAMS), T=1.0, steps=steps, paths=paths, seed=SEED, payoffs=pays)
+
+
+def mlp_init(n_in: int = 5, width: int = 256, hidden: int = 4, seed: int = SEED) -> np.ndarray:
+    """Packed initial parameters of the surrogate (per layer W [in x out]
+    row-major then b [out]): W ~ N(0, 1/in) (variance-preserving for SiLU
+    nets), b = 0; float32."""
+    rng = np.random.default_rng(seed)
+    sizes = [n_in] + [width] * hidden + [1]
+    parts = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        parts.append((rng.standard_normal((a, b)) / np.sqrt(a)).ravel())
+        parts.append(np.zeros(b))
+    return np.concatenate(parts).astype(np.float32)
+
+
+RISK_K_OVER_S0 = (0.8, 0.9, 1.0, 1.1, 1.2)
+RISK_T_DAYS = (63, 126, 252, 504)
+
+
+def risk_portfolio(n_under: int = 32, per_under: int = 32, seed: int = SEED, barriers: bool = True):
+    """1024 options on 32 correlated GBM underlyings (basket_market(32, 4)):
+    per underlying, half European calls / puts (K/S0 on {0.8 .. 1.2}, T on
+    {63, 126, 252, 504} days), half up-and-out calls (K/S0 on {0.8, 0.9, 1.0},
+    H/S0 ~ U[1.2, 1.5], daily monitoring); positions +-1.  With
+    barriers=False every option is European."""
+    s0, sigma, corr = basket_market(n_under, 4, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    under, kind, K, H, T, pos = [], [], [], [], [], []
+    for u in range(n_under):
+        for j in range(per_under):
+            barrier = barriers and j >= per_under // 2
+            if barrier:
+                k = 4  # up-and-out call
+                kk = rng.choice(RISK_K_OVER_S0[:3])
+                hh = rng.uniform(1.2, 1.5)
+            else:
+                k = int(rng.integers(0, 2))  # 0 call, 1 put
+                kk = rng.choice(RISK_K_OVER_S0)
+                hh = np.inf
+            under.append(u)
+            kind.append(k)
+            K.append(kk * s0[u])
+            H.append(hh * s0[u])
+            T.append(rng.choice(RISK_T_DAYS) / 252.0)
+            pos.append(float(rng.choice([-1.0, 1.0])))
+    return dict(s0=s0, sigma=sigma, corr=corr, r=0.05, mu=0.05, under=np.array(under, dtype=np.int32),
+                kind=np.array(kind, dtype=np.int32), strike=np.array(K), barrier=np.array(H),
+                maturity=np.array(T), position=np.array(pos), horizon=1.0 / 252, steps_per_year=252)
+
+
+def surrogate_points(n: int, seed: int = SEED + 2) -> np.ndarray:
+    """Training points of the surrogate over its parameter box: S/K ~ U[0.5, 1.6],
+    sigma ~ U[0.1, 0.4], tau = days / 252 with days ~ U{1..504}, r ~ U[0, 0.08],
+    K/H = 0 (European) for half of them, ~ U[0.5, 0.9] for the rest; float32 [n, 5]."""
+    rng = np.random.default_rng(seed)
+    x = np.empty((n, 5))
+    x[:, 0] = rng.uniform(0.5, 1.6, n)
+    x[:, 1] = rng.uniform(0.1, 0.4, n)
+    x[:, 2] = rng.integers(1, 505, n) / 252.0
+    x[:, 3] = rng.uniform(0.0, 0.08, n)
+    x[:, 4] = np.where(rng.uniform(size=n) < 0.5, 0.0, rng.uniform(0.5, 0.9, n))
+    return x.astype(np.float32)
