@@ -206,8 +206,9 @@ int mc_mlp_destroy(mc_mlp *net);
  *   1 / steps_per_year (up-and-out calls monitored at every step, and
  *   worthless when S' is already at or above the barrier); base values at
  *   (S0, T_o) use base_paths paths.  MC_RISK_SURROGATE evaluates the network
- *   v(S/K, sigma, tau, r, K/H) = V_call / K (K/H = 0 for European), puts by
- *   put-call parity, at the scenario states and at the base date.
+ *   v = V_call / K at the inputs of (S/K, sigma, tau, r, K/H) (K/H = 0 for
+ *   European; inputs as written by mc_surrogate_labels), puts by put-call
+ *   parity, at the scenario states and at the base date.
  *   PnL_s = sum_o position_o (V_o(scenario s) - V_o(base)); losses l = -PnL;
  *   VaR_alpha = the k-th largest loss, k = ceil((1 - alpha) n_scen);
  *   CVaR_alpha = the mean of the losses strictly above VaR_alpha (VaR_alpha
@@ -252,15 +253,20 @@ int mc_risk(const mc_portfolio *portfolio, const mc_risk_cfg *cfg, mc_risk_resul
             void *stream);
 
 /*
- * mc_surrogate_labels -- training labels of the surrogate: for each point p
- * of dev_points [n][5] = (S/K, sigma, tau, r, K/H), the discounted Monte Carlo
- * price / K of a call on S with strike K and maturity tau (an up-and-out call
- * with barrier H monitored at every step when K/H > 0; 0 when S >= H), with
- * `paths` paths and round(tau * steps_per_year) log-Euler steps on a stream
- * domain of its own.  dev_labels [n].  Asynchronous on `stream`.
+ * mc_surrogate_labels -- training set of the surrogate: for each point p of
+ * dev_points [n][5] = (S/K, sigma, tau, r, K/H), the label dev_labels[p] =
+ * discounted Monte Carlo price / K of a call on S with strike K and maturity
+ * tau (an up-and-out call with barrier H monitored at every step when
+ * K/H > 0; 0 when S >= H), with `paths` paths and round(tau * steps_per_year)
+ * log-Euler steps on a stream domain of its own; and, if dev_inputs is not
+ * NULL, the network inputs dev_inputs [n][5] =
+ *   ((S/K - 1.05)/0.55, (sigma - 0.25)/0.15, tau - 1, (r - 0.04)/0.04,
+ *    (K/H - 0.45)/0.45),
+ * the same map mc_risk applies before evaluating the network.  Asynchronous
+ * on `stream`.
  */
 int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
-                        uint64_t seed, float *dev_labels, void *stream);
+                        uint64_t seed, float *dev_labels, float *dev_inputs, void *stream);
 
 /*
  * Plans: the same computation as mc_price split into a set-up phase (argument

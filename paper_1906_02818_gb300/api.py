@@ -230,14 +230,19 @@ class Mlp:
 PORTFOLIO_KIND = {0: 0, 1: 1, 4: 4}  # call, put, up-and-out call (mc_payoff_kind codes)
 
 
-def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None):
-    """Monte Carlo training labels V_call / K at CUDA float32 points [n, 5]."""
+def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None, with_inputs=False):
+    """Monte Carlo training labels V_call / K at CUDA float32 points [n, 5]
+    (S/K, sigma, tau, r, K/H); with_inputs=True also returns the network
+    inputs of the points."""
     import torch
     pts = points.contiguous()
     out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    inp = torch.empty_like(pts) if with_inputs else None
     check(native.lib().mc_surrogate_labels(pts.shape[0], ctypes.c_void_p(pts.data_ptr()), paths, steps_per_year, seed,
-                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
-    return out
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(inp.data_ptr()) if with_inputs else None,
+                                           _stream_handle(stream)))
+    return (out, inp) if with_inputs else out
 
 
 def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_paths=1 << 12, base_paths=1 << 16,

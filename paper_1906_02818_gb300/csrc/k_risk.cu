@@ -26,15 +26,27 @@ namespace {
 
 __device__ __forceinline__ uint64_t tag(uint64_t domain, uint64_t idx) { return (domain << 56) | idx; }
 
+// Network inputs from the raw point (S/K, sigma, tau, r, K/H): each mapped
+// from its parameter-box range to about [-1, 1] (the constants of mc.h).
+__device__ __forceinline__ void surrogate_inputs(float sk, float sig, float tau, float r, float kh, float *f)
+{
+    f[0] = (sk - 1.05f) * (1.0f / 0.55f);
+    f[1] = (sig - 0.25f) * (1.0f / 0.15f);
+    f[2] = tau - 1.0f;
+    f[3] = (r - 0.04f) * (1.0f / 0.04f);
+    f[4] = (kh - 0.45f) * (1.0f / 0.45f);
+}
+
 // ------------------------------ labels -----------------------------------
 __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *__restrict__ pts, int paths,
                                                     float steps_per_year, uint32_t k0, uint32_t k1,
-                                                    float *__restrict__ labels)
+                                                    float *__restrict__ labels, float *__restrict__ inputs)
 {
     __shared__ double s_red[8];
     for (int64_t p = blockIdx.x; p < npts; p += gridDim.x) {
         const float sk = pts[p * 5 + 0], sig = pts[p * 5 + 1], tau = pts[p * 5 + 2], r = pts[p * 5 + 3],
                     kh = pts[p * 5 + 4];
+        if (inputs && threadIdx.x == 0) surrogate_inputs(sk, sig, tau, r, kh, inputs + p * 5);
         const int M = max(1, __float2int_rn(tau * steps_per_year));
         const float dt = tau / M;
         const float H = kh > 0.0f ? 1.0f / kh : INFINITY;  // barrier in units of K
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(256) nested_kernel(RiskArgs a, const float *__
 }
 
 // ------------------------------ surrogate --------------------------------
-// x[(s * nopt + o) * 5 ..]: S/K, sigma, tau_remaining, r, K/H (0 = no barrier);
+// x[(s * nopt + o) * 5 ..]: network inputs of S/K, sigma, tau_remaining, r, K/H (0 = no barrier);
 // Sp == nullptr: the base date (S0, full maturity).
 __global__ void features_kernel(RiskArgs a, int64_t nscen, const float *__restrict__ Sp, float *__restrict__ x)
 {
@@ -185,12 +197,8 @@ __global__ void features_kernel(RiskArgs a, int64_t nscen, const float *__restri
         const float S = Sp ? Sp[s * a.d + u] : a.s0[u];
         const float K = a.strike[o];
         const int steps = Sp ? a.rem[o] : a.rem[o] + a.horizon_steps;
-        float *f = x + i * 5;
-        f[0] = S / K;
-        f[1] = a.sigma[u];
-        f[2] = steps * a.dt;
-        f[3] = a.r;
-        f[4] = a.kind[o] == MC_UO_CALL ? K / a.barrier[o] : 0.0f;
+        surrogate_inputs(S / K, a.sigma[u], steps * a.dt, a.r, a.kind[o] == MC_UO_CALL ? K / a.barrier[o] : 0.0f,
+                         x + i * 5);
     }
 }
 
@@ -301,10 +309,10 @@ __global__ void __launch_bounds__(1024) tail_kernel(int64_t n, const double *pnl
 }  // namespace
 
 cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float spy, uint32_t k0, uint32_t k1,
-                          float *labels, cudaStream_t s)
+                          float *labels, float *inputs, cudaStream_t s)
 {
     const int64_t g = npts < 1216 * 4 ? npts : 1216 * 4;
-    label_kernel<<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, k0, k1, labels);
+    label_kernel<<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, k0, k1, labels, inputs);
     return cudaGetLastError();
 }
 

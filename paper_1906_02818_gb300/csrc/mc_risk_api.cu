@@ -56,14 +56,14 @@ struct DevBufs {
 extern "C" {
 
 int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
-                        uint64_t seed, float *dev_labels, void *stream)
+                        uint64_t seed, float *dev_labels, float *dev_inputs, void *stream)
 {
     if (n_points < 1 || !dev_points || !dev_labels) return fail(MC_EINVAL, "points and labels must be set, n >= 1");
     if (n_points > (int64_t(1) << 36)) return fail(MC_EINVAL, "too many points");
     if (paths < 1 || paths > 65536) return fail(MC_EINVAL, "paths must lie in [1, 65536]");
     if (steps_per_year < 1) return fail(MC_EINVAL, "steps_per_year must be >= 1");
     RK_CUDA(launch_labels(n_points, dev_points, paths, static_cast<float>(steps_per_year),
-                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), dev_labels,
+                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), dev_labels, dev_inputs,
                           static_cast<cudaStream_t>(stream)));
     return MC_OK;
 }

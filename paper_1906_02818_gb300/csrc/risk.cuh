@@ -27,7 +27,7 @@ struct RiskArgs {
 };
 
 cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float steps_per_year, uint32_t k0, uint32_t k1,
-                          float *labels, cudaStream_t s);
+                          float *labels, float *inputs, cudaStream_t s);
 cudaError_t launch_outer(int64_t nscen, int d, const float *Lc, const float *drift, const float *s0, uint32_t k0,
                          uint32_t k1, float *Sp, cudaStream_t s);
 cudaError_t launch_nested(const RiskArgs &a, int64_t nscen, const float *Sp, double *contrib, cudaStream_t s);

@@ -104,7 +104,7 @@ SIGNATURES = [
     ("mc_risk", ctypes.c_int, [ctypes.POINTER(McPortfolio), ctypes.POINTER(McRiskCfg),
                                ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_surrogate_labels", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_price_gbm1d_noalloc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg),
                                               ctypes.POINTER(McPayoff), ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p]),

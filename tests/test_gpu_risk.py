@@ -82,13 +82,14 @@ def test_var_cvar_selection_is_exact(gb):
 
 @pytest.fixture(scope="module")
 def trained(gb):
-    """A surrogate trained on GPU Monte Carlo labels (2^17 points, 2^11 paths
+    """A surrogate trained on GPU Monte Carlo labels (2^18 points, 2^11 paths
     each: a reduced version of the 2^20-label training)."""
     import torch
-    pts = torch.from_numpy(workloads.surrogate_points(1 << 17)).cuda()
-    lab = gb.surrogate_labels(pts, 2048)
+    pts = torch.from_numpy(workloads.surrogate_points(1 << 18)).cuda()
+    lab, x = gb.surrogate_labels(pts, 2048, with_inputs=True)
     net = gb.Mlp(5, 256, 4, workloads.mlp_init())
-    loss = net.train(pts, lab, epochs=40, batch=2048, lr=1e-3)
+    for lr, ep in workloads.SURROGATE_SCHEDULE:
+        loss = net.train(x, lab, epochs=ep, batch=4096, lr=lr)
     print("surrogate final epoch loss %.3e" % loss)
     return net, loss
 

@@ -140,3 +140,7 @@ def surrogate_points(n: int, seed: int = SEED + 2) -> np.ndarray:
     x[:, 3] = rng.uniform(0.0, 0.08, n)
     x[:, 4] = np.where(rng.uniform(size=n) < 0.5, 0.0, rng.uniform(0.5, 0.9, n))
     return x.astype(np.float32)
+
+
+# Adam learning-rate schedule of the surrogate: (lr, epochs) phases.
+SURROGATE_SCHEDULE = ((1e-3, 30), (3e-4, 20), (1e-4, 20))
