@@ -1,0 +1,452 @@
+// Large correlated basket (64 < d <= 512, European payoffs) with the
+// correlation contraction on the tensor cores, per time step (Sec. II.A.2):
+//   D[128 paths x d] (TMEM, FP32) += Z_i[128 x d] Lq^T        for i = 0..M-1,
+// so the tensor-memory accumulator is the running sum of the correlated
+// Brownian increments (the FP32 running log-price up to the drift), and
+// log2(S_n(T) / S0_n) = M drift_n + cs_n D_n at the end of the path.
+//
+// Warp roles (one CTA of 18 warps per SM; the accumulator takes all 512 TMEM
+// columns):
+//   warp 0   lane 0: TMA producer - streams the pre-swizzled 64 x 64 chunks
+//            of the quantised factor Lq (only chunks on or below the
+//            diagonal) into a ring of shared-memory slots;
+//   warp 1   lane 0: MMA issuer - for each 64-column panel p of Z and each
+//            64-row block b >= p of Lq: 4 (2 for E4M3) tcgen05.mma of
+//            128 x 64 x 16 (x32) into TMEM columns [64 b, 64 b + 64);
+//   warps 2..17: 512 threads; thread (warp w, lane l) owns path row
+//            32 (w mod 4) + l (its TMEM lane) and column group (w - 2) / 4;
+//            it draws 16 normals of every panel of its row per step
+//            (Philox4x32-10 + Box-Muller in registers), rounds them to the
+//            operand type and stores them in the 128B- (64B-) swizzled tile;
+//            at the end of a tile it reads its row's 128 columns of D,
+//            forms the terminal prices, the basket, the payoffs and the
+//            pathwise delta / vega / rho contributions.
+// The Z tile is split in two halves of panels with their own full / free
+// mbarriers, so drawing half A of step i+1 overlaps the MMAs of half B of
+// step i.  Every mbarrier wait is bounded; on expiry the CTA records an error
+// word and stops issuing work (results become NaN).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mc_kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace gbmc {
+namespace tcbig {
+
+constexpr int kRows = 128;
+constexpr int kPanel = 64;
+constexpr int kMaxPanels = 8;
+constexpr int kRing = 6;          // factor-chunk slots
+constexpr int kThreads = 576;     // 18 warps
+constexpr int kWorkers = 512;     // warps 2..17
+
+template <int PREC>
+struct L2 {
+    static constexpr int kElem = PREC == MC_FP8E4M3 ? 1 : 2;
+    static constexpr int kRowBytes = kPanel * kElem;             // 128 or 64
+    static constexpr int kPanelBytes = kRows * kRowBytes;        // Z panel
+    static constexpr int kChunkBytes = kPanel * kRowBytes;       // 64 x 64 factor chunk
+    static constexpr int kGroup = 8 * kRowBytes;                 // SBO
+    static constexpr int kKStep = PREC == MC_FP8E4M3 ? 32 : 16;
+    static constexpr int kMmas = kPanel / kKStep;
+    static constexpr tc::Swizzle kSw = PREC == MC_FP8E4M3 ? tc::SW_64B : tc::SW_128B;
+    static constexpr int kZBytes = kMaxPanels * kPanelBytes;
+    // [pad 1024] Z | ring | barriers (256 B) | accumulators
+    static constexpr int kBarOff = kZBytes + kRing * kChunkBytes;
+    static constexpr int kSmem = 1024 + kBarOff + 256;
+    __device__ static __forceinline__ uint32_t off(int row, int chunk)
+    {
+        const int phys = PREC == MC_FP8E4M3 ? (chunk ^ ((row >> 1) & 3)) : (chunk ^ (row & 7));
+        return static_cast<uint32_t>((row >> 3) * kGroup + (row & 7) * kRowBytes + phys * 16);
+    }
+};
+
+// E4M3 operands: fixed scale of the normals (|z| <= 5.78 < 6 by the uniform map).
+constexpr float kZScale8 = 448.0f / 6.0f;
+
+__device__ __forceinline__ void stv4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pk2(float lo, float hi)
+{
+    if (PREC == MC_BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ uint32_t pk4e(float a, float b, float c, float d)
+{
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b * kZScale8), "f"(a * kZScale8));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d * kZScale8), "f"(c * kZScale8));
+    return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+__device__ __forceinline__ void named_sync_workers() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// Bounded wait that gives up at once when the CTA has already failed, and
+// records a failure when it runs out.  Loops never exit early on failure:
+// every thread keeps arriving where it would have arrived, so no barrier is
+// left short of arrivals; the remaining waits are skipped.
+__device__ __forceinline__ bool wait_or_fail(volatile unsigned int *fail, uint32_t addr, uint32_t parity, uint32_t cap)
+{
+    if (*fail) return false;
+    if (tc::mbar_wait_bounded(addr, parity, cap)) return true;
+    *fail = 1u;
+    return false;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a)
+{
+    using Ly = L2<PREC>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ float s_u[4][kRows];                  // basket partials per column group
+    __shared__ float s_pay[MC_MAX_PAYOFFS][2];       // payoff sums of the CTA
+    __shared__ float s_g[kBigMaxD * 2 + 1][2];       // delta_n, vega_n, rho sums of the CTA (payoff 0)
+    __shared__ volatile unsigned int s_fail;
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t zt = base, ring = base + Ly::kZBytes, bars = base + Ly::kBarOff;
+    // barrier words: zfull[2], zfree[2], lfull[R], lfree[R], ddone, dfree, tslot
+    const uint32_t zfull = bars, zfree = bars + 16, lfull = bars + 32, lfree = lfull + 8 * kRing;
+    const uint32_t ddone = lfree + 8 * kRing, dfree = ddone + 8, tslot = dfree + 8;
+    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
+
+    const int d = a.d, NP = (d + kPanel - 1) / kPanel, half = (NP + 1) / 2;
+    const int M = a.run.steps;
+    const int nv = a.pay.n;
+    for (int i = t; i < nv * 2; i += kThreads) s_pay[i >> 1][i & 1] = 0.0f;
+    for (int i = t; i < (2 * d + 1) * 2; i += kThreads) s_g[i >> 1][i & 1] = 0.0f;
+    if (t == 0) {
+        s_fail = 0;
+        tc::mbar_init(zfull, kWorkers);
+        tc::mbar_init(zfull + 8, kWorkers);
+        tc::mbar_init(zfree, 1);
+        tc::mbar_init(zfree + 8, 1);
+        for (int r = 0; r < kRing; ++r) {
+            tc::mbar_init(lfull + 8 * r, 1);
+            tc::mbar_init(lfree + 8 * r, 1);
+        }
+        tc::mbar_init(ddone, 1);
+        tc::mbar_init(dfree, kWorkers);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot_ptr;
+    const int64_t ntiles = (a.run.paths + kRows - 1) / kRows;
+    // chunks per step: sum over panels p of (NP - p)
+    const uint32_t cap = a.wait_cap;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint64_t c = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+                for (int i = 0; i < M; ++i)
+                    for (int p = 0; p < NP; ++p)
+                        for (int b = p; b < NP; ++b, ++c) {
+                            const uint32_t slot = static_cast<uint32_t>(c % kRing);
+                            if (c >= kRing &&
+                                !wait_or_fail(&s_fail, lfree + 8 * slot, static_cast<uint32_t>((c / kRing - 1) & 1), cap))
+                                continue;
+                            if (s_fail) continue;
+                            tc::mbar_arrive_expect_tx(lfull + 8 * slot, Ly::kChunkBytes);
+                            tc::bulk_g2s(ring + slot * Ly::kChunkBytes,
+                                         a.bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes,
+                                         Ly::kChunkBytes, lfull + 8 * slot);
+                        }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = PREC == MC_FP8E4M3 ? tc::idesc_e4m3(kRows, kPanel)
+                                                      : tc::idesc_f16(kRows, kPanel, PREC == MC_BF16);
+            uint64_t c = 0, g = 0, tl = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+                if (tl > 0) wait_or_fail(&s_fail, dfree, static_cast<uint32_t>((tl - 1) & 1), cap);
+                for (int i = 0; i < M; ++i, ++g) {
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int p0 = hh ? half : 0, p1 = hh ? NP : half;
+                        const bool zok = wait_or_fail(&s_fail, zfull + 8 * hh, static_cast<uint32_t>(g & 1), cap);
+                        tc::fence_after_sync();
+                        for (int p = p0; p < p1; ++p)
+                            for (int b = p; b < NP; ++b, ++c) {
+                                const uint32_t slot = static_cast<uint32_t>(c % kRing);
+                                if (!zok || !wait_or_fail(&s_fail, lfull + 8 * slot, static_cast<uint32_t>((c / kRing) & 1), cap))
+                                    continue;
+                                tc::fence_after_sync();
+#pragma unroll
+                                for (int kk = 0; kk < Ly::kMmas; ++kk) {
+                                    const uint64_t ad = tc::smem_desc(zt + p * Ly::kPanelBytes + kk * 32, Ly::kGroup, Ly::kSw);
+                                    const uint64_t bd = tc::smem_desc(ring + slot * Ly::kChunkBytes + kk * 32, Ly::kGroup, Ly::kSw);
+                                    const uint32_t acc = (i == 0 && p == 0 && kk == 0) ? 0u : 1u;
+                                    if (PREC == MC_FP8E4M3) tc::mma_f8(tmem + b * kPanel, ad, bd, idesc, acc);
+                                    else tc::mma_f16(tmem + b * kPanel, ad, bd, idesc, acc);
+                                }
+                                tc::mma_commit(lfree + 8 * slot);
+                            }
+                        tc::mma_commit(zfree + 8 * hh);
+                    }
+                }
+                tc::mma_commit(ddone);
+            }
+        }
+    } else {
+        // ---------------- RNG + epilogue workers ----------------
+        const int row = 32 * (warp & 3) + lane;
+        const int grp = (warp - 2) >> 2;  // column group 0..3
+        uint64_t g = 0, tl = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+            const int64_t nl = tile * kRows + row;
+            const bool valid = nl < a.run.paths;
+            const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
+            NormalReader rd;
+            rd.init(n, a.run.k0, a.run.k1);
+            for (int i = 0; i < M; ++i, ++g) {
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int p0 = hh ? half : 0, p1 = hh ? NP : half;
+                    const bool ok = g == 0 || wait_or_fail(&s_fail, zfree + 8 * hh, static_cast<uint32_t>((g - 1) & 1), cap);
+                    if (ok && !s_fail) {
+                        for (int p = p0; p < p1; ++p) {
+                            float z[16];
+                            const int c0 = p * kPanel + grp * 16;
+#pragma unroll
+                            for (int l = 0; l < 16; ++l) z[l] = 0.0f;
+                            if (valid && c0 < d) {
+                                if (a.exact4 && c0 + 16 <= d) {
+                                    const uint64_t q = (static_cast<uint64_t>(i) * d + c0) >> 2;
+#pragma unroll
+                                    for (int bq = 0; bq < 4; ++bq) {
+                                        const float4 v = normals4(q + bq, n, a.run.k0, a.run.k1);
+                                        z[4 * bq] = v.x; z[4 * bq + 1] = v.y; z[4 * bq + 2] = v.z; z[4 * bq + 3] = v.w;
+                                    }
+                                } else {
+                                    for (int l = 0; l < 16; ++l)
+                                        if (c0 + l < d) z[l] = rd.get(static_cast<uint64_t>(i) * d + c0 + l);
+                                }
+                            }
+                            const uint32_t pan = zt + p * Ly::kPanelBytes;
+                            if (PREC == MC_FP8E4M3) {
+                                stv4(pan + Ly::off(row, grp), pk4e(z[0], z[1], z[2], z[3]), pk4e(z[4], z[5], z[6], z[7]),
+                                     pk4e(z[8], z[9], z[10], z[11]), pk4e(z[12], z[13], z[14], z[15]));
+                            } else {
+                                stv4(pan + Ly::off(row, 2 * grp), pk2<PREC>(z[0], z[1]), pk2<PREC>(z[2], z[3]),
+                                     pk2<PREC>(z[4], z[5]), pk2<PREC>(z[6], z[7]));
+                                stv4(pan + Ly::off(row, 2 * grp + 1), pk2<PREC>(z[8], z[9]), pk2<PREC>(z[10], z[11]),
+                                     pk2<PREC>(z[12], z[13]), pk2<PREC>(z[14], z[15]));
+                            }
+                        }
+                        tc::fence_proxy_async();
+                    }
+                    mbar_arrive(zfull + 8 * hh);  // always: the MMA issuer counts 512 arrivals
+                }
+            }
+            // ---- epilogue: terminal prices, basket, payoffs, pathwise Greeks ----
+            wait_or_fail(&s_fail, ddone, static_cast<uint32_t>(tl & 1), cap);
+            tc::fence_after_sync();
+            // warp-uniform decision for the warp-collective TMEM loads
+            const bool live = __all_sync(0xffffffffu, s_fail == 0u);
+            const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + grp * 128;
+            float upart = 0.0f;
+            const int cbeg = grp * 128;
+            if (live) {
+                for (int cc = 0; cc < 8; ++cc) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + cc * 16, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int l = 0; l < 16; ++l) {
+                        const int col = cbeg + cc * 16 + l;
+                        if (col < d) upart = fmaf(a.ws0[col], ex2_approx(fmaf(a.cs[col], v[l], a.mdrift[col])), upart);
+                    }
+                }
+            }
+            s_u[grp][row] = upart;
+            named_sync_workers();
+            const float U = s_u[0][row] + s_u[1][row] + s_u[2][row] + s_u[3][row];
+            const bool use = valid && live;
+            if (grp == 0) {  // payoffs: European kinds on U(T)
+                for (int p = 0; p < nv; ++p) {
+                    const float f = use ? payoff_eval(a.pay.kind[p], a.pay.strike[p], INFINITY, U, 0.0f, 0.0f, 0.0f) : 0.0f;
+                    const float s1 = warp_sum(f), s2 = warp_sum(f * f);
+                    if (lane == 0) {
+                        atomicAdd(&s_pay[p][0], s1);
+                        atomicAdd(&s_pay[p][1], s2);
+                    }
+                }
+            }
+            // pathwise Greeks of payoff 0: delta_n = g w_n S_n / S0_n,
+            // vega_n = g w_n S_n (-sigma_n T + sqrt(dt) (Lrho W)_n), rho = g U T - T f
+            if (a.greeks) {
+                const float gsl = use ? (a.pay.kind[0] == MC_PUT ? (U < a.pay.strike[0] ? -1.0f : 0.0f)
+                                                                 : (U > a.pay.strike[0] ? 1.0f : 0.0f))
+                                      : 0.0f;
+                for (int cc = 0; cc < 8; ++cc) {
+                    float v[16];
+                    if (live) {
+                        tc::tmem_ld16(taddr + cc * 16, v);
+                        tc::tmem_wait_ld();
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < 16; ++l) v[l] = 0.0f;
+                    }
+#pragma unroll
+                    for (int l = 0; l < 16; ++l) {
+                        const int col = cbeg + cc * 16 + l;
+                        const bool in = col < d;
+                        const float S = in ? a.s0[col] * ex2_approx(fmaf(a.cs[col], v[l], a.mdrift[col])) : 0.0f;
+                        const float dl = in ? gsl * a.w[col] * S / a.s0[col] : 0.0f;
+                        const float vg = in ? gsl * a.w[col] * S * fmaf(-a.sigma[col], a.T, a.vscale[col] * v[l]) : 0.0f;
+                        const float d1 = warp_sum(dl), d2 = warp_sum(dl * dl);
+                        const float v1 = warp_sum(vg), v2 = warp_sum(vg * vg);
+                        if (lane == 0 && in) {
+                            atomicAdd(&s_g[col][0], d1);
+                            atomicAdd(&s_g[col][1], d2);
+                            atomicAdd(&s_g[d + col][0], v1);
+                            atomicAdd(&s_g[d + col][1], v2);
+                        }
+                    }
+                }
+                if (grp == 0) {
+                    const float f = use ? payoff_eval(a.pay.kind[0], a.pay.strike[0], INFINITY, U, 0.0f, 0.0f, 0.0f) : 0.0f;
+                    const float rr = gsl * U * a.T - a.T * f;
+                    const float r1 = warp_sum(rr), r2 = warp_sum(rr * rr);
+                    if (lane == 0) {
+                        atomicAdd(&s_g[2 * d][0], r1);
+                        atomicAdd(&s_g[2 * d][1], r2);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            mbar_arrive(dfree);
+            named_sync_workers();
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+    if (t == 0 && s_fail) atomicExch(a.err, 1u);
+    // per-CTA partials -> last CTA sums them in FP64
+    const int nvals = nv + (a.greeks ? 2 * d + 1 : 0);
+    for (int i = t; i < nvals * 2; i += kThreads) {
+        const int k = i >> 1, m = i & 1;
+        const float v = k < nv ? s_pay[k][m] : s_g[k - nv][m];
+        a.partials[static_cast<size_t>(blockIdx.x) * nvals * 2 + i] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const bool bad = *reinterpret_cast<volatile unsigned int *>(a.err) != 0u;  // any CTA failed
+    const double N = static_cast<double>(a.run.paths);
+    for (int k = t; k < nvals; k += kThreads) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
+            s1 += a.partials[static_cast<size_t>(b) * nvals * 2 + 2 * k];
+            s2 += a.partials[static_cast<size_t>(b) * nvals * 2 + 2 * k + 1];
+        }
+        const double mean = s1 / N, var = fmax(s2 / N - mean * mean, 0.0);
+        mc_result r;
+        r.price = bad ? __longlong_as_double(0x7ff8000000000000ll) : a.disc * mean;
+        r.se = bad ? r.price : (a.run.paths > 1 ? a.disc * sqrt(var / (N - 1.0)) : 0.0);
+        a.out[k] = r;
+    }
+    __syncthreads();
+    if (t == 0) *a.ticket = 0u;
+}
+
+// Factor chunks (b, p) (64 x 64, rows 64 b.., columns 64 p..) of Lq = s_n Lrho,
+// each pre-swizzled for the MMA's B operand, at (b * 8 + p) * chunk bytes;
+// plus the per-column epilogue constants.
+template <int PREC>
+__global__ void big_prep_kernel(int d, const double *L, const double *sigma, double cfac, double sdt, double r,
+                                double dt, int M, uint8_t *bimg, float *cs, float *mdrift, float *vscale)
+{
+    using Ly = L2<PREC>;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= kMaxPanels * kPanel) return;
+    double amax = 0.0;
+    for (int k = 0; k <= n && k < d; ++k) amax = fmax(amax, fabs(n < d ? L[static_cast<int64_t>(n) * d + k] : 0.0));
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : 1.0;
+    const int b = n / kPanel, rb = n % kPanel;
+    for (int k = 0; k < kMaxPanels * kPanel; ++k) {
+        const int p = k / kPanel, kc = k % kPanel;
+        if (p > b) continue;  // chunks above the diagonal block are never loaded
+        const double v = (n < d && k <= n && k < d) ? L[static_cast<int64_t>(n) * d + k] * s : 0.0;
+        const float fv = static_cast<float>(v);
+        uint8_t *chunk = bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes;
+        const uint32_t off = Ly::off(rb, kc / (16 / Ly::kElem)) + (kc % (16 / Ly::kElem)) * Ly::kElem;
+        if (PREC == MC_BF16) *reinterpret_cast<__nv_bfloat16 *>(chunk + off) = __float2bfloat16_rn(fv);
+        else if (PREC == MC_FP16) *reinterpret_cast<__half *>(chunk + off) = __float2half_rn(fv);
+        else {
+            uint16_t pr;
+            asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(pr) : "f"(0.0f), "f"(fv));
+            chunk[off] = static_cast<uint8_t>(pr & 0xFFu);
+        }
+    }
+    if (n < d) {
+        const double zdeq = PREC == MC_FP8E4M3 ? 1.0 / kZScale8 : 1.0;
+        cs[n] = static_cast<float>(cfac * sdt * sigma[n] * zdeq / s);
+        mdrift[n] = static_cast<float>(cfac * (r - 0.5 * sigma[n] * sigma[n]) * dt * M);
+        vscale[n] = static_cast<float>(sdt * zdeq / s);  // sqrt(dt) (Lrho W)_n = vscale_n D_n
+    }
+}
+
+}  // namespace tcbig
+
+template <int PREC>
+const void *basket_big_fn()
+{
+    return reinterpret_cast<const void *>(&tcbig::basket_big_kernel<PREC>);
+}
+
+template <int PREC>
+int basket_big_smem()
+{
+    return tcbig::L2<PREC>::kSmem;
+}
+
+template <int PREC>
+cudaError_t big_prep(int d, const double *L, const double *sigma, double cfac, double sdt, double r, double dt, int M,
+                     uint8_t *bimg, float *cs, float *mdrift, float *vscale, cudaStream_t s)
+{
+    tcbig::big_prep_kernel<PREC><<<(tcbig::kMaxPanels * tcbig::kPanel + 127) / 128, 128, 0, s>>>(
+        d, L, sigma, cfac, sdt, r, dt, M, bimg, cs, mdrift, vscale);
+    return cudaGetLastError();
+}
+
+#define GBMC_INSTANTIATE_BIG(PREC)                                                                             \
+    template const void *basket_big_fn<PREC>();                                                               \
+    template int basket_big_smem<PREC>();                                                                     \
+    template cudaError_t big_prep<PREC>(int, const double *, const double *, double, double, double, double, int, \
+                                        uint8_t *, float *, float *, float *, cudaStream_t);
+
+}  // namespace gbmc

