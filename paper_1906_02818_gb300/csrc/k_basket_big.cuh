@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
                                         z[4 * bq] = v.x; z[4 * bq + 1] = v.y; z[4 * bq + 2] = v.z; z[4 * bq + 3] = v.w;
                                     }
                                 } else {
-                                    for (int l = 0; l < 16; ++l)
+#pragma unroll
+                                    for (int l = 0; l < 16; ++l)  // unrolled: z stays in registers
                                         if (c0 + l < d) z[l] = rd.get(static_cast<uint64_t>(i) * d + c0 + l);
                                 }
                             }

@@ -1,108 +1,223 @@
 // FP32 contraction for large baskets (64 < d <= 512), the reference
-// precision of the tensor-core kernels: one thread per path, the state and
-// the step's normals in thread-local memory (they do not fit registers), the
-// packed factor c sqrt(dt) diag(sigma) Lrho read from global memory (every
-// thread of a warp reads the same entry: one broadcast load), the
-// multivariate Euler step of Sec. II.A.2 row by row.  European payoffs on
-// U(T) and the pathwise Greeks of payoff 0, accumulated per CTA with shared
-// atomics and finished in FP64 by the last CTA.
+// precision of the tensor-core kernels: the multivariate Euler step of
+// Sec. II.A.2 for a tile of 64 paths as a register-tiled SIMT product.
+//   * CTA = 64 paths x D assets (D = 128, 256 or 512, zero-padded), 256
+//     threads; thread (pg, ag) owns paths 4 pg .. 4 pg + 3 and the assets
+//     64 j + 4 ag .. + 3 (j < D / 64): 4 x D / 16 running sums in registers,
+//     acc[p][a] = sum over steps of (Lhat z)_a, Lhat = log2(e) sqrt(dt)
+//     diag(sigma) Lrho.
+//   * per step: the CTA draws the 64 x d normals into shared memory
+//     (z[k][path], consecutive threads on consecutive paths), then streams
+//     Lhat^T in chunks of 16 rows (cp.async double buffer) and accumulates;
+//     64-asset blocks that lie above the chunk (zero in the lower-triangular
+//     factor) are skipped.
+//   * at the end of the tile: log2(S_a / S0_a) = M drift_a + acc, the basket,
+//     European payoffs and the pathwise delta / vega / rho of payoff 0.
 #include "mc_kernels.cuh"
 
 namespace gbmc {
 namespace {
 
-constexpr int kBlock = 128;
+constexpr int kP = 64;       // paths per CTA
+constexpr int kThreads = 256;
+constexpr int kKC = 16;      // factor rows per chunk
 
-__global__ void __launch_bounds__(kBlock) basket_wide_kernel(const BigArgs a)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs a)
+{
+    constexpr int J = D / 64;  // 4-asset groups per thread
+    extern __shared__ __align__(16) float sm[];
+    float *zs = sm;                      // [D][kP]
+    float *Ls = sm + D * kP;             // [2][kKC][D]
     __shared__ float s_pay[MC_MAX_PAYOFFS][2];
     __shared__ float s_g[kBigMaxD * 2 + 1][2];
-    const int d = a.d, nv = a.pay.n;
-    for (int i = threadIdx.x; i < nv * 2; i += blockDim.x) s_pay[i >> 1][i & 1] = 0.0f;
-    for (int i = threadIdx.x; i < (2 * d + 1) * 2; i += blockDim.x) s_g[i >> 1][i & 1] = 0.0f;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t gthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    const int64_t ppt = (a.run.paths + gthreads - 1) / gthreads;
-    const int M = a.run.steps;
-    float x[kBigMaxD], z[kBigMaxD];
-    for (int64_t it = 0; it < ppt; ++it) {
-        const int64_t nl = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x + it * gthreads;
-        const bool valid = nl < a.run.paths;
-        float U = 0.0f;
-        if (valid) {
-            const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
-            NormalReader rd;
-            rd.init(n, a.run.k0, a.run.k1);
-            for (int j = 0; j < d; ++j) x[j] = 0.0f;
-            for (int i = 0; i < M; ++i) {
-                for (int j = 0; j < d; ++j) z[j] = rd.get(static_cast<uint64_t>(i) * d + j);
-                for (int j = 0; j < d; ++j) {
-                    const float *row = a.Lp + static_cast<int64_t>(j) * (j + 1) / 2;
-                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-                    int k = 0;
-                    for (; k + 3 <= j; k += 4) {
-                        s0 = fmaf(row[k], z[k], s0);
-                        s1 = fmaf(row[k + 1], z[k + 1], s1);
-                        s2 = fmaf(row[k + 2], z[k + 2], s2);
-                        s3 = fmaf(row[k + 3], z[k + 3], s3);
+    __shared__ float s_u[kP];
+    const int t = threadIdx.x, lane = t & 31;
+    const int pg = t >> 4, ag = t & 15;
+    const int d = a.d, nv = a.pay.n, M = a.run.steps;
+    for (int i = t; i < nv * 2; i += kThreads) s_pay[i >> 1][i & 1] = 0.0f;
+    for (int i = t; i < (2 * d + 1) * 2; i += kThreads) s_g[i >> 1][i & 1] = 0.0f;
+    const int64_t ntiles = (a.run.paths + kP - 1) / kP;
+    const int nchunks = (d + kKC - 1) / kKC;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        float acc[4][J][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[p][j][e] = 0.0f;
+        // RNG mapping: path t % 64, normals [q*D/4, (q+1)*D/4) with q = t / 64
+        const int rp = t & (kP - 1), rq = t >> 6;
+        const int64_t rnl = tile * kP + rp;
+        const bool rvalid = rnl < a.run.paths;
+        const uint64_t rn = static_cast<uint64_t>(a.run.path_offset + (rvalid ? rnl : 0));
+        NormalReader rd;
+        rd.init(rn, a.run.k0, a.run.k1);
+        for (int i = 0; i < M; ++i) {
+            __syncthreads();  // previous step done with zs
+            for (int k = rq * (D / 4); k < (rq + 1) * (D / 4); k += 4) {
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (rvalid && k < d) {
+                    if (a.exact4) {
+                        z = normals4((static_cast<uint64_t>(i) * d + k) >> 2, rn, a.run.k0, a.run.k1);
+                    } else {
+                        const uint64_t j0 = static_cast<uint64_t>(i) * d + k;
+                        z.x = rd.get(j0);
+                        z.y = k + 1 < d ? rd.get(j0 + 1) : 0.f;
+                        z.z = k + 2 < d ? rd.get(j0 + 2) : 0.f;
+                        z.w = k + 3 < d ? rd.get(j0 + 3) : 0.f;
                     }
-                    for (; k <= j; ++k) s0 = fmaf(row[k], z[k], s0);
-                    x[j] += a.drift[j] + ((s0 + s1) + (s2 + s3));
+                }
+                zs[(k + 0) * kP + rp] = z.x;
+                zs[(k + 1) * kP + rp] = z.y;
+                zs[(k + 2) * kP + rp] = z.z;
+                zs[(k + 3) * kP + rp] = z.w;
+            }
+            // first factor chunk
+            for (int e = t * 4; e < kKC * D; e += kThreads * 4) cp_async16(Ls + e, a.Lp + e);
+            cp_async_commit();
+            for (int c = 0; c < nchunks; ++c) {
+                cp_async_wait_all();
+                __syncthreads();  // chunk c (and, at c = 0, the normals) visible
+                const float *Lc = Ls + (c & 1) * kKC * D;
+                if (c + 1 < nchunks) {  // prefetch the next chunk into the other buffer
+                    float *dst = Ls + ((c + 1) & 1) * kKC * D;
+                    const float *src = a.Lp + static_cast<size_t>(c + 1) * kKC * D;
+                    for (int e = t * 4; e < kKC * D; e += kThreads * 4) cp_async16(dst + e, src + e);
+                    cp_async_commit();
+                }
+                const int k0 = c * kKC;
+#pragma unroll 4
+                for (int kk = 0; kk < kKC; ++kk) {
+                    const float4 zv = *reinterpret_cast<const float4 *>(zs + (k0 + kk) * kP + 4 * pg);
+                    const float zz[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        if (64 * j + 63 < k0) continue;  // block above the diagonal chunk: zero
+                        const float4 lv = *reinterpret_cast<const float4 *>(Lc + kk * D + 64 * j + 4 * ag);
+                        const float ll[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[p][j][e] = fmaf(ll[e], zz[p], acc[p][j][e]);
+                    }
+                }
+                __syncthreads();  // everyone done with chunk c before it is overwritten
+            }
+        }
+        // ---- epilogue ----
+        float Ux[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = 64 * j + 4 * ag + e;
+                if (col < d) {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        Ux[p] = fmaf(a.ws0[col], ex2_approx(fmaf(static_cast<float>(M), a.drift[col], acc[p][j][e])), Ux[p]);
                 }
             }
-            for (int j = 0; j < d; ++j) U = fmaf(a.ws0[j], ex2_approx(x[j]), U);
-        }
-        for (int p = 0; p < nv; ++p) {
-            const float f = valid ? payoff_eval(a.pay.kind[p], a.pay.strike[p], INFINITY, U, 0.0f, 0.0f, 0.0f) : 0.0f;
-            const float s1 = warp_sum(f), s2 = warp_sum(f * f);
-            if (lane == 0) {
-                atomicAdd(&s_pay[p][0], s1);
-                atomicAdd(&s_pay[p][1], s2);
+        // sum over the 16 asset groups of each path (lanes with the same pg: a half warp)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) Ux[p] += __shfl_xor_sync(0xffffffffu, Ux[p], o);
+        if (ag == 0)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) s_u[4 * pg + p] = Ux[p];
+        __syncthreads();
+        if (t < kP) {  // payoffs, one thread per path
+            const bool valid = tile * kP + t < a.run.paths;
+            for (int q = 0; q < nv; ++q) {
+                const float f = valid ? payoff_eval(a.pay.kind[q], a.pay.strike[q], INFINITY, s_u[t], 0.f, 0.f, 0.f) : 0.f;
+                const float s1 = warp_sum(f), s2 = warp_sum(f * f);
+                if (lane == 0) {
+                    atomicAdd(&s_pay[q][0], s1);
+                    atomicAdd(&s_pay[q][1], s2);
+                }
             }
         }
         if (a.greeks) {
-            const float g = valid ? (a.pay.kind[0] == MC_PUT ? (U < a.pay.strike[0] ? -1.0f : 0.0f)
-                                                             : (U > a.pay.strike[0] ? 1.0f : 0.0f))
-                                  : 0.0f;
-            for (int j = 0; j < d; ++j) {
-                const float S = valid ? a.s0[j] * ex2_approx(x[j]) : 0.0f;
-                // sqrt(dt) (Lrho W)_j = (x_j - M drift_j) / (log2(e) sigma_j)
-                const float bw = valid ? (x[j] - M * a.drift[j]) / (kLog2e * a.sigma[j]) : 0.0f;
-                const float dl = g * a.w[j] * S / a.s0[j];
-                const float vg = g * a.w[j] * S * fmaf(-a.sigma[j], a.T, bw);
-                const float d1 = warp_sum(dl), d2 = warp_sum(dl * dl), v1 = warp_sum(vg), v2 = warp_sum(vg * vg);
+            float gs[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const float U = s_u[4 * pg + p];
+                const bool valid = tile * kP + 4 * pg + p < a.run.paths;
+                gs[p] = valid ? (a.pay.kind[0] == MC_PUT ? (U < a.pay.strike[0] ? -1.f : 0.f)
+                                                         : (U > a.pay.strike[0] ? 1.f : 0.f))
+                              : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = 64 * j + 4 * ag + e;
+                    float d1 = 0.f, d2 = 0.f, v1 = 0.f, v2 = 0.f;
+                    if (col < d) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const float S = a.s0[col] * ex2_approx(fmaf(static_cast<float>(M), a.drift[col], acc[p][j][e]));
+                            const float dl = gs[p] * a.w[col] * S / a.s0[col];
+                            // sqrt(dt) (Lrho W)_col = acc / (log2(e) sigma_col)
+                            const float vg = gs[p] * a.w[col] * S * fmaf(-a.sigma[col], a.T, acc[p][j][e] / (kLog2e * a.sigma[col]));
+                            d1 += dl; d2 += dl * dl; v1 += vg; v2 += vg * vg;
+                        }
+                    }
+                    // lanes l and l ^ 16 hold the same column for the two path groups of the warp
+                    d1 += __shfl_xor_sync(0xffffffffu, d1, 16);
+                    d2 += __shfl_xor_sync(0xffffffffu, d2, 16);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, 16);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, 16);
+                    if (lane < 16 && col < d) {
+                        atomicAdd(&s_g[col][0], d1);
+                        atomicAdd(&s_g[col][1], d2);
+                        atomicAdd(&s_g[d + col][0], v1);
+                        atomicAdd(&s_g[d + col][1], v2);
+                    }
+                }
+            if (t < kP) {
+                const float U = s_u[t];
+                const bool valid = tile * kP + t < a.run.paths;
+                const float g = valid ? (a.pay.kind[0] == MC_PUT ? (U < a.pay.strike[0] ? -1.f : 0.f)
+                                                                 : (U > a.pay.strike[0] ? 1.f : 0.f))
+                                      : 0.f;
+                const float f = valid ? payoff_eval(a.pay.kind[0], a.pay.strike[0], INFINITY, U, 0.f, 0.f, 0.f) : 0.f;
+                const float rr = g * U * a.T - a.T * f;
+                const float r1 = warp_sum(rr), r2 = warp_sum(rr * rr);
                 if (lane == 0) {
-                    atomicAdd(&s_g[j][0], d1);
-                    atomicAdd(&s_g[j][1], d2);
-                    atomicAdd(&s_g[d + j][0], v1);
-                    atomicAdd(&s_g[d + j][1], v2);
+                    atomicAdd(&s_g[2 * d][0], r1);
+                    atomicAdd(&s_g[2 * d][1], r2);
                 }
             }
-            const float f = valid ? payoff_eval(a.pay.kind[0], a.pay.strike[0], INFINITY, U, 0.0f, 0.0f, 0.0f) : 0.0f;
-            const float rr = g * U * a.T - a.T * f;
-            const float r1 = warp_sum(rr), r2 = warp_sum(rr * rr);
-            if (lane == 0) {
-                atomicAdd(&s_g[2 * d][0], r1);
-                atomicAdd(&s_g[2 * d][1], r2);
-            }
         }
+        __syncthreads();
     }
-    __syncthreads();
+    // per-CTA partials -> FP64 sum by the last CTA
     const int nvals = nv + (a.greeks ? 2 * d + 1 : 0);
-    for (int i = threadIdx.x; i < nvals * 2; i += blockDim.x) {
+    for (int i = t; i < nvals * 2; i += kThreads) {
         const int k = i >> 1, m = i & 1;
         a.partials[static_cast<size_t>(blockIdx.x) * nvals * 2 + i] = k < nv ? s_pay[k][m] : s_g[k - nv][m];
     }
     __threadfence();
     __syncthreads();
     __shared__ unsigned int s_last;
-    if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     const double N = static_cast<double>(a.run.paths);
-    for (int k = threadIdx.x; k < nvals; k += blockDim.x) {
+    for (int k = t; k < nvals; k += kThreads) {
         double s1 = 0.0, s2 = 0.0;
         for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
             s1 += a.partials[static_cast<size_t>(b) * nvals * 2 + 2 * k];
@@ -115,12 +230,48 @@ __global__ void __launch_bounds__(kBlock) basket_wide_kernel(const BigArgs a)
         a.out[k] = r;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *a.ticket = 0u;
+    if (t == 0) *a.ticket = 0u;
+}
+
+// LT[k][a] (D x D, k-major) = log2(e) sqrt(dt) sigma_a Lrho[a][k] (0 above the
+// diagonal and beyond d); drift[a] = log2(e) (r - sigma_a^2 / 2) dt.
+__global__ void wide_prep_kernel(int d, int D, const double *L, const double *sigma, double sdt, double r, double dt,
+                                 float *LT, float *drift)
+{
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < static_cast<int64_t>(D) * D;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int k = static_cast<int>(idx / D), col = static_cast<int>(idx % D);
+        double v = 0.0;
+        if (col < d && k <= col) v = M_LOG2E * sdt * sigma[col] * L[static_cast<int64_t>(col) * d + k];
+        LT[idx] = static_cast<float>(v);
+    }
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < d; col += gridDim.x * blockDim.x)
+        drift[col] = static_cast<float>(M_LOG2E * (r - 0.5 * sigma[col] * sigma[col]) * dt);
 }
 
 }  // namespace
 
-const void *basket_wide_fn() { return reinterpret_cast<const void *>(&basket_wide_kernel); }
-int basket_wide_block() { return kBlock; }
+int wide_width(int d) { return d <= 128 ? 128 : (d <= 256 ? 256 : 512); }
+
+size_t wide_smem(int D) { return static_cast<size_t>(D) * kP * sizeof(float) + 2 * kKC * static_cast<size_t>(D) * sizeof(float); }
+
+const void *basket_wide_fn(int D)
+{
+    switch (D) {
+    case 128: return reinterpret_cast<const void *>(&basket_wide_kernel<128>);
+    case 256: return reinterpret_cast<const void *>(&basket_wide_kernel<256>);
+    default: return reinterpret_cast<const void *>(&basket_wide_kernel<512>);
+    }
+}
+
+int basket_wide_block() { return kThreads; }
+
+cudaError_t launch_wide_prep(int d, const double *L, const double *sigma, double sdt, double r, double dt, float *LT,
+                             float *drift, cudaStream_t s)
+{
+    const int D = wide_width(d);
+    wide_prep_kernel<<<256, 256, 0, s>>>(d, D, L, sigma, sdt, r, dt, LT, drift);
+    return cudaGetLastError();
+}
 
 }  // namespace gbmc

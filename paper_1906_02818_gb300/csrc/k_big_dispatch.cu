@@ -11,21 +11,28 @@ int basket_big_smem();
 template <int PREC>
 cudaError_t big_prep(int d, const double *L, const double *sigma, double cfac, double sdt, double r, double dt, int M,
                      uint8_t *bimg, float *cs, float *mdrift, float *vscale, cudaStream_t s);
-const void *basket_wide_fn();
+const void *basket_wide_fn(int D);
 int basket_wide_block();
+int wide_width(int d);
+size_t wide_smem(int D);
 
 namespace {
 
 constexpr int kBigThreads = 576;
 
-const void *select(int prec, int *smem, int *threads)
+const void *select(int prec, int d, int *smem, int *threads)
 {
     *threads = kBigThreads;
     switch (prec) {
     case MC_BF16: *smem = basket_big_smem<MC_BF16>(); return basket_big_fn<MC_BF16>();
     case MC_FP16: *smem = basket_big_smem<MC_FP16>(); return basket_big_fn<MC_FP16>();
     case MC_FP8E4M3: *smem = basket_big_smem<MC_FP8E4M3>(); return basket_big_fn<MC_FP8E4M3>();
-    default: *smem = 0; *threads = basket_wide_block(); return basket_wide_fn();
+    default: {
+        const int D = wide_width(d);
+        *smem = static_cast<int>(wide_smem(D));
+        *threads = basket_wide_block();
+        return basket_wide_fn(D);
+    }
     }
 }
 
@@ -36,7 +43,7 @@ size_t big_bimg_bytes(int prec) { return static_cast<size_t>(64) * (prec == MC_F
 cudaError_t launch_basket_big(int prec, const BigArgs &a, int grid, cudaStream_t s)
 {
     int smem = 0, threads = 0;
-    const void *fn = select(prec, &smem, &threads);
+    const void *fn = select(prec, a.d, &smem, &threads);
     if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -45,24 +52,17 @@ cudaError_t launch_basket_big(int prec, const BigArgs &a, int grid, cudaStream_t
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, static_cast<size_t>(smem), s);
 }
 
-// Tensor cores: one CTA per SM (the accumulator takes all of TMEM), at most
-// one per 128-path tile.  FP32: a resident wave of path-per-thread blocks.
+// One CTA per SM for both variants (tensor cores: the accumulator takes all
+// of TMEM; FP32: the normals and factor chunks take most of shared memory),
+// at most one per tile (128 paths, resp. 64 paths).
 int basket_big_grid(int prec, int64_t paths)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    int smem = 0, threads = 0;
-    const void *fn = select(prec, &smem, &threads);
-    if (prec != MC_FP32) {
-        const int64_t tiles = (paths + 127) / 128;
-        return static_cast<int>(tiles < sms ? tiles : sms);
-    }
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess || nb < 1) return 0;
-    const int64_t need = (paths + threads - 1) / threads;
-    const int64_t res = static_cast<int64_t>(nb) * sms;
-    return static_cast<int>(need < res ? need : res);
+    const int rows = prec != MC_FP32 ? 128 : 64;
+    const int64_t tiles = (paths + rows - 1) / rows;
+    return static_cast<int>(tiles < sms ? tiles : sms);
 }
 
 cudaError_t launch_big_prep(int prec, int d, const double *L, const double *sigma, double cfac, double sdt, double r,

@@ -247,9 +247,9 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
         MC_CUDA(launch_big_prep(P->prec, d, P->dL, P->dsig, M_LOG2E, sdt, m->r, dt, c->steps, P->bimg, col,
                                 col + kBigMaxD, col + 2 * kBigMaxD, s));
     } else {
-        MC_CUDA(cudaMalloc(&P->dLp, static_cast<size_t>(d) * (d + 1) / 2 * sizeof(float)));
-        MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, M_LOG2E, sdt, m->r, dt, MC_LOG_EULER, P->dLp,
-                                    col + 3 * kBigMaxD, s));
+        const size_t D = static_cast<size_t>(wide_width(d));
+        MC_CUDA(cudaMalloc(&P->dLp, D * D * sizeof(float)));
+        MC_CUDA(launch_wide_prep(d, P->dL, P->dsig, sdt, m->r, dt, P->dLp, col + 3 * kBigMaxD, s));
     }
     std::vector<float> h(4 * static_cast<size_t>(kBigMaxD), 0.0f);
     for (int k = 0; k < d; ++k) {

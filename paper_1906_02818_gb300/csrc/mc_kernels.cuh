@@ -90,7 +90,7 @@ struct BigArgs {
     int exact4;             // d % 4 == 0: each 16-normal group is 4 whole Philox blocks
     int greeks;
     const uint8_t *bimg;    // tensor cores: pre-swizzled factor chunks
-    const float *Lp;        // FP32: packed lower triangle of c sqrt(dt) diag(sigma) Lrho
+    const float *Lp;        // FP32: k-major dense log2(e) sqrt(dt) diag(sigma) Lrho, [D x D]
     const float *cs, *mdrift, *vscale;  // tensor cores: epilogue constants per column
     const float *drift;     // FP32: per-step drift (log2 units)
     const float *ws0, *w, *s0, *sigma;
@@ -107,6 +107,10 @@ cudaError_t launch_basket_big(int prec, const BigArgs &a, int grid, cudaStream_t
 int basket_big_grid(int prec, int64_t paths);
 cudaError_t launch_big_prep(int prec, int d, const double *L, const double *sigma, double cfac, double sdt, double r,
                             double dt, int M, uint8_t *bimg, float *cs, float *mdrift, float *vscale, cudaStream_t s);
+// FP32 large baskets: dense k-major factor LT [D x D], D = wide_width(d).
+int wide_width(int d);
+cudaError_t launch_wide_prep(int d, const double *L, const double *sigma, double sdt, double r, double dt, float *LT,
+                             float *drift, cudaStream_t s);
 size_t big_bimg_bytes(int prec);
 
 // Pathwise Greeks (k_greeks.cu): single-asset GBM (log-Euler, closed forms)
