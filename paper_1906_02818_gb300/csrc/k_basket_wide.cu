@@ -1,15 +1,15 @@
 // FP32 contraction for large baskets (64 < d <= 512), the reference
 // precision of the tensor-core kernels: the multivariate Euler step of
 // Sec. II.A.2 for a tile of 64 paths as a register-tiled SIMT product.
-//   * CTA = 64 paths x D assets (D = 128, 256 or 512, zero-padded), 256
+//   * CTA = 64 paths x D assets (D = 128, 256 or 512, zero-padded), 512
 //     threads; thread (pg, ag) owns paths 4 pg .. 4 pg + 3 and the assets
-//     64 j + 4 ag .. + 3 (j < D / 64): 4 x D / 16 running sums in registers,
+//     128 j + 4 ag .. + 3 (j < D / 128): 4 x D / 32 running sums in registers,
 //     acc[p][a] = sum over steps of (Lhat z)_a, Lhat = log2(e) sqrt(dt)
 //     diag(sigma) Lrho.
 //   * per step: the CTA draws the 64 x d normals into shared memory
 //     (z[k][path], consecutive threads on consecutive paths), then streams
 //     Lhat^T in chunks of 16 rows (cp.async double buffer) and accumulates;
-//     64-asset blocks that lie above the chunk (zero in the lower-triangular
+//     128-asset blocks that lie above the chunk (zero in the lower-triangular
 //     factor) are skipped.
 //   * at the end of the tile: log2(S_a / S0_a) = M drift_a + acc, the basket,
 //     European payoffs and the pathwise delta / vega / rho of payoff 0.
@@ -19,7 +19,7 @@ namespace gbmc {
 namespace {
 
 constexpr int kP = 64;       // paths per CTA
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kKC = 16;      // factor rows per chunk
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -33,7 +33,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int D>
 __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs a)
 {
-    constexpr int J = D / 64;  // 4-asset groups per thread
+    constexpr int J = D / 128;  // 4-asset groups per thread
     extern __shared__ __align__(16) float sm[];
     float *zs = sm;                      // [D][kP]
     float *Ls = sm + D * kP;             // [2][kKC][D]
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
     __shared__ float s_g[kBigMaxD * 2 + 1][2];
     __shared__ float s_u[kP];
     const int t = threadIdx.x, lane = t & 31;
-    const int pg = t >> 4, ag = t & 15;
+    const int pg = t >> 5, ag = t & 31;  // a warp = one path group, 32 asset groups
     const int d = a.d, nv = a.pay.n, M = a.run.steps;
     for (int i = t; i < nv * 2; i += kThreads) s_pay[i >> 1][i & 1] = 0.0f;
     for (int i = t; i < (2 * d + 1) * 2; i += kThreads) s_g[i >> 1][i & 1] = 0.0f;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
             for (int j = 0; j < J; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[p][j][e] = 0.0f;
-        // RNG mapping: path t % 64, normals [q*D/4, (q+1)*D/4) with q = t / 64
+        // RNG mapping: path t % 64, normals [q*D/8, (q+1)*D/8) with q = t / 64
         const int rp = t & (kP - 1), rq = t >> 6;
         const int64_t rnl = tile * kP + rp;
         const bool rvalid = rnl < a.run.paths;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
         rd.init(rn, a.run.k0, a.run.k1);
         for (int i = 0; i < M; ++i) {
             __syncthreads();  // previous step done with zs
-            for (int k = rq * (D / 4); k < (rq + 1) * (D / 4); k += 4) {
+            for (int k = rq * (D / 8); k < (rq + 1) * (D / 8); k += 4) {
                 float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (rvalid && k < d) {
                     if (a.exact4) {
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
                     const float zz[4] = {zv.x, zv.y, zv.z, zv.w};
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        if (64 * j + 63 < k0) continue;  // block above the diagonal chunk: zero
-                        const float4 lv = *reinterpret_cast<const float4 *>(Lc + kk * D + 64 * j + 4 * ag);
+                        if (128 * j + 127 < k0) continue;  // block above the diagonal chunk: zero
+                        const float4 lv = *reinterpret_cast<const float4 *>(Lc + kk * D + 128 * j + 4 * ag);
                         const float ll[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
                         for (int p = 0; p < 4; ++p)
@@ -121,18 +121,16 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
         for (int j = 0; j < J; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int col = 64 * j + 4 * ag + e;
+                const int col = 128 * j + 4 * ag + e;
                 if (col < d) {
 #pragma unroll
                     for (int p = 0; p < 4; ++p)
                         Ux[p] = fmaf(a.ws0[col], ex2_approx(fmaf(static_cast<float>(M), a.drift[col], acc[p][j][e])), Ux[p]);
                 }
             }
-        // sum over the 16 asset groups of each path (lanes with the same pg: a half warp)
+        // sum over the 32 asset groups of each path (the lanes of one warp)
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) Ux[p] += __shfl_xor_sync(0xffffffffu, Ux[p], o);
+        for (int p = 0; p < 4; ++p) Ux[p] = warp_sum(Ux[p]);
         if (ag == 0)
 #pragma unroll
             for (int p = 0; p < 4; ++p) s_u[4 * pg + p] = Ux[p];
@@ -162,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
             for (int j = 0; j < J; ++j)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int col = 64 * j + 4 * ag + e;
+                    const int col = 128 * j + 4 * ag + e;
                     float d1 = 0.f, d2 = 0.f, v1 = 0.f, v2 = 0.f;
                     if (col < d) {
 #pragma unroll
@@ -174,12 +172,8 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
                             d1 += dl; d2 += dl * dl; v1 += vg; v2 += vg * vg;
                         }
                     }
-                    // lanes l and l ^ 16 hold the same column for the two path groups of the warp
-                    d1 += __shfl_xor_sync(0xffffffffu, d1, 16);
-                    d2 += __shfl_xor_sync(0xffffffffu, d2, 16);
-                    v1 += __shfl_xor_sync(0xffffffffu, v1, 16);
-                    v2 += __shfl_xor_sync(0xffffffffu, v2, 16);
-                    if (lane < 16 && col < d) {
+                    // each lane holds its own columns: one atomic per (warp, column)
+                    if (col < d) {
                         atomicAdd(&s_g[col][0], d1);
                         atomicAdd(&s_g[col][1], d2);
                         atomicAdd(&s_g[d + col][0], v1);
