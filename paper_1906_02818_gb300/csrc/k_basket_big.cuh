@@ -7,12 +7,13 @@
 //
 // Warp roles (one CTA of 18 warps per SM; the accumulator takes all 512 TMEM
 // columns):
-//   warp 0   lane 0: TMA producer - streams the pre-swizzled 64 x 64 chunks
+//   warp 0   lane 0: TMA producer - streams the pre-swizzled 128 x 64 chunks
 //            of the quantised factor Lq (only chunks on or below the
 //            diagonal) into a ring of shared-memory slots;
 //   warp 1   lane 0: MMA issuer - for each 64-column panel p of Z and each
-//            64-row block b >= p of Lq: 4 (2 for E4M3) tcgen05.mma of
-//            128 x 64 x 16 (x32) into TMEM columns [64 b, 64 b + 64);
+//            128-row block b of Lq on or below the diagonal (p <= 2 b + 1):
+//            4 (2 for E4M3) tcgen05.mma of 128 x 128 x 16 (x32) into TMEM
+//            columns [128 b, 128 b + 128);
 //   warps 2..17: 512 threads; thread (warp w, lane l) owns path row
 //            32 (w mod 4) + l (its TMEM lane) and column group (w - 2) / 4;
 //            it draws 16 normals of every panel of its row per step
@@ -23,7 +24,8 @@
 //            pathwise delta / vega / rho contributions.
 // The Z tile is split in two halves of panels with their own full / free
 // mbarriers, so drawing half A of step i+1 overlaps the MMAs of half B of
-// step i.  Every mbarrier wait is bounded; on expiry the CTA records an error
+// step i; the split balances the MMA work of the halves (the factor is
+// triangular: early panels meet more row blocks).  Every mbarrier wait is bounded; on expiry the CTA records an error
 // word and stops issuing work (results become NaN).
 #pragma once
 
@@ -37,9 +39,11 @@ namespace gbmc {
 namespace tcbig {
 
 constexpr int kRows = 128;
-constexpr int kPanel = 64;
+constexpr int kPanel = 64;        // K columns per panel
+constexpr int kBlk = 128;         // factor rows per chunk = UMMA N
 constexpr int kMaxPanels = 8;
-constexpr int kRing = 6;          // factor-chunk slots
+constexpr int kMaxBlocks = 4;
+constexpr int kRing = 5;          // factor-chunk slots (80 KB in flight for BF16)
 constexpr int kThreads = 576;     // 18 warps
 constexpr int kWorkers = 512;     // warps 2..17
 
@@ -48,7 +52,7 @@ struct L2 {
     static constexpr int kElem = PREC == MC_FP8E4M3 ? 1 : 2;
     static constexpr int kRowBytes = kPanel * kElem;             // 128 or 64
     static constexpr int kPanelBytes = kRows * kRowBytes;        // Z panel
-    static constexpr int kChunkBytes = kPanel * kRowBytes;       // 64 x 64 factor chunk
+    static constexpr int kChunkBytes = kBlk * kRowBytes;         // 128 x 64 factor chunk
     static constexpr int kGroup = 8 * kRowBytes;                 // SBO
     static constexpr int kKStep = PREC == MC_FP8E4M3 ? 32 : 16;
     static constexpr int kMmas = kPanel / kKStep;
@@ -57,6 +61,7 @@ struct L2 {
     // [pad 1024] Z | ring | barriers (256 B) | accumulators
     static constexpr int kBarOff = kZBytes + kRing * kChunkBytes;
     static constexpr int kSmem = 1024 + kBarOff + 256;
+    static_assert(32 + 16 * kRing + 20 <= 256, "mbarrier words exceed their area");
     __device__ static __forceinline__ uint32_t off(int row, int chunk)
     {
         const int phys = PREC == MC_FP8E4M3 ? (chunk ^ ((row >> 1) & 3)) : (chunk ^ (row & 7));
@@ -92,23 +97,48 @@ __device__ __forceinline__ uint32_t pk4e(float a, float b, float c, float d)
     return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
 }
 
+// Chunk (b, p): factor rows 128 b .. 128 b + 127, columns 64 p .. 64 p + 63;
+// below or on the diagonal (possibly non-zero) iff p <= 2 b + 1.
+__host__ __device__ constexpr bool chunk_live(int b, int p) { return p <= 2 * b + 1; }
+
 __device__ __forceinline__ void named_sync_workers() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t addr)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
-}
+using tc::mbar_arrive;
+using tc::wait_or_fail;
 
-// Bounded wait that gives up at once when the CTA has already failed, and
-// records a failure when it runs out.  Loops never exit early on failure:
-// every thread keeps arriving where it would have arrived, so no barrier is
-// left short of arrivals; the remaining waits are skipped.
-__device__ __forceinline__ bool wait_or_fail(volatile unsigned int *fail, uint32_t addr, uint32_t parity, uint32_t cap)
+// One worker's 16 normals of a Z panel (columns c0 .. c0 + 15 of its path
+// row at step i), rounded to the operand type and stored swizzled.
+template <int PREC>
+__device__ __forceinline__ void draw_panel(uint32_t pan, int row, int grp, int c0, int i, int d, bool valid, uint64_t n,
+                                           int exact4, uint32_t k0, uint32_t k1, NormalReader &rd)
 {
-    if (*fail) return false;
-    if (tc::mbar_wait_bounded(addr, parity, cap)) return true;
-    *fail = 1u;
-    return false;
+    using Ly = L2<PREC>;
+    float z[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) z[l] = 0.0f;
+    if (valid && c0 < d) {
+        if (exact4 && c0 + 16 <= d) {
+            const uint64_t q = (static_cast<uint64_t>(i) * d + c0) >> 2;
+#pragma unroll
+            for (int bq = 0; bq < 4; ++bq) {
+                const float4 v = normals4(q + bq, n, k0, k1);
+                z[4 * bq] = v.x; z[4 * bq + 1] = v.y; z[4 * bq + 2] = v.z; z[4 * bq + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < 16; ++l)  // unrolled: z stays in registers
+                if (c0 + l < d) z[l] = rd.get(static_cast<uint64_t>(i) * d + c0 + l);
+        }
+    }
+    if (PREC == MC_FP8E4M3) {
+        stv4(pan + Ly::off(row, grp), pk4e(z[0], z[1], z[2], z[3]), pk4e(z[4], z[5], z[6], z[7]),
+             pk4e(z[8], z[9], z[10], z[11]), pk4e(z[12], z[13], z[14], z[15]));
+    } else {
+        stv4(pan + Ly::off(row, 2 * grp), pk2<PREC>(z[0], z[1]), pk2<PREC>(z[2], z[3]), pk2<PREC>(z[4], z[5]),
+             pk2<PREC>(z[6], z[7]));
+        stv4(pan + Ly::off(row, 2 * grp + 1), pk2<PREC>(z[8], z[9]), pk2<PREC>(z[10], z[11]), pk2<PREC>(z[12], z[13]),
+             pk2<PREC>(z[14], z[15]));
+    }
 }
 
 template <int PREC>
@@ -125,22 +155,31 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t zt = base, ring = base + Ly::kZBytes, bars = base + Ly::kBarOff;
-    // barrier words: zfull[2], zfree[2], lfull[R], lfree[R], ddone, dfree, tslot
+    // barrier words: zfull[2], zfree[2] (one pair per half of Z), lfull[R], lfree[R], ddone, dfree, tslot
     const uint32_t zfull = bars, zfree = bars + 16, lfull = bars + 32, lfree = lfull + 8 * kRing;
     const uint32_t ddone = lfree + 8 * kRing, dfree = ddone + 8, tslot = dfree + 8;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
 
-    const int d = a.d, NP = (d + kPanel - 1) / kPanel, half = (NP + 1) / 2;
+    const int d = a.d, NP = (d + kPanel - 1) / kPanel, NB = (NP + 1) / 2;
+    // Split of the Z panels into the two halves: the first half ends at the
+    // panel where the MMA chunks (NB - p / 2 for panel p) reach half the step's
+    // total, so each half's MMAs run while the workers draw the other half.
+    int half = 1;
+    {
+        int total = 0, cum = NB;
+        for (int p = 0; p < NP; ++p) total += NB - p / 2;
+        while (half < NP - 1 && 2 * cum < total) cum += NB - half++ / 2;
+    }
     const int M = a.run.steps;
     const int nv = a.pay.n;
     for (int i = t; i < nv * 2; i += kThreads) s_pay[i >> 1][i & 1] = 0.0f;
     for (int i = t; i < (2 * d + 1) * 2; i += kThreads) s_g[i >> 1][i & 1] = 0.0f;
     if (t == 0) {
         s_fail = 0;
-        tc::mbar_init(zfull, kWorkers);
-        tc::mbar_init(zfull + 8, kWorkers);
-        tc::mbar_init(zfree, 1);
-        tc::mbar_init(zfree + 8, 1);
+        for (int hh = 0; hh < 2; ++hh) {
+            tc::mbar_init(zfull + 8 * hh, kWorkers);
+            tc::mbar_init(zfree + 8 * hh, 1);
+        }
         for (int r = 0; r < kRing; ++r) {
             tc::mbar_init(lfull + 8 * r, 1);
             tc::mbar_init(lfree + 8 * r, 1);
@@ -163,51 +202,61 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            uint64_t c = 0;
+            uint32_t slot = 0, phase = 0, primed = 0;  // ring position; slots filled once
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
                 for (int i = 0; i < M; ++i)
                     for (int p = 0; p < NP; ++p)
-                        for (int b = p; b < NP; ++b, ++c) {
-                            const uint32_t slot = static_cast<uint32_t>(c % kRing);
-                            if (c >= kRing &&
-                                !wait_or_fail(&s_fail, lfree + 8 * slot, static_cast<uint32_t>((c / kRing - 1) & 1), cap))
-                                continue;
-                            if (s_fail) continue;
-                            tc::mbar_arrive_expect_tx(lfull + 8 * slot, Ly::kChunkBytes);
-                            tc::bulk_g2s(ring + slot * Ly::kChunkBytes,
-                                         a.bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes,
-                                         Ly::kChunkBytes, lfull + 8 * slot);
+                        for (int b = p / 2; b < NB; ++b) {
+                            const bool ok = primed < kRing ? (++primed, true)
+                                                           : wait_or_fail(&s_fail, lfree + 8 * slot, phase ^ 1u, cap);
+                            if (ok && !s_fail) {
+                                tc::mbar_arrive_expect_tx(lfull + 8 * slot, Ly::kChunkBytes);
+                                tc::bulk_g2s(ring + slot * Ly::kChunkBytes,
+                                             a.bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes,
+                                             Ly::kChunkBytes, lfull + 8 * slot);
+                            }
+                            if (++slot == kRing) {
+                                slot = 0;
+                                phase ^= 1u;
+                            }
                         }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = PREC == MC_FP8E4M3 ? tc::idesc_e4m3(kRows, kPanel)
-                                                      : tc::idesc_f16(kRows, kPanel, PREC == MC_BF16);
-            uint64_t c = 0, g = 0, tl = 0;
+            const uint32_t idesc = PREC == MC_FP8E4M3 ? tc::idesc_e4m3(kRows, kBlk)
+                                                      : tc::idesc_f16(kRows, kBlk, PREC == MC_BF16);
+            // descriptors change only in their 14-bit start-address field (address / 16)
+            const uint64_t adesc0 = tc::smem_desc(zt, Ly::kGroup, Ly::kSw);
+            const uint64_t bdesc0 = tc::smem_desc(ring, Ly::kGroup, Ly::kSw);
+            uint32_t slot = 0, phase = 0;
+            uint64_t g = 0, tl = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
                 if (tl > 0) wait_or_fail(&s_fail, dfree, static_cast<uint32_t>((tl - 1) & 1), cap);
                 for (int i = 0; i < M; ++i, ++g) {
                     for (int hh = 0; hh < 2; ++hh) {
-                        const int p0 = hh ? half : 0, p1 = hh ? NP : half;
                         const bool zok = wait_or_fail(&s_fail, zfull + 8 * hh, static_cast<uint32_t>(g & 1), cap);
                         tc::fence_after_sync();
-                        for (int p = p0; p < p1; ++p)
-                            for (int b = p; b < NP; ++b, ++c) {
-                                const uint32_t slot = static_cast<uint32_t>(c % kRing);
-                                if (!zok || !wait_or_fail(&s_fail, lfull + 8 * slot, static_cast<uint32_t>((c / kRing) & 1), cap))
-                                    continue;
-                                tc::fence_after_sync();
+                        for (int p = hh ? half : 0; p < (hh ? NP : half); ++p) {
+                            const uint64_t ap = adesc0 + static_cast<uint32_t>(p * (Ly::kPanelBytes >> 4));
+                            for (int b = p / 2; b < NB; ++b) {
+                                if (zok && wait_or_fail(&s_fail, lfull + 8 * slot, phase, cap)) {
+                                    tc::fence_after_sync();
+                                    const uint64_t bp = bdesc0 + slot * static_cast<uint32_t>(Ly::kChunkBytes >> 4);
 #pragma unroll
-                                for (int kk = 0; kk < Ly::kMmas; ++kk) {
-                                    const uint64_t ad = tc::smem_desc(zt + p * Ly::kPanelBytes + kk * 32, Ly::kGroup, Ly::kSw);
-                                    const uint64_t bd = tc::smem_desc(ring + slot * Ly::kChunkBytes + kk * 32, Ly::kGroup, Ly::kSw);
-                                    const uint32_t acc = (i == 0 && p == 0 && kk == 0) ? 0u : 1u;
-                                    if (PREC == MC_FP8E4M3) tc::mma_f8(tmem + b * kPanel, ad, bd, idesc, acc);
-                                    else tc::mma_f16(tmem + b * kPanel, ad, bd, idesc, acc);
+                                    for (int kk = 0; kk < Ly::kMmas; ++kk) {
+                                        const uint32_t acc = (i == 0 && p == 0 && kk == 0) ? 0u : 1u;
+                                        if (PREC == MC_FP8E4M3) tc::mma_f8(tmem + b * kBlk, ap + 2 * kk, bp + 2 * kk, idesc, acc);
+                                        else tc::mma_f16(tmem + b * kBlk, ap + 2 * kk, bp + 2 * kk, idesc, acc);
+                                    }
+                                    tc::mma_commit(lfree + 8 * slot);
                                 }
-                                tc::mma_commit(lfree + 8 * slot);
+                                if (++slot == kRing) {
+                                    slot = 0;
+                                    phase ^= 1u;
+                                }
                             }
+                        }
                         tc::mma_commit(zfree + 8 * hh);
                     }
                 }
@@ -227,39 +276,11 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
             rd.init(n, a.run.k0, a.run.k1);
             for (int i = 0; i < M; ++i, ++g) {
                 for (int hh = 0; hh < 2; ++hh) {
-                    const int p0 = hh ? half : 0, p1 = hh ? NP : half;
                     const bool ok = g == 0 || wait_or_fail(&s_fail, zfree + 8 * hh, static_cast<uint32_t>((g - 1) & 1), cap);
                     if (ok && !s_fail) {
-                        for (int p = p0; p < p1; ++p) {
-                            float z[16];
-                            const int c0 = p * kPanel + grp * 16;
-#pragma unroll
-                            for (int l = 0; l < 16; ++l) z[l] = 0.0f;
-                            if (valid && c0 < d) {
-                                if (a.exact4 && c0 + 16 <= d) {
-                                    const uint64_t q = (static_cast<uint64_t>(i) * d + c0) >> 2;
-#pragma unroll
-                                    for (int bq = 0; bq < 4; ++bq) {
-                                        const float4 v = normals4(q + bq, n, a.run.k0, a.run.k1);
-                                        z[4 * bq] = v.x; z[4 * bq + 1] = v.y; z[4 * bq + 2] = v.z; z[4 * bq + 3] = v.w;
-                                    }
-                                } else {
-#pragma unroll
-                                    for (int l = 0; l < 16; ++l)  // unrolled: z stays in registers
-                                        if (c0 + l < d) z[l] = rd.get(static_cast<uint64_t>(i) * d + c0 + l);
-                                }
-                            }
-                            const uint32_t pan = zt + p * Ly::kPanelBytes;
-                            if (PREC == MC_FP8E4M3) {
-                                stv4(pan + Ly::off(row, grp), pk4e(z[0], z[1], z[2], z[3]), pk4e(z[4], z[5], z[6], z[7]),
-                                     pk4e(z[8], z[9], z[10], z[11]), pk4e(z[12], z[13], z[14], z[15]));
-                            } else {
-                                stv4(pan + Ly::off(row, 2 * grp), pk2<PREC>(z[0], z[1]), pk2<PREC>(z[2], z[3]),
-                                     pk2<PREC>(z[4], z[5]), pk2<PREC>(z[6], z[7]));
-                                stv4(pan + Ly::off(row, 2 * grp + 1), pk2<PREC>(z[8], z[9]), pk2<PREC>(z[10], z[11]),
-                                     pk2<PREC>(z[12], z[13]), pk2<PREC>(z[14], z[15]));
-                            }
-                        }
+                        for (int p = hh ? half : 0; p < (hh ? NP : half); ++p)
+                            draw_panel<PREC>(zt + p * Ly::kPanelBytes, row, grp, p * kPanel + grp * 16, i, d, valid, n,
+                                             a.exact4, a.run.k0, a.run.k1, rd);
                         tc::fence_proxy_async();
                     }
                     mbar_arrive(zfull + 8 * hh);  // always: the MMA issuer counts 512 arrivals
@@ -384,23 +405,24 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
     if (t == 0) *a.ticket = 0u;
 }
 
-// Factor chunks (b, p) (64 x 64, rows 64 b.., columns 64 p..) of Lq = s_n Lrho,
-// each pre-swizzled for the MMA's B operand, at (b * 8 + p) * chunk bytes;
-// plus the per-column epilogue constants.
+// Factor chunks (b, p) (128 x 64: rows 128 b.., columns 64 p..) of
+// Lq = s_n Lrho, each pre-swizzled for the MMA's B operand, at
+// (b * 8 + p) * chunk bytes (only chunks with p <= 2 b + 1 are written and
+// loaded); plus the per-column epilogue constants.
 template <int PREC>
 __global__ void big_prep_kernel(int d, const double *L, const double *sigma, double cfac, double sdt, double r,
                                 double dt, int M, uint8_t *bimg, float *cs, float *mdrift, float *vscale)
 {
     using Ly = L2<PREC>;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= kMaxPanels * kPanel) return;
+    if (n >= kMaxBlocks * kBlk) return;
     double amax = 0.0;
     for (int k = 0; k <= n && k < d; ++k) amax = fmax(amax, fabs(n < d ? L[static_cast<int64_t>(n) * d + k] : 0.0));
     const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : 1.0;
-    const int b = n / kPanel, rb = n % kPanel;
+    const int b = n / kBlk, rb = n % kBlk;
     for (int k = 0; k < kMaxPanels * kPanel; ++k) {
         const int p = k / kPanel, kc = k % kPanel;
-        if (p > b) continue;  // chunks above the diagonal block are never loaded
+        if (!chunk_live(b, p)) continue;
         const double v = (n < d && k <= n && k < d) ? L[static_cast<int64_t>(n) * d + k] * s : 0.0;
         const float fv = static_cast<float>(v);
         uint8_t *chunk = bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes;
@@ -439,7 +461,7 @@ template <int PREC>
 cudaError_t big_prep(int d, const double *L, const double *sigma, double cfac, double sdt, double r, double dt, int M,
                      uint8_t *bimg, float *cs, float *mdrift, float *vscale, cudaStream_t s)
 {
-    tcbig::big_prep_kernel<PREC><<<(tcbig::kMaxPanels * tcbig::kPanel + 127) / 128, 128, 0, s>>>(
+    tcbig::big_prep_kernel<PREC><<<(tcbig::kMaxBlocks * tcbig::kBlk + 127) / 128, 128, 0, s>>>(
         d, L, sigma, cfac, sdt, r, dt, M, bimg, cs, mdrift, vscale);
     return cudaGetLastError();
 }

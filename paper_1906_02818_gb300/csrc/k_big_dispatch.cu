@@ -38,7 +38,8 @@ const void *select(int prec, int d, int *smem, int *threads)
 
 }  // namespace
 
-size_t big_bimg_bytes(int prec) { return static_cast<size_t>(64) * (prec == MC_FP8E4M3 ? 4096 : 8192); }
+// 4 row blocks x 8 panels of 128 x 64 operand chunks
+size_t big_bimg_bytes(int prec) { return static_cast<size_t>(32) * (prec == MC_FP8E4M3 ? 8192 : 16384); }
 
 cudaError_t launch_basket_big(int prec, const BigArgs &a, int grid, cudaStream_t s)
 {

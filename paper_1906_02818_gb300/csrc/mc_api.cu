@@ -146,18 +146,6 @@ void size_grid(int64_t paths, int block, int resident, int *grid, int *ppt)
     *ppt = static_cast<int>(p);
 }
 
-// Polls of a bounded mbarrier wait before a kernel gives up (GBMC_WAIT_CAP
-// overrides; each poll suspends for at most a few microseconds).
-uint32_t wait_cap()
-{
-    const char *e = std::getenv("GBMC_WAIT_CAP");
-    if (e && *e) {
-        const long v = std::strtol(e, nullptr, 10);
-        if (v > 0) return static_cast<uint32_t>(v);
-    }
-    return 1u << 22;
-}
-
 template <class T>
 void dfree(T *&p)
 {
@@ -166,6 +154,18 @@ void dfree(T *&p)
 }
 
 }  // namespace
+
+// Polls of a bounded mbarrier wait before a kernel gives up (GBMC_WAIT_CAP
+// overrides; each poll suspends for at most a few microseconds).
+uint32_t gbmc::mbar_wait_cap()
+{
+    const char *e = std::getenv("GBMC_WAIT_CAP");
+    if (e && *e) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v > 0) return static_cast<uint32_t>(v);
+    }
+    return 1u << 22;
+}
 
 int gbmc::set_last_error(int code, const char *msg)
 {
@@ -284,7 +284,7 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
     b.pay = ps;
     b.err = P->err;
     b.disc = std::exp(-m->r * c->T);
-    b.wait_cap = wait_cap();
+    b.wait_cap = mbar_wait_cap();
     P->grid = basket_big_grid(P->prec, c->paths);
     if (P->grid <= 0) return fail(MC_ECUDA, "large-basket kernel cannot be resident");
     const int nvals = ps.n + (greeks ? 2 * d + 1 : 0);
@@ -431,7 +431,7 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             ta.red = red;
             ta.red.err = P->err;
             ta.err = P->err;
-            ta.wait_cap = wait_cap();
+            ta.wait_cap = mbar_wait_cap();
             P->block = 128;
             resident = basket_tc_occupancy(P->prec, ta) * di.sms;
         } else {

@@ -134,6 +134,8 @@ int greeks_block();
 
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
+// Polls of a bounded mbarrier wait before a tensor-core kernel gives up.
+uint32_t mbar_wait_cap();
 
 // Host launchers (return cudaError_t of the launch).
 cudaError_t launch_gbm1d(const Gbm1dArgs &a, int grid, int block, cudaStream_t s);

@@ -19,11 +19,17 @@ struct mc_mlp {
     size_t work_floats = 0;
     double *partial = nullptr;
     int step = 0;
+    // bf16 operand image of the weights, rebuilt when the parameters change
+    uint8_t *img = nullptr;
+    uint64_t version = 1, img_version = 0;
+    unsigned int *err = nullptr;  // set by the bf16 kernel when a bounded wait expires
     ~mc_mlp()
     {
         for (float *p : {params, grad, m, v, work})
             if (p) cudaFree(p);
         if (partial) cudaFree(partial);
+        if (img) cudaFree(img);
+        if (err) cudaFree(err);
     }
 };
 
@@ -71,6 +77,18 @@ int mlp_forward_any(mc_mlp *net, const float *x, int64_t n, float *y, int precis
 {
     return mc_mlp_forward(net, x, n, y, precision, s);
 }
+
+// Reads and clears the bf16 kernel's time-out word (synchronises `s`).
+int mlp_check_timeout(mc_mlp *net, cudaStream_t s)
+{
+    if (!net->err) return MC_OK;
+    unsigned int e = 0;
+    MLP_CUDA(cudaMemcpyAsync(&e, net->err, sizeof e, cudaMemcpyDeviceToHost, s));
+    MLP_CUDA(cudaStreamSynchronize(s));
+    if (!e) return MC_OK;
+    MLP_CUDA(cudaMemsetAsync(net->err, 0, sizeof(unsigned int), s));
+    return set_last_error(MC_ETIMEOUT, "a bounded wait of the bf16 network kernel expired (outputs are NaN)");
+}
 }  // namespace gbmc
 
 extern "C" {
@@ -116,6 +134,7 @@ int mc_mlp_set_params(mc_mlp *net, const float *host)
     if ((rc = check_net(net))) return rc;
     if (!host) return set_last_error(MC_EINVAL, "host is NULL");
     MLP_CUDA(cudaMemcpy(net->params, host, net->L.count * sizeof(float), cudaMemcpyHostToDevice));
+    ++net->version;
     net->step = 0;
     MLP_CUDA(cudaMemset(net->m, 0, net->L.count * sizeof(float)));
     MLP_CUDA(cudaMemset(net->v, 0, net->L.count * sizeof(float)));
@@ -128,7 +147,23 @@ int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int
     if ((rc = check_net(net))) return rc;
     if (!dev_x || !dev_y || n < 1) return set_last_error(MC_EINVAL, "x, y must be set and n >= 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (precision != MC_FP32) return set_last_error(MC_EUNSUPPORTED, "this build evaluates the network in FP32 here");
+    if (precision == MC_BF16) {
+        if (!mlp_bf16_supported(net->L))
+            return set_last_error(MC_EUNSUPPORTED, "bf16 inference needs n_in <= 10 and equal hidden widths, a "
+                                                   "multiple of 32 up to 256");
+        if (!net->img) MLP_CUDA(cudaMalloc(&net->img, mlp_bf16_image_bytes(net->L)));
+        if (!net->err) {
+            MLP_CUDA(cudaMalloc(&net->err, sizeof(unsigned int)));
+            MLP_CUDA(cudaMemset(net->err, 0, sizeof(unsigned int)));
+        }
+        if (net->img_version != net->version) {
+            MLP_CUDA(mlp_bf16_prepare(net->L, net->params, net->img, s));
+            net->img_version = net->version;
+        }
+        MLP_CUDA(mlp_forward_bf16(net->L, net->params, net->img, dev_x, n, dev_y, net->err, mbar_wait_cap(), s));
+        return MC_OK;
+    }
+    if (precision != MC_FP32) return set_last_error(MC_EUNSUPPORTED, "precision: MC_FP32 or MC_BF16");
     int maxw = 0;
     for (int v : net->L.sizes) maxw = v > maxw ? v : maxw;
     if ((rc = ensure_work(net, 2 * static_cast<size_t>(n) * maxw))) return rc;
@@ -167,6 +202,7 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
     const int64_t B = batch < n ? batch : n;
     if ((rc = ensure_work(net, mlp_train_floats(net->L, B)))) return rc;
     const int n_in = net->L.sizes[0];
+    ++net->version;
     std::vector<double> part(kPartials);
     double epoch_loss = 0.0;
     for (int ep = 0; ep < epochs; ++ep) {

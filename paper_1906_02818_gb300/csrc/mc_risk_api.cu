@@ -20,6 +20,7 @@ struct mc_mlp;
 namespace gbmc {
 const MlpLayout &mlp_layout_of(const mc_mlp *net);
 int mlp_forward_any(mc_mlp *net, const float *x, int64_t n, float *y, int precision, cudaStream_t s);
+int mlp_check_timeout(mc_mlp *net, cudaStream_t s);
 }  // namespace gbmc
 
 namespace {
@@ -230,6 +231,10 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
     RK_CUDA(cudaMemcpyAsync(base.data(), d_base, no * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (host_pnl) RK_CUDA(cudaMemcpyAsync(host_pnl, d_pnl, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
     RK_CUDA(cudaStreamSynchronize(s));
+    if (cf->method == MC_RISK_SURROGATE && cf->surrogate_precision == MC_BF16) {
+        const int rc = mlp_check_timeout(cf->surrogate, s);
+        if (rc) return rc;
+    }
     res->var = r3[0];
     res->cvar = r3[1];
     res->n_tail = static_cast<int64_t>(r3[2]);

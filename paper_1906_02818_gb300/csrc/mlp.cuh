@@ -27,6 +27,16 @@ cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const floa
 cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
                           float *acts, float *grad, double *partial, int npartial, cudaStream_t s);
 size_t mlp_train_floats(const MlpLayout &L, int64_t n);
+// BF16 tensor-core inference (k_mlp_tc.cu): hidden widths equal, a multiple
+// of 32 and at most 256, n_in <= 10, scalar output.
+bool mlp_bf16_supported(const MlpLayout &L);
+size_t mlp_bf16_image_bytes(const MlpLayout &L);
+// Rounds the weights into the pre-swizzled bf16 operand image (device).
+cudaError_t mlp_bf16_prepare(const MlpLayout &L, const float *params, uint8_t *img, cudaStream_t s);
+// y[n] = net(x) with bf16 operands and FP32 accumulation; *err is set to 1
+// (and the affected rows to NaN) if a bounded wait of the kernel expires.
+cudaError_t mlp_forward_bf16(const MlpLayout &L, const float *params, const uint8_t *img, const float *x, int64_t n,
+                             float *y, unsigned int *err, uint32_t cap, cudaStream_t s);
 cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
 
 }  // namespace gbmc

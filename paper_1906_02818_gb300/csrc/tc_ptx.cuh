@@ -46,6 +46,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// Bounded wait that gives up at once when the CTA has already failed, and
+// records a failure when it runs out.  Loops never exit early on failure:
+// every thread keeps arriving where it would have arrived, so no barrier is
+// left short of arrivals; the remaining waits are skipped.
+__device__ __forceinline__ bool wait_or_fail(volatile unsigned int *fail, uint32_t addr, uint32_t parity, uint32_t cap)
+{
+    if (*fail) return false;
+    if (mbar_wait_bounded(addr, parity, cap)) return true;
+    *fail = 1u;
+    return false;
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t addr, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");

@@ -78,3 +78,98 @@ def test_training_reduces_loss(gb):
     l1 = net.train(xd, td, epochs=20, batch=1024, lr=1e-3)
     assert l1 < 0.05 * l0, (l0, l1)
     net.close()
+
+
+# ----------------------------- BF16 inference ------------------------------
+
+def _bf16_emulation(P, x):
+    """The bf16 kernel's arithmetic in FP64: layer 0 as x_hi W_hi + x_lo W_hi
+    + x_hi W_lo (hi = bf16 rounding, lo = bf16 of the FP32 remainder), every
+    hidden operand rounded to bf16 after the SiLU, the last hidden layer's
+    SiLU and the output layer unrounded."""
+    from quant import to_bf16
+    (W0, b0), hid, (Wo, bo) = P[0], P[1:-1], P[-1]
+    x32 = np.asarray(x, dtype=np.float32)
+    xh = to_bf16(x32)
+    xl = to_bf16((x32 - xh.astype(np.float32)).astype(np.float32))
+    w32 = W0.astype(np.float32)
+    wh = to_bf16(w32)
+    wl = to_bf16((w32 - wh.astype(np.float32)).astype(np.float32))
+    z = xh @ wh + xl @ wh + xh @ wl + b0
+    for W, b in hid:
+        z = to_bf16(omlp.silu(z)) @ to_bf16(W) + b
+    return (omlp.silu(z) @ Wo + bo)[:, 0]
+
+
+def _bf16_case(gb, n_in, width, hidden, n, seed):
+    import torch
+    sizes = omlp.layer_sizes(n_in, width, hidden)
+    rng = np.random.default_rng(seed)
+    P = [(rng.normal(0, np.sqrt(2.0 / i), size=(i, o)), rng.normal(0, 0.1, size=o)) for i, o in zip(sizes, sizes[1:])]
+    flat = omlp.pack(P).astype(np.float32)
+    P = omlp.unpack(flat.astype(np.float64), sizes)
+    net = gb.Mlp(n_in, width, hidden, flat)
+    x = rng.uniform(-1.5, 1.5, size=(n, n_in)).astype(np.float32)
+    y = net.forward(torch.from_numpy(x).cuda(), precision="bf16").cpu().numpy()
+    net.close()
+    return y, _bf16_emulation(P, x.astype(np.float64)), omlp.forward(P, x.astype(np.float64))[0]
+
+
+@pytest.mark.parametrize("n", [1, 100, 128, 129, 384, 1000, 100003])
+def test_forward_bf16_matches_emulation(gb, n):
+    """Surrogate shape (5 -> 256 x 4 -> 1): ragged tile counts, one or two
+    tiles per CTA pair, many pairs per CTA."""
+    y, emu, exact = _bf16_case(gb, 5, 256, 4, n, seed=n)
+    assert np.all(np.isfinite(y))
+    scale = np.max(np.abs(exact)) + 1e-3
+    e_emu = np.max(np.abs(y - emu)) / scale
+    r_emu = np.sqrt(np.mean((y - emu) ** 2)) / scale
+    e_ex = np.max(np.abs(y - exact)) / scale
+    print(f"n={n}: |bf16 - emulation| max {e_emu:.2e} rms {r_emu:.2e}, |bf16 - fp64| max {e_ex:.2e} of max|y|")
+    # The emulation differs from the kernel by tanh.approx in the SiLU (relative
+    # 2^-11) and FP32 accumulation; each moves some activations across a bf16
+    # rounding boundary (one bf16 ulp, 2^-8 relative, each), which the next
+    # layers carry to the output: a few 1e-3 of max|y| at worst, far less on
+    # average.  Against unrounded FP64, bf16 operands in three 256-wide layers.
+    assert e_emu <= 6e-3 and r_emu <= 1e-3
+    assert e_ex <= 3e-2
+
+
+@pytest.mark.parametrize("n_in,width,hidden", [(1, 32, 1), (10, 64, 2), (3, 96, 3), (5, 128, 5), (8, 256, 2)])
+def test_forward_bf16_shapes(gb, n_in, width, hidden):
+    y, emu, exact = _bf16_case(gb, n_in, width, hidden, 777, seed=width + hidden)
+    scale = np.max(np.abs(exact)) + 1e-3
+    print(f"{n_in}->{width}x{hidden}: {np.max(np.abs(y - emu)) / scale:.2e} vs emulation, "
+          f"{np.max(np.abs(y - exact)) / scale:.2e} vs fp64")
+    assert np.max(np.abs(y - emu)) <= 6e-3 * scale
+    assert np.max(np.abs(y - exact)) <= 3e-2 * scale
+
+
+def test_forward_bf16_tracks_parameter_updates(gb):
+    """The bf16 operand image is rebuilt after set_params and training."""
+    import torch
+    init = workloads.mlp_init(seed=3)
+    net = gb.Mlp(5, 256, 4, init)
+    x, t = _data(4096, seed=5)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y0 = net.forward(xd, precision="bf16").cpu().numpy()
+    net.train(xd, td, epochs=2, batch=1024, lr=1e-3)
+    y1 = net.forward(xd, precision="bf16").cpu().numpy()
+    f1 = net.forward(xd).cpu().numpy()
+    assert np.max(np.abs(y1 - y0)) > 1e-3
+    assert np.max(np.abs(y1 - f1)) <= 3e-2 * np.max(np.abs(f1))
+    net.set_params(init)
+    assert np.array_equal(net.forward(xd, precision="bf16").cpu().numpy(), y0)
+    net.close()
+
+
+def test_forward_bf16_rejects_unsupported_shapes(gb):
+    import torch
+    from paper_1906_02818_gb300.native import MCError
+    for n_in, width, hidden in [(5, 48, 2), (11, 64, 2), (5, 320, 2)]:
+        sizes = omlp.layer_sizes(n_in, width, hidden)
+        flat = np.zeros(sum(i * o + o for i, o in zip(sizes, sizes[1:])), dtype=np.float32)
+        net = gb.Mlp(n_in, width, hidden, flat)
+        with pytest.raises(MCError, match="bf16"):
+            net.forward(torch.zeros((4, n_in), device="cuda"), precision="bf16")
+        net.close()
