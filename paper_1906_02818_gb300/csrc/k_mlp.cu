@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
     __shared__ float As[kK][kT + 4];
     __shared__ float Bs[kK][kT + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.y * kT, n0 = blockIdx.x * kT;
+    const int m0 = blockIdx.x * kT, n0 = blockIdx.y * kT;  // row tiles on x: up to 2^31 - 1 blocks
     float acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += kK) {
 #pragma unroll
@@ -158,7 +158,7 @@ template <bool TA, bool TB>
 cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, const float *bias, float *Z,
                  float *H, int ldc, int act, cudaStream_t s)
 {
-    dim3 grid((N + kT - 1) / kT, (M + kT - 1) / kT);
+    dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT);
     gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act);
     return cudaGetLastError();
 }
@@ -184,20 +184,24 @@ MlpLayout::MlpLayout(int n_in, int width, int hidden)
 cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const float *x, int64_t n, float *work,
                              float *y, cudaStream_t s)
 {
-    // work: activations ping-pong, 2 x n x max width
+    // work: activations ping-pong, 2 x min(n, 2^20) x max width; rows in slices of 2^20
     int maxw = 0;
     for (int v : L.sizes) maxw = v > maxw ? v : maxw;
-    const float *h = x;
-    float *buf[2] = {work, work + n * maxw};
     const int nl = static_cast<int>(L.sizes.size()) - 1;
-    for (int l = 0; l < nl; ++l) {
-        const bool last = l == nl - 1;
-        float *out = last ? y : buf[l & 1];
-        cudaError_t e = gemm<false, false>(static_cast<int>(n), L.sizes[l + 1], L.sizes[l], h, L.sizes[l],
-                                           params + L.w_off[l], L.sizes[l + 1], params + L.b_off[l], nullptr, out,
-                                           L.sizes[l + 1], last ? 0 : 1, s);
-        if (e != cudaSuccess) return e;
-        h = out;
+    constexpr int64_t kSlice = kMlpForwardSlice;
+    for (int64_t r0 = 0; r0 < n; r0 += kSlice) {
+        const int rows = static_cast<int>(n - r0 < kSlice ? n - r0 : kSlice);
+        const float *h = x + r0 * L.sizes[0];
+        float *buf[2] = {work, work + static_cast<int64_t>(rows) * maxw};
+        for (int l = 0; l < nl; ++l) {
+            const bool last = l == nl - 1;
+            float *out = last ? y + r0 : buf[l & 1];
+            cudaError_t e = gemm<false, false>(rows, L.sizes[l + 1], L.sizes[l], h, L.sizes[l], params + L.w_off[l],
+                                               L.sizes[l + 1], params + L.b_off[l], nullptr, out, L.sizes[l + 1],
+                                               last ? 0 : 1, s);
+            if (e != cudaSuccess) return e;
+            h = out;
+        }
     }
     return cudaSuccess;
 }

@@ -166,7 +166,7 @@ int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int
     if (precision != MC_FP32) return set_last_error(MC_EUNSUPPORTED, "precision: MC_FP32 or MC_BF16");
     int maxw = 0;
     for (int v : net->L.sizes) maxw = v > maxw ? v : maxw;
-    if ((rc = ensure_work(net, 2 * static_cast<size_t>(n) * maxw))) return rc;
+    if ((rc = ensure_work(net, 2 * static_cast<size_t>(n < kMlpForwardSlice ? n : kMlpForwardSlice) * maxw))) return rc;
     MLP_CUDA(mlp_forward_fp32(net->L, net->params, dev_x, n, net->work, dev_y, s));
     return MC_OK;
 }

@@ -19,7 +19,9 @@ struct MlpLayout {
     MlpLayout(int n_in, int width, int hidden);
 };
 
-// y[n] = net(x[n x n_in]) in FP32; work holds 2 n max_width floats.
+// y[n] = net(x[n x n_in]) in FP32, in row slices of kMlpForwardSlice; work
+// holds 2 min(n, kMlpForwardSlice) max_width floats.
+constexpr int64_t kMlpForwardSlice = int64_t(1) << 20;
 cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const float *x, int64_t n, float *work,
                              float *y, cudaStream_t s);
 // Loss partials (npartial doubles, sum / n = MSE) and the packed gradient of

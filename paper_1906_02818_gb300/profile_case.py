@@ -1,8 +1,13 @@
-"""Run one workload's plan a fixed number of times (for profilers).
+"""Run one workload a fixed number of times (for profilers).
 
   python -m paper_1906_02818_gb300.profile_case basket64 --paths 16384 --reps 2 [--prec fp32]
   python -m paper_1906_02818_gb300.profile_case gbm1d --paths 1048576
   python -m paper_1906_02818_gb300.profile_case heston --paths 65536
+  python -m paper_1906_02818_gb300.profile_case basket512 --paths 32768 --prec bf16
+  python -m paper_1906_02818_gb300.profile_case heston_greeks --paths 65536
+  python -m paper_1906_02818_gb300.profile_case mlp --paths 1048576 --prec bf16   (paths = network rows)
+  python -m paper_1906_02818_gb300.profile_case labels --paths 4096              (paths = label points)
+  python -m paper_1906_02818_gb300.profile_case risk_nested --paths 256          (paths = scenarios)
 """
 from __future__ import annotations
 
@@ -20,12 +25,16 @@ def main():
     import paper_1906_02818_gb300 as gb
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston"])
+    ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
+                                     "risk_nested"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case == "heston":
+    if a.case in ("mlp", "labels", "risk_nested"):
+        _other(a, torch, workloads, gb)
+        return
+    if a.case in ("heston", "heston_greeks"):
         w = workloads.heston(paths=a.paths or (1 << 16))
         model = dict(kind="heston", **w["model"])
     else:
@@ -34,11 +43,39 @@ def main():
             w["paths"] = a.paths
         model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], corr=w.get("corr"), weights=w.get("weights"), r=w["r"])
     cfg = dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=w["seed"], precision=a.prec)
+    if a.case == "heston_greeks":
+        for _ in range(a.reps):
+            _, g = gb.greeks(model, cfg, w["payoffs"])
+        print(a.case, w["paths"], g[0, :, 0].tolist())
+        return
     with gb.Plan(model, cfg, w["payoffs"]) as plan:
         for _ in range(a.reps):
             out = plan.execute()
         torch.cuda.synchronize()
         print(a.case, w["paths"], out.cpu().numpy().tolist())
+
+
+def _other(a, torch, workloads, gb):
+    if a.case == "mlp":
+        n = a.paths or (1 << 20)
+        net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+        x = torch.rand((n, 5), device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 2 - 1
+        for _ in range(a.reps):
+            y = net.forward(x, precision=a.prec)
+        torch.cuda.synchronize()
+        print(a.case, n, a.prec, float(y.sum()))
+        net.close()
+    elif a.case == "labels":
+        pts = torch.from_numpy(workloads.surrogate_points(a.paths or 4096)).cuda()
+        for _ in range(a.reps):
+            lab = gb.surrogate_labels(pts, 1 << 13)
+        torch.cuda.synchronize()
+        print(a.case, pts.shape[0], float(lab.sum()))
+    else:
+        pf = workloads.risk_portfolio()
+        for _ in range(a.reps):
+            r = gb.risk(pf, n_scen=a.paths or 256, method="nested", inner_paths=1 << 12, base_paths=1 << 16)
+        print(a.case, r["var"], r["cvar"])
 
 
 if __name__ == "__main__":
