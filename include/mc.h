@@ -80,6 +80,19 @@ typedef struct {
                                          d<W1, W2> = rho dt, |rho| < 1 */
 } mc_model;
 
+/* Barrier monitoring.  MC_DISCRETE: the barrier is checked at t_1..t_M.
+ * MC_BRIDGE: continuous monitoring through the maximum (minimum) of the
+ * Brownian bridge between consecutive grid values x, y of log S (Sec. VI.A.1,
+ * the "In and Out Put" experiment): m = (x + y + sqrt((x - y)^2 - 2 dt
+ * sigma^2 ln U)) / 2 (minimum: minus the root), U uniform on (0, 1).  Single
+ * asset GBM with MC_LOG_EULER only (MC_EUNSUPPORTED otherwise); the uniforms
+ * are numbers 2i (maximum) and 2i + 1 (minimum) of stream 2^56 + n, the bridge
+ * domain of path n, step i, mapped by the same uniform map as the normals. */
+typedef enum {
+    MC_DISCRETE = 0,
+    MC_BRIDGE = 1
+} mc_monitoring;
+
 typedef struct {
     int32_t scheme;        /* mc_scheme (MC_GBM); MC_HESTON always uses full-truncation Euler */
     int32_t steps;         /* M >= 1 equal steps of dt = T / M */
@@ -89,6 +102,7 @@ typedef struct {
     uint64_t seed;         /* Philox key */
     int32_t precision;     /* mc_precision of the correlation contraction */
     int32_t ckpt_every;    /* adjoint checkpoint stride in steps (0 = 32) */
+    int32_t monitoring;    /* mc_monitoring of the barrier payoffs */
 } mc_sim_cfg;
 
 /* Payoffs on the monitored underlying U(t) = sum_a w_a S_a(t) (U = S for d = 1),
@@ -169,6 +183,32 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
               mc_result *prices, mc_result *greeks, void *stream);
 
 /*
+ * mc_price_mlmc -- two-level precision estimator (Sec. V: a fast reduced-
+ * precision simulation whose bias is identified with few samples and
+ * corrected; Giles' multilevel Monte Carlo over precisions):
+ *   price = mean_{N0}(P_q) + mean_{N1}(P_fp32 - P_q),
+ * level 0 = the tensor-core kernel with cfg->precision (BF16, FP16 or E4M3)
+ * on paths [path_offset, path_offset + cfg->paths); level 1 = paths_ref
+ * further paths [path_offset + cfg->paths, ... + paths_ref), each simulated
+ * twice on the same normals: the FP32 contraction, and the tensor-core
+ * operand rounding with FP32 accumulation.  The two levels use disjoint
+ * paths, so se^2 = se_0^2 + se_1^2.
+ *   Correlated GBM baskets with 2 <= d <= 64, discrete monitoring;
+ *   1 <= n_payoff <= 10; paths_ref >= 2.  out: host [n_payoff].
+ * Synchronises `stream`.
+ */
+typedef struct {
+    double price, se;         /* the two-level estimate of the FP32 price */
+    mc_result coarse;         /* level 0: reduced precision, cfg->paths paths */
+    mc_result correction;     /* level 1: mean of P_fp32 - P_q, paths_ref paths */
+    mc_result ref_level;      /* level 1's P_fp32 alone */
+    mc_result coarse_level;   /* level 1's P_q alone */
+} mc_mlmc_result;
+int mc_price_mlmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+                  int64_t paths_ref, mc_mlmc_result *out, void *stream);
+
+/*
+ * Surrogate pricing network (mc_mlp)/*
  * Surrogate pricing network (mc_mlp): n_in -> width x hidden (SiLU) -> 1
  * (linear), the network that revalues the risk portfolio.  Parameters are
  * one packed FP32 vector: for each layer l, W_l [in x out] row-major, then

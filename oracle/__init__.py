@@ -15,8 +15,9 @@ Contents
              Philox4x32-10 (Sec. IV.A), Box-Muller (Sec. VI.D), Cholesky
              (Sec. II.A.3), correlated GBM Euler / log-Euler steps (Sec. II.A.1,
              II.A.2), Heston full-truncation Euler, European / Asian / barrier
-             payoffs (Sec. I.A.2), forward-mode pathwise Greeks (Sec. I.A.3),
-             the estimator of Eq. 3 with its standard error.
+             payoffs (Sec. I.A.2), continuous barrier monitoring through the
+             Brownian-bridge extremes (Sec. VI.A.1), forward-mode pathwise
+             Greeks (Sec. I.A.3), the estimator of Eq. 3 with its standard error.
   mlp.py     FP64 numpy forward / backward of the pricing surrogate.
   risk.py    VaR / CVaR of Sec. VI.B and nested revaluation.
 
@@ -27,7 +28,9 @@ martingale and put-call parity; discrete geometric-Asian closed form and the
 AM >= GM invariant; one-step barrier closed form and in + out = vanilla;
 Cholesky against numpy; d = 1 basket = scalar GBM; geometric-basket closed
 form; Heston xi = 0 reduction to Black-Scholes; Greeks against Black-Scholes
-closed forms and common-random-number finite differences.
+closed forms and common-random-number finite differences; the Brownian-bridge
+barrier against the paper's "In and Out Put" value 23.1371783926 and the
+continuous down-and-in call closed form, at one step and at many.
 """
 from __future__ import annotations
 
@@ -91,6 +94,8 @@ def _load():
     lib.orc_gbm_paths.restype = i32
     lib.orc_gbm_greeks.argtypes = gbm_common + [i32, i_p, d_p, d_p]
     lib.orc_gbm_greeks.restype = i32
+    lib.orc_gbm1d_bridge_payoffs.argtypes = [dbl] * 5 + [i32, u64, i64, i64, i32, i_p, d_p, d_p, d_p]
+    lib.orc_gbm1d_bridge_payoffs.restype = i32
     hes_common = [dbl] * 8 + [i32, u64, i64, i64]
     lib.orc_heston_payoffs.argtypes = hes_common + [i32, i_p, d_p, d_p, d_p]
     lib.orc_heston_payoffs.restype = i32
@@ -196,6 +201,20 @@ def gbm_payoffs(s0, sigma, r, T, steps, paths, payoffs, corr=None, weights=None,
                                  0 if scheme == "log_euler" else 1, seed, path_offset, paths,
                                  len(payoffs), ip, _dptr(K), _dptr(H), _dptr(out))
     _check(rc, "orc_gbm_payoffs")
+    return out
+
+
+def gbm1d_bridge_payoffs(s0, sigma, r, T, steps, paths, payoffs, weight=1.0, seed=42, path_offset=0) -> np.ndarray:
+    """Discounted per-path payoffs of a single-asset GBM whose barriers are
+    monitored continuously through the Brownian-bridge extremes (Sec. VI.A.1),
+    shape [len(payoffs), paths]."""
+    kinds, K, H = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), paths), dtype=np.float64)
+    rc = _load().orc_gbm1d_bridge_payoffs(float(s0), float(sigma), float(weight), float(r), float(T), int(steps),
+                                          seed, path_offset, paths, len(payoffs),
+                                          kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(K), _dptr(H),
+                                          _dptr(out))
+    _check(rc, "orc_gbm1d_bridge_payoffs")
     return out
 
 

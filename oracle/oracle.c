@@ -339,6 +339,64 @@ int orc_gbm_payoffs(int d, const double *s0, const double *sig, const double *co
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Single-asset GBM with continuously monitored barriers through the         */
+/* Brownian bridge (Sec. VI.A.1, the "In and Out Put" experiment).  log-Euler */
+/* on x = log S (exact in law at the grid); between consecutive grid values   */
+/* x = x_i and y = x_{i+1} the maximum of the bridge of log S is drawn as     */
+/*   m_i = (x + y + sqrt((x - y)^2 - 2 dt sig^2 ln U_i)) / 2                 */
+/* and the minimum as (x + y - sqrt((x - y)^2 - 2 dt sig^2 ln V_i)) / 2; the  */
+/* path's maximum (minimum) over [0, T] is the largest m_i (smallest).        */
+/* U_i, V_i: uniforms 2i and 2i + 1 of stream 2^56 + n (the bridge domain of  */
+/* path n), from the same Philox blocks and uniform map as the normals.       */
+/* The monitored underlying is U = w S.                                       */
+/* ------------------------------------------------------------------------ */
+static double bridge_uniform(uint64_t seed, uint64_t stream, uint64_t j)
+{
+    uint64_t q = j >> 2;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)stream, (uint32_t)(stream >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    return orc_uniform(x[j & 3]);
+}
+
+int orc_gbm1d_bridge_payoffs(double s0, double sig, double w, double r, double T, int steps, uint64_t seed,
+                             int64_t path0, int64_t npaths, int npay, const int *kind, const double *strike,
+                             const double *barrier, double *out)
+{
+    if (steps < 1 || npaths < 0 || !(T > 0.0) || !(s0 > 0.0) || !(sig >= 0.0)) return -1;
+    const double dt = T / steps, sdt = sqrt(dt), disc = exp(-r * T);
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < npaths; ++n) {
+        const uint64_t path = (uint64_t)(path0 + n);
+        const uint64_t bstream = ((uint64_t)1 << 56) | path;
+        orc_stream st;
+        stream_init(&st, seed, path);
+        double x = log(s0), sum = 0.0, mmax = -INFINITY, mmin = INFINITY;
+        for (int i = 0; i < steps; ++i) {
+            const double z = stream_normal(&st, (uint64_t)i);
+            const double y = x + (r - 0.5 * sig * sig) * dt + sig * sdt * z;
+            const double Ui = bridge_uniform(seed, bstream, 2 * (uint64_t)i);
+            const double Vi = bridge_uniform(seed, bstream, 2 * (uint64_t)i + 1);
+            const double hi = 0.5 * (x + y + sqrt((x - y) * (x - y) - 2.0 * dt * sig * sig * log(Ui)));
+            const double lo = 0.5 * (x + y - sqrt((x - y) * (x - y) - 2.0 * dt * sig * sig * log(Vi)));
+            if (hi > mmax) mmax = hi;
+            if (lo < mmin) mmin = lo;
+            x = y;
+            sum += w * exp(x);
+        }
+        orc_pathstats ps;
+        ps.u_T = w * exp(x);
+        ps.avg = sum / steps;
+        ps.umax = w * exp(mmax);
+        ps.umin = w * exp(mmin);
+        for (int p = 0; p < npay; ++p)
+            out[(size_t)p * npaths + n] = disc * payoff_value(kind[p], strike[p], barrier[p], &ps);
+    }
+    return 0;
+}
+
 /* Materialised paths: save[(slot*d + a)*npaths + n] = S_a at step slot*save_every
  * (slot 0 is t_0), for n in [0, npaths), path index path0 + n. */
 int orc_gbm_paths(int d, const double *s0, const double *sig, const double *corr, const double *w,

@@ -6,7 +6,7 @@ library's CUDA kernels.  Model and configuration are plain keyword arguments:
   model:  kind="gbm", s0, sigma, corr=None, weights=None, r
           kind="heston", s0, v0, r, kappa, theta, xi, rho
   cfg:    steps, T, paths, seed=42, scheme="log_euler", precision="fp32",
-          path_offset=0, ckpt_every=0
+          path_offset=0, ckpt_every=0, monitoring="discrete" | "bridge"
   payoff: dict(kind=<name in native.PAYOFF>, strike=K, barrier=H)
 """
 from __future__ import annotations
@@ -50,6 +50,7 @@ class _Marshalled:
         c.seed = int(cfg.get("seed", 42))
         c.precision = native.PRECISION[cfg.get("precision", "fp32")]
         c.ckpt_every = int(cfg.get("ckpt_every", 0))
+        c.monitoring = native.MONITORING[cfg.get("monitoring", "discrete")]
         self.cfg = c
         self.n_payoff = 0
         self.payoffs = None
@@ -88,6 +89,22 @@ def price(model: dict, cfg: dict, payoffs, stream=None):
     check(L.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out,
                      _stream_handle(stream)))
     return [(r.price, r.se) for r in out]
+
+
+def price_mlmc(model: dict, cfg: dict, payoffs, paths_ref: int, stream=None):
+    """Two-level precision estimator (mc_price_mlmc): cfg["precision"] is the
+    coarse level's operand type on cfg["paths"] paths, paths_ref further
+    paths carry the FP32 - reduced-precision correction.  Returns one dict
+    per payoff: price, se, and (price, se) of coarse, correction, ref_level,
+    coarse_level."""
+    L = native.lib()
+    mm = _Marshalled(model, cfg, payoffs)
+    out = (native.McMlmcResult * mm.n_payoff)()
+    check(L.mc_price_mlmc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, int(paths_ref), out,
+                          _stream_handle(stream)))
+    return [dict(price=r.price, se=r.se, coarse=(r.coarse.price, r.coarse.se),
+                 correction=(r.correction.price, r.correction.se), ref_level=(r.ref_level.price, r.ref_level.se),
+                 coarse_level=(r.coarse_level.price, r.coarse_level.se)) for r in out]
 
 
 def greeks(model: dict, cfg: dict, payoffs, stream=None):

@@ -28,8 +28,24 @@ __device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet
     }
 }
 
+// Four uniforms of Philox block q of stream n (the same map as the normals).
+__device__ __forceinline__ float4 uniforms4(uint64_t q, uint64_t n, uint32_t k0, uint32_t k1)
+{
+    const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+                                             static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)),
+                                  k0, k1);
+    return make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w));
+}
+
+constexpr uint64_t kBridgeDomain = uint64_t(1) << 56;  // stream of path n's bridge uniforms: 2^56 + n
+
 // ------------------------------- 1-D GBM ---------------------------------
-template <int SCHEME, bool STATS, bool SAVE>
+// BRIDGE (log-Euler only): continuous barrier monitoring.  Between grid values
+// yp, y of log2(S/S0) the maximum of the Brownian bridge is drawn as
+// (yp + y + sqrt((y - yp)^2 - cb lg2 U)) / 2 with cb = 2 dt sigma^2 log2(e)
+// (Sec. VI.A.1; the formula in log2 units) and the minimum with the root
+// subtracted; U = uniforms 2i and 2i + 1 of the bridge stream.
+template <int SCHEME, bool STATS, bool SAVE, bool BRIDGE>
 __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
 {
     __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
@@ -50,17 +66,33 @@ __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
         if (valid) {
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             float y = (SCHEME == MC_LOG_EULER) ? 0.0f : a.s0;  // log2(S/S0) or S
+            float bmax = 0.0f, bmin = 0.0f;                    // bridge extremes of y
             if (SAVE) a.run.save[nl] = a.s0;
             const int nq = (M + 3) >> 2;
             for (int q = 0; q < nq; ++q) {
                 const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.k0, a.run.k1);
                 const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
+                float4 ub[2];
+                if (BRIDGE) {  // uniforms 8q .. 8q + 7: (max, min) of steps 4q .. 4q + 3
+                    ub[0] = uniforms4(2 * static_cast<uint64_t>(q), kBridgeDomain + n, a.run.k0, a.run.k1);
+                    ub[1] = uniforms4(2 * static_cast<uint64_t>(q) + 1, kBridgeDomain + n, a.run.k0, a.run.k1);
+                }
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
                     const int i = 4 * q + l;
                     if (i < M) {
+                        const float yp = y;
                         if (SCHEME == MC_LOG_EULER) y += fmaf(a.b, zz[l], a.a);
                         else y = fmaf(y, fmaf(a.b, zz[l], a.a), y);
+                        if (BRIDGE) {
+                            const float4 u = ub[l >> 1];
+                            const float umx = (l & 1) ? u.z : u.x, umn = (l & 1) ? u.w : u.y;
+                            const float dy = y - yp, d2 = dy * dy;
+                            const float rmax = sqrt_approx(fmaf(-a.cb, lg2_approx(umx), d2));
+                            const float rmin = sqrt_approx(fmaf(-a.cb, lg2_approx(umn), d2));
+                            bmax = fmaxf(bmax, 0.5f * (yp + y + rmax));
+                            bmin = fminf(bmin, 0.5f * (yp + y - rmin));
+                        }
                         if (STATS || SAVE) {
                             const float S = (SCHEME == MC_LOG_EULER) ? a.s0 * ex2_approx(y) : y;
                             if (STATS) st.add(S);
@@ -72,16 +104,20 @@ __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
             }
             uT = (SCHEME == MC_LOG_EULER) ? a.s0 * ex2_approx(y) : y;
             avg = st.sum * inv_m;
+            if (BRIDGE) {
+                st.umax = a.s0 * ex2_approx(bmax);
+                st.umin = a.s0 * ex2_approx(bmin);
+            }
         }
         if (a.pay.n > 0) accumulate_payoffs(s_acc, a.pay, valid, uT, avg, st);
     }
     if (a.pay.n > 0) block_finish(s_acc, s_red, a.pay.n, a.red);
 }
 
-template <int SCHEME, bool STATS, bool SAVE>
+template <int SCHEME, bool STATS, bool SAVE, bool BRIDGE = false>
 const void *gbm1d_fn()
 {
-    return reinterpret_cast<const void *>(&gbm1d_kernel<SCHEME, STATS, SAVE>);
+    return reinterpret_cast<const void *>(&gbm1d_kernel<SCHEME, STATS, SAVE, BRIDGE>);
 }
 
 const void *gbm1d_select(const Gbm1dArgs &a)
@@ -90,6 +126,7 @@ const void *gbm1d_select(const Gbm1dArgs &a)
     const bool save = a.run.save != nullptr;
     if (a.scheme == MC_LOG_EULER) {
         if (save) return gbm1d_fn<MC_LOG_EULER, false, true>();
+        if (a.bridge) return gbm1d_fn<MC_LOG_EULER, true, false, true>();
         return stats ? gbm1d_fn<MC_LOG_EULER, true, false>() : gbm1d_fn<MC_LOG_EULER, false, false>();
     }
     if (save) return gbm1d_fn<MC_EULER, false, true>();

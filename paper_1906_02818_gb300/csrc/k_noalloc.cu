@@ -68,6 +68,7 @@ extern "C" int mc_price_gbm1d_noalloc(const mc_model *m, const mc_sim_cfg *c, co
     if (c->steps < 1 || !(c->T > 0.0) || c->paths < 1 || c->path_offset < 0 ||
         (c->scheme != MC_LOG_EULER && c->scheme != MC_EULER))
         return noalloc_fail(MC_EINVAL, "steps, T, paths, path_offset or scheme out of range");
+    if (c->monitoring != MC_DISCRETE) return noalloc_fail(MC_EUNSUPPORTED, "discrete barrier monitoring only");
     if (!(m->s0[0] > 0.0) || !(m->sigma[0] >= 0.0) || !std::isfinite(m->r))
         return noalloc_fail(MC_EINVAL, "s0 must be > 0, sigma >= 0, r finite");
 

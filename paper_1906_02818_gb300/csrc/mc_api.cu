@@ -96,6 +96,10 @@ int check_cfg(const mc_sim_cfg *c, const mc_model *m)
     if (c->ckpt_every < 0) return fail(MC_EINVAL, "ckpt_every must be >= 0");
     if (m->kind == MC_HESTON && c->precision != MC_FP32)
         return fail(MC_EINVAL, "Heston has no correlation contraction: precision must be MC_FP32");
+    if (c->monitoring != MC_DISCRETE && c->monitoring != MC_BRIDGE)
+        return fail(MC_EINVAL, "unknown monitoring %d", c->monitoring);
+    if (c->monitoring == MC_BRIDGE && (m->kind != MC_GBM || m->d != 1 || c->scheme != MC_LOG_EULER))
+        return fail(MC_EUNSUPPORTED, "Brownian-bridge monitoring: single-asset GBM with MC_LOG_EULER only");
     return MC_OK;
 }
 
@@ -359,6 +363,9 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         if (c->scheme == MC_LOG_EULER) {
             g.a = static_cast<float>(M_LOG2E * (m->r - 0.5 * sg * sg) * dt);
             g.b = static_cast<float>(M_LOG2E * sg * sdt);
+            // bridge in log2 units: (log2 e)^2 sigma^2 dt (-2 ln U) = -cb lg2 U
+            g.bridge = c->monitoring == MC_BRIDGE && !save && ps.n > 0 ? 1 : 0;
+            g.cb = static_cast<float>(2.0 * M_LOG2E * sg * sg * dt);
         } else {
             g.a = static_cast<float>(m->r * dt);
             g.b = static_cast<float>(sg * sdt);
@@ -703,6 +710,120 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     for (int p = 0; p < np; ++p) {
         if (prices) prices[p] = tmp[static_cast<size_t>(p) * (G + 1)];
         for (int k = 0; k < G; ++k) greeks[static_cast<size_t>(p) * G + k] = tmp[static_cast<size_t>(p) * (G + 1) + 1 + k];
+    }
+    return MC_OK;
+}
+
+int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, int64_t paths_ref,
+                  mc_mlmc_result *out, void *stream)
+{
+    int rc;
+    if (!out) return fail(MC_EINVAL, "out is NULL");
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
+    if (m->kind != MC_GBM || m->d < 2 || m->d > 64)
+        return fail(MC_EUNSUPPORTED, "two-level precision estimator: correlated GBM baskets with 2 <= d <= 64");
+    if (c->precision == MC_FP32) return fail(MC_EINVAL, "the coarse level needs a reduced precision (BF16, FP16, E4M3)");
+    if (c->monitoring != MC_DISCRETE) return fail(MC_EUNSUPPORTED, "two-level estimator: discrete monitoring only");
+    if (np < 1 || np > kMlmcMaxPayoffs) return fail(MC_EINVAL, "n_payoff = %d outside [1, %d]", np, kMlmcMaxPayoffs);
+    if (paths_ref < 2) return fail(MC_EINVAL, "paths_ref = %lld must be >= 2", static_cast<long long>(paths_ref));
+    if (c->path_offset + c->paths + paths_ref > (int64_t(1) << 56)) return fail(MC_EINVAL, "path range must lie in [0, 2^56)");
+    PayoffSet ps;
+    if ((rc = build_payoffs(pays, np, &ps))) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // level 0: the reduced-precision tensor-core estimator on [offset, offset + N0)
+    std::vector<mc_result> coarse(np);
+    if ((rc = mc_price(m, c, pays, np, coarse.data(), stream))) return rc;
+
+    // level 1: both arithmetics on the next paths_ref paths
+    const int d = m->d;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
+    const size_t dd = static_cast<size_t>(d) * d, tri = static_cast<size_t>(d) * (d + 1) / 2;
+    mc_plan P;  // owns the scratch buffers (freed on return)
+    MC_CUDA(cudaMalloc(&P.dcorr, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dL, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dsig, d * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dLp, (tri + 64 * 65 / 2 + 64) * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.ddrift, d * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.dstatus, sizeof(int)));
+    std::vector<double> corr(dd, 0.0);
+    if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+    else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
+    MC_CUDA(cudaMemcpyAsync(P.dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(P.dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_cholesky(d, P.dcorr, P.dL, P.dstatus, s));
+    float *dLq = P.dLp + tri, *dcsq = dLq + 64 * 65 / 2;
+    MC_CUDA(launch_scale_factor(d, P.dL, P.dsig, cfac, sdt, m->r, dt, c->scheme, P.dLp, P.ddrift, s));
+    MC_CUDA(launch_mlmc_prep(c->precision, d, P.dL, P.dsig, cfac, sdt, dLq, dcsq, s));
+    std::vector<float> Lp(tri), Lq(64 * 65 / 2), csq(64), drift(d);
+    int status = 0;
+    MC_CUDA(cudaMemcpyAsync(&status, P.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(Lp.data(), P.dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(Lq.data(), dLq, Lq.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(csq.data(), dcsq, 64 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(drift.data(), P.ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+    MlmcConst k;
+    std::memset(&k, 0, sizeof k);
+    for (int a = 0; a < 64; ++a) {
+        for (int j = 0; j <= a; ++j) {
+            k.L[a * (a + 1) / 2 + j] = a < d ? Lp[static_cast<size_t>(a) * (a + 1) / 2 + j] : 0.0f;
+            k.Lq[a * (a + 1) / 2 + j] = Lq[a * (a + 1) / 2 + j];
+        }
+        k.csq[a] = csq[a];
+        if (a < d) {
+            const double w = m->weights ? m->weights[a] : 1.0 / d;
+            k.drift[a] = drift[a];
+            k.ws0[a] = static_cast<float>(w * m->s0[a]);
+            k.w[a] = static_cast<float>(w);
+            k.s0[a] = static_cast<float>(m->s0[a]);
+        } else {
+            k.s0[a] = 1.0f;  // padded columns: zero weight, inert state
+        }
+    }
+    MlmcArgs a{};
+    a.run.paths = paths_ref;
+    a.run.path_offset = c->path_offset + c->paths;
+    a.run.k0 = static_cast<uint32_t>(c->seed);
+    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    a.run.steps = c->steps;
+    a.run.save_every = 1;
+    a.d = d;
+    a.scheme = c->scheme;
+    a.pay = ps;
+    const int nv = 3 * np;
+    const int block = mlmc_block();
+    const int occ = mlmc_occupancy(c->precision, a);
+    if (occ <= 0) return fail(MC_ECUDA, "correction kernel cannot be resident");
+    int grid = 0, ppt = 1;
+    size_grid(paths_ref, block, occ * di.sms, &grid, &ppt);
+    a.run.ppt = ppt;
+    MC_CUDA(cudaMalloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned int)));
+    MC_CUDA(cudaMemsetAsync(P.ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMalloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
+    a.red.partials = P.partials;
+    a.red.ticket = P.ticket;
+    a.red.out = P.dout;
+    a.red.paths = paths_ref;
+    a.red.disc = std::exp(-m->r * c->T);
+    a.red.err = nullptr;
+    MC_CUDA(launch_mlmc_coupled(c->precision, a, k, grid, s));
+    std::vector<mc_result> lv(nv);
+    MC_CUDA(cudaMemcpyAsync(lv.data(), P.dout, nv * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    for (int p = 0; p < np; ++p) {
+        mc_mlmc_result &o = out[p];
+        o.coarse = coarse[p];
+        o.correction = lv[p];
+        o.ref_level = lv[np + p];
+        o.coarse_level = lv[2 * np + p];
+        o.price = coarse[p].price + lv[p].price;
+        o.se = std::sqrt(coarse[p].se * coarse[p].se + lv[p].se * lv[p].se);
     }
     return MC_OK;
 }

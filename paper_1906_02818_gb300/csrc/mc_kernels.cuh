@@ -26,6 +26,8 @@ struct Gbm1dArgs {
     PathRun run;
     int scheme;
     float s0, a, b;
+    int bridge;   // continuous monitoring via the Brownian-bridge extremes (log-Euler)
+    float cb;     // 2 dt sigma^2 log2(e): squared bridge spread term per -lg2(U)
     PayoffSet pay;
     ReduceArgs red;
 };
@@ -131,6 +133,32 @@ struct GreeksArgs {
 cudaError_t launch_greeks(const GreeksArgs &a, int grid, cudaStream_t s);
 int greeks_occupancy(int model, int n_payoff);
 int greeks_block();
+
+// Correction level of the two-level precision estimator (k_mlmc.cu): d <= 64
+// padded to 64; the FP32 factor Lhat and the dequantised tensor-core factor
+// Lq (packed lower triangles), Lq's column scales, drift and weights.
+constexpr int kMlmcMaxPayoffs = 10;  // 3 accumulated values per payoff
+struct MlmcConst {
+    float L[64 * 65 / 2];
+    float Lq[64 * 65 / 2];
+    float csq[64];
+    float drift[64];
+    float ws0[64];
+    float w[64];
+    float s0[64];
+};
+struct MlmcArgs {
+    PathRun run;
+    int d;
+    int scheme;
+    PayoffSet pay;
+    ReduceArgs red;  // 3 n_payoff values: f_fp32 - f_q, f_fp32, f_q
+};
+cudaError_t launch_mlmc_prep(int prec, int d, const double *L, const double *sigma, double cfac, double sdt,
+                             float *Lq, float *csq, cudaStream_t s);
+cudaError_t launch_mlmc_coupled(int prec, const MlmcArgs &a, const MlmcConst &c, int grid, cudaStream_t s);
+int mlmc_occupancy(int prec, const MlmcArgs &a);
+int mlmc_block();
 
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "MC_OK", -1: "MC_EINVAL", -2: "MC_ENOTPSD", -3: "MC_ENOMEM", 
 MODEL = {"gbm": 0, "heston": 1}
 SCHEME = {"log_euler": 0, "euler": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
+MONITORING = {"discrete": 0, "bridge": 1}
 PAYOFF = {"call": 0, "put": 1, "asian_call": 2, "asian_put": 3,
           "uo_call": 4, "ui_call": 5, "uo_put": 6, "ui_put": 7,
           "do_call": 8, "di_call": 9, "do_put": 10, "di_put": 11}
@@ -37,7 +38,7 @@ class McModel(ctypes.Structure):
 class McSimCfg(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("steps", ctypes.c_int32), ("T", ctypes.c_double),
                 ("paths", ctypes.c_int64), ("path_offset", ctypes.c_int64), ("seed", ctypes.c_uint64),
-                ("precision", ctypes.c_int32), ("ckpt_every", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("ckpt_every", ctypes.c_int32), ("monitoring", ctypes.c_int32)]
 
 
 class McPayoff(ctypes.Structure):
@@ -46,6 +47,11 @@ class McPayoff(ctypes.Structure):
 
 class McResult(ctypes.Structure):
     _fields_ = [("price", ctypes.c_double), ("se", ctypes.c_double)]
+
+
+class McMlmcResult(ctypes.Structure):
+    _fields_ = [("price", ctypes.c_double), ("se", ctypes.c_double), ("coarse", McResult),
+                ("correction", McResult), ("ref_level", McResult), ("coarse_level", McResult)]
 
 
 class McPortfolio(ctypes.Structure):
@@ -78,6 +84,8 @@ SIGNATURES = [
                                    ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_price", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
                                 ctypes.c_int32, ctypes.POINTER(McResult), ctypes.c_void_p]),
+    ("mc_price_mlmc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
+                                     ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(McMlmcResult), ctypes.c_void_p]),
     ("mc_greek_count", ctypes.c_int32, [ctypes.POINTER(McModel)]),
     ("mc_greeks", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
                                  ctypes.c_int32, ctypes.POINTER(McResult), ctypes.POINTER(McResult),

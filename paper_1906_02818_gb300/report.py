@@ -4,7 +4,7 @@ the error against the FP64 oracle on the same random stream (on a path
 prefix the oracle finishes quickly), and the oracle's own throughput on the
 host cores.
 
-  python -m paper_1906_02818_gb300.report [--only gbm1d,basket64,heston,basket512,risk]
+  python -m paper_1906_02818_gb300.report [--only gbm1d,bridge,basket64,mlmc,heston,basket512,risk]
          [--reps 20] [--oracle-paths N]
 
 Device times are CUDA events around mc_plan_execute (inputs resident, the
@@ -73,6 +73,30 @@ def run_gbm1d(torch, gb, orc, a):
                 oracle_path_steps_per_s=ps / t_orc, oracle_sample="all 2^20 paths")
 
 
+def run_bridge(torch, gb, orc, a):
+    """The paper's "In and Out Put" (Sec. VI.A.1) with Brownian-bridge
+    monitoring: S0 100, K 120, H 140, r 0.03, sigma 0.8, T 2; 2^22 paths."""
+    model = dict(kind="gbm", s0=np.array([100.0]), sigma=np.array([0.8]), r=0.03)
+    pays = [dict(kind="ui_put", strike=120.0, barrier=140.0)]
+    out = dict(workload="up-and-in put, Brownian-bridge monitoring, 2^22 paths", paper_value=23.1371783926, steps={})
+    for steps in (25, 100):
+        cfg = dict(steps=steps, T=2.0, paths=1 << 22, seed=42, monitoring="bridge")
+        t, res = _plan_time(torch, gb, model, cfg, pays, a.reps)
+        disc, = gb.price(model, dict(cfg, monitoring="discrete"), pays)
+        n_or = a.oracle_paths or (1 << 14)
+        t0 = time.perf_counter()
+        ref = orc.gbm1d_bridge_payoffs(100.0, 0.8, 0.03, 2.0, steps, n_or, pays)[0]
+        t_orc = time.perf_counter() - t0
+        small, = gb.price(model, dict(cfg, paths=n_or), pays)
+        out["steps"][steps] = dict(seconds=t, path_steps_per_s=(1 << 22) * steps / t, price=float(res[0, 0]),
+                                   std_err=float(res[0, 1]),
+                                   diff_from_paper_in_se=float((res[0, 0] - 23.1371783926) / res[0, 1]),
+                                   discrete_monitoring_price=disc[0],
+                                   rel_err_vs_oracle_prefix=_rel(small[0], ref.mean()), oracle_prefix_paths=n_or,
+                                   oracle_path_steps_per_s=n_or * steps / t_orc)
+    return out
+
+
 def run_basket64(torch, gb, orc, a):
     import workloads
     w = workloads.basket_d64()
@@ -93,6 +117,30 @@ def run_basket64(torch, gb, orc, a):
                                        rel_err_vs_oracle_prefix=errs)
     out["oracle_prefix_paths"] = n_or
     out["oracle_path_steps_per_s"] = n_or * w["steps"] / t_orc
+    return out
+
+
+def run_mlmc(torch, gb, orc, a):
+    """Two-level precision estimator on the d = 64 workload: reduced-precision
+    coarse level on 2^18 paths plus the FP32 - reduced correction on 2^14."""
+    import workloads
+    w = workloads.basket_d64()
+    model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], corr=w["corr"], weights=w["weights"], r=w["r"])
+    base = dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=w["seed"])
+    fp32 = gb.price(model, base, w["payoffs"])
+    out = dict(workload="basket d=64, 2^18 coarse + 2^14 correction paths", fp32=[list(r) for r in fp32], precisions={})
+    for prec in ("fp8", "bf16"):
+        gb.price_mlmc(model, dict(base, precision=prec), w["payoffs"], 1 << 14)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = gb.price_mlmc(model, dict(base, precision=prec), w["payoffs"], 1 << 14)
+        t = time.perf_counter() - t0
+        out["precisions"][prec] = dict(
+            wall_seconds=t,
+            payoffs=[dict(coarse=r["coarse"], correction=r["correction"], two_level=(r["price"], r["se"]),
+                          coarse_bias_vs_fp32=r["coarse"][0] - f[0],
+                          two_level_minus_fp32_in_corr_se=(r["price"] - f[0]) / r["correction"][1],
+                          plain_se_at_2e14=r["ref_level"][1]) for r, f in zip(res, fp32)])
     return out
 
 
@@ -167,12 +215,13 @@ def main():
     import oracle
     import paper_1906_02818_gb300 as gb
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", default="gbm1d,basket64,heston,basket512,risk")
+    ap.add_argument("--only", default="gbm1d,bridge,basket64,mlmc,heston,basket512,risk")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--oracle-paths", type=int, default=0)
     a = ap.parse_args()
     oracle.build()
-    runs = dict(gbm1d=run_gbm1d, basket64=run_basket64, heston=run_heston, basket512=run_basket512, risk=run_risk)
+    runs = dict(gbm1d=run_gbm1d, bridge=run_bridge, basket64=run_basket64, mlmc=run_mlmc, heston=run_heston,
+                basket512=run_basket512, risk=run_risk)
     for name in a.only.split(","):
         out = runs[name](torch, gb, oracle, a)
         out["name"] = name

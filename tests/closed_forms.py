@@ -83,3 +83,13 @@ def up_and_in_put_continuous(S, K, H, r, sigma, T):
     # phi = -1 (put), eta = -1 (up barrier)
     return (-S * (H / S) ** (2.0 * (mu + 1.0)) * ncdf(-y1)
             + K * exp(-r * T) * (H / S) ** (2.0 * mu) * ncdf(-y1 + sT))
+
+
+def down_and_in_call_continuous(S, K, H, r, sigma, T):
+    """Continuously monitored down-and-in call, no dividends, H < S, H <= K
+    (reflection principle, the image of the call in the barrier)."""
+    mu = (r - 0.5 * sigma * sigma) / (sigma * sigma)
+    sT = sigma * sqrt(T)
+    y1 = log(H * H / (S * K)) / sT + (1.0 + mu) * sT
+    return (S * (H / S) ** (2.0 * (mu + 1.0)) * ncdf(y1)
+            - K * exp(-r * T) * (H / S) ** (2.0 * mu) * ncdf(y1 - sT))

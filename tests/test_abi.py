@@ -46,7 +46,8 @@ def _structs(kind="gbm", d=1, **over):
         model = dict(kind="heston", s0=100.0, v0=0.04, r=0.05, kappa=2.0, theta=0.04, xi=0.5, rho=-0.7)
     model.update({k: v for k, v in over.items() if k in ("s0", "sigma", "corr", "weights", "r", "rho", "xi", "v0")})
     cfg = dict(steps=4, T=1.0, paths=16)
-    cfg.update({k: v for k, v in over.items() if k in ("steps", "T", "paths", "scheme", "precision", "path_offset")})
+    cfg.update({k: v for k, v in over.items()
+                if k in ("steps", "T", "paths", "scheme", "precision", "path_offset", "monitoring")})
     pays = over.get("payoffs", [dict(kind="call", strike=100.0)])
     return api._Marshalled(model, cfg, pays)
 
@@ -92,3 +93,34 @@ def test_null_and_count_checks(lib):
                               ctypes.byref(h), None) == native.MC_EINVAL
     assert lib.mc_simulate(ctypes.byref(mm.model), ctypes.byref(mm.cfg), 3, ctypes.c_void_p(1), None) == native.MC_EINVAL
     assert lib.mc_plan_execute(None, ctypes.c_void_p(1), None) == native.MC_EINVAL
+
+
+def test_bridge_monitoring_checks(lib):
+    from paper_1906_02818_gb300 import native
+    out = (native.McResult * 1)()
+    pays = [dict(kind="uo_call", strike=100.0, barrier=130.0)]
+    for over, code, needle in [(dict(monitoring="bridge", scheme="euler"), native.MC_EUNSUPPORTED, "bridge"),
+                               (dict(d=3, monitoring="bridge"), native.MC_EUNSUPPORTED, "bridge")]:
+        mm = _structs(payoffs=pays, **over)
+        rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
+        assert rc == code, over
+        assert needle in lib.mc_last_error().decode().lower()
+    mm = _structs(payoffs=pays)
+    mm.cfg.monitoring = 7
+    rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
+    assert rc == native.MC_EINVAL and "monitoring" in lib.mc_last_error().decode()
+
+
+def test_two_level_estimator_checks(lib):
+    from paper_1906_02818_gb300 import native
+    out = (native.McMlmcResult * 12)()
+    for over, np_, ref, code, needle in [
+            (dict(d=4, precision="fp32"), 1, 64, native.MC_EINVAL, "reduced precision"),
+            (dict(d=1, precision="bf16"), 1, 64, native.MC_EUNSUPPORTED, "2 <= d"),
+            (dict(d=4, precision="bf16"), 11, 64, native.MC_EINVAL, "n_payoff"),
+            (dict(d=4, precision="bf16"), 1, 1, native.MC_EINVAL, "paths_ref")]:
+        mm = _structs(payoffs=[dict(kind="call", strike=100.0)] * np_, **over)
+        rc = lib.mc_price_mlmc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, np_, ref, out, None)
+        assert rc == code, (over, np_, ref)
+        assert needle in lib.mc_last_error().decode()
+    assert lib.mc_price_mlmc(None, None, None, 1, 64, out, None) == native.MC_EINVAL

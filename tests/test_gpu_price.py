@@ -178,3 +178,66 @@ def test_non_psd_correlation_is_reported(gb):
         gb.price(dict(kind="gbm", s0=[100.0] * 3, sigma=[0.2] * 3, corr=corr, r=0.05),
                  dict(steps=4, T=1.0, paths=64), [dict(kind="call", strike=100.0)])
     assert e.value.status == native.MC_ENOTPSD
+
+
+# ------------------------ Brownian-bridge monitoring ------------------------
+
+BRIDGE_PAYS = [dict(kind="ui_put", strike=120.0, barrier=140.0), dict(kind="uo_put", strike=120.0, barrier=140.0),
+               dict(kind="di_call", strike=100.0, barrier=80.0), dict(kind="do_call", strike=100.0, barrier=80.0),
+               dict(kind="put", strike=120.0), dict(kind="asian_call", strike=100.0)]
+
+
+def _bridge_band_mass(orc, s0, sg, r, T, steps, paths, payoffs):
+    """Payoff mass / N of the paths whose bridge extreme lies within BAND of
+    H, read from the oracle itself: the knock-in indicator (a knock-in call
+    struck at 0) differs between the barriers H (1 - BAND) and H (1 + BAND)."""
+    out = []
+    for p in payoffs:
+        if p["kind"][:2] not in ("ui", "uo", "di", "do"):
+            out.append(None)
+            continue
+        up = p["kind"][0] == "u"
+        H = p["barrier"]
+        probe = [dict(kind="ui_call" if up else "di_call", strike=0.0, barrier=H * (1 - BAND)),
+                 dict(kind="ui_call" if up else "di_call", strike=0.0, barrier=H * (1 + BAND)),
+                 dict(kind="call" if "call" in p["kind"] else "put", strike=p["strike"])]
+        f = orc.gbm1d_bridge_payoffs(s0, sg, r, T, steps, paths, probe)
+        near = (f[0] > 0) != (f[1] > 0)
+        out.append(float(f[2][near].sum()) / paths * 1.01 + 1e-12)
+    return out
+
+
+@pytest.mark.parametrize("steps,paths", [(25, 1 << 15), (1, 4099), (64, 777), (3, 1)])
+def test_gbm1d_bridge_matches_oracle(gb, orc, steps, paths):
+    s0, sg, r, T = 100.0, 0.8, 0.03, 2.0
+    model = dict(kind="gbm", s0=np.array([s0]), sigma=np.array([sg]), r=r)
+    cfg = dict(steps=steps, T=T, paths=paths, seed=42, monitoring="bridge")
+    got = gb.price(model, cfg, BRIDGE_PAYS)
+    ref = orc.gbm1d_bridge_payoffs(s0, sg, r, T, steps, paths, BRIDGE_PAYS)
+    assert_price_close(got, ref, BRIDGE_PAYS, _bridge_band_mass(orc, s0, sg, r, T, steps, paths, BRIDGE_PAYS),
+                       f"bridge/{steps}/{paths}")
+
+
+def test_gbm1d_bridge_reproduces_paper_value(gb):
+    """The paper's "In and Out Put" (Sec. VI.A.1) on the GPU: 2^22 paths at
+    25 steps, within 3 SE of 23.1371783926 (the bridge is exact in law for
+    GBM, so there is no discretisation bias to allow for)."""
+    model = dict(kind="gbm", s0=np.array([100.0]), sigma=np.array([0.8]), r=0.03)
+    cfg = dict(steps=25, T=2.0, paths=1 << 22, seed=7, monitoring="bridge")
+    (m, se), = gb.price(model, cfg, [dict(kind="ui_put", strike=120.0, barrier=140.0)])
+    print(f"in-and-out put {m:.5f} +- {se:.5f} (paper 23.1371783926)")
+    assert abs(m - 23.1371783926) <= 3 * se
+
+
+def test_bridge_monitoring_unsupported_cases(gb):
+    from paper_1906_02818_gb300 import native
+    pays = [dict(kind="uo_call", strike=100.0, barrier=130.0)]
+    w = workloads.basket_d64(paths=256, steps=4, d=4)
+    cases = [(gbm_model(w), dict(steps=4, T=1.0, paths=256, monitoring="bridge")),
+             (dict(kind="gbm", s0=np.array([100.0]), sigma=np.array([0.2]), r=0.05),
+              dict(steps=4, T=1.0, paths=256, monitoring="bridge", scheme="euler")),
+             (dict(kind="heston", **workloads.HESTON_PARAMS), dict(steps=4, T=1.0, paths=256, monitoring="bridge"))]
+    for model, cfg in cases:
+        with pytest.raises(native.MCError) as e:
+            gb.price(model, cfg, pays)
+        assert e.value.status == native.MC_EUNSUPPORTED
