@@ -208,6 +208,52 @@ int mc_price_mlmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff 
                   int64_t paths_ref, mc_mlmc_result *out, void *stream);
 
 /*
+ * mc_price_qmc -- randomised quasi-Monte Carlo (Sec. IV, Sobol QRNGs; the
+ * basket experiment of Sec. VI.D): the GBM basket of `model` driven by a
+ * Sobol sequence instead of Philox normals.  Dimension 1 is van der Corput;
+ * dimension j >= 2 uses the (j-1)-th primitive polynomial over GF(2) (by
+ * degree, then value) with initial direction integers m_1..m_s = 1 and the
+ * Bratley-Fox recurrence.  Point n of dimension j is the XOR of the direction
+ * words over the set bits of n; replication r XORs dimension j with word j of
+ * Philox stream 6 * 2^56 + r under cfg->seed (a random digital shift).
+ * Normal a of step i is the cosine branch of Box-Muller on dimensions
+ * 2 (i d + a), 2 (i d + a) + 1, through the uniform map of the Philox path.
+ *   cfg->paths = points per replication, cfg->path_offset = first point;
+ *   points in [0, 2^23); d <= 32 and 2 d steps <= 64; FP32 contraction,
+ *   discrete monitoring; 2 <= replications <= 65535.
+ *   out: host [n_payoff]: price = mean of the replication means, se = their
+ *   standard deviation / sqrt(replications).  rep_means: optional host
+ *   [replications][n_payoff].
+ * Synchronises `stream`.
+ */
+int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+                 int32_t replications, mc_result *out, double *rep_means, void *stream);
+
+/*
+ * Surrogate pricing network (mc_mlp)/*
+ * Surrogate pricing network (mc_mlp)/*
+ * mc_price_qmc -- randomised quasi-Monte Carlo (Sec. IV, Sobol QRNGs; the
+ * basket experiment of Sec. VI.D): the GBM basket of `model` driven by a
+ * Sobol sequence instead of Philox normals.  Dimension 1 is van der Corput;
+ * dimension j >= 2 uses the (j-1)-th primitive polynomial over GF(2) (by
+ * degree, then value) with initial direction integers m_1..m_s = 1 and the
+ * Bratley-Fox recurrence.  Point n of dimension j is the XOR of the direction
+ * words over the set bits of n; replication r XORs dimension j with word j of
+ * Philox stream 6 * 2^56 + r under cfg->seed (a random digital shift).
+ * Normal a of step i is the cosine branch of Box-Muller on dimensions
+ * 2 (i d + a), 2 (i d + a) + 1, through the uniform map of the Philox path.
+ *   cfg->paths = points per replication, cfg->path_offset = first point;
+ *   points in [0, 2^23); d <= 32 and 2 d steps <= 64; FP32 contraction,
+ *   discrete monitoring; 2 <= replications <= 65535.
+ *   out: host [n_payoff]: price = mean of the replication means, se = their
+ *   standard deviation / sqrt(replications).  rep_means: optional host
+ *   [replications][n_payoff].
+ * Synchronises `stream`.
+ */
+int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
+                 int32_t replications, mc_result *out, double *rep_means, void *stream);
+
+/*
  * Surrogate pricing network (mc_mlp)/*
  * Surrogate pricing network (mc_mlp): n_in -> width x hidden (SiLU) -> 1
  * (linear), the network that revalues the risk portfolio.  Parameters are

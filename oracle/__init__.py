@@ -16,8 +16,10 @@ Contents
              (Sec. II.A.3), correlated GBM Euler / log-Euler steps (Sec. II.A.1,
              II.A.2), Heston full-truncation Euler, European / Asian / barrier
              payoffs (Sec. I.A.2), continuous barrier monitoring through the
-             Brownian-bridge extremes (Sec. VI.A.1), forward-mode pathwise
-             Greeks (Sec. I.A.3), the estimator of Eq. 3 with its standard error.
+             Brownian-bridge extremes (Sec. VI.A.1), the factor-model
+             correlation (rho = B B^T + diag(e^2)), randomised Sobol
+             quasi-Monte Carlo (Sec. IV, VI.D), forward-mode pathwise Greeks
+             (Sec. I.A.3), the estimator of Eq. 3 with its standard error.
   mlp.py     FP64 numpy forward / backward of the pricing surrogate.
   risk.py    VaR / CVaR of Sec. VI.B and nested revaluation.
 
@@ -30,7 +32,10 @@ Cholesky against numpy; d = 1 basket = scalar GBM; geometric-basket closed
 form; Heston xi = 0 reduction to Black-Scholes; Greeks against Black-Scholes
 closed forms and common-random-number finite differences; the Brownian-bridge
 barrier against the paper's "In and Out Put" value 23.1371783926 and the
-continuous down-and-in call closed form, at one step and at many.
+continuous down-and-in call closed form, at one step and at many; the Sobol
+recurrence against its definition, one-dimensional stratification, the
+(0, m, 2)-net property of the first two dimensions, and the randomised-QMC
+price against Black-Scholes and its error rate against plain Monte Carlo.
 """
 from __future__ import annotations
 
@@ -96,6 +101,16 @@ def _load():
     lib.orc_gbm_greeks.restype = i32
     lib.orc_gbm1d_bridge_payoffs.argtypes = [dbl] * 5 + [i32, u64, i64, i64, i32, i_p, d_p, d_p, d_p]
     lib.orc_gbm1d_bridge_payoffs.restype = i32
+    lib.orc_gbm_factor_payoffs.argtypes = [i32, i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, i32, u64, i64, i64, i32, i_p,
+                                           d_p, d_p, d_p, d_p]
+    lib.orc_gbm_factor_payoffs.restype = i32
+    lib.orc_sobol_directions.argtypes = [i32, u32_p]
+    lib.orc_sobol_directions.restype = i32
+    lib.orc_sobol_points.argtypes = [i32, i64, i64, u32_p]
+    lib.orc_sobol_points.restype = i32
+    lib.orc_qmc_gbm_payoffs.argtypes = [i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, i32, u64, i64, i64, i64, i32, i_p,
+                                        d_p, d_p, d_p]
+    lib.orc_qmc_gbm_payoffs.restype = i32
     hes_common = [dbl] * 8 + [i32, u64, i64, i64]
     lib.orc_heston_payoffs.argtypes = hes_common + [i32, i_p, d_p, d_p, d_p]
     lib.orc_heston_payoffs.restype = i32
@@ -215,6 +230,57 @@ def gbm1d_bridge_payoffs(s0, sigma, r, T, steps, paths, payoffs, weight=1.0, see
                                           kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(K), _dptr(H),
                                           _dptr(out))
     _check(rc, "orc_gbm1d_bridge_payoffs")
+    return out
+
+
+def gbm_factor_payoffs(s0, sigma, loadings, r, T, steps, paths, payoffs, weights=None, scheme="log_euler", seed=42,
+                       path_offset=0, terminal=False):
+    """Discounted per-path payoffs [len(payoffs), paths] of the factor-model
+    GBM basket (loadings B: [d, k]); with terminal=True also the terminal
+    prices [d, paths]."""
+    s0 = _f64(np.atleast_1d(s0))
+    sigma = _f64(np.atleast_1d(sigma))
+    d = s0.size
+    B = _f64(np.asarray(loadings, dtype=np.float64).reshape(d, -1))
+    k = B.shape[1]
+    w = np.full(d, 1.0 / d) if weights is None else _f64(weights)
+    kinds, K, H = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), paths), dtype=np.float64)
+    ST = np.empty((d, paths), dtype=np.float64) if terminal else None
+    rc = _load().orc_gbm_factor_payoffs(d, k, _dptr(s0), _dptr(sigma), _dptr(B) if k else None, _dptr(w), r, T, steps,
+                                        0 if scheme == "log_euler" else 1, seed, path_offset, paths, len(payoffs),
+                                        kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(K), _dptr(H),
+                                        _dptr(out), _dptr(ST))
+    _check(rc, "orc_gbm_factor_payoffs")
+    return (out, ST) if terminal else out
+
+
+def sobol_directions(ndim: int) -> np.ndarray:
+    """Direction numbers V[j][k] (uint32) of the oracle's Sobol sequence."""
+    V = np.zeros((ndim, 32), dtype=np.uint32)
+    _check(_load().orc_sobol_directions(ndim, V.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), "orc_sobol_directions")
+    return V
+
+
+def sobol_points(ndim: int, n: int, n0: int = 0) -> np.ndarray:
+    """Unshifted 32-bit Sobol words of points n0 .. n0 + n - 1: [n, ndim]."""
+    P = np.zeros((n, ndim), dtype=np.uint32)
+    _check(_load().orc_sobol_points(ndim, n0, n, P.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), "orc_sobol_points")
+    return P
+
+
+def qmc_gbm_payoffs(s0, sigma, r, T, steps, points, payoffs, rep=0, corr=None, weights=None, scheme="log_euler",
+                    seed=42, point_offset=0) -> np.ndarray:
+    """Discounted payoffs of the randomised-Sobol GBM paths of replication
+    `rep`, shape [len(payoffs), points]."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    kinds, K, H = _payoff_arrays(payoffs)
+    out = np.empty((len(payoffs), points), dtype=np.float64)
+    rc = _load().orc_qmc_gbm_payoffs(d, _dptr(s0), _dptr(sigma), _dptr(corr), _dptr(w), r, T, steps,
+                                     0 if scheme == "log_euler" else 1, seed, rep, point_offset, points,
+                                     len(payoffs), kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(K),
+                                     _dptr(H), _dptr(out))
+    _check(rc, "orc_qmc_gbm_payoffs")
     return out
 
 

@@ -397,6 +397,237 @@ int orc_gbm1d_bridge_payoffs(double s0, double sig, double w, double r, double T
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Factor-model correlated GBM: the correlation is rho = B B^T + diag(e^2)    */
+/* with loadings B (d x k) and idiosyncratic weights e_a = sqrt(1 - sum_j    */
+/* B_aj^2), and the increment of step i is                                   */
+/*   dW_a = sqrt(dt) sig_a (sum_j B_aj z_j + e_a eps_a),                      */
+/* z_j = normal i (k + d) + j, eps_a = normal i (k + d) + k + a of the path's */
+/* stream (O(d k) per step instead of the Cholesky O(d^2); exact in law).     */
+/* Otherwise the step, statistics and payoffs of gbm_path.  Discounted        */
+/* payoffs out[p * npaths + n]; terminal prices ST[a * npaths + n] if ST.     */
+/* ------------------------------------------------------------------------ */
+int orc_gbm_factor_payoffs(int d, int k, const double *s0, const double *sig, const double *B, const double *w,
+                           double r, double T, int steps, int scheme, uint64_t seed, int64_t path0, int64_t npaths,
+                           int npay, const int *kind, const double *strike, const double *barrier, double *out,
+                           double *ST)
+{
+    if (d < 1 || k < 0 || steps < 1 || npaths < 0 || !(T > 0.0) || (scheme != 0 && scheme != 1)) return -1;
+    double *e = (double *)malloc(sizeof(double) * (size_t)d);
+    if (!e) return -3;
+    for (int a = 0; a < d; ++a) {
+        double q = 0.0;
+        for (int j = 0; j < k; ++j) q += B[(size_t)a * k + j] * B[(size_t)a * k + j];
+        if (q > 1.0 + 1e-12) { free(e); return -2; }
+        e[a] = sqrt(q < 1.0 ? 1.0 - q : 0.0);
+    }
+    const double dt = T / steps, sdt = sqrt(dt), disc = exp(-r * T);
+    int bad = 0;
+#pragma omp parallel
+    {
+        double *x = (double *)malloc(sizeof(double) * (size_t)(2 * d + k + 1));
+        if (!x) bad = 1;
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            if (!x) continue;
+            double *eps = x + d, *z = x + 2 * d;
+            orc_stream st;
+            stream_init(&st, seed, (uint64_t)(path0 + n));
+            for (int a = 0; a < d; ++a) x[a] = (scheme == 0) ? log(s0[a]) : s0[a];
+            double sum = 0.0, umax = -INFINITY, umin = INFINITY, u = 0.0;
+            for (int i = 0; i < steps; ++i) {
+                const uint64_t base = (uint64_t)i * (uint64_t)(k + d);
+                for (int j = 0; j < k; ++j) z[j] = stream_normal(&st, base + (uint64_t)j);
+                for (int a = 0; a < d; ++a) eps[a] = stream_normal(&st, base + (uint64_t)k + (uint64_t)a);
+                u = 0.0;
+                for (int a = 0; a < d; ++a) {
+                    double f = e[a] * eps[a];
+                    for (int j = 0; j < k; ++j) f += B[(size_t)a * k + j] * z[j];
+                    const double dW = sdt * sig[a] * f;
+                    if (scheme == 0) x[a] += (r - 0.5 * sig[a] * sig[a]) * dt + dW;
+                    else x[a] *= 1.0 + r * dt + dW;
+                    u += w[a] * ((scheme == 0) ? exp(x[a]) : x[a]);
+                }
+                sum += u;
+                if (u > umax) umax = u;
+                if (u < umin) umin = u;
+            }
+            orc_pathstats ps;
+            ps.u_T = u; ps.avg = sum / steps; ps.umax = umax; ps.umin = umin;
+            for (int p = 0; p < npay; ++p) out[(size_t)p * npaths + n] = disc * payoff_value(kind[p], strike[p], barrier[p], &ps);
+            if (ST)
+                for (int a = 0; a < d; ++a) ST[(size_t)a * npaths + n] = (scheme == 0) ? exp(x[a]) : x[a];
+        }
+        free(x);
+    }
+    free(e);
+    return bad ? -3 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sobol sequence and randomised quasi-Monte Carlo (Sec. IV, QRNGs; the      */
+/* basket experiment of Sec. VI.D).  Dimension 1 is the van der Corput       */
+/* sequence (m_k = 1).  Dimension j >= 2 uses the (j-1)-th primitive         */
+/* polynomial over GF(2), enumerated by degree s and then by its integer     */
+/* value x^s + a_1 x^{s-1} + ... + a_{s-1} x + 1, with initial m_1..m_s = 1   */
+/* and the recurrence (Bratley-Fox)                                          */
+/*   m_k = 2 a_1 m_{k-1} ^ 4 a_2 m_{k-2} ^ ... ^ 2^{s-1} a_{s-1} m_{k-s+1}   */
+/*         ^ 2^s m_{k-s} ^ m_{k-s};                                           */
+/* direction numbers V_k = m_k 2^{32-k}; point n (natural order) is the XOR  */
+/* of V_{k+1} over the set bits k of n.  Replication r shifts every point of */
+/* dimension j by the XOR of Philox word j of stream 6 * 2^56 + r (a random   */
+/* digital shift).  Uniforms use the map of orc_uniform; normal a is the      */
+/* cosine branch of Box-Muller on dimensions (2a, 2a + 1).                    */
+/* ------------------------------------------------------------------------ */
+#define ORC_SOBOL_MAX_DIM 64
+
+static int gf2_degree(uint32_t p)
+{
+    int d = -1;
+    while (p) { ++d; p >>= 1; }
+    return d;
+}
+
+/* a * b mod p over GF(2); a, b of degree < s, p of degree s */
+static uint32_t gf2_mulmod(uint32_t a, uint32_t b, uint32_t p, int s)
+{
+    uint64_t prod = 0;
+    for (int i = 0; i < s; ++i)
+        if ((b >> i) & 1) prod ^= (uint64_t)a << i;
+    for (int i = 2 * s - 2; i >= s; --i)
+        if ((prod >> i) & 1) prod ^= (uint64_t)p << (i - s);
+    return (uint32_t)prod;
+}
+
+/* x^e mod p over GF(2) */
+static uint32_t gf2_xpow_mod(uint64_t e, uint32_t p, int s)
+{
+    uint32_t r = 1, b = (s == 1) ? (2u ^ p) : 2u; /* x reduced mod p */
+    for (; e; e >>= 1) {
+        if (e & 1) r = gf2_mulmod(r, b, p, s);
+        b = gf2_mulmod(b, b, p, s);
+    }
+    return r;
+}
+
+/* p primitive: x has multiplicative order exactly 2^s - 1 modulo p, i.e.
+ * x^(2^s - 1) = 1 and x^((2^s - 1) / q) != 1 for every prime q dividing it. */
+static int gf2_primitive(uint32_t p)
+{
+    const int s = gf2_degree(p);
+    if (s < 1 || !(p & 1)) return 0;
+    const uint64_t order = ((uint64_t)1 << s) - 1;
+    if (gf2_xpow_mod(order, p, s) != 1) return 0;
+    uint64_t n = order;
+    for (uint64_t q = 2; q <= n; ++q) {
+        if (n % q) continue;
+        if (gf2_xpow_mod(order / q, p, s) == 1) return 0;
+        while (n % q == 0) n /= q;
+    }
+    return 1;
+}
+
+/* Direction numbers V[j][k] (k = 0..31) of dimensions j = 0..ndim-1. */
+int orc_sobol_directions(int ndim, uint32_t *V)
+{
+    if (ndim < 1 || ndim > ORC_SOBOL_MAX_DIM) return -1;
+    for (int k = 0; k < 32; ++k) V[k] = (uint32_t)1 << (31 - k);
+    uint32_t p = 2;
+    for (int j = 1; j < ndim; ++j) {
+        do { ++p; } while (!gf2_primitive(p));
+        int s = gf2_degree(p);
+        uint32_t m[33];
+        for (int k = 1; k <= s && k <= 32; ++k) m[k] = 1;
+        for (int k = s + 1; k <= 32; ++k) {
+            uint32_t v = m[k - s] ^ (m[k - s] << s);
+            for (int i = 1; i < s; ++i)
+                if ((p >> (s - i)) & 1) v ^= m[k - i] << i; /* a_i = coefficient of x^{s-i} */
+            m[k] = v;
+        }
+        for (int k = 1; k <= 32; ++k) V[(size_t)j * 32 + (k - 1)] = m[k] << (32 - k);
+    }
+    return 0;
+}
+
+static uint32_t sobol_word(const uint32_t *Vj, uint64_t n)
+{
+    uint32_t x = 0;
+    for (int k = 0; n; ++k, n >>= 1) if (n & 1) x ^= Vj[k];
+    return x;
+}
+
+int orc_sobol_points(int ndim, int64_t n0, int64_t npts, uint32_t *out /* [npts][ndim] */)
+{
+    uint32_t V[ORC_SOBOL_MAX_DIM * 32];
+    if (orc_sobol_directions(ndim, V)) return -1;
+    for (int64_t i = 0; i < npts; ++i)
+        for (int j = 0; j < ndim; ++j) out[(size_t)i * ndim + j] = sobol_word(V + (size_t)j * 32, (uint64_t)(n0 + i));
+    return 0;
+}
+
+/* Correlated GBM baskets on randomised Sobol points: replication `rep`,
+ * points [n0, n0 + npts); 2 d steps <= 64 dimensions; the normal of step i,
+ * asset a is normal i d + a of the point; otherwise the step, statistics and
+ * payoffs of gbm_path (log-Euler or Euler).  Discounted payoffs
+ * out[p * npts + i]. */
+int orc_qmc_gbm_payoffs(int d, const double *s0, const double *sig, const double *corr, const double *w,
+                        double r, double T, int steps, int scheme, uint64_t seed, int64_t rep, int64_t n0,
+                        int64_t npts, int npay, const int *kind, const double *strike, const double *barrier,
+                        double *out)
+{
+    const int ndim = 2 * d * steps;
+    if (d < 1 || steps < 1 || ndim > ORC_SOBOL_MAX_DIM || npts < 0 || (scheme != 0 && scheme != 1)) return -1;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, w, r, T, steps, scheme, seed);
+    if (rc) return rc;
+    uint32_t V[ORC_SOBOL_MAX_DIM * 32], shift[ORC_SOBOL_MAX_DIM];
+    orc_sobol_directions(ndim, V);
+    {
+        const uint64_t stream = ((uint64_t)6 << 56) | (uint64_t)rep;
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int q = 0; q * 4 < ndim; ++q) {
+            uint32_t ctr[4] = {(uint32_t)q, 0u, (uint32_t)stream, (uint32_t)(stream >> 32)}, x[4];
+            orc_philox4x32_10(ctr, key, x);
+            for (int l = 0; l < 4 && 4 * q + l < ndim; ++l) shift[4 * q + l] = x[l];
+        }
+    }
+    const double dt = T / steps, sdt = sqrt(dt), disc = exp(-r * T);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npts; ++i) {
+        double x[64], y[64], z[64];
+        double sum = 0.0, umax = -INFINITY, umin = INFINITY, u = 0.0;
+        for (int a = 0; a < d; ++a) x[a] = (scheme == 0) ? log(s0[a]) : s0[a];
+        for (int st = 0; st < steps; ++st) {
+            for (int a = 0; a < d; ++a) {
+                const int jn = st * d + a;
+                const double u1 = orc_uniform(sobol_word(V + (size_t)(2 * jn) * 32, (uint64_t)(n0 + i)) ^ shift[2 * jn]);
+                const double u2 = orc_uniform(sobol_word(V + (size_t)(2 * jn + 1) * 32, (uint64_t)(n0 + i)) ^ shift[2 * jn + 1]);
+                z[a] = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            }
+            for (int a = 0; a < d; ++a) {
+                double acc = 0.0;
+                for (int k = 0; k <= a; ++k) acc += m.Lrho[(size_t)a * d + k] * z[k];
+                y[a] = acc;
+            }
+            u = 0.0;
+            for (int a = 0; a < d; ++a) {
+                const double dW = sdt * sig[a] * y[a];
+                if (scheme == 0) x[a] += (r - 0.5 * sig[a] * sig[a]) * dt + dW;
+                else x[a] *= 1.0 + r * dt + dW;
+                u += w[a] * ((scheme == 0) ? exp(x[a]) : x[a]);
+            }
+            sum += u;
+            if (u > umax) umax = u;
+            if (u < umin) umin = u;
+        }
+        orc_pathstats ps;
+        ps.u_T = u; ps.avg = sum / steps; ps.umax = umax; ps.umin = umin;
+        for (int p = 0; p < npay; ++p) out[(size_t)p * npts + i] = disc * payoff_value(kind[p], strike[p], barrier[p], &ps);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
 /* Materialised paths: save[(slot*d + a)*npaths + n] = S_a at step slot*save_every
  * (slot 0 is t_0), for n in [0, npaths), path index path0 + n. */
 int orc_gbm_paths(int d, const double *s0, const double *sig, const double *corr, const double *w,

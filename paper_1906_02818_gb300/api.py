@@ -107,6 +107,19 @@ def price_mlmc(model: dict, cfg: dict, payoffs, paths_ref: int, stream=None):
                  coarse_level=(r.coarse_level.price, r.coarse_level.se)) for r in out]
 
 
+def price_qmc(model: dict, cfg: dict, payoffs, replications: int = 16, stream=None):
+    """Randomised Sobol quasi-Monte Carlo (mc_price_qmc): cfg["paths"] points
+    per replication.  Returns (list of (price, se), replication means
+    [replications, n_payoff])."""
+    L = native.lib()
+    mm = _Marshalled(model, cfg, payoffs)
+    out = (McResult * mm.n_payoff)()
+    reps = np.zeros((replications, mm.n_payoff))
+    check(L.mc_price_qmc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, int(replications),
+                         out, reps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)))
+    return [(r.price, r.se) for r in out], reps
+
+
 def greeks(model: dict, cfg: dict, payoffs, stream=None):
     """Pathwise Greeks: (prices, greeks) with prices a list of (price, se) and
     greeks an array [n_payoff, G, 2] of (mean, se); G = 7 for Heston

@@ -203,11 +203,13 @@ struct mc_plan {
     float *dLp = nullptr, *ddrift = nullptr;
     int *dstatus = nullptr;
     float *ckpt = nullptr;
+    double *dsums = nullptr;
 
     ~mc_plan()
     {
         dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
         dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err); dfree(ckpt); dfree(dcol);
+        dfree(dsums);
     }
 };
 
@@ -824,6 +826,112 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
         o.coarse_level = lv[2 * np + p];
         o.price = coarse[p].price + lv[p].price;
         o.se = std::sqrt(coarse[p].se * coarse[p].se + lv[p].se * lv[p].se);
+    }
+    return MC_OK;
+}
+
+int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, int32_t reps,
+                 mc_result *out, double *rep_means, void *stream)
+{
+    int rc;
+    if (!out) return fail(MC_EINVAL, "out is NULL");
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
+    if (m->kind != MC_GBM || m->d > kQmcMaxAssets)
+        return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: GBM with d <= %d", kQmcMaxAssets);
+    if (2 * m->d * c->steps > kQmcMaxDims)
+        return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: 2 d steps = %d exceeds %d Sobol dimensions",
+                    2 * m->d * c->steps, kQmcMaxDims);
+    if (c->precision != MC_FP32 || c->monitoring != MC_DISCRETE)
+        return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: FP32 contraction and discrete monitoring");
+    if (c->path_offset + c->paths > (int64_t(1) << 23))
+        return fail(MC_EINVAL, "quasi-Monte Carlo: points must lie in [0, 2^23) (23-bit uniforms)");
+    if (reps < 2 || reps > 65535) return fail(MC_EINVAL, "replications = %d outside [2, 65535]", reps);
+    if (np < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
+    PayoffSet ps;
+    if ((rc = build_payoffs(pays, np, &ps))) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    const int d = m->d;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
+    const size_t dd = static_cast<size_t>(d) * d, tri = static_cast<size_t>(d) * (d + 1) / 2;
+    mc_plan P;  // owns the scratch buffers (freed on return)
+    MC_CUDA(cudaMalloc(&P.dcorr, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dL, dd * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dsig, d * sizeof(double)));
+    MC_CUDA(cudaMalloc(&P.dLp, tri * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.ddrift, d * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P.dstatus, sizeof(int)));
+    std::vector<double> corr(dd, 0.0);
+    if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+    else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
+    MC_CUDA(cudaMemcpyAsync(P.dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(P.dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_cholesky(d, P.dcorr, P.dL, P.dstatus, s));
+    MC_CUDA(launch_scale_factor(d, P.dL, P.dsig, cfac, sdt, m->r, dt, c->scheme, P.dLp, P.ddrift, s));
+    std::vector<float> Lp(tri), drift(d);
+    int status = 0;
+    MC_CUDA(cudaMemcpyAsync(&status, P.dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(Lp.data(), P.dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(drift.data(), P.ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+    QmcConst k;
+    std::memset(&k, 0, sizeof k);
+    const int ndim = 2 * d * c->steps;
+    qmc_directions(ndim, k.V);
+    for (int a = 0; a < kQmcMaxAssets; ++a) {
+        if (a < d) {
+            for (int j = 0; j <= a; ++j) k.L[a * (a + 1) / 2 + j] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + j];
+            const double w = m->weights ? m->weights[a] : 1.0 / d;
+            k.drift[a] = drift[a];
+            k.ws0[a] = static_cast<float>(w * m->s0[a]);
+            k.w[a] = static_cast<float>(w);
+            k.s0[a] = static_cast<float>(m->s0[a]);
+        } else {
+            k.s0[a] = 1.0f;  // padded columns: zero weight, inert state
+        }
+    }
+    QmcArgs a{};
+    a.n0 = c->path_offset;
+    a.npts = c->paths;
+    a.steps = c->steps;
+    a.d = d;
+    a.scheme = c->scheme;
+    a.ndim = ndim;
+    a.reps = reps;
+    a.k0 = static_cast<uint32_t>(c->seed);
+    a.k1 = static_cast<uint32_t>(c->seed >> 32);
+    a.pay = ps;
+    MC_CUDA(cudaMalloc(&P.dsums, static_cast<size_t>(reps) * np * sizeof(double)));
+    MC_CUDA(cudaMemsetAsync(P.dsums, 0, static_cast<size_t>(reps) * np * sizeof(double), s));
+    a.sums = P.dsums;
+    const int occ = qmc_occupancy(a);
+    if (occ <= 0) return fail(MC_ECUDA, "quasi-Monte Carlo kernel cannot be resident");
+    const int64_t blocks = (c->paths + qmc_block() - 1) / qmc_block();
+    const int64_t per_rep = std::max<int64_t>(1, static_cast<int64_t>(occ) * di.sms / reps);
+    const int grid = static_cast<int>(std::min<int64_t>(blocks, std::max<int64_t>(per_rep, 1)));
+    MC_CUDA(launch_qmc(a, k, grid, s));
+    std::vector<double> sums(static_cast<size_t>(reps) * np);
+    MC_CUDA(cudaMemcpyAsync(sums.data(), P.dsums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    const double disc = std::exp(-m->r * c->T), N = static_cast<double>(c->paths);
+    for (int p = 0; p < np; ++p) {
+        double mean = 0.0, m2 = 0.0;
+        for (int r = 0; r < reps; ++r) {
+            const double v = disc * sums[static_cast<size_t>(r) * np + p] / N;
+            if (rep_means) rep_means[static_cast<size_t>(r) * np + p] = v;
+            mean += v;
+        }
+        mean /= reps;
+        for (int r = 0; r < reps; ++r) {
+            const double v = disc * sums[static_cast<size_t>(r) * np + p] / N - mean;
+            m2 += v * v;
+        }
+        out[p].price = mean;
+        out[p].se = std::sqrt(m2 / (reps - 1) / reps);
     }
     return MC_OK;
 }

@@ -160,6 +160,31 @@ cudaError_t launch_mlmc_coupled(int prec, const MlmcArgs &a, const MlmcConst &c,
 int mlmc_occupancy(int prec, const MlmcArgs &a);
 int mlmc_block();
 
+// Randomised quasi-Monte Carlo (k_qmc.cu): Sobol direction words of up to
+// kQmcMaxDims dimensions, the FP32 factor Lhat (packed, rows of width
+// kQmcMaxAssets) and the basket constants; d <= 32 and 2 d M <= 64.
+constexpr int kQmcMaxDims = 64;
+constexpr int kQmcMaxAssets = 32;
+struct QmcConst {
+    uint32_t V[kQmcMaxDims][32];
+    float L[kQmcMaxAssets * (kQmcMaxAssets + 1) / 2];
+    float drift[kQmcMaxAssets];
+    float ws0[kQmcMaxAssets];
+    float w[kQmcMaxAssets];
+    float s0[kQmcMaxAssets];
+};
+struct QmcArgs {
+    int64_t n0, npts;   // first point index, points per replication
+    int steps, d, scheme, ndim, reps;
+    uint32_t k0, k1;    // Philox key of the digital shifts
+    PayoffSet pay;
+    double *sums;       // [reps][n_payoff] undiscounted payoff totals (zero on entry)
+};
+void qmc_directions(int ndim, uint32_t (*V)[32]);
+cudaError_t launch_qmc(const QmcArgs &a, const QmcConst &c, int grid, cudaStream_t s);
+int qmc_occupancy(const QmcArgs &a);
+int qmc_block();
+
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
 // Polls of a bounded mbarrier wait before a tensor-core kernel gives up.

@@ -86,6 +86,9 @@ SIGNATURES = [
                                 ctypes.c_int32, ctypes.POINTER(McResult), ctypes.c_void_p]),
     ("mc_price_mlmc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
                                      ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(McMlmcResult), ctypes.c_void_p]),
+    ("mc_price_qmc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(McResult),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("mc_greek_count", ctypes.c_int32, [ctypes.POINTER(McModel)]),
     ("mc_greeks", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
                                  ctypes.c_int32, ctypes.POINTER(McResult), ctypes.POINTER(McResult),

@@ -4,7 +4,7 @@ the error against the FP64 oracle on the same random stream (on a path
 prefix the oracle finishes quickly), and the oracle's own throughput on the
 host cores.
 
-  python -m paper_1906_02818_gb300.report [--only gbm1d,bridge,basket64,mlmc,heston,basket512,risk]
+  python -m paper_1906_02818_gb300.report [--only gbm1d,bridge,basket64,mlmc,qmc,heston,basket512,risk]
          [--reps 20] [--oracle-paths N]
 
 Device times are CUDA events around mc_plan_execute (inputs resident, the
@@ -144,6 +144,30 @@ def run_mlmc(torch, gb, orc, a):
     return out
 
 
+def run_qmc(torch, gb, orc, a):
+    """Randomised Sobol QMC vs Philox Monte Carlo on the 16-asset one-step
+    basket call (Sec. VI.D): standard error and time at equal point counts."""
+    import workloads
+    s0, sg, corr = workloads.basket_market(16, 4)
+    w = np.full(16, 1.0 / 16)
+    model = dict(kind="gbm", s0=s0, sigma=sg, corr=corr, weights=w, r=0.05)
+    pays = [dict(kind="call", strike=float(w @ s0))]
+    out = dict(workload="16-asset basket call, one step, randomised Sobol (32 dims) vs Philox", points={})
+    for m in (12, 16, 20):
+        cfg = dict(steps=1, T=1.0, paths=1 << m, seed=42)
+        gb.price_qmc(model, cfg, pays, replications=16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (q,), _ = gb.price_qmc(model, cfg, pays, replications=16)
+        tq = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        (mc,) = gb.price(model, dict(cfg, paths=16 << m), pays)
+        tm = time.perf_counter() - t0
+        out["points"][m] = dict(qmc=q, qmc_seconds=tq, mc_same_total_points=mc, mc_seconds=tm,
+                                se_ratio_mc_over_qmc=mc[1] / q[1])
+    return out
+
+
 def run_heston(torch, gb, orc, a):
     import workloads
     w = workloads.heston()
@@ -215,13 +239,13 @@ def main():
     import oracle
     import paper_1906_02818_gb300 as gb
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", default="gbm1d,bridge,basket64,mlmc,heston,basket512,risk")
+    ap.add_argument("--only", default="gbm1d,bridge,basket64,mlmc,qmc,heston,basket512,risk")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--oracle-paths", type=int, default=0)
     a = ap.parse_args()
     oracle.build()
-    runs = dict(gbm1d=run_gbm1d, bridge=run_bridge, basket64=run_basket64, mlmc=run_mlmc, heston=run_heston,
-                basket512=run_basket512, risk=run_risk)
+    runs = dict(gbm1d=run_gbm1d, bridge=run_bridge, basket64=run_basket64, mlmc=run_mlmc, qmc=run_qmc,
+                heston=run_heston, basket512=run_basket512, risk=run_risk)
     for name in a.only.split(","):
         out = runs[name](torch, gb, oracle, a)
         out["name"] = name

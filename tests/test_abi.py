@@ -124,3 +124,18 @@ def test_two_level_estimator_checks(lib):
         assert rc == code, (over, np_, ref)
         assert needle in lib.mc_last_error().decode()
     assert lib.mc_price_mlmc(None, None, None, 1, 64, out, None) == native.MC_EINVAL
+
+
+def test_quasi_monte_carlo_checks(lib):
+    from paper_1906_02818_gb300 import native
+    out = (native.McResult * 2)()
+    for over, reps, code, needle in [(dict(d=33), 8, native.MC_EUNSUPPORTED, "d <= 32"),
+                                     (dict(d=4, steps=9), 8, native.MC_EUNSUPPORTED, "Sobol dimensions"),
+                                     (dict(d=4), 1, native.MC_EINVAL, "replications"),
+                                     (dict(d=4, paths=1 << 23, path_offset=1), 8, native.MC_EINVAL, "2^23"),
+                                     (dict(d=4, precision="bf16"), 8, native.MC_EUNSUPPORTED, "FP32")]:
+        mm = _structs(**over)
+        rc = lib.mc_price_qmc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, reps, out,
+                              None, None)
+        assert rc == code, over
+        assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())

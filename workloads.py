@@ -40,6 +40,29 @@ def basket_market(d: int, k: int, seed: int = SEED):
     return s0, sigma, corr
 
 
+def basket_market_factors(d: int, k: int, seed: int = SEED, ridge: float = 0.05):
+    """The market of basket_market(d, k, seed) (same draws, same order) with
+    its correlation given by factor loadings: rho = B B^T + diag(e^2),
+    B_aj = F_aj / sqrt(k C_aa), e_a^2 = ridge / C_aa, C = F F^T / k + ridge I.
+    Returns (s0, sigma, B [d, k])."""
+    rng = np.random.default_rng(seed)
+    s0 = rng.uniform(50.0, 150.0, size=d)
+    sigma = rng.uniform(0.1, 0.4, size=d)
+    F = rng.standard_normal((d, k))
+    caa = (F * F).sum(axis=1) / k + ridge
+    return s0, sigma, F / np.sqrt(k * caa)[:, None]
+
+
+def basket_d512_factor(paths: int = 1 << 20, steps: int = 252, d: int = 512, k: int = 16):
+    """The d = 512 market of basket_d512 with its 16-factor correlation given
+    by loadings (factor-model simulation): ATM arithmetic basket call."""
+    s0, sigma, B = basket_market_factors(d, k)
+    w = np.full(d, 1.0 / d)
+    b0 = float(w @ s0)
+    return dict(s0=s0, sigma=sigma, loadings=B, weights=w, r=0.05, T=1.0, steps=steps, paths=paths, seed=SEED,
+                payoffs=[dict(kind="call", strike=b0)])
+
+
 def gbm_1d(paths: int = 1 << 20, steps: int = 64):
     """Single-asset Black-Scholes GBM, European call at the money."""
     return dict(s0=np.array([100.0]), sigma=np.array([0.2]), corr=None, r=0.05, T=1.0,
