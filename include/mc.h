@@ -78,6 +78,17 @@ typedef struct {
     double r;              /* risk-free rate: drift of every asset and discount rate */
     double v0, kappa, theta, xi, rho; /* MC_HESTON only: dv = kappa (theta - v) dt + xi sqrt(v) dW1,
                                          d<W1, W2> = rho dt, |rho| < 1 */
+    /* Factor-model correlation (MC_GBM, corr must be NULL): rho = B B^T +
+     * diag(e^2), B = loadings (host [d][n_factors] row-major, every row norm
+     * <= 1), e_a = sqrt(1 - sum_j B_aj^2).  Step i of path n then draws
+     * normals i (k + d) + j (j < k, common factors z) and i (k + d) + k + a
+     * (idiosyncratic eps_a) and uses dW_a = sqrt(dt) sigma_a (sum_j B_aj z_j
+     * + e_a eps_a): O(d k) per step instead of the Cholesky O(d^2), exact in
+     * law.  d <= 512, n_factors <= 16, FP32, European / Asian / barrier
+     * payoffs; no Greeks, paths, two-level or QMC runs.  loadings NULL: the
+     * Cholesky scheme. */
+    int32_t n_factors;
+    const double *loadings;
 } mc_model;
 
 /* Barrier monitoring.  MC_DISCRETE: the barrier is checked at t_1..t_M.

@@ -3,7 +3,7 @@
 PyTorch provides device memory and streams; every simulation step runs in the
 library's CUDA kernels.  Model and configuration are plain keyword arguments:
 
-  model:  kind="gbm", s0, sigma, corr=None, weights=None, r
+  model:  kind="gbm", s0, sigma, corr=None, weights=None, r, loadings=None ([d, k] factor model)
           kind="heston", s0, v0, r, kappa, theta, xi, rho
   cfg:    steps, T, paths, seed=42, scheme="log_euler", precision="fp32",
           path_offset=0, ckpt_every=0, monitoring="discrete" | "bridge"
@@ -36,6 +36,10 @@ class _Marshalled:
                 m.corr = self._ptr(self._arr(model["corr"]))
             if model.get("weights") is not None:
                 m.weights = self._ptr(self._arr(model["weights"]))
+            if model.get("loadings") is not None:
+                B = self._arr(np.asarray(model["loadings"], dtype=np.float64).reshape(m.d, -1))
+                m.n_factors = B.shape[1]
+                m.loadings = self._ptr(B) if B.size else self._ptr(self._arr(np.zeros(1)))
         else:
             for k in ("v0", "kappa", "theta", "xi", "rho"):
                 setattr(m, k, float(model[k]))

@@ -61,8 +61,8 @@ extern "C" int mc_price_gbm1d_noalloc(const mc_model *m, const mc_sim_cfg *c, co
 {
     using namespace gbmc;
     if (!m || !c || !p || !dev_out) return noalloc_fail(MC_EINVAL, "NULL argument");
-    if (m->kind != MC_GBM || m->d != 1 || !m->s0 || !m->sigma)
-        return noalloc_fail(MC_EINVAL, "single-asset GBM only (kind MC_GBM, d = 1, s0 and sigma set)");
+    if (m->kind != MC_GBM || m->d != 1 || !m->s0 || !m->sigma || m->loadings)
+        return noalloc_fail(MC_EINVAL, "single-asset GBM only (kind MC_GBM, d = 1, s0 and sigma set, no loadings)");
     if (n_payoff < 1 || n_payoff > MC_MAX_PAYOFFS)
         return noalloc_fail(MC_EINVAL, "n_payoff = %d outside [1, %d]", n_payoff, MC_MAX_PAYOFFS);
     if (c->steps < 1 || !(c->T > 0.0) || c->paths < 1 || c->path_offset < 0 ||

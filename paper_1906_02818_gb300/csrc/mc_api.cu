@@ -55,6 +55,7 @@ int check_model(const mc_model *m)
         if (!(m->s0[a] > 0.0) || !std::isfinite(m->s0[a])) return fail(MC_EINVAL, "s0[%d] must be finite and > 0", a);
     if (m->kind == MC_HESTON) {
         if (m->d != 1) return fail(MC_EINVAL, "Heston requires d == 1");
+        if (m->loadings || m->corr) return fail(MC_EINVAL, "Heston takes no correlation or loadings");
         const double v[5] = {m->v0, m->kappa, m->theta, m->xi, m->rho};
         if (!finite_all(v, 5)) return fail(MC_EINVAL, "Heston parameters must be finite");
         if (m->v0 < 0 || m->kappa < 0 || m->theta < 0 || m->xi < 0)
@@ -66,6 +67,19 @@ int check_model(const mc_model *m)
     for (int a = 0; a < m->d; ++a)
         if (!(m->sigma[a] >= 0.0) || !std::isfinite(m->sigma[a])) return fail(MC_EINVAL, "sigma[%d] must be finite and >= 0", a);
     if (m->weights && !finite_all(m->weights, m->d)) return fail(MC_EINVAL, "weights must be finite");
+    if (m->loadings) {
+        const int d = m->d, k = m->n_factors;
+        if (m->corr) return fail(MC_EINVAL, "give either corr or loadings, not both");
+        if (k < 0 || k > kFactorMax) return fail(MC_EUNSUPPORTED, "n_factors = %d outside [0, %d]", k, kFactorMax);
+        if (d > kFactorMaxD) return fail(MC_EUNSUPPORTED, "factor model: d = %d exceeds %d", d, kFactorMaxD);
+        if (!finite_all(m->loadings, static_cast<int64_t>(d) * k)) return fail(MC_EINVAL, "loadings must be finite");
+        for (int i = 0; i < d; ++i) {
+            double q = 0.0;
+            for (int j = 0; j < k; ++j) q += m->loadings[static_cast<int64_t>(i) * k + j] * m->loadings[static_cast<int64_t>(i) * k + j];
+            if (q > 1.0 + 1e-12) return fail(MC_EINVAL, "loadings row %d has norm^2 %g > 1", i, q);
+        }
+        return MC_OK;
+    }
     if (m->corr) {
         const int d = m->d;
         if (!finite_all(m->corr, static_cast<int64_t>(d) * d)) return fail(MC_EINVAL, "corr must be finite");
@@ -96,9 +110,10 @@ int check_cfg(const mc_sim_cfg *c, const mc_model *m)
     if (c->ckpt_every < 0) return fail(MC_EINVAL, "ckpt_every must be >= 0");
     if (m->kind == MC_HESTON && c->precision != MC_FP32)
         return fail(MC_EINVAL, "Heston has no correlation contraction: precision must be MC_FP32");
+    if (m->loadings && c->precision != MC_FP32) return fail(MC_EUNSUPPORTED, "factor model: FP32 only");
     if (c->monitoring != MC_DISCRETE && c->monitoring != MC_BRIDGE)
         return fail(MC_EINVAL, "unknown monitoring %d", c->monitoring);
-    if (c->monitoring == MC_BRIDGE && (m->kind != MC_GBM || m->d != 1 || c->scheme != MC_LOG_EULER))
+    if (c->monitoring == MC_BRIDGE && (m->kind != MC_GBM || m->d != 1 || c->scheme != MC_LOG_EULER || m->loadings))
         return fail(MC_EUNSUPPORTED, "Brownian-bridge monitoring: single-asset GBM with MC_LOG_EULER only");
     return MC_OK;
 }
@@ -177,7 +192,7 @@ int gbmc::set_last_error(int code, const char *msg)
     return code;
 }
 
-enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3, K_BASKET_BIG = 4 };
+enum KernelKind { K_GBM1D = 0, K_BASKET_FP32 = 1, K_HESTON = 2, K_BASKET_TC = 3, K_BASKET_BIG = 4, K_FACTOR = 5 };
 
 struct mc_plan {
     int device = -1;
@@ -191,7 +206,8 @@ struct mc_plan {
     TcArgs tc{};
     TcConst tcc{};
     BigArgs bg{};
-    float *dcol = nullptr;  // large baskets: per-column float arrays
+    FactorArgs fa{};
+    float *dcol = nullptr;  // large baskets and factor models: per-column float arrays
     int prec = MC_FP32;
     uint8_t *bimg = nullptr;
     unsigned int *err = nullptr;
@@ -305,6 +321,68 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
     return MC_OK;
 }
 
+// Factor-model basket: B', e', drift and the basket columns in FP64 on the
+// host, padded to 256 G assets, then one upload.
+int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSet &ps, const PathRun &run,
+                 const ReduceArgs &red, const DeviceInfo &di, cudaStream_t s)
+{
+    const int d = m->d, k = m->n_factors, G = (d + 255) / 256, dp = 256 * G;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt);
+    const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
+    std::vector<float> h(static_cast<size_t>(k + 6) * dp, 0.0f);
+    float *Bp = h.data(), *ep = Bp + static_cast<size_t>(k) * dp, *dr = ep + dp, *ws0 = dr + dp, *w = ws0 + dp,
+          *s0 = w + dp;
+    for (int a = 0; a < dp; ++a) s0[a] = 1.0f;  // padded assets: inert
+    for (int a = 0; a < d; ++a) {
+        const double sg = m->sigma[a], cs = cfac * sdt * sg;
+        double q = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const double b = m->loadings[static_cast<int64_t>(a) * k + j];
+            q += b * b;
+            Bp[static_cast<size_t>(j) * dp + a] = static_cast<float>(cs * b);
+        }
+        ep[a] = static_cast<float>(cs * std::sqrt(std::max(0.0, 1.0 - q)));
+        dr[a] = static_cast<float>(c->scheme == MC_LOG_EULER ? cfac * (m->r - 0.5 * sg * sg) * dt : m->r * dt);
+        const double wa = m->weights ? m->weights[a] : 1.0 / d;
+        ws0[a] = static_cast<float>(wa * m->s0[a]);
+        w[a] = static_cast<float>(wa);
+        s0[a] = static_cast<float>(m->s0[a]);
+    }
+    MC_CUDA(cudaMalloc(&P->dcol, h.size() * sizeof(float)));
+    MC_CUDA(cudaMemcpyAsync(P->dcol, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    P->kk = K_FACTOR;
+    FactorArgs &f = P->fa;
+    f.run = run;
+    f.d = d;
+    f.k = k;
+    f.G = G;
+    f.scheme = c->scheme;
+    f.exact4 = (k % 4 == 0 && d % 4 == 0) ? 1 : 0;
+    f.Bp = P->dcol;
+    f.ep = P->dcol + static_cast<size_t>(k) * dp;
+    f.drift = f.ep + dp;
+    f.ws0 = f.drift + dp;
+    f.w = f.ws0 + dp;
+    f.s0 = f.w + dp;
+    f.pay = ps;
+    f.red = red;
+    const int occ = factor_occupancy(f);
+    if (occ <= 0) return fail(MC_ECUDA, "factor-model kernel cannot be resident");
+    const int per = factor_paths_per_cta(f);
+    const int64_t tiles = (c->paths + per - 1) / per;
+    P->grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(occ) * di.sms));
+    P->block = 256;
+    const int np = ps.n;
+    MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
+    MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+    MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
+    f.red.partials = P->partials;
+    f.red.ticket = P->ticket;
+    f.red.out = P->dout;
+    return MC_OK;
+}
+
 // Shared set-up of mc_plan_create and mc_simulate.  save != nullptr selects
 // the materialising kernels (no payoffs, no reduction).
 int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int np,
@@ -351,6 +429,10 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         h.pay = ps;
         h.red = red;
         resident = heston_occupancy(h, P->block) * di.sms;
+    } else if (m->loadings) {
+        if (save) return fail(MC_EUNSUPPORTED, "factor model: paths are not materialised");
+        if (np < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
+        return factor_setup(P, m, c, ps, run, red, di, s);
     } else if (m->d == 1) {
         P->kk = K_GBM1D;
         if (m->corr && std::fabs(m->corr[0] - 1.0) > 1e-12) return fail(MC_EINVAL, "corr[0] must be 1");
@@ -515,6 +597,10 @@ int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
         P->bg.out = dev_out ? dev_out : P->dout;
         MC_CUDA(launch_basket_big(P->prec, P->bg, P->grid, s));
         break;
+    case K_FACTOR:
+        P->fa.red.out = dev_out ? dev_out : P->dout;
+        MC_CUDA(launch_factor(P->fa, P->grid, s));
+        break;
     }
     return MC_OK;
 }
@@ -607,6 +693,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     if (!greeks) return fail(MC_EINVAL, "greeks is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
     if (np < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
+    if (m->loadings) return fail(MC_EUNSUPPORTED, "factor model: no pathwise Greeks");
     PayoffSet ps;
     if ((rc = build_payoffs(pays, np, &ps))) return rc;
     for (int i = 0; i < np; ++i)
@@ -722,8 +809,9 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     int rc;
     if (!out) return fail(MC_EINVAL, "out is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
-    if (m->kind != MC_GBM || m->d < 2 || m->d > 64)
-        return fail(MC_EUNSUPPORTED, "two-level precision estimator: correlated GBM baskets with 2 <= d <= 64");
+    if (m->kind != MC_GBM || m->d < 2 || m->d > 64 || m->loadings)
+        return fail(MC_EUNSUPPORTED, "two-level precision estimator: correlated GBM baskets with 2 <= d <= 64 "
+                                     "(Cholesky correlation)");
     if (c->precision == MC_FP32) return fail(MC_EINVAL, "the coarse level needs a reduced precision (BF16, FP16, E4M3)");
     if (c->monitoring != MC_DISCRETE) return fail(MC_EUNSUPPORTED, "two-level estimator: discrete monitoring only");
     if (np < 1 || np > kMlmcMaxPayoffs) return fail(MC_EINVAL, "n_payoff = %d outside [1, %d]", np, kMlmcMaxPayoffs);
@@ -836,8 +924,8 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
     int rc;
     if (!out) return fail(MC_EINVAL, "out is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
-    if (m->kind != MC_GBM || m->d > kQmcMaxAssets)
-        return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: GBM with d <= %d", kQmcMaxAssets);
+    if (m->kind != MC_GBM || m->d > kQmcMaxAssets || m->loadings)
+        return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: GBM with d <= %d (Cholesky correlation)", kQmcMaxAssets);
     if (2 * m->d * c->steps > kQmcMaxDims)
         return fail(MC_EUNSUPPORTED, "quasi-Monte Carlo: 2 d steps = %d exceeds %d Sobol dimensions",
                     2 * m->d * c->steps, kQmcMaxDims);

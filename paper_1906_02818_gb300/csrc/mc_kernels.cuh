@@ -185,6 +185,25 @@ cudaError_t launch_qmc(const QmcArgs &a, const QmcConst &c, int grid, cudaStream
 int qmc_occupancy(const QmcArgs &a);
 int qmc_block();
 
+// Factor-model GBM basket (k_factor.cu): device arrays padded to 256 G
+// assets (G = ceil(d / 256) warps per 4 paths): B' [k][256 G] =
+// c sqrt(dt) sigma_a B_aj, e' = c sqrt(dt) sigma_a e_a, drift, w S0, w, S0
+// (padded assets: zero B', e', weights; S0 = 1).
+constexpr int kFactorMax = 16;
+constexpr int kFactorMaxD = 512;
+struct FactorArgs {
+    PathRun run;
+    int d, k, G, scheme;
+    int exact4;  // k % 4 == 0 and d % 4 == 0: aligned Philox blocks
+    const float *Bp, *ep, *drift, *ws0, *w, *s0;
+    PayoffSet pay;
+    ReduceArgs red;
+};
+size_t factor_smem_bytes(const FactorArgs &a);
+cudaError_t launch_factor(const FactorArgs &a, int grid, cudaStream_t s);
+int factor_occupancy(const FactorArgs &a);
+int factor_paths_per_cta(const FactorArgs &a);
+
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
 // Polls of a bounded mbarrier wait before a tensor-core kernel gives up.

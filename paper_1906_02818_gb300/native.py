@@ -32,7 +32,8 @@ class McModel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("s0", c_double_p), ("sigma", c_double_p), ("corr", c_double_p), ("weights", c_double_p),
                 ("r", ctypes.c_double), ("v0", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("theta", ctypes.c_double), ("xi", ctypes.c_double), ("rho", ctypes.c_double)]
+                ("theta", ctypes.c_double), ("xi", ctypes.c_double), ("rho", ctypes.c_double),
+                ("n_factors", ctypes.c_int32), ("loadings", c_double_p)]
 
 
 class McSimCfg(ctypes.Structure):

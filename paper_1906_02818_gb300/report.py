@@ -211,6 +211,15 @@ def run_basket512(torch, gb, orc, a):
     m_or, se_or = orc.mean_se(ref[0])
     out = dict(workload="basket d=512, 2^20 paths x 252 steps, ATM call + 512-delta", precisions={},
                oracle_prefix_paths=n_or, oracle_path_steps_per_s=n_or * w["steps"] / t_orc)
+    wf = workloads.basket_d512_factor()
+    fmodel = dict(kind="gbm", s0=wf["s0"], sigma=wf["sigma"], loadings=wf["loadings"], weights=wf["weights"], r=wf["r"])
+    fcfg = dict(steps=wf["steps"], T=wf["T"], paths=wf["paths"], seed=wf["seed"])
+    t, res = _plan_time(torch, gb, fmodel, fcfg, wf["payoffs"], a.reps)
+    fref = orc.gbm_factor_payoffs(wf["s0"], wf["sigma"], wf["loadings"], wf["r"], wf["T"], wf["steps"], n_or,
+                                  wf["payoffs"], weights=wf["weights"])
+    fsmall = gb.price(fmodel, dict(fcfg, paths=n_or), wf["payoffs"])
+    out["factor_model_fp32"] = dict(seconds=t, path_steps_per_s=wf["paths"] * wf["steps"] / t, price=float(res[0, 0]),
+                                    std_err=float(res[0, 1]), rel_err_vs_oracle_prefix=_rel(fsmall[0][0], fref[0].mean()))
     for prec in ("bf16", "fp8", "fp16", "fp32"):
         cfg = dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=w["seed"], precision=prec)
         reps = a.reps if prec != "fp32" else 1

@@ -44,7 +44,8 @@ def _structs(kind="gbm", d=1, **over):
         model = dict(kind="gbm", s0=np.full(d, 100.0), sigma=np.full(d, 0.2), r=0.05)
     else:
         model = dict(kind="heston", s0=100.0, v0=0.04, r=0.05, kappa=2.0, theta=0.04, xi=0.5, rho=-0.7)
-    model.update({k: v for k, v in over.items() if k in ("s0", "sigma", "corr", "weights", "r", "rho", "xi", "v0")})
+    model.update({k: v for k, v in over.items()
+                  if k in ("s0", "sigma", "corr", "weights", "r", "rho", "xi", "v0", "loadings")})
     cfg = dict(steps=4, T=1.0, paths=16)
     cfg.update({k: v for k, v in over.items()
                 if k in ("steps", "T", "paths", "scheme", "precision", "path_offset", "monitoring")})
@@ -137,5 +138,22 @@ def test_quasi_monte_carlo_checks(lib):
         mm = _structs(**over)
         rc = lib.mc_price_qmc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, reps, out,
                               None, None)
+        assert rc == code, over
+        assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
+
+
+def test_factor_model_checks(lib):
+    from paper_1906_02818_gb300 import native
+    out = (native.McResult * 1)()
+    d = 4
+    good = np.full((d, 2), 0.5)
+    for over, code, needle in [
+            (dict(d=d, loadings=good, corr=np.eye(d)), native.MC_EINVAL, "either corr or loadings"),
+            (dict(d=d, loadings=np.full((d, 17), 0.1)), native.MC_EUNSUPPORTED, "n_factors"),
+            (dict(d=d, loadings=np.full((d, 2), 0.8)), native.MC_EINVAL, "norm"),
+            (dict(d=513, loadings=np.full((513, 2), 0.1)), native.MC_EUNSUPPORTED, "exceeds 512"),
+            (dict(d=d, loadings=good, precision="bf16"), native.MC_EUNSUPPORTED, "FP32")]:
+        mm = _structs(**over)
+        rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
         assert rc == code, over
         assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
