@@ -291,6 +291,10 @@ int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_
                      float *host_grad, void *stream);
 int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, int32_t epochs, int32_t batch,
                  float lr, double *last_epoch_loss, void *stream);
+/* One Adam step (the update of mc_mlp_train) with a given gradient: host_grad
+ * [mc_mlp_param_count] host floats, e.g. the average of the ranks' batch
+ * gradients in data-parallel training.  Synchronises `stream`. */
+int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *stream);
 int mc_mlp_destroy(mc_mlp *net);
 
 /*
@@ -338,6 +342,10 @@ typedef struct {
     uint64_t seed;
     mc_mlp *surrogate;       /* surrogate: the trained network */
     int32_t surrogate_precision; /* MC_FP32 or MC_BF16 */
+    int64_t scen_offset;     /* global index of the first scenario: a run over
+                                [scen_offset, scen_offset + n_scen) reproduces that
+                                slice of a run from 0 (sharding across devices);
+                                VaR / CVaR are those of this slice */
 } mc_risk_cfg;
 
 typedef struct {

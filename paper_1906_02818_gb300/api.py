@@ -249,6 +249,12 @@ class Mlp:
                                      _stream_handle(stream)))
         return loss.value
 
+    def apply_grad(self, g, lr, stream=None):
+        """One Adam step with the given packed gradient (host array)."""
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        check(self._lib.mc_mlp_apply_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(lr),
+                                          _stream_handle(stream)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.mc_mlp_destroy(self._h)
@@ -280,8 +286,9 @@ def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None, wi
 
 
 def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_paths=1 << 12, base_paths=1 << 16,
-         seed=42, surrogate=None, surrogate_precision="fp32", want_pnl=False, stream=None):
-    """VaR / CVaR of the portfolio (see mc_risk); returns a dict."""
+         seed=42, surrogate=None, surrogate_precision="fp32", want_pnl=False, scen_offset=0, stream=None):
+    """VaR / CVaR of the portfolio (see mc_risk) over scenarios
+    [scen_offset, scen_offset + n_scen); returns a dict."""
     L = native.lib()
     keep = []
 
@@ -311,6 +318,7 @@ def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_pat
     cf.inner_paths, cf.base_paths, cf.seed = int(inner_paths), int(base_paths), int(seed)
     cf.surrogate = surrogate.handle if surrogate is not None else None
     cf.surrogate_precision = native.PRECISION[surrogate_precision]
+    cf.scen_offset = int(scen_offset)
     res = native.McRiskResult()
     pnl = np.empty(int(n_scen)) if want_pnl else None
     check(L.mc_risk(ctypes.byref(pf), ctypes.byref(cf), ctypes.byref(res),

@@ -289,6 +289,127 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
     block_finish(s_acc, s_red, a.pay.n, a.red);
 }
 
+// Log-Euler with BF16 / FP16 operands: the running correlated increment
+// D = sum_{steps <= i} Z Lq^T accumulates in TMEM across the steps (each
+// step's MMA adds into it), so a thread keeps no per-asset state:
+// log2(S_n(t_{i+1}) / S0_n) = (i + 1) drift_n + cs_n D_n is formed when a
+// monitored statistic needs it and once at maturity.  One Z buffer; the
+// small per-CTA footprint (64 TMEM columns, ~28 KB of shared memory, <= 64
+// registers) lets 8 CTAs share an SM, which hides each CTA's MMA wait behind
+// the others' normals.  Bounded waits as in basket_tc_kernel.
+template <int PREC, bool STATS, bool EXACT>
+__global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const TcArgs a, const TcConst c)
+{
+    using Ly = Layout<PREC>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ float s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ double s_red[32];
+
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t zt = base, bt = base + Ly::kTileBytes;
+    const uint32_t mbar = bt + Ly::kBBytes, tslot = mbar + 16;
+    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
+
+    for (int i = t; i < (kThreads / 32) * a.pay.n * 2; i += kThreads) s_acc[i] = 0.0f;
+    if (t == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_init(mbar + 8, 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+        tc::mbar_arrive_expect_tx(mbar + 8, Ly::kBBytes);
+        tc::bulk_g2s(bt, a.bimg, Ly::kBBytes, mbar + 8);
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, kN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot_ptr;
+    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8, 0, a.wait_cap) ? 0 : 1) != 0;
+
+    uint32_t phase = 0;
+    const int M = a.run.steps, d = a.d;
+    const float inv_m = 1.0f / static_cast<float>(M);
+    const int64_t ntiles = (a.run.paths + kRows - 1) / kRows;
+    const uint32_t row_taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    // basket value of this thread's path after `steps` steps, from its accumulator row
+    auto basket = [&](float steps) {
+        float u = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < kN / 16; ++cc) {
+            float v[16];
+            tc::tmem_ld16(row_taddr + cc * 16, v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int l = 0; l < 16; ++l) {
+                const int j = cc * 16 + l;
+                u = fmaf(c.ws0[j], ex2_approx(fmaf(c.cs[j], v[l], steps * c.drift[j])), u);
+            }
+        }
+        return u;
+    };
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t nl = tile * kRows + t;
+        const bool valid = nl < a.run.paths;
+        const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
+        NormalReader rd;
+        rd.init(n, a.run.k0, a.run.k1);
+        Stats st{0.0f, -INFINITY, INFINITY};
+        bool ok = true;
+        for (int i = 0; i < M; ++i) {
+            if (!aborted) draw_row<PREC, EXACT>(zt, t, i, d, n, a.run.k0, a.run.k1, rd, valid);
+            tc::fence_proxy_async();
+            tc::fence_before_sync();  // this thread's accumulator reads precede the next MMA
+            if (__syncthreads_or(ok ? 0 : 1)) aborted = true;
+            if (aborted) break;
+            if (t == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int kk = 0; kk < Ly::kMmas; ++kk) {
+                    const uint64_t ad = tc::smem_desc(zt + kk * 32, Ly::kGroupBytes, Ly::kSw);
+                    const uint64_t bd = tc::smem_desc(bt + kk * 32, Ly::kGroupBytes, Ly::kSw);
+                    tc::mma_f16(tmem, ad, bd, tc::idesc_f16(kRows, kN, PREC == MC_BF16), (i > 0 || kk > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(mbar);
+            }
+            ok = tc::mbar_wait_bounded(mbar, phase & 1u, a.wait_cap);
+            ++phase;
+            tc::fence_after_sync();
+            // the Z buffer is free again (the MMA completed); the accumulator holds steps 0..i
+            if (STATS && __all_sync(0xffffffffu, ok)) {
+                const float u = basket(static_cast<float>(i + 1));
+                st.sum += u;
+                st.umax = fmaxf(st.umax, u);
+                st.umin = fminf(st.umin, u);
+            }
+        }
+        if (__syncthreads_or(ok ? 0 : 1)) aborted = true;
+        const float uT = aborted ? 0.0f : basket(static_cast<float>(M));
+        const float avg = st.sum * inv_m;
+        const bool use = valid && !aborted;
+        for (int p = 0; p < a.pay.n; ++p) {
+            const float f = payoff_eval(a.pay.kind[p], a.pay.strike[p], a.pay.barrier[p], uT, avg, st.umax, st.umin);
+            warp_accumulate(s_acc, a.pay.n, p, use ? f : 0.0f);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (aborted && t == 0) atomicExch(a.err, 1u);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kN);
+    }
+    block_finish(s_acc, s_red, a.pay.n, a.red);
+}
+
 // Factor tile for the MMA's B operand: row n = Lrho[n][0..63] (zero above
 // the diagonal and beyond d), scaled by s_n (E4M3: 448 / max_k |Lrho[n][k]|,
 // else 1), rounded to the operand type, at its swizzled position.  Also the
@@ -334,21 +455,27 @@ __global__ void tc_prep_kernel(int d, const double *L, const double *sigma, doub
 }  // namespace tcb
 
 template <int PREC, int SCHEME>
-const void *basket_tc_select(const TcArgs &a)
+const void *basket_tc_select(const TcArgs &a, int *smem)
 {
     const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
     const bool exact = a.d == tcb::kN;
+    if (PREC != MC_FP8E4M3 && SCHEME == MC_LOG_EULER) {
+        // TMEM running sum: Z tile + factor tile + barriers (~27 KB with the
+        // static arrays and the per-block reservation: at most 8 CTAs, 8 x 64
+        // TMEM columns, share an SM)
+        *smem = 1024 + tcb::Layout<PREC>::kTileBytes + tcb::Layout<PREC>::kBBytes + 64;
+        if (stats)
+            return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, true, true>)
+                         : reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, true, false>);
+        return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, false, true>)
+                     : reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, false, false>);
+    }
+    *smem = tcb::Layout<PREC>::kSmem;
     if (stats)
         return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, true, true>)
                      : reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, true, false>);
     return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, false, true>)
                  : reinterpret_cast<const void *>(&tcb::basket_tc_kernel<PREC, SCHEME, false, false>);
-}
-
-template <int PREC>
-int basket_tc_smem()
-{
-    return tcb::Layout<PREC>::kSmem;
 }
 
 template <int PREC>
@@ -360,9 +487,8 @@ cudaError_t tc_prep(int d, const double *L, const double *sigma, double cfac, do
 }
 
 #define GBMC_INSTANTIATE_TC(PREC)                                                                         \
-    template const void *basket_tc_select<PREC, MC_LOG_EULER>(const TcArgs &a);                           \
-    template const void *basket_tc_select<PREC, MC_EULER>(const TcArgs &a);                               \
-    template int basket_tc_smem<PREC>();                                                                  \
+    template const void *basket_tc_select<PREC, MC_LOG_EULER>(const TcArgs &a, int *smem);               \
+    template const void *basket_tc_select<PREC, MC_EULER>(const TcArgs &a, int *smem);                   \
     template cudaError_t tc_prep<PREC>(int, const double *, const double *, double, double, double, double, \
                                        int, uint8_t *, float *, float *, cudaStream_t);
 

@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
 
 // ------------------------------ scenarios --------------------------------
 // Lc: [d x d] FP32 of sqrt(h) diag(sigma) Lrho (lower); drift_u = (mu - sigma^2/2) h.
-__global__ void outer_kernel(int64_t nscen, int d, const float *__restrict__ Lc, const float *__restrict__ drift,
-                             const float *__restrict__ s0, uint32_t k0, uint32_t k1, float *__restrict__ Sp)
+__global__ void outer_kernel(int64_t nscen, int64_t off, int d, const float *__restrict__ Lc,
+                             const float *__restrict__ drift, const float *__restrict__ s0, uint32_t k0, uint32_t k1,
+                             float *__restrict__ Sp)
 {
     extern __shared__ float sL[];
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sL[i] = Lc[i];
@@ -96,7 +97,7 @@ __global__ void outer_kernel(int64_t nscen, int d, const float *__restrict__ Lc,
     for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < nscen;
          s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         NormalReader rd;
-        rd.init(tag(2, static_cast<uint64_t>(s)), k0, k1);
+        rd.init(tag(2, static_cast<uint64_t>(off + s)), k0, k1);  // global scenario index
         for (int u = 0; u < d; ++u) z[u] = rd.get(u);
         for (int u = 0; u < d; ++u) {
             float w = 0.0f;
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(256) nested_kernel(RiskArgs a, const float *__
     float acc[kRiskMaxOptPerUnder];
 #pragma unroll
     for (int j = 0; j < kRiskMaxOptPerUnder; ++j) acc[j] = 0.0f;
-    const uint64_t base_idx = Sp ? (static_cast<uint64_t>(pair) << 16) : (static_cast<uint64_t>(u) << 24);
+    const uint64_t gpair = static_cast<uint64_t>(a.scen_off + s) * d + u;  // global (scenario, underlying)
+    const uint64_t base_idx = Sp ? (gpair << 16) : (static_cast<uint64_t>(u) << 24);
     const uint64_t domain = Sp ? 3 : 5;
     for (int path = threadIdx.x; path < a.inner; path += blockDim.x) {
         const uint64_t n = tag(domain, base_idx | static_cast<uint64_t>(path));
@@ -316,12 +318,12 @@ cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float spy, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_outer(int64_t nscen, int d, const float *Lc, const float *drift, const float *s0, uint32_t k0,
-                         uint32_t k1, float *Sp, cudaStream_t s)
+cudaError_t launch_outer(int64_t nscen, int64_t off, int d, const float *Lc, const float *drift, const float *s0,
+                         uint32_t k0, uint32_t k1, float *Sp, cudaStream_t s)
 {
     const int64_t g = (nscen + 127) / 128;
-    outer_kernel<<<static_cast<int>(g < 4096 ? g : 4096), 128, d * d * sizeof(float), s>>>(nscen, d, Lc, drift, s0,
-                                                                                            k0, k1, Sp);
+    outer_kernel<<<static_cast<int>(g < 4096 ? g : 4096), 128, d * d * sizeof(float), s>>>(nscen, off, d, Lc, drift,
+                                                                                            s0, k0, k1, Sp);
     return cudaGetLastError();
 }
 

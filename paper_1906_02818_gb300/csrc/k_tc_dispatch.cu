@@ -8,9 +8,7 @@
 namespace gbmc {
 
 template <int PREC, int SCHEME>
-const void *basket_tc_select(const TcArgs &a);
-template <int PREC>
-int basket_tc_smem();
+const void *basket_tc_select(const TcArgs &a, int *smem);
 template <int PREC>
 cudaError_t tc_prep(int d, const double *L, const double *sigma, double cfac, double sdt, double r, double dt,
                     int scheme, uint8_t *bimg, float *cs, float *drift, cudaStream_t s);
@@ -20,17 +18,18 @@ namespace {
 constexpr int kTcThreads = 128;
 
 template <int PREC>
-const void *select_prec(const TcArgs &a)
+const void *select_prec(const TcArgs &a, int *smem)
 {
-    return a.scheme == MC_LOG_EULER ? basket_tc_select<PREC, MC_LOG_EULER>(a) : basket_tc_select<PREC, MC_EULER>(a);
+    return a.scheme == MC_LOG_EULER ? basket_tc_select<PREC, MC_LOG_EULER>(a, smem)
+                                    : basket_tc_select<PREC, MC_EULER>(a, smem);
 }
 
 const void *select(int prec, const TcArgs &a, int *smem)
 {
     switch (prec) {
-    case MC_BF16: *smem = basket_tc_smem<MC_BF16>(); return select_prec<MC_BF16>(a);
-    case MC_FP16: *smem = basket_tc_smem<MC_FP16>(); return select_prec<MC_FP16>(a);
-    case MC_FP8E4M3: *smem = basket_tc_smem<MC_FP8E4M3>(); return select_prec<MC_FP8E4M3>(a);
+    case MC_BF16: return select_prec<MC_BF16>(a, smem);
+    case MC_FP16: return select_prec<MC_FP16>(a, smem);
+    case MC_FP8E4M3: return select_prec<MC_FP8E4M3>(a, smem);
     default: *smem = 0; return nullptr;
     }
 }

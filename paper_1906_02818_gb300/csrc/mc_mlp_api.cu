@@ -224,6 +224,19 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
     return MC_OK;
 }
 
+int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!host_grad || !(lr > 0.0f)) return set_last_error(MC_EINVAL, "host_grad set and lr > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MLP_CUDA(cudaMemcpyAsync(net->grad, host_grad, net->L.count * sizeof(float), cudaMemcpyHostToDevice, s));
+    MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
+    ++net->version;
+    MLP_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
 int mc_mlp_destroy(mc_mlp *net)
 {
     delete net;

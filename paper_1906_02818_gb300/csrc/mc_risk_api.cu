@@ -79,6 +79,8 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
         return fail(MC_EINVAL, "portfolio arrays must be set");
     if (!(cf->alpha > 0.0 && cf->alpha < 1.0)) return fail(MC_EINVAL, "alpha must lie in (0, 1)");
     if (cf->n_scen < 1 || cf->n_scen > (int64_t(1) << 24)) return fail(MC_EINVAL, "n_scen outside [1, 2^24]");
+    if (cf->scen_offset < 0 || cf->scen_offset + cf->n_scen > (int64_t(1) << 34))
+        return fail(MC_EINVAL, "scenario range must lie in [0, 2^34)");
     if (cf->steps_per_year < 1) return fail(MC_EINVAL, "steps_per_year must be >= 1");
     const double spy = cf->steps_per_year, dt = 1.0 / spy;
     const int hsteps = static_cast<int>(std::lround(cf->horizon * spy));
@@ -175,7 +177,7 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
     RK_CUDA(cudaMemcpyAsync(d_Lc, Lc.data(), Lc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     RK_CUDA(cudaMemcpyAsync(d_drift, drift.data(), d * sizeof(float), cudaMemcpyHostToDevice, s));
     const uint32_t k0 = static_cast<uint32_t>(cf->seed), k1 = static_cast<uint32_t>(cf->seed >> 32);
-    RK_CUDA(launch_outer(ns, d, d_Lc, d_drift, d_s0, k0, k1, d_Sp, s));
+    RK_CUDA(launch_outer(ns, cf->scen_offset, d, d_Lc, d_drift, d_s0, k0, k1, d_Sp, s));
 
     RiskArgs a{};
     a.d = d;
@@ -196,6 +198,7 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
     a.base_out = d_base;
     a.k0 = k0;
     a.k1 = k1;
+    a.scen_off = cf->scen_offset;
     if (cf->method == MC_RISK_NESTED) {
         double *d_contrib;
         RK_CUDA(B.alloc(&d_contrib, ns * d));

@@ -67,7 +67,7 @@ class McRiskCfg(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("horizon", ctypes.c_double), ("n_scen", ctypes.c_int64),
                 ("steps_per_year", ctypes.c_int32), ("method", ctypes.c_int32), ("inner_paths", ctypes.c_int32),
                 ("base_paths", ctypes.c_int32), ("seed", ctypes.c_uint64), ("surrogate", ctypes.c_void_p),
-                ("surrogate_precision", ctypes.c_int32)]
+                ("surrogate_precision", ctypes.c_int32), ("scen_offset", ctypes.c_int64)]
 
 
 class McRiskResult(ctypes.Structure):
@@ -112,6 +112,7 @@ SIGNATURES = [
     ("mc_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("mc_mlp_apply_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p]),
     ("mc_mlp_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("mc_risk", ctypes.c_int, [ctypes.POINTER(McPortfolio), ctypes.POINTER(McRiskCfg),
                                ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),
