@@ -33,10 +33,10 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Warp instructions the basket kernel issues per path-step (smsp__inst_executed.sum
 # divided by paths x steps) from the ncu capture of the same kernel build,
 # recorded in profiles/.  None where no capture of the current build exists.
-INST_PER_PATH_STEP = {"fp32": None, "bf16": 52.89, "fp16": None, "fp8": None}
+INST_PER_PATH_STEP = {"fp32": None, "bf16": 56.45, "fp16": None, "fp8": None}
 # DRAM bytes (read + write) of one launch of that kernel in the same capture:
 # only the factor tile and launch constants are read, whatever the path count.
-DRAM_BYTES_PER_LAUNCH = {"bf16": 86528}
+DRAM_BYTES_PER_LAUNCH = {"bf16": 73728}
 
 
 def peaks():
@@ -240,7 +240,8 @@ def run_gbmc(args):
         achieved = inst * P * w["steps"] / (ms_step * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": issue_peak, "unit": "Twarp-inst/s",
                 "frac": achieved / issue_peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(args.prec),
-                "kernel": "basket_tc_kernel" if args.prec != "fp32" else "basket_fp32_kernel",
+                "kernel": ("basket_tc_acc_kernel" if args.prec in ("bf16", "fp16") else "basket_tc_kernel")
+                if args.prec != "fp32" else "basket_fp32_kernel",
                 "basis": f"{inst} warp instructions per path-step (ncu, profiles/) x path-steps / CUDA-event "
                          f"time; peak = 152 SMs x 4 issue slots x {pk.get('sm_max_mhz', 2070.0)} MHz "
                          f"(issue rate; sm_max_mhz from MEASURED_PEAKS.json, {pk_kind})"}

@@ -9,6 +9,7 @@
 //   adam_kernel      Adam update of the packed FP32 master parameters
 // plus the host runtime behind mc_mlp_* (include/mc.h).  Inference in BF16
 // on the tensor cores lives in k_mlp_tc.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -21,6 +22,7 @@ namespace gbmc {
 namespace {
 
 constexpr int kT = 64, kK = 16;
+constexpr int kMaxSlices = 16;  // K slices of a weight-gradient product
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
 __device__ __forceinline__ float silu_grad_f(float z)
@@ -31,17 +33,25 @@ __device__ __forceinline__ float silu_grad_f(float z)
 
 // C[M x N] = op(A)[M x K] * op(B)[K x N]; TA: A stored K x M; TB: B stored N x K.
 // Epilogue: v = acc + bias[n]; Z = v (if Z); H = silu(v) or v (if H).
+// Split K (grid.z > 1): slice z sums k in [z kchunk, (z + 1) kchunk) and
+// writes its partial product at Z + z M ldc (summed by sum_slices_kernel).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
                                                    const float *__restrict__ B, int ldb, const float *__restrict__ bias,
-                                                   float *__restrict__ Z, float *__restrict__ H, int ldc, int act)
+                                                   float *__restrict__ Z, float *__restrict__ H, int ldc, int act,
+                                                   int kchunk)
 {
     __shared__ float As[kK][kT + 4];
     __shared__ float Bs[kK][kT + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.x * kT, n0 = blockIdx.y * kT;  // row tiles on x: up to 2^31 - 1 blocks
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kK) {
+    const int kb0 = blockIdx.z * kchunk, kend = min(K, kb0 + kchunk);
+    if (gridDim.z > 1) {
+        Z += static_cast<int64_t>(blockIdx.z) * M * ldc;
+        K = kend;
+    }
+    for (int k0 = kb0; k0 < K; k0 += kK) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = tid + 256 * r;
@@ -86,6 +96,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
             if (Z) Z[o] = v;
             if (H) H[o] = act ? silu_f(v) : v;
         }
+    }
+}
+
+// out[i] = sum_z part[z count + i] (the K slices of a split product, in order).
+__global__ void sum_slices_kernel(int64_t count, int slices, const float *part, float *out)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < slices; ++z) s += part[static_cast<int64_t>(z) * count + i];
+        out[i] = s;
     }
 }
 
@@ -159,7 +180,24 @@ cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, i
                  float *H, int ldc, int act, cudaStream_t s)
 {
     dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT);
-    gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act);
+    gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act, K);
+    return cudaGetLastError();
+}
+
+// C = op(A) op(B) with K cut into `slices` pieces (no bias, no activation):
+// partial products into ws [slices][M][N], then one ordered sum into C.
+template <bool TA, bool TB>
+cudaError_t gemm_split_k(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int slices,
+                         float *ws, cudaStream_t s)
+{
+    const int kchunk = ((K + slices - 1) / slices + kK - 1) / kK * kK;
+    slices = (K + kchunk - 1) / kchunk;
+    dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT, slices);
+    gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, nullptr, ws, nullptr, N, 0, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t count = static_cast<int64_t>(M) * N;
+    sum_slices_kernel<<<grid_for(count), 256, 0, s>>>(count, slices, ws, C);
     return cudaGetLastError();
 }
 
@@ -221,7 +259,7 @@ cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *
         maxw = L.sizes[l + 1] > maxw ? L.sizes[l + 1] : maxw;
     }
     for (int v : L.sizes) maxw = v > maxw ? v : maxw;
-    float *dH = p, *dZ = p + n * maxw;
+    float *dH = p, *dZ = p + n * maxw, *ws = dZ + n * maxw;  // ws: split-K partials of the weight gradients
     cudaError_t e;
     const float *h = x;
     for (int l = 0; l < nl; ++l) {
@@ -239,8 +277,12 @@ cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         const float *hin = l == 0 ? x : Hp[l - 1];
-        // dW = H_in^T dZ   [in x out]
-        e = gemm<true, false>(in, out, static_cast<int>(n), hin, in, dZ, out, nullptr, nullptr, grad + L.w_off[l], out, 0, s);
+        // dW = H_in^T dZ   [in x out]: a small output over a long K, so K is split
+        const int slices = static_cast<int>(std::min<int64_t>(kMaxSlices, std::max<int64_t>(1, n / 256)));
+        e = slices > 1 ? gemm_split_k<true, false>(in, out, static_cast<int>(n), hin, in, dZ, out, grad + L.w_off[l],
+                                                   slices, ws, s)
+                       : gemm<true, false>(in, out, static_cast<int>(n), hin, in, dZ, out, nullptr, nullptr,
+                                           grad + L.w_off[l], out, 0, s);
         if (e != cudaSuccess) return e;
         colsum_kernel<<<out, 256, 0, s>>>(static_cast<int>(n), out, dZ, grad + L.b_off[l]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -262,7 +304,7 @@ size_t mlp_train_floats(const MlpLayout &L, int64_t n)
         f += 2 * static_cast<size_t>(n) * L.sizes[l + 1];
     }
     for (int v : L.sizes) maxw = v > maxw ? v : maxw;
-    return f + 2 * static_cast<size_t>(n) * maxw;
+    return f + 2 * static_cast<size_t>(n) * maxw + static_cast<size_t>(kMaxSlices) * maxw * maxw;
 }
 
 cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s)

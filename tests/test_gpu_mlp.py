@@ -173,3 +173,19 @@ def test_forward_bf16_rejects_unsupported_shapes(gb):
         with pytest.raises(MCError, match="bf16"):
             net.forward(torch.zeros((4, n_in), device="cuda"), precision="bf16")
         net.close()
+
+
+def test_apply_grad_is_one_training_step(gb):
+    """An Adam step with the batch gradient from loss_grad (the data-parallel
+    path's update) equals one step of native training on that batch."""
+    import torch
+    init = workloads.mlp_init(seed=12)
+    a, b = gb.Mlp(5, 256, 4, init), gb.Mlp(5, 256, 4, init)
+    x, t = _data(1024, seed=6)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    _, g = a.loss_grad(xd, td)
+    a.apply_grad(g, 1e-3)
+    b.train(xd, td, epochs=1, batch=1024, lr=1e-3)
+    assert np.max(np.abs(a.params() - b.params())) <= 1e-7
+    a.close()
+    b.close()

@@ -121,3 +121,23 @@ def test_surrogate_judged_by_nested(gb, trained):
     assert corr > 0.93
     assert rv < 0.15 and rc < 0.15
     assert t2 - t1 < t1 - t0  # the network revalues faster than the inner simulation
+
+
+def test_scenario_shards_reproduce_the_full_run(gb, trained):
+    """Scenarios are indexed globally: two slices [0, n1) and [n1, n) revalue
+    exactly the PnL of the single run (nested and surrogate), and the tail
+    statistics of the gathered PnL are the single run's."""
+    from paper_1906_02818_gb300 import shard
+    net, _ = trained
+    pf = workloads.risk_portfolio(n_under=4, per_under=8, seed=7)
+    n, n1 = 777, 300
+    for kw in (dict(method="nested", inner_paths=256, base_paths=1024),
+               dict(method="surrogate", surrogate=net), dict(method="surrogate", surrogate=net,
+                                                              surrogate_precision="bf16")):
+        full = gb.risk(pf, alpha=0.97, n_scen=n, want_pnl=True, **kw)
+        a = gb.risk(pf, alpha=0.97, n_scen=n1, want_pnl=True, **kw)
+        b = gb.risk(pf, alpha=0.97, n_scen=n - n1, scen_offset=n1, want_pnl=True, **kw)
+        pnl = np.concatenate([a["pnl"], b["pnl"]])
+        assert np.array_equal(pnl, full["pnl"]), kw["method"]
+        var, cvar, nt = shard.tail_statistics(pnl, 0.97)
+        assert var == full["var"] and nt == full["n_tail"] and abs(cvar - full["cvar"]) <= 1e-12 * abs(cvar)
