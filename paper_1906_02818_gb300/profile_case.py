@@ -8,6 +8,7 @@
   python -m paper_1906_02818_gb300.profile_case mlp --paths 1048576 --prec bf16   (paths = network rows)
   python -m paper_1906_02818_gb300.profile_case labels --paths 4096              (paths = label points)
   python -m paper_1906_02818_gb300.profile_case risk_nested --paths 256          (paths = scenarios)
+  python -m paper_1906_02818_gb300.profile_case train --paths 262144            (paths = samples, 1 epoch)
 """
 from __future__ import annotations
 
@@ -26,12 +27,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
-                                     "risk_nested"])
+                                     "risk_nested", "train"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case in ("mlp", "labels", "risk_nested"):
+    if a.case in ("mlp", "labels", "risk_nested", "train"):
         _other(a, torch, workloads, gb)
         return
     if a.case in ("heston", "heston_greeks"):
@@ -64,6 +65,20 @@ def _other(a, torch, workloads, gb):
             y = net.forward(x, precision=a.prec)
         torch.cuda.synchronize()
         print(a.case, n, a.prec, float(y.sum()))
+        net.close()
+    elif a.case == "train":
+        import time
+        n = a.paths or (1 << 18)
+        net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+        g = torch.Generator("cuda").manual_seed(2)
+        x = torch.rand((n, 5), device="cuda", generator=g) * 2 - 1
+        t = torch.rand(n, device="cuda", generator=g)
+        for _ in range(a.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = net.train(x, t, epochs=1, batch=4096, lr=1e-3)
+            dt = time.perf_counter() - t0
+        print(a.case, n, loss, f"{dt:.4f} s/epoch, {dt / (n // 4096) * 1e3:.3f} ms/step")
         net.close()
     elif a.case == "labels":
         pts = torch.from_numpy(workloads.surrogate_points(a.paths or 4096)).cuda()
