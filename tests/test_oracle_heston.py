@@ -95,3 +95,26 @@ def test_semi_closed_form_within_bias(orc, K):
     m, se = orc.mean_se(f[0])
     exact = heston_call_semi_closed(100.0, K, 0.05, 1.0, 0.04, 2.0, 0.04, 0.5, -0.7)
     assert abs(m - exact) <= 3 * se + 0.005 * exact, (m, se, exact)
+
+
+def test_heston_against_semi_closed_form(orc):
+    """Bias-aware sanity check (not a parity test): the 256-step
+    full-truncation scheme against Heston's semi-closed form for the workload's
+    parameters.  The Euler bias is not zero (the Feller condition is violated);
+    the difference is reported and must stay within a loose bound.  The
+    closed form itself is pinned by its xi -> 0 limit (Black-Scholes, reached
+    at first order in xi)."""
+    import workloads
+    from closed_forms import bs_call, heston_call
+    bs = bs_call(100.0, 95.0, 0.05, 0.2, 1.0)
+    gaps = [heston_call(100.0, 95.0, 0.05, 1.0, 0.04, 2.0, 0.04, xi, -0.7) - bs for xi in (1e-4, 1e-5)]
+    assert abs(gaps[1]) < 1e-4 and 5.0 < gaps[0] / gaps[1] < 20.0  # first order in xi
+    h = dict(workloads.HESTON_PARAMS)
+    pays = [dict(kind="call", strike=K) for K in (80.0, 100.0, 120.0)]
+    per = orc.heston_payoffs(h, 1.0, 256, 1 << 15, pays)
+    for p, row in zip(pays, per):
+        m, se = orc.mean_se(row)
+        cf = heston_call(h["s0"], p["strike"], h["r"], 1.0, h["v0"], h["kappa"], h["theta"], h["xi"], h["rho"])
+        print(f"K={p['strike']:.0f}: Monte Carlo {m:.4f} +- {se:.4f}, semi-closed form {cf:.4f}, "
+              f"difference {m - cf:+.4f} ({(m - cf) / se:+.1f} SE)")
+        assert abs(m - cf) <= 4 * se + 0.02 * cf

@@ -4,7 +4,7 @@ the error against the FP64 oracle on the same random stream (on a path
 prefix the oracle finishes quickly), and the oracle's own throughput on the
 host cores.
 
-  python -m paper_1906_02818_gb300.report [--only gbm1d,bridge,basket64,mlmc,qmc,heston,basket512,risk]
+  python tests/workload_report.py [--only gbm1d,bridge,basket64,mlmc,qmc,heston,basket512,risk]
          [--reps 20] [--oracle-paths N]
 
 Device times are CUDA events around mc_plan_execute (inputs resident, the
@@ -20,7 +20,8 @@ import time
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))  # repository root
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))  # tests/ (closed forms)
 
 
 def _events(torch, stream, fn, reps, warmup=3):
@@ -188,7 +189,15 @@ def run_heston(torch, gb, orc, a):
     _, gs = gb.greeks(model, dict(cfg, paths=min(n_or, 4096)), w["payoffs"][:1])
     gerr = [float(abs(gs[0, k, 0] - gref[k].mean()) / max(abs(gref[k].mean()), 1e-2)) for k in range(7)]
     ps = w["paths"] * w["steps"]
+    from closed_forms import heston_call
+    h = w["model"]
+    semi = {}
+    for i, K in enumerate(workloads.HESTON_STRIKES):
+        cf = heston_call(h["s0"], K, h["r"], w["T"], h["v0"], h["kappa"], h["theta"], h["xi"], h["rho"])
+        semi[str(int(K))] = dict(gpu=float(res[i, 0]), se=float(res[i, 1]), semi_closed_form=cf,
+                                 euler_bias_in_se=float((res[i, 0] - cf) / res[i, 1]))
     return dict(workload="Heston, 2^22 paths x 256 steps, 9 strikes x {European, Asian}", dtype="f32",
+                european_vs_semi_closed_form=semi,
                 seconds=t, path_steps_per_s=ps / t, options_per_s=18 / t,
                 max_rel_err_vs_oracle_prefix=max(errs), oracle_prefix_paths=n_or,
                 greeks_seconds=t_g, greeks_path_steps_per_s=ps / t_g,
@@ -238,7 +247,8 @@ def run_basket512(torch, gb, orc, a):
 def run_risk(torch, gb, orc, a):
     import subprocess
     r = subprocess.run([sys.executable, "-m", "paper_1906_02818_gb300.risk_report", "--scen", str(1 << 16)],
-                       capture_output=True, text=True)
+                       capture_output=True, text=True,
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
