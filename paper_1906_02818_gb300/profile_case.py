@@ -9,6 +9,10 @@
   python -m paper_1906_02818_gb300.profile_case labels --paths 4096              (paths = label points)
   python -m paper_1906_02818_gb300.profile_case risk_nested --paths 256          (paths = scenarios)
   python -m paper_1906_02818_gb300.profile_case train --paths 262144            (paths = samples, 1 epoch)
+  python -m paper_1906_02818_gb300.profile_case bridge --paths 1048576          (the In and Out Put, 25 steps)
+  python -m paper_1906_02818_gb300.profile_case qmc --paths 262144              (points x 16 replications)
+  python -m paper_1906_02818_gb300.profile_case mlmc --paths 16384              (correction paths, d = 64, bf16)
+  python -m paper_1906_02818_gb300.profile_case factor512 --paths 65536
 """
 from __future__ import annotations
 
@@ -27,12 +31,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
-                                     "risk_nested", "train"])
+                                     "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case in ("mlp", "labels", "risk_nested", "train"):
+    if a.case in ("mlp", "labels", "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512"):
         _other(a, torch, workloads, gb)
         return
     if a.case in ("heston", "heston_greeks"):
@@ -66,6 +70,35 @@ def _other(a, torch, workloads, gb):
         torch.cuda.synchronize()
         print(a.case, n, a.prec, float(y.sum()))
         net.close()
+    elif a.case == "bridge":
+        import numpy as np
+        model = dict(kind="gbm", s0=np.array([100.0]), sigma=np.array([0.8]), r=0.03)
+        cfg = dict(steps=25, T=2.0, paths=a.paths or (1 << 20), seed=42, monitoring="bridge")
+        for _ in range(a.reps):
+            r = gb.price(model, cfg, [dict(kind="ui_put", strike=120.0, barrier=140.0)])
+        print(a.case, r)
+    elif a.case == "qmc":
+        import numpy as np
+        s0, sg, corr = workloads.basket_market(16, 4)
+        w = np.full(16, 1 / 16)
+        model = dict(kind="gbm", s0=s0, sigma=sg, corr=corr, weights=w, r=0.05)
+        for _ in range(a.reps):
+            r, _ = gb.price_qmc(model, dict(steps=1, T=1.0, paths=a.paths or (1 << 18), seed=42),
+                                [dict(kind="call", strike=float(w @ s0))], replications=16)
+        print(a.case, r)
+    elif a.case == "mlmc":
+        w = workloads.basket_d64(paths=1 << 14)
+        model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], corr=w["corr"], weights=w["weights"], r=w["r"])
+        cfg = dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=w["seed"], precision="bf16")
+        for _ in range(a.reps):
+            r = gb.price_mlmc(model, cfg, w["payoffs"], a.paths or (1 << 14))
+        print(a.case, r[0]["price"], r[0]["correction"])
+    elif a.case == "factor512":
+        w = workloads.basket_d512_factor(paths=a.paths or (1 << 16))
+        model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], loadings=w["loadings"], weights=w["weights"], r=w["r"])
+        for _ in range(a.reps):
+            r = gb.price(model, dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=42), w["payoffs"])
+        print(a.case, r)
     elif a.case == "train":
         import time
         n = a.paths or (1 << 18)
