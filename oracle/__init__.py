@@ -19,7 +19,11 @@ Contents
              Brownian-bridge extremes (Sec. VI.A.1), the factor-model
              correlation (rho = B B^T + diag(e^2)), randomised Sobol
              quasi-Monte Carlo (Sec. IV, VI.D), forward-mode pathwise Greeks
-             (Sec. I.A.3), the estimator of Eq. 3 with its standard error.
+             (Sec. I.A.3) including the tangents of the terminal log-prices
+             in the Cholesky-factor entries, the estimator of Eq. 3 with its
+             standard error.
+  (here)     the forward derivative of the Cholesky factor and the chain rule
+             from factor tangents to correlation sensitivities (numpy).
   mlp.py     FP64 numpy forward / backward of the pricing surrogate.
   risk.py    VaR / CVaR of Sec. VI.B and nested revaluation.
 
@@ -35,7 +39,11 @@ barrier against the paper's "In and Out Put" value 23.1371783926 and the
 continuous down-and-in call closed form, at one step and at many; the Sobol
 recurrence against its definition, one-dimensional stratification, the
 (0, m, 2)-net property of the first two dimensions, and the randomised-QMC
-price against Black-Scholes and its error rate against plain Monte Carlo.
+price against Black-Scholes and its error rate against plain Monte Carlo;
+the Cholesky tangent against LAPACK differences, per-path correlation
+tangents against bumped simulations, the geometric-basket correlation
+sensitivity against its closed form and the arithmetic basket's against
+common-random-number differences.
 """
 from __future__ import annotations
 
@@ -99,6 +107,8 @@ def _load():
     lib.orc_gbm_paths.restype = i32
     lib.orc_gbm_greeks.argtypes = gbm_common + [i32, i_p, d_p, d_p]
     lib.orc_gbm_greeks.restype = i32
+    lib.orc_gbm_corr_tangents.argtypes = [i32, d_p, d_p, d_p, dbl, dbl, i32, u64, i64, i64, d_p, d_p]
+    lib.orc_gbm_corr_tangents.restype = i32
     lib.orc_gbm1d_bridge_payoffs.argtypes = [dbl] * 5 + [i32, u64, i64, i64, i32, i_p, d_p, d_p, d_p]
     lib.orc_gbm1d_bridge_payoffs.restype = i32
     lib.orc_gbm_factor_payoffs.argtypes = [i32, i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, i32, u64, i64, i64, i32, i_p,
@@ -310,6 +320,84 @@ def gbm_greeks(s0, sigma, r, T, steps, paths, payoffs, corr=None, weights=None,
                                 len(payoffs), ip, _dptr(K), _dptr(out))
     _check(rc, "orc_gbm_greeks")
     return out
+
+
+def gbm_corr_tangents(s0, sigma, corr, r, T, steps, paths, seed=42, path_offset=0):
+    """log-Euler terminal log-prices x_a(T), shape [d, paths], and their
+    forward tangents d x_a(T) / d Lrho[a][b] (b <= a, Lrho = chol(corr), drift
+    held fixed), packed row by row, shape [d (d + 1) / 2, paths]."""
+    d, s0, sigma, corr, _ = _gbm_args(s0, sigma, corr, None)
+    xT = np.empty((d, paths), dtype=np.float64)
+    tL = np.empty((d * (d + 1) // 2, paths), dtype=np.float64)
+    rc = _load().orc_gbm_corr_tangents(d, _dptr(s0), _dptr(sigma), _dptr(corr), r, T, steps, seed, path_offset,
+                                       paths, _dptr(xT), _dptr(tL))
+    _check(rc, "orc_gbm_corr_tangents")
+    return xT, tL
+
+
+def cholesky_tangent(L, E) -> np.ndarray:
+    """Forward derivative of the Cholesky factor: if A = L L^T moves by a
+    symmetric E, L moves by L Phi(L^-1 E L^-T), Phi = the lower triangle with
+    the diagonal halved (differentiating A = L L^T and keeping L lower
+    triangular)."""
+    L = np.asarray(L, dtype=np.float64)
+    Li = np.linalg.inv(L)
+    X = Li @ np.asarray(E, dtype=np.float64) @ Li.T
+    return L @ (np.tril(X, -1) + 0.5 * np.diag(np.diag(X)))
+
+
+def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, seed=42, path_offset=0):
+    """Per-path discounted pathwise correlation sensitivities of a European
+    basket call or put on U = sum_a w_a S_a(T) (log-Euler), forward mode:
+      f     [paths]        discounted payoff
+      dl    [d, d, paths]  d/d Lrho[a][b] (b <= a; zero above the diagonal)
+      drho  [d, d, paths]  d/d corr[a][b] for a != b, corr[a][b] and
+                           corr[b][a] moved together; zero on the diagonal
+    The payoff's slope in x_a is w_a S_a 1{U > K} (call), -w_a S_a 1{U < K}
+    (put); d/d corr[a][b] = sum over (c, e) of d/d Lrho[c][e] times the
+    (c, e) entry of cholesky_tangent(Lrho, E_ab), E_ab the symmetric unit
+    direction of the pair."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    kind, K = payoff["kind"], float(payoff["strike"])
+    if kind not in ("call", "put"):
+        raise ValueError("European call or put only")
+    xT, tL = gbm_corr_tangents(s0, sigma, corr, r, T, steps, paths, seed, path_offset)
+    S = np.exp(xT)
+    U = w @ S
+    disc = np.exp(-r * T)
+    if kind == "call":
+        f, slope = np.maximum(U - K, 0.0), (U > K).astype(np.float64)
+    else:
+        f, slope = np.maximum(K - U, 0.0), -(U < K).astype(np.float64)
+    g = disc * slope[None, :] * w[:, None] * S          # d (discounted payoff) / d x_a
+    dl = np.zeros((d, d, paths))
+    for a in range(d):
+        for b in range(a + 1):
+            dl[a, b] = g[a] * tL[a * (a + 1) // 2 + b]
+    return dict(f=disc * f, dl=dl, drho=corr_chain(corr, dl))
+
+
+def corr_chain(corr, dl) -> np.ndarray:
+    """Chain rule from d/d Lrho (shape [d, d, ...], lower triangle) to
+    d/d corr[a][b], a != b, with corr[a][b] and corr[b][a] moved together:
+    the inner product of dl with cholesky_tangent(chol(corr), E_ab) for every
+    pair.  Returns the symmetric array, zero on the diagonal."""
+    d = dl.shape[0]
+    rest = dl.shape[2:]
+    flat = dl.reshape(d * d, -1)
+    Lr = cholesky(corr)
+    pairs = [(a, b) for a in range(d) for b in range(a)]
+    drho = np.zeros((d, d, flat.shape[1]))
+    if pairs:
+        J = np.empty((len(pairs), d * d))
+        for k, (a, b) in enumerate(pairs):
+            E = np.zeros((d, d))
+            E[a, b] = E[b, a] = 1.0
+            J[k] = cholesky_tangent(Lr, E).ravel()
+        vals = J @ flat
+        for k, (a, b) in enumerate(pairs):
+            drho[a, b] = drho[b, a] = vals[k]
+    return drho.reshape((d, d) + rest)
 
 
 # --------------------------------------------------------------------------

@@ -700,6 +700,56 @@ int orc_gbm_greeks(int d, const double *s0, const double *sig, const double *cor
 }
 
 /* ------------------------------------------------------------------------ */
+/* Correlation sensitivities, forward mode (Sec. I.A.3: sensitivities to     */
+/* model parameters; Sec. VI.A.2 differentiates the basket simulation).      */
+/* log-Euler only.  With dW_a = sqrt(Delta) sig_a sum_{b<=a} Lrho[a][b] z_b,  */
+/* the tangent of x_a = log S_a with respect to the factor entry Lrho[a][b]   */
+/* (b <= a; the drift (r - sig_a^2/2) held fixed) grows at every step by      */
+/*   d x_a / d Lrho[a][b]  +=  sqrt(Delta) sig_a z_b,                         */
+/* and x_c (c != a) does not depend on Lrho[a][b].  Per path n:               */
+/*   xT[a * npaths + n]               = x_a(T)                                */
+/*   tL[(a(a+1)/2 + b) * npaths + n]  = d x_a(T) / d Lrho[a][b],  b <= a.     */
+/* The map from these to d/d corr goes through the derivative of the          */
+/* Cholesky factor (oracle/__init__.py, forward mode).                        */
+/* ------------------------------------------------------------------------ */
+int orc_gbm_corr_tangents(int d, const double *s0, const double *sig, const double *corr, double r, double T,
+                          int steps, uint64_t seed, int64_t path0, int64_t npaths, double *xT, double *tL)
+{
+    if (d < 1 || steps < 1 || npaths < 0 || !(T > 0.0)) return -1;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, NULL, r, T, steps, 0, seed);
+    if (rc) return rc;
+    const double dt = T / steps, sdt = sqrt(dt);
+    const size_t nt = (size_t)d * (d + 1) / 2;
+#pragma omp parallel
+    {
+        double *x = (double *)malloc(sizeof(double) * (2 * (size_t)d + nt));
+        double *z = x + d, *t = z + d;
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            orc_stream st;
+            stream_init(&st, seed, (uint64_t)(path0 + n));
+            for (int a = 0; a < d; ++a) x[a] = log(s0[a]);
+            for (size_t k = 0; k < nt; ++k) t[k] = 0.0;
+            for (int i = 0; i < steps; ++i) {
+                for (int a = 0; a < d; ++a) z[a] = stream_normal(&st, (uint64_t)i * d + a);
+                for (int a = 0; a < d; ++a) {
+                    double y = 0.0;
+                    for (int b = 0; b <= a; ++b) y += m.Lrho[(size_t)a * d + b] * z[b];
+                    x[a] += (r - 0.5 * sig[a] * sig[a]) * dt + sdt * sig[a] * y;
+                    for (int b = 0; b <= a; ++b) t[(size_t)a * (a + 1) / 2 + b] += sdt * sig[a] * z[b];
+                }
+            }
+            for (int a = 0; a < d; ++a) xT[(size_t)a * npaths + n] = x[a];
+            for (size_t k = 0; k < nt; ++k) tL[k * npaths + n] = t[k];
+        }
+        free(x);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Heston stochastic volatility (Sec. II.A.1 names stochastic-volatility     */
 /* extensions of the scalar Euler scheme), full-truncation Euler on          */
 /* (x = log S, v), two normals per step: z1 = normal 2i, z2 = normal 2i+1.   */
