@@ -194,6 +194,31 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
               mc_result *prices, mc_result *greeks, void *stream);
 
 /*
+ * mc_corr_greeks -- pathwise sensitivities of a European basket call or put
+ * on U = sum_a w_a S_a(T) to the correlation matrix (Sec. I.A.3:
+ * sensitivities to model parameters; Sec. II.A.2: dW = sqrt(dt) diag(sigma)
+ * Lrho z with Lrho the Cholesky factor of corr; Sec. VI.A.2 differentiates
+ * the basket simulation), reverse mode, FP32 paths and FP64 post-processing.
+ *   model: MC_GBM, 2 <= d <= 64, corr given or NULL (= identity), no
+ *          loadings.  cfg: MC_LOG_EULER, MC_FP32, MC_DISCRETE.
+ *   payoff: one MC_CALL or MC_PUT (weights from the model, 1/d if NULL).
+ *   price: host [1] or NULL: the discounted price and its standard error.
+ *   dl:    host [d*d] or NULL, row-major: dP/dLrho[a][b] for b <= a (the
+ *          entry's coefficient in dW_a, the drift (r - sigma_a^2/2) held
+ *          fixed); zero above the diagonal.
+ *   drho:  host [d*d] or NULL, row-major: dP/dcorr[a][b] for a != b, with
+ *          corr[a][b] and corr[b][a] moved together (symmetric); zero on the
+ *          diagonal.
+ * Standard errors of dl and drho are batch-means errors over min(64, CTAs of
+ * the launch) groups of paths (NaN with one group, i.e. paths <= 128); the
+ * price's is the usual one.  Errors: MC_EUNSUPPORTED outside the cases above,
+ * MC_ENOTPSD if corr is not positive definite, MC_EINVAL on bad arguments;
+ * outputs are untouched on error.  Synchronises `stream` before returning.
+ */
+int mc_corr_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoff, mc_result *price,
+                   mc_result *dl, mc_result *drho, void *stream);
+
+/*
  * mc_price_mlmc -- two-level precision estimator (Sec. V: a fast reduced-
  * precision simulation whose bias is identified with few samples and
  * corrected; Giles' multilevel Monte Carlo over precisions):

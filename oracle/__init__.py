@@ -350,6 +350,7 @@ def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, s
     """Per-path discounted pathwise correlation sensitivities of a European
     basket call or put on U = sum_a w_a S_a(T) (log-Euler), forward mode:
       f     [paths]        discounted payoff
+      U     [paths]        the basket value at T
       dl    [d, d, paths]  d/d Lrho[a][b] (b <= a; zero above the diagonal)
       drho  [d, d, paths]  d/d corr[a][b] for a != b, corr[a][b] and
                            corr[b][a] moved together; zero on the diagonal
@@ -358,6 +359,7 @@ def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, s
     (c, e) entry of cholesky_tangent(Lrho, E_ab), E_ab the symmetric unit
     direction of the pair."""
     d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    corr = np.eye(d) if corr is None else corr
     kind, K = payoff["kind"], float(payoff["strike"])
     if kind not in ("call", "put"):
         raise ValueError("European call or put only")
@@ -374,7 +376,7 @@ def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, s
     for a in range(d):
         for b in range(a + 1):
             dl[a, b] = g[a] * tL[a * (a + 1) // 2 + b]
-    return dict(f=disc * f, dl=dl, drho=corr_chain(corr, dl))
+    return dict(f=disc * f, U=U, dl=dl, drho=corr_chain(corr, dl))
 
 
 def corr_chain(corr, dl) -> np.ndarray:

@@ -139,6 +139,24 @@ def greeks(model: dict, cfg: dict, payoffs, stream=None):
     return [(r.price, r.se) for r in pr], g
 
 
+def corr_greeks(model: dict, cfg: dict, payoff: dict, stream=None):
+    """Pathwise correlation sensitivities of one European basket call or put
+    (mc_corr_greeks): ((price, se), dl [d, d, 2], drho [d, d, 2]) with
+    dl[a, b] = (mean, se) of dP/dLrho[a][b] (b <= a) and drho[a, b] of
+    dP/dcorr[a][b] (a != b, both entries moved)."""
+    L = native.lib()
+    mm = _Marshalled(model, cfg, [payoff])
+    d = mm.model.d
+    pr = McResult()
+    dl = (McResult * (d * d))()
+    dr = (McResult * (d * d))()
+    check(L.mc_corr_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, ctypes.byref(pr), dl, dr,
+                           _stream_handle(stream)))
+    a = np.array([[r.price, r.se] for r in dl]).reshape(d, d, 2)
+    b = np.array([[r.price, r.se] for r in dr]).reshape(d, d, 2)
+    return (pr.price, pr.se), a, b
+
+
 def simulate(model: dict, cfg: dict, save_every: int = 1, stream=None):
     """Simulated paths as a CUDA float32 tensor [steps/save_every + 1, D, paths]."""
     import torch

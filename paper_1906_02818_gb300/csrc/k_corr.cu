@@ -1,0 +1,277 @@
+// Pathwise correlation sensitivities of a European basket call or put
+// (Sec. I.A.3: sensitivities to model parameters; Sec. VI.A.2 obtains basket
+// sensitivities by differentiating the simulation), reverse mode.
+//
+// Log-Euler with constant coefficients: after M steps
+//   x_a(T) = log S0_a + M drift_a + sqrt(dt) sigma_a (Lrho W)_a,  W = sum_i z_i,
+// so the terminal prices depend on the correlation only through the sum W of
+// the path's normal vectors.  The payoff's slope in x_a is
+// u_a = w_a S_a(T) 1{U > K} (call), -w_a S_a(T) 1{U < K} (put), and
+//   dP/dLrho[a][b] = disc sqrt(dt) sigma_a E[u_a W_b],   b <= a.
+// The path kernel accumulates H = sum_paths u W^T per CTA (an FP32 outer-
+// product sum over tiles of 32 paths staged in shared memory); a second
+// kernel sums the CTA partials in FP64 into batches; the adjoint kernel maps
+// each batch's dP/dLrho through the transpose of the Cholesky derivative,
+//   S = Lrho^-T Phi(Lrho^T Lbar) Lrho^-1   (Phi: lower triangle, diagonal
+//   halved),  dP/dcorr[a][b] = S_ab + S_ba  (a != b, both entries moved),
+// and the last kernel forms means and batch-means standard errors.
+#include "mc_kernels.cuh"
+
+namespace gbmc {
+
+namespace {
+
+constexpr int kD = kCorrMaxD;     // assets (padded)
+constexpr int kThreads = 128;     // paths per tile
+constexpr int kQuarter = 32;      // paths staged per outer-product pass
+constexpr int kStride = kD + 4;   // shared row stride (floats; 16-B aligned rows)
+
+template <bool EXACT>
+__global__ void __launch_bounds__(kThreads) corr_path_kernel(const CorrArgs a, const CorrConst c)
+{
+    __shared__ __align__(16) float su[kQuarter * kStride];   // w_a S_a(T) of the staged paths
+    __shared__ __align__(16) float sw[kQuarter * kStride];   // W of the staged paths
+    __shared__ float s_slope[kQuarter];
+    __shared__ float sh[32 * kThreads];                       // this CTA's H, thread t owns column t
+    __shared__ float s_acc[(kThreads / 32) * 2];
+    __shared__ double s_red[32];
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int j = 0; j < 32; ++j) sh[j * kThreads + t] = 0.0f;
+    if (t < (kThreads / 32) * 2) s_acc[t] = 0.0f;
+    __syncthreads();
+
+    const int M = a.run.steps, d = a.d;
+    const float fM = static_cast<float>(M);
+    const int64_t ntiles = (a.run.paths + kThreads - 1) / kThreads;
+    // H entries of this thread: row ra, columns cb .. cb + 31
+    const int ra = t >> 1, cb = (t & 1) * 32;
+    int64_t cnt = 0;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t nl = tile * kThreads + t;
+        const bool valid = nl < a.run.paths;
+        const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
+        const int64_t left = a.run.paths - tile * kThreads;
+        cnt += left < kThreads ? left : kThreads;
+        float W[kD];
+#pragma unroll
+        for (int k = 0; k < kD; ++k) W[k] = 0.0f;
+        if (EXACT) {
+            const int nb = d >> 2;
+            for (int i = 0; i < M; ++i) {
+#pragma unroll
+                for (int kb = 0; kb < kD / 4; ++kb) {
+                    if (kb < nb) {
+                        const float4 z = normals4(static_cast<uint64_t>(i) * nb + kb, n, a.run.k0, a.run.k1);
+                        W[4 * kb] += z.x;
+                        W[4 * kb + 1] += z.y;
+                        W[4 * kb + 2] += z.z;
+                        W[4 * kb + 3] += z.w;
+                    }
+                }
+            }
+        } else {
+            NormalReader rd;
+            rd.init(n, a.run.k0, a.run.k1);
+            for (int i = 0; i < M; ++i) {
+#pragma unroll
+                for (int k = 0; k < kD; ++k)
+                    if (k < d) W[k] += rd.get(static_cast<uint64_t>(i) * d + k);
+            }
+        }
+        // Four passes of 32 paths (one warp each): the staging warp forms its
+        // paths' terminal prices, basket and payoff; all threads then add the
+        // staged paths' u W^T to their H entries.
+        for (int q = 0; q < kThreads / kQuarter; ++q) {
+            if (warp == q) {
+                float U = 0.0f;
+#pragma unroll
+                for (int ra2 = 0; ra2 < kD; ++ra2) {
+                    float y = fM * c.drift[ra2];
+#pragma unroll
+                    for (int k = 0; k <= ra2; ++k) y = fmaf(c.L[ra2 * (ra2 + 1) / 2 + k], W[k], y);
+                    const float p = c.ws0[ra2] * ex2_approx(y);
+                    U += p;
+                    su[lane * kStride + ra2] = p;
+                    sw[lane * kStride + ra2] = W[ra2];
+                }
+                const bool call = a.kind == MC_CALL;
+                const float f = call ? fmaxf(U - a.strike, 0.0f) : fmaxf(a.strike - U, 0.0f);
+                const float slope = call ? (U > a.strike ? 1.0f : 0.0f) : (U < a.strike ? -1.0f : 0.0f);
+                s_slope[lane] = valid ? slope : 0.0f;
+                warp_accumulate(s_acc, 1, 0, valid ? f : 0.0f);
+            }
+            __syncthreads();
+            float acc[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
+            for (int p = 0; p < kQuarter; ++p) {
+                const float ua = s_slope[p] * su[p * kStride + ra];
+                const float4 *wr = reinterpret_cast<const float4 *>(sw + p * kStride + cb);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 w4 = wr[j];
+                    acc[4 * j] = fmaf(ua, w4.x, acc[4 * j]);
+                    acc[4 * j + 1] = fmaf(ua, w4.y, acc[4 * j + 1]);
+                    acc[4 * j + 2] = fmaf(ua, w4.z, acc[4 * j + 2]);
+                    acc[4 * j + 3] = fmaf(ua, w4.w, acc[4 * j + 3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sh[j * kThreads + t] += acc[j];
+            __syncthreads();
+        }
+    }
+    float *dst = a.partials + static_cast<size_t>(blockIdx.x) * kD * kD + ra * kD + cb;
+    for (int j = 0; j < 32; ++j) dst[j] = sh[j * kThreads + t];
+    if (t == 0) a.counts[blockIdx.x] = static_cast<double>(cnt);
+    block_finish(s_acc, s_red, 1, a.red);
+}
+
+// Batch k of B: the FP64 sum of the partials of CTAs k, k + B, k + 2B, ...
+__global__ void corr_batch_kernel(const float *partials, const double *counts, int G, int B, double *Hb,
+                                  double *nb)
+{
+    const int k = blockIdx.x;
+    for (int e = threadIdx.x; e < kD * kD; e += blockDim.x) {
+        double s = 0.0;
+        for (int c = k; c < G; c += B) s += static_cast<double>(partials[static_cast<size_t>(c) * kD * kD + e]);
+        Hb[static_cast<size_t>(k) * kD * kD + e] = s;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int c = k; c < G; c += B) s += counts[c];
+        nb[k] = s;
+    }
+}
+
+// Block k < B: batch k; block B: all paths.  FP64, d <= 64, one CTA each.
+// Outputs per block: dP/dLrho (lower, d-stride) and dP/dcorr (symmetric).
+__global__ void __launch_bounds__(256) corr_adjoint_kernel(int d, int B, const double *Hb, const double *nb,
+                                                            const double *L, const double *cfac, double *out_dl,
+                                                            double *out_drho)
+{
+    extern __shared__ double sm[];
+    double *sL = sm, *sG = sm + d * d, *sA = sm + 2 * d * d;   // Lrho, Lbar then S, A then P then X
+    const int k = blockIdx.x, tid = threadIdx.x;
+    double n = 0.0;
+    if (k < B) n = nb[k];
+    else for (int j = 0; j < B; ++j) n += nb[j];
+    const double inv_n = n > 0.0 ? 1.0 / n : 0.0;
+    double *odl = out_dl + static_cast<size_t>(k) * d * d, *odr = out_drho + static_cast<size_t>(k) * d * d;
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int i = e / d, j = e % d;
+        double h = 0.0;
+        if (j <= i) {
+            if (k < B) h = Hb[static_cast<size_t>(k) * kD * kD + i * kD + j];
+            else for (int q = 0; q < B; ++q) h += Hb[static_cast<size_t>(q) * kD * kD + i * kD + j];
+        }
+        const double g = cfac[i] * h * inv_n;   // Lbar = dP/dLrho
+        sG[e] = g;
+        odl[e] = g;
+        sL[e] = L[e];
+    }
+    __syncthreads();
+    // A = Lrho^T Lbar, then P = Phi(A)
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int i = e / d, j = e % d;
+        double s = 0.0;
+        if (j <= i) {
+            for (int q = i; q < d; ++q) s = fma(sL[q * d + i], sG[q * d + j], s);
+            if (j == i) s *= 0.5;
+        }
+        sA[e] = s;
+    }
+    __syncthreads();
+    // X = P Lrho^-1 (rows, in place): x_ij = (p_ij - sum_{q > j} x_iq L_qj) / L_jj, j = i .. 0
+    if (tid < d) {
+        const int i = tid;
+        for (int j = i; j >= 0; --j) {
+            double s = sA[i * d + j];
+            for (int q = j + 1; q <= i; ++q) s = fma(-sA[i * d + q], sL[q * d + j], s);
+            sA[i * d + j] = s / sL[j * d + j];
+        }
+    }
+    __syncthreads();
+    // S = Lrho^-T X (columns, into sG): s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii, i = d-1 .. 0
+    if (tid < d) {
+        const int j = tid;
+        for (int i = d - 1; i >= 0; --i) {
+            double s = sA[i * d + j];
+            for (int q = i + 1; q < d; ++q) s = fma(-sL[q * d + i], sG[q * d + j], s);
+            sG[i * d + j] = s / sL[i * d + i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += blockDim.x) {
+        const int i = e / d, j = e % d;
+        odr[e] = (i == j) ? 0.0 : sG[i * d + j] + sG[j * d + i];
+    }
+}
+
+// Mean (all-path block) and batch-means standard error
+// se^2 = sum_k n_k (m_k - m)^2 / ((B - 1) N) of each output entry.
+__global__ void corr_finish_kernel(int d, int B, const double *nb, const double *out_dl, const double *out_drho,
+                                   mc_result *res_dl, mc_result *res_drho)
+{
+    const int dd = d * d;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * dd; e += gridDim.x * blockDim.x) {
+        const double *o = e < dd ? out_dl : out_drho;
+        const int i = e < dd ? e : e - dd;
+        const double m = o[static_cast<size_t>(B) * dd + i];
+        double N = 0.0, v = 0.0;
+        for (int k = 0; k < B; ++k) {
+            const double x = o[static_cast<size_t>(k) * dd + i] - m;
+            v = fma(nb[k] * x, x, v);
+            N += nb[k];
+        }
+        mc_result r;
+        r.price = m;
+        r.se = B > 1 && N > 0.0 ? sqrt(v / ((B - 1) * N)) : __longlong_as_double(0x7ff8000000000000ll);
+        (e < dd ? res_dl : res_drho)[i] = r;
+    }
+}
+
+const void *corr_select(const CorrArgs &a)
+{
+    return a.exact4 ? reinterpret_cast<const void *>(&corr_path_kernel<true>)
+                    : reinterpret_cast<const void *>(&corr_path_kernel<false>);
+}
+
+}  // namespace
+
+int corr_occupancy(const CorrArgs &a)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, corr_select(a), kThreads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+int corr_block() { return kThreads; }
+
+size_t corr_adjoint_smem(int d) { return 3 * static_cast<size_t>(d) * d * sizeof(double); }
+
+cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int batches, const double *L,
+                        const double *cfac, double *Hb, double *nb, double *out_dl, double *out_drho,
+                        mc_result *res_dl, mc_result *res_drho, cudaStream_t s)
+{
+    void *args[] = {const_cast<CorrArgs *>(&a), const_cast<CorrConst *>(&c)};
+    cudaError_t e = cudaLaunchKernel(corr_select(a), dim3(grid), dim3(kThreads), args, 0, s);
+    if (e != cudaSuccess) return e;
+    corr_batch_kernel<<<batches, 256, 0, s>>>(a.partials, a.counts, grid, batches, Hb, nb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = corr_adjoint_smem(a.d);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(corr_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    corr_adjoint_kernel<<<batches + 1, 256, smem, s>>>(a.d, batches, Hb, nb, L, cfac, out_dl, out_drho);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int dd2 = 2 * a.d * a.d;
+    corr_finish_kernel<<<(dd2 + 255) / 256, 256, 0, s>>>(a.d, batches, nb, out_dl, out_drho, res_dl, res_drho);
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

@@ -172,6 +172,22 @@ void dfree(T *&p)
     p = nullptr;
 }
 
+// One device allocation carved into 256-byte aligned pieces, freed on scope exit.
+struct DeviceArena {
+    unsigned char *base = nullptr;
+    size_t used = 0;
+    ~DeviceArena() { if (base) cudaFree(base); }
+    static size_t up(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
+    template <class T>
+    T *take(size_t count)
+    {
+        T *p = reinterpret_cast<T *>(base + used);
+        used += up(count * sizeof(T));
+        return p;
+    }
+};
+
+
 }  // namespace
 
 // Polls of a bounded mbarrier wait before a kernel gives up (GBMC_WAIT_CAP
@@ -800,6 +816,107 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
         if (prices) prices[p] = tmp[static_cast<size_t>(p) * (G + 1)];
         for (int k = 0; k < G; ++k) greeks[static_cast<size_t>(p) * G + k] = tmp[static_cast<size_t>(p) * (G + 1) + 1 + k];
     }
+    return MC_OK;
+}
+
+int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay, mc_result *price, mc_result *dl,
+                   mc_result *drho, void *stream)
+{
+    int rc;
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
+    if (!pay) return fail(MC_EINVAL, "payoff is NULL");
+    if (m->kind != MC_GBM || m->loadings || m->d < 2 || m->d > kCorrMaxD)
+        return fail(MC_EUNSUPPORTED, "correlation sensitivities: correlated GBM baskets with 2 <= d <= %d "
+                                     "(Cholesky correlation)", kCorrMaxD);
+    if (c->scheme != MC_LOG_EULER) return fail(MC_EUNSUPPORTED, "correlation sensitivities use the log-Euler scheme");
+    if (c->precision != MC_FP32) return fail(MC_EUNSUPPORTED, "correlation sensitivities are computed in FP32");
+    if (c->monitoring != MC_DISCRETE) return fail(MC_EUNSUPPORTED, "correlation sensitivities: European payoffs only");
+    if (pay->kind != MC_CALL && pay->kind != MC_PUT)
+        return fail(MC_EUNSUPPORTED, "correlation sensitivities: a European basket call or put");
+    if (!std::isfinite(pay->strike)) return fail(MC_EINVAL, "strike not finite");
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int d = m->d;
+    const size_t dd = static_cast<size_t>(d) * d;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt), disc = std::exp(-m->r * c->T);
+
+    CorrArgs a{};
+    a.run.paths = c->paths;
+    a.run.path_offset = c->path_offset;
+    a.run.k0 = static_cast<uint32_t>(c->seed);
+    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    a.run.steps = c->steps;
+    a.run.save_every = 1;
+    a.d = d;
+    a.exact4 = d % 4 == 0 ? 1 : 0;
+    a.kind = pay->kind;
+    a.strike = static_cast<float>(pay->strike);
+    const int occ = corr_occupancy(a);
+    if (occ <= 0) return fail(MC_ECUDA, "correlation-sensitivity kernel cannot be resident");
+    const int64_t tiles = (c->paths + corr_block() - 1) / corr_block();
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(occ) * di.sms));
+    const int B = std::min(grid, 64);
+    const size_t H = static_cast<size_t>(kCorrMaxD) * kCorrMaxD;
+
+    DeviceArena ar;
+    const size_t bytes = DeviceArena::up(dd * 8) * 2 + DeviceArena::up(d * 8) * 2 + DeviceArena::up(sizeof(int)) +
+                         DeviceArena::up(static_cast<size_t>(grid) * H * 4) + DeviceArena::up(grid * 8) +
+                         DeviceArena::up(static_cast<size_t>(B) * H * 8) + DeviceArena::up(B * 8) +
+                         2 * DeviceArena::up((B + 1) * dd * 8) + 2 * DeviceArena::up(dd * sizeof(mc_result)) +
+                         DeviceArena::up(static_cast<size_t>(grid) * 2 * 4) + DeviceArena::up(4) +
+                         DeviceArena::up(sizeof(mc_result)) + DeviceArena::up(sizeof(float) * (kCorrMaxD * (kCorrMaxD + 1) / 2 + kCorrMaxD));
+    MC_CUDA(cudaMalloc(&ar.base, bytes));
+    double *dcorr = ar.take<double>(dd), *dL = ar.take<double>(dd), *dsig = ar.take<double>(d);
+    double *dcfac = ar.take<double>(d);
+    int *dstatus = ar.take<int>(1);
+    a.partials = ar.take<float>(static_cast<size_t>(grid) * H);
+    a.counts = ar.take<double>(grid);
+    double *Hb = ar.take<double>(static_cast<size_t>(B) * H), *nb = ar.take<double>(B);
+    double *odl = ar.take<double>((B + 1) * dd), *odr = ar.take<double>((B + 1) * dd);
+    mc_result *rdl = ar.take<mc_result>(dd), *rdr = ar.take<mc_result>(dd);
+    a.red.partials = ar.take<float>(static_cast<size_t>(grid) * 2);
+    a.red.ticket = ar.take<unsigned int>(1);
+    a.red.out = ar.take<mc_result>(1);
+    float *dLp = ar.take<float>(kCorrMaxD * (kCorrMaxD + 1) / 2 + kCorrMaxD), *ddrift = dLp + kCorrMaxD * (kCorrMaxD + 1) / 2;
+    a.red.paths = c->paths;
+    a.red.disc = disc;
+    a.red.err = nullptr;
+
+    std::vector<double> corr(dd, 0.0), cf(d);
+    if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+    else for (int k = 0; k < d; ++k) corr[static_cast<size_t>(k) * d + k] = 1.0;
+    for (int k = 0; k < d; ++k) cf[k] = disc * sdt * m->sigma[k];
+    MC_CUDA(cudaMemsetAsync(a.red.ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMemcpyAsync(dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dcfac, cf.data(), d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_cholesky(d, dcorr, dL, dstatus, s));
+    MC_CUDA(launch_scale_factor(d, dL, dsig, M_LOG2E, sdt, m->r, dt, MC_LOG_EULER, dLp, ddrift, s));
+    std::vector<float> Lp(static_cast<size_t>(d) * (d + 1) / 2), drift(d);
+    int status = 0;
+    MC_CUDA(cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(Lp.data(), dLp, Lp.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(drift.data(), ddrift, d * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+    CorrConst k{};
+    for (int i = 0; i < d; ++i) {
+        for (int j = 0; j <= i; ++j) k.L[i * (i + 1) / 2 + j] = Lp[static_cast<size_t>(i) * (i + 1) / 2 + j];
+        k.drift[i] = drift[i];
+        const double w = m->weights ? m->weights[i] : 1.0 / d;
+        k.ws0[i] = static_cast<float>(w * m->s0[i]);
+    }
+    MC_CUDA(launch_corr(a, k, grid, B, dL, dcfac, Hb, nb, odl, odr, rdl, rdr, s));
+    mc_result pr;
+    std::vector<mc_result> hdl(dd), hdr(dd);
+    MC_CUDA(cudaMemcpyAsync(&pr, a.red.out, sizeof pr, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(hdl.data(), rdl, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(hdr.data(), rdr, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (price) *price = pr;
+    if (dl) std::memcpy(dl, hdl.data(), dd * sizeof(mc_result));
+    if (drho) std::memcpy(drho, hdr.data(), dd * sizeof(mc_result));
     return MC_OK;
 }
 

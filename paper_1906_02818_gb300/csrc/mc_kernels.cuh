@@ -204,6 +204,37 @@ cudaError_t launch_factor(const FactorArgs &a, int grid, cudaStream_t s);
 int factor_occupancy(const FactorArgs &a);
 int factor_paths_per_cta(const FactorArgs &a);
 
+// Correlation sensitivities (k_corr.cu): European basket call / put,
+// log-Euler, d <= kCorrMaxD; launch-parameter block with the packed FP32
+// factor Lhat = log2(e) sqrt(dt) diag(sigma) Lrho (row a at a(a+1)/2), the
+// per-step log2 drift and w_a S0_a (zero beyond d).
+constexpr int kCorrMaxD = 64;
+struct CorrConst {
+    float L[kCorrMaxD * (kCorrMaxD + 1) / 2];
+    float drift[kCorrMaxD];
+    float ws0[kCorrMaxD];
+};
+struct CorrArgs {
+    PathRun run;
+    int d;
+    int exact4;         // d % 4 == 0: every step is d/4 whole Philox blocks
+    int kind;           // MC_CALL or MC_PUT on U = sum_a w_a S_a(T)
+    float strike;
+    float *partials;    // [grid][64 x 64] per-CTA sums of u_a W_b (FP32)
+    double *counts;     // [grid] paths simulated by each CTA
+    ReduceArgs red;     // the price (one payoff)
+};
+int corr_occupancy(const CorrArgs &a);
+int corr_block();
+size_t corr_adjoint_smem(int d);
+// Path kernel, batch sums (Hb [B][64 x 64], nb [B]), the Cholesky adjoint per
+// batch and for all paths (out_dl, out_drho [B + 1][d x d]), and the means
+// with batch-means standard errors (res_dl, res_drho [d x d]).  L: FP64
+// Cholesky factor of corr [d x d]; cfac[a] = disc sqrt(dt) sigma_a.
+cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int batches, const double *L,
+                        const double *cfac, double *Hb, double *nb, double *out_dl, double *out_drho,
+                        mc_result *res_dl, mc_result *res_drho, cudaStream_t s);
+
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
 // Polls of a bounded mbarrier wait before a tensor-core kernel gives up.

@@ -94,6 +94,9 @@ SIGNATURES = [
     ("mc_greeks", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
                                  ctypes.c_int32, ctypes.POINTER(McResult), ctypes.POINTER(McResult),
                                  ctypes.c_void_p]),
+    ("mc_corr_greeks", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),
+                                      ctypes.POINTER(McResult), ctypes.POINTER(McResult), ctypes.POINTER(McResult),
+                                      ctypes.c_void_p]),
     ("mc_plan_create", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg),
                                       ctypes.POINTER(McPayoff), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),

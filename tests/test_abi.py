@@ -157,3 +157,27 @@ def test_factor_model_checks(lib):
         rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
         assert rc == code, over
         assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
+
+
+def test_correlation_sensitivity_checks(lib):
+    from paper_1906_02818_gb300 import native
+    pr, dl, dr = native.McResult(), (native.McResult * 4096)(), (native.McResult * 4096)()
+    for over, code, needle in [
+            (dict(d=1), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
+            (dict(d=65), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
+            (dict(d=4, loadings=np.full((4, 2), 0.5)), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
+            (dict(d=4, scheme="euler"), native.MC_EUNSUPPORTED, "log-Euler"),
+            (dict(d=4, precision="bf16"), native.MC_EUNSUPPORTED, "FP32"),
+            (dict(d=4, payoffs=[dict(kind="asian_call", strike=100.0)]), native.MC_EUNSUPPORTED, "European"),
+            (dict(d=4, payoffs=[dict(kind="uo_call", strike=100.0, barrier=130.0)]), native.MC_EUNSUPPORTED,
+             "European"),
+            (dict(d=2, corr=np.array([[1.0, 0.5], [0.4, 1.0]])), native.MC_EINVAL, "symmetric")]:
+        mm = _structs(**over)
+        rc = lib.mc_corr_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, ctypes.byref(pr), dl, dr,
+                                None)
+        assert rc == code, over
+        assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
+    mm = _structs(d=4)
+    assert lib.mc_corr_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), None, ctypes.byref(pr), dl, dr,
+                              None) == native.MC_EINVAL
+    assert lib.mc_corr_greeks(None, None, None, None, None, None, None) == native.MC_EINVAL

@@ -1,0 +1,129 @@
+"""GPU parity of the correlation sensitivities (mc_corr_greeks; Sec. I.A.3,
+Sec. VI.A.2): the reverse-mode kernel path (FP32 paths, FP64 Cholesky
+adjoint) against the oracle's forward-mode tangents on identical streams, per
+entry of dP/dLrho and dP/dcorr; the batch-means standard errors against the
+oracle's per-path standard errors; and, at the d = 64 workload's full size,
+the identity that ties dP/dLrho to the basket delta and vega of mc_greeks on
+the same paths.
+
+Tolerance per entry: 2e-5 of the mean absolute per-path contribution (FP32
+normals and sums against FP64), plus the contribution of the paths whose
+basket lies within the FP32 band 2e-5 K of the strike (their payoff slope may
+legitimately differ)."""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import BAND, REL, cfg_of, gbm_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def _market(d, k=3, seed=13):
+    s0, sg, corr = workloads.basket_market(d, k, seed=seed)
+    w = np.full(d, 1.0 / d)
+    return dict(s0=s0, sigma=sg, corr=corr, weights=w, r=0.05, T=1.0, seed=42, steps=1, paths=1)
+
+
+def _check_entries(got, per_path, U, K, label):
+    """got [d, d, 2] (mean, se); per_path [d, d, N] from the oracle."""
+    band = np.abs(U - K) <= BAND * K
+    N = per_path.shape[-1]
+    mean = per_path.mean(axis=-1)
+    scale = np.abs(per_path).mean(axis=-1)
+    flips = np.abs(per_path[..., band]).sum(axis=-1) / N
+    err = np.abs(got[..., 0] - mean)
+    tol = 2e-5 * scale + flips + 1e-12
+    bad = np.argwhere(err > tol)
+    assert bad.size == 0, (label, bad[:5], err[tuple(bad[0])], tol[tuple(bad[0])], int(band.sum()))
+    return mean
+
+
+def _check_se(got, per_path, label):
+    """Batch-means SE against the oracle's per-path SE: median ratio near 1,
+    every ratio within the range of a chi distribution with >= 20 degrees of
+    freedom."""
+    N = per_path.shape[-1]
+    d = per_path.shape[0]
+    mask = per_path.std(axis=-1) > 0
+    mask &= ~np.eye(d, dtype=bool) if label == "drho" else np.tril(np.ones((d, d), dtype=bool))
+    se_ref = per_path.std(axis=-1, ddof=1)[mask] / np.sqrt(N)
+    ratio = got[..., 1][mask] / se_ref
+    assert 0.8 <= np.median(ratio) <= 1.2, (label, np.median(ratio))
+    assert ratio.min() >= 0.3 and ratio.max() <= 2.5, (label, ratio.min(), ratio.max())
+
+
+@pytest.mark.parametrize("d,paths,steps", [(4, 3000, 12), (7, 2900, 9), (64, 2600, 16)])
+@pytest.mark.parametrize("kind", ["call", "put"])
+def test_corr_greeks_match_oracle(gb, orc, d, paths, steps, kind):
+    """d = 4 (whole Philox blocks per step), d = 7 (blocks straddle steps),
+    d = 64 (the basket workload's width); >= 20 tiles of 128 paths with a
+    ragged last tile."""
+    w = _market(d)
+    K = float(w["weights"] @ w["s0"]) * (1.0 if kind == "call" else 1.03)
+    pay = dict(kind=kind, strike=K)
+    (p, pse), dl, dr = gb.corr_greeks(gbm_model(w), cfg_of(w, paths=paths, steps=steps), pay)
+    ref = orc.gbm_corr_greeks(w["s0"], w["sigma"], w["corr"], w["r"], w["T"], steps, paths, pay,
+                              weights=w["weights"])
+    m, se = orc.mean_se(ref["f"])
+    assert abs(p - m) <= REL * abs(m), (p, m)
+    assert abs(pse - se) <= 1e-3 * se
+    _check_entries(dl, ref["dl"], ref["U"], K, "dl")
+    _check_entries(dr, ref["drho"], ref["U"], K, "drho")
+    assert np.all(dl[..., 0][np.triu_indices(d, 1)] == 0.0)
+    assert np.all(dr[..., 0][np.arange(d), np.arange(d)] == 0.0)
+    assert np.allclose(dr[..., 0], dr[..., 0].T, rtol=0, atol=1e-12 * np.abs(dr[..., 0]).max())
+    _check_se(dl, ref["dl"], "dl")
+    _check_se(dr, ref["drho"], "drho")
+
+
+def test_corr_greeks_edge_cases(gb, orc):
+    """Two assets; identity correlation (corr omitted); one tile (<= 128
+    paths: one batch, so NaN standard errors for the sensitivities); a path
+    offset."""
+    w = _market(2)
+    K = float(w["weights"] @ w["s0"])
+    pay = dict(kind="call", strike=K)
+    for corr, paths, off in [(w["corr"], 1000, 0), (None, 700, 12345), (w["corr"], 100, 7)]:
+        ww = dict(w, corr=corr)
+        (p, _), dl, dr = gb.corr_greeks(gbm_model(ww), cfg_of(ww, paths=paths, steps=6, path_offset=off), pay)
+        ref = orc.gbm_corr_greeks(w["s0"], w["sigma"], corr if corr is not None else np.eye(2), w["r"], w["T"], 6,
+                                  paths, pay, weights=w["weights"], path_offset=off)
+        assert abs(p - ref["f"].mean()) <= REL * abs(ref["f"].mean())
+        _check_entries(dl, ref["dl"], ref["U"], K, "dl")
+        _check_entries(dr, ref["drho"], ref["U"], K, "drho")
+        if paths <= 128:
+            assert np.all(np.isnan(dl[..., 1])) and np.all(np.isnan(dr[..., 1]))
+
+
+def test_corr_greeks_d64_full_shape(gb):
+    """The d = 64 workload (2^18 paths, 252 steps, ATM basket call) in full:
+    the price equals mc_price's on the same stream, and per path
+    sum_b Lrho[a][b] dP/dLrho[a][b] = sigma_a vega_a + sigma_a^2 T S0_a delta_a
+    (the diffusion part of vega), so the same holds for the means returned by
+    mc_corr_greeks and mc_greeks (both FP32, different kernels)."""
+    w = workloads.basket_d64()
+    pay = w["payoffs"][0]
+    (p, pse), dl, dr = gb.corr_greeks(gbm_model(w), cfg_of(w), pay)
+    ref = gb.price(gbm_model(w), cfg_of(w), [pay])
+    assert abs(p - ref[0][0]) <= 2 * REL * abs(ref[0][0]), (p, ref)
+    _, g = gb.greeks(gbm_model(w), cfg_of(w), [pay])
+    d = 64
+    delta, vega = g[0, :d, 0], g[0, d:2 * d, 0]
+    L = np.linalg.cholesky(w["corr"])
+    lhs = (L * dl[..., 0]).sum(axis=1)
+    rhs = w["sigma"] * vega + w["sigma"] ** 2 * w["T"] * w["s0"] * delta
+    scale = np.abs(rhs).max()
+    assert np.max(np.abs(lhs - rhs)) <= 1e-4 * scale, np.max(np.abs(lhs - rhs)) / scale
+    # the call gains from correlation (a larger basket variance) on average
+    off = dr[..., 0][~np.eye(d, dtype=bool)]
+    assert off.mean() > 0
+    assert np.all(np.isfinite(dr[..., 1]))

@@ -114,3 +114,18 @@ def test_arithmetic_basket_against_crn_differences(orc, kind):
         assert abs(np.mean(res["drho"][a, b])) > 10 * abs(m)
     base = orc.gbm_payoffs(S0, SIG, R, T, M, N, [pay], corr=CORR)[0]
     assert np.allclose(res["f"], base, rtol=1e-13)
+
+
+def test_factor_tangents_tie_to_delta_and_vega(orc):
+    """Per path, sum_b Lrho[a][b] d/dLrho[a][b] is the diffusion part of the
+    sigma_a tangent: sigma_a vega_a + sigma_a^2 T S0_a delta_a, with delta and
+    vega from the oracle's separate forward-mode Greeks of the same paths."""
+    d, M, N = 4, 10, 2000
+    w = np.array([0.1, 0.4, 0.3, 0.2])
+    pay = dict(kind="call", strike=100.0)
+    res = orc.gbm_corr_greeks(S0, SIG, CORR, R, T, M, N, pay, weights=w)
+    g = orc.gbm_greeks(S0, SIG, R, T, M, N, [pay], corr=CORR, weights=w)[0]
+    L = np.linalg.cholesky(CORR)
+    lhs = np.einsum("ab,abn->an", L, res["dl"])
+    rhs = SIG[:, None] * g[d:2 * d] + (SIG ** 2 * T * S0)[:, None] * g[:d]
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.abs(rhs).max()
