@@ -14,7 +14,7 @@ def __getattr__(name):
                 "surrogate_labels"):
         from . import api
         return getattr(api, name)
-    if name in ("HestonPricer", "GbmPricer"):
+    if name in ("HestonPricer", "GbmPricer", "BasketPricer"):
         from . import autograd
         return getattr(autograd, name)
     raise AttributeError(name)

@@ -8,6 +8,14 @@ float64 CPU tensors (the library returns host results).
   GbmPricer.apply(params, cfg, payoffs)
       params = tensor [3]: (s0, sigma, r)  (single asset, log-Euler)
 Both return the tensor [n_payoff] of discounted prices.
+
+  BasketPricer.apply(s0, sigma, r, corr, cfg, payoff, weights=None)
+      s0, sigma: [d]; r: []; corr: [d, d] (2 <= d <= 64); one European
+      basket call or put, log-Euler, FP32.  Returns the price [].  Backward:
+      d/ds0, d/dsigma, d/dr from mc_greeks and d/dcorr from mc_corr_greeks;
+      the gradient of a correlation entry pair is split evenly between
+      corr[a][b] and corr[b][a] (so a symmetric perturbation of both sees the
+      pair's derivative) and the diagonal, fixed at 1, gets 0.
 """
 from __future__ import annotations
 
@@ -60,3 +68,29 @@ class GbmPricer(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         return _backward(ctx, grad_out)
+
+
+def _basket_model(s0, sigma, r, corr, weights):
+    def arr(t):
+        return t.detach().cpu().double().numpy()
+    return dict(kind="gbm", s0=arr(s0), sigma=arr(sigma), r=float(r), corr=arr(corr), weights=weights)
+
+
+class BasketPricer(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, s0, sigma, r, corr, cfg, payoff, weights=None):
+        model = _basket_model(s0, sigma, r, corr, weights)
+        (p, _), = api.price(model, cfg, [payoff])
+        ctx.model, ctx.cfg, ctx.payoff = model, cfg, payoff
+        ctx.dtype, ctx.device = s0.dtype, s0.device
+        return torch.tensor(p, dtype=s0.dtype, device=s0.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        d = len(ctx.model["s0"])
+        _, g = api.greeks(ctx.model, ctx.cfg, [ctx.payoff])      # [1, 2d + 1, 2]
+        _, _, dr = api.corr_greeks(ctx.model, ctx.cfg, ctx.payoff)
+
+        def t(x):
+            return torch.as_tensor(x, dtype=ctx.dtype, device=ctx.device) * grad_out
+        return (t(g[0, :d, 0]), t(g[0, d:2 * d, 0]), t(g[0, 2 * d, 0]), t(0.5 * dr[..., 0]), None, None, None)

@@ -110,7 +110,7 @@ using tc::wait_or_fail;
 // row at step i), rounded to the operand type and stored swizzled.
 template <int PREC>
 __device__ __forceinline__ void draw_panel(uint32_t pan, int row, int grp, int c0, int i, int d, bool valid, uint64_t n,
-                                           int exact4, uint32_t k0, uint32_t k1, NormalReader &rd)
+                                           int exact4, const RoundKeys &rk, NormalReader &rd)
 {
     using Ly = L2<PREC>;
     float z[16];
@@ -121,7 +121,7 @@ __device__ __forceinline__ void draw_panel(uint32_t pan, int row, int grp, int c
             const uint64_t q = (static_cast<uint64_t>(i) * d + c0) >> 2;
 #pragma unroll
             for (int bq = 0; bq < 4; ++bq) {
-                const float4 v = normals4(q + bq, n, k0, k1);
+                const float4 v = normals4(q + bq, n, rk);
                 z[4 * bq] = v.x; z[4 * bq + 1] = v.y; z[4 * bq + 2] = v.z; z[4 * bq + 3] = v.w;
             }
         } else {
@@ -142,7 +142,7 @@ __device__ __forceinline__ void draw_panel(uint32_t pan, int row, int grp, int c
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a)
+__global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_constant__ BigArgs a)
 {
     using Ly = L2<PREC>;
     extern __shared__ uint8_t smem_raw[];
@@ -273,14 +273,14 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const BigArgs a
             const bool valid = nl < a.run.paths;
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
             NormalReader rd;
-            rd.init(n, a.run.k0, a.run.k1);
+            rd.init(n, a.run.rk);
             for (int i = 0; i < M; ++i, ++g) {
                 for (int hh = 0; hh < 2; ++hh) {
                     const bool ok = g == 0 || wait_or_fail(&s_fail, zfree + 8 * hh, static_cast<uint32_t>((g - 1) & 1), cap);
                     if (ok && !s_fail) {
                         for (int p = hh ? half : 0; p < (hh ? NP : half); ++p)
                             draw_panel<PREC>(zt + p * Ly::kPanelBytes, row, grp, p * kPanel + grp * 16, i, d, valid, n,
-                                             a.exact4, a.run.k0, a.run.k1, rd);
+                                             a.exact4, a.run.rk, rd);
                         tc::fence_proxy_async();
                     }
                     mbar_arrive(zfull + 8 * hh);  // always: the MMA issuer counts 512 arrivals

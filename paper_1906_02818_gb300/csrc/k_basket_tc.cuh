@@ -91,8 +91,8 @@ struct Stats {
 // Draws Z_i of path n (row `row`) into the tile at `tile`; returns the
 // dequantisation factor of the row (1 unless E4M3).
 template <int PREC, bool EXACT>
-__device__ __forceinline__ float draw_row(uint32_t tile, int row, int i, int d, uint64_t n, uint32_t k0,
-                                          uint32_t k1, NormalReader &rd, bool valid)
+__device__ __forceinline__ float draw_row(uint32_t tile, int row, int i, int d, uint64_t n,
+                                          const RoundKeys &rk, NormalReader &rd, bool valid)
 {
     using Ly = Layout<PREC>;
     auto normal8 = [&](int c0, float (&z)[8]) {
@@ -101,7 +101,7 @@ __device__ __forceinline__ float draw_row(uint32_t tile, int row, int i, int d, 
             for (int l = 0; l < 8; ++l) z[l] = 0.0f;
         } else if (EXACT) {
             const uint64_t q = static_cast<uint64_t>(i) * (kN / 4) + c0 / 4;
-            const float4 a = normals4(q, n, k0, k1), b = normals4(q + 1, n, k0, k1);
+            const float4 a = normals4(q, n, rk), b = normals4(q + 1, n, rk);
             z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
         } else {
 #pragma unroll
@@ -157,7 +157,7 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem_d, uint32_t ztile, uint
 }
 
 template <int PREC, int SCHEME, bool STATS, bool EXACT>
-__global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, const TcConst c)
+__global__ void __launch_bounds__(kThreads) basket_tc_kernel(const __grid_constant__ TcArgs a, const TcConst c)
 {
     using Ly = Layout<PREC>;
     extern __shared__ uint8_t smem_raw[];
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
         const bool valid = nl < a.run.paths;
         const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
         NormalReader rd;
-        rd.init(n, a.run.k0, a.run.k1);
+        rd.init(n, a.run.rk);
         float x[kN];
 #pragma unroll
         for (int j = 0; j < kN; ++j) x[j] = (SCHEME == MC_LOG_EULER) ? 0.0f : c.s0[j];
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
 
         float deq_cur = 1.0f, deq_next = 1.0f;
         if (!aborted) {
-            deq_cur = draw_row<PREC, EXACT>(zt[0], t, 0, d, n, a.run.k0, a.run.k1, rd, valid);
+            deq_cur = draw_row<PREC, EXACT>(zt[0], t, 0, d, n, a.run.rk, rd, valid);
             tc::fence_proxy_async();
         }
         __syncthreads();
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
         }
         for (int i = 0; i < M && !aborted; ++i) {
             if (i + 1 < M) {
-                deq_next = draw_row<PREC, EXACT>(zt[(i + 1) & 1], t, i + 1, d, n, a.run.k0, a.run.k1, rd, valid);
+                deq_next = draw_row<PREC, EXACT>(zt[(i + 1) & 1], t, i + 1, d, n, a.run.rk, rd, valid);
                 tc::fence_proxy_async();
             }
             const bool ok = tc::mbar_wait_bounded(mbar, phase & 1u, a.wait_cap);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const TcArgs a, con
 // registers) lets 8 CTAs share an SM, which hides each CTA's MMA wait behind
 // the others' normals.  Bounded waits as in basket_tc_kernel.
 template <int PREC, bool STATS, bool EXACT>
-__global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const TcArgs a, const TcConst c)
+__global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid_constant__ TcArgs a, const TcConst c)
 {
     using Ly = Layout<PREC>;
     extern __shared__ uint8_t smem_raw[];
@@ -359,11 +359,11 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const TcArgs
         const bool valid = nl < a.run.paths;
         const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
         NormalReader rd;
-        rd.init(n, a.run.k0, a.run.k1);
+        rd.init(n, a.run.rk);
         Stats st{0.0f, -INFINITY, INFINITY};
         bool ok = true;
         for (int i = 0; i < M; ++i) {
-            if (!aborted) draw_row<PREC, EXACT>(zt, t, i, d, n, a.run.k0, a.run.k1, rd, valid);
+            if (!aborted) draw_row<PREC, EXACT>(zt, t, i, d, n, a.run.rk, rd, valid);
             tc::fence_proxy_async();
             tc::fence_before_sync();  // this thread's accumulator reads precede the next MMA
             if (__syncthreads_or(ok ? 0 : 1)) aborted = true;

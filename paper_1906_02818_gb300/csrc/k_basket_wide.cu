@@ -31,7 +31,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs a)
+__global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_constant__ BigArgs a)
 {
     constexpr int J = D / 128;  // 4-asset groups per thread
     extern __shared__ __align__(16) float sm[];
@@ -62,14 +62,14 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const BigArgs 
         const bool rvalid = rnl < a.run.paths;
         const uint64_t rn = static_cast<uint64_t>(a.run.path_offset + (rvalid ? rnl : 0));
         NormalReader rd;
-        rd.init(rn, a.run.k0, a.run.k1);
+        rd.init(rn, a.run.rk);
         for (int i = 0; i < M; ++i) {
             __syncthreads();  // previous step done with zs
             for (int k = rq * (D / 8); k < (rq + 1) * (D / 8); k += 4) {
                 float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (rvalid && k < d) {
                     if (a.exact4) {
-                        z = normals4((static_cast<uint64_t>(i) * d + k) >> 2, rn, a.run.k0, a.run.k1);
+                        z = normals4((static_cast<uint64_t>(i) * d + k) >> 2, rn, a.run.rk);
                     } else {
                         const uint64_t j0 = static_cast<uint64_t>(i) * d + k;
                         z.x = rd.get(j0);

@@ -27,7 +27,7 @@ constexpr int kQuarter = 32;      // paths staged per outer-product pass
 constexpr int kStride = kD + 4;   // shared row stride (floats; 16-B aligned rows)
 
 template <bool EXACT>
-__global__ void __launch_bounds__(kThreads) corr_path_kernel(const CorrArgs a, const CorrConst c)
+__global__ void __launch_bounds__(kThreads) corr_path_kernel(const __grid_constant__ CorrArgs a, const CorrConst c)
 {
     __shared__ __align__(16) float su[kQuarter * kStride];   // w_a S_a(T) of the staged paths
     __shared__ __align__(16) float sw[kQuarter * kStride];   // W of the staged paths
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) corr_path_kernel(const CorrArgs a, c
 #pragma unroll
                 for (int kb = 0; kb < kD / 4; ++kb) {
                     if (kb < nb) {
-                        const float4 z = normals4(static_cast<uint64_t>(i) * nb + kb, n, a.run.k0, a.run.k1);
+                        const float4 z = normals4(static_cast<uint64_t>(i) * nb + kb, n, a.run.rk);
                         W[4 * kb] += z.x;
                         W[4 * kb + 1] += z.y;
                         W[4 * kb + 2] += z.z;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) corr_path_kernel(const CorrArgs a, c
             }
         } else {
             NormalReader rd;
-            rd.init(n, a.run.k0, a.run.k1);
+            rd.init(n, a.run.rk);
             for (int i = 0; i < M; ++i) {
 #pragma unroll
                 for (int k = 0; k < kD; ++k)

@@ -26,7 +26,7 @@ constexpr int kP = 4;   // paths per warp
 constexpr int kA = 8;   // assets per lane
 
 template <int SCHEME, bool STATS, bool EXACT>
-__global__ void __launch_bounds__(kBlock, 2) factor_kernel(const FactorArgs a)
+__global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant__ FactorArgs a)
 {
     extern __shared__ float smem[];
     const int d = a.d, k = a.k, G = a.G, dp = 256 * G;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const FactorArgs a)
         NormalReader rd[kP];
         if (!EXACT) {
 #pragma unroll
-            for (int p = 0; p < kP; ++p) rd[p].init(n[p], a.run.k0, a.run.k1);
+            for (int p = 0; p < kP; ++p) rd[p].init(n[p], a.run.rk);
         }
         for (int i = 0; i < M; ++i) {
             const uint64_t base = static_cast<uint64_t>(i) * stride;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const FactorArgs a)
                     uint64_t np = n[0];
 #pragma unroll
                     for (int q = 1; q < kP; ++q) np = (p == q) ? n[q] : np;
-                    zb = normals4(base / 4 + b, np, a.run.k0, a.run.k1);
+                    zb = normals4(base / 4 + b, np, a.run.rk);
                 }
 #pragma unroll
                 for (int p = 0; p < kP; ++p)
@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const FactorArgs a)
                 float eps[kA];
                 if (EXACT) {
                     const uint64_t q = (base + k + a0) / 4;
-                    const float4 e0 = a0 < d ? normals4(q, n[p], a.run.k0, a.run.k1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 e1 = a0 + 4 < d ? normals4(q + 1, n[p], a.run.k0, a.run.k1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 e0 = a0 < d ? normals4(q, n[p], a.run.rk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 e1 = a0 + 4 < d ? normals4(q + 1, n[p], a.run.rk) : make_float4(0.f, 0.f, 0.f, 0.f);
                     eps[0] = e0.x; eps[1] = e0.y; eps[2] = e0.z; eps[3] = e0.w;
                     eps[4] = e1.x; eps[5] = e1.y; eps[6] = e1.z; eps[7] = e1.w;
                 } else {

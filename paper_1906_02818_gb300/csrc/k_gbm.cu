@@ -29,11 +29,11 @@ __device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet
 }
 
 // Four uniforms of Philox block q of stream n (the same map as the normals).
-__device__ __forceinline__ float4 uniforms4(uint64_t q, uint64_t n, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ float4 uniforms4(uint64_t q, uint64_t n, const RoundKeys &rk)
 {
     const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
                                              static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)),
-                                  k0, k1);
+                                  rk);
     return make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w));
 }
 
@@ -46,7 +46,7 @@ constexpr uint64_t kBridgeDomain = uint64_t(1) << 56;  // stream of path n's bri
 // (Sec. VI.A.1; the formula in log2 units) and the minimum with the root
 // subtracted; U = uniforms 2i and 2i + 1 of the bridge stream.
 template <int SCHEME, bool STATS, bool SAVE, bool BRIDGE>
-__global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
+__global__ void __launch_bounds__(kBlock) gbm1d_kernel(const __grid_constant__ Gbm1dArgs a)
 {
     __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
@@ -70,12 +70,12 @@ __global__ void __launch_bounds__(kBlock) gbm1d_kernel(const Gbm1dArgs a)
             if (SAVE) a.run.save[nl] = a.s0;
             const int nq = (M + 3) >> 2;
             for (int q = 0; q < nq; ++q) {
-                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.k0, a.run.k1);
+                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.rk);
                 const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
                 float4 ub[2];
                 if (BRIDGE) {  // uniforms 8q .. 8q + 7: (max, min) of steps 4q .. 4q + 3
-                    ub[0] = uniforms4(2 * static_cast<uint64_t>(q), kBridgeDomain + n, a.run.k0, a.run.k1);
-                    ub[1] = uniforms4(2 * static_cast<uint64_t>(q) + 1, kBridgeDomain + n, a.run.k0, a.run.k1);
+                    ub[0] = uniforms4(2 * static_cast<uint64_t>(q), kBridgeDomain + n, a.run.rk);
+                    ub[1] = uniforms4(2 * static_cast<uint64_t>(q) + 1, kBridgeDomain + n, a.run.rk);
                 }
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {

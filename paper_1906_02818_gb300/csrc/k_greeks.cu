@@ -60,7 +60,7 @@ __device__ __forceinline__ void accumulate_greeks(float *s_acc, const PayoffSet 
 }
 
 // ------------------------------ 1-D GBM ----------------------------------
-__global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const GreeksArgs a)
+__global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const __grid_constant__ GreeksArgs a)
 {
     extern __shared__ float s_acc[];
     __shared__ double s_red[32];
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const GreeksArgs a
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             float y = 0.0f, W = 0.0f, sS = 0.0f, sSt = 0.0f, sSW = 0.0f;
             for (int q = 0; q < (M + 3) / 4; ++q) {
-                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.k0, a.run.k1);
+                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.rk);
                 const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const GreeksArgs a
 
 // --------------------------- Heston adjoint --------------------------------
 // Greek order: 0 S0, 1 v0, 2 r, 3 kappa, 4 theta, 5 xi, 6 rho.
-__global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const GreeksArgs a)
+__global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const __grid_constant__ GreeksArgs a)
 {
     extern __shared__ float s_acc[];
     __shared__ double s_red[32];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const GreeksArgs
         if (valid) {
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             NormalReader rd;
-            rd.init(n, a.run.k0, a.run.k1);
+            rd.init(n, a.run.rk);
             // forward pass with checkpoints every K steps
             float x = 0.0f, v = a.v0, sS = 0.0f;
             for (int s = 0; s < nseg; ++s) {

@@ -13,7 +13,7 @@ namespace {
 constexpr int kBlock = 256;
 
 template <bool STATS, bool SAVE>
-__global__ void __launch_bounds__(kBlock) heston_kernel(const HestonArgs a)
+__global__ void __launch_bounds__(kBlock) heston_kernel(const __grid_constant__ HestonArgs a)
 {
     __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kBlock) heston_kernel(const HestonArgs a)
             }
             const int nq = (M + 1) >> 1;
             for (int q = 0; q < nq; ++q) {
-                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.k0, a.run.k1);
+                const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.rk);
                 const float z1s[2] = {z4.x, z4.z}, z2s[2] = {z4.y, z4.w};
 #pragma unroll
                 for (int l = 0; l < 2; ++l) {

@@ -98,8 +98,7 @@ extern "C" int mc_price_gbm1d_noalloc(const mc_model *m, const mc_sim_cfg *c, co
     Gbm1dArgs a{};
     a.run.paths = c->paths;
     a.run.path_offset = c->path_offset;
-    a.run.k0 = static_cast<uint32_t>(c->seed);
-    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    set_seed(a.run, c->seed);
     a.run.steps = c->steps;
     a.run.save = nullptr;
     a.run.save_every = 1;

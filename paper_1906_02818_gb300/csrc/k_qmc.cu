@@ -27,7 +27,7 @@ constexpr int kBlock = 256;
 constexpr int kDmax = kQmcMaxAssets;
 
 template <int SCHEME, bool STATS>
-__global__ void __launch_bounds__(kBlock) qmc_kernel(const QmcArgs a, const QmcConst c)
+__global__ void __launch_bounds__(kBlock) qmc_kernel(const __grid_constant__ QmcArgs a, const QmcConst c)
 {
     __shared__ uint32_t s_v[kQmcMaxDims][32];
     __shared__ uint32_t s_shift[kQmcMaxDims];
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kBlock) qmc_kernel(const QmcArgs a, const QmcC
         const uint64_t stream = (uint64_t(6) << 56) | static_cast<uint64_t>(rep);
         const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(t), 0u, static_cast<uint32_t>(stream),
                                                  static_cast<uint32_t>(stream >> 32)),
-                                      a.k0, a.k1);
+                                      a.rk);
         const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
         for (int l = 0; l < 4 && 4 * t + l < nd; ++l) s_shift[4 * t + l] = w4[l];
     }

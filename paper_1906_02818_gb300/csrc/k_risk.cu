@@ -39,7 +39,7 @@ __device__ __forceinline__ void surrogate_inputs(float sk, float sig, float tau,
 
 // ------------------------------ labels -----------------------------------
 __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *__restrict__ pts, int paths,
-                                                    float steps_per_year, uint32_t k0, uint32_t k1,
+                                                    float steps_per_year, const __grid_constant__ RoundKeys rk,
                                                     float *__restrict__ labels, float *__restrict__ inputs)
 {
     __shared__ double s_red[8];
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
                 float y = 0.0f;
                 bool alive = true;
                 for (int q = 0; q < (M + 3) / 4; ++q) {
-                    const float4 z = normals4(static_cast<uint64_t>(q), n, k0, k1);
+                    const float4 z = normals4(static_cast<uint64_t>(q), n, rk);
                     const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
 // ------------------------------ scenarios --------------------------------
 // Lc: [d x d] FP32 of sqrt(h) diag(sigma) Lrho (lower); drift_u = (mu - sigma^2/2) h.
 __global__ void outer_kernel(int64_t nscen, int64_t off, int d, const float *__restrict__ Lc,
-                             const float *__restrict__ drift, const float *__restrict__ s0, uint32_t k0, uint32_t k1,
+                             const float *__restrict__ drift, const float *__restrict__ s0, const __grid_constant__ RoundKeys rk,
                              float *__restrict__ Sp)
 {
     extern __shared__ float sL[];
@@ -97,7 +97,7 @@ __global__ void outer_kernel(int64_t nscen, int64_t off, int d, const float *__r
     for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < nscen;
          s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         NormalReader rd;
-        rd.init(tag(2, static_cast<uint64_t>(off + s)), k0, k1);  // global scenario index
+        rd.init(tag(2, static_cast<uint64_t>(off + s)), rk);  // global scenario index
         for (int u = 0; u < d; ++u) z[u] = rd.get(u);
         for (int u = 0; u < d; ++u) {
             float w = 0.0f;
@@ -111,7 +111,7 @@ __global__ void outer_kernel(int64_t nscen, int64_t off, int d, const float *__r
 // One CTA per (scenario s, underlying u); inner paths from S'_u, daily steps,
 // every option of u valued at its remaining maturity; out[s*d + u] =
 // sum_{o of u} pos_o (V_o(s) - base_o) in FP64.
-__global__ void __launch_bounds__(256) nested_kernel(RiskArgs a, const float *__restrict__ Sp, double *__restrict__ out)
+__global__ void __launch_bounds__(256) nested_kernel(const __grid_constant__ RiskArgs a, const float *__restrict__ Sp, double *__restrict__ out)
 {
     __shared__ double s_v[kRiskMaxOptPerUnder];
     __shared__ double s_red[8][kRiskMaxOptPerUnder];
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) nested_kernel(RiskArgs a, const float *__
         float y = 0.0f, mx = -INFINITY;  // log2(S/S1) and its running maximum over the dates
         int jn = 0;                      // next option to mature
         for (int q = 0; q < (maxrem + 3) / 4; ++q) {
-            const float4 z = normals4(static_cast<uint64_t>(q), n, a.k0, a.k1);
+            const float4 z = normals4(static_cast<uint64_t>(q), n, a.rk);
             const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
@@ -310,20 +310,20 @@ __global__ void __launch_bounds__(1024) tail_kernel(int64_t n, const double *pnl
 
 }  // namespace
 
-cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float spy, uint32_t k0, uint32_t k1,
+cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float spy, const RoundKeys &rk,
                           float *labels, float *inputs, cudaStream_t s)
 {
     const int64_t g = npts < 1216 * 4 ? npts : 1216 * 4;
-    label_kernel<<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, k0, k1, labels, inputs);
+    label_kernel<<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, rk, labels, inputs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_outer(int64_t nscen, int64_t off, int d, const float *Lc, const float *drift, const float *s0,
-                         uint32_t k0, uint32_t k1, float *Sp, cudaStream_t s)
+                         const RoundKeys &rk, float *Sp, cudaStream_t s)
 {
     const int64_t g = (nscen + 127) / 128;
     outer_kernel<<<static_cast<int>(g < 4096 ? g : 4096), 128, d * d * sizeof(float), s>>>(nscen, off, d, Lc, drift,
-                                                                                            s0, k0, k1, Sp);
+                                                                                            s0, rk, Sp);
     return cudaGetLastError();
 }
 

@@ -416,8 +416,7 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
     PathRun run{};
     run.paths = c->paths;
     run.path_offset = c->path_offset;
-    run.k0 = static_cast<uint32_t>(c->seed);
-    run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    set_seed(run, c->seed);
     run.steps = c->steps;
     run.save = save;
     run.save_every = save_every > 0 ? save_every : 1;
@@ -724,8 +723,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
         PathRun run{};
         run.paths = c->paths;
         run.path_offset = c->path_offset;
-        run.k0 = static_cast<uint32_t>(c->seed);
-        run.k1 = static_cast<uint32_t>(c->seed >> 32);
+        set_seed(run, c->seed);
         run.steps = c->steps;
         run.save_every = 1;
         mc_plan P;
@@ -758,8 +756,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     GreeksArgs a{};
     a.run.paths = c->paths;
     a.run.path_offset = c->path_offset;
-    a.run.k0 = static_cast<uint32_t>(c->seed);
-    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    set_seed(a.run, c->seed);
     a.run.steps = c->steps;
     a.run.save_every = 1;
     a.model = m->kind;
@@ -844,8 +841,7 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
     CorrArgs a{};
     a.run.paths = c->paths;
     a.run.path_offset = c->path_offset;
-    a.run.k0 = static_cast<uint32_t>(c->seed);
-    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    set_seed(a.run, c->seed);
     a.run.steps = c->steps;
     a.run.save_every = 1;
     a.d = d;
@@ -995,8 +991,7 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     MlmcArgs a{};
     a.run.paths = paths_ref;
     a.run.path_offset = c->path_offset + c->paths;
-    a.run.k0 = static_cast<uint32_t>(c->seed);
-    a.run.k1 = static_cast<uint32_t>(c->seed >> 32);
+    set_seed(a.run, c->seed);
     a.run.steps = c->steps;
     a.run.save_every = 1;
     a.d = d;
@@ -1109,6 +1104,7 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
     a.reps = reps;
     a.k0 = static_cast<uint32_t>(c->seed);
     a.k1 = static_cast<uint32_t>(c->seed >> 32);
+    a.rk = round_keys(a.k0, a.k1);
     a.pay = ps;
     MC_CUDA(cudaMalloc(&P.dsums, static_cast<size_t>(reps) * np * sizeof(double)));
     MC_CUDA(cudaMemsetAsync(P.dsums, 0, static_cast<size_t>(reps) * np * sizeof(double), s));

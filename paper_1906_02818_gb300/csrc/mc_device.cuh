@@ -16,9 +16,26 @@ constexpr float kLog2e = 1.4426950408889634f;
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
 // with the round multipliers, xor of the high halves with the other counter
-// words and the round key, and a Weyl bump of the key between rounds.
+// words and the round key, and a Weyl bump of the key between rounds.  The
+// ten round keys are formed once per launch on the host and read from the
+// kernel's parameter block (constant bank), so no round spends an
+// instruction or a register on the key schedule.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+struct RoundKeys {
+    uint32_t k[20];  // round r: (k[2r], k[2r + 1]) = (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85)
+};
+
+__host__ __device__ inline RoundKeys round_keys(uint32_t k0, uint32_t k1)
+{
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        rk.k[2 * r + 1] = k1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
@@ -26,9 +43,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
         const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
         const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ rk.k[2 * round], lo1, hi0 ^ c.w ^ rk.k[2 * round + 1], lo0);
     }
     return c;
 }
@@ -91,11 +106,11 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, fl
 }
 
 // The four normals of block q of stream (path) n.
-__device__ __forceinline__ float4 normals4(uint64_t q, uint64_t n, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ float4 normals4(uint64_t q, uint64_t n, const RoundKeys &rk)
 {
     const uint4 x = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
                                              static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)),
-                                  k0, k1);
+                                  rk);
     float4 z;
     box_muller(x.x, x.y, z.x, z.y);
     box_muller(x.z, x.w, z.z, z.w);
@@ -106,17 +121,17 @@ __device__ __forceinline__ float4 normals4(uint64_t q, uint64_t n, uint32_t k0, 
 // j leaves the cached one (warp-uniform when all lanes are at the same j).
 struct NormalReader {
     uint64_t n;
-    uint32_t k0, k1;
+    const RoundKeys *rk;
     uint64_t q;
     float4 z;
-    __device__ __forceinline__ void init(uint64_t stream, uint32_t key0, uint32_t key1)
+    __device__ __forceinline__ void init(uint64_t stream, const RoundKeys &keys)
     {
-        n = stream; k0 = key0; k1 = key1; q = ~0ull;
+        n = stream; rk = &keys; q = ~0ull;
     }
     __device__ __forceinline__ float get(uint64_t j)
     {
         const uint64_t qj = j >> 2;
-        if (qj != q) { q = qj; z = normals4(qj, n, k0, k1); }
+        if (qj != q) { q = qj; z = normals4(qj, n, *rk); }
         const uint32_t l = static_cast<uint32_t>(j) & 3u;
         return l == 0 ? z.x : (l == 1 ? z.y : (l == 2 ? z.z : z.w));
     }

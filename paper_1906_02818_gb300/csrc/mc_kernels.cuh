@@ -13,11 +13,20 @@ struct PathRun {
     int64_t paths;        // paths of this launch
     int64_t path_offset;  // global index of the first one
     uint32_t k0, k1;      // Philox key
+    RoundKeys rk;         // its ten round keys (set_seed)
     int steps;
     int ppt;              // paths per thread (grid-stride count)
     float *save;          // mc_simulate output or nullptr
     int save_every;
 };
+
+// Key (seed lo, seed hi) and its round keys.
+inline void set_seed(PathRun &r, uint64_t seed)
+{
+    r.k0 = static_cast<uint32_t>(seed);
+    r.k1 = static_cast<uint32_t>(seed >> 32);
+    r.rk = round_keys(r.k0, r.k1);
+}
 
 // Single-asset GBM.  log-Euler: y = log2(S/S0) += a + b z with
 // a = log2(e) (r - sigma^2/2) dt, b = log2(e) sigma sqrt(dt).
@@ -177,6 +186,7 @@ struct QmcArgs {
     int64_t n0, npts;   // first point index, points per replication
     int steps, d, scheme, ndim, reps;
     uint32_t k0, k1;    // Philox key of the digital shifts
+    RoundKeys rk;       // its round keys
     PayoffSet pay;
     double *sums;       // [reps][n_payoff] undiscounted payoff totals (zero on entry)
 };

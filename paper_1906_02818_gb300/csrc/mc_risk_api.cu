@@ -64,7 +64,7 @@ int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths
     if (paths < 1 || paths > 65536) return fail(MC_EINVAL, "paths must lie in [1, 65536]");
     if (steps_per_year < 1) return fail(MC_EINVAL, "steps_per_year must be >= 1");
     RK_CUDA(launch_labels(n_points, dev_points, paths, static_cast<float>(steps_per_year),
-                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), dev_labels, dev_inputs,
+                          round_keys(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)), dev_labels, dev_inputs,
                           static_cast<cudaStream_t>(stream)));
     return MC_OK;
 }
@@ -177,7 +177,8 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
     RK_CUDA(cudaMemcpyAsync(d_Lc, Lc.data(), Lc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     RK_CUDA(cudaMemcpyAsync(d_drift, drift.data(), d * sizeof(float), cudaMemcpyHostToDevice, s));
     const uint32_t k0 = static_cast<uint32_t>(cf->seed), k1 = static_cast<uint32_t>(cf->seed >> 32);
-    RK_CUDA(launch_outer(ns, cf->scen_offset, d, d_Lc, d_drift, d_s0, k0, k1, d_Sp, s));
+    const RoundKeys rk = round_keys(k0, k1);
+    RK_CUDA(launch_outer(ns, cf->scen_offset, d, d_Lc, d_drift, d_s0, rk, d_Sp, s));
 
     RiskArgs a{};
     a.d = d;
@@ -196,8 +197,7 @@ int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, 
     a.pos = d_pos;
     a.base = d_base;
     a.base_out = d_base;
-    a.k0 = k0;
-    a.k1 = k1;
+    a.rk = rk;
     a.scen_off = cf->scen_offset;
     if (cf->method == MC_RISK_NESTED) {
         double *d_contrib;

@@ -23,14 +23,14 @@ struct RiskArgs {
     const double *pos, *base;
     double *base_out;
     int inner;
-    uint32_t k0, k1;
+    RoundKeys rk;      // Philox round keys of the seed
     int64_t scen_off;  // global index of the first scenario (stream indices)
 };
 
-cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float steps_per_year, uint32_t k0, uint32_t k1,
+cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float steps_per_year, const RoundKeys &rk,
                           float *labels, float *inputs, cudaStream_t s);
 cudaError_t launch_outer(int64_t nscen, int64_t off, int d, const float *Lc, const float *drift, const float *s0,
-                         uint32_t k0, uint32_t k1, float *Sp, cudaStream_t s);
+                         const RoundKeys &rk, float *Sp, cudaStream_t s);
 cudaError_t launch_nested(const RiskArgs &a, int64_t nscen, const float *Sp, double *contrib, cudaStream_t s);
 cudaError_t launch_sum_under(int64_t nscen, int d, const double *contrib, double *pnl, cudaStream_t s);
 cudaError_t launch_features(const RiskArgs &a, int64_t nscen, const float *Sp, float *x, cudaStream_t s);

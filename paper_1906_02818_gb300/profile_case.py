@@ -13,6 +13,7 @@
   python -m paper_1906_02818_gb300.profile_case qmc --paths 262144              (points x 16 replications)
   python -m paper_1906_02818_gb300.profile_case mlmc --paths 16384              (correction paths, d = 64, bf16)
   python -m paper_1906_02818_gb300.profile_case factor512 --paths 65536
+  python -m paper_1906_02818_gb300.profile_case corr64 --paths 65536          (correlation sensitivities, d = 64)
 """
 from __future__ import annotations
 
@@ -31,12 +32,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
-                                     "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512"])
+                                     "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512", "corr64"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case in ("mlp", "labels", "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512"):
+    if a.case in ("mlp", "labels", "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512", "corr64"):
         _other(a, torch, workloads, gb)
         return
     if a.case in ("heston", "heston_greeks"):
@@ -93,6 +94,12 @@ def _other(a, torch, workloads, gb):
         for _ in range(a.reps):
             r = gb.price_mlmc(model, cfg, w["payoffs"], a.paths or (1 << 14))
         print(a.case, r[0]["price"], r[0]["correction"])
+    elif a.case == "corr64":
+        w = workloads.basket_d64(paths=a.paths or (1 << 18))
+        model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], corr=w["corr"], weights=w["weights"], r=w["r"])
+        for _ in range(a.reps):
+            r = gb.corr_greeks(model, dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=42), w["payoffs"][0])
+        print(a.case, r[0])
     elif a.case == "factor512":
         w = workloads.basket_d512_factor(paths=a.paths or (1 << 16))
         model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], loadings=w["loadings"], weights=w["weights"], r=w["r"])
