@@ -143,6 +143,15 @@ typedef struct {
 /* Library version (MC_VERSION of the build). */
 int mc_version(void);
 
+/* Device scratch of the set-up paths (model copies, Cholesky factors,
+ * per-block partials, checkpoints) is taken from a per-device cache of blocks
+ * that earlier calls released, so repeated calls of one shape allocate
+ * nothing; a block is cached only once the call or plan that used it has
+ * synchronised.  mc_release_cache frees every cached block (all devices) back
+ * to CUDA; blocks held by live plans or running calls are not affected.
+ * Returns MC_OK. */
+int mc_release_cache(void);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *mc_last_error(void);
 

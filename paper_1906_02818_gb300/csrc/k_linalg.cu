@@ -49,6 +49,43 @@ __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const doubl
     if (threadIdx.x == 0) *status = s_fail;
 }
 
+// The same factorisation for d <= 64 with W in shared memory (the same FP64
+// operations in the same order as cholesky_kernel).
+constexpr int kCholSmallD = 64;
+constexpr int kCholSmallBlock = 256;
+__global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, const double *A, double *L, int *status)
+{
+    __shared__ double W[kCholSmallD][kCholSmallD + 1];
+    __shared__ int s_fail;
+    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) W[idx / d][idx % d] = A[idx];
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    for (int k = 0; k < d; ++k) {
+        if (threadIdx.x == 0) {
+            const double p = W[k][k];
+            if (!(p > 0.0)) s_fail = 1;
+            else W[k][k] = sqrt(p);
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const double lkk = W[k][k];
+        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[i][k] /= lkk;
+        __syncthreads();
+        const int m = d - k - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int ii = idx / m, jj = idx % m;
+            if (jj <= ii) W[k + 1 + ii][k + 1 + jj] -= W[k + 1 + ii][k] * W[k + 1 + jj][k];
+        }
+        __syncthreads();
+    }
+    if (!s_fail)
+        for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+            const int i = idx / d, j = idx % d;
+            L[idx] = j > i ? 0.0 : W[i][j];
+        }
+    if (threadIdx.x == 0) *status = s_fail;
+}
+
 __global__ void scale_factor_kernel(int d, const double *L, const double *sigma, double c, double sdt,
                                     double r, double dt, int scheme, float *Lp, float *drift)
 {
@@ -70,7 +107,8 @@ __global__ void scale_factor_kernel(int d, const double *L, const double *sigma,
 
 cudaError_t launch_cholesky(int d, const double *A, double *L, int *status, cudaStream_t s)
 {
-    cholesky_kernel<<<1, kCholBlock, 0, s>>>(d, A, L, status);
+    if (d <= kCholSmallD) cholesky_small_kernel<<<1, kCholSmallBlock, 0, s>>>(d, A, L, status);
+    else cholesky_kernel<<<1, kCholBlock, 0, s>>>(d, A, L, status);
     return cudaGetLastError();
 }
 

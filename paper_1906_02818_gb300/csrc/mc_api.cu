@@ -6,8 +6,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "mc_kernels.cuh"
@@ -165,18 +167,129 @@ void size_grid(int64_t paths, int block, int resident, int *grid, int *ppt)
     *ppt = static_cast<int>(p);
 }
 
+// Device allocations of the set-up paths come from a cache of freed blocks
+// (per device; sizes rounded up to 256 bytes; a request takes the smallest
+// free block of at least its size and at most twice it), so that repeated
+// calls of the same shape pay neither cudaMalloc nor cudaFree (which also
+// synchronises the device).  A block goes back to the cache only when no
+// launch can still use it (its owner has synchronised); mc_release_cache()
+// hands the cached blocks back to CUDA.
+struct CachedBlock {
+    void *p;
+    size_t size;
+    int dev;
+};
+std::mutex g_cache_mu;
+std::vector<CachedBlock> g_free_blocks;
+std::unordered_map<void *, CachedBlock> g_live_blocks;
+
+void release_cached(int dev)  // dev < 0: every device; caller holds g_cache_mu
+{
+    std::vector<CachedBlock> keep;
+    for (const CachedBlock &b : g_free_blocks) {
+        if (dev < 0 || b.dev == dev) {
+            int cur = -1;
+            cudaGetDevice(&cur);
+            if (cur != b.dev) cudaSetDevice(b.dev);
+            cudaFree(b.p);
+            if (cur != b.dev) cudaSetDevice(cur);
+        } else {
+            keep.push_back(b);
+        }
+    }
+    g_free_blocks.swap(keep);
+}
+
+cudaError_t dev_alloc_raw(void **p, size_t n)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t sz = n <= 256 ? 256 : (n + 255) & ~static_cast<size_t>(255);
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    size_t best = static_cast<size_t>(-1), bi = 0;
+    for (size_t i = 0; i < g_free_blocks.size(); ++i) {
+        const CachedBlock &b = g_free_blocks[i];
+        if (b.dev == dev && b.size >= sz && b.size <= 2 * sz && b.size < best) {
+            best = b.size;
+            bi = i;
+        }
+    }
+    if (best != static_cast<size_t>(-1)) {
+        const CachedBlock b = g_free_blocks[bi];
+        g_free_blocks[bi] = g_free_blocks.back();
+        g_free_blocks.pop_back();
+        g_live_blocks[b.p] = b;
+        *p = b.p;
+        return cudaSuccess;
+    }
+    e = cudaMalloc(p, sz);
+    if (e == cudaErrorMemoryAllocation && !g_free_blocks.empty()) {
+        cudaGetLastError();
+        release_cached(dev);
+        e = cudaMalloc(p, sz);
+    }
+    if (e != cudaSuccess) return e;
+    g_live_blocks[*p] = CachedBlock{*p, sz, dev};
+    return cudaSuccess;
+}
+
+void dev_free_raw(void *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_live_blocks.find(p);
+    if (it == g_live_blocks.end()) {
+        cudaFree(p);
+        return;
+    }
+    g_free_blocks.push_back(it->second);
+    g_live_blocks.erase(it);
+}
+
+template <class T>
+cudaError_t dev_alloc(T **p, size_t n)
+{
+    return dev_alloc_raw(reinterpret_cast<void **>(p), n);
+}
+
 template <class T>
 void dfree(T *&p)
 {
-    if (p) cudaFree(p);
+    dev_free_raw(p);
     p = nullptr;
+}
+
+// Waits for every launch of `dev` (the owner of buffers about to return to
+// the cache may not have synchronised).
+void sync_device(int dev)
+{
+    if (dev < 0) {
+        cudaDeviceSynchronize();
+        return;
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    if (cur != dev) cudaSetDevice(cur);
 }
 
 // One device allocation carved into 256-byte aligned pieces, freed on scope exit.
 struct DeviceArena {
     unsigned char *base = nullptr;
     size_t used = 0;
-    ~DeviceArena() { if (base) cudaFree(base); }
+    bool idle = false;  // set once the owner's stream has been synchronised
+    ~DeviceArena()
+    {
+        if (!base) return;
+        if (!idle) {
+            int dev = -1;
+            cudaGetDevice(&dev);
+            sync_device(dev);
+        }
+        dev_free_raw(base);
+    }
     static size_t up(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
     template <class T>
     T *take(size_t count)
@@ -237,8 +350,11 @@ struct mc_plan {
     float *ckpt = nullptr;
     double *dsums = nullptr;
 
+    bool idle = false;  // set once every launch that uses the buffers has completed
+
     ~mc_plan()
     {
+        if (!idle) sync_device(device);
         dfree(partials); dfree(ticket); dfree(dout); dfree(dcorr); dfree(dL); dfree(dsig);
         dfree(dLp); dfree(ddrift); dfree(dstatus); dfree(bimg); dfree(err); dfree(ckpt); dfree(dcol);
         dfree(dsums);
@@ -264,14 +380,14 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
     P->prec = c->precision;
     const double dt = c->T / c->steps, sdt = std::sqrt(dt);
     const size_t dd = static_cast<size_t>(d) * d;
-    MC_CUDA(cudaMalloc(&P->dcorr, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P->dL, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P->dsig, d * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P->dstatus, sizeof(int)));
-    MC_CUDA(cudaMalloc(&P->err, sizeof(unsigned int)));
+    MC_CUDA(dev_alloc(&P->dcorr, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P->dL, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P->dsig, d * sizeof(double)));
+    MC_CUDA(dev_alloc(&P->dstatus, sizeof(int)));
+    MC_CUDA(dev_alloc(&P->err, sizeof(unsigned int)));
     MC_CUDA(cudaMemsetAsync(P->err, 0, sizeof(unsigned int), s));
     // per-column floats: cs, mdrift, vscale, drift, ws0, w, s0, sigma (8 x d)
-    MC_CUDA(cudaMalloc(&P->dcol, 8 * static_cast<size_t>(kBigMaxD) * sizeof(float)));
+    MC_CUDA(dev_alloc(&P->dcol, 8 * static_cast<size_t>(kBigMaxD) * sizeof(float)));
     float *col = P->dcol;
     std::vector<double> corr(dd, 0.0);
     if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
@@ -280,13 +396,13 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
     MC_CUDA(cudaMemcpyAsync(P->dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
     MC_CUDA(launch_cholesky(d, P->dcorr, P->dL, P->dstatus, s));
     if (tcp) {
-        MC_CUDA(cudaMalloc(&P->bimg, big_bimg_bytes(P->prec)));
+        MC_CUDA(dev_alloc(&P->bimg, big_bimg_bytes(P->prec)));
         MC_CUDA(cudaMemsetAsync(P->bimg, 0, big_bimg_bytes(P->prec), s));
         MC_CUDA(launch_big_prep(P->prec, d, P->dL, P->dsig, M_LOG2E, sdt, m->r, dt, c->steps, P->bimg, col,
                                 col + kBigMaxD, col + 2 * kBigMaxD, s));
     } else {
         const size_t D = static_cast<size_t>(wide_width(d));
-        MC_CUDA(cudaMalloc(&P->dLp, D * D * sizeof(float)));
+        MC_CUDA(dev_alloc(&P->dLp, D * D * sizeof(float)));
         MC_CUDA(launch_wide_prep(d, P->dL, P->dsig, sdt, m->r, dt, P->dLp, col + 3 * kBigMaxD, s));
     }
     std::vector<float> h(4 * static_cast<size_t>(kBigMaxD), 0.0f);
@@ -327,10 +443,10 @@ int big_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const PayoffSe
     if (P->grid <= 0) return fail(MC_ECUDA, "large-basket kernel cannot be resident");
     const int nvals = ps.n + (greeks ? 2 * d + 1 : 0);
     P->np = nvals;
-    MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * nvals * 2 * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+    MC_CUDA(dev_alloc(&P->partials, static_cast<size_t>(P->grid) * nvals * 2 * sizeof(float)));
+    MC_CUDA(dev_alloc(&P->ticket, sizeof(unsigned int)));
     MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
-    MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(nvals) * sizeof(mc_result)));
+    MC_CUDA(dev_alloc(&P->dout, static_cast<size_t>(nvals) * sizeof(mc_result)));
     b.partials = P->partials;
     b.ticket = P->ticket;
     b.out = P->dout;
@@ -364,7 +480,7 @@ int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const Payof
         w[a] = static_cast<float>(wa);
         s0[a] = static_cast<float>(m->s0[a]);
     }
-    MC_CUDA(cudaMalloc(&P->dcol, h.size() * sizeof(float)));
+    MC_CUDA(dev_alloc(&P->dcol, h.size() * sizeof(float)));
     MC_CUDA(cudaMemcpyAsync(P->dcol, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     P->kk = K_FACTOR;
     FactorArgs &f = P->fa;
@@ -389,10 +505,10 @@ int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const Payof
     P->grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(occ) * di.sms));
     P->block = 256;
     const int np = ps.n;
-    MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+    MC_CUDA(dev_alloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
+    MC_CUDA(dev_alloc(&P->ticket, sizeof(unsigned int)));
     MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
-    MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
+    MC_CUDA(dev_alloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
     f.red.partials = P->partials;
     f.red.ticket = P->ticket;
     f.red.out = P->dout;
@@ -485,12 +601,12 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
         P->D = D;
         const size_t dd = static_cast<size_t>(d) * d;
         const size_t tri = static_cast<size_t>(d) * (d + 1) / 2;
-        MC_CUDA(cudaMalloc(&P->dcorr, dd * sizeof(double)));
-        MC_CUDA(cudaMalloc(&P->dL, dd * sizeof(double)));
-        MC_CUDA(cudaMalloc(&P->dsig, d * sizeof(double)));
-        MC_CUDA(cudaMalloc(&P->dLp, (tcpath ? 64 : tri) * sizeof(float)));
-        MC_CUDA(cudaMalloc(&P->ddrift, (tcpath ? 64 : d) * sizeof(float)));
-        MC_CUDA(cudaMalloc(&P->dstatus, sizeof(int)));
+        MC_CUDA(dev_alloc(&P->dcorr, dd * sizeof(double)));
+        MC_CUDA(dev_alloc(&P->dL, dd * sizeof(double)));
+        MC_CUDA(dev_alloc(&P->dsig, d * sizeof(double)));
+        MC_CUDA(dev_alloc(&P->dLp, (tcpath ? 64 : tri) * sizeof(float)));
+        MC_CUDA(dev_alloc(&P->ddrift, (tcpath ? 64 : d) * sizeof(float)));
+        MC_CUDA(dev_alloc(&P->dstatus, sizeof(int)));
         std::vector<double> corr(dd, 0.0);
         if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
         else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
@@ -503,8 +619,8 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             // Quantised, swizzled factor tile + per-column scales (FP64 -> operand type).
             P->kk = K_BASKET_TC;
             P->prec = c->precision;
-            MC_CUDA(cudaMalloc(&P->bimg, tc_bimg_bytes(P->prec)));
-            MC_CUDA(cudaMalloc(&P->err, sizeof(unsigned int)));
+            MC_CUDA(dev_alloc(&P->bimg, tc_bimg_bytes(P->prec)));
+            MC_CUDA(dev_alloc(&P->err, sizeof(unsigned int)));
             MC_CUDA(cudaMemsetAsync(P->err, 0, sizeof(unsigned int), s));
             MC_CUDA(launch_tc_prep(P->prec, d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->bimg, P->dLp,
                                    P->ddrift, s));
@@ -587,10 +703,10 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
     P->bk.run.ppt = ppt;
     P->hs.run.ppt = ppt;
     if (np > 0) {
-        MC_CUDA(cudaMalloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
-        MC_CUDA(cudaMalloc(&P->ticket, sizeof(unsigned int)));
+        MC_CUDA(dev_alloc(&P->partials, static_cast<size_t>(P->grid) * np * 2 * sizeof(float)));
+        MC_CUDA(dev_alloc(&P->ticket, sizeof(unsigned int)));
         MC_CUDA(cudaMemsetAsync(P->ticket, 0, sizeof(unsigned int), s));
-        MC_CUDA(cudaMalloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
+        MC_CUDA(dev_alloc(&P->dout, static_cast<size_t>(np) * sizeof(mc_result)));
         for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red, &P->tc.red}) {
             r->partials = P->partials;
             r->ticket = P->ticket;
@@ -602,6 +718,7 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
 
 int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
 {
+    P->idle = false;
     for (ReduceArgs *r : {&P->g1.red, &P->bk.red, &P->hs.red, &P->tc.red}) r->out = dev_out ? dev_out : P->dout;
     switch (P->kk) {
     case K_GBM1D: MC_CUDA(launch_gbm1d(P->g1, P->grid, P->block, s)); break;
@@ -625,6 +742,13 @@ int plan_launch(mc_plan *P, mc_result *dev_out, cudaStream_t s)
 extern "C" {
 
 int mc_version(void) { return MC_VERSION; }
+
+int mc_release_cache(void)
+{
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    release_cached(-1);
+    return MC_OK;
+}
 
 const char *mc_last_error(void) { return g_err.c_str(); }
 
@@ -682,6 +806,7 @@ int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payo
         cudaError_t e = cudaMemcpyAsync(tmp.data(), P->dout, n_payoff * sizeof(mc_result), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = fail(MC_ECUDA, "mc_price: %s", cudaGetErrorString(e));
+        else P->idle = true;
     }
     if (!rc && P->err) {
         unsigned int e = 0;
@@ -733,6 +858,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
         std::vector<mc_result> tmp(1 + G);
         MC_CUDA(cudaMemcpyAsync(tmp.data(), P.dout, tmp.size() * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
         MC_CUDA(cudaStreamSynchronize(s));
+        P.idle = true;
         unsigned int e = 0;
         MC_CUDA(cudaMemcpy(&e, P.err, sizeof e, cudaMemcpyDeviceToHost));
         if (e) return fail(MC_ETIMEOUT, "a bounded wait on the tensor-core pipeline gave up");
@@ -790,13 +916,13 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
 
     mc_plan P;  // owns the scratch buffers (freed on return)
     P.np = nv;
-    MC_CUDA(cudaMalloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned int)));
+    MC_CUDA(dev_alloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.ticket, sizeof(unsigned int)));
     MC_CUDA(cudaMemsetAsync(P.ticket, 0, sizeof(unsigned int), s));
-    MC_CUDA(cudaMalloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
+    MC_CUDA(dev_alloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
     if (m->kind == MC_HESTON) {
         const size_t nseg = (c->steps + K - 1) / K;
-        MC_CUDA(cudaMalloc(&P.ckpt, nseg * 2 * static_cast<size_t>(grid) * block * sizeof(float)));
+        MC_CUDA(dev_alloc(&P.ckpt, nseg * 2 * static_cast<size_t>(grid) * block * sizeof(float)));
     }
     a.ckpt = P.ckpt;
     a.red.partials = P.partials;
@@ -809,6 +935,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     std::vector<mc_result> tmp(nv);
     MC_CUDA(cudaMemcpyAsync(tmp.data(), P.dout, nv * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
+    P.idle = true;
     for (int p = 0; p < np; ++p) {
         if (prices) prices[p] = tmp[static_cast<size_t>(p) * (G + 1)];
         for (int k = 0; k < G; ++k) greeks[static_cast<size_t>(p) * G + k] = tmp[static_cast<size_t>(p) * (G + 1) + 1 + k];
@@ -862,7 +989,7 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
                          2 * DeviceArena::up((B + 1) * dd * 8) + 2 * DeviceArena::up(dd * sizeof(mc_result)) +
                          DeviceArena::up(static_cast<size_t>(grid) * 2 * 4) + DeviceArena::up(4) +
                          DeviceArena::up(sizeof(mc_result)) + DeviceArena::up(sizeof(float) * (kCorrMaxD * (kCorrMaxD + 1) / 2 + kCorrMaxD));
-    MC_CUDA(cudaMalloc(&ar.base, bytes));
+    MC_CUDA(dev_alloc(&ar.base, bytes));
     double *dcorr = ar.take<double>(dd), *dL = ar.take<double>(dd), *dsig = ar.take<double>(d);
     double *dcfac = ar.take<double>(d);
     int *dstatus = ar.take<int>(1);
@@ -910,6 +1037,7 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
     MC_CUDA(cudaMemcpyAsync(hdl.data(), rdl, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaMemcpyAsync(hdr.data(), rdr, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
+    ar.idle = true;
     if (price) *price = pr;
     if (dl) std::memcpy(dl, hdl.data(), dd * sizeof(mc_result));
     if (drho) std::memcpy(drho, hdr.data(), dd * sizeof(mc_result));
@@ -946,12 +1074,12 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
     const size_t dd = static_cast<size_t>(d) * d, tri = static_cast<size_t>(d) * (d + 1) / 2;
     mc_plan P;  // owns the scratch buffers (freed on return)
-    MC_CUDA(cudaMalloc(&P.dcorr, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dL, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dsig, d * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dLp, (tri + 64 * 65 / 2 + 64) * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.ddrift, d * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.dstatus, sizeof(int)));
+    MC_CUDA(dev_alloc(&P.dcorr, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dL, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dsig, d * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dLp, (tri + 64 * 65 / 2 + 64) * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.ddrift, d * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.dstatus, sizeof(int)));
     std::vector<double> corr(dd, 0.0);
     if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
     else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
@@ -1004,10 +1132,10 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     int grid = 0, ppt = 1;
     size_grid(paths_ref, block, occ * di.sms, &grid, &ppt);
     a.run.ppt = ppt;
-    MC_CUDA(cudaMalloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.ticket, sizeof(unsigned int)));
+    MC_CUDA(dev_alloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.ticket, sizeof(unsigned int)));
     MC_CUDA(cudaMemsetAsync(P.ticket, 0, sizeof(unsigned int), s));
-    MC_CUDA(cudaMalloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
+    MC_CUDA(dev_alloc(&P.dout, static_cast<size_t>(nv) * sizeof(mc_result)));
     a.red.partials = P.partials;
     a.red.ticket = P.ticket;
     a.red.out = P.dout;
@@ -1018,6 +1146,7 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     std::vector<mc_result> lv(nv);
     MC_CUDA(cudaMemcpyAsync(lv.data(), P.dout, nv * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
+    P.idle = true;
     for (int p = 0; p < np; ++p) {
         mc_mlmc_result &o = out[p];
         o.coarse = coarse[p];
@@ -1058,12 +1187,12 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
     const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
     const size_t dd = static_cast<size_t>(d) * d, tri = static_cast<size_t>(d) * (d + 1) / 2;
     mc_plan P;  // owns the scratch buffers (freed on return)
-    MC_CUDA(cudaMalloc(&P.dcorr, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dL, dd * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dsig, d * sizeof(double)));
-    MC_CUDA(cudaMalloc(&P.dLp, tri * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.ddrift, d * sizeof(float)));
-    MC_CUDA(cudaMalloc(&P.dstatus, sizeof(int)));
+    MC_CUDA(dev_alloc(&P.dcorr, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dL, dd * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dsig, d * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dLp, tri * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.ddrift, d * sizeof(float)));
+    MC_CUDA(dev_alloc(&P.dstatus, sizeof(int)));
     std::vector<double> corr(dd, 0.0);
     if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
     else for (int a = 0; a < d; ++a) corr[static_cast<size_t>(a) * d + a] = 1.0;
@@ -1106,7 +1235,7 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
     a.k1 = static_cast<uint32_t>(c->seed >> 32);
     a.rk = round_keys(a.k0, a.k1);
     a.pay = ps;
-    MC_CUDA(cudaMalloc(&P.dsums, static_cast<size_t>(reps) * np * sizeof(double)));
+    MC_CUDA(dev_alloc(&P.dsums, static_cast<size_t>(reps) * np * sizeof(double)));
     MC_CUDA(cudaMemsetAsync(P.dsums, 0, static_cast<size_t>(reps) * np * sizeof(double), s));
     a.sums = P.dsums;
     const int occ = qmc_occupancy(a);
@@ -1118,6 +1247,7 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
     std::vector<double> sums(static_cast<size_t>(reps) * np);
     MC_CUDA(cudaMemcpyAsync(sums.data(), P.dsums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
+    P.idle = true;
     const double disc = std::exp(-m->r * c->T), N = static_cast<double>(c->paths);
     for (int p = 0; p < np; ++p) {
         double mean = 0.0, m2 = 0.0;
@@ -1153,6 +1283,7 @@ int mc_simulate(const mc_model *model, const mc_sim_cfg *cfg, int32_t save_every
     // no longer needs them (the factor travels in the launch parameters), but
     // cudaFree must not race the launch's argument capture: synchronise.
     MC_CUDA(cudaStreamSynchronize(s));
+    P.idle = true;
     return MC_OK;
 }
 

@@ -81,6 +81,7 @@ RISK_METHOD = {"nested": 0, "surrogate": 1}
 SIGNATURES = [
     ("mc_version", ctypes.c_int, []),
     ("mc_last_error", ctypes.c_char_p, []),
+    ("mc_release_cache", ctypes.c_int, []),
     ("mc_simulate", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_price", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg), ctypes.POINTER(McPayoff),

@@ -181,3 +181,7 @@ def test_correlation_sensitivity_checks(lib):
     assert lib.mc_corr_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), None, ctypes.byref(pr), dl, dr,
                               None) == native.MC_EINVAL
     assert lib.mc_corr_greeks(None, None, None, None, None, None, None) == native.MC_EINVAL
+
+
+def test_release_cache_without_work(lib):
+    assert lib.mc_release_cache() == 0

@@ -241,3 +241,23 @@ def test_bridge_monitoring_unsupported_cases(gb):
         with pytest.raises(native.MCError) as e:
             gb.price(model, cfg, pays)
         assert e.value.status == native.MC_EUNSUPPORTED
+
+
+def test_repeated_calls_reuse_cached_scratch(gb, orc):
+    """Calls of one shape reuse the cached device scratch (and calls after
+    mc_release_cache allocate afresh): identical results every time, equal
+    to the oracle's."""
+    from paper_1906_02818_gb300 import native
+    w = workloads.basket_d64(paths=3000, steps=12)
+    model = gbm_model(w)
+    outs = []
+    for i in range(4):
+        if i == 2:
+            assert native.lib().mc_release_cache() == 0
+        outs.append(gb.price(model, cfg_of(w, precision="bf16"), w["payoffs"]))
+        outs.append(gb.price(model, cfg_of(w), w["payoffs"]))
+    for i in range(2, len(outs)):
+        assert outs[i] == outs[i % 2]
+    ref = oracle_gbm(orc, w, w["paths"], w["payoffs"][:1])
+    m, _ = orc.mean_se(ref[0])
+    assert abs(outs[1][0][0] - m) <= REL * abs(m)
