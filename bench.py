@@ -33,10 +33,10 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Warp instructions the basket kernel issues per path-step (smsp__inst_executed.sum
 # divided by paths x steps) from the ncu capture of the same kernel build,
 # recorded in profiles/.  None where no capture of the current build exists.
-INST_PER_PATH_STEP = {"fp32": None, "bf16": 54.48, "fp16": None, "fp8": None}
+INST_PER_PATH_STEP = {"fp32": None, "bf16": 49.82, "fp16": None, "fp8": None}
 # DRAM bytes (read + write) of one launch of that kernel in the same capture:
 # only the factor tile and launch constants are read, whatever the path count.
-DRAM_BYTES_PER_LAUNCH = {"bf16": 72704}
+DRAM_BYTES_PER_LAUNCH = {"bf16": 67840}
 
 
 def peaks():

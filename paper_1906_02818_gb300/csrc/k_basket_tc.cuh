@@ -304,6 +304,10 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
     extern __shared__ uint8_t smem_raw[];
     __shared__ float s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
+    // per-asset terms of the step s being observed, double-buffered by the
+    // parity of s (written before the step's barrier, read after it):
+    // BF16 w_n S0_n 2^{s drift_n}; FP16 s drift_n
+    __shared__ __align__(16) float s_g[2][kN];
 
     const int t = threadIdx.x, warp = t >> 5;
     const uint32_t raw = tc::smem_u32(smem_raw);
@@ -337,21 +341,37 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
     const float inv_m = 1.0f / static_cast<float>(M);
     const int64_t ntiles = (a.run.paths + kRows - 1) / kRows;
     const uint32_t row_taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    // basket value of this thread's path after `steps` steps, from its accumulator row
-    auto basket = [&](float steps) {
+    // basket value of this thread's path after s steps, from its accumulator
+    // row: sum_n w_n S0_n 2^{s drift_n + cs_n D_n}; BF16 (cs_n = 1, folded into
+    // the operand) as sum_n g_n 2^{D_n} with g_n = w_n S0_n 2^{s drift_n} from
+    // s_g[s & 1]; FP16 with s drift_n from s_g[s & 1]
+    constexpr bool kFold = PREC == MC_BF16;
+    auto basket = [&](int buf) {
         float u = 0.0f;
+        const float4 *g4 = reinterpret_cast<const float4 *>(s_g[buf]);
 #pragma unroll
         for (int cc = 0; cc < kN / 16; ++cc) {
             float v[16];
             tc::tmem_ld16(row_taddr + cc * 16, v);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int l = 0; l < 16; ++l) {
-                const int j = cc * 16 + l;
-                u = fmaf(c.ws0[j], ex2_approx(fmaf(c.cs[j], v[l], steps * c.drift[j])), u);
+            for (int q = 0; q < 4; ++q) {
+                const float4 g = g4[cc * 4 + q];
+                const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                for (int l4 = 0; l4 < 4; ++l4) {
+                    const int l = 4 * q + l4, j = cc * 16 + l;
+                    u = kFold ? fmaf(gv[l4], ex2_approx(v[l]), u)
+                              : fmaf(c.ws0[j], ex2_approx(fmaf(c.cs[j], v[l], gv[l4])), u);
+                }
             }
         }
         return u;
+    };
+    auto set_g = [&](int steps) {
+        if (t < kN)
+            s_g[steps & 1][t] = kFold ? c.ws0[t] * ex2_approx(static_cast<float>(steps) * c.drift[t])
+                                      : static_cast<float>(steps) * c.drift[t];
     };
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -363,6 +383,8 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
         Stats st{0.0f, -INFINITY, INFINITY};
         bool ok = true;
         for (int i = 0; i < M; ++i) {
+            // s_g[(i + 1) & 1] was last read before the previous step's barrier
+            if (STATS || i + 1 == M) set_g(i + 1);
             if (!aborted) draw_row<PREC, EXACT>(zt, t, i, d, n, a.run.rk, rd, valid);
             tc::fence_proxy_async();
             tc::fence_before_sync();  // this thread's accumulator reads precede the next MMA
@@ -383,14 +405,14 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
             tc::fence_after_sync();
             // the Z buffer is free again (the MMA completed); the accumulator holds steps 0..i
             if (STATS && __all_sync(0xffffffffu, ok)) {
-                const float u = basket(static_cast<float>(i + 1));
+                const float u = basket((i + 1) & 1);
                 st.sum += u;
                 st.umax = fmaxf(st.umax, u);
                 st.umin = fminf(st.umin, u);
             }
         }
         if (__syncthreads_or(ok ? 0 : 1)) aborted = true;
-        const float uT = aborted ? 0.0f : basket(static_cast<float>(M));
+        const float uT = aborted ? 0.0f : basket(M & 1);
         const float avg = st.sum * inv_m;
         const bool use = valid && !aborted;
         for (int p = 0; p < a.pay.n; ++p) {
@@ -411,9 +433,10 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
 }
 
 // Factor tile for the MMA's B operand: row n = Lrho[n][0..63] (zero above
-// the diagonal and beyond d), scaled by s_n (E4M3: 448 / max_k |Lrho[n][k]|,
-// else 1), rounded to the operand type, at its swizzled position.  Also the
-// FP32 per-column scale cs_n = c sqrt(dt) sigma_n / s_n and the drift.
+// the diagonal and beyond d), scaled by s_n (E4M3: 448 / max_k |Lrho[n][k]|;
+// BF16: c sqrt(dt) sigma_n; FP16: 1), rounded to the operand type, at its
+// swizzled position.  Also the FP32 per-column scale
+// cs_n = c sqrt(dt) sigma_n / s_n and the drift.
 template <int PREC>
 __global__ void tc_prep_kernel(int d, const double *L, const double *sigma, double cfac, double sdt, double r,
                                double dt, int scheme, uint8_t *bimg, float *cs, float *drift)
@@ -426,7 +449,12 @@ __global__ void tc_prep_kernel(int d, const double *L, const double *sigma, doub
         const double v = (nrow < d && k <= nrow) ? L[static_cast<int64_t>(nrow) * d + k] : 0.0;
         amax = fmax(amax, fabs(v));
     }
-    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : 1.0;
+    // BF16: the row carries its column scale c sqrt(dt) sigma_n (bf16 keeps
+    // the full FP32 exponent range), so the accumulator holds log2-price
+    // increments and cs_n = 1.
+    const double colscale = nrow < d ? cfac * sdt * sigma[nrow] : 0.0;
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax
+                     : (PREC == MC_BF16 && colscale > 0.0) ? colscale : 1.0;
     for (int k = 0; k < kN; ++k) {
         const double v = (nrow < d && k <= nrow) ? L[static_cast<int64_t>(nrow) * d + k] * s : 0.0;
         const uint32_t off = Ly::chunk_off(nrow, k / Ly::kPerChunk) + (k % Ly::kPerChunk) * Ly::kElemBytes;

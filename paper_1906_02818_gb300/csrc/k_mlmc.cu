@@ -24,7 +24,8 @@ const void *select(int prec, const MlmcArgs &a)
 // Dequantised factor entries as the tensor-core factor tile holds them, in
 // units of the scaled row (Lq[n][k] = round(L[n][k] s_n)), and the column
 // scales cs_n = c sqrt(dt) sigma_n / s_n; s_n = 448 / max_k |L[n][k]| for
-// E4M3, else 1.  Packed lower triangle, rows of width 64.
+// E4M3, c sqrt(dt) sigma_n for BF16 (so cs_n = 1), 1 for FP16.  Packed lower
+// triangle, rows of width 64.
 template <int PREC>
 __global__ void mlmc_prep_kernel(int d, const double *L, const double *sigma, double cfac, double sdt, float *Lq,
                                  float *csq)
@@ -33,7 +34,9 @@ __global__ void mlmc_prep_kernel(int d, const double *L, const double *sigma, do
     if (nrow >= kD) return;
     double amax = 0.0;
     for (int k = 0; k <= nrow && k < d; ++k) amax = fmax(amax, fabs(nrow < d ? L[static_cast<int64_t>(nrow) * d + k] : 0.0));
-    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : 1.0;
+    const double colscale = nrow < d ? cfac * sdt * sigma[nrow] : 0.0;
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax
+                     : (PREC == MC_BF16 && colscale > 0.0) ? colscale : 1.0;
     for (int k = 0; k <= nrow; ++k) {
         const double v = (nrow < d && k < d) ? L[static_cast<int64_t>(nrow) * d + k] * s : 0.0;
         Lq[nrow * (nrow + 1) / 2 + k] = round_operand<PREC>(static_cast<float>(v));

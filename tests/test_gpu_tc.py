@@ -29,17 +29,26 @@ def gb():
     return gb
 
 
-def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_fixed=False):
+def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_fixed=False, fold=None):
     """Per-path monitored U of the quantised-operand scheme:
     dW_n = sqrt(dt) sigma_n sum_k Lq[n,k] zq[k] / (s_n s_z); E4M3 normals are
-    scaled per path and step by 448 / max|z| (fp8_fixed: by 448 / 6)."""
+    scaled per path and step by 448 / max|z| (fp8_fixed: by 448 / 6).  Row
+    scales s_n: E4M3 448 / max_k |L[n,k]|; BF16 on the d <= 64 path (fold)
+    the column scale c sqrt(dt) sigma_n, c = log2(e) (log-Euler) or 1
+    (Euler); otherwise 1."""
     d = len(w["s0"])
+    if fold is None:
+        fold = prec == "bf16" and d <= 64
     L = orc.cholesky(w["corr"]) if w.get("corr") is not None else np.eye(d)
+    dt = w["T"] / steps
     s_n = np.ones(d)
     if prec == "fp8":
         s_n = np.where(np.abs(L).max(axis=1) > 0, 448.0 / np.abs(L).max(axis=1), 1.0)
+    elif fold:
+        c = np.log2(np.e) if scheme == "log_euler" else 1.0
+        col = c * np.sqrt(dt) * np.asarray(w["sigma"], dtype=np.float64)
+        s_n = np.where(col > 0, col, 1.0)
     Lq = quantize((L * s_n[:, None]).astype(np.float32), prec) / s_n[:, None]
-    dt = w["T"] / steps
     Z = np.stack([orc.normals(w["seed"], path_offset + n, 0, steps * d) for n in range(paths)]).reshape(paths, steps, d)
     Z32 = Z.astype(np.float32)
     if prec == "fp8" and fp8_fixed:
