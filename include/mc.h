@@ -275,31 +275,6 @@ int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *
                  int32_t replications, mc_result *out, double *rep_means, void *stream);
 
 /*
- * Surrogate pricing network (mc_mlp)/*
- * Surrogate pricing network (mc_mlp)/*
- * mc_price_qmc -- randomised quasi-Monte Carlo (Sec. IV, Sobol QRNGs; the
- * basket experiment of Sec. VI.D): the GBM basket of `model` driven by a
- * Sobol sequence instead of Philox normals.  Dimension 1 is van der Corput;
- * dimension j >= 2 uses the (j-1)-th primitive polynomial over GF(2) (by
- * degree, then value) with initial direction integers m_1..m_s = 1 and the
- * Bratley-Fox recurrence.  Point n of dimension j is the XOR of the direction
- * words over the set bits of n; replication r XORs dimension j with word j of
- * Philox stream 6 * 2^56 + r under cfg->seed (a random digital shift).
- * Normal a of step i is the cosine branch of Box-Muller on dimensions
- * 2 (i d + a), 2 (i d + a) + 1, through the uniform map of the Philox path.
- *   cfg->paths = points per replication, cfg->path_offset = first point;
- *   points in [0, 2^23); d <= 32 and 2 d steps <= 64; FP32 contraction,
- *   discrete monitoring; 2 <= replications <= 65535.
- *   out: host [n_payoff]: price = mean of the replication means, se = their
- *   standard deviation / sqrt(replications).  rep_means: optional host
- *   [replications][n_payoff].
- * Synchronises `stream`.
- */
-int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
-                 int32_t replications, mc_result *out, double *rep_means, void *stream);
-
-/*
- * Surrogate pricing network (mc_mlp)/*
  * Surrogate pricing network (mc_mlp): n_in -> width x hidden (SiLU) -> 1
  * (linear), the network that revalues the risk portfolio.  Parameters are
  * one packed FP32 vector: for each layer l, W_l [in x out] row-major, then
@@ -314,7 +289,17 @@ int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *
  *   mc_mlp_train: `epochs` passes of mini-batch Adam (lr; beta 0.9, 0.999;
  *     eps 1e-8) over the n samples in whole batches; last_epoch_loss = mean
  *     batch loss of the final epoch; synchronises `stream`.
+ *   mc_mlp_set_train_mode: arithmetic of mc_mlp_loss_grad and mc_mlp_train.
+ *     MC_MLP_TRAIN_FP32 (default): FP32 SIMT products.  MC_MLP_TRAIN_TF32X3:
+ *     the width -> width layers' forward, input-gradient and weight-gradient
+ *     products on the tensor cores with operands split hi + lo and
+ *     accumulated as hi*hi + hi*lo + lo*hi in FP32 (FP32-like accuracy); needs
+ *     >= 2 hidden layers of a width that is a multiple of 64
+ *     (MC_EUNSUPPORTED otherwise).  A bounded wait that expires makes the
+ *     call return MC_ETIMEOUT.
  */
+#define MC_MLP_TRAIN_FP32 0
+#define MC_MLP_TRAIN_TF32X3 1
 typedef struct mc_mlp mc_mlp;
 int mc_mlp_create(int32_t n_in, int32_t width, int32_t hidden, const float *init, mc_mlp **net);
 int64_t mc_mlp_param_count(const mc_mlp *net);
@@ -329,6 +314,7 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
  * [mc_mlp_param_count] host floats, e.g. the average of the ranks' batch
  * gradients in data-parallel training.  Synchronises `stream`. */
 int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *stream);
+int mc_mlp_set_train_mode(mc_mlp *net, int32_t mode);
 int mc_mlp_destroy(mc_mlp *net);
 
 /*

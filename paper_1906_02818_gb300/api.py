@@ -242,6 +242,12 @@ class Mlp:
         p = np.ascontiguousarray(p, dtype=np.float32)
         check(self._lib.mc_mlp_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
 
+    def set_train_mode(self, mode: str):
+        """Arithmetic of loss_grad / train: "fp32" (FP32 SIMT products) or
+        "tf32x3" (width -> width products on the tensor cores, three-pass TF32)."""
+        code = {"fp32": native.MC_MLP_TRAIN_FP32, "tf32x3": native.MC_MLP_TRAIN_TF32X3}[mode]
+        check(self._lib.mc_mlp_set_train_mode(self._h, code))
+
     def forward(self, x, precision="fp32", stream=None):
         import torch
         x = x.contiguous()

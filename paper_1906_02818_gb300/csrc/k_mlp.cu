@@ -24,12 +24,6 @@ namespace {
 constexpr int kT = 64, kK = 16;
 constexpr int kMaxSlices = 16;  // K slices of a weight-gradient product
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
-__device__ __forceinline__ float silu_grad_f(float z)
-{
-    const float s = 1.0f / (1.0f + expf(-z));
-    return s * (1.0f + z * (1.0f - s));
-}
 
 // C[M x N] = op(A)[M x K] * op(B)[K x N]; TA: A stored K x M; TB: B stored N x K.
 // Epilogue: v = acc + bias[n]; Z = v (if Z); H = silu(v) or v (if H).
@@ -131,6 +125,119 @@ __global__ void colsum_kernel(int M, int N, const float *dZ, float *db)
         float t = 0.0f;
         for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += ws[w];
         db[n] = t;
+    }
+}
+
+// dst[c][r] = src[r][c] for a rows x cols block (32 x 32 shared tiles).
+__global__ void transpose_kernel(int64_t rows, int cols, const float *src, int64_t lds, float *dst, int64_t ldd)
+{
+    __shared__ float tile[32][33];
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = src[r * lds + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[static_cast<int64_t>(c) * ldd + r] = tile[threadIdx.x][i];
+    }
+}
+
+// out[r] = sum_c src[r][c] (one block per row, FP32 in a fixed order).
+__global__ void rowsum_kernel(int cols, const float *src, int64_t ld, float *out)
+{
+    const float *row = src + static_cast<int64_t>(blockIdx.x) * ld;
+    float s = 0.0f;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += row[c];
+    s = warp_sum(s);
+    __shared__ float ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += ws[w];
+        out[blockIdx.x] = t;
+    }
+}
+
+// Skinny products over the batch: for row f of Mt [F x ld] (one block each)
+// out[j ldo_j + f] = sum_r Mt[f][r] V[r][j] for j < J (V [n x J], row-major),
+// and rsum[f] = sum_r Mt[f][r] if rsum is set.  FP32, fixed order.
+constexpr int kRowDotMaxJ = 16;
+__global__ void rowdot_kernel(int64_t n, const float *Mt, int64_t ld, const float *V, int J, float *out,
+                              int64_t ldo_j, float *rsum)
+{
+    const int f = blockIdx.x;
+    const float *row = Mt + static_cast<int64_t>(f) * ld;
+    float acc[kRowDotMaxJ + 1];
+#pragma unroll
+    for (int j = 0; j <= kRowDotMaxJ; ++j) acc[j] = 0.0f;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const float m = row[r];
+#pragma unroll
+        for (int j = 0; j < kRowDotMaxJ; ++j)
+            if (j < J) acc[j] = fmaf(m, V[r * J + j], acc[j]);
+        acc[kRowDotMaxJ] += m;
+    }
+    __shared__ float ws[kRowDotMaxJ + 1][32];
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j <= kRowDotMaxJ; ++j) {
+        if (j >= J && j < kRowDotMaxJ) continue;
+        const float v = warp_sum(acc[j]);
+        if (lane == 0) ws[j][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < J || (rsum && threadIdx.x == kRowDotMaxJ)) {
+        const int j = threadIdx.x;
+        float t = 0.0f;
+        for (int q = 0; q < nw; ++q) t += ws[j][q];
+        if (j < J) out[j * ldo_j + f] = t;
+        else rsum[f] = t;
+    }
+}
+
+// dZ[r][c] = dy[r] w[c] silu'(Z[r][c]) (the output layer's input gradient
+// through the last activation) in both layouts: dZ [n x C] and dZt [C x ldt]
+// (32 x 32 shared tiles).
+__global__ void outer_silu_bwd_kernel(int64_t n, int C, const float *dy, const float *w, const float *Z, float *dZ,
+                                      float *dZt, int64_t ldt)
+{
+    __shared__ float tile[32][33];
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        if (r < n && c < C) {
+            const int64_t o = r * C + c;
+            const float v = dy[r] * w[c] * silu_grad_f(Z[o]);
+            dZ[o] = v;
+            tile[i][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < n && c < C) dZt[static_cast<int64_t>(c) * ldt + r] = tile[threadIdx.x][i];
+    }
+}
+
+// out[n][m] = sum_z part[z][m][n] (split-K partials of W^T summed into W).
+__global__ void sum_slices_t_kernel(int M, int N, int slices, const float *part, float *out)
+{
+    const int64_t count = static_cast<int64_t>(M) * N;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(i / N), n = static_cast<int>(i % N);
+        float s = 0.0f;
+        for (int z = 0; z < slices; ++z) s += part[static_cast<int64_t>(z) * count + i];
+        out[static_cast<int64_t>(n) * M + m] = s;
     }
 }
 
@@ -294,6 +401,156 @@ cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *
         }
     }
     return cudaSuccess;
+}
+
+// Tensor-core training (k_mlp_tf32.cu) covers the width -> width layers:
+// sizes n_in, W x hidden, 1 with hidden >= 2 and W a multiple of 64.
+bool mlp_tc_supported(const MlpLayout &L)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1;
+    if (nl < 3 || L.sizes[nl] != 1) return false;
+    const int W = L.sizes[1];
+    if (W % 64 != 0) return false;
+    for (int l = 1; l < nl; ++l)
+        if (L.sizes[l] != W) return false;
+    return true;
+}
+
+namespace {
+constexpr int kTcMaxSlices = 32;
+int64_t round4(int64_t n) { return (n + 3) / 4 * 4; }
+}  // namespace
+
+size_t mlp_train_floats_tc(const MlpLayout &L, int64_t n)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1, W = L.sizes[1];
+    const size_t nt = static_cast<size_t>(round4(n));
+    size_t f = 0;
+    for (int l = 0; l < nl; ++l) f += 2 * static_cast<size_t>(n) * L.sizes[l + 1];  // Z, H
+    f += static_cast<size_t>(nl - 1) * W * nt;                                      // H^T of the hidden layers
+    f += 3 * static_cast<size_t>(n) * W + 2 * static_cast<size_t>(W) * nt;           // dH, dZ[2], dZt[2]
+    f += static_cast<size_t>(nl - 2) * W * W;                                        // W_l^T
+    const int in0 = L.sizes[0];
+    f += static_cast<size_t>(std::max(kTcMaxSlices, kMaxSlices)) * std::max(W, in0) * W;  // split-K partials
+    return f + 64;  // 16-byte alignment of the pieces
+}
+
+// As mlp_loss_grad, with the width -> width layers' forward, input-gradient
+// and weight-gradient products on the tensor cores (three-pass TF32, FP32
+// accumulation); the input layer, the scalar output layer, the loss and the
+// element-wise steps as in mlp_loss_grad.
+cudaError_t mlp_loss_grad_tc(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
+                             float *acts, float *grad, double *partial, int npartial, unsigned int *err, uint32_t cap,
+                             cudaStream_t s)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1, W = L.sizes[1], n_in = L.sizes[0];
+    const int64_t nt = round4(n);
+    float *p = acts;
+    auto take = [&](size_t count) {
+        float *q = p;
+        p += (count + 3) / 4 * 4;
+        return q;
+    };
+    std::vector<float *> Zp(nl), Hp(nl), Ht(nl - 1), WT(nl - 1, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        Zp[l] = take(static_cast<size_t>(n) * L.sizes[l + 1]);
+        Hp[l] = take(static_cast<size_t>(n) * L.sizes[l + 1]);
+    }
+    for (int l = 0; l < nl - 1; ++l) Ht[l] = take(static_cast<size_t>(W) * nt);
+    float *dH = take(static_cast<size_t>(n) * W);
+    float *dZ[2] = {take(static_cast<size_t>(n) * W), take(static_cast<size_t>(n) * W)};
+    float *dZt[2] = {take(static_cast<size_t>(W) * nt), take(static_cast<size_t>(W) * nt)};
+    for (int l = 1; l < nl - 1; ++l) WT[l] = take(static_cast<size_t>(W) * W);
+    float *ws = p;
+    cudaError_t e;
+    const dim3 tb(32, 8);
+    auto transpose = [&](int64_t rows, int cols, const float *src, int64_t lds, float *dst, int64_t ldd) {
+        const dim3 g(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((cols + 31) / 32));
+        transpose_kernel<<<g, tb, 0, s>>>(rows, cols, src, lds, dst, ldd);
+        return cudaGetLastError();
+    };
+    TfGemmArgs base{};
+    base.err = err;
+    base.cap = cap;
+    // W_l^T (out x in, K-major over in) of the width -> width layers
+    for (int l = 1; l < nl - 1; ++l)
+        if ((e = transpose(W, W, params + L.w_off[l], W, WT[l], W)) != cudaSuccess) return e;
+    // forward
+    e = gemm<false, false>(static_cast<int>(n), W, n_in, x, n_in, params + L.w_off[0], W, params + L.b_off[0], Zp[0],
+                           Hp[0], W, 1, s);
+    if (e != cudaSuccess) return e;
+    if ((e = transpose(n, W, Hp[0], W, Ht[0], nt)) != cudaSuccess) return e;
+    for (int l = 1; l < nl - 1; ++l) {
+        TfGemmArgs a = base;
+        a.A = Hp[l - 1]; a.lda = W;
+        a.B = WT[l]; a.ldb = W;
+        a.M = n; a.N = W; a.K = W; a.kchunk = W;
+        a.mode = kTfFwd;
+        a.bias = params + L.b_off[l];
+        a.Z = Zp[l]; a.H = Hp[l]; a.Ht = Ht[l];
+        a.ldc = W; a.ldt = nt;
+        if ((e = tf32_gemm(a, 1, s)) != cudaSuccess) return e;
+    }
+    const int lo = nl - 1;  // scalar output layer
+    e = gemm<false, false>(static_cast<int>(n), 1, W, Hp[lo - 1], W, params + L.w_off[lo], 1, params + L.b_off[lo],
+                           Zp[lo], Hp[lo], 1, 0, s);
+    if (e != cudaSuccess) return e;
+    float *dy = dZ[1];
+    mse_kernel<<<npartial, 256, 0, s>>>(n, Hp[lo], t, dy, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // output layer: dW = H^T dy (from H^T), db = sum dy, dZ = (dy w^T) silu'(Z) in both layouts
+    rowdot_kernel<<<W, 256, 0, s>>>(n, Ht[lo - 1], nt, dy, 1, grad + L.w_off[lo], 0, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    colsum_kernel<<<1, 256, 0, s>>>(static_cast<int>(n), 1, dy, grad + L.b_off[lo]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        const dim3 g(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((W + 31) / 32));
+        outer_silu_bwd_kernel<<<g, tb, 0, s>>>(n, W, dy, params + L.w_off[lo], Zp[lo - 1], dZ[0], dZt[0], nt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // width -> width layers, l = nl - 2 .. 1: dZ[cur] / dZt[cur] hold dZ_l
+    int cur = 0;
+    const int slices0 = static_cast<int>(std::min<int64_t>(kTcMaxSlices, std::max<int64_t>(1, (n + 255) / 256)));
+    const int kchunk = static_cast<int>(((n + slices0 - 1) / slices0 + 31) / 32 * 32);
+    const int slices = static_cast<int>((n + kchunk - 1) / kchunk);
+    for (int l = nl - 2; l >= 1; --l) {
+        // dW_l^T [out x in] = dZ_l^T H_{l-1}: split-K partials, summed into W's layout
+        TfGemmArgs a = base;
+        a.A = dZt[cur]; a.lda = nt;
+        a.B = Ht[l - 1]; a.ldb = nt;
+        a.M = W; a.N = W; a.K = static_cast<int>(n); a.kchunk = kchunk;
+        a.mode = kTfPart;
+        a.P = ws;
+        if ((e = tf32_gemm(a, slices, s)) != cudaSuccess) return e;
+        sum_slices_t_kernel<<<grid_for(static_cast<int64_t>(W) * W), 256, 0, s>>>(W, W, slices, ws, grad + L.w_off[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        rowsum_kernel<<<W, 256, 0, s>>>(static_cast<int>(n), dZt[cur], nt, grad + L.b_off[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // dZ_{l-1} = (dZ_l W_l^T) silu'(Z_{l-1}): B = W_l [in x out], K-major over out
+        TfGemmArgs b = base;
+        b.A = dZ[cur]; b.lda = W;
+        b.B = params + L.w_off[l]; b.ldb = W;
+        b.M = n; b.N = W; b.K = W; b.kchunk = W;
+        b.mode = kTfBwd;
+        b.Zin = Zp[l - 1];
+        b.dZ = dZ[cur ^ 1]; b.dZt = dZt[cur ^ 1];
+        b.ldc = W; b.ldt = nt;
+        if ((e = tf32_gemm(b, 1, s)) != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    // input layer: dW_0[i][f] = sum_r dZ_0^T[f][r] x[r][i], db_0 = row sums of dZ_0^T
+    if (n_in <= kRowDotMaxJ) {
+        rowdot_kernel<<<W, 256, 0, s>>>(n, dZt[cur], nt, x, n_in, grad + L.w_off[0], W, grad + L.b_off[0]);
+        return cudaGetLastError();
+    }
+    const int sl0 = static_cast<int>(std::min<int64_t>(kMaxSlices, std::max<int64_t>(1, n / 256)));
+    e = sl0 > 1 ? gemm_split_k<true, false>(n_in, W, static_cast<int>(n), x, n_in, dZ[cur], W, grad + L.w_off[0], sl0,
+                                             ws, s)
+                : gemm<true, false>(n_in, W, static_cast<int>(n), x, n_in, dZ[cur], W, nullptr, nullptr,
+                                    grad + L.w_off[0], W, 0, s);
+    if (e != cudaSuccess) return e;
+    rowsum_kernel<<<W, 256, 0, s>>>(static_cast<int>(n), dZt[cur], nt, grad + L.b_off[0]);
+    return cudaGetLastError();
 }
 
 size_t mlp_train_floats(const MlpLayout &L, int64_t n)

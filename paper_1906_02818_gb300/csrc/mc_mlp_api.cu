@@ -23,6 +23,7 @@ struct mc_mlp {
     uint8_t *img = nullptr;
     uint64_t version = 1, img_version = 0;
     unsigned int *err = nullptr;  // set by the bf16 kernel when a bounded wait expires
+    int train_mode = MC_MLP_TRAIN_FP32;  // arithmetic of mc_mlp_loss_grad / mc_mlp_train
     ~mc_mlp()
     {
         for (float *p : {params, grad, m, v, work})
@@ -58,6 +59,27 @@ int ensure_work(mc_mlp *N, size_t floats)
     return MC_OK;
 }
 
+// One batch's loss partials and gradient in the network's training arithmetic.
+int loss_grad_batch(mc_mlp *N, const float *x, const float *t, int64_t n, cudaStream_t s)
+{
+    if (N->train_mode == MC_MLP_TRAIN_TF32X3) {
+        if (!N->err) {
+            MLP_CUDA(cudaMalloc(&N->err, sizeof(unsigned int)));
+            MLP_CUDA(cudaMemsetAsync(N->err, 0, sizeof(unsigned int), s));
+        }
+        MLP_CUDA(mlp_loss_grad_tc(N->L, N->params, x, t, n, N->work, N->grad, N->partial, kPartials, N->err,
+                                  mbar_wait_cap(), s));
+    } else {
+        MLP_CUDA(mlp_loss_grad(N->L, N->params, x, t, n, N->work, N->grad, N->partial, kPartials, s));
+    }
+    return MC_OK;
+}
+
+size_t train_floats(const mc_mlp *N, int64_t n)
+{
+    return N->train_mode == MC_MLP_TRAIN_TF32X3 ? mlp_train_floats_tc(N->L, n) : mlp_train_floats(N->L, n);
+}
+
 int check_net(const mc_mlp *N)
 {
     if (!N) return set_last_error(MC_EINVAL, "network is NULL");
@@ -78,7 +100,7 @@ int mlp_forward_any(mc_mlp *net, const float *x, int64_t n, float *y, int precis
     return mc_mlp_forward(net, x, n, y, precision, s);
 }
 
-// Reads and clears the bf16 kernel's time-out word (synchronises `s`).
+// Reads and clears the tensor-core kernels' time-out word (synchronises `s`).
 int mlp_check_timeout(mc_mlp *net, cudaStream_t s)
 {
     if (!net->err) return MC_OK;
@@ -87,7 +109,8 @@ int mlp_check_timeout(mc_mlp *net, cudaStream_t s)
     MLP_CUDA(cudaStreamSynchronize(s));
     if (!e) return MC_OK;
     MLP_CUDA(cudaMemsetAsync(net->err, 0, sizeof(unsigned int), s));
-    return set_last_error(MC_ETIMEOUT, "a bounded wait of the bf16 network kernel expired (outputs are NaN)");
+    return set_last_error(MC_ETIMEOUT, "a bounded wait of a tensor-core network kernel expired (outputs are NaN "
+                                        "or undefined)");
 }
 }  // namespace gbmc
 
@@ -178,8 +201,8 @@ int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_
     if ((rc = check_net(net))) return rc;
     if (!dev_x || !dev_t || n < 1) return set_last_error(MC_EINVAL, "x, t must be set and n >= 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((rc = ensure_work(net, mlp_train_floats(net->L, n)))) return rc;
-    MLP_CUDA(mlp_loss_grad(net->L, net->params, dev_x, dev_t, n, net->work, net->grad, net->partial, kPartials, s));
+    if ((rc = ensure_work(net, train_floats(net, n)))) return rc;
+    if ((rc = loss_grad_batch(net, dev_x, dev_t, n, s))) return rc;
     std::vector<double> part(kPartials);
     MLP_CUDA(cudaMemcpyAsync(part.data(), net->partial, kPartials * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (host_grad)
@@ -188,7 +211,7 @@ int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_
     double tot = 0.0;
     for (double p : part) tot += p;
     if (loss) *loss = tot / static_cast<double>(n);
-    return MC_OK;
+    return mlp_check_timeout(net, s);
 }
 
 int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, int32_t epochs, int32_t batch,
@@ -200,7 +223,7 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
         return set_last_error(MC_EINVAL, "x, t set; n, epochs, batch >= 1; lr > 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t B = batch < n ? batch : n;
-    if ((rc = ensure_work(net, mlp_train_floats(net->L, B)))) return rc;
+    if ((rc = ensure_work(net, train_floats(net, B)))) return rc;
     const int n_in = net->L.sizes[0];
     ++net->version;
     std::vector<double> part(kPartials);
@@ -209,8 +232,7 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
         epoch_loss = 0.0;
         const bool last = ep == epochs - 1;
         for (int64_t b0 = 0; b0 + B <= n; b0 += B) {  // whole batches; the samples are i.i.d.
-            MLP_CUDA(mlp_loss_grad(net->L, net->params, dev_x + b0 * n_in, dev_t + b0, B, net->work, net->grad,
-                                   net->partial, kPartials, s));
+            if ((rc = loss_grad_batch(net, dev_x + b0 * n_in, dev_t + b0, B, s))) return rc;
             MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
             if (last) {
                 MLP_CUDA(cudaMemcpyAsync(part.data(), net->partial, kPartials * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -221,6 +243,19 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
     }
     MLP_CUDA(cudaStreamSynchronize(s));
     if (last_epoch_loss) *last_epoch_loss = epoch_loss / static_cast<double>((n / B) * B);
+    return mlp_check_timeout(net, s);
+}
+
+int mc_mlp_set_train_mode(mc_mlp *net, int32_t mode)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (mode != MC_MLP_TRAIN_FP32 && mode != MC_MLP_TRAIN_TF32X3)
+        return set_last_error(MC_EINVAL, "mode: MC_MLP_TRAIN_FP32 or MC_MLP_TRAIN_TF32X3");
+    if (mode == MC_MLP_TRAIN_TF32X3 && !mlp_tc_supported(net->L))
+        return set_last_error(MC_EUNSUPPORTED, "tensor-core training needs >= 2 hidden layers of a width that is a "
+                                               "multiple of 64");
+    net->train_mode = mode;
     return MC_OK;
 }
 

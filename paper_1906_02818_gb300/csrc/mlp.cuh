@@ -29,6 +29,14 @@ cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const floa
 cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
                           float *acts, float *grad, double *partial, int npartial, cudaStream_t s);
 size_t mlp_train_floats(const MlpLayout &L, int64_t n);
+// The same with the width -> width products on the tensor cores (three-pass
+// TF32) when mlp_tc_supported(L); acts holds mlp_train_floats_tc(L, n)
+// floats; *err is set to 1 if a bounded wait of the tensor-core kernel expires.
+bool mlp_tc_supported(const MlpLayout &L);
+size_t mlp_train_floats_tc(const MlpLayout &L, int64_t n);
+cudaError_t mlp_loss_grad_tc(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
+                             float *acts, float *grad, double *partial, int npartial, unsigned int *err, uint32_t cap,
+                             cudaStream_t s);
 // BF16 tensor-core inference (k_mlp_tc.cu): hidden widths equal, a multiple
 // of 32 and at most 256, n_in <= 10, scalar output.
 bool mlp_bf16_supported(const MlpLayout &L);
@@ -40,5 +48,41 @@ cudaError_t mlp_bf16_prepare(const MlpLayout &L, const float *params, uint8_t *i
 cudaError_t mlp_forward_bf16(const MlpLayout &L, const float *params, const uint8_t *img, const float *x, int64_t n,
                              float *y, unsigned int *err, uint32_t cap, cudaStream_t s);
 cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
+
+// SiLU and its derivative in FP32 (the training path's activation).
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_grad_f(float z)
+{
+    const float s = 1.0f / (1.0f + expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// Tensor-core training GEMM (k_mlp_tf32.cu): C[M x N] = A[M x K] B[N x K]^T,
+// A and B K-major FP32 (row strides lda, ldb, multiples of 4 floats; 16-byte
+// aligned bases; any K), three-pass TF32 products with FP32
+// accumulation; grid M/128 x N/64 x slices, slice z covering K columns
+// [z kchunk, (z + 1) kchunk) (kchunk a multiple of 32).  Epilogues:
+constexpr int kTfFwd = 0;   // Z = C + bias, H = silu(Z) ([M x ldc]), Ht = H^T ([N x ldt])
+constexpr int kTfBwd = 1;   // dZ = C * silu'(Zin) ([M x ldc]), dZt = dZ^T ([N x ldt])
+constexpr int kTfPart = 2;  // P[z][M][N] = C of slice z
+struct TfGemmArgs {
+    const float *A;
+    int64_t lda;
+    const float *B;
+    int64_t ldb;
+    int64_t M;
+    int N, K, kchunk;
+    int mode;
+    const float *bias;
+    float *Z, *H, *Ht;
+    const float *Zin;
+    float *dZ, *dZt;
+    float *P;
+    int64_t ldc, ldt;
+    unsigned int *err;   // set to 1 when a bounded wait expires
+    uint32_t cap;        // polls per wait
+};
+size_t tf32_gemm_smem();
+cudaError_t tf32_gemm(const TfGemmArgs &a, int slices, cudaStream_t s);
 
 }  // namespace gbmc

@@ -16,6 +16,7 @@ c_double_p = ctypes.POINTER(ctypes.c_double)
 
 # enums of mc.h
 MC_OK, MC_EINVAL, MC_ENOTPSD, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MC_MLP_TRAIN_FP32, MC_MLP_TRAIN_TF32X3 = 0, 1
 STATUS_NAMES = {0: "MC_OK", -1: "MC_EINVAL", -2: "MC_ENOTPSD", -3: "MC_ENOMEM", -4: "MC_ECUDA",
                 -5: "MC_ETIMEOUT", -6: "MC_EUNSUPPORTED"}
 MODEL = {"gbm": 0, "heston": 1}
@@ -117,6 +118,7 @@ SIGNATURES = [
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("mc_mlp_apply_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p]),
+    ("mc_mlp_set_train_mode", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("mc_mlp_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("mc_risk", ctypes.c_int, [ctypes.POINTER(McPortfolio), ctypes.POINTER(McRiskCfg),
                                ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),

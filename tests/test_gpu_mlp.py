@@ -189,3 +189,69 @@ def test_apply_grad_is_one_training_step(gb):
     assert np.max(np.abs(a.params() - b.params())) <= 1e-7
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n", [130, 777, 4096])
+def test_tf32x3_loss_and_gradient_match_oracle(gb, n):
+    """Tensor-core training products (three-pass TF32, FP32 accumulation)
+    against the FP64 oracle at the FP32 path's tolerances, and against the
+    FP32 SIMT path; n = 130 (two row tiles, ragged), 777 (ragged K of the
+    weight-gradient products), 4096 (the training batch, split K)."""
+    import torch
+    init = workloads.mlp_init(seed=7)
+    net = gb.Mlp(5, 256, 4, init)
+    x, t = _data(n, seed=2)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    l32, g32 = net.loss_grad(xd, td)
+    net.set_train_mode("tf32x3")
+    loss, g = net.loss_grad(xd, td)
+    P = omlp.unpack(init.astype(np.float64), SIZES)
+    l_ref, G = omlp.loss_and_grads(P, x.astype(np.float64), t.astype(np.float64))
+    g_ref = omlp.pack(G)
+    assert abs(loss - l_ref) <= 1e-5 * l_ref
+    scale = np.max(np.abs(g_ref))
+    err = np.max(np.abs(g - g_ref)) / scale
+    print(f"n={n}: tf32x3 gradient max err {err:.2e} of max|g| (fp32 SIMT {np.max(np.abs(g32 - g_ref)) / scale:.2e})")
+    assert err <= 1e-4
+    # every layer's weights and biases, against its own scale
+    off = 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        for cnt in (a * b, b):
+            seg = slice(off, off + cnt)
+            ls = np.max(np.abs(g_ref[seg]))
+            assert np.max(np.abs(g[seg] - g_ref[seg])) <= 2e-4 * ls + 1e-12, (a, b, cnt)
+            off += cnt
+    net.close()
+
+
+def test_tf32x3_training_tracks_fp32_training(gb):
+    """Three epochs of Adam from the same initialisation in both arithmetics:
+    both reduce the loss, and the final losses agree to 1 %."""
+    import torch
+    init = workloads.mlp_init(seed=5)
+    x, t = _data(1 << 14, seed=4)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    out = {}
+    for mode in ("fp32", "tf32x3"):
+        net = gb.Mlp(5, 256, 4, init)
+        net.set_train_mode(mode)
+        l0, _ = net.loss_grad(xd, td)
+        out[mode] = (l0, net.train(xd, td, epochs=3, batch=1024, lr=1e-3))
+        net.close()
+    print("training losses", out)
+    for l0, l1 in out.values():
+        assert l1 < 0.5 * l0
+    assert abs(out["tf32x3"][1] - out["fp32"][1]) <= 0.01 * out["fp32"][1]
+
+
+def test_train_mode_checks(gb):
+    """Tensor-core training needs a width that is a multiple of 64; unknown
+    modes are rejected."""
+    from paper_1906_02818_gb300 import native
+    sizes = omlp.layer_sizes(5, 100, 3)
+    count = sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:]))
+    net = gb.Mlp(5, 100, 3, np.zeros(count, dtype=np.float32))
+    with pytest.raises(native.MCError):
+        net.set_train_mode("tf32x3")
+    assert native.lib().mc_mlp_set_train_mode(net.handle, 7) == native.MC_EINVAL
+    net.close()
