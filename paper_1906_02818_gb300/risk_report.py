@@ -4,7 +4,7 @@ training of the network, VaR / CVaR of the 1024-option book by the
 surrogate, and the same by nested Monte Carlo (the judge), with timings.
 
   python -m paper_1906_02818_gb300.risk_report [--labels 1048576] [--label-paths 8192]
-         [--scen 65536] [--inner 4096] [--prec fp32|bf16] [--alpha 0.99]
+         [--scen 65536] [--inner 4096] [--prec fp32|bf16] [--train fp32|tf32x3] [--alpha 0.99]
 """
 from __future__ import annotations
 
@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--scen", type=int, default=1 << 16)
     ap.add_argument("--inner", type=int, default=1 << 12)
     ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--train", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--alpha", type=float, default=0.99)
     ap.add_argument("--skip-nested", action="store_true")
     a = ap.parse_args()
@@ -45,6 +46,7 @@ def main():
     pts = torch.from_numpy(workloads.surrogate_points(a.labels)).cuda()
     (lab, x), t_lab = wall(lambda: gb.surrogate_labels(pts, a.label_paths, with_inputs=True))
     net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+    net.set_train_mode(a.train)
     losses = []
 
     def train():
@@ -59,10 +61,11 @@ def main():
         "alpha": a.alpha, "scenarios": a.scen,
         "labels": {"points": a.labels, "paths_each": a.label_paths, "seconds": t_lab,
                    "path_steps_per_s": float(a.labels * a.label_paths * 252.5 / t_lab)},
-        "training": {"epochs": sum(e for _, e in workloads.SURROGATE_SCHEDULE), "seconds": t_train,
+        "training": {"epochs": sum(e for _, e in workloads.SURROGATE_SCHEDULE), "seconds": t_train, "arithmetic": a.train,
                      "final_epoch_mse": losses[-1]},
         "surrogate": {"var": sur["var"], "cvar": sur["cvar"], "seconds": t_sur, "precision": a.prec,
                       "revaluations_per_s": a.scen * 1024 / t_sur},
+        "surrogate_pipeline_seconds": t_lab + t_train + t_sur,
     }
     if not a.skip_nested:
         nested, t_nest = wall(lambda: gb.risk(pf, alpha=a.alpha, n_scen=a.scen, method="nested", inner_paths=a.inner,
