@@ -9,14 +9,16 @@
 // hi*hi + hi*lo + lo*hi; the dropped lo*lo term and the TF32 reading of lo
 // leave a relative error near 2^-21 per product, FP32-like.
 //
-// One CTA = 256 threads computes a 128 x 64 tile: every thread loads its
-// share of each 32-wide K chunk two chunks ahead into registers and stages it
-// (A: 128 rows, B: 64 rows, 128-byte rows, 128-byte swizzle) as hi and lo
-// planes in one of two stages; thread 0 issues the chunk's 12 MMAs (4 K-steps
-// of 8, 3 passes) and commits them to the stage's mbarrier, which the threads
-// wait on before refilling the stage.  The epilogue reads the accumulator
-// (TMEM lane = row), writes the transposed output from registers, stages the
-// tile in shared memory for coalesced row-major stores, and applies one of:
+// One CTA computes a 128 x 64 tile.  Eight loader warps load their share of
+// each 32-wide K chunk two chunks ahead into registers and stage it (A: 128
+// rows, B: 64 rows, 128-byte rows, 128-byte swizzle) as hi and lo planes in
+// one of two stages, then arrive on the stage's `full` mbarrier; one lane of
+// a ninth warp waits on it, issues the chunk's 12 MMAs (4 K-steps of 8, 3
+// passes) and commits them to the stage's `empty` mbarrier, on which the
+// loaders wait before refilling the stage.  The epilogue (loader warps)
+// reads the accumulator (TMEM lane = row), writes the transposed output from
+// registers, stages the tile in shared memory for coalesced row-major
+// stores, and applies one of:
 //   FWD: v = acc + b; Z = v; H = silu(v); Ht = H^T        (forward layer)
 //   BWD: dZ = acc * silu'(Zin); dZt = dZ^T                (dH = dZ_next W)
 //   PART: P[slice] = acc                                   (split-K, dW^T)
@@ -33,7 +35,7 @@ constexpr int kBM = 128, kBN = 64, kBK = 32, kThreads = 256;
 constexpr int kATile = kBM * kBK * 4;                  // 16 KB per plane
 constexpr int kBTile = kBN * kBK * 4;                  // 8 KB per plane
 constexpr int kStage = 2 * kATile + 2 * kBTile;        // hi + lo of A and B
-constexpr int kSmem = 1024 + 2 * kStage + 64;          // align pad, 2 stages, barriers
+constexpr int kSmem = 1024 + 2 * kStage + 64;          // align pad, 2 stages, barriers + TMEM slot
 
 // Byte offset of 16-byte chunk `ch` (0..7) of row `row` in a 128-byte-row,
 // 128-byte-swizzled K-major tile (8-row groups of 1024 bytes).
@@ -133,14 +135,15 @@ __device__ __forceinline__ void store_frag(const Frag &f, uint32_t a_hi, uint32_
     for (int i = 0; i < kBLoads; ++i) store4(f.b[i], b_hi, b_lo, threadIdx.x + i * kThreads);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tf32_gemm_kernel(const __grid_constant__ TfGemmArgs a)
+__global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __grid_constant__ TfGemmArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ volatile unsigned int s_fail;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t bars = base + 2 * kStage, tslot = bars + 16;
+    // barriers: full[2] (loaders staged the chunk), empty[2] (its MMAs completed), done
+    const uint32_t full = base + 2 * kStage, empty = full + 16, done = empty + 16, tslot = done + 8;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
     const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
     const int n0 = blockIdx.y * kBN;
@@ -150,8 +153,11 @@ __global__ void __launch_bounds__(kThreads, 1) tf32_gemm_kernel(const __grid_con
 
     if (t == 0) {
         s_fail = 0u;
-        tc::mbar_init(bars, 1);
-        tc::mbar_init(bars + 8, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(full + 8 * i, kThreads);
+            tc::mbar_init(empty + 8 * i, 1);
+        }
+        tc::mbar_init(done, 1);
     }
     if (warp == 0) {
         tc::tmem_alloc(tslot, kBN);
@@ -161,102 +167,120 @@ __global__ void __launch_bounds__(kThreads, 1) tf32_gemm_kernel(const __grid_con
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot_ptr;
-    const uint32_t idesc = idesc_tf32(kBM, kBN);
 
-    // chunk c: stage c & 1, registers loaded two chunks ahead
-    auto step = [&](int c, Frag &f) {
-        const int st = c & 1;
-        const uint32_t a_hi = base + st * kStage, a_lo = a_hi + kATile, b_hi = a_lo + kATile, b_lo = b_hi + kBTile;
-        // the stage is free once the MMAs of chunk c - 2 have read it
-        if (c >= 2) tc::wait_or_fail(&s_fail, bars + 8 * st, ((c - 2) >> 1) & 1u, a.cap);
-        tc::fence_after_sync();
-        if (!s_fail) store_frag(f, a_hi, a_lo, b_hi, b_lo);
-        if (c + 2 < nk) load_frag(f, a, m0, n0, ke, kb + (c + 2) * kBK);
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (t == 0 && !s_fail) {
-            tc::fence_after_sync();
+    if (warp == kThreads / 32) {
+        // ---------------- MMA issuer (one lane) ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(kBM, kBN);
+            for (int c = 0; c < nk; ++c) {
+                const int st = c & 1;
+                const uint32_t a_hi = base + st * kStage, a_lo = a_hi + kATile, b_hi = a_lo + kATile,
+                               b_lo = b_hi + kBTile;
+                if (tc::wait_or_fail(&s_fail, full + 8 * st, (c >> 1) & 1u, a.cap)) {
+                    tc::fence_after_sync();
 #pragma unroll
-            for (int k = 0; k < kBK / 8; ++k) {
-                const uint64_t ah = tc::smem_desc(a_hi + 32 * k, 1024, tc::SW_128B);
-                const uint64_t al = tc::smem_desc(a_lo + 32 * k, 1024, tc::SW_128B);
-                const uint64_t bh = tc::smem_desc(b_hi + 32 * k, 1024, tc::SW_128B);
-                const uint64_t bl = tc::smem_desc(b_lo + 32 * k, 1024, tc::SW_128B);
-                mma_tf32(tmem, ah, bh, idesc, (c > 0 || k > 0) ? 1u : 0u);
-                mma_tf32(tmem, ah, bl, idesc, 1u);
-                mma_tf32(tmem, al, bh, idesc, 1u);
+                    for (int k = 0; k < kBK / 8; ++k) {
+                        const uint64_t ah = tc::smem_desc(a_hi + 32 * k, 1024, tc::SW_128B);
+                        const uint64_t al = tc::smem_desc(a_lo + 32 * k, 1024, tc::SW_128B);
+                        const uint64_t bh = tc::smem_desc(b_hi + 32 * k, 1024, tc::SW_128B);
+                        const uint64_t bl = tc::smem_desc(b_lo + 32 * k, 1024, tc::SW_128B);
+                        mma_tf32(tmem, ah, bh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                        mma_tf32(tmem, ah, bl, idesc, 1u);
+                        mma_tf32(tmem, al, bh, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(empty + 8 * st);
             }
-            tc::mma_commit(bars + 8 * st);
+            tc::mma_commit(done);
         }
-    };
-    Frag f0, f1;
-    if (nk > 0) load_frag(f0, a, m0, n0, ke, kb);
-    if (nk > 1) load_frag(f1, a, m0, n0, ke, kb + kBK);
-    for (int c = 0; c < nk; c += 2) {
-        step(c, f0);
-        if (c + 1 < nk) step(c + 1, f1);
+    } else {
+        // ---------------- loaders: chunk c into stage c & 1, two chunks ahead ----------------
+        auto step = [&](int c, Frag &f) {
+            const int st = c & 1;
+            const uint32_t a_hi = base + st * kStage, a_lo = a_hi + kATile, b_hi = a_lo + kATile,
+                           b_lo = b_hi + kBTile;
+            // the stage is free once the MMAs of chunk c - 2 have read it
+            if (c >= 2) tc::wait_or_fail(&s_fail, empty + 8 * st, ((c - 2) >> 1) & 1u, a.cap);
+            tc::fence_after_sync();
+            if (!s_fail) store_frag(f, a_hi, a_lo, b_hi, b_lo);
+            if (c + 2 < nk) load_frag(f, a, m0, n0, ke, kb + (c + 2) * kBK);
+            tc::fence_proxy_async();
+            tc::mbar_arrive(full + 8 * st);
+        };
+        Frag f0, f1;
+        if (nk > 0) load_frag(f0, a, m0, n0, ke, kb);
+        if (nk > 1) load_frag(f1, a, m0, n0, ke, kb + kBK);
+        for (int c = 0; c < nk; c += 2) {
+            step(c, f0);
+            if (c + 1 < nk) step(c + 1, f1);
+        }
+        // every MMA has completed once `done` fires
+        tc::wait_or_fail(&s_fail, done, 0u, a.cap);
+        tc::fence_after_sync();
     }
-    // the last commit completes after every earlier MMA of this thread
-    if (nk > 0) tc::wait_or_fail(&s_fail, bars + 8 * ((nk - 1) & 1), ((nk - 1) >> 1) & 1u, a.cap);
+    __syncthreads();  // the operand stages are free for the staged output tile
     tc::fence_after_sync();
 
-    // epilogue, part 1: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows),
-    // columns 32 (w / 4) .. + 31; applies the element-wise step, writes the
-    // transposed output (lanes = consecutive rows: coalesced) and stages the
-    // tile in shared memory (the operand stages are no longer read).
+    // epilogue (warps 0..7; the issuer warp only passes the barriers).
+    // Part 1: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), columns
+    // 32 (w / 4) .. + 31; applies the element-wise step, writes the transposed
+    // output (lanes = consecutive rows: coalesced) and stages the tile in
+    // shared memory (the operand stages are no longer read).
+    const bool worker = warp < kThreads / 32;
     const bool live = __all_sync(0xffffffffu, s_fail == 0u) && nk > 0;  // warp-uniform: tcgen05.ld is collective
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, half = (warp >> 2) & 1;
     const int row = q * 32 + lane;
     const int64_t gr = m0 + row;
     float *sC = reinterpret_cast<float *>(smem_raw + (base - raw));
     const uint32_t taddr = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * 32;
+    if (worker) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float v[16];
-        if (live) {
-            tc::tmem_ld16(taddr + 16 * h, v);
-            tc::tmem_wait_ld();
-        } else {
+        for (int h = 0; h < 2; ++h) {
+            float v[16];
+            if (live) {
+                tc::tmem_ld16(taddr + 16 * h, v);
+                tc::tmem_wait_ld();
+            } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = 0.0f;
-        }
-        const int c0 = half * 32 + 16 * h;
-        const bool rok = live && gr < a.M;
-        if (a.mode == kTfFwd) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int n = n0 + c0 + e;
-                const float z = v[e] + (n < a.N ? a.bias[n] : 0.0f);
-                v[e] = z;
-                if (rok && n < a.N) a.Ht[static_cast<int64_t>(n) * a.ldt + gr] = silu_f(z);
+                for (int e = 0; e < 16; ++e) v[e] = 0.0f;
             }
-        } else if (a.mode == kTfBwd) {
+            const int c0 = half * 32 + 16 * h;
+            const bool rok = live && gr < a.M;
+            if (a.mode == kTfFwd) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int n = n0 + c0 + e;
-                const float dz = (rok && n < a.N) ? v[e] * silu_grad_f(a.Zin[gr * a.ldc + n]) : 0.0f;
-                v[e] = dz;
-                if (rok && n < a.N) a.dZt[static_cast<int64_t>(n) * a.ldt + gr] = dz;
+                for (int e = 0; e < 16; ++e) {
+                    const int n = n0 + c0 + e;
+                    const float z = v[e] + (n < a.N ? a.bias[n] : 0.0f);
+                    v[e] = z;
+                    if (rok && n < a.N) a.Ht[static_cast<int64_t>(n) * a.ldt + gr] = silu_f(z);
+                }
+            } else if (a.mode == kTfBwd) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int n = n0 + c0 + e;
+                    const float dz = (rok && n < a.N) ? v[e] * silu_grad_f(a.Zin[gr * a.ldc + n]) : 0.0f;
+                    v[e] = dz;
+                    if (rok && n < a.N) a.dZt[static_cast<int64_t>(n) * a.ldt + gr] = dz;
+                }
             }
-        }
 #pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4)
-            *reinterpret_cast<float4 *>(sC + row * kCStride + c0 + 4 * e4) =
-                make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+            for (int e4 = 0; e4 < 4; ++e4)
+                *reinterpret_cast<float4 *>(sC + row * kCStride + c0 + 4 * e4) =
+                    make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+        }
     }
     __syncthreads();
     // part 2: row-major outputs, 16 threads per 64-column row (coalesced)
-    for (int i = 0; i < kBM * kBN / 4 / kThreads; ++i) {
+    for (int i = 0; worker && i < kBM * kBN / 4 / kThreads; ++i) {
         const int idx = t + i * kThreads, r = idx >> 4, c4 = idx & 15;
         const int64_t g = m0 + r;
         const int n = n0 + 4 * c4;
         if (!live || g >= a.M || n >= a.N) continue;
         const float4 v = *reinterpret_cast<const float4 *>(sC + r * kCStride + 4 * c4);
         const float vv[4] = {v.x, v.y, v.z, v.w};
-        const bool full = n + 3 < a.N;
+        const bool whole = n + 3 < a.N;
         if (a.mode == kTfFwd) {
-            if (full) {
+            if (whole) {
                 *reinterpret_cast<float4 *>(a.Z + g * a.ldc + n) = v;
                 *reinterpret_cast<float4 *>(a.H + g * a.ldc + n) =
                     make_float4(silu_f(v.x), silu_f(v.y), silu_f(v.z), silu_f(v.w));
@@ -267,11 +291,11 @@ __global__ void __launch_bounds__(kThreads, 1) tf32_gemm_kernel(const __grid_con
                 }
             }
         } else if (a.mode == kTfBwd) {
-            if (full) *reinterpret_cast<float4 *>(a.dZ + g * a.ldc + n) = v;
+            if (whole) *reinterpret_cast<float4 *>(a.dZ + g * a.ldc + n) = v;
             else for (int j = 0; j < 4 && n + j < a.N; ++j) a.dZ[g * a.ldc + n + j] = vv[j];
         } else {
             float *P = a.P + (static_cast<int64_t>(blockIdx.z) * a.M + g) * a.N + n;
-            if (full) *reinterpret_cast<float4 *>(P) = v;
+            if (whole) *reinterpret_cast<float4 *>(P) = v;
             else for (int j = 0; j < 4 && n + j < a.N; ++j) P[j] = vv[j];
         }
     }
@@ -299,7 +323,7 @@ cudaError_t tf32_gemm(const TfGemmArgs &a, int slices, cudaStream_t s)
     }
     const dim3 grid(static_cast<unsigned>((a.M + mtf::kBM - 1) / mtf::kBM),
                     static_cast<unsigned>((a.N + mtf::kBN - 1) / mtf::kBN), static_cast<unsigned>(slices));
-    mtf::tf32_gemm_kernel<<<grid, mtf::kThreads, mtf::kSmem, s>>>(a);
+    mtf::tf32_gemm_kernel<<<grid, mtf::kThreads + 32, mtf::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

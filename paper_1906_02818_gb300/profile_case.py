@@ -8,7 +8,8 @@
   python -m paper_1906_02818_gb300.profile_case mlp --paths 1048576 --prec bf16   (paths = network rows)
   python -m paper_1906_02818_gb300.profile_case labels --paths 4096              (paths = label points)
   python -m paper_1906_02818_gb300.profile_case risk_nested --paths 256          (paths = scenarios)
-  python -m paper_1906_02818_gb300.profile_case train --paths 262144            (paths = samples, 1 epoch)
+  python -m paper_1906_02818_gb300.profile_case train --paths 262144            (paths = samples, 1 epoch;
+                                                                                 --prec tf32x3: tensor-core training)
   python -m paper_1906_02818_gb300.profile_case bridge --paths 1048576          (the In and Out Put, 25 steps)
   python -m paper_1906_02818_gb300.profile_case qmc --paths 262144              (points x 16 replications)
   python -m paper_1906_02818_gb300.profile_case mlmc --paths 16384              (correction paths, d = 64, bf16)
@@ -110,6 +111,7 @@ def _other(a, torch, workloads, gb):
         import time
         n = a.paths or (1 << 18)
         net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+        net.set_train_mode("tf32x3" if a.prec == "tf32x3" else "fp32")
         g = torch.Generator("cuda").manual_seed(2)
         x = torch.rand((n, 5), device="cuda", generator=g) * 2 - 1
         t = torch.rand(n, device="cuda", generator=g)
