@@ -33,6 +33,8 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Warp instructions the basket kernel issues per path-step (smsp__inst_executed.sum
 # divided by paths x steps) from the ncu capture of the same kernel build,
 # recorded in profiles/.  None where no capture of the current build exists.
+WORKLOAD = ("basket d=64 k=4 factors, 2^18 paths x 252 log-Euler steps, ATM basket call + up-and-out call at "
+            "1.3 B0, seed 42")
 INST_PER_PATH_STEP = {"fp32": None, "bf16": 49.82, "fp16": None, "fp8": None}
 # DRAM bytes (read + write) of one launch of that kernel in the same capture:
 # only the factor tile and launch constants are read, whatever the path count.
@@ -131,10 +133,8 @@ def run_reference(args):
     if rank != 0:
         return
     w = workloads.basket_d64()
-    times, n = [], 0
-    for _ in range(max(1, args.warmup)):
-        pass
-    n, _ = oracle_sample(w, target_s=8.0)
+    times = []
+    n, _ = oracle_sample(w, target_s=8.0)  # sizes the sample; its runs are the warm-up
     import oracle
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -143,12 +143,12 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     ps = n * w["steps"] / float(np.median(times))
     cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": ps, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": ps, "unit": UNIT, "n_gpus": world,
+            "device": f"host CPU, {cores} threads (the FP64 oracle uses no GPU)",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.median(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "basket d=64 k=4, 252 log-Euler steps, call + up-and-out call, seed 42",
-                       "paths_sampled": n},
+            "config": {"workload": WORKLOAD, "paths_sampled": n},
             "cpu_baseline": {"value": ps, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {n} of 2^18 paths, all 252 steps"},
             "e2e": {"value": ps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -263,8 +263,7 @@ def run_gbmc(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"{args.prec}+f32",
             "data": "synthetic",
-            "config": {"workload": "basket d=64 k=4 factors, 2^18 paths x 252 log-Euler steps, "
-                                   "ATM basket call + up-and-out call at 1.3 B0, seed 42",
+            "config": {"workload": WORKLOAD,
                        "paths_per_gpu": P, "time_steps": w["steps"], "d": d,
                        "contraction": args.prec, "l2": "flushed between timed iterations (512 MB write)",
                        "parallelism": f"path shards x{world}"},

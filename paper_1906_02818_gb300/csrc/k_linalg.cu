@@ -10,24 +10,45 @@ namespace {
 
 constexpr int kCholBlock = 1024;
 
-// Right-looking Cholesky, one CTA, in place on W (initialised with A).
+// 1/sqrt(p) for p > 0: an FP32 estimate refined by two Newton steps
+// r <- r (3/2 - p r^2 / 2) in FP64 (quadratic convergence: 2^-23 -> 2^-46 ->
+// a few ulp); outside FP32's range, FP64 square root and division.  FP64
+// division and square root are long serial chains on this part, and the
+// factorisation's column loop is serial in them.
+__device__ __forceinline__ double rsqrt_refined(double p)
+{
+    if (!(p > 1e-30 && p < 1e30)) return 1.0 / sqrt(p);
+    double r = static_cast<double>(rsqrtf(static_cast<float>(p)));
+    r = r * fma(-0.5 * p, r * r, 1.5);
+    r = r * fma(-0.5 * p, r * r, 1.5);
+    return r;
+}
+
+// Right-looking Cholesky, one CTA, in place on W (initialised with A); each
+// column is scaled by its pivot's reciprocal square root (rsqrt_refined).
 // status: 0 ok, 1 a pivot was not positive (A not positive definite).
 __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const double *A, double *W, int *status)
 {
     __shared__ int s_fail;
+    __shared__ double s_inv;
     for (int64_t idx = threadIdx.x; idx < static_cast<int64_t>(d) * d; idx += blockDim.x) W[idx] = A[idx];
     if (threadIdx.x == 0) s_fail = 0;
     __syncthreads();
     for (int k = 0; k < d; ++k) {
         if (threadIdx.x == 0) {
             const double p = W[static_cast<int64_t>(k) * d + k];
-            if (!(p > 0.0)) s_fail = 1;
-            else W[static_cast<int64_t>(k) * d + k] = sqrt(p);
+            if (!(p > 0.0)) {
+                s_fail = 1;
+            } else {
+                const double r = rsqrt_refined(p);
+                W[static_cast<int64_t>(k) * d + k] = p * r;
+                s_inv = r;
+            }
         }
         __syncthreads();
         if (s_fail) break;
-        const double lkk = W[static_cast<int64_t>(k) * d + k];
-        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[static_cast<int64_t>(i) * d + k] /= lkk;
+        const double inv = s_inv;
+        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[static_cast<int64_t>(i) * d + k] *= inv;
         __syncthreads();
         const int m = d - k - 1;
         for (int64_t idx = threadIdx.x; idx < static_cast<int64_t>(m) * m; idx += blockDim.x) {
@@ -49,13 +70,13 @@ __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const doubl
     if (threadIdx.x == 0) *status = s_fail;
 }
 
-// The same factorisation for d <= 64 with W in shared memory (the same FP64
-// operations in the same order as cholesky_kernel).
+// The same factorisation for d <= 64 with W in shared memory.
 constexpr int kCholSmallD = 64;
 constexpr int kCholSmallBlock = 256;
 __global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, const double *A, double *L, int *status)
 {
     __shared__ double W[kCholSmallD][kCholSmallD + 1];
+    __shared__ double s_inv;
     __shared__ int s_fail;
     for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) W[idx / d][idx % d] = A[idx];
     if (threadIdx.x == 0) s_fail = 0;
@@ -63,13 +84,18 @@ __global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, 
     for (int k = 0; k < d; ++k) {
         if (threadIdx.x == 0) {
             const double p = W[k][k];
-            if (!(p > 0.0)) s_fail = 1;
-            else W[k][k] = sqrt(p);
+            if (!(p > 0.0)) {
+                s_fail = 1;
+            } else {
+                const double r = rsqrt_refined(p);
+                W[k][k] = p * r;
+                s_inv = r;
+            }
         }
         __syncthreads();
         if (s_fail) break;
-        const double lkk = W[k][k];
-        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[i][k] /= lkk;
+        const double inv = s_inv;
+        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[i][k] *= inv;
         __syncthreads();
         const int m = d - k - 1;
         for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
