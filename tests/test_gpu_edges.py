@@ -1,0 +1,85 @@
+"""Edge cases of the pricing kernels against the oracle: the maximum number of
+payoffs in one launch (MC_MAX_PAYOFFS = 32), zero volatility (every path is
+the deterministic forward: closed form, zero standard error), and tensor-core
+launches smaller than one 128-path tile."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import REL, assert_price_close, cfg_of, gbm_model, oracle_gbm
+from test_gpu_price import barrier_band_mass
+from test_gpu_tc import emulate, payoffs_from_U
+
+pytestmark = pytest.mark.gpu
+
+MAX_PAYOFFS = 32
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1906_02818_gb300 as gb
+    return gb
+
+
+def _many_payoffs(s0):
+    kinds = ["call", "put", "asian_call", "asian_put", "uo_call", "ui_call", "uo_put", "ui_put",
+             "do_call", "di_call", "do_put", "di_put"]
+    pays = []
+    for i in range(MAX_PAYOFFS):
+        k = kinds[i % len(kinds)]
+        K = s0 * (0.8 + 0.4 * i / (MAX_PAYOFFS - 1))
+        p = dict(kind=k, strike=K)
+        if k.startswith("u"):
+            p["barrier"] = s0 * 1.35
+        elif k.startswith("d"):
+            p["barrier"] = s0 * 0.7
+        pays.append(p)
+    return pays
+
+
+def test_maximum_payoff_count_1d(gb, orc):
+    """32 payoffs of every kind on one 1-D launch, each against the oracle
+    (the barrier ones up to the paths whose extreme is within the FP32 band
+    of the barrier)."""
+    w = workloads.gbm_1d(paths=5000, steps=32)
+    pays = _many_payoffs(100.0)
+    got = gb.price(gbm_model(w), cfg_of(w), pays)
+    ref = oracle_gbm(orc, w, w["paths"], pays)
+    U = orc.gbm_paths(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], w["paths"])[:, 0]
+    assert_price_close(got, ref, pays, barrier_band_mass(orc, U, ref, pays), "32 payoffs")
+    with pytest.raises(Exception):
+        gb.price(gbm_model(w), cfg_of(w), pays + [dict(kind="call", strike=100.0)])
+
+
+def test_zero_volatility_is_the_forward(gb):
+    """sigma = 0: every path follows the forward S0 e^{r t}; the call is
+    e^{-rT} (sum w S0 e^{rT} - K)^+ with zero standard error, for the 1-D,
+    FP32 basket and BF16 tensor-core kernels."""
+    r, T, K = 0.05, 1.0, 95.0
+    want = math.exp(-r * T) * max(100.0 * math.exp(r * T) - K, 0.0)
+    pay = [dict(kind="call", strike=K), dict(kind="asian_call", strike=K)]
+    fwd_avg = 100.0 * np.mean(np.exp(r * T * np.arange(1, 17) / 16))
+    want_avg = math.exp(-r * T) * max(fwd_avg - K, 0.0)
+    for d, prec in [(1, "fp32"), (8, "fp32"), (64, "bf16")]:
+        model = dict(kind="gbm", s0=np.full(d, 100.0), sigma=np.zeros(d), r=r,
+                     corr=None if d == 1 else np.eye(d))
+        got = gb.price(model, dict(steps=16, T=T, paths=1000, precision=prec), pay)
+        assert abs(got[0][0] - want) <= 2e-5 * want, (d, prec, got[0][0], want)
+        assert abs(got[1][0] - want_avg) <= 2e-5 * want_avg, (d, prec, got[1][0], want_avg)
+        assert got[0][1] <= 1e-3 * want, (d, prec, got[0][1])  # FP32 moment sums: ~1e-4, vs ~0.45 at sigma 0.2
+
+
+@pytest.mark.parametrize("paths", [1, 5, 127])
+def test_tensor_core_launch_below_one_tile(gb, orc, paths):
+    """Fewer paths than one 128-row tile on the BF16 tensor-core path: the
+    rows past the path count are simulated as zeros and left out."""
+    w = workloads.basket_d64(paths=paths, steps=6)
+    pays = [dict(kind="call", strike=float(w["weights"] @ w["s0"]))]
+    got = gb.price(gbm_model(w), cfg_of(w, precision="bf16"), pays)
+    U = emulate(orc, w, "bf16", paths, w["steps"])
+    m = payoffs_from_U(U, pays, w["r"], w["T"])[0].mean()
+    assert abs(got[0][0] - m) <= REL * max(abs(m), 1e-6) + 1e-9, (paths, got[0][0], m)
