@@ -452,9 +452,9 @@ __global__ void tc_prep_kernel(int d, const double *L, const double *sigma, doub
     // BF16: the row carries its column scale c sqrt(dt) sigma_n (bf16 keeps
     // the full FP32 exponent range), so the accumulator holds log2-price
     // increments and cs_n = 1.
+    // (sigma_n = 0: a zero row)
     const double colscale = nrow < d ? cfac * sdt * sigma[nrow] : 0.0;
-    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax
-                     : (PREC == MC_BF16 && colscale > 0.0) ? colscale : 1.0;
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : (PREC == MC_BF16 ? colscale : 1.0);
     for (int k = 0; k < kN; ++k) {
         const double v = (nrow < d && k <= nrow) ? L[static_cast<int64_t>(nrow) * d + k] * s : 0.0;
         const uint32_t off = Ly::chunk_off(nrow, k / Ly::kPerChunk) + (k % Ly::kPerChunk) * Ly::kElemBytes;
@@ -471,7 +471,7 @@ __global__ void tc_prep_kernel(int d, const double *L, const double *sigma, doub
         }
     }
     if (nrow < d) {
-        cs[nrow] = static_cast<float>(cfac * sdt * sigma[nrow] / s);
+        cs[nrow] = PREC == MC_BF16 ? 1.0f : static_cast<float>(cfac * sdt * sigma[nrow] / s);
         drift[nrow] = static_cast<float>(scheme == MC_LOG_EULER ? cfac * (r - 0.5 * sigma[nrow] * sigma[nrow]) * dt
                                                                 : r * dt);
     } else {

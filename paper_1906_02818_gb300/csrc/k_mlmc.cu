@@ -34,14 +34,13 @@ __global__ void mlmc_prep_kernel(int d, const double *L, const double *sigma, do
     if (nrow >= kD) return;
     double amax = 0.0;
     for (int k = 0; k <= nrow && k < d; ++k) amax = fmax(amax, fabs(nrow < d ? L[static_cast<int64_t>(nrow) * d + k] : 0.0));
-    const double colscale = nrow < d ? cfac * sdt * sigma[nrow] : 0.0;
-    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax
-                     : (PREC == MC_BF16 && colscale > 0.0) ? colscale : 1.0;
+    const double colscale = nrow < d ? cfac * sdt * sigma[nrow] : 0.0;  // sigma_n = 0: a zero row
+    const double s = (PREC == MC_FP8E4M3 && amax > 0.0) ? 448.0 / amax : (PREC == MC_BF16 ? colscale : 1.0);
     for (int k = 0; k <= nrow; ++k) {
         const double v = (nrow < d && k < d) ? L[static_cast<int64_t>(nrow) * d + k] * s : 0.0;
         Lq[nrow * (nrow + 1) / 2 + k] = round_operand<PREC>(static_cast<float>(v));
     }
-    csq[nrow] = nrow < d ? static_cast<float>(cfac * sdt * sigma[nrow] / s) : 0.0f;
+    csq[nrow] = nrow < d ? (PREC == MC_BF16 ? 1.0f : static_cast<float>(cfac * sdt * sigma[nrow] / s)) : 0.0f;
 }
 
 }  // namespace

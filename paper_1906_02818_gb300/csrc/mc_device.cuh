@@ -234,26 +234,38 @@ __device__ inline void block_finish(float *s_acc, double *s_red, int np, const R
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // Sums of all blocks' partials in FP64, in a fixed order (deterministic):
+    // few payoffs: one warp per payoff, its lanes striding over the blocks;
+    // many payoffs: one thread per payoff, over the blocks in order (each
+    // block's row of partials is then read coalesced across the threads).
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int p = 0; p < np; ++p) {
-        double t[2];
-        for (int m = 0; m < 2; ++m) {
-            double v = 0.0;
-            for (int b = threadIdx.x; b < nb; b += blockDim.x)
-                v += static_cast<double>(ra.partials[static_cast<size_t>(b) * np * 2 + p * 2 + m]);
-            v = warp_sum_d(v);
-            if (lane == 0) s_red[warp] = v;
-            __syncthreads();
-            double tot = 0.0;
-            for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-            t[m] = tot;
-            __syncthreads();
+    (void)s_red;
+    const bool wide = np >= 32;
+    const int first = wide ? static_cast<int>(threadIdx.x) : warp;
+    const int stride = wide ? static_cast<int>(blockDim.x) : nwarps;
+    for (int p = first; p < np; p += stride) {
+        double t0 = 0.0, t1 = 0.0;
+        if (wide) {
+#pragma unroll 4
+            for (int b = 0; b < nb; ++b) {
+                const float2 q = *reinterpret_cast<const float2 *>(ra.partials + static_cast<size_t>(b) * np * 2 + p * 2);
+                t0 += static_cast<double>(q.x);
+                t1 += static_cast<double>(q.y);
+            }
+        } else {
+            for (int b = lane; b < nb; b += 32) {
+                const float *q = ra.partials + static_cast<size_t>(b) * np * 2 + p * 2;
+                t0 += static_cast<double>(q[0]);
+                t1 += static_cast<double>(q[1]);
+            }
+            t0 = warp_sum_d(t0);
+            t1 = warp_sum_d(t1);
         }
-        if (threadIdx.x == 0) {
+        if (wide || lane == 0) {
             const bool bad = ra.err && *reinterpret_cast<const volatile unsigned int *>(ra.err) != 0u;
             const double N = static_cast<double>(ra.paths);
-            const double mean = t[0] / N, m2 = t[1] / N;
+            const double mean = t0 / N, m2 = t1 / N;
             const double var = fmax(m2 - mean * mean, 0.0);
             mc_result res;
             res.price = bad ? __longlong_as_double(0x7ff8000000000000ll) : ra.disc * mean;
