@@ -314,13 +314,10 @@ size_t tf32_gemm_smem() { return mtf::kSmem; }
 
 cudaError_t tf32_gemm(const TfGemmArgs &a, int slices, cudaStream_t s)
 {
-    static int attr_set = 0;  // per process; the attribute is per function
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(mtf::tf32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(mtf::kSmem));
-        if (e != cudaSuccess) return e;
-        attr_set = 1;
-    }
+    // per device (the current one): set on every launch
+    const cudaError_t e = cudaFuncSetAttribute(mtf::tf32_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(mtf::kSmem));
+    if (e != cudaSuccess) return e;
     const dim3 grid(static_cast<unsigned>((a.M + mtf::kBM - 1) / mtf::kBM),
                     static_cast<unsigned>((a.N + mtf::kBN - 1) / mtf::kBN), static_cast<unsigned>(slices));
     mtf::tf32_gemm_kernel<<<grid, mtf::kThreads + 32, mtf::kSmem, s>>>(a);
