@@ -8,7 +8,7 @@
 //                    move of every underlying over the horizon h;
 //   nested_kernel    one (scenario, underlying) per CTA: inner Monte Carlo
 //                    revaluation of that underlying's options at the scenario
-//                    state (the judge of the surrogate, and its fallback);
+//                    state (the yardstick of the surrogate, and its fallback);
 //   features_kernel  network inputs of every (scenario, option) pair;
 //   pnl_kernel       one scenario per CTA: portfolio PnL from the revalued
 //                    options (FP64 sum over options);

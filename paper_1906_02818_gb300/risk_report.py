@@ -1,7 +1,7 @@
 """Portfolio-risk run of the surrogate pipeline on one GPU, as a JSON line:
 Monte Carlo training labels over the surrogate's parameter box, native
 training of the network, VaR / CVaR of the 1024-option book by the
-surrogate, and the same by nested Monte Carlo (the judge), with timings.
+surrogate, and the same by nested Monte Carlo (the yardstick), with timings.
 
   python -m paper_1906_02818_gb300.risk_report [--labels 1048576] [--label-paths 8192]
          [--scen 65536] [--inner 4096] [--prec fp32|bf16] [--train fp32|tf32x3] [--alpha 0.99]
