@@ -5,6 +5,7 @@ surrogate, and the same by nested Monte Carlo (the yardstick), with timings.
 
   python -m paper_1906_02818_gb300.risk_report [--labels 1048576] [--label-paths 8192]
          [--scen 65536] [--inner 4096] [--prec fp32|bf16] [--train fp32|tf32x3] [--alpha 0.99]
+         [--accuracy-sweep]
 """
 from __future__ import annotations
 
@@ -34,6 +35,8 @@ def main():
     ap.add_argument("--train", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--alpha", type=float, default=0.99)
     ap.add_argument("--skip-nested", action="store_true")
+    ap.add_argument("--accuracy-sweep", action="store_true",
+                    help="nested runs at 2^8 .. 2^14 inner paths; errors against the 2^14 run")
     a = ap.parse_args()
 
     def wall(fn):
@@ -79,6 +82,36 @@ def main():
             "pnl_rmse": float(np.sqrt(np.mean((sur["pnl"] - nested["pnl"]) ** 2))),
             "pnl_std_nested": float(np.std(nested["pnl"])),
             "speedup": t_nest / t_sur}
+    if a.accuracy_sweep:
+        # Plain nested Monte Carlo at several inner path counts on the same
+        # scenarios; the 2^14-path run is the reference for every error.
+        runs = {}
+        for inner in (1 << 8, 1 << 10, 1 << 12, 1 << 14):
+            r, t = wall(lambda: gb.risk(pf, alpha=a.alpha, n_scen=a.scen, method="nested", inner_paths=inner,
+                                        base_paths=1 << 16, want_pnl=True))
+            runs[inner] = (r, t)
+        ref = runs[1 << 14][0]
+
+        def errs(r):
+            return {"var_rel": abs(r["var"] - ref["var"]) / abs(ref["var"]),
+                    "cvar_rel": abs(r["cvar"] - ref["cvar"]) / abs(ref["cvar"]),
+                    "pnl_rmse": float(np.sqrt(np.mean((r["pnl"] - ref["pnl"]) ** 2)))}
+        # a nested run with N inner paths uses the first N of the reference's
+        # paths: its error against the reference is sqrt(1 - N / 2^14) of its
+        # error against the exact revaluation; pnl_rmse_exact undoes that
+        sweep = {}
+        for k, (r, t) in runs.items():
+            if k == 1 << 14:
+                continue
+            e = errs(r)
+            e["pnl_rmse_exact"] = e["pnl_rmse"] / np.sqrt(1.0 - k / float(1 << 14))
+            sweep[str(k)] = dict(seconds=t, **e)
+        se = errs(sur)  # includes the reference's own noise: conservative for the surrogate
+        match = [int(k) for k, v in sweep.items() if v["pnl_rmse_exact"] <= se["pnl_rmse"]]
+        out["accuracy_vs_nested_2^14"] = {
+            "reference_seconds": runs[1 << 14][1], "nested": sweep,
+            "surrogate": dict(seconds=t_sur, **se),
+            "cheapest_nested_at_surrogate_pnl_rmse": min(match) if match else None}
     print(json.dumps(out), flush=True)
     net.close()
 
