@@ -112,6 +112,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def oracle_one_core(paths=2048):
+    """The FP64 oracle on one host core (OMP_NUM_THREADS=1, a subprocess):
+    path-steps/s on the first `paths` paths of the d = 64 workload."""
+    code = ("import sys, time; sys.path.insert(0, %r); import workloads, oracle; oracle.build(); "
+            "w = workloads.basket_d64(); t0 = time.perf_counter(); "
+            "oracle.gbm_payoffs(w['s0'], w['sigma'], w['r'], w['T'], w['steps'], %d, w['payoffs'], corr=w['corr'], "
+            "weights=w['weights'], seed=w['seed']); print(time.perf_counter() - t0)") % (ROOT, paths)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return {"value": paths * 252 / dt, "unit": UNIT, "cores": 1, "sample": f"first {paths} of 2^18 paths, all 252 steps"}
+
+
 def oracle_sample(w, target_s=12.0, max_paths=1 << 16):
     """Time the FP64 oracle on a prefix of the workload's paths, doubling the
     prefix until one run takes at least ~1/4 of target_s (bounded)."""
@@ -258,6 +271,10 @@ def run_gbmc(args):
             n, dt = oracle_sample(w)
             cpu = {"value": n * w["steps"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"first {n} of 2^18 paths, all 252 steps, one run"}
+            try:
+                cpu["one_core"] = oracle_one_core()
+            except Exception as exc:  # reported, never fatal to the GPU line
+                cpu["one_core"] = {"unavailable": str(exc)[:200]}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
