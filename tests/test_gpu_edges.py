@@ -10,7 +10,7 @@ import pytest
 import workloads
 from gpu_util import REL, assert_price_close, cfg_of, gbm_model, oracle_gbm
 from test_gpu_price import barrier_band_mass
-from test_gpu_tc import emulate, payoffs_from_U
+from test_gpu_tc import emulate, flip_bound, payoffs_from_U
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +80,7 @@ def test_tensor_core_launch_below_one_tile(gb, orc, paths):
     w = workloads.basket_d64(paths=paths, steps=6)
     pays = [dict(kind="call", strike=float(w["weights"] @ w["s0"]))]
     got = gb.price(gbm_model(w), cfg_of(w, precision="bf16"), pays)
-    U = emulate(orc, w, "bf16", paths, w["steps"])
+    U, aux = emulate(orc, w, "bf16", paths, w["steps"], detail=True)
     m = payoffs_from_U(U, pays, w["r"], w["T"])[0].mean()
-    assert abs(got[0][0] - m) <= REL * max(abs(m), 1e-6) + 1e-9, (paths, got[0][0], m)
+    fb = flip_bound(aux, U, pays, w["r"], w["T"])[0]
+    assert abs(got[0][0] - m) <= REL * max(abs(m), 1e-6) + fb + 1e-9, (paths, got[0][0], m)

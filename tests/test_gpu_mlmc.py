@@ -8,7 +8,7 @@ import pytest
 
 import workloads
 from gpu_util import BAND, REL, cfg_of, gbm_model, oracle_gbm
-from test_gpu_tc import emulate, payoffs_from_U
+from test_gpu_tc import emulate, flip_bound, payoffs_from_U
 
 pytestmark = pytest.mark.gpu
 
@@ -40,14 +40,15 @@ def test_correction_level_matches_oracle(gb, orc, prec, d):
     w, pays = _case(d, N0, steps)
     res = gb.price_mlmc(gbm_model(w), cfg_of(w, precision=prec), pays, N1)
     exact = oracle_gbm(orc, w, N1, pays, path_offset=N0)                # FP32 level, FP64 arithmetic
-    U = emulate(orc, w, prec, N1, steps, path_offset=N0)               # reduced-precision level
+    U, aux = emulate(orc, w, prec, N1, steps, path_offset=N0, detail=True)   # reduced-precision level
     quant = payoffs_from_U(U, pays, w["r"], w["T"])
+    fb = flip_bound(aux, U, pays, w["r"], w["T"])
     for i, p in enumerate(pays):
         scale = max(abs(exact[i].mean()), 1e-3)
-        flip = 0.0
+        flip = fb[i]
         if p["kind"] == "uo_call":  # paths whose monitored max is within the FP32 band of H on either side
             near = np.abs(U[1:].max(axis=0) - p["barrier"]) <= 4 * BAND * p["barrier"]
-            flip = 2.02 * float(np.maximum(U[-1][near] - p["strike"], 0).sum()) / N1
+            flip += 2.02 * float(np.maximum(U[-1][near] - p["strike"], 0).sum()) / N1
         for key, want in [("ref_level", exact[i]), ("coarse_level", quant[i]), ("correction", exact[i] - quant[i])]:
             got = res[i][key][0]
             assert abs(got - want.mean()) <= 2 * REL * scale + flip, (prec, d, p["kind"], key, got, want.mean())

@@ -57,3 +57,31 @@ def test_heston_paths(gb, orc, paths):
     assert rel_err(got[:, 0], ref[:, 0]) <= BAND
     # the variance is O(0.04) and crosses zero: compare on an absolute scale
     assert np.max(np.abs(got[:, 1] - ref[:, 1])) <= BAND * 0.04 * 10
+
+
+def test_normals_within_error_model(gb, orc):
+    """The kernels' normals against the oracle's, read through the 1-D Euler
+    path with r = 0 and sigma sqrt(dt) = 1: each step is the single rounding
+    S_{i+1} = fl(S_i + S_i z_i), so (S_{i+1} - S_i) / S_i recovers the GPU's
+    z_i to within 2^-24 |S_{i+1} / S_i|.  2^18 paths x 8 steps cover all four
+    lanes of two Philox blocks per path; every normal lies within
+    normal_error_bound, the window that the reduced-precision emulation tests
+    grant each normal, plus that resolution."""
+    from test_gpu_tc import normal_error_bound
+    N, M = 1 << 18, 8
+    model = dict(kind="gbm", s0=[1.0], sigma=[1.0], r=0.0)
+    cfg = dict(steps=M, T=float(M), paths=N, scheme="euler", seed=42)
+    S = gb.simulate(model, cfg, save_every=1)[:, 0].double().cpu().numpy()          # [M + 1, N]
+    So = orc.gbm_paths([1.0], [1.0], 0.0, float(M), M, N, scheme="euler", seed=42)[:, 0]
+    zg = (S[1:] - S[:-1]) / S[:-1]
+    zo = So[1:] / So[:-1] - 1.0
+    res = 2.0 ** -24 * np.abs(S[1:] / S[:-1]) * 1.01
+    eps = normal_error_bound(zo.T).T
+    err = np.abs(zg - zo)
+    r = np.hypot(zo[0::2], zo[1::2]).repeat(2, axis=0)
+    for lo, hi in [(0, 0.01), (0.01, 0.5), (0.5, 2), (2, 4), (4, 6)]:
+        m = (r >= lo) & (r < hi)
+        if m.any():
+            print(f"r in [{lo}, {hi}): {m.sum():8d} normals, max |err| {err[m].max():.2e}, "
+                  f"max |err| / bound {np.max((err / (eps + res))[m]):.3f}")
+    assert np.all(err <= eps + res), np.max(err / (eps + res))
