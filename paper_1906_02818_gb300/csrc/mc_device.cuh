@@ -60,9 +60,13 @@ __device__ __forceinline__ float u01(uint32_t x)
 // (lg2, sqrt, sin, cos: one issue slot each).  The angle is taken as
 // theta = 2 pi (u_b - 1/2) in (-pi, pi), the range where sin/cos.approx are
 // most accurate, and the sign flip (cos(theta) = -cos(2 pi u_b), likewise
-// sin) is folded into r.  -2 ln u_a is clamped at 0: lg2.approx has an
-// absolute error near 2^-22 close to u = 1.  Per-normal absolute error is a
-// few 1e-6 at worst.
+// sin) is folded into r.  theta comes from one FMA on f = 1 + floor(b/2^9)
+// 2^-23 (the bits of u01 before its subtraction): f fl(2 pi) - fl(3 pi),
+// within 3.5e-7 of 2 pi (u_b - 1/2) over all 2^23 values of f (two roundings
+// of the constants, one of the FMA) and inside (-pi, pi).  -2 ln u_a is
+// clamped at 0: lg2.approx has an absolute error near 2^-22 close to u = 1.
+// The per-normal absolute error is a few 1e-6, except for u_a within ~1e-6
+// of 1, where r < ~1.5e-3 is off by at most sqrt(1.39 * 2^-22) ~ 6e-4.
 __device__ __forceinline__ float lg2_approx(float x)
 {
     float y;
@@ -96,11 +100,11 @@ __device__ __forceinline__ float ex2_approx(float x)
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
 {
-    const float ua = u01(a), ub = u01(b);
+    const float ua = u01(a);
     // -2 ln u = -2 ln(2) log2(u)
     const float r2 = fmaxf(-1.3862943611198906f * lg2_approx(ua), 0.0f);
     const float nrad = -sqrt_approx(r2);
-    const float theta = 6.2831853071795865f * (ub - 0.5f);
+    const float theta = fmaf(__uint_as_float(0x3F800000u | (b >> 9)), 6.2831854820251465f, -9.42477798461914f);
     z0 = nrad * cos_approx(theta);
     z1 = nrad * sin_approx(theta);
 }
