@@ -1,6 +1,6 @@
 """GPU parity of portfolio risk (mc_risk) and of the surrogate's labels with
 the FP64 oracle on identical streams; exactness of the VaR / CVaR selection;
-the trained surrogate judged by nested Monte Carlo, and what it gains."""
+the trained surrogate measured against nested Monte Carlo, and what it gains."""
 import math
 import time
 
@@ -101,9 +101,9 @@ def trained(gb):
     return net, loss
 
 
-def test_surrogate_judged_by_nested(gb, trained):
+def test_surrogate_against_nested(gb, trained):
     """The trained surrogate's VaR / CVaR against nested Monte Carlo (the
-    judge) on the same 2048 scenarios of the full 1024-option book, and the
+    yardstick) on the same 2048 scenarios of the full 1024-option book, and the
     time each revaluation takes."""
     import torch
     net, loss = trained
@@ -122,7 +122,7 @@ def test_surrogate_judged_by_nested(gb, trained):
           f"CVaR nested {nested['cvar']:.3f} surrogate {sur['cvar']:.3f} (rel {rc:.3%}); "
           f"PnL corr {corr:.4f}; time nested {t1 - t0:.3f}s surrogate {t2 - t1:.3f}s")
     # Reduced training (2^18 points, 2^11-path labels) and a 2048-scenario
-    # judge with 2^12 inner paths (its own PnL noise is ~5 on a PnL standard
+    # yardstick with 2^12 inner paths (its own PnL noise is ~5 on a PnL standard
     # deviation of ~26): VaR / CVaR within 15 %; the full-size run
     # (2^20 labels x 2^13 paths, risk_report) lands within 3 %.
     assert corr > 0.93
