@@ -41,7 +41,7 @@ def normal_error_bound(zf):
 
 
 def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_fixed=False, fold=None,
-            detail=False):
+            detail=False, flip=False):
     """Per-path monitored U of the quantised-operand scheme:
     dW_n = sqrt(dt) sigma_n sum_k Lq[n,k] zq[k] / (s_n s_z); E4M3 normals are
     scaled per path and step by 448 / max|z| (fp8_fixed: by 448 / 6).  Row
@@ -53,7 +53,9 @@ def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_f
     FP32 normals, which differ from the oracle's by up to
     normal_error_bound, so an operand whose window [z - e, z + e] straddles a
     rounding boundary may take either neighbouring code; D [paths, steps, d]
-    is the width of the codes the window can reach (in units of z)."""
+    is the width of the codes the window can reach (in units of z).
+    flip=True rounds every such operand to the code at the other end of its
+    window instead (a planted worst case for checking flip_bound)."""
     d = len(w["s0"])
     if fold is None:
         fold = prec == "bf16" and d <= 64
@@ -77,7 +79,8 @@ def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_f
         s = np.float32(448.0 / 6.0)
         Zq = quantize((Z32 * s).astype(np.float32), "fp8") / np.float64(s)
         ex = s * E + np.abs(Z32 * s) * 1.2e-7
-        D = (quantize(Z32 * s + ex, "fp8") - quantize(Z32 * s - ex, "fp8")) / np.float64(s)
+        lo = quantize(Z32 * s - ex, "fp8") / np.float64(s)
+        hi = quantize(Z32 * s + ex, "fp8") / np.float64(s)
     elif prec == "fp8":
         amax = np.abs(Z32).max(axis=2, keepdims=True)
         s = (np.float32(448.0) / amax).astype(np.float32)
@@ -87,10 +90,14 @@ def emulate(orc, w, prec, paths, steps, scheme="log_euler", path_offset=0, fp8_f
         rel_s = np.take_along_axis(E, np.abs(Z32).argmax(axis=2)[..., None], axis=2) / amax + 2.4e-7
         x = Z32.astype(np.float64) * s
         ex = s * E + np.abs(x) * rel_s
-        D = (quantize(x + ex, "fp8") - quantize(x - ex, "fp8")) * (amax / 448.0)
+        lo = quantize(x - ex, "fp8") * (amax / 448.0)
+        hi = quantize(x + ex, "fp8") * (amax / 448.0)
     else:
         Zq = quantize(Z32, prec)
-        D = quantize(Z + E, prec) - quantize(Z - E, prec)
+        lo, hi = quantize(Z - E, prec), quantize(Z + E, prec)
+    D = hi - lo
+    if flip:  # every ambiguous operand takes the code at the other end of its window
+        Zq = np.where(D > 0, np.where(np.abs(Zq - lo) <= np.abs(Zq - hi), hi, lo), Zq)
     sig, s0, wt = w["sigma"], w["s0"], w["weights"]
     x = np.log(s0)[None, :].repeat(paths, 0) if scheme == "log_euler" else s0[None, :].repeat(paths, 0).copy()
     U = np.empty((steps + 1, paths))
