@@ -70,46 +70,72 @@ __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const doubl
     if (threadIdx.x == 0) *status = s_fail;
 }
 
-// The same factorisation for d <= 64 with W in shared memory.
+// The same factorisation for d <= 64 with W in shared memory.  FP64 issue is
+// the scarce resource here (a warp's FP64 instruction holds its SM quarter
+// for tens of cycles), so the trailing update of column k walks the lower
+// triangle of the (d-k-1)^2 block densely, through a table of (row, column)
+// offsets enumerated row by row: every lane of every issued FMA does work, and
+// no index needs a division.  Entry 0 of the walk is the next pivot, which
+// thread 0 therefore updates itself: it forms the next pivot's reciprocal
+// square root without waiting, and each column costs two block barriers.
+// The arithmetic and its order are those of cholesky_kernel.
 constexpr int kCholSmallD = 64;
 constexpr int kCholSmallBlock = 256;
+constexpr int kCholTri = (kCholSmallD - 1) * kCholSmallD / 2;  // entries of the largest trailing triangle
+
 __global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, const double *A, double *L, int *status)
 {
     __shared__ double W[kCholSmallD][kCholSmallD + 1];
+    __shared__ uint16_t tri[kCholTri];  // (ii << 6) | jj, jj <= ii, row by row
     __shared__ double s_inv;
     __shared__ int s_fail;
-    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) W[idx / d][idx % d] = A[idx];
-    if (threadIdx.x == 0) s_fail = 0;
+    const int t = threadIdx.x;
+    for (int idx = t; idx < d * d; idx += blockDim.x) W[idx / d][idx % d] = A[idx];
+    for (int ii = t; ii < kCholSmallD - 1; ii += blockDim.x)
+        for (int jj = 0; jj <= ii; ++jj) tri[ii * (ii + 1) / 2 + jj] = static_cast<uint16_t>((ii << 6) | jj);
+    if (t == 0) {
+        s_fail = 0;
+        const double p = d > 0 ? A[0] : 1.0;
+        if (!(p > 0.0)) {
+            s_fail = 1;
+        } else {
+            const double r = rsqrt_refined(p);
+            s_inv = r;
+        }
+    }
     __syncthreads();
+    if (t == 0 && !s_fail && d > 0) W[0][0] = W[0][0] * s_inv;  // p r with p = W[0][0]
     for (int k = 0; k < d; ++k) {
-        if (threadIdx.x == 0) {
-            const double p = W[k][k];
+        // s_inv holds 1/sqrt of the pivot W[k][k] (thread 0 wrote both)
+        __syncthreads();
+        if (s_fail) break;
+        const double inv = s_inv;
+        for (int i = k + 1 + t; i < d; i += blockDim.x) W[i][k] *= inv;
+        __syncthreads();
+        const int m = d - k - 1, n = m * (m + 1) / 2;
+        for (int e = t; e < n; e += blockDim.x) {
+            const int code = tri[e], i = k + 1 + (code >> 6), j = k + 1 + (code & 63);
+            W[i][j] -= W[i][k] * W[j][k];
+        }
+        // entry 0 is (k + 1, k + 1), updated above by this same thread
+        if (t == 0 && k + 1 < d) {
+            const double p = W[k + 1][k + 1];
             if (!(p > 0.0)) {
                 s_fail = 1;
             } else {
                 const double r = rsqrt_refined(p);
-                W[k][k] = p * r;
+                W[k + 1][k + 1] = p * r;
                 s_inv = r;
             }
         }
-        __syncthreads();
-        if (s_fail) break;
-        const double inv = s_inv;
-        for (int i = k + 1 + threadIdx.x; i < d; i += blockDim.x) W[i][k] *= inv;
-        __syncthreads();
-        const int m = d - k - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int ii = idx / m, jj = idx % m;
-            if (jj <= ii) W[k + 1 + ii][k + 1 + jj] -= W[k + 1 + ii][k] * W[k + 1 + jj][k];
-        }
-        __syncthreads();
     }
+    __syncthreads();
     if (!s_fail)
-        for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+        for (int idx = t; idx < d * d; idx += blockDim.x) {
             const int i = idx / d, j = idx % d;
             L[idx] = j > i ? 0.0 : W[i][j];
         }
-    if (threadIdx.x == 0) *status = s_fail;
+    if (t == 0) *status = s_fail;
 }
 
 __global__ void scale_factor_kernel(int d, const double *L, const double *sigma, double c, double sdt,

@@ -84,3 +84,30 @@ def test_tensor_core_launch_below_one_tile(gb, orc, paths):
     m = payoffs_from_U(U, pays, w["r"], w["T"])[0].mean()
     fb = flip_bound(aux, U, pays, w["r"], w["T"])[0]
     assert abs(got[0][0] - m) <= REL * max(abs(m), 1e-6) + fb + 1e-9, (paths, got[0][0], m)
+
+
+@pytest.mark.parametrize("d", [2, 16, 64, 100])
+def test_indefinite_correlation_is_reported(gb, d):
+    """A correlation matrix with entries in [-1, 1] that is not positive
+    definite (d = 2: correlation 1, a zero second pivot; otherwise three
+    assets at 0.9, 0.9, -0.9, determinant -2.89) makes the device's FP64
+    Cholesky report MC_ENOTPSD (the small-matrix kernel for d <= 64, the
+    general one above), on the FP32 and BF16 paths; the library stays usable,
+    and the same market with a valid correlation prices."""
+    from paper_1906_02818_gb300 import native
+    corr = np.eye(d)
+    if d == 2:
+        corr[0, 1] = corr[1, 0] = 1.0
+    else:
+        corr[0, 1] = corr[1, 0] = corr[0, 2] = corr[2, 0] = 0.9
+        corr[1, 2] = corr[2, 1] = -0.9
+    assert np.linalg.eigvalsh(corr).min() <= 1e-12
+    model = dict(kind="gbm", s0=np.full(d, 100.0), sigma=np.full(d, 0.2), r=0.05, corr=corr)
+    pays = [dict(kind="call", strike=100.0)]
+    for prec in ("fp32", "bf16"):
+        with pytest.raises(native.MCError) as e:
+            gb.price(model, dict(steps=4, T=1.0, paths=256, precision=prec), pays)
+        assert e.value.status == native.MC_ENOTPSD
+    valid = np.where(np.eye(d) > 0, 1.0, np.where(corr != 0, 0.5, 0.0))
+    got = gb.price(dict(model, corr=valid), dict(steps=4, T=1.0, paths=256), pays)
+    assert got[0][0] > 0 and np.isfinite(got[0][1])
