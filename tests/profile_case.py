@@ -1,20 +1,20 @@
 """Run one workload a fixed number of times (for profilers).
 
-  python -m paper_1906_02818_gb300.profile_case basket64 --paths 16384 --reps 2 [--prec fp32]
-  python -m paper_1906_02818_gb300.profile_case gbm1d --paths 1048576
-  python -m paper_1906_02818_gb300.profile_case heston --paths 65536
-  python -m paper_1906_02818_gb300.profile_case basket512 --paths 32768 --prec bf16
-  python -m paper_1906_02818_gb300.profile_case heston_greeks --paths 65536
-  python -m paper_1906_02818_gb300.profile_case mlp --paths 1048576 --prec bf16   (paths = network rows)
-  python -m paper_1906_02818_gb300.profile_case labels --paths 4096              (paths = label points)
-  python -m paper_1906_02818_gb300.profile_case risk_nested --paths 256          (paths = scenarios)
-  python -m paper_1906_02818_gb300.profile_case train --paths 262144            (paths = samples, 1 epoch;
+  python tests/profile_case.py basket64 --paths 16384 --reps 2 [--prec fp32]
+  python tests/profile_case.py gbm1d --paths 1048576
+  python tests/profile_case.py heston --paths 65536
+  python tests/profile_case.py basket512 --paths 32768 --prec bf16
+  python tests/profile_case.py heston_greeks --paths 65536
+  python tests/profile_case.py mlp --paths 1048576 --prec bf16   (paths = network rows)
+  python tests/profile_case.py labels --paths 4096              (paths = label points)
+  python tests/profile_case.py risk_nested --paths 256          (paths = scenarios)
+  python tests/profile_case.py train --paths 262144            (paths = samples, 1 epoch;
                                                                                  --prec tf32x3: tensor-core training)
-  python -m paper_1906_02818_gb300.profile_case bridge --paths 1048576          (the In and Out Put, 25 steps)
-  python -m paper_1906_02818_gb300.profile_case qmc --paths 262144              (points x 16 replications)
-  python -m paper_1906_02818_gb300.profile_case mlmc --paths 16384              (correction paths, d = 64, bf16)
-  python -m paper_1906_02818_gb300.profile_case factor512 --paths 65536
-  python -m paper_1906_02818_gb300.profile_case corr64 --paths 65536          (correlation sensitivities, d = 64)
+  python tests/profile_case.py bridge --paths 1048576          (the In and Out Put, 25 steps)
+  python tests/profile_case.py qmc --paths 262144              (points x 16 replications)
+  python tests/profile_case.py mlmc --paths 16384              (correction paths, d = 64, bf16)
+  python tests/profile_case.py factor512 --paths 65536
+  python tests/profile_case.py corr64 --paths 65536          (correlation sensitivities, d = 64)
 """
 from __future__ import annotations
 

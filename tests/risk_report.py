@@ -3,7 +3,7 @@ Monte Carlo training labels over the surrogate's parameter box, native
 training of the network, VaR / CVaR of the 1024-option book by the
 surrogate, and the same by nested Monte Carlo (the yardstick), with timings.
 
-  python -m paper_1906_02818_gb300.risk_report [--labels 1048576] [--label-paths 8192]
+  python tests/risk_report.py [--labels 1048576] [--label-paths 8192]
          [--scen 65536] [--inner 4096] [--prec fp32|bf16] [--train fp32|tf32x3] [--alpha 0.99]
          [--accuracy-sweep]
 """

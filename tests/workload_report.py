@@ -246,7 +246,7 @@ def run_basket512(torch, gb, orc, a):
 
 def run_risk(torch, gb, orc, a):
     import subprocess
-    r = subprocess.run([sys.executable, "-m", "paper_1906_02818_gb300.risk_report", "--scen", str(1 << 16)],
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(os.path.abspath(__file__)), "risk_report.py"), "--scen", str(1 << 16)],
                        capture_output=True, text=True,
                        cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     return json.loads(r.stdout.strip().splitlines()[-1])
