@@ -156,6 +156,28 @@ int mc_release_cache(void);
 const char *mc_last_error(void);
 
 /*
+ * The random stream (Sec. IV.A: keyed counter-based Philox4x32-10; Sec. VI.D:
+ * Box-Muller), written out by the device functions every path kernel draws
+ * from, e.g. to check them bit for bit against another implementation or to
+ * feed the same normals to other code.  Key = (seed mod 2^32, seed div 2^32).
+ *   mc_philox_words: dev_out (DEVICE, 16-byte aligned, caller-owned) [blocks][4]
+ *     uint32 = Philox4x32-10 of counter (q mod 2^32, q div 2^32, n mod 2^32,
+ *     n div 2^32) for q = q0 .. q0 + blocks - 1, n = stream_index.
+ *     0 <= blocks <= 2^40 and the block range must not wrap past 2^64
+ *     (MC_EINVAL otherwise).
+ *   mc_normals: dev_out (DEVICE, caller-owned) [count] float32 = normals
+ *     j0 .. j0 + count - 1 of stream stream_index (normal j from block j/4,
+ *     lane j mod 4, Box-Muller on lanes (0,1) and (2,3), uniforms
+ *     (floor(x/2^9) + 1/2) 2^-23; the SFU's approximate lg2, sqrt, sin and
+ *     cos, so each normal is within a few 1e-6 of its exact value).
+ *     0 <= count <= 2^40, no wrap past 2^64.
+ * Both are asynchronous on `stream`.
+ */
+int mc_philox_words(uint64_t seed, uint64_t stream_index, uint64_t q0, int64_t blocks, uint32_t *dev_out,
+                    void *stream);
+int mc_normals(uint64_t seed, uint64_t stream_index, uint64_t j0, int64_t count, float *dev_out, void *stream);
+
+/*
  * mc_simulate -- materialise simulated paths (Sec. II.A.1 / II.A.2 scheme).
  *   dev_out: caller-owned DEVICE buffer of float32, layout
  *            [steps/save_every + 1][D][paths], D = d for MC_GBM (asset prices)
@@ -192,10 +214,20 @@ int32_t mc_greek_count(const mc_model *model);
  *     every cfg->ckpt_every steps (0 = 32, at most 64) in device scratch and
  *     each segment is recomputed from its checkpoint during the backward
  *     sweep.  d sqrt(v+)/dv is taken as 0 where v <= 0.
- *   MC_GBM: d == 1 and MC_LOG_EULER (the adjoint of log S is constant along
- *     the path and the sweep reduces to closed forms per path).
- * Payoffs: European and Asian kinds only (a barrier's knock indicator has no
- * pathwise derivative: MC_EUNSUPPORTED).
+ *   MC_GBM, d == 1: MC_LOG_EULER (the adjoint of log S is constant along
+ *     the path and the sweep reduces to closed forms per path); European and
+ *     Asian payoffs, 1 <= n_payoff.
+ *   MC_GBM, 2 <= d <= 512 (correlated basket on U = sum_a w_a S_a): exactly
+ *     one payoff, MC_CALL or MC_PUT on U(T) (MC_EINVAL for n_payoff != 1,
+ *     MC_EUNSUPPORTED for other kinds); MC_LOG_EULER; sigma_a > 0 for every
+ *     asset (MC_EINVAL otherwise); any cfg->precision (the Greeks' per-path
+ *     terms are formed in the path kernel's epilogue from the same paths as
+ *     the price).  greeks[0..d-1] = delta_a = dP/dS0_a,
+ *     greeks[d..2d-1] = vega_a = dP/dsigma_a (sigma_a scales column a of
+ *     diag(sigma) Lrho), greeks[2d] = rho = dP/dr.  MC_ENOTPSD if corr is
+ *     not positive definite, MC_ETIMEOUT if a bounded device wait gave up.
+ * Barrier payoffs are rejected (a knock indicator has no pathwise derivative:
+ * MC_EUNSUPPORTED).
  *   prices: host [n_payoff] or NULL; greeks: host [n_payoff][mc_greek_count].
  * Synchronises `stream` before returning.
  */
@@ -314,6 +346,19 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
  * [mc_mlp_param_count] host floats, e.g. the average of the ranks' batch
  * gradients in data-parallel training.  Synchronises `stream`. */
 int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *stream);
+/* Data-parallel training without host round trips (every buffer on the
+ * network's device, everything asynchronous on `stream`):
+ *   mc_mlp_loss_grad_sums: dev_out [count + 1] floats: [0, count) = the
+ *     gradient of the batch's SUMMED loss sum_i (y_i - t_i)^2 (n times the
+ *     gradient of mc_mlp_loss_grad), [count] = that summed loss; adding the
+ *     ranks' buffers (an all-reduce) gives the global batch's sums.
+ *   mc_mlp_apply_grad_sums: one Adam step with gradient scale * dev_grad
+ *     (scale = 1 / global batch size turns summed gradients into the mean).
+ * A bounded wait that expires in the tensor-core training products is
+ * reported by the network's next synchronising call (MC_ETIMEOUT). */
+int mc_mlp_loss_grad_sums(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, float *dev_out,
+                          void *stream);
+int mc_mlp_apply_grad_sums(mc_mlp *net, const float *dev_grad, float scale, float lr, void *stream);
 int mc_mlp_set_train_mode(mc_mlp *net, int32_t mode);
 int mc_mlp_destroy(mc_mlp *net);
 
@@ -378,6 +423,16 @@ int mc_risk(const mc_portfolio *portfolio, const mc_risk_cfg *cfg, mc_risk_resul
             void *stream);
 
 /*
+ * mc_tail -- VaR and CVaR (Sec. VI.B, the selection of mc_risk) of the
+ * losses -pnl over a DEVICE vector of n PnLs, e.g. every shard's scenario
+ * PnLs gathered on one device: VaR_alpha = the k-th largest loss,
+ * k = ceil((1 - alpha) n); CVaR_alpha = the mean of the losses strictly above
+ * VaR_alpha (VaR_alpha itself if none is); n_tail = their count;
+ * base_value = 0.  1 <= n <= 2^24, 0 < alpha < 1.  Synchronises `stream`.
+ */
+int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *result, void *stream);
+
+/*
  * mc_surrogate_labels -- training set of the surrogate: for each point p of
  * dev_points [n][5] = (S/K, sigma, tau, r, K/H), the label dev_labels[p] =
  * discounted Monte Carlo price / K of a call on S with strike K and maturity
@@ -411,6 +466,19 @@ int mc_plan_destroy(mc_plan *plan);
 
 /* Number of kernel launches one mc_plan_execute issues (for accounting). */
 int mc_plan_launches(const mc_plan *plan);
+
+/*
+ * Runs over disjoint path ranges (path_offset; one per device or process)
+ * combine into the estimator of Eq. 3 over their union:
+ *   mc_moments: moments [n_payoff][3] = (N mean, N mean(f^2), N), discounted
+ *     units, of a run's results over N = paths paths (recovered from
+ *     price and se exactly up to rounding).
+ *   mc_combine: out [n_payoff] = (price, se) from moments summed over runs
+ *     (e.g. by an all-reduce).
+ * Host arrays only; no device work.  MC_EINVAL on non-finite input.
+ */
+int mc_moments(const mc_result *res, int32_t n_payoff, int64_t paths, double *moments);
+int mc_combine(const double *moments, int32_t n_payoff, mc_result *out);
 
 /*
  * mc_price_gbm1d_noalloc -- single-asset GBM pricing that allocates nothing.

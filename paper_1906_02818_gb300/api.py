@@ -170,6 +170,54 @@ def simulate(model: dict, cfg: dict, save_every: int = 1, stream=None):
     return out
 
 
+def moments(results, paths: int) -> np.ndarray:
+    """(N mean, N mean(f^2), N) per payoff [n, 3] of a run's (price, se)
+    list over `paths` paths (mc_moments)."""
+    n = len(results)
+    res = (McResult * n)(*[McResult(float(p), float(se)) for p, se in results])
+    out = np.empty((n, 3), dtype=np.float64)
+    check(native.lib().mc_moments(res, n, int(paths), out.ctypes.data_as(native.c_double_p)))
+    return out
+
+
+def combine(mom) -> list:
+    """(price, se) per payoff from moments summed over runs (mc_combine)."""
+    mom = np.ascontiguousarray(mom, dtype=np.float64).reshape(-1, 3)
+    out = (McResult * mom.shape[0])()
+    check(native.lib().mc_combine(mom.ctypes.data_as(native.c_double_p), mom.shape[0], out))
+    return [(r.price, r.se) for r in out]
+
+
+def tail(dev_pnl, alpha: float = 0.99, stream=None) -> dict:
+    """VaR / CVaR of the losses -pnl of a CUDA float64 vector (mc_tail)."""
+    pnl = dev_pnl.contiguous()
+    if not pnl.is_cuda or pnl.dtype.itemsize != 8 or pnl.dim() != 1:
+        raise ValueError("dev_pnl must be a 1-D CUDA float64 tensor")
+    res = native.McRiskResult()
+    check(native.lib().mc_tail(ctypes.c_void_p(pnl.data_ptr()), pnl.numel(), float(alpha), ctypes.byref(res),
+                               _stream_handle(stream)))
+    return dict(var=res.var, cvar=res.cvar, n_tail=res.n_tail)
+
+
+def philox_words(seed: int, stream_index: int, q0: int, blocks: int, stream=None):
+    """Philox4x32-10 blocks q0 .. q0 + blocks - 1 of a stream (mc_philox_words)
+    as a CUDA int32 tensor [blocks, 4] holding the uint32 words' bits."""
+    import torch
+    out = torch.empty((max(blocks, 1), 4), dtype=torch.int32, device="cuda")
+    check(native.lib().mc_philox_words(int(seed), int(stream_index), int(q0), int(blocks),
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out[:blocks]
+
+
+def normals(seed: int, stream_index: int, j0: int, count: int, stream=None):
+    """Normals j0 .. j0 + count - 1 of a stream (mc_normals), CUDA float32 [count]."""
+    import torch
+    out = torch.empty(max(count, 1), dtype=torch.float32, device="cuda")
+    check(native.lib().mc_normals(int(seed), int(stream_index), int(j0), int(count),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out[:count]
+
+
 class Plan:
     """A set-up computation (mc_plan_create) executable asynchronously."""
 
@@ -278,6 +326,25 @@ class Mlp:
         g = np.ascontiguousarray(g, dtype=np.float32)
         check(self._lib.mc_mlp_apply_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(lr),
                                           _stream_handle(stream)))
+
+    def loss_grad_sums(self, x, t, stream=None):
+        """CUDA float32 [count + 1]: the gradient of the batch's summed
+        squared error and that sum (mc_mlp_loss_grad_sums, asynchronous)."""
+        import torch
+        x, t = x.contiguous(), t.contiguous()
+        out = torch.empty(self.count + 1, dtype=torch.float32, device=x.device)
+        check(self._lib.mc_mlp_loss_grad_sums(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                              x.shape[0], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def apply_grad_sums(self, g, scale, lr, stream=None):
+        """One Adam step with gradient scale * g[:count] (g a CUDA float32
+        tensor; mc_mlp_apply_grad_sums, asynchronous)."""
+        g = g.contiguous()
+        if not g.is_cuda or g.numel() < self.count:
+            raise ValueError("g must be a CUDA float32 tensor of at least count entries")
+        check(self._lib.mc_mlp_apply_grad_sums(self._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_float(scale),
+                                               ctypes.c_float(lr), _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -61,7 +61,7 @@ struct L2 {
     // [pad 1024] Z | ring | barriers (256 B) | accumulators
     static constexpr int kBarOff = kZBytes + kRing * kChunkBytes;
     static constexpr int kSmem = 1024 + kBarOff + 256;
-    static_assert(32 + 16 * kRing + 20 <= 256, "mbarrier words exceed their area");
+    static_assert(32 + 16 * kRing + 32 <= 256, "mbarrier words exceed their area");
     __device__ static __forceinline__ uint32_t off(int row, int chunk)
     {
         const int phys = PREC == MC_FP8E4M3 ? (chunk ^ ((row >> 1) & 3)) : (chunk ^ (row & 7));
@@ -155,9 +155,10 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_co
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t zt = base, ring = base + Ly::kZBytes, bars = base + Ly::kBarOff;
-    // barrier words: zfull[2], zfree[2] (one pair per half of Z), lfull[R], lfree[R], ddone, dfree, tslot
+    // barrier words: zfull[2], zfree[2] (one pair per half of Z), lfull[R], lfree[R], ddone, dfree, tslot,
+    // xbar (the failure path's drain of the MMA issuer, and the test stall)
     const uint32_t zfull = bars, zfree = bars + 16, lfull = bars + 32, lfree = lfull + 8 * kRing;
-    const uint32_t ddone = lfree + 8 * kRing, dfree = ddone + 8, tslot = dfree + 8;
+    const uint32_t ddone = lfree + 8 * kRing, dfree = ddone + 8, tslot = dfree + 8, xbar = dfree + 16;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
 
     const int d = a.d, NP = (d + kPanel - 1) / kPanel, NB = (NP + 1) / 2;
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_co
         }
         tc::mbar_init(ddone, 1);
         tc::mbar_init(dfree, kWorkers);
+        tc::mbar_init(xbar, 1);
     }
     if (warp == 0) {
         tc::tmem_alloc(tslot, 512);
@@ -197,7 +199,13 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_co
     const uint32_t tmem = *tslot_ptr;
     const int64_t ntiles = (a.run.paths + kRows - 1) / kRows;
     // chunks per step: sum over panels p of (NP - p)
-    const uint32_t cap = a.wait_cap;
+    const uint32_t cap = tc::cap_polls(a.wait_cap);
+    uint32_t issued = 0, lastpar = 0;  // producer: per ring slot, a copy was issued; its lfull parity
+    if (tc::stall_requested(a.wait_cap)) {
+        // test request: a wait that nothing completes, before any copy or MMA
+        if (t == 0 && !tc::mbar_wait_bounded(xbar, 0, cap)) s_fail = 1u;
+        __syncthreads();
+    }
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -214,6 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_co
                                 tc::bulk_g2s(ring + slot * Ly::kChunkBytes,
                                              a.bimg + static_cast<size_t>(b * kMaxPanels + p) * Ly::kChunkBytes,
                                              Ly::kChunkBytes, lfull + 8 * slot);
+                                issued |= 1u << slot;
+                                lastpar = (lastpar & ~(1u << slot)) | (phase << slot);
                             }
                             if (++slot == kRing) {
                                 slot = 0;
@@ -368,6 +378,21 @@ __global__ void __launch_bounds__(kThreads, 1) basket_big_kernel(const __grid_co
         }
     }
     __syncthreads();
+    if (s_fail) {
+        // failure path, before the shared memory and TMEM are released: the
+        // producer waits for the last copy into each ring slot, and one more
+        // commit of the MMA issuer tracks every MMA it issued (xbar is still
+        // in phase 0: waiting never completes a phase)
+        if (t == 0)
+            for (int r = 0; r < kRing; ++r)
+                if ((issued >> r) & 1u) tc::mbar_wait_bounded(lfull + 8 * r, (lastpar >> r) & 1u, cap);
+        if (t == 32) {
+            tc::mma_commit(xbar);
+            tc::mbar_wait_bounded(xbar, 0u, cap);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);

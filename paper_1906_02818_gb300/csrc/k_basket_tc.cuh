@@ -193,7 +193,9 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const __grid_consta
     tc::fence_after_sync();
     const uint32_t tmem = *tslot_ptr;
     // CTA-uniform: every change goes through __syncthreads_or.
-    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8, 0, a.wait_cap) ? 0 : 1) != 0;
+    // The factor tile's wait; a test request (a.stall = 1) redirects it to the
+    // MMA barrier, to which no MMA has been committed yet, so it runs out.
+    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8 - 8 * a.stall, 0, a.wait_cap) ? 0 : 1) != 0;
 
     uint32_t phase = 0;
     const int M = a.run.steps, d = a.d;
@@ -279,7 +281,15 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const __grid_consta
         }
         __syncthreads();
     }
-    if (aborted && t == 0) atomicExch(a.err, 1u);
+    if (aborted && t == 0) {
+        atomicExch(a.err, 1u);
+        // drain before the shared memory and TMEM are released.  Without an
+        // MMA (phase 0) the factor tile's copy may still be landing; after
+        // one, that copy had landed, and the last committed MMA group may
+        // still be running (every group is waited on once, `phase` counts
+        // them, and only the last wait can have given up).  Bounded as ever.
+        tc::mbar_wait_bounded(phase > 0 ? mbar : mbar + 8, phase > 0 ? (phase - 1) & 1u : 0u, a.wait_cap);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -334,7 +344,9 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot_ptr;
-    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8, 0, a.wait_cap) ? 0 : 1) != 0;
+    // The factor tile's wait; a test request (a.stall = 1) redirects it to the
+    // MMA barrier, to which no MMA has been committed yet, so it runs out.
+    bool aborted = __syncthreads_or(tc::mbar_wait_bounded(mbar + 8 - 8 * a.stall, 0, a.wait_cap) ? 0 : 1) != 0;
 
     uint32_t phase = 0;
     const int M = a.run.steps, d = a.d;
@@ -422,7 +434,15 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
         tc::fence_before_sync();
         __syncthreads();
     }
-    if (aborted && t == 0) atomicExch(a.err, 1u);
+    if (aborted && t == 0) {
+        atomicExch(a.err, 1u);
+        // drain before the shared memory and TMEM are released.  Without an
+        // MMA (phase 0) the factor tile's copy may still be landing; after
+        // one, that copy had landed, and the last committed MMA group may
+        // still be running (every group is waited on once, `phase` counts
+        // them, and only the last wait can have given up).  Bounded as ever.
+        tc::mbar_wait_bounded(phase > 0 ? mbar : mbar + 8, phase > 0 ? (phase - 1) & 1u : 0u, a.wait_cap);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {

@@ -564,6 +564,49 @@ size_t mlp_train_floats(const MlpLayout &L, int64_t n)
     return f + 2 * static_cast<size_t>(n) * maxw + static_cast<size_t>(kMaxSlices) * maxw * maxw;
 }
 
+// out[i] = n grad[i] for i < count (the gradient of the batch's summed loss);
+// out[count] = the sum of the loss partials, added by one block in FP64.
+__global__ void sums_out_kernel(int64_t count, const float *__restrict__ grad, double n,
+                                const double *__restrict__ partial, int npartial, float *__restrict__ out)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride)
+        out[i] = static_cast<float>(n * grad[i]);
+    if (blockIdx.x == 0) {
+        __shared__ double s_red[8];
+        double v = 0.0;
+        for (int i = threadIdx.x; i < npartial; i += blockDim.x) v += partial[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += s_red[w];
+            out[count] = static_cast<float>(tot);
+        }
+    }
+}
+
+__global__ void scale_copy_kernel(int64_t count, const float *__restrict__ src, float scale, float *__restrict__ g)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride)
+        g[i] = scale * src[i];
+}
+
+cudaError_t mlp_sums_out(int64_t count, const float *grad, double n, const double *partial, int npartial, float *out,
+                         cudaStream_t s)
+{
+    sums_out_kernel<<<grid_for(count), 256, 0, s>>>(count, grad, n, partial, npartial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_scale_copy(int64_t count, const float *src, float scale, float *g, cudaStream_t s)
+{
+    scale_copy_kernel<<<grid_for(count), 256, 0, s>>>(count, src, scale, g);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s)
 {
     const float b1 = 0.9f, b2 = 0.999f;

@@ -37,6 +37,7 @@ constexpr int kMaxW = 256;
 constexpr int kMaxIn = 10;               // 3 n_in <= 32: layer 0 fits one K = 32 panel
 constexpr int kMaxLayers = 16;
 constexpr int kRing = 5;
+static_assert(32 + 16 * kRing + 16 <= 128, "mbarrier words exceed their area");
 constexpr int kThreads = 576;
 constexpr int kLaneThreads = 256;        // epilogue threads of one tile lane
 constexpr int kPanelBytes = kRows * 64;  // one 128 x 32 bf16 panel
@@ -109,9 +110,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
     const uint32_t abytes = static_cast<uint32_t>(KC) * kPanelBytes;  // one tile's activations
     const uint32_t cbytes = static_cast<uint32_t>(W) * 64;            // one weight chunk
     const uint32_t ring = base + 2 * abytes, bars = ring + kRing * cbytes;
-    // barrier words: afull[2], dfull[2], lfull[R], lfree[R], tslot
+    // barrier words: afull[2], dfull[2], lfull[R], lfree[R], tslot, xbar (the
+    // failure path's drain of the MMA issuer, and the test stall)
     const uint32_t afull = bars, dfull = bars + 16, lfull = bars + 32, lfree = lfull + 8 * kRing;
-    const uint32_t tslot = lfree + 8 * kRing;
+    const uint32_t tslot = lfree + 8 * kRing, xbar = tslot + 8;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
 
     if (t == 0) {
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
             tc::mbar_init(lfull + 8 * r, 1);
             tc::mbar_init(lfree + 8 * r, 1);
         }
+        tc::mbar_init(xbar, 1);
     }
     if (warp == 0) {
         tc::tmem_alloc(tslot, 512);
@@ -135,7 +138,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
     const uint32_t tmem = *tslot_ptr;
     const int64_t ntiles = (a.n + kRows - 1) / kRows;
     const int64_t G = gridDim.x;
-    const uint32_t cap = a.cap;
+    const uint32_t cap = tc::cap_polls(a.cap);
+    uint32_t issued = 0, lastpar = 0;  // producer: per ring slot, a copy was issued; its lfull parity
+    if (tc::stall_requested(a.cap)) {
+        // test request: a wait that nothing completes, before any copy or MMA
+        if (t == 0 && !tc::mbar_wait_bounded(xbar, 0, cap)) s_fail = 1u;
+        __syncthreads();
+    }
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -153,6 +162,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
                                 tc::bulk_g2s(ring + slot * cbytes,
                                              a.img + static_cast<size_t>(chunk_id(l, kc, KC)) * cbytes, cbytes,
                                              lfull + 8 * slot);
+                                issued |= 1u << slot;
+                                lastpar = (lastpar & ~(1u << slot)) | (phase << slot);
                             }
                             if (++slot == kRing) {
                                 slot = 0;
@@ -289,6 +300,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
         }
     }
     __syncthreads();
+    if (s_fail) {
+        // failure path, before the shared memory and TMEM are released: the
+        // producer waits for the last copy into each ring slot, and one more
+        // commit of the MMA issuer tracks every MMA it issued (xbar is still
+        // in phase 0: waiting never completes a phase)
+        if (t == 0)
+            for (int r = 0; r < kRing; ++r)
+                if ((issued >> r) & 1u) tc::mbar_wait_bounded(lfull + 8 * r, (lastpar >> r) & 1u, cap);
+        if (t == 32) {
+            tc::mma_commit(xbar);
+            tc::mbar_wait_bounded(xbar, 0u, cap);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
@@ -379,7 +405,7 @@ cudaError_t mlp_forward_bf16(const MlpLayout &L, const float *params, const uint
     a.err = err;
     const int KC = a.W / kKc;
     // at least half the SM's shared memory: one CTA per SM, which owns all 512 TMEM columns
-    int smem = 1024 + 2 * KC * kPanelBytes + kRing * a.W * 64 + 128;
+    int smem = 1024 + 2 * KC * kPanelBytes + kRing * a.W * 64 + 128;  // barriers: 16 + 16 + 16 R + 8 + 8 <= 128
     if (smem < 120 * 1024) smem = 120 * 1024;
     cudaError_t e = cudaFuncSetAttribute(mlp_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -142,8 +142,10 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    // barriers: full[2] (loaders staged the chunk), empty[2] (its MMAs completed), done
-    const uint32_t full = base + 2 * kStage, empty = full + 16, done = empty + 16, tslot = done + 8;
+    // barriers: full[2] (loaders staged the chunk), empty[2] (its MMAs completed), done, tslot,
+    // xbar (the test stall)
+    const uint32_t full = base + 2 * kStage, empty = full + 16, done = empty + 16, tslot = done + 8,
+                   xbar = done + 16;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
     const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
     const int n0 = blockIdx.y * kBN;
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
             tc::mbar_init(empty + 8 * i, 1);
         }
         tc::mbar_init(done, 1);
+        tc::mbar_init(xbar, 1);
     }
     if (warp == 0) {
         tc::tmem_alloc(tslot, kBN);
@@ -167,6 +170,12 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot_ptr;
+    const uint32_t cap = tc::cap_polls(a.cap);
+    if (tc::stall_requested(a.cap)) {
+        // test request: a wait that nothing completes, before any MMA
+        if (t == 0 && !tc::mbar_wait_bounded(xbar, 0, cap)) s_fail = 1u;
+        __syncthreads();
+    }
 
     if (warp == kThreads / 32) {
         // ---------------- MMA issuer (one lane) ----------------
@@ -176,7 +185,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
                 const int st = c & 1;
                 const uint32_t a_hi = base + st * kStage, a_lo = a_hi + kATile, b_hi = a_lo + kATile,
                                b_lo = b_hi + kBTile;
-                if (tc::wait_or_fail(&s_fail, full + 8 * st, (c >> 1) & 1u, a.cap)) {
+                if (tc::wait_or_fail(&s_fail, full + 8 * st, (c >> 1) & 1u, cap)) {
                     tc::fence_after_sync();
 #pragma unroll
                     for (int k = 0; k < kBK / 8; ++k) {
@@ -200,7 +209,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
             const uint32_t a_hi = base + st * kStage, a_lo = a_hi + kATile, b_hi = a_lo + kATile,
                            b_lo = b_hi + kBTile;
             // the stage is free once the MMAs of chunk c - 2 have read it
-            if (c >= 2) tc::wait_or_fail(&s_fail, empty + 8 * st, ((c - 2) >> 1) & 1u, a.cap);
+            if (c >= 2) tc::wait_or_fail(&s_fail, empty + 8 * st, ((c - 2) >> 1) & 1u, cap);
             tc::fence_after_sync();
             if (!s_fail) store_frag(f, a_hi, a_lo, b_hi, b_lo);
             if (c + 2 < nk) load_frag(f, a, m0, n0, ke, kb + (c + 2) * kBK);
@@ -215,10 +224,16 @@ __global__ void __launch_bounds__(kThreads + 32, 1) tf32_gemm_kernel(const __gri
             if (c + 1 < nk) step(c + 1, f1);
         }
         // every MMA has completed once `done` fires
-        tc::wait_or_fail(&s_fail, done, 0u, a.cap);
+        tc::wait_or_fail(&s_fail, done, 0u, cap);
         tc::fence_after_sync();
     }
     __syncthreads();  // the operand stages are free for the staged output tile
+    if (s_fail) {
+        // failure path: `done` tracks every MMA the issuer committed; they
+        // must complete before the stages are reused and the TMEM is released
+        if (t == kThreads) tc::mbar_wait_bounded(done, 0u, cap);
+        __syncthreads();
+    }
     tc::fence_after_sync();
 
     // epilogue (warps 0..7; the issuer warp only passes the barriers).

@@ -60,37 +60,26 @@ extern "C" int mc_price_gbm1d_noalloc(const mc_model *m, const mc_sim_cfg *c, co
                                       int32_t n_payoff, mc_result *dev_out, void *stream)
 {
     using namespace gbmc;
-    if (!m || !c || !p || !dev_out) return noalloc_fail(MC_EINVAL, "NULL argument");
-    if (m->kind != MC_GBM || m->d != 1 || !m->s0 || !m->sigma || m->loadings)
-        return noalloc_fail(MC_EINVAL, "single-asset GBM only (kind MC_GBM, d = 1, s0 and sigma set, no loadings)");
+    if (!dev_out) return noalloc_fail(MC_EINVAL, "dev_out is NULL");
     if (n_payoff < 1 || n_payoff > MC_MAX_PAYOFFS)
         return noalloc_fail(MC_EINVAL, "n_payoff = %d outside [1, %d]", n_payoff, MC_MAX_PAYOFFS);
-    if (c->steps < 1 || !(c->T > 0.0) || c->paths < 1 || c->path_offset < 0 ||
-        (c->scheme != MC_LOG_EULER && c->scheme != MC_EULER))
-        return noalloc_fail(MC_EINVAL, "steps, T, paths, path_offset or scheme out of range");
-    if (c->monitoring != MC_DISCRETE) return noalloc_fail(MC_EUNSUPPORTED, "discrete barrier monitoring only");
-    if (!(m->s0[0] > 0.0) || !(m->sigma[0] >= 0.0) || !std::isfinite(m->r))
-        return noalloc_fail(MC_EINVAL, "s0 must be > 0, sigma >= 0, r finite");
-
+    // The same checks as mc_price (finite and positive s0, sigma, T; finite
+    // r, weights, strikes; no NaN barrier; path range inside [0, 2^56);
+    // unit correlation diagonal), then this entry point's own restrictions.
     PayoffSet ps{};
-    ps.n = n_payoff;
-    for (int i = 0; i < n_payoff; ++i) {
-        const int k = p[i].kind;
-        if (k < MC_CALL || k > MC_DI_PUT) return noalloc_fail(MC_EINVAL, "payoff %d: unknown kind %d", i, k);
-        ps.kind[i] = k;
-        ps.strike[i] = static_cast<float>(p[i].strike);
-        ps.barrier[i] = k >= MC_UO_CALL ? static_cast<float>(p[i].barrier) : INFINITY;
-        if (k == MC_ASIAN_CALL || k == MC_ASIAN_PUT) ps.need_avg = 1;
-        if (k >= MC_UO_CALL && k <= MC_UI_PUT) ps.need_max = 1;
-        if (k >= MC_DO_CALL) ps.need_min = 1;
-    }
+    int rc = check_price_args(m, c, p, n_payoff, &ps);
+    if (rc) return rc;
+    if (m->kind != MC_GBM || m->d != 1 || m->loadings)
+        return noalloc_fail(MC_EINVAL, "single-asset GBM only (kind MC_GBM, d = 1, no loadings)");
+    if (m->corr && std::fabs(m->corr[0] - 1.0) > 1e-12) return noalloc_fail(MC_EINVAL, "corr[0] must be 1");
+    if (c->monitoring != MC_DISCRETE) return noalloc_fail(MC_EUNSUPPORTED, "discrete barrier monitoring only");
 
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return noalloc_fail(MC_ECUDA, "device query: %s", cudaGetErrorString(e));
     unsigned char *scratch = nullptr;
-    int rc = scratch_for_device(dev, &scratch);
+    rc = scratch_for_device(dev, &scratch);
     if (rc) return rc;
 
     const double dt = c->T / c->steps, sdt = std::sqrt(dt), sg = m->sigma[0];

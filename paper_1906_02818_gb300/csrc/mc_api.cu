@@ -305,14 +305,27 @@ struct DeviceArena {
 
 // Polls of a bounded mbarrier wait before a kernel gives up (GBMC_WAIT_CAP
 // overrides; each poll suspends for at most a few microseconds).
+int gbmc::check_price_args(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *p, int np, PayoffSet *ps)
+{
+    int rc;
+    if ((rc = check_model(m)) || (rc = check_cfg(c, m)) || (rc = build_payoffs(p, np, ps))) return rc;
+    return MC_OK;
+}
+
+// GBMC_TEST_STALL=1 sets the cap's top bit: each tensor-core kernel then
+// starts with a wait that nothing completes and fails by design (the test of
+// the failure path; no asynchronous work is in flight at that point).
 uint32_t gbmc::mbar_wait_cap()
 {
+    uint32_t cap = 1u << 22;
     const char *e = std::getenv("GBMC_WAIT_CAP");
     if (e && *e) {
         const long v = std::strtol(e, nullptr, 10);
-        if (v > 0) return static_cast<uint32_t>(v);
+        if (v > 0) cap = static_cast<uint32_t>(v < 0x7fffffffL ? v : 0x7fffffffL);
     }
-    return 1u << 22;
+    const char *st = std::getenv("GBMC_TEST_STALL");
+    if (st && st[0] == '1') cap |= 0x80000000u;
+    return cap;
 }
 
 int gbmc::set_last_error(int code, const char *msg)
@@ -653,7 +666,9 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             ta.red = red;
             ta.red.err = P->err;
             ta.err = P->err;
-            ta.wait_cap = mbar_wait_cap();
+            const uint32_t cap = mbar_wait_cap();
+            ta.wait_cap = cap & 0x7fffffffu;
+            ta.stall = cap >> 31;
             P->block = 128;
             resident = basket_tc_occupancy(P->prec, ta) * di.sms;
         } else {
@@ -791,6 +806,41 @@ int mc_plan_destroy(mc_plan *plan)
 }
 
 int mc_plan_launches(const mc_plan *plan) { return plan ? 1 : 0; }
+
+// Eq. 3 over a union of disjoint path ranges.  A run over N paths reported
+// price = e^{-rT} S1 / N and se = e^{-rT} sqrt((S2 / N - (S1 / N)^2) / (N - 1))
+// (S1, S2 the sums of f and f^2), so (N mean, N mean(f^2), N) in discounted
+// units are recovered exactly up to rounding, add over runs, and give back
+// the estimator and its standard error of the union.
+int mc_moments(const mc_result *res, int32_t n_payoff, int64_t paths, double *moments)
+{
+    if (!res || !moments || n_payoff < 1 || paths < 1) return fail(MC_EINVAL, "res, moments set; n_payoff, paths >= 1");
+    const double n = static_cast<double>(paths);
+    for (int i = 0; i < n_payoff; ++i) {
+        const double m = res[i].price, se = res[i].se;
+        if (!std::isfinite(m) || !std::isfinite(se) || se < 0.0) return fail(MC_EINVAL, "result %d is not finite", i);
+        const double m2 = paths > 1 ? se * se * (n - 1.0) + m * m : m * m;
+        moments[3 * i] = n * m;
+        moments[3 * i + 1] = n * m2;
+        moments[3 * i + 2] = n;
+    }
+    return MC_OK;
+}
+
+int mc_combine(const double *moments, int32_t n_payoff, mc_result *out)
+{
+    if (!moments || !out || n_payoff < 1) return fail(MC_EINVAL, "moments, out set; n_payoff >= 1");
+    for (int i = 0; i < n_payoff; ++i)
+        if (!(moments[3 * i + 2] >= 1.0) || !std::isfinite(moments[3 * i]) || !std::isfinite(moments[3 * i + 1]))
+            return fail(MC_EINVAL, "moments of payoff %d: path count < 1 or sums not finite", i);
+    for (int i = 0; i < n_payoff; ++i) {
+        const double n = moments[3 * i + 2], m = moments[3 * i] / n;
+        const double var = std::fmax(moments[3 * i + 1] / n - m * m, 0.0);
+        out[i].price = m;
+        out[i].se = n > 1.0 ? std::sqrt(var / (n - 1.0)) : 0.0;
+    }
+    return MC_OK;
+}
 
 int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
              mc_result *out, void *stream)

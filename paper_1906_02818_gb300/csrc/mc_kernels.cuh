@@ -89,6 +89,7 @@ struct TcArgs {
     ReduceArgs red;
     unsigned int *err;     // set to 1 when a bounded wait gave up
     uint32_t wait_cap;     // polls per mbarrier wait before giving up
+    uint32_t stall;        // test request: fail through a wait nothing completes (GBMC_TEST_STALL)
 };
 
 // Large baskets (k_basket_big.cuh, tensor cores; k_basket_wide.cu, FP32):
@@ -247,6 +248,10 @@ cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int bat
 
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
+// The argument checks of mc_price (model, simulation configuration, payoff
+// list), shared by every pricing entry point; fills *ps on success and sets
+// the thread-local error message otherwise.
+int check_price_args(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *p, int np, PayoffSet *ps);
 // Polls of a bounded mbarrier wait before a tensor-core kernel gives up.
 uint32_t mbar_wait_cap();
 

@@ -272,6 +272,32 @@ int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *strea
     return MC_OK;
 }
 
+int mc_mlp_loss_grad_sums(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, float *dev_out,
+                          void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!dev_x || !dev_t || !dev_out || n < 1) return set_last_error(MC_EINVAL, "x, t, out must be set and n >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_work(net, train_floats(net, n)))) return rc;
+    if ((rc = loss_grad_batch(net, dev_x, dev_t, n, s))) return rc;
+    MLP_CUDA(mlp_sums_out(net->L.count, net->grad, static_cast<double>(n), net->partial, kPartials, dev_out, s));
+    return MC_OK;
+}
+
+int mc_mlp_apply_grad_sums(mc_mlp *net, const float *dev_grad, float scale, float lr, void *stream)
+{
+    int rc;
+    if ((rc = check_net(net))) return rc;
+    if (!dev_grad || !(lr > 0.0f) || !(scale > 0.0f) || !std::isfinite(scale))
+        return set_last_error(MC_EINVAL, "dev_grad set, lr > 0 and a finite scale > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MLP_CUDA(mlp_scale_copy(net->L.count, dev_grad, scale, net->grad, s));
+    MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
+    ++net->version;
+    return MC_OK;
+}
+
 int mc_mlp_destroy(mc_mlp *net)
 {
     delete net;

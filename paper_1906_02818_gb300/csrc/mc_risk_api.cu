@@ -69,6 +69,29 @@ int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths
     return MC_OK;
 }
 
+int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *res, void *stream)
+{
+    if (!dev_pnl || !res) return fail(MC_EINVAL, "dev_pnl and result must be set");
+    if (n < 1 || n > (int64_t(1) << 24)) return fail(MC_EINVAL, "n outside [1, 2^24]");
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(MC_EINVAL, "alpha must lie in (0, 1)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    DevBufs B;
+    double *d_work, *d_res;
+    RK_CUDA(B.alloc(&d_work, np2));
+    RK_CUDA(B.alloc(&d_res, 3));
+    RK_CUDA(launch_tail(n, dev_pnl, d_work, np2, alpha, d_res, s));
+    double r3[3];
+    RK_CUDA(cudaMemcpyAsync(r3, d_res, sizeof r3, cudaMemcpyDeviceToHost, s));
+    RK_CUDA(cudaStreamSynchronize(s));
+    res->var = r3[0];
+    res->cvar = r3[1];
+    res->n_tail = static_cast<int64_t>(r3[2]);
+    res->base_value = 0.0;
+    return MC_OK;
+}
+
 int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, double *host_pnl, void *stream)
 {
     if (!pf || !cf || !res) return fail(MC_EINVAL, "portfolio, cfg and result must be set");

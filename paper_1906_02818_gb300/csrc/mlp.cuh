@@ -48,6 +48,11 @@ cudaError_t mlp_bf16_prepare(const MlpLayout &L, const float *params, uint8_t *i
 cudaError_t mlp_forward_bf16(const MlpLayout &L, const float *params, const uint8_t *img, const float *x, int64_t n,
                              float *y, unsigned int *err, uint32_t cap, cudaStream_t s);
 cudaError_t mlp_adam(int64_t count, float *p, const float *g, float *m, float *v, float lr, int step, cudaStream_t s);
+// Data-parallel building blocks: out[0..count) = n grad, out[count] = sum of
+// the loss partials; g = scale src.
+cudaError_t mlp_sums_out(int64_t count, const float *grad, double n, const double *partial, int npartial, float *out,
+                         cudaStream_t s);
+cudaError_t mlp_scale_copy(int64_t count, const float *src, float scale, float *g, cudaStream_t s);
 
 // SiLU and its derivative in FP32 (the training path's activation).
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }

@@ -46,6 +46,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
     return false;
 }
 
+// A wait cap with its top bit set carries a test request (the host sets it
+// when GBMC_TEST_STALL is 1): every CTA first waits on a barrier phase that
+// nothing completes, before it has issued any asynchronous copy or MMA, so
+// that wait runs out after the cap's polls and the kernel takes its failure
+// path deterministically.  The low 31 bits are the poll count of every wait.
+constexpr uint32_t kStallFlag = 0x80000000u;
+__device__ __forceinline__ uint32_t cap_polls(uint32_t cap) { return cap & ~kStallFlag; }
+__device__ __forceinline__ bool stall_requested(uint32_t cap) { return (cap & kStallFlag) != 0u; }
+
 __device__ __forceinline__ void mbar_arrive(uint32_t addr)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");

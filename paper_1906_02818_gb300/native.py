@@ -124,6 +124,19 @@ SIGNATURES = [
                                ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_surrogate_labels", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_moments", ctypes.c_int, [ctypes.POINTER(McResult), ctypes.c_int32, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_double)]),
+    ("mc_combine", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(McResult)]),
+    ("mc_tail", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(McRiskResult),
+                               ctypes.c_void_p]),
+    ("mc_mlp_loss_grad_sums", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_mlp_apply_grad_sums", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                                              ctypes.c_void_p]),
+    ("mc_philox_words", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_normals", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_price_gbm1d_noalloc", ctypes.c_int, [ctypes.POINTER(McModel), ctypes.POINTER(McSimCfg),
                                               ctypes.POINTER(McPayoff), ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p]),

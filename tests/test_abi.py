@@ -185,3 +185,42 @@ def test_correlation_sensitivity_checks(lib):
 
 def test_release_cache_without_work(lib):
     assert lib.mc_release_cache() == 0
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(T=float("inf")), "T must"),
+    (dict(s0=np.array([np.inf])), "s0[0]"),
+    (dict(sigma=np.array([np.inf])), "sigma[0]"),
+    (dict(payoffs=[dict(kind="call", strike=float("nan"))]), "strike"),
+    (dict(payoffs=[dict(kind="uo_call", strike=100.0, barrier=float("nan"))]), "barrier"),
+    (dict(weights=np.array([np.nan])), "weights"),
+    (dict(path_offset=(1 << 56) - 8), "path range"),
+    (dict(corr=np.array([[0.5]])), "corr"),
+    (dict(d=2), "single-asset"),
+])
+def test_noalloc_rejects_what_mc_price_rejects(lib, over, needle):
+    """The allocation-free pricer applies mc_price's argument checks (and
+    its own single-asset restriction) before any CUDA call."""
+    from paper_1906_02818_gb300 import native
+    mm = _structs(**over)
+    rc = lib.mc_price_gbm1d_noalloc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff,
+                                    ctypes.c_void_p(16), None)
+    assert rc == native.MC_EINVAL, (over, lib.mc_last_error())
+    assert needle in lib.mc_last_error().decode()
+    for n in (0, 33):
+        assert lib.mc_price_gbm1d_noalloc(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, n,
+                                          ctypes.c_void_p(16), None) == native.MC_EINVAL
+
+
+def test_rng_entry_points_check_arguments_on_host(lib):
+    from paper_1906_02818_gb300 import native
+    assert lib.mc_philox_words(42, 0, 0, 0, ctypes.c_void_p(16), None) == native.MC_OK  # empty: no launch
+    assert lib.mc_philox_words(42, 0, 0, 4, None, None) == native.MC_EINVAL
+    assert lib.mc_philox_words(42, 0, 0, 4, ctypes.c_void_p(20), None) == native.MC_EINVAL
+    assert b"aligned" in lib.mc_last_error()
+    assert lib.mc_philox_words(42, 0, 0, -1, ctypes.c_void_p(16), None) == native.MC_EINVAL
+    assert lib.mc_philox_words(42, 0, (1 << 64) - 2, 4, ctypes.c_void_p(16), None) == native.MC_EINVAL
+    assert b"wraps" in lib.mc_last_error()
+    assert lib.mc_normals(42, 0, 0, 0, ctypes.c_void_p(16), None) == native.MC_OK
+    assert lib.mc_normals(42, 0, (1 << 64) - 2, 4, ctypes.c_void_p(16), None) == native.MC_EINVAL
+    assert lib.mc_normals(42, 0, 0, 1 << 41, ctypes.c_void_p(16), None) == native.MC_EINVAL

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_util import REL, cfg_of, gbm_model, oracle_gbm
+from gpu_util import REL, assert_price_close, cfg_of, gbm_model, oracle_gbm
 from test_gpu_tc import emulate, flip_bound, payoffs_from_U
 
 pytestmark = pytest.mark.gpu
@@ -84,3 +84,110 @@ def test_d512_workload_full_shape(gb):
     # homogeneity of degree 1 in S0: sum_n S0_n dP/dS0_n = P + K e^{-rT} P(B > K)
     lhs = float(deltas @ w["s0"])
     assert lhs > bf[0][0]
+
+
+# ---------------------------------------------------------------------------
+# The d = 512 workload (16-factor market, ATM basket call) at its full
+# horizon of 252 steps.  One FP64 oracle run on the first 2^14 paths serves
+# both the 2^14-path accuracy check of every precision and, through its first
+# P_EXACT paths (16 tensor-core tiles of 128 paths and a ragged tail), the
+# exact checks.
+# ---------------------------------------------------------------------------
+N_SUBSET = 1 << 14
+P_EXACT = 2048 + 77
+
+
+@pytest.fixture(scope="module")
+def c5(orc):
+    w = workloads.basket_d512(paths=N_SUBSET)
+    b0 = w["payoffs"][0]["strike"]
+    pays = [w["payoffs"][0], dict(kind="put", strike=1.05 * b0)]
+    ref = oracle_gbm(orc, w, N_SUBSET, pays)  # [2, 2^14] discounted per-path payoffs
+    return w, pays, ref
+
+
+def flip_bound_terminal(aux, U, pays, r, T):
+    """flip_bound for European payoffs on U(T) under log-Euler with a fixed
+    operand scale: a code change of z_k at any step moves U(T) by at most
+    |D| |sum_n w_n S_n(T) sqrt(dt) sigma_n Lq[n, k]| (the same factor for
+    every step), so the per-path bound is that factor against the code
+    widths summed over the steps; O(paths d^2) instead of O(steps^2)."""
+    G = np.abs(np.einsum("pn,n,nk->pk", aux["S"][-1], aux["coef"], aux["Lq"]))
+    FT = np.einsum("pk,pk->p", aux["D"].sum(axis=1), G)
+    disc, N, uT = np.exp(-r * T), U.shape[1], U[-1]
+    out = []
+    for p in pays:
+        K = p["strike"]
+        active = (uT - K > -FT) if p["kind"] == "call" else (K - uT > -FT)
+        out.append(disc * float(np.sum(FT * active)) / N)
+    return out
+
+
+def test_d512_full_horizon_fp32_exact(gb, c5):
+    """FP32 (register-tiled SIMT contraction) against the FP64 oracle on the
+    identical stream: 1e-5 relative per price, standard errors 1e-3."""
+    w, pays, ref = c5
+    got = gb.price(gbm_model(w), cfg_of(w, paths=P_EXACT, precision="fp32"), pays)
+    assert_price_close(got, ref[:, :P_EXACT], pays, label="d512 fp32 252 steps")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_d512_full_horizon_tensor_cores_exact(gb, orc, c5, prec):
+    """The tensor-core kernel (TMEM accumulation over all 252 steps, the
+    factor ring wrapping every step) against the oracle's normals rounded as
+    the kernel rounds them, within 2e-5 relative plus the rounding-flip bound."""
+    w, pays, _ = c5
+    got = gb.price(gbm_model(w), cfg_of(w, paths=P_EXACT, precision=prec), pays)
+    want, fb = np.zeros(len(pays)), np.zeros(len(pays))
+    for off in range(0, P_EXACT, 128):
+        n = min(128, P_EXACT - off)
+        U, aux = emulate(orc, w, prec, n, w["steps"], path_offset=off, fp8_fixed=True, detail=True)
+        want += payoffs_from_U(U, pays, w["r"], w["T"]).sum(axis=1)
+        fb += np.array(flip_bound_terminal(aux, U, pays, w["r"], w["T"])) * n
+    want, fb = want / P_EXACT, fb / P_EXACT
+    for i, p in enumerate(pays):
+        print(f"d512 {prec} {p['kind']}: GPU {got[i][0]:.7f} emulation {want[i]:.7f} "
+              f"(|diff| {abs(got[i][0] - want[i]):.2e}, flip bound {fb[i]:.2e})")
+        assert abs(got[i][0] - want[i]) <= 2 * REL * abs(want[i]) + fb[i], (prec, p, got[i][0], want[i], fb[i])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_d512_subset_error_vs_fp64(gb, orc, c5, prec):
+    """The error of each precision against the unrounded FP64 oracle on the
+    first 2^14 paths of the workload (the same paths): printed per price, and
+    within 3 standard errors (FP32: within 1e-5 relative)."""
+    w, pays, ref = c5
+    got = gb.price(gbm_model(w), cfg_of(w, paths=N_SUBSET, precision=prec), pays)
+    for i, p in enumerate(pays):
+        m, se = orc.mean_se(ref[i])
+        err = got[i][0] - m
+        print(f"d512 {prec} {p['kind']} 2^14 paths x 252 steps: GPU {got[i][0]:.7f} FP64 {m:.7f} "
+              f"error {err:+.3e} ({abs(err) / abs(m):.2e} relative, {abs(err) / se:.3f} SE)")
+        assert abs(err) <= 3 * se
+        if prec == "fp32":
+            assert abs(err) <= REL * abs(m)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_d512_full_horizon_greek_vectors(gb, orc, c5, prec):
+    """The 512 deltas, 512 vegas and rho of the basket call from mc_greeks
+    against the oracle's forward-mode pathwise tangents on the same P_EXACT
+    paths, entry by entry.  The scale of an entry is the largest of its
+    mean, the largest mean delta and its mean absolute per-path term (many
+    vegas are means of large terms of both signs that nearly cancel, and the
+    FP32 error of a mean follows its terms, not the mean); FP32 within 2e-5
+    of that scale, BF16 within 3 SE + 3e-3 of it."""
+    w, pays, _ = c5
+    pr, g = gb.greeks(gbm_model(w), cfg_of(w, paths=P_EXACT, precision=prec), pays[:1])
+    ref = orc.gbm_greeks(w["s0"], w["sigma"], w["r"], w["T"], w["steps"], P_EXACT, pays[:1], corr=w["corr"],
+                         weights=w["weights"])[0]
+    d = len(w["s0"])
+    scale = np.max(np.abs(ref.mean(axis=1)[:d]))
+    worst = 0.0
+    for k in range(2 * d + 1):
+        m, se = orc.mean_se(ref[k])
+        sc = max(abs(m), scale, float(np.mean(np.abs(ref[k]))))
+        tol = 2e-5 * sc if prec == "fp32" else 3 * se + 3e-3 * sc
+        worst = max(worst, abs(g[0, k, 0] - m) / tol)
+        assert abs(g[0, k, 0] - m) <= tol, (prec, k, g[0, k, 0], m, se)
+    print(f"d512 {prec} Greeks: largest |GPU - oracle| / tolerance over the {2 * d + 1} entries {worst:.3f}")

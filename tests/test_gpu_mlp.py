@@ -191,6 +191,36 @@ def test_apply_grad_is_one_training_step(gb):
     b.close()
 
 
+@pytest.mark.parametrize("mode", ["fp32", "tf32x3"])
+def test_device_sums_equal_the_host_path(gb, mode):
+    """The data-parallel building blocks on the device: two part-batch
+    gradient sums (mc_mlp_loss_grad_sums) add up to n times the full batch's
+    mean gradient and MSE (mc_mlp_loss_grad), and a summed gradient applied
+    with scale 1/n (mc_mlp_apply_grad_sums) is the host path's Adam step
+    (mc_mlp_apply_grad), three steps in a row."""
+    import torch
+    init = workloads.mlp_init(seed=13)
+    a, b = gb.Mlp(5, 256, 4, init), gb.Mlp(5, 256, 4, init)
+    a.set_train_mode(mode)
+    b.set_train_mode(mode)
+    x, t = _data(2048, seed=8)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    for step in range(3):
+        loss, g = a.loss_grad(xd, td)
+        # split batch: the summed halves reproduce the full batch's mean
+        tot = b.loss_grad_sums(xd[:1000], td[:1000]) + b.loss_grad_sums(xd[1000:], td[1000:])
+        assert abs(float(tot[-1]) / 2048 - loss) <= 1e-5 * loss, (step, float(tot[-1]) / 2048, loss)
+        gd = tot[:-1].cpu().numpy() / 2048
+        assert np.max(np.abs(gd - g)) <= 2e-5 * np.max(np.abs(g)), step
+        # the update: the full batch's sums scaled by 1 / n, as the host step
+        a.apply_grad(g, 1e-3)
+        b.apply_grad_sums(b.loss_grad_sums(xd, td), 1.0 / 2048, 1e-3)
+    pa, pb = a.params(), b.params()
+    assert np.max(np.abs(pa - pb)) <= 1e-6 * max(1.0, np.max(np.abs(pa)))
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("n", [130, 777, 4096])
 def test_tf32x3_loss_and_gradient_match_oracle(gb, n):
     """Tensor-core training products (three-pass TF32, FP32 accumulation)

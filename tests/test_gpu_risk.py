@@ -148,3 +148,18 @@ def test_scenario_shards_reproduce_the_full_run(gb, trained):
         assert np.array_equal(pnl, full["pnl"]), kw["method"]
         var, cvar, nt = shard.tail_statistics(pnl, 0.97)
         assert var == full["var"] and nt == full["n_tail"] and abs(cvar - full["cvar"]) <= 1e-12 * abs(cvar)
+
+
+def test_device_tail_selection_matches_oracle_rule(gb):
+    """mc_tail (the device VaR / CVaR selection used by mc_risk and by the
+    sharded risk path) against the oracle's rule, with ties on purpose and
+    sizes that are not powers of two."""
+    import torch
+    from oracle import risk as orisk
+    rng = np.random.default_rng(1)
+    for n, alpha in [(1, 0.99), (3, 0.5), (1000, 0.99), (4096, 0.95), (65536, 0.99), (100_003, 0.975)]:
+        pnl = np.round(rng.standard_normal(n) * 10.0, 1)
+        got = gb.tail(torch.from_numpy(pnl).cuda(), alpha)
+        var, cvar, nt = orisk.var_cvar(pnl, alpha)
+        assert got["var"] == var and got["n_tail"] == nt, (n, alpha, got, var, nt)
+        assert abs(got["cvar"] - cvar) <= 1e-12 * max(1.0, abs(cvar))

@@ -60,3 +60,25 @@ def test_two_rank_gloo_combine_equals_single_run(orc):
         for r in range(2):
             assert abs(got[r][i][0] - m) <= 1e-12 * abs(m)
             assert abs(got[r][i][1] - se) <= 1e-9 * se
+
+
+def test_moments_and_combine_through_the_library(orc):
+    """mc_moments / mc_combine (host code of the library, no device): three
+    disjoint path ranges of one stream combine into the single-range
+    estimator and standard error; non-finite input is rejected."""
+    from paper_1906_02818_gb300 import api, native
+    pays = [dict(kind="call", strike=100.0), dict(kind="put", strike=90.0)]
+    cuts = [0, 1, 4000, 10_001]
+    tot = np.zeros((len(pays), 3))
+    for a, b in zip(cuts, cuts[1:]):
+        per = orc.gbm_payoffs(100.0, 0.25, 0.05, 1.0, 16, b - a, pays, path_offset=a)
+        tot += api.moments([orc.mean_se(row) for row in per], b - a)
+    got = api.combine(tot)
+    full = orc.gbm_payoffs(100.0, 0.25, 0.05, 1.0, 16, 10_001, pays)
+    for i in range(len(pays)):
+        m, se = orc.mean_se(full[i])
+        assert abs(got[i][0] - m) <= 1e-12 * abs(m) and abs(got[i][1] - se) <= 1e-9 * se
+    with pytest.raises(native.MCError):
+        api.moments([(float("nan"), 1.0)], 10)
+    with pytest.raises(native.MCError):
+        api.combine(np.array([[1.0, 2.0, 0.0]]))

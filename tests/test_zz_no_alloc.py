@@ -2,7 +2,9 @@
 callers that cannot call cudaMalloc: through the C ABI it must reproduce the
 regular entry point (mc_price) within the pricing tolerance, on two calls in
 a row (the second call reuses the library's fixed scratch array left behind
-by the first).  This file is collected last on purpose."""
+by the first), and the second call, small enough for the FP64 oracle, must
+also match the oracle on the same random stream.  This file is collected
+last on purpose."""
 import ctypes
 
 import numpy as np
@@ -35,6 +37,24 @@ def test_noalloc_matches_mc_price_twice():
         for i in range(len(pays)):
             assert abs(got[i, 0] - want[i][0]) <= REL * abs(want[i][0]), (run, pays[i], got[i], want[i])
             assert abs(got[i, 1] - want[i][1]) <= 1e-3 * want[i][1]
+        if cfg["paths"] <= 8192:
+            # independent of both launch paths: the FP64 oracle on the same
+            # path range (path_offset 123); the barrier payoff may differ by
+            # the paths whose monitored maximum lies within 2e-5 of H
+            import oracle
+            ref = oracle.gbm_payoffs(100.0, 0.25, 0.05, cfg["T"], cfg["steps"], cfg["paths"], pays,
+                                     seed=cfg["seed"], path_offset=cfg["path_offset"])
+            for i, pay in enumerate(pays):
+                m, se = oracle.mean_se(ref[i])
+                tol = REL * abs(m)
+                if pay["kind"] == "uo_call":
+                    near = oracle.gbm_payoffs(100.0, 0.25, 0.05, cfg["T"], cfg["steps"], cfg["paths"],
+                                              [dict(pay, barrier=pay["barrier"] * (1 - 2e-5)),
+                                               dict(pay, barrier=pay["barrier"] * (1 + 2e-5))],
+                                              seed=cfg["seed"], path_offset=cfg["path_offset"])
+                    tol += float(np.abs(near[1] - near[0]).sum()) / cfg["paths"]
+                assert abs(got[i, 0] - m) <= tol, (pay, got[i, 0], m)
+                assert abs(got[i, 1] - se) <= 1e-3 * se
 
 
 def test_noalloc_rejects_out_of_range():
