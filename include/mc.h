@@ -39,7 +39,9 @@ extern "C" {
 typedef enum {
     MC_OK = 0,
     MC_EINVAL = -1,        /* an argument is out of range or inconsistent */
-    MC_ENOTPSD = -2,       /* the correlation matrix is not positive definite */
+    MC_ENOTPSD = -2,       /* the correlation matrix is not positive definite: a pivot of
+                              its FP64 Cholesky factorisation is at or below 4 d 2^-52 times
+                              its diagonal entry (rank-deficient or numerically singular) */
     MC_ENOMEM = -3,        /* device or host allocation failed */
     MC_ECUDA = -4,         /* a CUDA runtime call failed (message has the name) */
     MC_ETIMEOUT = -5,      /* a bounded device wait ran out */

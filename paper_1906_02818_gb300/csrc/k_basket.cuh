@@ -25,7 +25,7 @@ struct Stats {
     __device__ __forceinline__ void add(float u) { sum += u; umax = fmaxf(umax, u); umin = fminf(umin, u); }
 };
 
-__device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet &pay, bool valid,
+__device__ __forceinline__ void accumulate_payoffs(AccSlot *s_acc, const PayoffSet &pay, bool valid,
                                                    float uT, float avg, const Stats &st)
 {
     for (int p = 0; p < pay.n; ++p) {
@@ -38,7 +38,7 @@ __device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet
 template <int D, int SCHEME, bool STATS, bool SAVE, bool EXACT>
 __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_constant__ BasketArgs a, const BasketConst<D> c)
 {
-    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     for (int i = threadIdx.x; i < (kBlock / 32) * a.pay.n * 2; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) basket_tc_kernel(const __grid_consta
 {
     using Ly = Layout<PREC>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ float s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
 
     const int t = threadIdx.x, warp = t >> 5;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
 {
     using Ly = Layout<PREC>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ float s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     // per-asset terms of the step s being observed, double-buffered by the
     // parity of s (written before the step's barrier, read after it):

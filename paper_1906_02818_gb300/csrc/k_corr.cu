@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) corr_path_kernel(const __grid_consta
     __shared__ __align__(16) float sw[kQuarter * kStride];   // W of the staged paths
     __shared__ float s_slope[kQuarter];
     __shared__ float sh[32 * kThreads];                       // this CTA's H, thread t owns column t
-    __shared__ float s_acc[(kThreads / 32) * 2];
+    __shared__ AccSlot s_acc[(kThreads / 32) * 2];
     __shared__ double s_red[32];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant
     float *sDr = sE + dp;             // drift
     float *sWs = sDr + dp;            // w S0 (log-Euler U) or w (Euler U)
     float *sPart = sWs + dp;          // [kWarps][kP] partial U of each warp
-    __shared__ float s_acc[kWarps * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[kWarps * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;

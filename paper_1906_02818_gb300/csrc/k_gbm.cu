@@ -19,7 +19,7 @@ struct Stats {
     __device__ __forceinline__ void add(float u) { sum += u; umax = fmaxf(umax, u); umin = fminf(umin, u); }
 };
 
-__device__ __forceinline__ void accumulate_payoffs(float *s_acc, const PayoffSet &pay, bool valid,
+__device__ __forceinline__ void accumulate_payoffs(AccSlot *s_acc, const PayoffSet &pay, bool valid,
                                                    float uT, float avg, const Stats &st)
 {
     for (int p = 0; p < pay.n; ++p) {
@@ -51,7 +51,7 @@ constexpr uint64_t kBridgeDomain = uint64_t(1) << 56;  // stream of path n's bri
 template <int SCHEME, bool STATS, bool SAVE, bool BRIDGE>
 __global__ void __launch_bounds__(kBlock, 8) gbm1d_kernel(const __grid_constant__ Gbm1dArgs a)
 {
-    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     for (int i = threadIdx.x; i < (kBlock / 32) * a.pay.n * 2; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();

@@ -40,7 +40,7 @@ __device__ __forceinline__ float slope_of(int kind, float K, float uT, float avg
 __device__ __forceinline__ bool is_asian(int kind) { return kind == MC_ASIAN_CALL || kind == MC_ASIAN_PUT; }
 
 template <int NG>
-__device__ __forceinline__ void accumulate_greeks(float *s_acc, const PayoffSet &pay, bool valid, float uT,
+__device__ __forceinline__ void accumulate_greeks(AccSlot *s_acc, const PayoffSet &pay, bool valid, float uT,
                                                   float avg, const float (&dE)[NG], const float (&dA)[NG],
                                                   int rho_slot, float T)
 {
@@ -62,7 +62,7 @@ __device__ __forceinline__ void accumulate_greeks(float *s_acc, const PayoffSet 
 // ------------------------------ 1-D GBM ----------------------------------
 __global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const __grid_constant__ GreeksArgs a)
 {
-    extern __shared__ float s_acc[];
+    extern __shared__ AccSlot s_acc[];
     __shared__ double s_red[32];
     const int nv = a.pay.n * 4;
     for (int i = threadIdx.x; i < (kBlock / 32) * nv * 2; i += blockDim.x) s_acc[i] = 0.0f;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) gbm1d_greeks_kernel(const __grid_const
 // Greek order: 0 S0, 1 v0, 2 r, 3 kappa, 4 theta, 5 xi, 6 rho.
 __global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const __grid_constant__ GreeksArgs a)
 {
-    extern __shared__ float s_acc[];
+    extern __shared__ AccSlot s_acc[];
     __shared__ double s_red[32];
     const int nv = a.pay.n * 8;
     for (int i = threadIdx.x; i < (kBlock / 32) * nv * 2; i += blockDim.x) s_acc[i] = 0.0f;
@@ -223,7 +223,7 @@ const void *greeks_kernel(int model) {
 size_t greeks_smem(int model, int n_payoff)
 {
     const int per = model == MC_HESTON ? 8 : 4;
-    return static_cast<size_t>(kBlock / 32) * n_payoff * per * 2 * sizeof(float);
+    return static_cast<size_t>(kBlock / 32) * n_payoff * per * 2 * sizeof(AccSlot);
 }
 
 int greeks_block() { return kBlock; }

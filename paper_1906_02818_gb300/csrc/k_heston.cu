@@ -15,7 +15,7 @@ constexpr int kBlock = 256;
 template <bool STATS, bool SAVE>
 __global__ void __launch_bounds__(kBlock) heston_kernel(const __grid_constant__ HestonArgs a)
 {
-    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     for (int i = threadIdx.x; i < (kBlock / 32) * a.pay.n * 2; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();

@@ -24,9 +24,21 @@ __device__ __forceinline__ double rsqrt_refined(double p)
     return r;
 }
 
+// A pivot at or below kPivotTol A_kk is taken as zero: the matrix is
+// rejected as not positive definite.  4 d eps (eps = 2^-52) is a few times the
+// rounding a pivot collects over its d updates, so a semi-definite
+// (rank-deficient) matrix is rejected whatever that rounding gives, while a
+// positive definite one passes unless its conditional variance falls below
+// ~1e-13 of its variance (a factor that small, 3e-7, is below FP32 paths'
+// resolution anyway).
+__device__ __forceinline__ bool pivot_ok(double p, double akk, int d)
+{
+    return p > 4.0 * d * 2.220446049250313e-16 * akk;
+}
+
 // Right-looking Cholesky, one CTA, in place on W (initialised with A); each
 // column is scaled by its pivot's reciprocal square root (rsqrt_refined).
-// status: 0 ok, 1 a pivot was not positive (A not positive definite).
+// status: 0 ok, 1 a pivot failed pivot_ok (A not positive definite).
 __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const double *A, double *W, int *status)
 {
     __shared__ int s_fail;
@@ -37,7 +49,7 @@ __global__ void __launch_bounds__(kCholBlock) cholesky_kernel(int d, const doubl
     for (int k = 0; k < d; ++k) {
         if (threadIdx.x == 0) {
             const double p = W[static_cast<int64_t>(k) * d + k];
-            if (!(p > 0.0)) {
+            if (!pivot_ok(p, A[static_cast<int64_t>(k) * d + k], d)) {
                 s_fail = 1;
             } else {
                 const double r = rsqrt_refined(p);
@@ -96,7 +108,7 @@ __global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, 
     if (t == 0) {
         s_fail = 0;
         const double p = d > 0 ? A[0] : 1.0;
-        if (!(p > 0.0)) {
+        if (!pivot_ok(p, p, d)) {
             s_fail = 1;
         } else {
             const double r = rsqrt_refined(p);
@@ -120,7 +132,7 @@ __global__ void __launch_bounds__(kCholSmallBlock) cholesky_small_kernel(int d, 
         // entry 0 is (k + 1, k + 1), updated above by this same thread
         if (t == 0 && k + 1 < d) {
             const double p = W[k + 1][k + 1];
-            if (!(p > 0.0)) {
+            if (!pivot_ok(p, A[(k + 1) * d + (k + 1)], d)) {
                 s_fail = 1;
             } else {
                 const double r = rsqrt_refined(p);

@@ -104,7 +104,7 @@ __device__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n)
 template <int PREC, int SCHEME, bool STATS>
 __global__ void __launch_bounds__(kBlock) mlmc_coupled_kernel(const __grid_constant__ MlmcArgs a, const MlmcConst c)
 {
-    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     const int np = a.pay.n, nv = 3 * np;
     for (int i = threadIdx.x; i < (kBlock / 32) * nv * 2; i += blockDim.x) s_acc[i] = 0.0f;

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kBlock) qmc_kernel(const __grid_constant__ Qmc
 {
     __shared__ uint32_t s_v[kQmcMaxDims][32];
     __shared__ uint32_t s_shift[kQmcMaxDims];
-    __shared__ float s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
+    __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     const int t = threadIdx.x, nd = a.ndim, np = a.pay.n;
     const int64_t rep = blockIdx.y;
     for (int i = t; i < nd * 32; i += kBlock) s_v[i / 32][i % 32] = c.V[i / 32][i % 32];

@@ -922,7 +922,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     if (m->kind == MC_HESTON && (K < 1 || K > 64)) return fail(MC_EINVAL, "ckpt_every = %d outside [1, 64]", K);
     const int G = mc_greek_count(m);
     const int nv = np * (G + 1);
-    if (nv * 2 * 4 * 4 > 48 * 1024) return fail(MC_EINVAL, "too many payoffs for one Greeks launch");
+    if (nv * 2 * 4 * static_cast<int>(sizeof(AccSlot)) > 48 * 1024) return fail(MC_EINVAL, "too many payoffs for one Greeks launch");
     DeviceInfo di;
     if ((rc = device_info(&di))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -178,14 +178,30 @@ __device__ __forceinline__ float payoff_eval(int kind, float K, float H, float u
 
 // ---------------------------------------------------------------------------
 // Reduction.  Each warp owns a slot per payoff in shared memory; after every
-// grid-stride iteration the warp's 32 payoffs (and squares) are summed with
-// shuffles and lane 0 adds them to its slot (fixed order: deterministic).  At
-// block end the warp slots are summed into one FP32 (sum f, sum f^2) pair per
-// payoff and written to the block's partials.  The last block to finish
-// (atomic ticket, no spin-wait) sums all block partials in FP64, forms mean
-// and standard error, discounts and writes the results, then resets the
-// ticket for the next launch.
+// grid-stride iteration the warp's 32 payoffs (and squares) are summed in
+// FP32 with shuffles and lane 0 adds them to its FP64 slot (fixed order:
+// deterministic; FP64 so that a slot's error does not grow with the paths
+// per thread).  At block end the warp slots are summed into one (sum f,
+// sum f^2) pair per payoff, written to the block's partials in FP32.  The
+// last block to finish (atomic ticket, no spin-wait) adds all block partials
+// with compensated (Kahan) FP64 sums, forms mean and standard error,
+// discounts and writes the results, then resets the ticket for the next
+// launch.
 // ---------------------------------------------------------------------------
+using AccSlot = double;  // per-warp payoff slot in shared memory
+
+// Compensated summation (Kahan): s + c carries the sum to about one FP64
+// rounding whatever the number of terms.
+struct KahanSum {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double x)
+    {
+        const double y = x - c;
+        const double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
 struct ReduceArgs {
     float *partials;        // [gridDim.x][n_payoff][2]
     unsigned int *ticket;   // zero on entry to the launch, reset by the last block
@@ -210,26 +226,26 @@ __device__ __forceinline__ double warp_sum_d(double v)
 }
 
 // Adds this warp's 32 payoff values to s_acc[warp][p][*].
-__device__ __forceinline__ void warp_accumulate(float *s_acc, int np, int p, float f)
+__device__ __forceinline__ void warp_accumulate(AccSlot *s_acc, int np, int p, float f)
 {
     const float a = warp_sum(f), b = warp_sum(f * f);
     if ((threadIdx.x & 31) == 0) {
-        float *slot = s_acc + ((threadIdx.x >> 5) * np + p) * 2;
-        slot[0] += a;
-        slot[1] += b;
+        AccSlot *slot = s_acc + ((threadIdx.x >> 5) * np + p) * 2;
+        slot[0] += static_cast<double>(a);
+        slot[1] += static_cast<double>(b);
     }
 }
 
 // Called by every thread of the block after its last path.  s_acc holds
-// nwarps*np*2 floats; s_red is scratch for 32 doubles.
-__device__ inline void block_finish(float *s_acc, double *s_red, int np, const ReduceArgs &ra)
+// nwarps*np*2 slots; s_red is scratch for 32 doubles.
+__device__ inline void block_finish(AccSlot *s_acc, double *s_red, int np, const ReduceArgs &ra)
 {
     const int nwarps = blockDim.x >> 5;
     __syncthreads();
     for (int i = threadIdx.x; i < np * 2; i += blockDim.x) {
-        float s = 0.0f;
+        double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += s_acc[w * np * 2 + i];
-        ra.partials[static_cast<size_t>(blockIdx.x) * np * 2 + i] = s;
+        ra.partials[static_cast<size_t>(blockIdx.x) * np * 2 + i] = static_cast<float>(s);
     }
     __threadfence();
     __syncthreads();
@@ -249,22 +265,26 @@ __device__ inline void block_finish(float *s_acc, double *s_red, int np, const R
     const int first = wide ? static_cast<int>(threadIdx.x) : warp;
     const int stride = wide ? static_cast<int>(blockDim.x) : nwarps;
     for (int p = first; p < np; p += stride) {
-        double t0 = 0.0, t1 = 0.0;
+        KahanSum k0, k1;
+        double t0, t1;
         if (wide) {
 #pragma unroll 4
             for (int b = 0; b < nb; ++b) {
                 const float2 q = *reinterpret_cast<const float2 *>(ra.partials + static_cast<size_t>(b) * np * 2 + p * 2);
-                t0 += static_cast<double>(q.x);
-                t1 += static_cast<double>(q.y);
+                k0.add(static_cast<double>(q.x));
+                k1.add(static_cast<double>(q.y));
             }
+            t0 = k0.s;
+            t1 = k1.s;
         } else {
             for (int b = lane; b < nb; b += 32) {
                 const float *q = ra.partials + static_cast<size_t>(b) * np * 2 + p * 2;
-                t0 += static_cast<double>(q[0]);
-                t1 += static_cast<double>(q[1]);
+                k0.add(static_cast<double>(q[0]));
+                k1.add(static_cast<double>(q[1]));
             }
-            t0 = warp_sum_d(t0);
-            t1 = warp_sum_d(t1);
+            // the 32 lanes' compensated sums, then a pairwise (shuffle tree) sum
+            t0 = warp_sum_d(k0.s - k0.c);
+            t1 = warp_sum_d(k1.s - k1.c);
         }
         if (wide || lane == 0) {
             const bool bad = ra.err && *reinterpret_cast<const volatile unsigned int *>(ra.err) != 0u;

@@ -111,3 +111,40 @@ def test_indefinite_correlation_is_reported(gb, d):
     valid = np.where(np.eye(d) > 0, 1.0, np.where(corr != 0, 0.5, 0.0))
     got = gb.price(dict(model, corr=valid), dict(steps=4, T=1.0, paths=256), pays)
     assert got[0][0] > 0 and np.isfinite(got[0][1])
+
+
+@pytest.mark.parametrize("d", [2, 16, 100])
+def test_rank_deficient_correlation_threshold(gb, d):
+    """Semi-definite (rank-deficient) correlations are rejected by the pivot
+    threshold of the device Cholesky (a pivot at or below 4 d 2^-52 of its
+    diagonal entry), not by how one rounding falls: d = 2 with correlation 1
+    and 1 - 2^-53 (pivots 0 and ~2e-16, far below the threshold), and a
+    rank-4 factor correlation for d = 16 and 100 (pivots from the fifth on
+    are rounding noise).  Nearly singular but positive definite matrices
+    (d = 2 at 1 - 1e-12, pivot 2e-12; the rank-4 correlation plus 1e-9 I)
+    are accepted and priced."""
+    from paper_1906_02818_gb300 import native
+    pays = [dict(kind="call", strike=100.0)]
+    model = dict(kind="gbm", s0=np.full(d, 100.0), sigma=np.full(d, 0.2), r=0.05)
+    if d == 2:
+        bad = [np.array([[1.0, c], [c, 1.0]]) for c in (1.0, 1.0 - 2.0 ** -53)]
+        good = [np.array([[1.0, 1.0 - 1e-12], [1.0 - 1e-12, 1.0]])]
+    else:
+        F = np.random.default_rng(d).standard_normal((d, 4))
+        C = F @ F.T
+        C = C / np.sqrt(np.outer(np.diag(C), np.diag(C)))
+        np.fill_diagonal(C, 1.0)
+        C = 0.5 * (C + C.T)
+        bad = [C]
+        G = C + 1e-9 * np.eye(d)
+        G = G / np.sqrt(np.outer(np.diag(G), np.diag(G)))
+        np.fill_diagonal(G, 1.0)
+        good = [0.5 * (G + G.T)]
+    for corr in bad:
+        for prec in ("fp32", "bf16"):
+            with pytest.raises(native.MCError) as e:
+                gb.price(dict(model, corr=corr), dict(steps=4, T=1.0, paths=256, precision=prec), pays)
+            assert e.value.status == native.MC_ENOTPSD
+    for corr in good:
+        got = gb.price(dict(model, corr=corr), dict(steps=4, T=1.0, paths=256), pays)
+        assert got[0][0] > 0 and np.isfinite(got[0][1])
