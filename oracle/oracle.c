@@ -997,6 +997,57 @@ int orc_risk_values(int d, const double *state, const double *sig, double r, dou
 /* Surrogate label of point p = (S/K, sig, tau, r, K/H): discounted Monte Carlo
  * call price / K (up-and-out with H = K / (K/H) when K/H > 0), `paths` paths
  * of streams tag(4, (p << 16) | path), round(tau * spy) steps. */
+/* Pathwise Greeks of the surrogate's European labels (Sec. I.A.3: the
+ * derivative of each simulated payoff with respect to the inputs, averaged
+ * over the paths).  Point (S/K, sigma, tau, r, K/H) with K/H = 0; the same
+ * paths as orc_surrogate_labels (log-Euler in ln S, round(tau spy) steps,
+ * stream tag(4, p << 16 | path)).  Per path, with f = e^{-r tau} (S_T - 1)^+
+ * in units of K and ln S_T = ln S + (r - sigma^2/2) tau + sigma sqrt(dt) sum z:
+ *   df/dS     = e^{-r tau} 1{S_T > 1} S_T / S
+ *   df/dsigma = e^{-r tau} 1{S_T > 1} S_T (sqrt(dt) sum z - sigma tau).
+ * out[p][0..5] = mean and standard error (Eq. 3) of f, df/dS, df/dsigma;
+ * all NaN for barrier points (K/H > 0: a knock-out has no pathwise Greek). */
+int orc_surrogate_label_greeks(int64_t npts, const double *pts, int paths, int spy, uint64_t seed, double *out)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t p = 0; p < npts; ++p) {
+        const double *q = pts + 5 * p;
+        double *o = out + 6 * p;
+        if (q[4] > 0.0) {
+            for (int k = 0; k < 6; ++k) o[k] = NAN;
+            continue;
+        }
+        const double S = q[0], sig = q[1], r = q[3];
+        int M = (int)lround(q[2] * spy);
+        if (M < 1) M = 1;
+        const double dt = q[2] / M, tau = M * dt, disc = exp(-r * tau);
+        double s[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+        for (int n = 0; n < paths; ++n) {
+            orc_stream st;
+            stream_init(&st, seed, domain_tag(4, ((uint64_t)p << 16) | (uint64_t)n));
+            double x = log(S), zs = 0.0;
+            for (int i = 0; i < M; ++i) {
+                const double z = stream_normal(&st, (uint64_t)i);
+                x += (r - 0.5 * sig * sig) * dt + sig * sqrt(dt) * z;
+                zs += z;
+            }
+            const double ST = exp(x), in = ST > 1.0 ? 1.0 : 0.0;
+            const double v[3] = {disc * (ST > 1.0 ? ST - 1.0 : 0.0), disc * in * ST / S,
+                                 disc * in * ST * (sqrt(dt) * zs - sig * tau)};
+            for (int k = 0; k < 3; ++k) {
+                s[k] += v[k];
+                s2[k] += v[k] * v[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double m = s[k] / paths, var = s2[k] / paths - m * m;
+            o[2 * k] = m;
+            o[2 * k + 1] = paths > 1 ? sqrt(var > 0.0 ? var / (paths - 1) : 0.0) : 0.0;
+        }
+    }
+    return 0;
+}
+
 int orc_surrogate_labels(int64_t npts, const double *pts, int paths, int spy, uint64_t seed, double *labels)
 {
 #pragma omp parallel for schedule(dynamic)

@@ -66,3 +66,16 @@ def labels(points, paths, spy=252, seed=42):
                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
     lib.orc_surrogate_labels(pts.shape[0], _dptr(pts), paths, spy, seed, _dptr(out))
     return out
+
+
+def label_greeks(points, paths, spy=252, seed=42):
+    """Pathwise price, delta (d/d S/K) and vega (d/d sigma) of the European
+    training points, each (mean, se): shape [n, 6]; NaN rows for barrier
+    points (orc_surrogate_label_greeks)."""
+    lib = _load()
+    pts = _f64(points).reshape(-1, 5)
+    out = np.empty((pts.shape[0], 6))
+    lib.orc_surrogate_label_greeks.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+    lib.orc_surrogate_label_greeks(pts.shape[0], _dptr(pts), paths, spy, seed, _dptr(out))
+    return out

@@ -55,3 +55,66 @@ def test_pack_roundtrip():
     Q = mlp.unpack(mlp.pack(P), sizes)
     assert all(np.array_equal(a, c) and np.array_equal(b, d) for (a, b), (c, d) in zip(P, Q))
     assert mlp.pack(P).size == 5 * 16 + 16 + 3 * (16 * 16 + 16) + 16 + 1
+
+
+def test_silu_second_derivative_matches_difference():
+    z = np.linspace(-8, 8, 101)
+    h = 1e-5
+    assert np.allclose(mlp.silu_grad2(z), (mlp.silu_grad(z + h) - mlp.silu_grad(z - h)) / (2 * h), rtol=1e-7,
+                       atol=1e-9)
+
+
+def test_input_grads_match_finite_differences():
+    rng = np.random.default_rng(6)
+    sizes = mlp.layer_sizes(5, 9, 3)
+    P = _params(sizes, rng)
+    x = rng.standard_normal((13, 5))
+    dirs = [0, 1, 4]
+    got = mlp.input_grads(P, x, dirs)
+    h = 1e-6
+    for k, j in enumerate(dirs):
+        up, dn = x.copy(), x.copy()
+        up[:, j] += h
+        dn[:, j] -= h
+        fd = (mlp.forward(P, up)[0] - mlp.forward(P, dn)[0]) / (2 * h)
+        assert np.allclose(got[:, k], fd, rtol=1e-7, atol=1e-9)
+
+
+def test_derivative_loss_gradient_matches_finite_differences():
+    """Every part of the derivative-label loss: masked labels (NaN) included,
+    unequal weights, directions not in input order."""
+    rng = np.random.default_rng(7)
+    sizes = mlp.layer_sizes(5, 7, 3)
+    P = _params(sizes, rng)
+    x = rng.standard_normal((12, 5))
+    t = rng.standard_normal(12)
+    dirs, lams = [1, 0], [0.7, 2.5]
+    g = rng.standard_normal((12, 2))
+    g[3, 0] = g[7, 1] = g[9, :] = np.nan
+    loss, parts, grads = mlp.dloss_and_grads(P, x, t, g, dirs, lams)
+    dy = mlp.input_grads(P, x, dirs)
+    y = mlp.forward(P, x)[0]
+    ok = np.isfinite(g)
+    want = [np.mean((y - t) ** 2)] + [lams[k] * np.mean(np.where(ok[:, k], dy[:, k] - np.nan_to_num(g[:, k]), 0) ** 2)
+                                      for k in range(2)]
+    assert np.allclose(parts, want, rtol=1e-12) and abs(loss - sum(want)) <= 1e-12 * abs(loss)
+    flat, gf = mlp.pack(P), mlp.pack(grads)
+    h = 1e-6
+    for i in rng.choice(flat.size, 80, replace=False):
+        up, dn = flat.copy(), flat.copy()
+        up[i] += h
+        dn[i] -= h
+        fd = (mlp.dloss_and_grads(mlp.unpack(up, sizes), x, t, g, dirs, lams)[0] -
+              mlp.dloss_and_grads(mlp.unpack(dn, sizes), x, t, g, dirs, lams)[0]) / (2 * h)
+        assert abs(fd - gf[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, gf[i])
+
+
+def test_derivative_loss_without_weights_is_the_plain_loss():
+    rng = np.random.default_rng(8)
+    sizes = mlp.layer_sizes(5, 6, 2)
+    P = _params(sizes, rng)
+    x, t = rng.standard_normal((9, 5)), rng.standard_normal(9)
+    a, _, ga = mlp.dloss_and_grads(P, x, t, rng.standard_normal((9, 2)), [0, 1], [0.0, 0.0])
+    b, gb = mlp.loss_and_grads(P, x, t)
+    assert abs(a - b) <= 1e-14 * b
+    assert np.allclose(mlp.pack(ga), mlp.pack(gb), rtol=1e-12, atol=1e-15)

@@ -91,3 +91,35 @@ def test_european_portfolio_nested_matches_exact_revaluation(orc):
         Vx = exact(S[s], rem / 252)
         # inner SE of each value <= 0.6 here; positions +-1, 32 options
         assert abs(pf["position"] @ (V - Vx)) < 3 * 0.6 * math.sqrt(32)
+
+
+def test_label_greeks_pins():
+    """The oracle's pathwise label Greeks (orc_surrogate_label_greeks): the
+    price column is the label oracle's own value on the same paths; delta
+    (d/d S/K) and vega (d/d sigma) of the European points match the
+    Black-Scholes closed forms within 4 standard errors (log-Euler is exact in
+    law) and the central common-random-number differences of the oracle's own
+    labels; barrier points carry NaN."""
+    pts = np.array([[1.0, 0.2, 1.0, 0.05, 0.0], [0.8, 0.35, 0.5, 0.02, 0.0], [1.3, 0.15, 63 / 252, 0.07, 0.0],
+                    [1.1, 0.25, 2.0, 0.0, 0.0], [1.0, 0.3, 1.0, 0.04, 0.8]])
+    paths = 1 << 14
+    out = risk.label_greeks(pts, paths)
+    lab = risk.labels(pts, paths)
+    assert np.all(np.isnan(out[4])) and np.all(np.isfinite(out[:4]))
+    for p in range(4):
+        sk, sig, tau, r, _ = pts[p]
+        assert abs(out[p, 0] - lab[p]) <= 1e-12 * abs(lab[p])
+        M = max(1, round(tau * 252))
+        T = M * (tau / M)
+        d1 = (math.log(sk) + (r + 0.5 * sig * sig) * T) / (sig * math.sqrt(T))
+        delta, vega = cf.ncdf(d1), sk * cf.npdf(d1) * math.sqrt(T)
+        assert abs(out[p, 2] - delta) <= 4 * out[p, 3], (p, out[p, 2], delta, out[p, 3])
+        assert abs(out[p, 4] - vega) <= 4 * out[p, 5], (p, out[p, 4], vega, out[p, 5])
+        # central differences of the same-stream label (h relative 1e-5)
+        for col, k in ((2, 0), (4, 1)):
+            h = 1e-5 * pts[p, k]
+            up, dn = pts.copy(), pts.copy()  # point p keeps its own stream (tag 4, p << 16 | path)
+            up[p, k] += h
+            dn[p, k] -= h
+            fd = (risk.labels(up, paths)[p] - risk.labels(dn, paths)[p]) / (2 * h)
+            assert abs(fd - out[p, col]) <= 2e-4 * abs(out[p, col]) + 1e-6, (p, col, fd, out[p, col])
