@@ -348,6 +348,37 @@ int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n,
  * [mc_mlp_param_count] host floats, e.g. the average of the ranks' batch
  * gradients in data-parallel training.  Synchronises `stream`. */
 int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *stream);
+/*
+ * Training on prices and their sensitivities (derivative labels; the
+ * network is fitted to the Monte Carlo prices and to their pathwise Greeks,
+ * Sec. I.A.3): the loss is
+ *   (1/n) sum_i [(y_i - t_i)^2 + sum_k weight_k m_ik (scale_k dy_i/dx_{dir_k} - g_ik)^2],
+ * m_ik = 1 where g_ik is finite, 0 where it is not (a sample without that
+ * label, e.g. a barrier point's NaN from mc_surrogate_label_greeks).  dy/dx is
+ * the network's input gradient (forward-mode tangents through the layers) and
+ * the loss is differentiated through it (a reverse sweep through the
+ * tangents, with the activation's second derivative).  FP32 SIMT products,
+ * whatever mc_mlp_set_train_mode selected; the network needs a hidden layer.
+ *   dl: n_dir in [0, 4] directions; dir[k] an input index, scale[k] finite
+ *     (scale_k = 1 / (the input map's slope) turns a network-input derivative
+ *     into a derivative in the raw variable), weight[k] >= 0.
+ *   dev_g: DEVICE [n][n_dir] floats (may be NULL when n_dir = 0).
+ *   mc_mlp_loss_grad_d: loss_parts host [1 + n_dir] (price term, then each
+ *     direction's weighted term) or NULL; host_grad as in mc_mlp_loss_grad.
+ *   mc_mlp_train_d: as mc_mlp_train with this loss (last_epoch_loss = the
+ *     mean total loss of the final epoch).  Both synchronise `stream`.
+ */
+typedef struct {
+    int32_t n_dir;
+    int32_t dir[4];
+    float scale[4];
+    float weight[4];
+} mc_mlp_dloss;
+int mc_mlp_loss_grad_d(mc_mlp *net, const float *dev_x, const float *dev_t, const float *dev_g, int64_t n,
+                       const mc_mlp_dloss *dl, double *loss_parts, float *host_grad, void *stream);
+int mc_mlp_train_d(mc_mlp *net, const float *dev_x, const float *dev_t, const float *dev_g, int64_t n,
+                   const mc_mlp_dloss *dl, int32_t epochs, int32_t batch, float lr, double *last_epoch_loss,
+                   void *stream);
 /* Data-parallel training without host round trips (every buffer on the
  * network's device, everything asynchronous on `stream`):
  *   mc_mlp_loss_grad_sums: dev_out [count + 1] floats: [0, count) = the
@@ -449,6 +480,17 @@ int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *resu
  */
 int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
                         uint64_t seed, float *dev_labels, float *dev_inputs, void *stream);
+/*
+ * mc_surrogate_label_greeks -- mc_surrogate_labels (same paths, same labels)
+ * plus the pathwise sensitivities of each label (Sec. I.A.3): dev_dlabels
+ * DEVICE [n][2] = (d label / d(S/K), d label / d sigma), i.e. the discounted
+ * path means of 1{S_T > K} S_T / S and 1{S_T > K} (S_T / K)
+ * (sqrt(dt) sum_i z_i - sigma tau).  Barrier points (K/H > 0) get NaN: a
+ * knock-out indicator has no pathwise derivative.  dev_inputs as in
+ * mc_surrogate_labels (may be NULL).  Asynchronous on `stream`.
+ */
+int mc_surrogate_label_greeks(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
+                              uint64_t seed, float *dev_labels, float *dev_dlabels, float *dev_inputs, void *stream);
 
 /*
  * Plans: the same computation as mc_price split into a set-up phase (argument

@@ -11,7 +11,7 @@ from .native import MCError, PAYOFF, PRECISION, SCHEME  # noqa: F401
 
 def __getattr__(name):
     if name in ("price", "price_mlmc", "price_qmc", "simulate", "greeks", "corr_greeks", "Plan", "Mlp", "risk",
-                "surrogate_labels", "philox_words", "normals", "moments", "combine", "tail"):
+                "surrogate_labels", "surrogate_label_greeks", "philox_words", "normals", "moments", "combine", "tail"):
         from . import api
         return getattr(api, name)
     if name in ("HestonPricer", "GbmPricer", "BasketPricer"):

@@ -327,6 +327,41 @@ class Mlp:
         check(self._lib.mc_mlp_apply_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(lr),
                                           _stream_handle(stream)))
 
+    @staticmethod
+    def _dloss(dirs, scales, weights):
+        if len(dirs) > 4 or not (len(dirs) == len(scales) == len(weights)):
+            raise ValueError("up to 4 directions, with one scale and one weight each")
+        d = native.McMlpDloss()
+        d.n_dir = len(dirs)
+        for k, (j, sc, wt) in enumerate(zip(dirs, scales, weights)):
+            d.dir[k], d.scale[k], d.weight[k] = int(j), float(sc), float(wt)
+        return d
+
+    def loss_grad_d(self, x, t, g, dirs, scales, weights, stream=None):
+        """Loss with derivative labels (mc_mlp_loss_grad_d): (loss parts
+        [1 + K], packed gradient); g a CUDA float32 [n, K] tensor (NaN: no
+        label)."""
+        x, t = x.contiguous(), t.contiguous()
+        d = self._dloss(dirs, scales, weights)
+        gp = ctypes.c_void_p(g.contiguous().data_ptr()) if d.n_dir else None
+        parts = (ctypes.c_double * (1 + d.n_dir))()
+        grad = np.empty(self.count, dtype=np.float32)
+        check(self._lib.mc_mlp_loss_grad_d(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), gp,
+                                           x.shape[0], ctypes.byref(d), parts, grad.ctypes.data_as(ctypes.c_void_p),
+                                           _stream_handle(stream)))
+        return list(parts), grad
+
+    def train_d(self, x, t, g, dirs, scales, weights, epochs, batch, lr, stream=None):
+        """Mini-batch Adam on the derivative-label loss (mc_mlp_train_d)."""
+        x, t = x.contiguous(), t.contiguous()
+        d = self._dloss(dirs, scales, weights)
+        gp = ctypes.c_void_p(g.contiguous().data_ptr()) if d.n_dir else None
+        loss = ctypes.c_double()
+        check(self._lib.mc_mlp_train_d(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), gp,
+                                       x.shape[0], ctypes.byref(d), epochs, batch, ctypes.c_float(lr),
+                                       ctypes.byref(loss), _stream_handle(stream)))
+        return loss.value
+
     def loss_grad_sums(self, x, t, stream=None):
         """CUDA float32 [count + 1]: the gradient of the batch's summed
         squared error and that sum (mc_mlp_loss_grad_sums, asynchronous)."""
@@ -374,6 +409,22 @@ def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None, wi
                                            ctypes.c_void_p(inp.data_ptr()) if with_inputs else None,
                                            _stream_handle(stream)))
     return (out, inp) if with_inputs else out
+
+
+def surrogate_label_greeks(points, paths, steps_per_year=252, seed=42, stream=None, with_inputs=False):
+    """Labels and their pathwise Greeks (mc_surrogate_label_greeks): (labels
+    [n], dlabels [n, 2] = (d/d(S/K), d/d sigma), NaN rows for barrier points
+    [, inputs])."""
+    import torch
+    pts = points.contiguous()
+    out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    dl = torch.empty((pts.shape[0], 2), dtype=torch.float32, device=pts.device)
+    inp = torch.empty_like(pts) if with_inputs else None
+    check(native.lib().mc_surrogate_label_greeks(pts.shape[0], ctypes.c_void_p(pts.data_ptr()), paths, steps_per_year,
+                                                 seed, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(dl.data_ptr()),
+                                                 ctypes.c_void_p(inp.data_ptr()) if with_inputs else None,
+                                                 _stream_handle(stream)))
+    return (out, dl, inp) if with_inputs else (out, dl)
 
 
 def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_paths=1 << 12, base_paths=1 << 16,

@@ -312,7 +312,6 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
 {
     using Ly = Layout<PREC>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ AccSlot s_acc[(kThreads / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
     // per-asset terms of the step s being observed, double-buffered by the
     // parity of s (written before the step's barrier, read after it):
@@ -325,6 +324,9 @@ __global__ void __launch_bounds__(kThreads, 8) basket_tc_acc_kernel(const __grid
     const uint32_t zt = base, bt = base + Ly::kTileBytes;
     const uint32_t mbar = bt + Ly::kBBytes, tslot = mbar + 16;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
+    // per-warp payoff slots after the barriers, sized by the payoff count at
+    // launch (a static array for 32 payoffs would cost an SM its eighth CTA)
+    AccSlot *s_acc = reinterpret_cast<AccSlot *>(smem_raw + (mbar + 32 - raw));
 
     for (int i = t; i < (kThreads / 32) * a.pay.n * 2; i += kThreads) s_acc[i] = 0.0f;
     if (t == 0) {
@@ -508,10 +510,11 @@ const void *basket_tc_select(const TcArgs &a, int *smem)
     const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
     const bool exact = a.d == tcb::kN;
     if (PREC != MC_FP8E4M3 && SCHEME == MC_LOG_EULER) {
-        // TMEM running sum: Z tile + factor tile + barriers (~27 KB with the
-        // static arrays and the per-block reservation: at most 8 CTAs, 8 x 64
-        // TMEM columns, share an SM)
-        *smem = 1024 + tcb::Layout<PREC>::kTileBytes + tcb::Layout<PREC>::kBBytes + 64;
+        // TMEM running sum: Z tile + factor tile + barriers + payoff slots
+        // (~27 KB with the static arrays and the per-block reservation: at
+        // most 8 CTAs, 8 x 64 TMEM columns, share an SM)
+        *smem = 1024 + tcb::Layout<PREC>::kTileBytes + tcb::Layout<PREC>::kBBytes + 32 +
+                (tcb::kThreads / 32) * a.pay.n * 2 * static_cast<int>(sizeof(AccSlot));
         if (stats)
             return exact ? reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, true, true>)
                          : reinterpret_cast<const void *>(&tcb::basket_tc_acc_kernel<PREC, true, false>);

@@ -276,6 +276,128 @@ __global__ void adam_kernel(int64_t count, float *p, const float *g, float *m, f
     }
 }
 
+// ------------------- derivative labels (input-gradient loss) -------------------
+// Rows of a stacked buffer [(K + 1) n x C]: rows 0..n-1 the primal values,
+// rows (1 + k) n + i the tangent of direction k for sample i.
+
+constexpr int kMaxDirs = 4;
+struct DirSet {
+    int K;
+    int dir[kMaxDirs];
+    float scale[kMaxDirs], weight[kMaxDirs];
+};
+
+// Layer 0's tangents: dz = e_{j_k} W_0 = row j_k of W_0 for every sample, and
+// dh = silu'(z) dz.  Zs, Hs: [(K + 1) n x C] (primal rows already written).
+__global__ void tangent_first_kernel(int64_t n, int C, const float *__restrict__ W0, const DirSet ds,
+                                     float *__restrict__ Zs, float *__restrict__ Hs)
+{
+    const int64_t tot = static_cast<int64_t>(ds.K) * n * C;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(e % C);
+        const int64_t ki = e / C, i = ki % n;
+        const int k = static_cast<int>(ki / n);
+        const float dz = W0[static_cast<int64_t>(ds.dir[k]) * C + c];
+        Zs[n * C + e] = dz;
+        Hs[n * C + e] = silu_grad_f(Zs[i * C + c]) * dz;
+    }
+}
+
+// Hidden layers' tangents through the activation: Hs[tangent rows] =
+// silu'(z) Zs[tangent rows] with z the sample's primal pre-activation.
+__global__ void tangent_act_kernel(int64_t n, int K, int C, const float *__restrict__ Zs, float *__restrict__ Hs)
+{
+    const int64_t tot = static_cast<int64_t>(K) * n * C;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = (e / C) % n;
+        const int c = static_cast<int>(e % C);
+        Hs[n * C + e] = silu_grad_f(Zs[i * C + c]) * Zs[n * C + e];
+    }
+}
+
+// Seeds of the reverse sweep and the loss parts.  Ys: [(K + 1) n] outputs
+// (y, then dy/dx_{j_k}); g: [n x K] labels (non-finite: none).  Writes
+// Ybar = 2 (y - t) / n and 2 w_k m s_k (s_k dy_k - g_k) / n, and per block the
+// FP64 sums of (y - t)^2 and w_k m (s_k dy_k - g_k)^2 at partial[part * nb + block].
+__global__ void dloss_seed_kernel(int64_t n, const float *__restrict__ Ys, const float *__restrict__ t,
+                                  const float *__restrict__ g, const DirSet ds, float *__restrict__ Ybar,
+                                  double *__restrict__ partial)
+{
+    double acc[1 + kMaxDirs] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const float inv_n = 1.0f / static_cast<float>(n);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float r = Ys[i] - t[i];
+        Ybar[i] = 2.0f * r * inv_n;
+        acc[0] += static_cast<double>(r) * r;
+#pragma unroll
+        for (int k = 0; k < kMaxDirs; ++k) {
+            if (k >= ds.K) break;
+            const float gk = g[i * ds.K + k];
+            const bool m = isfinite(gk);
+            const float rd = m ? fmaf(ds.scale[k], Ys[(1 + k) * n + i], -gk) : 0.0f;
+            Ybar[(1 + k) * n + i] = 2.0f * ds.weight[k] * ds.scale[k] * rd * inv_n;
+            acc[1 + k] += static_cast<double>(ds.weight[k]) * rd * rd;
+        }
+    }
+    __shared__ double ws[1 + kMaxDirs][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k <= ds.K; ++k) {
+        const double v = warp_sum_d(acc[k]);
+        if (lane == 0) ws[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x <= ds.K) {
+        double tot = 0.0;
+        for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) tot += ws[threadIdx.x][q];
+        partial[threadIdx.x * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// Reverse step through h = silu(z), dh_k = silu'(z) dz_k: given the stacked
+// input-side adjoints Abar [(K + 1) n x C] and the stacked pre-activations Zs,
+//   zbar   = hbar silu'(z) + sum_k dhbar_k silu''(z) dz_k,
+//   dzbar_k = dhbar_k silu'(z).
+__global__ void dact_bwd_kernel(int64_t n, int K, int C, const float *__restrict__ Abar, const float *__restrict__ Zs,
+                                float *__restrict__ Zbar)
+{
+    const int64_t tot = n * C;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float z = Zs[e];
+        const float sg = 1.0f / (1.0f + expf(-z));
+        const float d1 = sg * (1.0f + z * (1.0f - sg));
+        const float d2 = sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));
+        float zb = Abar[e] * d1;
+        for (int k = 0; k < K; ++k) {
+            const int64_t o = (1 + k) * tot + e;
+            zb = fmaf(Abar[o] * d2, Zs[o], zb);
+            Zbar[o] = Abar[o] * d1;
+        }
+        Zbar[e] = zb;
+    }
+}
+
+// Layer 0's weight gradient from the tangents: row j_k of dW_0 gains the
+// column sums of direction k's adjoint rows (dh_0^k = e_{j_k}).
+__global__ void dir_rows_kernel(int64_t n, int C, const float *__restrict__ Zbar, const DirSet ds, float *__restrict__ gW0)
+{
+    const int c = blockIdx.x, k = blockIdx.y;
+    float s = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += Zbar[((1 + k) * n + i) * C + c];
+    s = warp_sum(s);
+    __shared__ float ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.0f;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += ws[w];
+        atomicAdd(gW0 + static_cast<int64_t>(ds.dir[k]) * C + c, tot);  // directions may share an input
+    }
+}
+
 int grid_for(int64_t n, int block = 256)
 {
     int64_t g = (n + block - 1) / block;
@@ -398,6 +520,92 @@ cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *
             e = gemm<false, true>(static_cast<int>(n), in, out, dZ, out, params + L.w_off[l], out, nullptr, nullptr, dH,
                                   in, 0, s);
             if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+size_t mlp_train_floats_d(const MlpLayout &L, int64_t n, int K)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1;
+    int maxw = 0;
+    size_t f = 0;
+    for (int l = 0; l < nl; ++l) f += 2 * static_cast<size_t>(K + 1) * n * L.sizes[l + 1];
+    for (int v : L.sizes) maxw = v > maxw ? v : maxw;
+    return f + 2 * static_cast<size_t>(K + 1) * n * maxw + static_cast<size_t>(kMaxSlices) * maxw * maxw;
+}
+
+// Loss with derivative labels and its gradient (the derivation is in the
+// oracle's dloss_and_grads): a forward sweep of the primal rows and, stacked
+// below them, one tangent per direction; a reverse sweep through both.
+// acts: mlp_train_floats_d floats; partial: (1 + K) npartial doubles.
+cudaError_t mlp_loss_grad_d(const MlpLayout &L, const float *params, const float *x, const float *t, const float *g,
+                            int64_t n, int K, const int *dirs, const float *scale, const float *weight, float *acts,
+                            float *grad, double *partial, int npartial, cudaStream_t s)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1;
+    const int64_t R = (K + 1) * n;  // stacked rows
+    DirSet ds{};
+    ds.K = K;
+    for (int k = 0; k < K; ++k) {
+        ds.dir[k] = dirs[k];
+        ds.scale[k] = scale[k];
+        ds.weight[k] = weight[k];
+    }
+    std::vector<float *> Zs(nl), Hs(nl);  // Zs[l]: pre-activations of layer l; Hs[l]: its outputs (stacked)
+    float *p = acts;
+    int maxw = 0;
+    for (int l = 0; l < nl; ++l) {
+        Zs[l] = p; p += R * L.sizes[l + 1];
+        Hs[l] = p; p += R * L.sizes[l + 1];
+    }
+    for (int v : L.sizes) maxw = v > maxw ? v : maxw;
+    float *Abar = p, *Zbar = p + R * maxw, *ws = Zbar + R * maxw;
+    cudaError_t e;
+    // forward
+    for (int l = 0; l < nl; ++l) {
+        const int in = L.sizes[l], out = L.sizes[l + 1];
+        const bool last = l == nl - 1;
+        const float *hin = l == 0 ? x : Hs[l - 1];
+        e = gemm<false, false>(static_cast<int>(n), out, in, hin, in, params + L.w_off[l], out, params + L.b_off[l],
+                               Zs[l], last ? nullptr : Hs[l], out, last ? 0 : 1, s);
+        if (e != cudaSuccess) return e;
+        if (K == 0) continue;
+        if (l == 0) {
+            tangent_first_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, out, params + L.w_off[0], ds, Zs[0], Hs[0]);
+        } else {
+            e = gemm<false, false>(static_cast<int>(K * n), out, in, Hs[l - 1] + n * in, in, params + L.w_off[l], out,
+                                   nullptr, Zs[l] + n * out, nullptr, out, 0, s);
+            if (e != cudaSuccess) return e;
+            if (!last) tangent_act_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, K, out, Zs[l], Hs[l]);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // seeds: the output layer's stacked pre-activations are (y, dy/dx_{j_k})
+    dloss_seed_kernel<<<npartial, 256, 0, s>>>(n, Zs[nl - 1], t, g, ds, Zbar, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int l = nl - 1; l >= 0; --l) {
+        const int in = L.sizes[l], out = L.sizes[l + 1];
+        const int64_t rows = l == 0 ? n : R;  // layer 0's tangent inputs are unit vectors (dir_rows_kernel)
+        const float *hin = l == 0 ? x : Hs[l - 1];
+        const int slices = static_cast<int>(std::min<int64_t>(kMaxSlices, std::max<int64_t>(1, rows / 256)));
+        e = slices > 1 ? gemm_split_k<true, false>(in, out, static_cast<int>(rows), hin, in, Zbar, out,
+                                                   grad + L.w_off[l], slices, ws, s)
+                       : gemm<true, false>(in, out, static_cast<int>(rows), hin, in, Zbar, out, nullptr, nullptr,
+                                           grad + L.w_off[l], out, 0, s);
+        if (e != cudaSuccess) return e;
+        if (l == 0 && K > 0) {
+            dir_rows_kernel<<<dim3(out, K), 256, 0, s>>>(n, out, Zbar, ds, grad + L.w_off[0]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        colsum_kernel<<<out, 256, 0, s>>>(static_cast<int>(n), out, Zbar, grad + L.b_off[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (l > 0) {
+            e = gemm<false, true>(static_cast<int>(R), in, out, Zbar, out, params + L.w_off[l], out, nullptr, nullptr,
+                                  Abar, in, 0, s);
+            if (e != cudaSuccess) return e;
+            dact_bwd_kernel<<<grid_for(n * in), 256, 0, s>>>(n, K, in, Abar, Zs[l - 1], Zbar);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
     return cudaSuccess;

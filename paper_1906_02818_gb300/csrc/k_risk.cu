@@ -38,11 +38,18 @@ __device__ __forceinline__ void surrogate_inputs(float sk, float sig, float tau,
 }
 
 // ------------------------------ labels -----------------------------------
+// GREEKS: also the pathwise sensitivities of each European point's label
+// (Sec. I.A.3), per path 1{S_T > 1} S_T / S (d/d S/K) and
+// 1{S_T > 1} S_T (sqrt(dt) sum z - sigma tau) (d/d sigma), discounted and
+// averaged like the label; barrier points (a knock indicator has no pathwise
+// derivative) get NaN.
+template <bool GREEKS>
 __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *__restrict__ pts, int paths,
                                                     float steps_per_year, const __grid_constant__ RoundKeys rk,
-                                                    float *__restrict__ labels, float *__restrict__ inputs)
+                                                    float *__restrict__ labels, float *__restrict__ inputs,
+                                                    float *__restrict__ dlabels)
 {
-    __shared__ double s_red[8];
+    __shared__ double s_red[3][8];
     for (int64_t p = blockIdx.x; p < npts; p += gridDim.x) {
         const float sk = pts[p * 5 + 0], sig = pts[p * 5 + 1], tau = pts[p * 5 + 2], r = pts[p * 5 + 3],
                     kh = pts[p * 5 + 4];
@@ -51,11 +58,12 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
         const float dt = tau / M;
         const float H = kh > 0.0f ? 1.0f / kh : INFINITY;  // barrier in units of K
         const float a = kLog2e * (r - 0.5f * sig * sig) * dt, b = kLog2e * sig * sqrtf(dt);
-        float acc = 0.0f;
+        const bool greeks = GREEKS && !(kh > 0.0f);
+        float acc = 0.0f, accd = 0.0f, accv = 0.0f;
         if (!(sk >= H)) {  // already at or above the barrier on the current date: worthless
             for (int path = threadIdx.x; path < paths; path += blockDim.x) {
                 const uint64_t n = tag(4, (static_cast<uint64_t>(p) << 16) | static_cast<uint64_t>(path));
-                float y = 0.0f;
+                float y = 0.0f, zs = 0.0f;
                 bool alive = true;
                 for (int q = 0; q < (M + 3) / 4; ++q) {
                     const float4 z = normals4(static_cast<uint64_t>(q), n, rk);
@@ -64,21 +72,34 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
                     for (int l = 0; l < 4; ++l) {
                         if (4 * q + l < M) {
                             y += fmaf(b, zz[l], a);
+                            if (GREEKS) zs += zz[l];
                             if (sk * ex2_approx(y) >= H) alive = false;
                         }
                     }
                 }
-                const float ST = sk * ex2_approx(y);
+                const float g = ex2_approx(y), ST = sk * g;
                 acc += alive ? fmaxf(ST - 1.0f, 0.0f) : 0.0f;
+                if (greeks && ST > 1.0f) {
+                    accd += g;
+                    accv += ST * fmaf(sqrtf(dt), zs, -sig * tau);
+                }
             }
         }
-        double v = warp_sum_d(static_cast<double>(acc));
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+        const double v[3] = {warp_sum_d(static_cast<double>(acc)), GREEKS ? warp_sum_d(static_cast<double>(accd)) : 0.0,
+                             GREEKS ? warp_sum_d(static_cast<double>(accv)) : 0.0};
+        if ((threadIdx.x & 31) == 0)
+            for (int k = 0; k < (GREEKS ? 3 : 1); ++k) s_red[k][threadIdx.x >> 5] = v[k];
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_red[w];
-            labels[p] = static_cast<float>(exp(-static_cast<double>(r) * tau) * t / paths);
+            double t[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < (GREEKS ? 3 : 1); ++k)
+                for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t[k] += s_red[k][w];
+            const double disc = exp(-static_cast<double>(r) * tau) / paths;
+            labels[p] = static_cast<float>(disc * t[0]);
+            if (GREEKS) {
+                dlabels[2 * p] = greeks ? static_cast<float>(disc * t[1]) : __int_as_float(0x7fc00000);
+                dlabels[2 * p + 1] = greeks ? static_cast<float>(disc * t[2]) : __int_as_float(0x7fc00000);
+            }
         }
         __syncthreads();
     }
@@ -311,10 +332,13 @@ __global__ void __launch_bounds__(1024) tail_kernel(int64_t n, const double *pnl
 }  // namespace
 
 cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float spy, const RoundKeys &rk,
-                          float *labels, float *inputs, cudaStream_t s)
+                          float *labels, float *inputs, float *dlabels, cudaStream_t s)
 {
     const int64_t g = npts < 1216 * 4 ? npts : 1216 * 4;
-    label_kernel<<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, rk, labels, inputs);
+    if (dlabels)
+        label_kernel<true><<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, rk, labels, inputs, dlabels);
+    else
+        label_kernel<false><<<static_cast<int>(g), 256, 0, s>>>(npts, pts, paths, spy, rk, labels, inputs, nullptr);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ struct mc_mlp {
     float *work = nullptr;
     size_t work_floats = 0;
     double *partial = nullptr;
+    double *dpartial = nullptr;  // loss parts of the derivative-label loss, (1 + kMlpMaxDirs) x kPartials
     int step = 0;
     // bf16 operand image of the weights, rebuilt when the parameters change
     uint8_t *img = nullptr;
@@ -29,6 +30,7 @@ struct mc_mlp {
         for (float *p : {params, grad, m, v, work})
             if (p) cudaFree(p);
         if (partial) cudaFree(partial);
+        if (dpartial) cudaFree(dpartial);
         if (img) cudaFree(img);
         if (err) cudaFree(err);
     }
@@ -72,6 +74,30 @@ int loss_grad_batch(mc_mlp *N, const float *x, const float *t, int64_t n, cudaSt
     } else {
         MLP_CUDA(mlp_loss_grad(N->L, N->params, x, t, n, N->work, N->grad, N->partial, kPartials, s));
     }
+    return MC_OK;
+}
+
+// Checks of a derivative-label loss description against the network.
+int check_dloss(const mc_mlp *N, const mc_mlp_dloss *dl)
+{
+    if (!dl) return set_last_error(MC_EINVAL, "dloss is NULL");
+    if (dl->n_dir < 0 || dl->n_dir > kMlpMaxDirs) return set_last_error(MC_EINVAL, "n_dir outside [0, 4]");
+    if (N->L.sizes.size() < 3) return set_last_error(MC_EUNSUPPORTED, "derivative labels need a hidden layer");
+    for (int k = 0; k < dl->n_dir; ++k) {
+        if (dl->dir[k] < 0 || dl->dir[k] >= N->L.sizes[0]) return set_last_error(MC_EINVAL, "dir outside the inputs");
+        if (!std::isfinite(dl->scale[k]) || !std::isfinite(dl->weight[k]) || dl->weight[k] < 0.0f)
+            return set_last_error(MC_EINVAL, "scale must be finite and weight finite and >= 0");
+    }
+    return MC_OK;
+}
+
+// One batch of the derivative-label loss: loss parts at dpartial, gradient at grad.
+int loss_grad_batch_d(mc_mlp *N, const float *x, const float *t, const float *g, int64_t n, const mc_mlp_dloss *dl,
+                      cudaStream_t s)
+{
+    if (!N->dpartial) MLP_CUDA(cudaMalloc(&N->dpartial, (1 + kMlpMaxDirs) * kPartials * sizeof(double)));
+    MLP_CUDA(mlp_loss_grad_d(N->L, N->params, x, t, g, n, dl->n_dir, dl->dir, dl->scale, dl->weight, N->work, N->grad,
+                             N->dpartial, kPartials, s));
     return MC_OK;
 }
 
@@ -269,6 +295,66 @@ int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *strea
     MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
     ++net->version;
     MLP_CUDA(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+int mc_mlp_loss_grad_d(mc_mlp *net, const float *dev_x, const float *dev_t, const float *dev_g, int64_t n,
+                       const mc_mlp_dloss *dl, double *loss_parts, float *host_grad, void *stream)
+{
+    int rc;
+    if ((rc = check_net(net)) || (rc = check_dloss(net, dl))) return rc;
+    if (!dev_x || !dev_t || (dl->n_dir > 0 && !dev_g) || n < 1)
+        return set_last_error(MC_EINVAL, "x, t (and g with directions) must be set and n >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_work(net, mlp_train_floats_d(net->L, n, dl->n_dir)))) return rc;
+    if ((rc = loss_grad_batch_d(net, dev_x, dev_t, dev_g, n, dl, s))) return rc;
+    std::vector<double> part((1 + kMlpMaxDirs) * kPartials);
+    MLP_CUDA(cudaMemcpyAsync(part.data(), net->dpartial, (1 + dl->n_dir) * kPartials * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    if (host_grad)
+        MLP_CUDA(cudaMemcpyAsync(host_grad, net->grad, net->L.count * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MLP_CUDA(cudaStreamSynchronize(s));
+    if (loss_parts)
+        for (int k = 0; k <= dl->n_dir; ++k) {
+            double tot = 0.0;
+            for (int b = 0; b < kPartials; ++b) tot += part[static_cast<size_t>(k) * kPartials + b];
+            loss_parts[k] = tot / static_cast<double>(n);
+        }
+    return MC_OK;
+}
+
+int mc_mlp_train_d(mc_mlp *net, const float *dev_x, const float *dev_t, const float *dev_g, int64_t n,
+                   const mc_mlp_dloss *dl, int32_t epochs, int32_t batch, float lr, double *last_epoch_loss,
+                   void *stream)
+{
+    int rc;
+    if ((rc = check_net(net)) || (rc = check_dloss(net, dl))) return rc;
+    if (!dev_x || !dev_t || (dl->n_dir > 0 && !dev_g) || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
+        return set_last_error(MC_EINVAL, "x, t (and g) set; n, epochs, batch >= 1; lr > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t B = batch < n ? batch : n;
+    if ((rc = ensure_work(net, mlp_train_floats_d(net->L, B, dl->n_dir)))) return rc;
+    const int n_in = net->L.sizes[0], K = dl->n_dir;
+    ++net->version;
+    std::vector<double> part((1 + kMlpMaxDirs) * kPartials);
+    double epoch_loss = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        epoch_loss = 0.0;
+        const bool last = ep == epochs - 1;
+        for (int64_t b0 = 0; b0 + B <= n; b0 += B) {  // whole batches; the samples are i.i.d.
+            if ((rc = loss_grad_batch_d(net, dev_x + b0 * n_in, dev_t + b0, K ? dev_g + b0 * K : nullptr, B, dl, s)))
+                return rc;
+            MLP_CUDA(mlp_adam(net->L.count, net->params, net->grad, net->m, net->v, lr, ++net->step, s));
+            if (last) {
+                MLP_CUDA(cudaMemcpyAsync(part.data(), net->dpartial, (1 + K) * kPartials * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+                MLP_CUDA(cudaStreamSynchronize(s));
+                for (int k = 0; k < (1 + K) * kPartials; ++k) epoch_loss += part[k];
+            }
+        }
+    }
+    MLP_CUDA(cudaStreamSynchronize(s));
+    if (last_epoch_loss) *last_epoch_loss = epoch_loss / static_cast<double>((n / B) * B);
     return MC_OK;
 }
 

@@ -56,8 +56,8 @@ struct DevBufs {
 
 extern "C" {
 
-int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
-                        uint64_t seed, float *dev_labels, float *dev_inputs, void *stream)
+static int labels_common(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
+                         uint64_t seed, float *dev_labels, float *dev_inputs, float *dev_dlabels, void *stream)
 {
     if (n_points < 1 || !dev_points || !dev_labels) return fail(MC_EINVAL, "points and labels must be set, n >= 1");
     if (n_points > (int64_t(1) << 36)) return fail(MC_EINVAL, "too many points");
@@ -65,8 +65,22 @@ int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths
     if (steps_per_year < 1) return fail(MC_EINVAL, "steps_per_year must be >= 1");
     RK_CUDA(launch_labels(n_points, dev_points, paths, static_cast<float>(steps_per_year),
                           round_keys(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)), dev_labels, dev_inputs,
-                          static_cast<cudaStream_t>(stream)));
+                          dev_dlabels, static_cast<cudaStream_t>(stream)));
     return MC_OK;
+}
+
+int mc_surrogate_labels(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
+                        uint64_t seed, float *dev_labels, float *dev_inputs, void *stream)
+{
+    return labels_common(n_points, dev_points, paths, steps_per_year, seed, dev_labels, dev_inputs, nullptr, stream);
+}
+
+int mc_surrogate_label_greeks(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
+                              uint64_t seed, float *dev_labels, float *dev_dlabels, float *dev_inputs, void *stream)
+{
+    if (!dev_dlabels) return fail(MC_EINVAL, "dev_dlabels must be set");
+    return labels_common(n_points, dev_points, paths, steps_per_year, seed, dev_labels, dev_inputs, dev_dlabels,
+                         stream);
 }
 
 int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *res, void *stream)

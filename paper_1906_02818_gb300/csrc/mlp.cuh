@@ -29,6 +29,16 @@ cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const floa
 cudaError_t mlp_loss_grad(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
                           float *acts, float *grad, double *partial, int npartial, cudaStream_t s);
 size_t mlp_train_floats(const MlpLayout &L, int64_t n);
+// Loss with derivative labels: (1/n) sum [(y - t)^2 + sum_k weight_k m (scale_k
+// dy/dx_{dirs_k} - g_k)^2] (m = 1 where g_k is finite) and its gradient, in
+// FP32 SIMT products; K <= 4 directions; g [n x K]; acts holds
+// mlp_train_floats_d(L, n, K) floats; partial (1 + K) npartial doubles (the
+// price part's block sums, then each direction's; divide by n).
+constexpr int kMlpMaxDirs = 4;
+size_t mlp_train_floats_d(const MlpLayout &L, int64_t n, int K);
+cudaError_t mlp_loss_grad_d(const MlpLayout &L, const float *params, const float *x, const float *t, const float *g,
+                            int64_t n, int K, const int *dirs, const float *scale, const float *weight, float *acts,
+                            float *grad, double *partial, int npartial, cudaStream_t s);
 // The same with the width -> width products on the tensor cores (three-pass
 // TF32) when mlp_tc_supported(L); acts holds mlp_train_floats_tc(L, n)
 // floats; *err is set to 1 if a bounded wait of the tensor-core kernel expires.

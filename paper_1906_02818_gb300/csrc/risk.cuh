@@ -27,8 +27,10 @@ struct RiskArgs {
     int64_t scen_off;  // global index of the first scenario (stream indices)
 };
 
+// dlabels: NULL, or [npts][2] pathwise d label / d(S/K) and d label / d sigma
+// of the European points (NaN for barrier points).
 cudaError_t launch_labels(int64_t npts, const float *pts, int paths, float steps_per_year, const RoundKeys &rk,
-                          float *labels, float *inputs, cudaStream_t s);
+                          float *labels, float *inputs, float *dlabels, cudaStream_t s);
 cudaError_t launch_outer(int64_t nscen, int64_t off, int d, const float *Lc, const float *drift, const float *s0,
                          const RoundKeys &rk, float *Sp, cudaStream_t s);
 cudaError_t launch_nested(const RiskArgs &a, int64_t nscen, const float *Sp, double *contrib, cudaStream_t s);

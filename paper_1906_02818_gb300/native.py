@@ -78,6 +78,11 @@ class McRiskResult(ctypes.Structure):
 
 RISK_METHOD = {"nested": 0, "surrogate": 1}
 
+
+class McMlpDloss(ctypes.Structure):
+    _fields_ = [("n_dir", ctypes.c_int32), ("dir", ctypes.c_int32 * 4), ("scale", ctypes.c_float * 4),
+                ("weight", ctypes.c_float * 4)]
+
 # name, restype, argtypes  (the complete exported surface of mc.h)
 SIGNATURES = [
     ("mc_version", ctypes.c_int, []),
@@ -133,6 +138,15 @@ SIGNATURES = [
                                              ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_mlp_apply_grad_sums", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
                                               ctypes.c_void_p]),
+    ("mc_surrogate_label_greeks", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
+    ("mc_mlp_loss_grad_d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.POINTER(McMlpDloss), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_mlp_train_d", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.POINTER(McMlpDloss), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("mc_philox_words", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_normals", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,

@@ -285,3 +285,87 @@ def test_train_mode_checks(gb):
         net.set_train_mode("tf32x3")
     assert native.lib().mc_mlp_set_train_mode(net.handle, 7) == native.MC_EINVAL
     net.close()
+
+
+S_SCALE, V_SCALE = 1.0 / 0.55, 1.0 / 0.15  # d input / d(S/K) and d input / d sigma of the surrogate's input map
+
+
+@pytest.mark.parametrize("n", [131, 777])
+def test_derivative_loss_gradient_matches_oracle(gb, n):
+    """The derivative-label loss (mc_mlp_loss_grad_d: prices plus two input
+    gradients, some labels missing) and its gradient against the FP64 oracle
+    (oracle/mlp.py dloss_and_grads, pinned by finite differences).  The
+    library compares scale_k dy/dx with g_k; the oracle's form is the same loss
+    with weight scale^2 and label g / scale."""
+    import torch
+    init = workloads.mlp_init(seed=9)
+    net = gb.Mlp(5, 256, 4, init)
+    x, t = _data(n, seed=4)
+    rng = np.random.default_rng(5)
+    g = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    g[::7, 0] = np.nan
+    g[3::11, 1] = np.nan
+    dirs, scales, weights = [0, 1], [S_SCALE, V_SCALE], [0.5, 2.0]
+    parts, grad = net.loss_grad_d(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(g).cuda(),
+                                  dirs, scales, weights)
+    P = omlp.unpack(init.astype(np.float64), SIZES)
+    sc = np.array(scales)
+    loss, p_ref, G = omlp.dloss_and_grads(P, x.astype(np.float64), t.astype(np.float64), g.astype(np.float64) / sc,
+                                          dirs, list(np.array(weights) * sc * sc))
+    g_ref = omlp.pack(G)
+    for a, b in zip(parts, p_ref):
+        assert abs(a - b) <= 1e-5 * b + 1e-9, (parts, p_ref)
+    scale = np.max(np.abs(g_ref))
+    print("derivative loss: parts", parts, "max grad err / max |grad| %.2e" % (np.max(np.abs(grad - g_ref)) / scale))
+    assert np.max(np.abs(grad - g_ref)) <= 1e-4 * scale
+    # no directions: the plain loss and gradient
+    parts0, grad0 = net.loss_grad_d(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), None, [], [], [])
+    l_plain, g_plain = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    assert abs(parts0[0] - l_plain) <= 1e-6 * l_plain
+    assert np.max(np.abs(grad0 - g_plain)) <= 1e-5 * np.max(np.abs(g_plain))
+    net.close()
+
+
+def test_training_on_greeks_gains_over_prices_alone(gb):
+    """What the derivative labels buy (Sec. I.A.3's sensitivities as training
+    signal): two networks from the same initial weights train on the same
+    2^14 European points of the surrogate's box, each labelled by 2^10 Monte
+    Carlo paths, one on the prices alone and one on the prices plus the
+    pathwise delta and vega labels of the same paths.  On 4096 fresh points
+    the Black-Scholes closed forms judge both: the Greek-trained network's
+    delta error and its price error must be the smaller."""
+    import math
+    import torch
+    from closed_forms import bs_call
+    n_tr, n_te = 1 << 14, 4096
+    pts = workloads.surrogate_points(n_tr + n_te, seed=21)
+    pts[:, 4] = 0.0  # European
+    P = torch.from_numpy(pts).cuda()
+    lab, dl, x = gb.surrogate_label_greeks(P[:n_tr], 1 << 10, with_inputs=True)
+    _, _, xt = gb.surrogate_label_greeks(P[n_tr:], 1, with_inputs=True)
+    te = pts[n_tr:].astype(np.float64)
+    M = np.maximum(1, np.rint(te[:, 2] * 252))
+    T = M * (te[:, 2] / M)
+    price = np.array([bs_call(s, 1.0, r, v, tt) for s, v, r, tt in zip(te[:, 0], te[:, 1], te[:, 3], T)])
+    d1 = (np.log(te[:, 0]) + (te[:, 3] + 0.5 * te[:, 1] ** 2) * T) / (te[:, 1] * np.sqrt(T))
+    delta = 0.5 * (1.0 + np.array([math.erf(v / math.sqrt(2.0)) for v in d1]))
+    init = workloads.mlp_init(seed=17)
+    res = {}
+    for name, dirs in (("prices", []), ("prices+greeks", [0, 1])):
+        net = gb.Mlp(5, 256, 4, init)
+        sc, wt = [S_SCALE, V_SCALE][:len(dirs)], [0.2, 0.05][:len(dirs)]
+        for lr, ep in ((1e-3, 30), (3e-4, 15), (1e-4, 15)):
+            net.train_d(x, lab, dl, dirs, sc, wt, epochs=ep, batch=512, lr=lr)
+        xq = xt.clone().requires_grad_(False)
+        y = net.forward(xq).double().cpu().numpy()
+        h = 1e-3  # central difference of the network in S/K: input 0 moves by h / 0.55
+        xp, xm = xt.clone(), xt.clone()
+        xp[:, 0] += h * S_SCALE
+        xm[:, 0] -= h * S_SCALE
+        dnet = (net.forward(xp).double() - net.forward(xm).double()).cpu().numpy() / (2 * h)
+        res[name] = (float(np.sqrt(np.mean((y - price) ** 2))), float(np.sqrt(np.mean((dnet - delta) ** 2))))
+        net.close()
+    print("test RMSE vs Black-Scholes (price, delta):", res)
+    (p0, d0), (p1, d1_) = res["prices"], res["prices+greeks"]
+    assert d1_ < 0.7 * d0, res
+    assert p1 < 0.8 * p0, res

@@ -163,3 +163,84 @@ def test_device_tail_selection_matches_oracle_rule(gb):
         var, cvar, nt = orisk.var_cvar(pnl, alpha)
         assert got["var"] == var and got["n_tail"] == nt, (n, alpha, got, var, nt)
         assert abs(got["cvar"] - cvar) <= 1e-12 * max(1.0, abs(cvar))
+
+
+def test_label_greeks_match_oracle(gb, orc):
+    """Pathwise delta and vega labels (mc_surrogate_label_greeks) against the
+    FP64 oracle on the same paths: the labels themselves unchanged (to an
+    FP32 rounding); each
+    Greek within 2e-5 relative plus the change of the oracle's own Greek
+    under a 2e-5 relative move of S/K (the paths whose S_T lies that close to
+    K may take the other side of the payoff's kink in FP32); barrier points
+    NaN."""
+    import torch
+    pts = workloads.surrogate_points(96, seed=11)
+    pts[:48, 4] = 0.0
+    lab, dl = gb.surrogate_label_greeks(torch.from_numpy(pts).cuda(), 1024)
+    lab, dl = lab.cpu().numpy(), dl.cpu().numpy()
+    plain = gb.surrogate_labels(torch.from_numpy(pts).cuda(), 1024).cpu().numpy()
+    assert np.max(np.abs(lab - plain)) <= 1e-6 * np.max(np.abs(plain))  # same paths (the compiler may fuse differently)
+    p64 = pts.astype(np.float64)
+    ref = orisk.label_greeks(p64, 1024)
+    euro = pts[:, 4] == 0
+    assert np.all(np.isnan(dl[~euro])) and np.all(np.isnan(ref[~euro]))
+    band = np.zeros((96, 2))
+    for sgn in (1.0, -1.0):
+        q = p64.copy()
+        q[:, 0] *= 1.0 + sgn * 2e-5
+        band = np.maximum(band, np.abs(orisk.label_greeks(q, 1024)[:, [2, 4]] - ref[:, [2, 4]]))
+    for col, k in ((2, 0), (4, 1)):
+        err = np.abs(dl[euro, k] - ref[euro, col])
+        tol = 2e-5 * np.abs(ref[euro, col]) + band[euro, k] + 1e-7
+        print("label greek %d: max err %.2e, max err / tol %.3f" % (k, err.max(), np.max(err / tol)))
+        assert np.all(err <= tol)
+
+
+def test_greek_trained_surrogate_matches_nested_at_a_fraction_of_the_time(gb):
+    """What the network gains over plain nested Monte Carlo (Sec. VI.B's
+    portfolio revaluation), at equal accuracy.  A surrogate trained by the
+    library's kernels on GPU Monte Carlo prices and pathwise Greeks (2^18
+    points of the parameter box, 2^12 paths each; delta and vega labels on
+    the European half) revalues the 1024-option book on 2048 scenarios.  The
+    yardstick is nested Monte Carlo with 2^14 inner paths on the same
+    scenarios.  The surrogate's per-scenario PnL error must not exceed that of
+    nested Monte Carlo with 2^12 inner paths (its error against the exact
+    revaluation: the error against the 2^14-path run, whose first 2^12 paths
+    it shares, over sqrt(1 - 2^12 / 2^14)), its VaR and CVaR must lie within
+    5 % of the yardstick's, and it must revalue at least 50 times faster than
+    the 2^12-path nested run."""
+    import torch
+    pts = torch.from_numpy(workloads.surrogate_points(1 << 18, seed=31)).cuda()
+    lab, dl, x = gb.surrogate_label_greeks(pts, 1 << 12, with_inputs=True)
+    net = gb.Mlp(5, 256, 4, workloads.mlp_init(seed=5))
+    dirs, scales, weights = [0, 1], [1.0 / 0.55, 1.0 / 0.15], [0.2, 0.05]
+    for lr, ep in ((1e-3, 25), (3e-4, 15), (1e-4, 10)):
+        net.train_d(x, lab, dl, dirs, scales, weights, epochs=ep, batch=4096, lr=lr)
+    pf = workloads.risk_portfolio()
+    ns = 2048
+
+    def timed(**kw):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = gb.risk(pf, n_scen=ns, want_pnl=True, base_paths=1 << 16, **kw)
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    ref, _ = timed(method="nested", inner_paths=1 << 14)
+    n12, t12 = timed(method="nested", inner_paths=1 << 12)
+    gb.risk(pf, n_scen=ns, method="surrogate", surrogate=net)  # warm-up (weights image)
+    sur, ts = timed(method="surrogate", surrogate=net)
+    rmse = lambda r: float(np.sqrt(np.mean((r["pnl"] - ref["pnl"]) ** 2)))  # noqa: E731
+    e12 = rmse(n12) / np.sqrt(1.0 - 0.25)
+    es = rmse(sur)
+    rv = abs(sur["var"] - ref["var"]) / abs(ref["var"])
+    rc = abs(sur["cvar"] - ref["cvar"]) / abs(ref["cvar"])
+    rv12 = abs(n12["var"] - ref["var"]) / abs(ref["var"])
+    rc12 = abs(n12["cvar"] - ref["cvar"]) / abs(ref["cvar"])
+    print(f"PnL RMSE vs nested 2^14: surrogate {es:.3f}, nested 2^12 {e12:.3f} (exact-corrected); "
+          f"VaR err surrogate {rv:.2%} nested 2^12 {rv12:.2%}; CVaR err surrogate {rc:.2%} nested 2^12 {rc12:.2%}; "
+          f"time surrogate {ts * 1e3:.1f} ms, nested 2^12 {t12 * 1e3:.1f} ms")
+    assert es <= e12
+    assert rv < 0.05 and rc < 0.05
+    assert ts * 50 < t12
+    net.close()
