@@ -1,8 +1,12 @@
 // FP32 correlated-basket path kernel (the multivariate Euler-Maruyama scheme
 // of Sec. II.A.2), instantiated per basket width D in separate translation
 // units so that they compile in parallel.  The contraction dW = Lhat z runs
-// in FP32 FMAs with the packed factor in the launch-parameter block
-// (constant bank): every FMA takes its factor entry as a constant operand.
+// in packed FP32x2 FMAs (fma.rn.f32x2: two assets per instruction, each lane
+// an ordinary FP32 fma) with the factor's column pairs in the
+// launch-parameter block (constant bank) as 64-bit operands; the state is
+// held as asset pairs.  A scalar FMA with a 32-bit constant-bank operand
+// sustains a fraction of the FMA pipe's rate on this part; the 64-bit pair
+// operand carries two factor entries per instruction.
 #pragma once
 
 #include "mc_kernels.cuh"
@@ -18,6 +22,40 @@ const void *basket_select_scheme(const BasketArgs &a);
 namespace basket_detail {
 
 constexpr int kBlock = 256;
+
+// Packed FP32 pairs (low = even asset, high = odd asset).
+using f32x2 = unsigned long long;
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 fadd2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float lo_of(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi_of(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ float elem(const f32x2 *v, int j) { return (j & 1) ? hi_of(v[j >> 1]) : lo_of(v[j >> 1]); }
 
 struct Stats {
     float sum, umax, umin;
@@ -55,9 +93,11 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_consta
         st.init();
         if (valid) {
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
-            float x[D];  // log-Euler: log2(S_a / S0_a); Euler: S_a
+            constexpr int H = D / 2;
+            f32x2 x[H];  // asset pairs; log-Euler: log2(S_a / S0_a); Euler: S_a
 #pragma unroll
-            for (int j = 0; j < D; ++j) x[j] = (SCHEME == MC_LOG_EULER) ? 0.0f : c.s0[j];
+            for (int q = 0; q < H; ++q)
+                x[q] = (SCHEME == MC_LOG_EULER) ? pack2(0.0f, 0.0f) : pack2(c.s0[2 * q], c.s0[2 * q + 1]);
             if (SAVE) {
                 for (int j = 0; j < d; ++j) a.run.save[static_cast<int64_t>(j) * a.run.paths + nl] = c.s0[j];
             }
@@ -67,15 +107,16 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_consta
                 // log-Euler accumulates L z straight into the state (|y| = O(1):
                 // ~65 roundings of <= 3e-8 per step, ~2e-6 rms over 252 steps);
                 // Euler needs dW apart because the step is multiplicative.
-                float dw[SCHEME == MC_EULER ? D : 1];
+                f32x2 dw[SCHEME == MC_EULER ? H : 1];
                 if (SCHEME == MC_EULER) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) dw[j] = 0.0f;
+                    for (int q = 0; q < H; ++q) dw[q] = pack2(0.0f, 0.0f);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) x[j] += c.drift[j];
+                    for (int q = 0; q < H; ++q) x[q] = fadd2(x[q], pack2(c.drift[2 * q], c.drift[2 * q + 1]));
                 }
-                // dW = Lhat z, column by column as the normals are produced.
+                // dW = Lhat z, column by column as the normals are produced;
+                // column k updates the pairs q >= k/2 with (z_k, z_k).
 #pragma unroll
                 for (int kb = 0; kb < D / 4 + (D % 4 ? 1 : 0); ++kb) {
                     float zz[4];
@@ -93,24 +134,28 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_consta
                     for (int l = 0; l < 4; ++l) {
                         const int k = 4 * kb + l;
                         if (k < D) {
+                            const f32x2 z2 = pack2(zz[l], zz[l]);
 #pragma unroll
-                            for (int j = k; j < D; ++j) {
-                                if (SCHEME == MC_EULER) dw[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], dw[j]);
-                                else x[j] = fmaf(c.L[j * (j + 1) / 2 + k], zz[l], x[j]);
+                            for (int q = k / 2; q < H; ++q) {
+                                const f32x2 Lq = c.Lp[basket_pair_base(D, k) + q - k / 2];
+                                if (SCHEME == MC_EULER) dw[q] = ffma2(Lq, z2, dw[q]);
+                                else x[q] = ffma2(Lq, z2, x[q]);
                             }
                         }
                     }
                 }
                 if (SCHEME == MC_EULER) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) x[j] = fmaf(x[j], c.drift[j] + dw[j], x[j]);
+                    for (int q = 0; q < H; ++q)
+                        x[q] = ffma2(x[q], fadd2(pack2(c.drift[2 * q], c.drift[2 * q + 1]), dw[q]), x[q]);
                 }
                 if (STATS || (SAVE && ((i + 1) % a.run.save_every) == 0)) {
                     float u = 0.0f;
                     const int64_t slot = (i + 1) / a.run.save_every;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * ex2_approx(x[j]) : x[j];
+                        const float xj = elem(x, j);
+                        const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * ex2_approx(xj) : xj;
                         if (STATS) u = fmaf(c.w[j], Sj, u);
                         if (SAVE && ((i + 1) % a.run.save_every) == 0 && j < d)
                             a.run.save[(slot * d + j) * a.run.paths + nl] = Sj;
@@ -121,8 +166,8 @@ __global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_consta
             float u = 0.0f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                if (SCHEME == MC_LOG_EULER) u = fmaf(c.ws0[j], ex2_approx(x[j]), u);
-                else u = fmaf(c.w[j], x[j], u);
+                if (SCHEME == MC_LOG_EULER) u = fmaf(c.ws0[j], ex2_approx(elem(x, j)), u);
+                else u = fmaf(c.w[j], elem(x, j), u);
             }
             uT = u;
             avg = st.sum * inv_m;

@@ -194,7 +194,7 @@ size_t basket_const_bytes(int D)
 template <int D>
 static void offsets_of(size_t *L, size_t *drift, size_t *ws0, size_t *w, size_t *s0)
 {
-    *L = offsetof(BasketConst<D>, L);
+    *L = offsetof(BasketConst<D>, Lp);
     *drift = offsetof(BasketConst<D>, drift);
     *ws0 = offsetof(BasketConst<D>, ws0);
     *w = offsetof(BasketConst<D>, w);

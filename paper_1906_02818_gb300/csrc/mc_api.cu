@@ -684,13 +684,19 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             P->cst.assign(basket_const_bytes(D), 0);
             size_t oL, oDr, oWs, oW, oS;
             basket_const_offsets(D, &oL, &oDr, &oWs, &oW, &oS);
-            float *cL = reinterpret_cast<float *>(P->cst.data() + oL);
+            float *cL = reinterpret_cast<float *>(P->cst.data() + oL);  // column pairs, see BasketConst
             float *cDr = reinterpret_cast<float *>(P->cst.data() + oDr);
             float *cWs = reinterpret_cast<float *>(P->cst.data() + oWs);
             float *cW = reinterpret_cast<float *>(P->cst.data() + oW);
             float *cS = reinterpret_cast<float *>(P->cst.data() + oS);
+            for (int k = 0; k < d; ++k)
+                for (int q = k / 2; q < D / 2; ++q)
+                    for (int h = 0; h < 2; ++h) {
+                        const int a = 2 * q + h;  // row; zero above the diagonal and beyond d
+                        if (a >= k && a < d)
+                            cL[2 * (basket_pair_base(D, k) + q - k / 2) + h] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + k];
+                    }
             for (int a = 0; a < d; ++a) {
-                for (int k = 0; k <= a; ++k) cL[a * (a + 1) / 2 + k] = Lp[static_cast<size_t>(a) * (a + 1) / 2 + k];
                 const double w = m->weights ? m->weights[a] : 1.0 / d;
                 cDr[a] = drift[a];
                 cWs[a] = static_cast<float>(w * m->s0[a]);

@@ -41,13 +41,22 @@ struct Gbm1dArgs {
     ReduceArgs red;
 };
 
-// Correlated basket of at most D assets with the Cholesky factor in the
-// launch-parameter block (constant bank): packed lower triangle of
-// Lhat = c sqrt(dt) diag(sigma) Lrho (c = log2(e) for log-Euler, 1 for Euler),
-// row a at offset a(a+1)/2.  Entries for assets >= d are zero.
+// Correlated basket of at most D assets (D even) with the Cholesky factor in
+// the launch-parameter block (constant bank): the lower triangle of
+// Lhat = c sqrt(dt) diag(sigma) Lrho (c = log2(e) for log-Euler, 1 for Euler)
+// as column pairs for packed FP32x2 FMAs: column k holds the row pairs
+// (2q, 2q + 1), q = k/2 .. D/2 - 1, low half row 2q, at pair
+// basket_pair_base(D, k) + q - k/2 (row 2q = k - 1 of the first pair is the
+// zero above the diagonal).  Entries for assets >= d are zero.
+__host__ __device__ constexpr int basket_pair_count(int D) { return D * D / 4 + D / 2; }
+__host__ __device__ constexpr int basket_pair_base(int D, int k)
+{
+    // sum over k' < k of (D/2 - floor(k'/2))
+    return k * (D / 2) - (k / 2) * ((k / 2) - 1) - ((k & 1) ? k / 2 : 0);
+}
 template <int D>
 struct BasketConst {
-    float L[D * (D + 1) / 2];
+    unsigned long long Lp[basket_pair_count(D)];
     float drift[D];  // log-Euler: log2(e) (r - sigma_a^2/2) dt; Euler: r dt
     float ws0[D];    // w_a * S0_a
     float w[D];
