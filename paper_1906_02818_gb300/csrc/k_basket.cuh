@@ -21,40 +21,9 @@ const void *basket_select_scheme(const BasketArgs &a);
 #ifdef GBMC_BASKET_IMPL
 namespace basket_detail {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;        // slots of the reduction (at most 8 warps)
+constexpr int kLaunchBlock = 128;  // the launch's block (mc_api); 5 blocks, 20 warps, per SM
 
-// Packed FP32 pairs (low = even asset, high = odd asset).
-using f32x2 = unsigned long long;
-__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 fadd2(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 pack2(float lo, float hi)
-{
-    f32x2 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ float lo_of(f32x2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi_of(f32x2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
 __device__ __forceinline__ float elem(const f32x2 *v, int j) { return (j & 1) ? hi_of(v[j >> 1]) : lo_of(v[j >> 1]); }
 
 struct Stats {
@@ -74,7 +43,7 @@ __device__ __forceinline__ void accumulate_payoffs(AccSlot *s_acc, const PayoffS
 
 // ------------------------------ FP32 basket -------------------------------
 template <int D, int SCHEME, bool STATS, bool SAVE, bool EXACT>
-__global__ void __launch_bounds__(kBlock) basket_fp32_kernel(const __grid_constant__ BasketArgs a, const BasketConst<D> c)
+__global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __grid_constant__ BasketArgs a, const BasketConst<D> c)
 {
     __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];

@@ -3,9 +3,10 @@
 // Sec. II.A.2 for a tile of 64 paths as a register-tiled SIMT product.
 //   * CTA = 64 paths x D assets (D = 128, 256 or 512, zero-padded), 512
 //     threads; thread (pg, ag) owns paths 4 pg .. 4 pg + 3 and the assets
-//     128 j + 4 ag .. + 3 (j < D / 128): 4 x D / 32 running sums in registers,
-//     acc[p][a] = sum over steps of (Lhat z)_a, Lhat = log2(e) sqrt(dt)
-//     diag(sigma) Lrho.
+//     128 j + 4 ag .. + 3 (j < D / 128): 4 x D / 32 running sums in registers
+//     as asset pairs, acc[p][a] = sum over steps of (Lhat z)_a, Lhat =
+//     log2(e) sqrt(dt) diag(sigma) Lrho, accumulated by packed FP32x2 FMAs
+//     (one instruction for two assets of one path; each lane an FP32 fma).
 //   * per step: the CTA draws the 64 x d normals into shared memory
 //     (z[k][path], consecutive threads on consecutive paths), then streams
 //     Lhat^T in chunks of 16 rows (cp.async double buffer) and accumulates;
@@ -30,6 +31,9 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Element e (0..3) of a thread's four consecutive assets held as two pairs.
+__device__ __forceinline__ float accel(const f32x2 *pr, int e) { return (e & 1) ? hi_of(pr[e >> 1]) : lo_of(pr[e >> 1]); }
+
 template <int D>
 __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_constant__ BigArgs a)
 {
@@ -49,13 +53,13 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_c
     const int nchunks = (d + kKC - 1) / kKC;
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        float acc[4][J][4];
+        f32x2 acc2[4][J][2];  // [path][asset group][asset pair]
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int j = 0; j < J; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[p][j][e] = 0.0f;
+                for (int e = 0; e < 2; ++e) acc2[p][j][e] = pack2(0.0f, 0.0f);
         // RNG mapping: path t % 64, normals [q*D/8, (q+1)*D/8) with q = t / 64
         const int rp = t & (kP - 1), rq = t >> 6;
         const int64_t rnl = tile * kP + rp;
@@ -100,16 +104,16 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_c
 #pragma unroll 4
                 for (int kk = 0; kk < kKC; ++kk) {
                     const float4 zv = *reinterpret_cast<const float4 *>(zs + (k0 + kk) * kP + 4 * pg);
-                    const float zz[4] = {zv.x, zv.y, zv.z, zv.w};
+                    const f32x2 zz[4] = {pack2(zv.x, zv.x), pack2(zv.y, zv.y), pack2(zv.z, zv.z), pack2(zv.w, zv.w)};
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         if (128 * j + 127 < k0) continue;  // block above the diagonal chunk: zero
-                        const float4 lv = *reinterpret_cast<const float4 *>(Lc + kk * D + 128 * j + 4 * ag);
-                        const float ll[4] = {lv.x, lv.y, lv.z, lv.w};
+                        const ulonglong2 lv = *reinterpret_cast<const ulonglong2 *>(Lc + kk * D + 128 * j + 4 * ag);
 #pragma unroll
-                        for (int p = 0; p < 4; ++p)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[p][j][e] = fmaf(ll[e], zz[p], acc[p][j][e]);
+                        for (int p = 0; p < 4; ++p) {
+                            acc2[p][j][0] = ffma2(lv.x, zz[p], acc2[p][j][0]);
+                            acc2[p][j][1] = ffma2(lv.y, zz[p], acc2[p][j][1]);
+                        }
                     }
                 }
                 __syncthreads();  // everyone done with chunk c before it is overwritten
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_c
                 if (col < d) {
 #pragma unroll
                     for (int p = 0; p < 4; ++p)
-                        Ux[p] = fmaf(a.ws0[col], ex2_approx(fmaf(static_cast<float>(M), a.drift[col], acc[p][j][e])), Ux[p]);
+                        Ux[p] = fmaf(a.ws0[col], ex2_approx(fmaf(static_cast<float>(M), a.drift[col], accel(acc2[p][j], e))), Ux[p]);
                 }
             }
         // sum over the 32 asset groups of each path (the lanes of one warp)
@@ -165,10 +169,10 @@ __global__ void __launch_bounds__(kThreads, 1) basket_wide_kernel(const __grid_c
                     if (col < d) {
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
-                            const float S = a.s0[col] * ex2_approx(fmaf(static_cast<float>(M), a.drift[col], acc[p][j][e]));
+                            const float S = a.s0[col] * ex2_approx(fmaf(static_cast<float>(M), a.drift[col], accel(acc2[p][j], e)));
                             const float dl = gs[p] * a.w[col] * S / a.s0[col];
                             // sqrt(dt) (Lrho W)_col = acc / (log2(e) sigma_col)
-                            const float vg = gs[p] * a.w[col] * S * fmaf(-a.sigma[col], a.T, acc[p][j][e] / (kLog2e * a.sigma[col]));
+                            const float vg = gs[p] * a.w[col] * S * fmaf(-a.sigma[col], a.T, accel(acc2[p][j], e) / (kLog2e * a.sigma[col]));
                             d1 += dl; d2 += dl * dl; v1 += vg; v2 += vg * vg;
                         }
                     }

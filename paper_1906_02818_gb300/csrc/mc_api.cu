@@ -673,6 +673,7 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             resident = basket_tc_occupancy(P->prec, ta) * di.sms;
         } else {
             P->kk = K_BASKET_FP32;
+            P->block = 128;  // the kernel's launch bounds: 5 blocks of 128 per SM
             MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
             std::vector<float> Lp(tri), drift(d);
             MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
