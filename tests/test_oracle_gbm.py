@@ -173,3 +173,28 @@ def test_path_offset_selects_streams(orc):
     a = orc.gbm_payoffs(100.0, 0.2, 0.05, 1.0, 8, 100, [dict(kind="call", strike=100.0)])
     b = orc.gbm_payoffs(100.0, 0.2, 0.05, 1.0, 8, 40, [dict(kind="call", strike=100.0)], path_offset=60)
     assert np.array_equal(a[0, 60:], b[0])
+
+
+def test_mean_se_definition(orc):
+    """Eq. 3's estimator and its standard error against their textbook
+    forms: mean = sum f / N, se = sample standard deviation / sqrt(N)
+    (np.std with ddof = 1), on small exact cases and on random vectors,
+    including one with a large common offset (the compensated sums keep the
+    mean to rounding)."""
+    import math
+    m, se = orc.mean_se([1.0, 2.0, 3.0, 4.0])
+    assert m == 2.5 and abs(se - math.sqrt(5.0 / 3.0) / 2.0) <= 1e-15
+    m, se = orc.mean_se([7.0])
+    assert m == 7.0 and se == 0.0
+    m, se = orc.mean_se([3.0, 5.0])
+    assert m == 4.0 and se == 1.0
+    m, se = orc.mean_se(np.full(1000, 0.1))
+    assert abs(m - 0.1) <= 1e-16 and se <= 1e-9
+    rng = np.random.default_rng(9)
+    for n, off in ((10, 0.0), (1000, 0.0), (100_000, 0.0), (4096, 1e6)):
+        f = off + rng.standard_normal(n) * 3.0
+        m, se = orc.mean_se(f)
+        want_m = math.fsum(f) / n
+        want_se = np.std(f, ddof=1) / math.sqrt(n)
+        assert abs(m - want_m) <= 1e-15 * max(1.0, abs(want_m))
+        assert abs(se - want_se) <= (1e-9 if off == 0.0 else 1e-3) * want_se, (n, off, se, want_se)
