@@ -777,6 +777,7 @@ const char *mc_last_error(void) { return g_err.c_str(); }
 int mc_plan_create(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
                    mc_plan **plan, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: plan set-up");
     if (!plan) return fail(MC_EINVAL, "plan is NULL");
     *plan = nullptr;
     if (n_payoff < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
@@ -798,6 +799,7 @@ int mc_plan_create(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff
 
 int mc_plan_execute(mc_plan *plan, mc_result *dev_out, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: plan execute");
     if (!plan) return fail(MC_EINVAL, "plan is NULL");
     if (!dev_out) return fail(MC_EINVAL, "dev_out is NULL");
     int dev = -1;
@@ -852,6 +854,7 @@ int mc_combine(const double *moments, int32_t n_payoff, mc_result *out)
 int mc_price(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
              mc_result *out, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_price");
     if (!out) return fail(MC_EINVAL, "out is NULL");
     mc_plan *P = nullptr;
     int rc = mc_plan_create(model, cfg, payoffs, n_payoff, &P, stream);
@@ -886,6 +889,7 @@ int32_t mc_greek_count(const mc_model *model)
 int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, mc_result *prices,
               mc_result *greeks, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_greeks");
     int rc;
     if (!greeks) return fail(MC_EINVAL, "greeks is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
@@ -1003,6 +1007,7 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
 int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay, mc_result *price, mc_result *dl,
                    mc_result *drho, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_corr_greeks");
     int rc;
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
     if (!pay) return fail(MC_EINVAL, "payoff is NULL");
@@ -1104,6 +1109,7 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
 int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, int64_t paths_ref,
                   mc_mlmc_result *out, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_price_mlmc");
     int rc;
     if (!out) return fail(MC_EINVAL, "out is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
@@ -1219,6 +1225,7 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
 int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int32_t np, int32_t reps,
                  mc_result *out, double *rep_means, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_price_qmc");
     int rc;
     if (!out) return fail(MC_EINVAL, "out is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
@@ -1326,6 +1333,7 @@ int mc_price_qmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, 
 
 int mc_simulate(const mc_model *model, const mc_sim_cfg *cfg, int32_t save_every, float *dev_out, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_simulate");
     if (!dev_out) return fail(MC_EINVAL, "dev_out is NULL");
     if (!cfg) return fail(MC_EINVAL, "cfg is NULL");
     if (save_every < 1 || cfg->steps < 1 || cfg->steps % save_every)

@@ -130,18 +130,8 @@ __device__ __forceinline__ f32x2 pack2(float lo, float hi)
     asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
     return d;
 }
-__device__ __forceinline__ float lo_of(f32x2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi_of(f32x2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
+__device__ __forceinline__ float lo_of(f32x2 v) { return __uint_as_float(static_cast<uint32_t>(v)); }
+__device__ __forceinline__ float hi_of(f32x2 v) { return __uint_as_float(static_cast<uint32_t>(v >> 32)); }
 // The four normals of block q of stream (path) n.
 __device__ __forceinline__ float4 normals4(uint64_t q, uint64_t n, const RoundKeys &rk)
 {

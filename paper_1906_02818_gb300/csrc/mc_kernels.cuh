@@ -6,7 +6,19 @@
 
 #include "mc_device.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace gbmc {
+
+// A named NVTX range around a host phase of an entry point (set-up, launch,
+// read-back), for timeline profilers; header-only, inert unless a profiler
+// attaches.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Common per-launch fields of every path kernel.
 struct PathRun {

@@ -192,6 +192,7 @@ int mc_mlp_set_params(mc_mlp *net, const float *host)
 
 int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int32_t precision, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_mlp_forward");
     int rc;
     if ((rc = check_net(net))) return rc;
     if (!dev_x || !dev_y || n < 1) return set_last_error(MC_EINVAL, "x, y must be set and n >= 1");
@@ -223,6 +224,7 @@ int mc_mlp_forward(mc_mlp *net, const float *dev_x, int64_t n, float *dev_y, int
 int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, double *loss, float *host_grad,
                      void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_mlp_loss_grad");
     int rc;
     if ((rc = check_net(net))) return rc;
     if (!dev_x || !dev_t || n < 1) return set_last_error(MC_EINVAL, "x, t must be set and n >= 1");
@@ -243,6 +245,7 @@ int mc_mlp_loss_grad(mc_mlp *net, const float *dev_x, const float *dev_t, int64_
 int mc_mlp_train(mc_mlp *net, const float *dev_x, const float *dev_t, int64_t n, int32_t epochs, int32_t batch,
                  float lr, double *last_epoch_loss, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_mlp_train");
     int rc;
     if ((rc = check_net(net))) return rc;
     if (!dev_x || !dev_t || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))
@@ -327,6 +330,7 @@ int mc_mlp_train_d(mc_mlp *net, const float *dev_x, const float *dev_t, const fl
                    const mc_mlp_dloss *dl, int32_t epochs, int32_t batch, float lr, double *last_epoch_loss,
                    void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_mlp_train_d");
     int rc;
     if ((rc = check_net(net)) || (rc = check_dloss(net, dl))) return rc;
     if (!dev_x || !dev_t || (dl->n_dir > 0 && !dev_g) || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f))

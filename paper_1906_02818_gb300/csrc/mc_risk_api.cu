@@ -59,6 +59,7 @@ extern "C" {
 static int labels_common(int64_t n_points, const float *dev_points, int32_t paths, int32_t steps_per_year,
                          uint64_t seed, float *dev_labels, float *dev_inputs, float *dev_dlabels, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: surrogate labels");
     if (n_points < 1 || !dev_points || !dev_labels) return fail(MC_EINVAL, "points and labels must be set, n >= 1");
     if (n_points > (int64_t(1) << 36)) return fail(MC_EINVAL, "too many points");
     if (paths < 1 || paths > 65536) return fail(MC_EINVAL, "paths must lie in [1, 65536]");
@@ -85,6 +86,7 @@ int mc_surrogate_label_greeks(int64_t n_points, const float *dev_points, int32_t
 
 int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *res, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_tail");
     if (!dev_pnl || !res) return fail(MC_EINVAL, "dev_pnl and result must be set");
     if (n < 1 || n > (int64_t(1) << 24)) return fail(MC_EINVAL, "n outside [1, 2^24]");
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(MC_EINVAL, "alpha must lie in (0, 1)");
@@ -108,6 +110,7 @@ int mc_tail(const double *dev_pnl, int64_t n, double alpha, mc_risk_result *res,
 
 int mc_risk(const mc_portfolio *pf, const mc_risk_cfg *cf, mc_risk_result *res, double *host_pnl, void *stream)
 {
+    gbmc::NvtxRange nvtx_("gbmc: mc_risk");
     if (!pf || !cf || !res) return fail(MC_EINVAL, "portfolio, cfg and result must be set");
     const int d = pf->n_under, no = pf->n_opt;
     if (d < 1 || d > kRiskMaxUnder) return fail(MC_EINVAL, "n_under outside [1, 64]");
