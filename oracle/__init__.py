@@ -72,25 +72,31 @@ HESTON_PARAM_ORDER = ("s0", "v0", "r", "kappa", "theta", "xi", "rho")
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (plain gcc, no CUDA)."""
+    """Compile oracle.c into liboracle.so next to it (plain gcc, no CUDA).
+    With GBMC_ORACLE_SANITIZE=1 the AddressSanitizer + UndefinedBehaviorSanitizer
+    build liboracle_asan.so instead (the sanitizer tests load it with the
+    sanitizer runtimes preloaded)."""
+    san = os.environ.get("GBMC_ORACLE_SANITIZE") == "1"
+    path = _LIB_PATH.replace("liboracle.so", "liboracle_asan.so") if san else _LIB_PATH
     with _lock:
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-            return _LIB_PATH
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+        if (not force and os.path.exists(path)
+                and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+            return path
+        tmp = path + f".tmp{os.getpid()}"
+        opt = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+               "-fno-omit-frame-pointer"] if san else ["-O2"]
+        cmd = ["gcc", *opt, "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                "-std=c11", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-        return _LIB_PATH
+        os.replace(tmp, path)
+        return path
 
 
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_LIB_PATH)
+    lib = ctypes.CDLL(build())
     P = ctypes.POINTER
     d_p, i_p, u32_p = P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint32)
     i64, u64, i32, dbl = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double

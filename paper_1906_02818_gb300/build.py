@@ -43,16 +43,29 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+# Host-code sanitizer variant (AddressSanitizer + UndefinedBehaviorSanitizer
+# on the host side of every translation unit: argument checks, plan set-up,
+# marshalling); the device code is unchanged.  Built apart from the release
+# library and loaded through GBMC_LIBRARY by the sanitizer tests.
+SANITIZE_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+                  "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=undefined"]
+SANITIZE_LIB = os.path.join(ROOT, "_build", "asan", "libgbmc.so")
+
+
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, sanitize: bool = False) -> str:
+    lib = SANITIZE_LIB if sanitize else LIB
+    obj_dir = os.path.join(ROOT, "_build", "asan", "obj") if sanitize else OBJ
+    if not force and (up_to_date() if not sanitize else
+                      os.path.exists(lib) and all(os.path.getmtime(f) <= os.path.getmtime(lib) for f in _inputs())):
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
+    extra = SANITIZE_FLAGS if sanitize else []
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.splitext(os.path.basename(src))[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, os.path.splitext(os.path.basename(src))[0] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -62,13 +75,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     with cf.ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc, *ARCH, "-shared", *extra, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -10,7 +10,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgbmc.so")
+# GBMC_LIBRARY selects another build of the same library (the sanitizer
+# build of the tests); by default the in-tree release build.
+LIB_PATH = os.environ.get("GBMC_LIBRARY") or os.path.join(_PKG, "libgbmc.so")
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 
@@ -170,7 +172,7 @@ def lib(build: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    if build:
+    if build and not os.environ.get("GBMC_LIBRARY"):
         from . import build as _build
         _build.build()
     if not os.path.exists(LIB_PATH):
