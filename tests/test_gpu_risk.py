@@ -201,7 +201,8 @@ def test_greek_trained_surrogate_matches_nested_at_a_fraction_of_the_time(gb):
     portfolio revaluation), at equal accuracy.  A surrogate trained by the
     library's kernels on GPU Monte Carlo prices and pathwise Greeks (2^19
     points of the parameter box, 2^12 paths each; delta and vega labels on
-    the European half) revalues the 1024-option book on 16384 scenarios.  The
+    the European half; BF16 inference) revalues the 1024-option book on
+    16384 scenarios.  The
     yardstick is nested Monte Carlo with 2^14 inner paths on the same
     scenarios.  The surrogate's per-scenario PnL error must not exceed that of
     nested Monte Carlo with 2^12 inner paths (its error against the exact
@@ -228,8 +229,8 @@ def test_greek_trained_surrogate_matches_nested_at_a_fraction_of_the_time(gb):
 
     ref, _ = timed(method="nested", inner_paths=1 << 14)
     n12, t12 = timed(method="nested", inner_paths=1 << 12)
-    gb.risk(pf, n_scen=ns, method="surrogate", surrogate=net)  # warm-up (weights image)
-    sur, ts = timed(method="surrogate", surrogate=net)
+    gb.risk(pf, n_scen=ns, method="surrogate", surrogate=net, surrogate_precision="bf16")  # warm-up (weight image)
+    sur, ts = timed(method="surrogate", surrogate=net, surrogate_precision="bf16")
     rmse = lambda r: float(np.sqrt(np.mean((r["pnl"] - ref["pnl"]) ** 2)))  # noqa: E731
     e12 = rmse(n12) / np.sqrt(1.0 - 0.25)
     es = rmse(sur)
