@@ -158,6 +158,21 @@ int mc_release_cache(void);
 const char *mc_last_error(void);
 
 /*
+ * mc_debug_status -- the bounds checks of a debug build (compiled with
+ * GBMC_DEBUG).  In that build the kernels check the index of their accesses
+ * to caller buffers and checkpoints (materialised paths, Heston adjoint
+ * checkpoints, network outputs, random-stream outputs, training labels)
+ * against the buffer's extent; an access outside is skipped and recorded
+ * (no trap: the kernel and the context carry on).  This call synchronises
+ * the device, returns the number of skipped accesses since the previous
+ * call, the site code and index of the first one (0 and 0 if none), and
+ * clears them.  Site codes: 1 1-D GBM paths, 2 basket paths, 3 Heston paths,
+ * 4 / 5 checkpoint store / load, 6 network output, 7 Philox words,
+ * 8 normals, 9 labels.  A release build returns MC_EUNSUPPORTED.
+ */
+int mc_debug_status(uint32_t *violations, uint32_t *first_site, int64_t *first_index);
+
+/*
  * The random stream (Sec. IV.A: keyed counter-based Philox4x32-10; Sec. VI.D:
  * Box-Muller), written out by the device functions every path kernel draws
  * from, e.g. to check them bit for bit against another implementation or to

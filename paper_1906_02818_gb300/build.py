@@ -50,18 +50,23 @@ def up_to_date() -> bool:
 SANITIZE_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
                   "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=undefined"]
 SANITIZE_LIB = os.path.join(ROOT, "_build", "asan", "libgbmc.so")
+# Debug variant: the device code's bounds checks (GBMC_DEBUG, mc_debug_status).
+DEBUG_FLAGS = ["-DGBMC_DEBUG=1"]
+DEBUG_LIB = os.path.join(ROOT, "_build", "debug", "libgbmc.so")
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None, sanitize: bool = False) -> str:
-    lib = SANITIZE_LIB if sanitize else LIB
-    obj_dir = os.path.join(ROOT, "_build", "asan", "obj") if sanitize else OBJ
-    if not force and (up_to_date() if not sanitize else
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, sanitize: bool = False,
+          debug: bool = False) -> str:
+    variant = "asan" if sanitize else ("debug" if debug else None)
+    lib = {None: LIB, "asan": SANITIZE_LIB, "debug": DEBUG_LIB}[variant]
+    obj_dir = os.path.join(ROOT, "_build", variant, "obj") if variant else OBJ
+    if not force and (up_to_date() if not variant else
                       os.path.exists(lib) and all(os.path.getmtime(f) <= os.path.getmtime(lib) for f in _inputs())):
         return lib
     os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
-    extra = SANITIZE_FLAGS if sanitize else []
+    extra = SANITIZE_FLAGS if sanitize else (DEBUG_FLAGS if debug else [])
 
     def compile_one(src):
         obj = os.path.join(obj_dir, os.path.splitext(os.path.basename(src))[0] + ".o")

@@ -67,8 +67,11 @@ __global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __gr
 #pragma unroll
             for (int q = 0; q < H; ++q)
                 x[q] = (SCHEME == MC_LOG_EULER) ? pack2(0.0f, 0.0f) : pack2(c.s0[2 * q], c.s0[2 * q + 1]);
+            const int64_t save_len = (static_cast<int64_t>(M / a.run.save_every) + 1) * d * a.run.paths;
             if (SAVE) {
-                for (int j = 0; j < d; ++j) a.run.save[static_cast<int64_t>(j) * a.run.paths + nl] = c.s0[j];
+                for (int j = 0; j < d; ++j)
+                    if (GBMC_IN_BOUNDS(static_cast<int64_t>(j) * a.run.paths + nl, save_len, kDbgBasketSave))
+                        a.run.save[static_cast<int64_t>(j) * a.run.paths + nl] = c.s0[j];
             }
             NormalReader rd;
             rd.init(n, a.run.rk);
@@ -126,7 +129,8 @@ __global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __gr
                         const float xj = elem(x, j);
                         const float Sj = (SCHEME == MC_LOG_EULER) ? c.s0[j] * ex2_approx(xj) : xj;
                         if (STATS) u = fmaf(c.w[j], Sj, u);
-                        if (SAVE && ((i + 1) % a.run.save_every) == 0 && j < d)
+                        if (SAVE && ((i + 1) % a.run.save_every) == 0 && j < d &&
+                            GBMC_IN_BOUNDS((slot * d + j) * a.run.paths + nl, save_len, kDbgBasketSave))
                             a.run.save[(slot * d + j) * a.run.paths + nl] = Sj;
                     }
                     if (STATS) st.add(u);

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kBlock, 8) gbm1d_kernel(const __grid_constant_
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             float y = (SCHEME == MC_LOG_EULER) ? 0.0f : a.s0;  // log2(S/S0) or S
             float bmax = 0.0f, bmin = 0.0f;                    // bridge extremes of y
-            if (SAVE) a.run.save[nl] = a.s0;
+            const int64_t save_len = (static_cast<int64_t>(M / a.run.save_every) + 1) * a.run.paths;
+            if (SAVE && GBMC_IN_BOUNDS(nl, save_len, kDbgGbm1dSave)) a.run.save[nl] = a.s0;
             const int nq = (M + 3) >> 2;
             for (int q = 0; q < nq; ++q) {
                 const float4 z4 = normals4(static_cast<uint64_t>(q), n, a.run.rk);
@@ -99,8 +100,10 @@ __global__ void __launch_bounds__(kBlock, 8) gbm1d_kernel(const __grid_constant_
                         if (STATS || SAVE) {
                             const float S = (SCHEME == MC_LOG_EULER) ? a.s0 * ex2_approx(y) : y;
                             if (STATS) st.add(S);
-                            if (SAVE && ((i + 1) % a.run.save_every) == 0)
-                                a.run.save[static_cast<int64_t>((i + 1) / a.run.save_every) * a.run.paths + nl] = S;
+                            if (SAVE && ((i + 1) % a.run.save_every) == 0) {
+                                const int64_t o = static_cast<int64_t>((i + 1) / a.run.save_every) * a.run.paths + nl;
+                                if (GBMC_IN_BOUNDS(o, save_len, kDbgGbm1dSave)) a.run.save[o] = S;
+                            }
                         }
                     }
                 }

@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const __grid_con
             // forward pass with checkpoints every K steps
             float x = 0.0f, v = a.v0, sS = 0.0f;
             for (int s = 0; s < nseg; ++s) {
-                a.ckpt[(static_cast<int64_t>(s) * 2) * gthreads + tid] = x;
-                a.ckpt[(static_cast<int64_t>(s) * 2 + 1) * gthreads + tid] = v;
+                if (GBMC_IN_BOUNDS((static_cast<int64_t>(s) * 2 + 1) * gthreads + tid,
+                                   static_cast<int64_t>(nseg) * 2 * gthreads, kDbgCkptStore)) {
+                    a.ckpt[(static_cast<int64_t>(s) * 2) * gthreads + tid] = x;
+                    a.ckpt[(static_cast<int64_t>(s) * 2 + 1) * gthreads + tid] = v;
+                }
                 const int e = min(M, (s + 1) * K);
                 for (int i = s * K; i < e; ++i) {
                     const float z1 = rd.get(2 * static_cast<uint64_t>(i));
@@ -163,8 +166,12 @@ __global__ void __launch_bounds__(kBlock) heston_adjoint_kernel(const __grid_con
             float lv = 0.0f, mx = uT * inv_m, mv = 0.0f;
             float gEr = 0, gEk = 0, gEt = 0, gEx = 0, gEp = 0, gAr = 0, gAk = 0, gAt = 0, gAx = 0, gAp = 0;
             for (int s = nseg - 1; s >= 0; --s) {
-                float xc = a.ckpt[(static_cast<int64_t>(s) * 2) * gthreads + tid];
-                float vc = a.ckpt[(static_cast<int64_t>(s) * 2 + 1) * gthreads + tid];
+                float xc = 0.0f, vc = 0.0f;
+                if (GBMC_IN_BOUNDS((static_cast<int64_t>(s) * 2 + 1) * gthreads + tid,
+                                   static_cast<int64_t>(nseg) * 2 * gthreads, kDbgCkptLoad)) {
+                    xc = a.ckpt[(static_cast<int64_t>(s) * 2) * gthreads + tid];
+                    vc = a.ckpt[(static_cast<int64_t>(s) * 2 + 1) * gthreads + tid];
+                }
                 const int b = s * K, e = min(M, (s + 1) * K);
                 for (int i = b; i < e; ++i) {  // recompute the segment's states
                     xs[i - b] = xc;

@@ -32,9 +32,10 @@ __global__ void __launch_bounds__(kBlock) heston_kernel(const __grid_constant__ 
         if (valid) {
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             float y = 0.0f, v = a.v0, sum = 0.0f, S = a.s0;
+            const int64_t save_len = (static_cast<int64_t>(M / a.run.save_every) + 1) * 2 * a.run.paths;
             if (SAVE) {
-                a.run.save[nl] = a.s0;
-                a.run.save[a.run.paths + nl] = a.v0;
+                if (GBMC_IN_BOUNDS(nl, save_len, kDbgHestonSave)) a.run.save[nl] = a.s0;
+                if (GBMC_IN_BOUNDS(a.run.paths + nl, save_len, kDbgHestonSave)) a.run.save[a.run.paths + nl] = a.v0;
             }
             const int nq = (M + 1) >> 1;
             for (int q = 0; q < nq; ++q) {
@@ -56,8 +57,10 @@ __global__ void __launch_bounds__(kBlock) heston_kernel(const __grid_constant__ 
                             umin = fminf(umin, S);
                             if (SAVE && ((i + 1) % a.run.save_every) == 0) {
                                 const int64_t slot = (i + 1) / a.run.save_every;
-                                a.run.save[(slot * 2) * a.run.paths + nl] = S;
-                                a.run.save[(slot * 2 + 1) * a.run.paths + nl] = v;
+                                if (GBMC_IN_BOUNDS((slot * 2 + 1) * a.run.paths + nl, save_len, kDbgHestonSave)) {
+                                    a.run.save[(slot * 2) * a.run.paths + nl] = S;
+                                    a.run.save[(slot * 2 + 1) * a.run.paths + nl] = v;
+                                }
                             }
                         }
                     }

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bf16_kernel(const Args a)
                     lane_sync(T);
                     if (half == 0 && valid) {
                         const float yv = s_part[T][0][row] + s_part[T][1][row] + __ldg(a.params + a.b_out);
-                        a.y[rg] = live ? yv : __int_as_float(0x7fc00000);
+                        if (GBMC_IN_BOUNDS(rg, a.n, kDbgMlpOut)) a.y[rg] = live ? yv : __int_as_float(0x7fc00000);
                     }
                     lane_sync(T);  // s_part is reused by the next tile
                 }

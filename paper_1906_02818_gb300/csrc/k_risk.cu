@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) label_kernel(int64_t npts, const float *_
             for (int k = 0; k < (GREEKS ? 3 : 1); ++k)
                 for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t[k] += s_red[k][w];
             const double disc = exp(-static_cast<double>(r) * tau) / paths;
-            labels[p] = static_cast<float>(disc * t[0]);
+            if (GBMC_IN_BOUNDS(p, npts, kDbgLabelOut)) labels[p] = static_cast<float>(disc * t[0]);
             if (GREEKS) {
                 dlabels[2 * p] = greeks ? static_cast<float>(disc * t[1]) : __int_as_float(0x7fc00000);
                 dlabels[2 * p + 1] = greeks ? static_cast<float>(disc * t[2]) : __int_as_float(0x7fc00000);

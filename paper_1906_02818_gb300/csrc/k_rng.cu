@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) philox_words_kernel(uint64_t n, uint64_t 
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < blocks; i += stride) {
         const uint64_t q = q0 + static_cast<uint64_t>(i);
-        out[i] = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
+        if (GBMC_IN_BOUNDS(i, blocks, kDbgPhiloxOut)) out[i] = philox4x32_10(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
                                           static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)),
                                rk);
     }
@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(256) normals_kernel(uint64_t n, uint64_t j0, i
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const uint64_t j = 4 * q + l;
-            if (j >= j0 && j - j0 < static_cast<uint64_t>(count)) out[j - j0] = v[l];
+            if (j >= j0 && j - j0 < static_cast<uint64_t>(count) &&
+                GBMC_IN_BOUNDS(static_cast<int64_t>(j - j0), count, kDbgNormalsOut))
+                out[j - j0] = v[l];
         }
     }
 }

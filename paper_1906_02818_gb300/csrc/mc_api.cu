@@ -328,6 +328,16 @@ uint32_t gbmc::mbar_wait_cap()
     return cap;
 }
 
+namespace {
+std::vector<gbmc::DebugReader> &debug_readers()
+{
+    static std::vector<gbmc::DebugReader> v;  // filled while the library loads
+    return v;
+}
+}  // namespace
+
+void gbmc::debug_register(DebugReader fn) { debug_readers().push_back(fn); }
+
 int gbmc::set_last_error(int code, const char *msg)
 {
     g_err = msg ? msg : "";
@@ -815,6 +825,30 @@ int mc_plan_destroy(mc_plan *plan)
 }
 
 int mc_plan_launches(const mc_plan *plan) { return plan ? 1 : 0; }
+
+int mc_debug_status(uint32_t *violations, uint32_t *first_site, int64_t *first_index)
+{
+#ifdef GBMC_DEBUG
+    if (!violations || !first_site || !first_index) return fail(MC_EINVAL, "outputs must be set");
+    MC_CUDA(cudaDeviceSynchronize());
+    uint32_t total = 0;
+    unsigned long long first = 0;
+    for (DebugReader fn : debug_readers()) {
+        unsigned long long f = 0;
+        unsigned c = 0;
+        if (fn(&f, &c) != 0) return fail(MC_ECUDA, "reading a debug word failed");
+        total += c;
+        if (!first && f) first = f;
+    }
+    *violations = total;
+    *first_site = static_cast<uint32_t>(first >> 48);
+    *first_index = static_cast<int64_t>(first & 0xFFFFFFFFFFFFull);
+    return MC_OK;
+#else
+    (void)violations; (void)first_site; (void)first_index;
+    return fail(MC_EUNSUPPORTED, "this is a release build without bounds checks (build with GBMC_DEBUG)");
+#endif
+}
 
 // Eq. 3 over a union of disjoint path ranges.  A run over N paths reported
 // price = e^{-rT} S1 / N and se = e^{-rT} sqrt((S2 / N - (S1 / N)^2) / (N - 1))

@@ -8,6 +8,8 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "mc_debug.cuh"
+
 namespace gbmc {
 
 // A named NVTX range around a host phase of an entry point (set-up, launch,

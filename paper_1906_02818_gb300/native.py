@@ -131,6 +131,8 @@ SIGNATURES = [
                                ctypes.POINTER(McRiskResult), ctypes.c_void_p, ctypes.c_void_p]),
     ("mc_surrogate_labels", ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mc_debug_status", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_int64)]),
     ("mc_moments", ctypes.c_int, [ctypes.POINTER(McResult), ctypes.c_int32, ctypes.c_int64,
                                   ctypes.POINTER(ctypes.c_double)]),
     ("mc_combine", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(McResult)]),
