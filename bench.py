@@ -338,16 +338,27 @@ def config_c4(torch, gb, orc, hw, reps):
     from oracle import risk as orisk
     pts = torch.from_numpy(workloads.surrogate_points(1 << 20)).cuda()
     lab_paths = 1 << 13
-    t_lab, _, (lab, x) = time_call(torch, lambda: gb.surrogate_labels(pts, lab_paths, with_inputs=True), 1)
+    t_lab, _, (lab, dl, x) = time_call(torch, lambda: gb.surrogate_label_greeks(pts, lab_paths, with_inputs=True), 1)
+    epochs = sum(e for _, e in workloads.SURROGATE_SCHEDULE)
+    # the surrogate trained on prices and their pathwise delta / vega (FP32 products)
     net = gb.Mlp(5, 256, 4, workloads.mlp_init())
-    net.set_train_mode("tf32x3")
     losses = []
 
     def train():
         for lr, ep in workloads.SURROGATE_SCHEDULE:
-            losses.append(net.train(x, lab, epochs=ep, batch=4096, lr=lr))
+            losses.append(net.train_d(x, lab, dl, [0, 1], [1.0 / 0.55, 1.0 / 0.15], [0.2, 0.05], epochs=ep,
+                                      batch=4096, lr=lr))
     t_train, _, _ = time_call(torch, train, 1, warmup=0)
-    epochs = sum(e for _, e in workloads.SURROGATE_SCHEDULE)
+    # the same network and schedule on prices alone, three-pass TF32 tensor-core products
+    net_p = gb.Mlp(5, 256, 4, workloads.mlp_init())
+    net_p.set_train_mode("tf32x3")
+    losses_p = []
+
+    def train_p():
+        for lr, ep in workloads.SURROGATE_SCHEDULE:
+            losses_p.append(net_p.train(x, lab, epochs=ep, batch=4096, lr=lr))
+    t_train_p, _, _ = time_call(torch, train_p, 1, warmup=0)
+    net_p.close()
     pf = workloads.risk_portfolio()
     n_scen, n_opt = 1 << 16, len(pf["strike"])
     t_sur, _, sur = time_call(torch, lambda: gb.risk(pf, n_scen=n_scen, method="surrogate", surrogate=net,
@@ -372,14 +383,21 @@ def config_c4(torch, gb, orc, hw, reps):
     inner_path_steps = n_scen * (1 << 12) * float(sum(steps_u))
     return {"workload": "1024 options (512 European, 512 up-and-out daily) on 32 correlated GBMs, 1-day horizon, "
                         "2^16 scenarios, 99% VaR / CVaR; surrogate 5 -> 256 x 4 (SiLU) -> 1 trained on 2^20 Monte "
-                        "Carlo labels (2^13 paths each); nested 2^12 inner paths",
+                        "Carlo labels (2^13 paths each) and their pathwise delta / vega; nested 2^12 inner paths",
             "labels": {"ms": t_lab * 1e3, "points": 1 << 20, "paths_each": lab_paths,
                        "value": (1 << 20) * lab_paths * 252.5 / t_lab, "unit": UNIT},
-            "training": {"ms": t_train * 1e3, "epochs": epochs, "batch": 4096, "arithmetic": "three-pass TF32",
-                         "final_epoch_mse": losses[-1], "samples_per_s": (1 << 20) * epochs / t_train,
-                         "roofline_tensor": hw.tensor((1 << 20) * epochs * 3 * flop_row / t_train, "tf32",
-                                                      f"3 x {flop_row} flop per sample (forward, input and weight "
-                                                      "gradients)")},
+            "training": {"ms": t_train * 1e3, "epochs": epochs, "batch": 4096,
+                         "labels": "prices + pathwise delta and vega (weights 0.2, 0.05)",
+                         "arithmetic": "FP32 SIMT (forward with 2 input tangents, reverse through them)",
+                         "final_epoch_loss": losses[-1], "samples_per_s": (1 << 20) * epochs / t_train,
+                         "roofline_fma": hw.fma((1 << 20) * epochs * 9 * flop_row / 2 / t_train,
+                                                f"9 x {flop_row // 2} FMA per sample (3 stacked rows through forward, "
+                                                "input and weight gradients)")},
+            "training_prices_tf32x3": {"ms": t_train_p * 1e3, "epochs": epochs, "batch": 4096,
+                                       "final_epoch_mse": losses_p[-1],
+                                       "roofline_tensor": hw.tensor((1 << 20) * epochs * 3 * flop_row / t_train_p,
+                                                                    "tf32", f"3 x {flop_row} flop per sample "
+                                                                    "(forward, input and weight gradients)")},
             "surrogate": {"ms": t_sur * 1e3, "var": sur["var"], "cvar": sur["cvar"], "value": rows / t_sur,
                           "unit": "option revaluations/s", "precision": "bf16",
                           "roofline": hw.tensor(rows * flop_row / t_sur, "bf16", f"{flop_row} flop per revaluation")},
