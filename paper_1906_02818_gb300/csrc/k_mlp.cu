@@ -35,11 +35,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
                                                    float *__restrict__ Z, float *__restrict__ H, int ldc, int act,
                                                    int kchunk)
 {
-    __shared__ float As[kK][kT + 4];
-    __shared__ float Bs[kK][kT + 4];
+    // Rows of 68 floats (272 bytes) keep every 4-float group 16-byte aligned.
+    __shared__ __align__(16) float As[kK][kT + 4];
+    __shared__ __align__(16) float Bs[kK][kT + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.x * kT, n0 = blockIdx.y * kT;  // row tiles on x: up to 2^31 - 1 blocks
-    float acc[4][4] = {};
+    // acc2[i][h] holds the products of row i with columns 2h, 2h + 1 of this
+    // thread's 4 columns (packed FP32 pairs: two FMAs per instruction).
+    f32x2 acc2[4][2] = {};
     const int kb0 = blockIdx.z * kchunk, kend = min(K, kb0 + kchunk);
     if (gridDim.z > 1) {
         Z += static_cast<int64_t>(blockIdx.z) * M * ldc;
@@ -65,15 +68,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
-            float a[4], b[4];
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&Bs[k][tx * 4]);
+            const f32x2 ai[4] = {pack2(a.x, a.x), pack2(a.y, a.y), pack2(a.z, a.z), pack2(a.w, a.w)};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int i = 0; i < 4; ++i) {
+                acc2[i][0] = ffma2(ai[i], b.x, acc2[i][0]);
+                acc2[i][1] = ffma2(ai[i], b.y, acc2[i][1]);
+            }
         }
         __syncthreads();
     }
@@ -85,7 +87,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx * 4 + j;
             if (n >= N) continue;
-            const float v = acc[i][j] + (bias ? bias[n] : 0.0f);
+            const f32x2 pr = acc2[i][j >> 1];
+            const float v = ((j & 1) ? hi_of(pr) : lo_of(pr)) + (bias ? bias[n] : 0.0f);
             const int64_t o = static_cast<int64_t>(m) * ldc + n;
             if (Z) Z[o] = v;
             if (H) H[o] = act ? silu_f(v) : v;
