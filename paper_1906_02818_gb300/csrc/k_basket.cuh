@@ -7,6 +7,15 @@
 // held as asset pairs.  A scalar FMA with a 32-bit constant-bank operand
 // sustains a fraction of the FMA pipe's rate on this part; the 64-bit pair
 // operand carries two factor entries per instruction.
+//
+// Large runs launch one block of 640 threads per SM whose warps meet at a
+// block barrier after every four columns of a step, so that all warps of an
+// SM read the same few hundred bytes of the factor at a time; small runs
+// launch blocks of 128 (more SMs busy).  Either way every thread runs every
+// step (threads past the last path compute a path whose results are
+// dropped), which keeps the barriers uniform.  A factor staged in shared
+// memory instead was slower: each 16-byte shared load costs four cycles of
+// the shared-memory port, a quarter of the rate the packed FMAs need.
 #pragma once
 
 #include "mc_kernels.cuh"
@@ -21,8 +30,8 @@ const void *basket_select_scheme(const BasketArgs &a);
 #ifdef GBMC_BASKET_IMPL
 namespace basket_detail {
 
-constexpr int kBlock = 256;        // slots of the reduction (at most 8 warps)
-constexpr int kLaunchBlock = 128;  // the launch's block (mc_api); 5 blocks, 20 warps, per SM
+constexpr int kBlock = 640;        // slots of the reduction (at most 20 warps)
+constexpr int kLaunchBlock = 640;  // the largest launch block (mc_api: 640 or 128); 20 warps per SM
 
 __device__ __forceinline__ float elem(const f32x2 *v, int j) { return (j & 1) ? hi_of(v[j >> 1]) : lo_of(v[j >> 1]); }
 
@@ -43,7 +52,7 @@ __device__ __forceinline__ void accumulate_payoffs(AccSlot *s_acc, const PayoffS
 
 // ------------------------------ FP32 basket -------------------------------
 template <int D, int SCHEME, bool STATS, bool SAVE, bool EXACT>
-__global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __grid_constant__ BasketArgs a, const BasketConst<D> c)
+__global__ void __launch_bounds__(kLaunchBlock, 1) basket_fp32_kernel(const __grid_constant__ BasketArgs a, const BasketConst<D> c)
 {
     __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __gr
         float uT = 0.0f, avg = 0.0f;
         Stats st;
         st.init();
-        if (valid) {
+        if (valid || !SAVE) {  // every thread steps (block barriers below) unless it writes paths
             const uint64_t n = static_cast<uint64_t>(a.run.path_offset + nl);
             constexpr int H = D / 2;
             f32x2 x[H];  // asset pairs; log-Euler: log2(S_a / S0_a); Euler: S_a
@@ -88,12 +97,17 @@ __global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __gr
                     for (int q = 0; q < H; ++q) x[q] = fadd2(x[q], pack2(c.drift[2 * q], c.drift[2 * q + 1]));
                 }
                 // dW = Lhat z, column by column as the normals are produced;
-                // column k updates the pairs q >= k/2 with (z_k, z_k).
+                // column k updates the pairs q >= k/2 with (z_k, z_k).  The
+                // next block of four normals is drawn before this block's
+                // products (independent work while the SFU results arrive).
+                float4 znext = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (EXACT) znext = normals4(static_cast<uint64_t>(i) * (D / 4), n, a.run.rk);
 #pragma unroll
                 for (int kb = 0; kb < D / 4 + (D % 4 ? 1 : 0); ++kb) {
                     float zz[4];
                     if (EXACT) {
-                        const float4 z4 = normals4(static_cast<uint64_t>(i) * (D / 4) + kb, n, a.run.rk);
+                        const float4 z4 = znext;
+                        if (kb + 1 < D / 4) znext = normals4(static_cast<uint64_t>(i) * (D / 4) + kb + 1, n, a.run.rk);
                         zz[0] = z4.x; zz[1] = z4.y; zz[2] = z4.z; zz[3] = z4.w;
                     } else {
 #pragma unroll
@@ -115,13 +129,24 @@ __global__ void __launch_bounds__(kLaunchBlock, 5) basket_fp32_kernel(const __gr
                             }
                         }
                     }
+                    if (!SAVE) __syncthreads();
                 }
                 if (SCHEME == MC_EULER) {
 #pragma unroll
                     for (int q = 0; q < H; ++q)
                         x[q] = ffma2(x[q], fadd2(pack2(c.drift[2 * q], c.drift[2 * q + 1]), dw[q]), x[q]);
                 }
-                if (STATS || (SAVE && ((i + 1) % a.run.save_every) == 0)) {
+                if (STATS && !SAVE && SCHEME == MC_LOG_EULER) {
+                    // monitored basket: sum of (w_a S0_a) 2^{x_a}, asset pairs
+                    static_assert(D % 2 == 0 && (sizeof(unsigned long long) * basket_pair_count(D) + sizeof(float) * D) % 8 == 0,
+                                  "ws0 is read as 8-byte pairs");
+                    f32x2 u2 = pack2(0.0f, 0.0f);
+#pragma unroll
+                    for (int q = 0; q < H; ++q)
+                        u2 = ffma2(reinterpret_cast<const f32x2 *>(c.ws0)[q],
+                                   pack2(ex2_approx(lo_of(x[q])), ex2_approx(hi_of(x[q]))), u2);
+                    st.add(lo_of(u2) + hi_of(u2));
+                } else if (STATS || (SAVE && ((i + 1) % a.run.save_every) == 0)) {
                     float u = 0.0f;
                     const int64_t slot = (i + 1) / a.run.save_every;
 #pragma unroll

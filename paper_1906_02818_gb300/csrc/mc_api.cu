@@ -683,7 +683,9 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             resident = basket_tc_occupancy(P->prec, ta) * di.sms;
         } else {
             P->kk = K_BASKET_FP32;
-            P->block = 128;  // the kernel's launch bounds: 5 blocks of 128 per SM
+            // one block of 640 per SM when every SM gets at least two rounds
+            // of paths, else blocks of 128 (5 per SM) to spread small runs
+            P->block = (c->paths >= static_cast<int64_t>(2) * 640 * di.sms) ? 640 : 128;
             MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
             std::vector<float> Lp(tri), drift(d);
             MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
