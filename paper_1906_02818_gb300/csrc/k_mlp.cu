@@ -2,7 +2,7 @@
 // activations and a scalar linear output (the DNN-layer / simulation-step
 // analogy of Sec. III.C), its MSE training by back-propagation (Sec. I.A.3)
 // with Adam, all in this file's kernels:
-//   gemm_kernel      C = op(A) op(B) (+ bias, + SiLU) in FP32, 64x64 tiles
+//   gemm_kernel      C = op(A) op(B) (+ bias, + SiLU) in FP32, 64x64 tiles, 8x8 per thread
 //   silu_bwd_kernel  dZ = dH * silu'(Z)
 //   colsum_kernel    db = column sums of dZ
 //   mse_kernel       residual gradient 2 (y - t) / n and loss partials
@@ -22,26 +22,121 @@ namespace gbmc {
 namespace {
 
 constexpr int kT = 64, kK = 16;
-constexpr int kMaxSlices = 16;  // K slices of a weight-gradient product
+constexpr int kGemmThreads = 64;  // threads of gemm_kernel (8 x 8 outputs each)
+constexpr int kMaxSlices = 64;    // K slices of a weight-gradient product
 
+
+// Epilogue of the products: rows m < bias_rows take v = acc + bias[n],
+// Z = v (if Z) and H = silu(v) or v (if H); rows at or past bias_rows (the
+// tangent rows stacked below a layer's primal rows) take Z = acc only.
+__device__ __forceinline__ void store_out(int m, int n, float acc, const float *bias, float *Z, float *H, int ldc,
+                                          int act, int bias_rows)
+{
+    const int64_t o = static_cast<int64_t>(m) * ldc + n;
+    if (m < bias_rows) {
+        const float v = acc + (bias ? bias[n] : 0.0f);
+        if (Z) Z[o] = v;
+        if (H) H[o] = act ? silu_f(v) : v;
+    } else if (Z) {
+        Z[o] = acc;
+    }
+}
 
 // C[M x N] = op(A)[M x K] * op(B)[K x N]; TA: A stored K x M; TB: B stored N x K.
-// Epilogue: v = acc + bias[n]; Z = v (if Z); H = silu(v) or v (if H).
+// Epilogue: store_out.
 // Split K (grid.z > 1): slice z sums k in [z kchunk, (z + 1) kchunk) and
 // writes its partial product at Z + z M ldc (summed by sum_slices_kernel).
+//
+// 64 x 64 tiles, 64 threads, each an 8 x 8 block of C: rows
+// {4 ty + i} u {32 + 4 ty + i} and columns {4 tx + j} u {32 + 4 tx + j}
+// (i, j < 4), so that the 16-byte shared loads of a quarter warp touch
+// distinct banks.  Per k a thread reads 8 + 8 values for 64 products, in
+// packed FP32x2 FMAs over column pairs (each lane an ordinary FP32 fma, k in
+// order): the shared-memory port keeps pace with the FMA pipe, which a
+// 4 x 4 block per thread (8 values per 16 products) cannot.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
-                                                   const float *__restrict__ B, int ldb, const float *__restrict__ bias,
-                                                   float *__restrict__ Z, float *__restrict__ H, int ldc, int act,
-                                                   int kchunk)
+__global__ void __launch_bounds__(kGemmThreads, 8) gemm8_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
+                                                             const float *__restrict__ B, int ldb,
+                                                             const float *__restrict__ bias, float *__restrict__ Z,
+                                                             float *__restrict__ H, int ldc, int act, int kchunk,
+                                                             int bias_rows)
 {
     // Rows of 68 floats (272 bytes) keep every 4-float group 16-byte aligned.
     __shared__ __align__(16) float As[kK][kT + 4];
     __shared__ __align__(16) float Bs[kK][kT + 4];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int m0 = blockIdx.x * kT, n0 = blockIdx.y * kT;  // row tiles on x: up to 2^31 - 1 blocks
-    // acc2[i][h] holds the products of row i with columns 2h, 2h + 1 of this
-    // thread's 4 columns (packed FP32 pairs: two FMAs per instruction).
+    // acc2[i][h]: row i of this thread's 8, column pair h (columns 4 tx + 2h,
+    // + 1 for h < 2; 32 + 4 tx + 2 (h - 2), + 1 for h >= 2)
+    f32x2 acc2[8][4] = {};
+    const int kb0 = blockIdx.z * kchunk, kend = min(K, kb0 + kchunk);
+    if (gridDim.z > 1) {
+        Z += static_cast<int64_t>(blockIdx.z) * M * ldc;
+        K = kend;
+    }
+    for (int k0 = kb0; k0 < K; k0 += kK) {
+#pragma unroll
+        for (int r = 0; r < (kT * kK) / kGemmThreads; ++r) {
+            const int e = tid + kGemmThreads * r;
+            int m, k;
+            if (TA) { m = e & 63; k = e >> 6; } else { m = e >> 4; k = e & 15; }
+            const int gm = m0 + m, gk = k0 + k;
+            float v = 0.0f;
+            if (gm < M && gk < K) v = TA ? A[static_cast<int64_t>(gk) * lda + gm] : A[static_cast<int64_t>(gm) * lda + gk];
+            As[k][m] = v;
+            int n, kb;
+            if (TB) { kb = e & 15; n = e >> 4; } else { kb = e >> 6; n = e & 63; }
+            const int gn = n0 + n, gkb = k0 + kb;
+            float w = 0.0f;
+            if (gn < N && gkb < K) w = TB ? B[static_cast<int64_t>(gn) * ldb + gkb] : B[static_cast<int64_t>(gkb) * ldb + gn];
+            Bs[kb][n] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[k][32 + ty * 4]);
+            const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(&Bs[k][tx * 4]);
+            const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(&Bs[k][32 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const f32x2 ai = pack2(av[i], av[i]);
+                acc2[i][0] = ffma2(ai, b0.x, acc2[i][0]);
+                acc2[i][1] = ffma2(ai, b0.y, acc2[i][1]);
+                acc2[i][2] = ffma2(ai, b1.x, acc2[i][2]);
+                acc2[i][3] = ffma2(ai, b1.y, acc2[i][3]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + (i < 4 ? ty * 4 + i : 32 + ty * 4 + (i - 4));
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = n0 + (j < 4 ? tx * 4 + j : 32 + tx * 4 + (j - 4));
+            if (n >= N) continue;
+            const f32x2 pr = acc2[i][j >> 1];
+            store_out(m, n, (j & 1) ? hi_of(pr) : lo_of(pr), bias, Z, H, ldc, act, bias_rows);
+        }
+    }
+}
+
+// The 64 x 64 tile with 256 threads of 4 x 4 outputs: more warps for the
+// same tile count, used where the 8 x 8 form would leave SMs short of warps
+// (a few hundred tiles or fewer).  Same arguments and k order.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm4_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
+                                                    const float *__restrict__ B, int ldb, const float *__restrict__ bias,
+                                                    float *__restrict__ Z, float *__restrict__ H, int ldc, int act,
+                                                    int kchunk, int bias_rows)
+{
+    __shared__ __align__(16) float As[kK][kT + 4];
+    __shared__ __align__(16) float Bs[kK][kT + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * kT, n0 = blockIdx.y * kT;
     f32x2 acc2[4][2] = {};
     const int kb0 = blockIdx.z * kchunk, kend = min(K, kb0 + kchunk);
     if (gridDim.z > 1) {
@@ -88,10 +183,87 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
             const int n = n0 + tx * 4 + j;
             if (n >= N) continue;
             const f32x2 pr = acc2[i][j >> 1];
-            const float v = ((j & 1) ? hi_of(pr) : lo_of(pr)) + (bias ? bias[n] : 0.0f);
-            const int64_t o = static_cast<int64_t>(m) * ldc + n;
-            if (Z) Z[o] = v;
-            if (H) H[o] = act ? silu_f(v) : v;
+            store_out(m, n, (j & 1) ? hi_of(pr) : lo_of(pr), bias, Z, H, ldc, act, bias_rows);
+        }
+    }
+}
+
+// Few inner terms (K <= kSmallK, e.g. the network's input layer): one
+// thread per output, k in order.
+constexpr int kSmallK = 16;
+template <bool TB>
+__global__ void smallk_kernel(int M, int N, int K, const float *__restrict__ A, int lda, const float *__restrict__ B,
+                              int ldb, const float *__restrict__ bias, float *__restrict__ Z, float *__restrict__ H,
+                              int ldc, int act, int bias_rows)
+{
+    const int64_t total = static_cast<int64_t>(M) * N;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int m = static_cast<int>(e / N), n = static_cast<int>(e % N);
+        const float *a = A + static_cast<int64_t>(m) * lda;
+        float acc = 0.0f;
+        for (int k = 0; k < K; ++k) acc = fmaf(a[k], TB ? B[static_cast<int64_t>(n) * ldb + k] : B[static_cast<int64_t>(k) * ldb + n], acc);
+        store_out(m, n, acc, bias, Z, H, ldc, act, bias_rows);
+    }
+}
+
+// One output column (N = 1, e.g. the network's scalar output layer): a warp
+// per row, lanes over k, then a fixed-order warp sum.
+__global__ void rowvec_kernel(int M, int K, const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
+                              const float *__restrict__ bias, float *__restrict__ Z, float *__restrict__ H, int ldc,
+                              int act, int bias_rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t m = w0; m < M; m += nw) {
+        const float *a = A + m * lda;
+        float acc = 0.0f;
+        for (int k = lane; k < K; k += 32) acc = fmaf(a[k], B[static_cast<int64_t>(k) * ldb], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) store_out(static_cast<int>(m), 0, acc, bias, Z, H, ldc, act, bias_rows);
+    }
+}
+
+// Weight gradients with one small side, partial sums over a chunk of rows:
+// part[z][i][c] = sum over rows r of chunk z of X[r][i] Y[r][c], with
+// i < I <= kColDotMaxI (X [R x I], Y [R x C], row-major) -- lanes over c --
+// or, with I large and C = 1, lanes over i.  FP32, fixed order; the chunks
+// are summed by sum_slices_kernel.
+constexpr int kColDotMaxI = 8;
+template <bool WIDE_X>
+__global__ void __launch_bounds__(256) coldot_kernel(int64_t R, int I, int C, const float *__restrict__ X, int ldx,
+                                                     const float *__restrict__ Y, int ldy, int64_t rows_per_chunk,
+                                                     float *__restrict__ part)
+{
+    __shared__ float ws[8][kColDotMaxI][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;  // c (or i when WIDE_X)
+    const int64_t r0 = blockIdx.y * rows_per_chunk, r1 = min(R, r0 + rows_per_chunk);
+    float acc[kColDotMaxI];
+#pragma unroll
+    for (int i = 0; i < kColDotMaxI; ++i) acc[i] = 0.0f;
+    if (WIDE_X) {
+        if (col < I)
+            for (int64_t r = r0 + w; r < r1; r += 8) acc[0] = fmaf(X[r * ldx + col], Y[r * ldy], acc[0]);
+    } else if (col < C) {
+        for (int64_t r = r0 + w; r < r1; r += 8) {
+            const float y = Y[r * ldy + col];
+#pragma unroll
+            for (int i = 0; i < kColDotMaxI; ++i)
+                if (i < I) acc[i] = fmaf(X[r * ldx + i], y, acc[i]);
+        }
+    }
+    const int ni = WIDE_X ? 1 : I;
+    for (int i = 0; i < ni; ++i) ws[w][i][lane] = acc[i];
+    __syncthreads();
+    if (w == 0) {
+        const int64_t slice = WIDE_X ? static_cast<int64_t>(I) : static_cast<int64_t>(I) * C;
+        for (int i = 0; i < ni; ++i) {
+            float t = 0.0f;
+            for (int q = 0; q < 8; ++q) t += ws[q][i][lane];
+            if (WIDE_X ? col < I : col < C)
+                part[blockIdx.y * slice + (WIDE_X ? col : static_cast<int64_t>(i) * C + col)] = t;
         }
     }
 }
@@ -407,25 +579,62 @@ int grid_for(int64_t n, int block = 256)
     return static_cast<int>(g > 4096 ? 4096 : (g < 1 ? 1 : g));
 }
 
+// Tiled products: the 8 x 8-per-thread kernel once the launch has enough
+// tiles to keep every SM's warps busy, else the 4 x 4 one.
+constexpr int64_t kGemm8MinOutputs = int64_t(1) << 21;  // outputs x K slices
+
+template <bool TA, bool TB>
+void launch_tiled(int M, int N, int K, const float *A, int lda, const float *B, int ldb, const float *bias, float *Z,
+                  float *H, int ldc, int act, int kchunk, int slices, int bias_rows, cudaStream_t s)
+{
+    const dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT, slices);
+    if (static_cast<int64_t>(M) * N * slices >= kGemm8MinOutputs)
+        gemm8_kernel<TA, TB><<<grid, kGemmThreads, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act, kchunk,
+                                                           bias_rows);
+    else
+        gemm4_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act, kchunk, bias_rows);
+}
+
+// C = op(A) op(B) with the epilogue of store_out (bias and activation on
+// rows m < bias_rows; every row when bias_rows < 0).
 template <bool TA, bool TB>
 cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, const float *bias, float *Z,
-                 float *H, int ldc, int act, cudaStream_t s)
+                 float *H, int ldc, int act, cudaStream_t s, int bias_rows = -1)
 {
-    dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT);
-    gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act, K);
+    if (bias_rows < 0) bias_rows = M;
+    if (!TA && N == 1) {
+        rowvec_kernel<<<grid_for(static_cast<int64_t>(M) * 32), 256, 0, s>>>(M, K, A, lda, B, ldb, bias, Z, H, ldc, act,
+                                                                             bias_rows);
+    } else if (!TA && K <= kSmallK) {
+        smallk_kernel<TB><<<grid_for(static_cast<int64_t>(M) * N), 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Z, H,
+                                                                                ldc, act, bias_rows);
+    } else {
+        launch_tiled<TA, TB>(M, N, K, A, lda, B, ldb, bias, Z, H, ldc, act, K, 1, bias_rows, s);
+    }
     return cudaGetLastError();
 }
 
 // C = op(A) op(B) with K cut into `slices` pieces (no bias, no activation):
 // partial products into ws [slices][M][N], then one ordered sum into C.
+// Weight gradients with few input features (M <= kColDotMaxI) or one
+// output (N = 1) take the row-chunked dot-product kernel instead of tiles.
 template <bool TA, bool TB>
 cudaError_t gemm_split_k(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int slices,
                          float *ws, cudaStream_t s)
 {
-    const int kchunk = ((K + slices - 1) / slices + kK - 1) / kK * kK;
-    slices = (K + kchunk - 1) / kchunk;
-    dim3 grid((M + kT - 1) / kT, (N + kT - 1) / kT, slices);
-    gemm_kernel<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, nullptr, ws, nullptr, N, 0, kchunk);
+    if (TA && !TB && (M <= kColDotMaxI || N == 1)) {
+        const int64_t rows = (K + slices - 1) / slices;
+        const int chunks = static_cast<int>((K + rows - 1) / rows);
+        if (N == 1)
+            coldot_kernel<true><<<dim3((M + 31) / 32, chunks), 256, 0, s>>>(K, M, 1, A, lda, B, ldb, rows, ws);
+        else
+            coldot_kernel<false><<<dim3((N + 31) / 32, chunks), 256, 0, s>>>(K, M, N, A, lda, B, ldb, rows, ws);
+        slices = chunks;
+    } else {
+        const int kchunk = ((K + slices - 1) / slices + kK - 1) / kK * kK;
+        slices = (K + kchunk - 1) / kchunk;
+        launch_tiled<TA, TB>(M, N, K, A, lda, B, ldb, nullptr, ws, nullptr, N, 0, kchunk, slices, M, s);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t count = static_cast<int64_t>(M) * N;
@@ -570,17 +779,18 @@ cudaError_t mlp_loss_grad_d(const MlpLayout &L, const float *params, const float
         const int in = L.sizes[l], out = L.sizes[l + 1];
         const bool last = l == nl - 1;
         const float *hin = l == 0 ? x : Hs[l - 1];
-        e = gemm<false, false>(static_cast<int>(n), out, in, hin, in, params + L.w_off[l], out, params + L.b_off[l],
-                               Zs[l], last ? nullptr : Hs[l], out, last ? 0 : 1, s);
+        // layer 0: the primal rows (tangents by tangent_first_kernel); later
+        // layers: primal and tangent rows in one product, bias and activation
+        // on the primal rows only (the tangents' H by tangent_act_kernel)
+        const int64_t rows = (l == 0 || K == 0) ? n : R;
+        e = gemm<false, false>(static_cast<int>(rows), out, in, hin, in, params + L.w_off[l], out, params + L.b_off[l],
+                               Zs[l], last ? nullptr : Hs[l], out, last ? 0 : 1, s, static_cast<int>(n));
         if (e != cudaSuccess) return e;
         if (K == 0) continue;
         if (l == 0) {
             tangent_first_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, out, params + L.w_off[0], ds, Zs[0], Hs[0]);
-        } else {
-            e = gemm<false, false>(static_cast<int>(K * n), out, in, Hs[l - 1] + n * in, in, params + L.w_off[l], out,
-                                   nullptr, Zs[l] + n * out, nullptr, out, 0, s);
-            if (e != cudaSuccess) return e;
-            if (!last) tangent_act_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, K, out, Zs[l], Hs[l]);
+        } else if (!last) {
+            tangent_act_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, K, out, Zs[l], Hs[l]);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -10,6 +10,8 @@
   python tests/profile_case.py risk_nested --paths 256          (paths = scenarios)
   python tests/profile_case.py train --paths 262144            (paths = samples, 1 epoch;
                                                                                  --prec tf32x3: tensor-core training)
+  python tests/profile_case.py train_d --paths 262144          (derivative-label training: prices + 2
+                                                                input-gradient labels, 1 epoch)
   python tests/profile_case.py bridge --paths 1048576          (the In and Out Put, 25 steps)
   python tests/profile_case.py qmc --paths 262144              (points x 16 replications)
   python tests/profile_case.py mlmc --paths 16384              (correction paths, d = 64, bf16)
@@ -33,12 +35,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
-                                     "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512", "corr64"])
+                                     "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case in ("mlp", "labels", "risk_nested", "train", "bridge", "qmc", "mlmc", "factor512", "corr64"):
+    if a.case in ("mlp", "labels", "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64"):
         _other(a, torch, workloads, gb)
         return
     if a.case in ("heston", "heston_greeks"):
@@ -119,6 +121,21 @@ def _other(a, torch, workloads, gb):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             loss = net.train(x, t, epochs=1, batch=4096, lr=1e-3)
+            dt = time.perf_counter() - t0
+        print(a.case, n, loss, f"{dt:.4f} s/epoch, {dt / (n // 4096) * 1e3:.3f} ms/step")
+        net.close()
+    elif a.case == "train_d":
+        import time
+        n = a.paths or (1 << 18)
+        net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+        g = torch.Generator("cuda").manual_seed(2)
+        x = torch.rand((n, 5), device="cuda", generator=g) * 2 - 1
+        t = torch.rand(n, device="cuda", generator=g)
+        dl = torch.rand((n, 2), device="cuda", generator=g)
+        for _ in range(a.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = net.train_d(x, t, dl, [0, 1], [1.0, 1.0], [0.2, 0.05], epochs=1, batch=4096, lr=1e-3)
             dt = time.perf_counter() - t0
         print(a.case, n, loss, f"{dt:.4f} s/epoch, {dt / (n // 4096) * 1e3:.3f} ms/step")
         net.close()
