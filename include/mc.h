@@ -257,8 +257,11 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
  * sensitivities to model parameters; Sec. II.A.2: dW = sqrt(dt) diag(sigma)
  * Lrho z with Lrho the Cholesky factor of corr; Sec. VI.A.2 differentiates
  * the basket simulation), reverse mode, FP32 paths and FP64 post-processing.
- *   model: MC_GBM, 2 <= d <= 64, corr given or NULL (= identity), no
- *          loadings.  cfg: MC_LOG_EULER, MC_FP32, MC_DISCRETE.
+ *   model: MC_GBM, 2 <= d <= 512, corr given or NULL (= identity), no
+ *          loadings.  cfg: MC_LOG_EULER, MC_FP32, MC_DISCRETE.  For d > 64
+ *          the per-path vectors live in device scratch (8 d bytes per path;
+ *          paths x d <= 2^31) and the path contractions run as FP32
+ *          products.
  *   payoff: one MC_CALL or MC_PUT (weights from the model, 1/d if NULL).
  *   price: host [1] or NULL: the discounted price and its standard error.
  *   dl:    host [d*d] or NULL, row-major: dP/dLrho[a][b] for b <= a (the
@@ -268,7 +271,8 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
  *          corr[a][b] and corr[b][a] moved together (symmetric); zero on the
  *          diagonal.
  * Standard errors of dl and drho are batch-means errors over min(64, CTAs of
- * the launch) groups of paths (NaN with one group, i.e. paths <= 128); the
+ * the launch) groups of paths for d <= 64, min(32, ceil(paths / 128))
+ * contiguous groups for d > 64 (NaN with one group, i.e. paths <= 128); the
  * price's is the usual one.  Errors: MC_EUNSUPPORTED outside the cases above,
  * MC_ENOTPSD if corr is not positive definite, MC_EINVAL on bad arguments;
  * outputs are untouched on error.  Synchronises `stream` before returning.

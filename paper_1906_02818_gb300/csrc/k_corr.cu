@@ -233,6 +233,172 @@ __global__ void corr_finish_kernel(int d, int B, const double *nb, const double 
     }
 }
 
+// ------------------------- wide baskets (d > 64) ---------------------------
+// Same estimator, with the per-path vectors in global memory and the two
+// path-sized contractions as FP32 products:
+//   W_p = sum_i z_i                        corr_wsum_kernel (chunks of 64 assets)
+//   Y = W Lhat^T                           gemm_f32_abt
+//   u_p,a = slope_p w_a S_a(T)             corr_u_kernel (and the price)
+//   H_b = sum over batch b of u_p W_p^T     gemm_f32_atb_slices (one slice per batch)
+// then dP/dLrho and the Cholesky adjoint per batch in FP64 (global memory).
+constexpr int kWChunk = 64;
+
+template <bool EXACT>
+__global__ void __launch_bounds__(128) corr_wsum_kernel(const __grid_constant__ CorrArgs a, float *__restrict__ Wbuf)
+{
+    const int d = a.d, M = a.run.steps;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < a.run.paths; p += stride) {
+        const uint64_t n = static_cast<uint64_t>(a.run.path_offset + p);
+        for (int c0 = 0; c0 < d; c0 += kWChunk) {
+            float W[kWChunk];
+#pragma unroll
+            for (int k = 0; k < kWChunk; ++k) W[k] = 0.0f;
+            if (EXACT) {  // d % 4 == 0: step i's normals are blocks i d/4 .. i d/4 + d/4 - 1
+                const uint64_t nb = static_cast<uint64_t>(d >> 2);
+                for (int i = 0; i < M; ++i) {
+#pragma unroll
+                    for (int kb = 0; kb < kWChunk / 4; ++kb) {
+                        if (c0 + 4 * kb < d) {
+                            const float4 z = normals4(static_cast<uint64_t>(i) * nb + (c0 >> 2) + kb, n, a.run.rk);
+                            W[4 * kb] += z.x;
+                            W[4 * kb + 1] += z.y;
+                            W[4 * kb + 2] += z.z;
+                            W[4 * kb + 3] += z.w;
+                        }
+                    }
+                }
+            } else {
+                NormalReader rd;
+                rd.init(n, a.run.rk);
+                for (int i = 0; i < M; ++i) {
+#pragma unroll
+                    for (int k = 0; k < kWChunk; ++k)
+                        if (c0 + k < d) W[k] += rd.get(static_cast<uint64_t>(i) * d + c0 + k);
+                }
+            }
+            float *dst = Wbuf + p * d + c0;
+#pragma unroll
+            for (int k = 0; k < kWChunk; ++k)
+                if (c0 + k < d) dst[k] = W[k];
+        }
+    }
+}
+
+// One warp per path: S_a = w_a S0_a 2^{M drift_a + Y_a}, U = sum_a S_a, the
+// payoff (into the price reduction) and u_a = slope S_a written over Y.
+__global__ void __launch_bounds__(256) corr_u_kernel(const __grid_constant__ CorrArgs a, const float *__restrict__ drift,
+                                                     const float *__restrict__ ws0, float *__restrict__ Y)
+{
+    __shared__ AccSlot s_acc[(256 / 32) * 2];
+    __shared__ double s_red[32];
+    if (threadIdx.x < (256 / 32) * 2) s_acc[threadIdx.x] = 0.0f;
+    __syncthreads();
+    const int d = a.d, lane = threadIdx.x & 31;
+    const float fM = static_cast<float>(a.run.steps);
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const bool call = a.kind == MC_CALL;
+    for (int64_t p = w0; p < a.run.paths; p += nw) {
+        float *y = Y + p * d;
+        float U = 0.0f;
+        for (int k = lane; k < d; k += 32) {
+            const float S = ws0[k] * ex2_approx(fmaf(fM, drift[k], y[k]));
+            y[k] = S;
+            U += S;
+        }
+        U = warp_sum(U);
+        const float f = call ? fmaxf(U - a.strike, 0.0f) : fmaxf(a.strike - U, 0.0f);
+        const float slope = call ? (U > a.strike ? 1.0f : 0.0f) : (U < a.strike ? -1.0f : 0.0f);
+        for (int k = lane; k < d; k += 32) y[k] *= slope;
+        warp_accumulate(s_acc, 1, 0, lane == 0 ? f : 0.0f);
+    }
+    block_finish(s_acc, s_red, 1, a.red);
+}
+
+// Lbar_k[q][j] = cfac_q H_k[q][j] / n_k (lower triangle) for batches k < B
+// and, at k = B, for all paths (the batches' sums added in order).
+__global__ void corr_lbar_kernel(int d, int B, const float *__restrict__ part, const double *__restrict__ nb,
+                                 const double *__restrict__ cfac, double *__restrict__ out_dl)
+{
+    const int64_t dd = static_cast<int64_t>(d) * d;
+    const int k = blockIdx.y;
+    double n = 0.0;
+    if (k < B) n = nb[k];
+    else for (int j = 0; j < B; ++j) n += nb[j];
+    const double inv_n = n > 0.0 ? 1.0 / n : 0.0;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < dd;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int q = static_cast<int>(e / d), j = static_cast<int>(e % d);
+        double h = 0.0;
+        if (j <= q) {
+            if (k < B) h = static_cast<double>(part[k * dd + e]);
+            else for (int b = 0; b < B; ++b) h += static_cast<double>(part[b * dd + e]);
+        }
+        out_dl[k * dd + e] = cfac[q] * h * inv_n;
+    }
+}
+
+// P_k = Phi(Lrho^T Lbar_k): lower triangle, diagonal halved.
+__global__ void corr_adj_a_kernel(int d, const double *__restrict__ L, const double *__restrict__ lbar,
+                                  double *__restrict__ Pm)
+{
+    const int64_t dd = static_cast<int64_t>(d) * d;
+    const int k = blockIdx.y;
+    const double *G = lbar + k * dd;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < dd;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
+        double s = 0.0;
+        if (j <= i) {
+            for (int q = i; q < d; ++q) s = fma(L[static_cast<int64_t>(q) * d + i], G[static_cast<int64_t>(q) * d + j], s);
+            if (j == i) s *= 0.5;
+        }
+        Pm[k * dd + e] = s;
+    }
+}
+
+// X_k = P_k Lrho^-1 in place, one thread per row: x_ij = (p_ij - sum_{q > j} x_iq L_qj) / L_jj, j = i .. 0.
+__global__ void corr_adj_x_kernel(int d, const double *__restrict__ L, double *__restrict__ Pm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    double *X = Pm + static_cast<int64_t>(blockIdx.y) * d * d + static_cast<int64_t>(i) * d;
+    for (int j = i; j >= 0; --j) {
+        double s = X[j];
+        for (int q = j + 1; q <= i; ++q) s = fma(-X[q], L[static_cast<int64_t>(q) * d + j], s);
+        X[j] = s / L[static_cast<int64_t>(j) * d + j];
+    }
+}
+
+// S_k = Lrho^-T X_k, one thread per column: s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii, i = d-1 .. 0.
+__global__ void corr_adj_s_kernel(int d, const double *__restrict__ L, const double *__restrict__ Pm,
+                                  double *__restrict__ Sm)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    const int64_t off = static_cast<int64_t>(blockIdx.y) * d * d;
+    const double *X = Pm + off;
+    double *S = Sm + off;
+    for (int i = d - 1; i >= 0; --i) {
+        double s = X[static_cast<int64_t>(i) * d + j];
+        for (int q = i + 1; q < d; ++q) s = fma(-L[static_cast<int64_t>(q) * d + i], S[static_cast<int64_t>(q) * d + j], s);
+        S[static_cast<int64_t>(i) * d + j] = s / L[static_cast<int64_t>(i) * d + i];
+    }
+}
+
+// dP/dcorr[a][b] = S_ab + S_ba (a != b), zero on the diagonal.
+__global__ void corr_sym_kernel(int d, const double *__restrict__ Sm, double *__restrict__ out_drho)
+{
+    const int64_t dd = static_cast<int64_t>(d) * d;
+    const int64_t off = static_cast<int64_t>(blockIdx.y) * dd;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < dd;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
+        out_drho[off + e] = i == j ? 0.0 : Sm[off + e] + Sm[off + static_cast<int64_t>(j) * d + i];
+    }
+}
+
 const void *corr_select(const CorrArgs &a)
 {
     return a.exact4 ? reinterpret_cast<const void *>(&corr_path_kernel<true>)
@@ -271,6 +437,42 @@ cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int bat
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int dd2 = 2 * a.d * a.d;
     corr_finish_kernel<<<(dd2 + 255) / 256, 256, 0, s>>>(a.d, batches, nb, out_dl, out_drho, res_dl, res_drho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_wide(const CorrArgs &a, const CorrWide &w, int grid, cudaStream_t s)
+{
+    const int d = a.d, B = w.batches;
+    const int64_t P = a.run.paths;
+    if (P > INT32_MAX) return cudaErrorInvalidValue;
+    if (a.exact4) corr_wsum_kernel<true><<<grid, 128, 0, s>>>(a, w.Wbuf);
+    else corr_wsum_kernel<false><<<grid, 128, 0, s>>>(a, w.Wbuf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // Y = W Lhat^T: Y[p][a] = sum_b W[p][b] Lhat[a][b]
+    if ((e = gemm_f32_abt(static_cast<int>(P), d, d, w.Wbuf, d, w.Ls, d, w.Ybuf, d, s)) != cudaSuccess) return e;
+    const int64_t warps = (P < int64_t(1) << 20) ? P : (int64_t(1) << 20);
+    corr_u_kernel<<<static_cast<int>((warps * 32 + 255) / 256), 256, 0, s>>>(a, w.drift, w.ws0, w.Ybuf);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // H_b [d x d] = sum over batch b of u_p W_p^T
+    if ((e = gemm_f32_atb_slices(d, d, static_cast<int>(P), w.Ybuf, d, w.Wbuf, d, w.kchunk, w.part, s)) != cudaSuccess)
+        return e;
+    const int64_t dd = static_cast<int64_t>(d) * d;
+    const unsigned ge = static_cast<unsigned>(std::min<int64_t>((dd + 255) / 256, 1024));
+    corr_lbar_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, B, w.part, w.nb, w.cfac, w.out_dl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    corr_adj_a_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, w.L, w.out_dl, w.Pm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned gr = static_cast<unsigned>((d + 63) / 64);
+    corr_adj_x_kernel<<<dim3(gr, B + 1), 64, 0, s>>>(d, w.L, w.Pm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    corr_adj_s_kernel<<<dim3(gr, B + 1), 64, 0, s>>>(d, w.L, w.Pm, w.Sm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    corr_sym_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, w.Sm, w.out_drho);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t dd2 = 2 * dd;
+    corr_finish_kernel<<<static_cast<unsigned>((dd2 + 255) / 256), 256, 0, s>>>(d, B, w.nb, w.out_dl, w.out_drho,
+                                                                              w.res_dl, w.res_drho);
     return cudaGetLastError();
 }
 

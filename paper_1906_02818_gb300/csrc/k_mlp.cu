@@ -660,6 +660,23 @@ MlpLayout::MlpLayout(int n_in, int width, int hidden)
     count = o;
 }
 
+// FP32 products for the other path kernels (correlation sensitivities of
+// wide baskets), through the same tiled kernels.
+cudaError_t gemm_f32_abt(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                         cudaStream_t s)
+{
+    return gemm<false, true>(M, N, K, A, lda, B, ldb, nullptr, C, nullptr, ldc, 0, s);
+}
+
+cudaError_t gemm_f32_atb_slices(int M, int N, int K, const float *A, int lda, const float *B, int ldb, int kchunk,
+                                float *part, cudaStream_t s)
+{
+    if (kchunk <= 0 || kchunk % kK != 0) return cudaErrorInvalidValue;
+    const int slices = (K + kchunk - 1) / kchunk;
+    launch_tiled<true, false>(M, N, K, A, lda, B, ldb, nullptr, part, nullptr, N, 0, kchunk, slices, M, s);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_forward_fp32(const MlpLayout &L, const float *params, const float *x, int64_t n, float *work,
                              float *y, cudaStream_t s)
 {

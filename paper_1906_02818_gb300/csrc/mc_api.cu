@@ -1040,6 +1040,114 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     return MC_OK;
 }
 
+// mc_corr_greeks for kCorrMaxD < d <= kBigMaxD (arguments already checked):
+// the per-path vectors in global memory, the contractions as FP32 products,
+// the Cholesky adjoint of each batch in global memory (k_corr.cu).
+static int corr_greeks_wide(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay, mc_result *price,
+                            mc_result *dl, mc_result *drho, cudaStream_t s, const DeviceInfo &di)
+{
+    const int d = m->d;
+    const size_t dd = static_cast<size_t>(d) * d, tri = static_cast<size_t>(d) * (d + 1) / 2;
+    const double dt = c->T / c->steps, sdt = std::sqrt(dt), disc = std::exp(-m->r * c->T);
+    const int64_t P = c->paths;
+    if (P * d > (int64_t(1) << 31))
+        return fail(MC_EUNSUPPORTED, "correlation sensitivities for d > %d hold paths x d <= 2^31 values per buffer",
+                    kCorrMaxD);
+    CorrArgs a{};
+    a.run.paths = P;
+    a.run.path_offset = c->path_offset;
+    set_seed(a.run, c->seed);
+    a.run.steps = c->steps;
+    a.run.save_every = 1;
+    a.d = d;
+    a.exact4 = d % 4 == 0 ? 1 : 0;
+    a.kind = pay->kind;
+    a.strike = static_cast<float>(pay->strike);
+    // batches of kchunk paths (a multiple of 16) for the batch-means errors
+    int B = static_cast<int>(std::min<int64_t>(32, std::max<int64_t>(1, (P + 127) / 128)));
+    const int kchunk = static_cast<int>(((P + B - 1) / B + 15) / 16 * 16);
+    B = static_cast<int>((P + kchunk - 1) / kchunk);
+    const int64_t uwarps = std::min<int64_t>(P, int64_t(1) << 20);
+    const int ugrid = static_cast<int>((uwarps * 32 + 255) / 256);
+    const int wgrid = static_cast<int>(std::min<int64_t>((P + 127) / 128, static_cast<int64_t>(di.sms) * 8));
+
+    DeviceArena ar;
+    const size_t bytes = DeviceArena::up(dd * 8) * 2 + DeviceArena::up(d * 8) * 2 + DeviceArena::up(sizeof(int)) +
+                         DeviceArena::up(tri * 4) + DeviceArena::up(d * 4) * 2 + DeviceArena::up(dd * 4) +
+                         DeviceArena::up(static_cast<size_t>(P) * d * 4) * 2 + DeviceArena::up(B * dd * 4) +
+                         DeviceArena::up(B * 8) + 4 * DeviceArena::up((B + 1) * dd * 8) +
+                         2 * DeviceArena::up(dd * sizeof(mc_result)) + DeviceArena::up(static_cast<size_t>(ugrid) * 2 * 4) +
+                         DeviceArena::up(4) + DeviceArena::up(sizeof(mc_result));
+    MC_CUDA(dev_alloc(&ar.base, bytes));
+    double *dcorr = ar.take<double>(dd), *dL = ar.take<double>(dd), *dsig = ar.take<double>(d);
+    double *dcfac = ar.take<double>(d);
+    int *dstatus = ar.take<int>(1);
+    float *dLp = ar.take<float>(tri), *ddrift = ar.take<float>(d), *dws0 = ar.take<float>(d), *dLs = ar.take<float>(dd);
+    CorrWide w{};
+    w.Wbuf = ar.take<float>(static_cast<size_t>(P) * d);
+    w.Ybuf = ar.take<float>(static_cast<size_t>(P) * d);
+    w.part = ar.take<float>(B * dd);
+    double *dnb = ar.take<double>(B);
+    w.Pm = ar.take<double>((B + 1) * dd);
+    w.Sm = ar.take<double>((B + 1) * dd);
+    w.out_dl = ar.take<double>((B + 1) * dd);
+    w.out_drho = ar.take<double>((B + 1) * dd);
+    w.res_dl = ar.take<mc_result>(dd);
+    w.res_drho = ar.take<mc_result>(dd);
+    a.red.partials = ar.take<float>(static_cast<size_t>(ugrid) * 2);
+    a.red.ticket = ar.take<unsigned int>(1);
+    a.red.out = ar.take<mc_result>(1);
+    a.red.paths = P;
+    a.red.disc = disc;
+    a.red.err = nullptr;
+    w.Ls = dLs;
+    w.drift = ddrift;
+    w.ws0 = dws0;
+    w.L = dL;
+    w.cfac = dcfac;
+    w.nb = dnb;
+    w.batches = B;
+    w.kchunk = kchunk;
+
+    std::vector<double> corr(dd, 0.0), cf(d), nb(B);
+    if (m->corr) std::memcpy(corr.data(), m->corr, dd * sizeof(double));
+    else for (int k = 0; k < d; ++k) corr[static_cast<size_t>(k) * d + k] = 1.0;
+    for (int k = 0; k < d; ++k) cf[k] = disc * sdt * m->sigma[k];
+    for (int b = 0; b < B; ++b) nb[b] = static_cast<double>(std::min<int64_t>(P, int64_t(b + 1) * kchunk) - int64_t(b) * kchunk);
+    std::vector<float> ws0(d);
+    for (int k = 0; k < d; ++k) ws0[k] = static_cast<float>((m->weights ? m->weights[k] : 1.0 / d) * m->s0[k]);
+    MC_CUDA(cudaMemsetAsync(a.red.ticket, 0, sizeof(unsigned int), s));
+    MC_CUDA(cudaMemcpyAsync(dcorr, corr.data(), dd * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dsig, m->sigma, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dcfac, cf.data(), d * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dnb, nb.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    MC_CUDA(cudaMemcpyAsync(dws0, ws0.data(), d * sizeof(float), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_cholesky(d, dcorr, dL, dstatus, s));
+    MC_CUDA(launch_scale_factor(d, dL, dsig, M_LOG2E, sdt, m->r, dt, MC_LOG_EULER, dLp, ddrift, s));
+    int status = 0;
+    MC_CUDA(cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
+    std::vector<float> Lp(tri), Ls(dd, 0.0f);
+    MC_CUDA(cudaMemcpyAsync(Lp.data(), dLp, tri * sizeof(float), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j <= i; ++j) Ls[static_cast<size_t>(i) * d + j] = Lp[static_cast<size_t>(i) * (i + 1) / 2 + j];
+    MC_CUDA(cudaMemcpyAsync(dLs, Ls.data(), dd * sizeof(float), cudaMemcpyHostToDevice, s));
+    MC_CUDA(launch_corr_wide(a, w, wgrid, s));
+    mc_result pr;
+    std::vector<mc_result> hdl(dd), hdr(dd);
+    MC_CUDA(cudaMemcpyAsync(&pr, a.red.out, sizeof pr, cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(hdl.data(), w.res_dl, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(hdr.data(), w.res_drho, dd * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    ar.idle = true;
+    if (price) *price = pr;
+    if (dl) std::memcpy(dl, hdl.data(), dd * sizeof(mc_result));
+    if (drho) std::memcpy(drho, hdr.data(), dd * sizeof(mc_result));
+    return MC_OK;
+}
+
 int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay, mc_result *price, mc_result *dl,
                    mc_result *drho, void *stream)
 {
@@ -1047,9 +1155,9 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
     int rc;
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
     if (!pay) return fail(MC_EINVAL, "payoff is NULL");
-    if (m->kind != MC_GBM || m->loadings || m->d < 2 || m->d > kCorrMaxD)
+    if (m->kind != MC_GBM || m->loadings || m->d < 2 || m->d > kBigMaxD)
         return fail(MC_EUNSUPPORTED, "correlation sensitivities: correlated GBM baskets with 2 <= d <= %d "
-                                     "(Cholesky correlation)", kCorrMaxD);
+                                     "(Cholesky correlation)", kBigMaxD);
     if (c->scheme != MC_LOG_EULER) return fail(MC_EUNSUPPORTED, "correlation sensitivities use the log-Euler scheme");
     if (c->precision != MC_FP32) return fail(MC_EUNSUPPORTED, "correlation sensitivities are computed in FP32");
     if (c->monitoring != MC_DISCRETE) return fail(MC_EUNSUPPORTED, "correlation sensitivities: European payoffs only");
@@ -1059,6 +1167,7 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
     DeviceInfo di;
     if ((rc = device_info(&di))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (m->d > kCorrMaxD) return corr_greeks_wide(m, c, pay, price, dl, drho, s, di);
     const int d = m->d;
     const size_t dd = static_cast<size_t>(d) * d;
     const double dt = c->T / c->steps, sdt = std::sqrt(dt), disc = std::exp(-m->r * c->T);

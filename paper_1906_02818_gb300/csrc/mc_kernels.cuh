@@ -269,6 +269,37 @@ cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int bat
                         const double *cfac, double *Hb, double *nb, double *out_dl, double *out_drho,
                         mc_result *res_dl, mc_result *res_drho, cudaStream_t s);
 
+// FP32 products (k_mlp.cu): C [M x N] = A [M x K] B^T (B stored N x K), and
+// the K-slice partials part[z] [M x N] = A_z^T B_z of C = A^T B (A stored
+// K x M, B stored K x N), slice z covering k in [z kchunk, (z + 1) kchunk),
+// kchunk a multiple of 16.
+cudaError_t gemm_f32_abt(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                         cudaStream_t s);
+cudaError_t gemm_f32_atb_slices(int M, int N, int K, const float *A, int lda, const float *B, int ldb, int kchunk,
+                                float *part, cudaStream_t s);
+
+// Correlation sensitivities of wide baskets (kCorrMaxD < d <= kBigMaxD):
+// W (the paths' summed normal vectors) by one kernel, Y = W Lhat^T by an
+// FP32 product, the payoff slope u per path, the per-batch sums
+// H_b = sum u W^T as K-slice partials of one product, and the Cholesky
+// adjoint of every batch in global memory.  Scratch (caller-owned, device):
+// Wbuf, Ybuf [paths x d] floats; part [batches x d x d] floats; Pm, Sm,
+// out_dl, out_drho [(batches + 1) x d x d] doubles.
+struct CorrWide {
+    const float *Ls;      // [d x d] row-major Lhat (zero above the diagonal)
+    const float *drift;   // [d] per-step log2 drift
+    const float *ws0;     // [d] w_a S0_a
+    const double *L;      // [d x d] FP64 Cholesky factor of corr
+    const double *cfac;   // [d] disc sqrt(dt) sigma_a
+    const double *nb;     // [batches] paths per batch
+    int batches;
+    int kchunk;           // paths per batch (a multiple of 16; the last batch may hold fewer)
+    float *Wbuf, *Ybuf, *part;
+    double *Pm, *Sm, *out_dl, *out_drho;
+    mc_result *res_dl, *res_drho;
+};
+cudaError_t launch_corr_wide(const CorrArgs &a, const CorrWide &w, int grid, cudaStream_t s);
+
 // Records the thread-local message returned by mc_last_error(); returns code.
 int set_last_error(int code, const char *msg);
 // The argument checks of mc_price (model, simulation configuration, payoff

@@ -17,6 +17,7 @@
   python tests/profile_case.py mlmc --paths 16384              (correction paths, d = 64, bf16)
   python tests/profile_case.py factor512 --paths 65536
   python tests/profile_case.py corr64 --paths 65536          (correlation sensitivities, d = 64)
+  python tests/profile_case.py corr512 --paths 65536         (correlation sensitivities, d = 512)
 """
 from __future__ import annotations
 
@@ -35,12 +36,12 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["gbm1d", "basket64", "basket512", "heston", "heston_greeks", "mlp", "labels",
-                                     "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64"])
+                                     "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64", "corr512"])
     ap.add_argument("--paths", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--prec", default="fp32")
     a = ap.parse_args()
-    if a.case in ("mlp", "labels", "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64"):
+    if a.case in ("mlp", "labels", "risk_nested", "train", "train_d", "bridge", "qmc", "mlmc", "factor512", "corr64", "corr512"):
         _other(a, torch, workloads, gb)
         return
     if a.case in ("heston", "heston_greeks"):
@@ -103,6 +104,16 @@ def _other(a, torch, workloads, gb):
         for _ in range(a.reps):
             r = gb.corr_greeks(model, dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=42), w["payoffs"][0])
         print(a.case, r[0])
+    elif a.case == "corr512":
+        import time
+        w = workloads.basket_d512(paths=a.paths or (1 << 16))
+        model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], corr=w["corr"], weights=w["weights"], r=w["r"])
+        for _ in range(a.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = gb.corr_greeks(model, dict(steps=w["steps"], T=w["T"], paths=w["paths"], seed=42), w["payoffs"][0])
+            dt = time.perf_counter() - t0
+        print(a.case, w["paths"], r[0], f"{dt:.3f} s per call")
     elif a.case == "factor512":
         w = workloads.basket_d512_factor(paths=a.paths or (1 << 16))
         model = dict(kind="gbm", s0=w["s0"], sigma=w["sigma"], loadings=w["loadings"], weights=w["weights"], r=w["r"])

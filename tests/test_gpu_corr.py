@@ -167,3 +167,76 @@ def test_basket_pricer_autograd(gb, orc):
     il = np.tril_indices(d, -1)
     dth_path = (ref["drho"] * (1.0 - w["corr"])[..., None])[il].sum(axis=0)
     close(theta.grad.numpy(), dth_path, "theta")
+
+
+def _wide_reference(orc, w, steps, paths, pay, pairs):
+    """The oracle's forward-mode tangents reduced row by row (no [d, d, paths]
+    array): per entry of dP/dLrho the mean, mean |per-path value|, the
+    contribution of paths in the strike band and the per-path standard
+    error; the same for dP/dcorr on the listed pairs (per path, the inner
+    product of the path's dP/dLrho with cholesky_tangent(Lrho, E_ab))."""
+    d, K = len(w["s0"]), float(pay["strike"])
+    xT, tL = orc.gbm_corr_tangents(w["s0"], w["sigma"], w["corr"], w["r"], w["T"], steps, paths)
+    S = np.exp(xT)
+    U = w["weights"] @ S
+    call = pay["kind"] == "call"
+    slope = (U > K).astype(np.float64) if call else -(U < K).astype(np.float64)
+    f = np.exp(-w["r"] * w["T"]) * (np.maximum(U - K, 0.0) if call else np.maximum(K - U, 0.0))
+    g = np.exp(-w["r"] * w["T"]) * slope[None, :] * w["weights"][:, None] * S
+    band = np.abs(U - K) <= BAND * K
+    stats = {k: np.zeros((d, d)) for k in ("mean", "scale", "flips", "se")}
+    L = np.linalg.cholesky(w["corr"])
+    J = {ab: orc.cholesky_tangent(L, _unit_pair(d, *ab)) for ab in pairs}
+    pair_paths = {ab: np.zeros(paths) for ab in pairs}
+    for a in range(d):
+        per = g[a][None, :] * tL[a * (a + 1) // 2: a * (a + 1) // 2 + a + 1]
+        stats["mean"][a, :a + 1] = per.mean(axis=1)
+        stats["scale"][a, :a + 1] = np.abs(per).mean(axis=1)
+        stats["flips"][a, :a + 1] = np.abs(per[:, band]).sum(axis=1) / paths
+        stats["se"][a, :a + 1] = per.std(axis=1, ddof=1) / np.sqrt(paths)
+        for ab in pairs:
+            pair_paths[ab] += J[ab][a, :a + 1] @ per
+    return f, U, stats, pair_paths, band
+
+
+def _unit_pair(d, a, b):
+    E = np.zeros((d, d))
+    E[a, b] = E[b, a] = 1.0
+    return E
+
+
+@pytest.mark.parametrize("d,paths,steps,kind", [(96, 4096, 6, "call"), (130, 700, 5, "put"), (512, 256, 3, "call")])
+def test_corr_greeks_wide_baskets(gb, orc, d, paths, steps, kind):
+    """d > 64 (the wide path: summed normals in device memory, FP32 products,
+    the Cholesky adjoint per batch in global memory): d = 96 (whole Philox
+    blocks, 32 batches, standard errors checked), d = 130 (blocks straddle
+    steps, ragged 64-wide tiles), d = 512 (the large-basket workload's
+    width).  Every entry of dP/dLrho and the symmetric dP/dcorr on sampled
+    pairs against the oracle with the tolerance of the d <= 64 tests."""
+    w = _market(d, k=4)
+    K = float(w["weights"] @ w["s0"]) * (1.0 if kind == "call" else 1.02)
+    pay = dict(kind=kind, strike=K)
+    rng = np.random.default_rng(d)
+    pairs = [(1, 0), (d - 1, 0), (d - 1, d - 2)] + [tuple(sorted(rng.choice(d, 2, replace=False))[::-1])
+                                                     for _ in range(5)]
+    (p, pse), dl, dr = gb.corr_greeks(gbm_model(w), cfg_of(w, paths=paths, steps=steps), pay)
+    f, U, st, pair_paths, band = _wide_reference(orc, w, steps, paths, pay, pairs)
+    m, se = orc.mean_se(f)
+    assert abs(p - m) <= REL * abs(m) + 1e-12, (p, m)
+    assert abs(pse - se) <= 1e-3 * se
+    err = np.abs(dl[..., 0] - st["mean"])
+    tol = 2e-5 * st["scale"] + st["flips"] + 1e-12
+    bad = np.argwhere(err > tol)
+    assert bad.size == 0, (d, bad[:5], err[tuple(bad[0])], tol[tuple(bad[0])], int(band.sum()))
+    assert np.all(dl[..., 0][np.triu_indices(d, 1)] == 0.0)
+    for (a, b), per in pair_paths.items():
+        want = per.mean()
+        tol = 2e-5 * np.abs(per).mean() + np.abs(per[band]).sum() / paths + 1e-12
+        assert abs(dr[a, b, 0] - want) <= tol, (d, a, b, dr[a, b, 0], want, tol)
+        assert dr[a, b, 0] == dr[b, a, 0]
+    assert np.all(dr[..., 0][np.arange(d), np.arange(d)] == 0.0)
+    if paths >= 32 * 128:
+        mask = np.tril(np.ones((d, d), dtype=bool)) & (st["se"] > 0)
+        ratio = dl[..., 1][mask] / st["se"][mask]
+        assert 0.8 <= np.median(ratio) <= 1.2, np.median(ratio)
+        assert ratio.min() >= 0.3 and ratio.max() <= 2.5, (ratio.min(), ratio.max())
