@@ -163,9 +163,9 @@ def test_correlation_sensitivity_checks(lib):
     from paper_1906_02818_gb300 import native
     pr, dl, dr = native.McResult(), (native.McResult * 4096)(), (native.McResult * 4096)()
     for over, code, needle in [
-            (dict(d=1), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
-            (dict(d=65), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
-            (dict(d=4, loadings=np.full((4, 2), 0.5)), native.MC_EUNSUPPORTED, "2 <= d <= 64"),
+            (dict(d=1), native.MC_EUNSUPPORTED, "2 <= d <= 512"),
+            (dict(d=513), native.MC_EUNSUPPORTED, "2 <= d <= 512"),
+            (dict(d=4, loadings=np.full((4, 2), 0.5)), native.MC_EUNSUPPORTED, "2 <= d <= 512"),
             (dict(d=4, scheme="euler"), native.MC_EUNSUPPORTED, "log-Euler"),
             (dict(d=4, precision="bf16"), native.MC_EUNSUPPORTED, "FP32"),
             (dict(d=4, payoffs=[dict(kind="asian_call", strike=100.0)]), native.MC_EUNSUPPORTED, "European"),
