@@ -271,6 +271,37 @@ def gbm_factor_payoffs(s0, sigma, loadings, r, T, steps, paths, payoffs, weights
     return (out, ST) if terminal else out
 
 
+def gbm_factor_greeks(s0, sigma, loadings, r, T, steps, paths, payoff, weights=None, seed=42, path_offset=0):
+    """Per-path discounted pathwise Greeks [2d + 1, paths] of a European
+    basket call or put under the factor model, log-Euler (Sec. I.A.3: the
+    derivative of the discounted payoff along the path, the normals held
+    fixed).  With ln S_a(T) = ln S0_a + (r - sigma_a^2/2) T + sigma_a X_a,
+    X_a a sum of the path's normals that depends on neither parameter, and
+    f' the payoff's slope in U = sum_a w_a S_a(T):
+      d/dS0_a    = e^{-rT} f' w_a S_a / S0_a                    (a < d)
+      d/dsigma_a = e^{-rT} f' w_a S_a (ln(S_a / S0_a) - (r + sigma_a^2/2) T) / sigma_a
+      d/dr       = e^{-rT} (f' U T - T f)                       (k = 2d)"""
+    s0 = _f64(np.atleast_1d(s0))
+    sigma = _f64(np.atleast_1d(sigma))
+    d = s0.size
+    w = np.full(d, 1.0 / d) if weights is None else _f64(weights)
+    kind, K = payoff["kind"], float(payoff["strike"])
+    if kind not in ("call", "put"):
+        raise ValueError("European call or put only")
+    f, ST = gbm_factor_payoffs(s0, sigma, loadings, r, T, steps, paths, [payoff], weights=w, seed=seed,
+                               path_offset=path_offset, terminal=True)
+    disc = np.exp(-r * T)
+    U = w @ ST
+    slope = (U > K).astype(np.float64) if kind == "call" else -(U < K).astype(np.float64)
+    wS = w[:, None] * ST
+    out = np.empty((2 * d + 1, paths), dtype=np.float64)
+    out[:d] = disc * slope[None, :] * wS / s0[:, None]
+    out[d:2 * d] = disc * slope[None, :] * wS * (np.log(ST / s0[:, None]) - ((r + 0.5 * sigma ** 2) * T)[:, None]) \
+        / sigma[:, None]
+    out[2 * d] = disc * slope * U * T - T * f[0]
+    return out
+
+
 def sobol_directions(ndim: int) -> np.ndarray:
     """Direction numbers V[j][k] (uint32) of the oracle's Sobol sequence."""
     V = np.zeros((ndim, 32), dtype=np.uint32)

@@ -7,11 +7,16 @@ from k common and d idiosyncratic normals per step):
   * the exact-lognormal geometric basket call (closed form with that
     correlation) within 3 SE, and the empirical correlation of one-step log
     returns;
-  * one asset with a partial loading is Black-Scholes."""
+  * one asset with a partial loading is Black-Scholes;
+  * the pathwise Greeks of a basket call / put: common-random-number central
+    differences in S0_a, sigma_a and r, and the one-asset Black-Scholes
+    delta, vega and rho within 3 SE."""
 import numpy as np
 
 import workloads
-from closed_forms import bs_call, geometric_basket_call
+import pytest
+
+from closed_forms import bs_call, bs_call_greeks, geometric_basket_call
 
 PAYS = [dict(kind="call", strike=95.0), dict(kind="put", strike=105.0), dict(kind="asian_call", strike=100.0),
         dict(kind="uo_call", strike=95.0, barrier=125.0), dict(kind="di_put", strike=105.0, barrier=85.0)]
@@ -56,3 +61,52 @@ def test_geometric_basket_and_return_correlation(orc):
 def test_one_asset_partial_loading_is_black_scholes(orc):
     f = orc.gbm_factor_payoffs(100.0, 0.3, np.array([[0.6]]), 0.05, 1.0, 4, 1 << 17, [dict(kind="call", strike=100.0)])[0]
     assert abs(f.mean() - bs_call(100.0, 100.0, 0.05, 0.3, 1.0)) <= 3 * f.std(ddof=1) / np.sqrt(f.size)
+
+
+@pytest.mark.parametrize("kind", ["call", "put"])
+def test_factor_greeks_against_crn_differences(orc, kind):
+    """Pathwise d/dS0_a, d/dsigma_a, d/dr against central differences of the
+    per-path payoffs simulated with the bumped parameter on the same stream
+    (the loadings held fixed): per path they differ only where the basket
+    crosses the strike within the bump, so the mean difference lies within
+    3 SE of the per-path difference, and far below the Greek itself."""
+    d, k, M, N = 6, 2, 8, 1 << 13
+    s0, sg, B = workloads.basket_market_factors(d, k, seed=5)
+    w = np.linspace(1.0, 2.0, d)
+    w /= w.sum()
+    r, T = 0.04, 1.0
+    K = float(w @ s0) * (1.0 if kind == "call" else 1.02)
+    pay = dict(kind=kind, strike=K)
+    g = orc.gbm_factor_greeks(s0, sg, B, r, T, M, N, pay, weights=w)
+    assert np.all(np.isfinite(g))
+    checks = []
+    for a in (0, 3, d - 1):
+        e = np.zeros(d)
+        e[a] = 1.0
+        h = 1e-4 * s0[a]
+        up = orc.gbm_factor_payoffs(s0 + h * e, sg, B, r, T, M, N, [pay], weights=w)[0]
+        dn = orc.gbm_factor_payoffs(s0 - h * e, sg, B, r, T, M, N, [pay], weights=w)[0]
+        checks.append((f"delta{a}", (up - dn) / (2 * h), g[a]))
+        h = 1e-5
+        up = orc.gbm_factor_payoffs(s0, sg + h * e, B, r, T, M, N, [pay], weights=w)[0]
+        dn = orc.gbm_factor_payoffs(s0, sg - h * e, B, r, T, M, N, [pay], weights=w)[0]
+        checks.append((f"vega{a}", (up - dn) / (2 * h), g[d + a]))
+    h = 1e-6
+    up = orc.gbm_factor_payoffs(s0, sg, B, r + h, T, M, N, [pay], weights=w)[0]
+    dn = orc.gbm_factor_payoffs(s0, sg, B, r - h, T, M, N, [pay], weights=w)[0]
+    checks.append(("rho", (up - dn) / (2 * h), g[2 * d]))
+    for name, f_d, pw in checks:
+        diff = f_d - pw
+        m, se = orc.mean_se(diff)
+        assert abs(m) <= 3 * se + 1e-9, (kind, name, m, se)
+        assert abs(np.mean(pw)) > 10 * abs(m), (kind, name, np.mean(pw), m)
+
+
+def test_factor_greeks_one_asset_black_scholes(orc):
+    """One asset with a partial loading is Black-Scholes: the pathwise delta,
+    vega and rho within 3 SE of the closed-form Greeks."""
+    S, K, r, sg, T = 100.0, 95.0, 0.05, 0.3, 1.0
+    g = orc.gbm_factor_greeks(S, sg, np.array([[0.6]]), r, T, 4, 1 << 17, dict(kind="call", strike=K))
+    for row, want in zip(g, bs_call_greeks(S, K, r, sg, T)):
+        m, se = orc.mean_se(row)
+        assert abs(m - want) <= 3 * se, (m, se, want)
