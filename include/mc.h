@@ -243,6 +243,10 @@ int32_t mc_greek_count(const mc_model *model);
  *     greeks[d..2d-1] = vega_a = dP/dsigma_a (sigma_a scales column a of
  *     diag(sigma) Lrho), greeks[2d] = rho = dP/dr.  MC_ENOTPSD if corr is
  *     not positive definite, MC_ETIMEOUT if a bounded device wait gave up.
+ *   MC_GBM with loadings (the factor model): the same layout and payoff
+ *     rules, MC_LOG_EULER and MC_FP32; sigma_a scales asset a's whole
+ *     increment (loadings and idiosyncratic weight held fixed), so
+ *     vega_a = e^{-rT} E[f' w_a S_a (ln(S_a/S0_a) - (r + sigma_a^2/2) T) / sigma_a].
  * Barrier payoffs are rejected (a knock indicator has no pathwise derivative:
  * MC_EUNSUPPORTED).
  *   prices: host [n_payoff] or NULL; greeks: host [n_payoff][mc_greek_count].

@@ -12,7 +12,11 @@
 //     each) and broadcast them by shuffles; every lane draws the
 //     idiosyncratic normals of its 8 assets;
 //   * B' is staged in shared memory as [factor][asset], so one 16-byte load
-//     feeds 16 FMAs (4 assets x 4 paths).
+//     feeds 16 FMAs (4 assets x 4 paths);
+//   * GREEKS (log-Euler, one European call or put): at T each lane adds its
+//     assets' pathwise delta and vega terms of its 4 paths (Sec. I.A.3; the
+//     normals held fixed, ln S_a = ln S0_a + (r - sigma_a^2/2) T + sigma_a X_a)
+//     to per-CTA sums in shared memory, and the path holders add rho's.
 // Stream layout: normals i (k + d) + j (z_j) and i (k + d) + k + a (eps_a).
 #include "mc_kernels.cuh"
 
@@ -25,7 +29,7 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kP = 4;   // paths per warp
 constexpr int kA = 8;   // assets per lane
 
-template <int SCHEME, bool STATS, bool EXACT>
+template <int SCHEME, bool STATS, bool EXACT, bool GREEKS>
 __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant__ FactorArgs a)
 {
     extern __shared__ float smem[];
@@ -35,6 +39,7 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant
     float *sDr = sE + dp;             // drift
     float *sWs = sDr + dp;            // w S0 (log-Euler U) or w (Euler U)
     float *sPart = sWs + dp;          // [kWarps][kP] partial U of each warp
+    float *sG = sPart + kWarps * kP;  // GREEKS: [2d + 1][2] sums of the terms and their squares
     __shared__ AccSlot s_acc[kWarps * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
 
@@ -46,6 +51,8 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant
         sWs[i] = SCHEME == MC_LOG_EULER ? a.ws0[i] : a.w[i];
     }
     for (int i = t; i < kWarps * a.pay.n * 2; i += kBlock) s_acc[i] = 0.0f;
+    if (GREEKS)
+        for (int i = t; i < (2 * d + 1) * 2; i += kBlock) sG[i] = 0.0f;
     __syncthreads();
 
     const int group = warp / G, gw = warp % G, groups = kWarps / G;
@@ -178,6 +185,50 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant
         bool ok = false;
 #pragma unroll
         for (int p = 0; p < kP; ++p) ok = (lane == p) ? valid[p] : ok;
+        if (GREEKS) {
+            // the payoff slope of each path to every lane of its group (the
+            // partial sums are free after the last step's barrier)
+            const float K = a.pay.strike[0];
+            const bool put = a.pay.kind[0] == MC_PUT;
+            if (holder) sPart[group * kP + lane] = ok ? (put ? (uT < K ? -1.0f : 0.0f) : (uT > K ? 1.0f : 0.0f)) : 0.0f;
+            __syncthreads();
+            float gp[kP];
+#pragma unroll
+            for (int p = 0; p < kP; ++p) gp[p] = sPart[group * kP + p];
+            const float rT = a.r * a.T;
+#pragma unroll
+            for (int e = 0; e < kA; ++e) {
+                const int col = a0 + e;
+                if (col < d) {
+                    const float wa = a.w[col], s0a = a.s0[col], sga = a.sigma[col];
+                    const float c = fmaf(0.5f * sga * sga, a.T, rT);  // (r + sigma^2 / 2) T
+                    float d1 = 0.0f, d2 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+#pragma unroll
+                    for (int p = 0; p < kP; ++p) {
+                        const float dl = gp[p] * wa * ex2_approx(x[p][e]);  // f' w_a S_a / S0_a
+                        const float vg = dl * s0a * (fmaf(x[p][e], 0.6931471805599453f, -c) / sga);
+                        d1 += dl;
+                        d2 += dl * dl;
+                        v1 += vg;
+                        v2 += vg * vg;
+                    }
+                    if (d1 != 0.0f || d2 != 0.0f) {
+                        atomicAdd(&sG[2 * col], d1);
+                        atomicAdd(&sG[2 * col + 1], d2);
+                        atomicAdd(&sG[2 * (d + col)], v1);
+                        atomicAdd(&sG[2 * (d + col) + 1], v2);
+                    }
+                }
+            }
+            if (holder && ok) {
+                const float g = sPart[group * kP + lane];
+                const float f = payoff_eval(a.pay.kind[0], K, INFINITY, uT, 0.0f, 0.0f, 0.0f);
+                const float rr = g * uT * a.T - a.T * f;
+                atomicAdd(&sG[4 * d], rr);
+                atomicAdd(&sG[4 * d + 1], rr * rr);
+            }
+            __syncthreads();  // the slopes are read before the next tile's last step rewrites them
+        }
         for (int pi = 0; pi < a.pay.n; ++pi) {
             const float f = (holder && ok) ? payoff_eval(a.pay.kind[pi], a.pay.strike[pi], a.pay.barrier[pi], uT,
                                                          sum * inv_m, umax, umin)
@@ -185,17 +236,43 @@ __global__ void __launch_bounds__(kBlock, 2) factor_kernel(const __grid_constant
             warp_accumulate(s_acc, a.pay.n, pi, f);
         }
     }
+    if (GREEKS) {
+        __syncthreads();
+        float *dst = a.gpart + static_cast<size_t>(blockIdx.x) * (2 * d + 1) * 2;
+        for (int i = t; i < (2 * d + 1) * 2; i += kBlock) dst[i] = sG[i];
+    }
     block_finish(s_acc, s_red, a.pay.n, a.red);
 }
 
-template <int SCHEME, bool STATS, bool EXACT>
-const void *fn() { return reinterpret_cast<const void *>(&factor_kernel<SCHEME, STATS, EXACT>); }
+// out[g] = disc (mean, standard error) of Greek g from the CTAs' sums.
+__global__ void factor_greeks_finish_kernel(int nv, int grid, const float *__restrict__ gpart, int64_t paths,
+                                            double disc, mc_result *__restrict__ out)
+{
+    const double N = static_cast<double>(paths);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nv; g += gridDim.x * blockDim.x) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < grid; ++b) {
+            s1 += static_cast<double>(gpart[(static_cast<size_t>(b) * nv + g) * 2]);
+            s2 += static_cast<double>(gpart[(static_cast<size_t>(b) * nv + g) * 2 + 1]);
+        }
+        const double mean = s1 / N, var = fmax(s2 / N - mean * mean, 0.0);
+        mc_result r;
+        r.price = disc * mean;
+        r.se = paths > 1 ? disc * sqrt(var / (N - 1.0)) : 0.0;
+        out[g] = r;
+    }
+}
+
+template <int SCHEME, bool STATS, bool EXACT, bool GREEKS = false>
+const void *fn() { return reinterpret_cast<const void *>(&factor_kernel<SCHEME, STATS, EXACT, GREEKS>); }
 
 template <int SCHEME, bool STATS>
 const void *pick(const FactorArgs &a) { return a.exact4 ? fn<SCHEME, STATS, true>() : fn<SCHEME, STATS, false>(); }
 
 const void *select(const FactorArgs &a)
 {
+    if (a.greeks)  // log-Euler, European payoff (checked by the caller)
+        return a.exact4 ? fn<MC_LOG_EULER, false, true, true>() : fn<MC_LOG_EULER, false, false, true>();
     const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
     if (a.scheme == MC_LOG_EULER) return stats ? pick<MC_LOG_EULER, true>(a) : pick<MC_LOG_EULER, false>(a);
     return stats ? pick<MC_EULER, true>(a) : pick<MC_EULER, false>(a);
@@ -206,7 +283,14 @@ const void *select(const FactorArgs &a)
 size_t factor_smem_bytes(const FactorArgs &a)
 {
     const int dp = 256 * a.G;
-    return static_cast<size_t>(a.k * dp + 3 * dp + kWarps * kP) * sizeof(float);
+    return static_cast<size_t>(a.k * dp + 3 * dp + kWarps * kP + (a.greeks ? (2 * a.d + 1) * 2 : 0)) * sizeof(float);
+}
+
+cudaError_t launch_factor_greeks_finish(const FactorArgs &a, int grid, double disc, mc_result *out, cudaStream_t s)
+{
+    const int nv = 2 * a.d + 1;
+    factor_greeks_finish_kernel<<<(nv + 255) / 256, 256, 0, s>>>(nv, grid, a.gpart, a.run.paths, disc, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_factor(const FactorArgs &a, int grid, cudaStream_t s)

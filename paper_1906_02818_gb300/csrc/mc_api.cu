@@ -484,10 +484,10 @@ int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const Payof
     const int d = m->d, k = m->n_factors, G = (d + 255) / 256, dp = 256 * G;
     const double dt = c->T / c->steps, sdt = std::sqrt(dt);
     const double cfac = c->scheme == MC_LOG_EULER ? M_LOG2E : 1.0;
-    std::vector<float> h(static_cast<size_t>(k + 6) * dp, 0.0f);
+    std::vector<float> h(static_cast<size_t>(k + 7) * dp, 0.0f);
     float *Bp = h.data(), *ep = Bp + static_cast<size_t>(k) * dp, *dr = ep + dp, *ws0 = dr + dp, *w = ws0 + dp,
-          *s0 = w + dp;
-    for (int a = 0; a < dp; ++a) s0[a] = 1.0f;  // padded assets: inert
+          *s0 = w + dp, *sgm = s0 + dp;
+    for (int a = 0; a < dp; ++a) s0[a] = sgm[a] = 1.0f;  // padded assets: inert
     for (int a = 0; a < d; ++a) {
         const double sg = m->sigma[a], cs = cfac * sdt * sg;
         double q = 0.0;
@@ -502,6 +502,7 @@ int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const Payof
         ws0[a] = static_cast<float>(wa * m->s0[a]);
         w[a] = static_cast<float>(wa);
         s0[a] = static_cast<float>(m->s0[a]);
+        sgm[a] = static_cast<float>(sg);
     }
     MC_CUDA(dev_alloc(&P->dcol, h.size() * sizeof(float)));
     MC_CUDA(cudaMemcpyAsync(P->dcol, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -519,6 +520,11 @@ int factor_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const Payof
     f.ws0 = f.drift + dp;
     f.w = f.ws0 + dp;
     f.s0 = f.w + dp;
+    f.sigma = f.s0 + dp;
+    f.greeks = 0;
+    f.T = static_cast<float>(c->T);
+    f.r = static_cast<float>(m->r);
+    f.gpart = nullptr;
     f.pay = ps;
     f.red = red;
     const int occ = factor_occupancy(f);
@@ -930,9 +936,48 @@ int mc_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays, int
     if (!greeks) return fail(MC_EINVAL, "greeks is NULL");
     if ((rc = check_model(m)) || (rc = check_cfg(c, m))) return rc;
     if (np < 1) return fail(MC_EINVAL, "n_payoff must be >= 1");
-    if (m->loadings) return fail(MC_EUNSUPPORTED, "factor model: no pathwise Greeks");
     PayoffSet ps;
     if ((rc = build_payoffs(pays, np, &ps))) return rc;
+    if (m->loadings) {
+        // factor model: delta_n, vega_n, rho of a European basket call or put
+        if (c->scheme != MC_LOG_EULER) return fail(MC_EUNSUPPORTED, "factor-model Greeks use the log-Euler scheme");
+        if (np != 1 || (ps.kind[0] != MC_CALL && ps.kind[0] != MC_PUT))
+            return fail(MC_EUNSUPPORTED, "factor-model Greeks take exactly one European call or put");
+        for (int k = 0; k < m->d; ++k)
+            if (!(m->sigma[k] > 0.0)) return fail(MC_EINVAL, "factor-model Greeks need sigma > 0 for every asset");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        mc_plan P;
+        if ((rc = plan_setup(&P, m, c, pays, np, nullptr, 1, s))) return rc;
+        FactorArgs &f = P.fa;
+        f.greeks = 1;
+        const int occ = factor_occupancy(f);
+        if (occ <= 0) return fail(MC_ECUDA, "factor-model Greeks kernel cannot be resident");
+        const int per = factor_paths_per_cta(f);
+        DeviceInfo di;
+        if ((rc = device_info(&di))) return rc;
+        // at most the plan's grid (its reduction buffers are sized for it)
+        const int64_t tiles = (c->paths + per - 1) / per;
+        P.grid = static_cast<int>(std::min(std::min(tiles, static_cast<int64_t>(occ) * di.sms),
+                                           static_cast<int64_t>(P.grid)));
+        const int G = 2 * m->d + 1;
+        DeviceArena ar;
+        MC_CUDA(dev_alloc(&ar.base, DeviceArena::up(static_cast<size_t>(P.grid) * G * 2 * sizeof(float)) +
+                                        DeviceArena::up(G * sizeof(mc_result))));
+        f.gpart = ar.take<float>(static_cast<size_t>(P.grid) * G * 2);
+        mc_result *dg = ar.take<mc_result>(G);
+        if ((rc = plan_launch(&P, P.dout, s))) return rc;
+        MC_CUDA(launch_factor_greeks_finish(f, P.grid, std::exp(-m->r * c->T), dg, s));
+        std::vector<mc_result> hg(G);
+        mc_result pr;
+        MC_CUDA(cudaMemcpyAsync(&pr, P.dout, sizeof pr, cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(hg.data(), dg, G * sizeof(mc_result), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        P.idle = true;
+        ar.idle = true;
+        if (prices) prices[0] = pr;
+        for (int k = 0; k < G; ++k) greeks[k] = hg[k];
+        return MC_OK;
+    }
     for (int i = 0; i < np; ++i)
         if (ps.kind[i] > MC_ASIAN_PUT)
             return fail(MC_EUNSUPPORTED, "payoff %d: barrier payoffs have no pathwise Greek", i);

@@ -232,7 +232,17 @@ struct FactorArgs {
     const float *Bp, *ep, *drift, *ws0, *w, *s0;
     PayoffSet pay;
     ReduceArgs red;
+    // Pathwise Greeks (log-Euler, one European call or put): per-CTA sums of
+    // the undiscounted per-path delta_a, vega_a (a < d) and rho terms and
+    // of their squares, gpart [grid][2d + 1][2].
+    int greeks;
+    const float *sigma;  // [256 G]
+    float T, r;
+    float *gpart;
 };
+// Means and standard errors of the Greeks from gpart (FP64 over the CTAs in
+// order, times disc): out [2d + 1].
+cudaError_t launch_factor_greeks_finish(const FactorArgs &a, int grid, double disc, mc_result *out, cudaStream_t s);
 size_t factor_smem_bytes(const FactorArgs &a);
 cudaError_t launch_factor(const FactorArgs &a, int grid, cudaStream_t s);
 int factor_occupancy(const FactorArgs &a);

@@ -76,9 +76,40 @@ def test_factor_model_unsupported_calls(gb):
     model = dict(kind="gbm", s0=s0, sigma=sg, loadings=B, r=0.05)
     cfg = dict(steps=4, T=1.0, paths=64)
     pays = [dict(kind="call", strike=100.0)]
-    for call in (lambda: gb.greeks(model, cfg, pays), lambda: gb.price_qmc(model, cfg, pays),
+    for call in (lambda: gb.greeks(model, cfg, [dict(kind="asian_call", strike=100.0)]),
+                 lambda: gb.greeks(model, dict(cfg, scheme="euler"), pays),
+                 lambda: gb.price_qmc(model, cfg, pays),
                  lambda: gb.price_mlmc(model, dict(cfg, precision="bf16"), pays, 64),
                  lambda: gb.price(model, dict(cfg, precision="bf16"), pays)):
         with pytest.raises(native.MCError) as e:
             call()
         assert e.value.status == native.MC_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("d,k,paths,steps,kind", [(12, 4, 3000, 8, "call"), (37, 3, 2000, 6, "put"),
+                                                  (300, 16, 1500, 4, "call")])
+def test_factor_greeks_match_oracle(gb, orc, d, k, paths, steps, kind):
+    """Pathwise delta_a, vega_a and rho of the factor-model kernel against the
+    oracle's per-path terms on the same stream: d = 12 (aligned Philox
+    blocks), d = 37 with k = 3 (unaligned, blocks straddle), d = 300 with
+    k = 16 (two warps per path group); each Greek within 2e-5 of the
+    largest |delta| (or its own size) plus the terms of the paths whose basket
+    lies within the FP32 band of the strike."""
+    s0, sg, B = workloads.basket_market_factors(d, k, seed=d)
+    w = np.full(d, 1.0 / d)
+    K = float(w @ s0) * (1.0 if kind == "call" else 1.02)
+    pay = dict(kind=kind, strike=K)
+    model = dict(kind="gbm", s0=s0, sigma=sg, loadings=B, weights=w, r=0.04)
+    pr, g = gb.greeks(model, dict(steps=steps, T=1.0, paths=paths, seed=42), [pay])
+    ref = orc.gbm_factor_greeks(s0, sg, B, 0.04, 1.0, steps, paths, pay, weights=w)
+    f, ST = orc.gbm_factor_payoffs(s0, sg, B, 0.04, 1.0, steps, paths, [pay], weights=w, terminal=True)
+    m, se = orc.mean_se(f[0])
+    assert abs(pr[0][0] - m) <= REL * abs(m) and abs(pr[0][1] - se) <= 1e-3 * se
+    U = w @ ST
+    band = np.abs(U - K) <= BAND * K
+    scale = np.max(np.abs(ref[:d].mean(axis=1)))
+    for j in range(2 * d + 1):
+        want, sej = orc.mean_se(ref[j])
+        tol = 2e-5 * max(abs(want), scale) + np.abs(ref[j][band]).sum() / paths + 1e-12
+        assert abs(g[0, j, 0] - want) <= tol, (d, j, g[0, j, 0], want, tol, int(band.sum()))
+        assert abs(g[0, j, 1] - sej) <= 1e-3 * sej + 1e-9 + np.abs(ref[j][band]).sum() / paths, (d, j)
