@@ -991,6 +991,156 @@ cudaError_t mlp_loss_grad_tc(const MlpLayout &L, const float *params, const floa
     return cudaGetLastError();
 }
 
+namespace {
+// Rows r < n of a layer's stacked pre-activations: Z += b, H = silu(Z).
+__global__ void bias_act_rows_kernel(int64_t n, int C, const float *__restrict__ b, float *__restrict__ Z,
+                                     float *__restrict__ H)
+{
+    const int64_t tot = n * C;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < tot;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float z = Z[e] + b[e % C];
+        Z[e] = z;
+        H[e] = silu_f(z);
+    }
+}
+}  // namespace
+
+size_t mlp_train_floats_d_tc(const MlpLayout &L, int64_t n, int K)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1, W = L.sizes[1];
+    const int64_t R = (K + 1) * n, Rt = round4(R);
+    size_t f = 0;
+    for (int l = 0; l < nl; ++l) f += 2 * static_cast<size_t>(round4(R * L.sizes[l + 1]));  // Z, H (stacked)
+    f += 2 * static_cast<size_t>(Rt) * W;                                                   // Abar, Zbar
+    f += 2 * static_cast<size_t>(W) * Rt;                                                   // H^T, Zbar^T
+    f += static_cast<size_t>(nl - 2) * W * W;                                               // W_l^T
+    f += static_cast<size_t>(std::max(kTcMaxSlices, kMaxSlices)) * W * W;                   // split-K partials
+    return f + 64;
+}
+
+// As mlp_loss_grad_d, with the width -> width layers' three products (the
+// stacked forward rows, the input gradient and the weight gradient) on the
+// tensor cores in three-pass TF32 (plain row-major outputs, then the same
+// element-wise steps as the SIMT path); the input layer, the scalar output
+// layer and the element-wise steps unchanged.
+cudaError_t mlp_loss_grad_d_tc(const MlpLayout &L, const float *params, const float *x, const float *t,
+                               const float *g, int64_t n, int K, const int *dirs, const float *scale,
+                               const float *weight, float *acts, float *grad, double *partial, int npartial,
+                               unsigned int *err, uint32_t cap, cudaStream_t s)
+{
+    const int nl = static_cast<int>(L.sizes.size()) - 1, W = L.sizes[1];
+    const int64_t R = (K + 1) * n, Rt = round4(R);
+    DirSet ds{};
+    ds.K = K;
+    for (int k = 0; k < K; ++k) {
+        ds.dir[k] = dirs[k];
+        ds.scale[k] = scale[k];
+        ds.weight[k] = weight[k];
+    }
+    float *p = acts;
+    auto take = [&](size_t count) {
+        float *q = p;
+        p += (count + 3) / 4 * 4;
+        return q;
+    };
+    std::vector<float *> Zs(nl), Hs(nl), WT(nl - 1, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        Zs[l] = take(static_cast<size_t>(R) * L.sizes[l + 1]);
+        Hs[l] = take(static_cast<size_t>(R) * L.sizes[l + 1]);
+    }
+    float *Abar = take(static_cast<size_t>(Rt) * W), *Zbar = take(static_cast<size_t>(Rt) * W);
+    float *Ht = take(static_cast<size_t>(W) * Rt), *Zt = take(static_cast<size_t>(W) * Rt);
+    for (int l = 1; l < nl - 1; ++l) WT[l] = take(static_cast<size_t>(W) * W);
+    float *ws = p;
+    cudaError_t e;
+    const dim3 tb(32, 8);
+    auto transpose = [&](int64_t rows, int cols, const float *src, int64_t lds, float *dst, int64_t ldd) {
+        const dim3 gt(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((cols + 31) / 32));
+        transpose_kernel<<<gt, tb, 0, s>>>(rows, cols, src, lds, dst, ldd);
+        return cudaGetLastError();
+    };
+    TfGemmArgs base{};
+    base.err = err;
+    base.cap = cap;
+    base.mode = kTfPart;
+    // C [M x N] = A [M x Kd] B [N x Kd]^T into P (row-major, ld N); split K when slices > 1
+    auto product = [&](const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int N, int Kd, int slices,
+                       float *P) {
+        TfGemmArgs a = base;
+        a.A = A; a.lda = lda;
+        a.B = B; a.ldb = ldb;
+        a.M = M; a.N = N; a.K = Kd;
+        a.kchunk = slices > 1 ? static_cast<int>(((Kd + slices - 1) / slices + 31) / 32 * 32) : Kd;
+        a.P = P;
+        const int sl = (Kd + a.kchunk - 1) / a.kchunk;
+        cudaError_t r = tf32_gemm(a, sl, s);
+        return std::make_pair(r, sl);
+    };
+    for (int l = 1; l < nl - 1; ++l)
+        if ((e = transpose(W, W, params + L.w_off[l], W, WT[l], W)) != cudaSuccess) return e;
+    // forward
+    for (int l = 0; l < nl; ++l) {
+        const int in = L.sizes[l], out = L.sizes[l + 1];
+        const bool last = l == nl - 1;
+        if (l == 0 || last) {
+            const int64_t rows = (l == 0 || K == 0) ? n : R;
+            e = gemm<false, false>(static_cast<int>(rows), out, in, l == 0 ? x : Hs[l - 1], in, params + L.w_off[l], out,
+                                   params + L.b_off[l], Zs[l], last ? nullptr : Hs[l], out, last ? 0 : 1, s,
+                                   static_cast<int>(n));
+            if (e != cudaSuccess) return e;
+            if (l == 0 && K > 0)
+                tangent_first_kernel<<<grid_for(K * n * out), 256, 0, s>>>(n, out, params + L.w_off[0], ds, Zs[0], Hs[0]);
+        } else {
+            const auto r = product(Hs[l - 1], W, WT[l], W, R, W, W, 1, Zs[l]);
+            if ((e = r.first) != cudaSuccess) return e;
+            bias_act_rows_kernel<<<grid_for(n * W), 256, 0, s>>>(n, W, params + L.b_off[l], Zs[l], Hs[l]);
+            if (K > 0) tangent_act_kernel<<<grid_for(K * n * W), 256, 0, s>>>(n, K, W, Zs[l], Hs[l]);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    dloss_seed_kernel<<<npartial, 256, 0, s>>>(n, Zs[nl - 1], t, g, ds, Zbar, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int l = nl - 1; l >= 0; --l) {
+        const int in = L.sizes[l], out = L.sizes[l + 1];
+        const int64_t rows = l == 0 ? n : R;
+        const float *hin = l == 0 ? x : Hs[l - 1];
+        if (l == 0 || l == nl - 1) {
+            const int slices = static_cast<int>(std::min<int64_t>(kMaxSlices, std::max<int64_t>(1, rows / 256)));
+            e = slices > 1 ? gemm_split_k<true, false>(in, out, static_cast<int>(rows), hin, in, Zbar, out,
+                                                       grad + L.w_off[l], slices, ws, s)
+                           : gemm<true, false>(in, out, static_cast<int>(rows), hin, in, Zbar, out, nullptr, nullptr,
+                                               grad + L.w_off[l], out, 0, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            // dW_l^T [out x in] = Zbar^T H_{l-1}: both transposed to K-major over the stacked rows
+            if ((e = transpose(R, W, Zbar, W, Zt, Rt)) != cudaSuccess) return e;
+            if ((e = transpose(R, W, hin, W, Ht, Rt)) != cudaSuccess) return e;
+            const int slices0 = static_cast<int>(std::min<int64_t>(kTcMaxSlices, std::max<int64_t>(1, (R + 255) / 256)));
+            const auto r = product(Zt, Rt, Ht, Rt, W, W, static_cast<int>(R), slices0, ws);
+            if ((e = r.first) != cudaSuccess) return e;
+            sum_slices_t_kernel<<<grid_for(static_cast<int64_t>(W) * W), 256, 0, s>>>(W, W, r.second, ws,
+                                                                                     grad + L.w_off[l]);
+        }
+        if (l == 0 && K > 0) dir_rows_kernel<<<dim3(out, K), 256, 0, s>>>(n, out, Zbar, ds, grad + L.w_off[0]);
+        colsum_kernel<<<out, 256, 0, s>>>(static_cast<int>(n), out, Zbar, grad + L.b_off[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (l > 0) {
+            if (l == nl - 1) {
+                e = gemm<false, true>(static_cast<int>(R), in, out, Zbar, out, params + L.w_off[l], out, nullptr,
+                                      nullptr, Abar, in, 0, s);
+            } else {
+                // Abar [R x in] = Zbar W_l^T: B = W_l [in x out], K-major over out
+                e = product(Zbar, W, params + L.w_off[l], W, R, W, W, 1, Abar).first;
+            }
+            if (e != cudaSuccess) return e;
+            dact_bwd_kernel<<<grid_for(n * in), 256, 0, s>>>(n, K, in, Abar, Zs[l - 1], Zbar);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 size_t mlp_train_floats(const MlpLayout &L, int64_t n)
 {
     int maxw = 0;

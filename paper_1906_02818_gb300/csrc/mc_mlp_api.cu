@@ -96,9 +96,23 @@ int loss_grad_batch_d(mc_mlp *N, const float *x, const float *t, const float *g,
                       cudaStream_t s)
 {
     if (!N->dpartial) MLP_CUDA(cudaMalloc(&N->dpartial, (1 + kMlpMaxDirs) * kPartials * sizeof(double)));
-    MLP_CUDA(mlp_loss_grad_d(N->L, N->params, x, t, g, n, dl->n_dir, dl->dir, dl->scale, dl->weight, N->work, N->grad,
-                             N->dpartial, kPartials, s));
+    if (N->train_mode == MC_MLP_TRAIN_TF32X3) {
+        if (!N->err) {
+            MLP_CUDA(cudaMalloc(&N->err, sizeof(unsigned int)));
+            MLP_CUDA(cudaMemsetAsync(N->err, 0, sizeof(unsigned int), s));
+        }
+        MLP_CUDA(mlp_loss_grad_d_tc(N->L, N->params, x, t, g, n, dl->n_dir, dl->dir, dl->scale, dl->weight, N->work,
+                                    N->grad, N->dpartial, kPartials, N->err, mbar_wait_cap(), s));
+    } else {
+        MLP_CUDA(mlp_loss_grad_d(N->L, N->params, x, t, g, n, dl->n_dir, dl->dir, dl->scale, dl->weight, N->work,
+                                 N->grad, N->dpartial, kPartials, s));
+    }
     return MC_OK;
+}
+
+size_t train_floats_d(const mc_mlp *N, int64_t n, int K)
+{
+    return N->train_mode == MC_MLP_TRAIN_TF32X3 ? mlp_train_floats_d_tc(N->L, n, K) : mlp_train_floats_d(N->L, n, K);
 }
 
 size_t train_floats(const mc_mlp *N, int64_t n)
@@ -309,7 +323,7 @@ int mc_mlp_loss_grad_d(mc_mlp *net, const float *dev_x, const float *dev_t, cons
     if (!dev_x || !dev_t || (dl->n_dir > 0 && !dev_g) || n < 1)
         return set_last_error(MC_EINVAL, "x, t (and g with directions) must be set and n >= 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((rc = ensure_work(net, mlp_train_floats_d(net->L, n, dl->n_dir)))) return rc;
+    if ((rc = ensure_work(net, train_floats_d(net, n, dl->n_dir)))) return rc;
     if ((rc = loss_grad_batch_d(net, dev_x, dev_t, dev_g, n, dl, s))) return rc;
     std::vector<double> part((1 + kMlpMaxDirs) * kPartials);
     MLP_CUDA(cudaMemcpyAsync(part.data(), net->dpartial, (1 + dl->n_dir) * kPartials * sizeof(double),
@@ -317,6 +331,7 @@ int mc_mlp_loss_grad_d(mc_mlp *net, const float *dev_x, const float *dev_t, cons
     if (host_grad)
         MLP_CUDA(cudaMemcpyAsync(host_grad, net->grad, net->L.count * sizeof(float), cudaMemcpyDeviceToHost, s));
     MLP_CUDA(cudaStreamSynchronize(s));
+    if ((rc = mlp_check_timeout(net, s))) return rc;
     if (loss_parts)
         for (int k = 0; k <= dl->n_dir; ++k) {
             double tot = 0.0;
@@ -337,7 +352,7 @@ int mc_mlp_train_d(mc_mlp *net, const float *dev_x, const float *dev_t, const fl
         return set_last_error(MC_EINVAL, "x, t (and g) set; n, epochs, batch >= 1; lr > 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t B = batch < n ? batch : n;
-    if ((rc = ensure_work(net, mlp_train_floats_d(net->L, B, dl->n_dir)))) return rc;
+    if ((rc = ensure_work(net, train_floats_d(net, B, dl->n_dir)))) return rc;
     const int n_in = net->L.sizes[0], K = dl->n_dir;
     ++net->version;
     std::vector<double> part((1 + kMlpMaxDirs) * kPartials);
@@ -358,6 +373,7 @@ int mc_mlp_train_d(mc_mlp *net, const float *dev_x, const float *dev_t, const fl
         }
     }
     MLP_CUDA(cudaStreamSynchronize(s));
+    if ((rc = mlp_check_timeout(net, s))) return rc;
     if (last_epoch_loss) *last_epoch_loss = epoch_loss / static_cast<double>((n / B) * B);
     return MC_OK;
 }

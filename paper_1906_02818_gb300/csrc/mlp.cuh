@@ -44,6 +44,13 @@ cudaError_t mlp_loss_grad_d(const MlpLayout &L, const float *params, const float
 // floats; *err is set to 1 if a bounded wait of the tensor-core kernel expires.
 bool mlp_tc_supported(const MlpLayout &L);
 size_t mlp_train_floats_tc(const MlpLayout &L, int64_t n);
+// Derivative-label loss with the width -> width products on the tensor cores
+// (three-pass TF32); acts holds mlp_train_floats_d_tc(L, n, K) floats.
+size_t mlp_train_floats_d_tc(const MlpLayout &L, int64_t n, int K);
+cudaError_t mlp_loss_grad_d_tc(const MlpLayout &L, const float *params, const float *x, const float *t,
+                               const float *g, int64_t n, int K, const int *dirs, const float *scale,
+                               const float *weight, float *acts, float *grad, double *partial, int npartial,
+                               unsigned int *err, uint32_t cap, cudaStream_t s);
 cudaError_t mlp_loss_grad_tc(const MlpLayout &L, const float *params, const float *x, const float *t, int64_t n,
                              float *acts, float *grad, double *partial, int npartial, unsigned int *err, uint32_t cap,
                              cudaStream_t s);

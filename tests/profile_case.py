@@ -11,7 +11,8 @@
   python tests/profile_case.py train --paths 262144            (paths = samples, 1 epoch;
                                                                                  --prec tf32x3: tensor-core training)
   python tests/profile_case.py train_d --paths 262144          (derivative-label training: prices + 2
-                                                                input-gradient labels, 1 epoch)
+                                                                input-gradient labels, 1 epoch;
+                                                                --prec tf32x3: tensor-core products)
   python tests/profile_case.py bridge --paths 1048576          (the In and Out Put, 25 steps)
   python tests/profile_case.py qmc --paths 262144              (points x 16 replications)
   python tests/profile_case.py mlmc --paths 16384              (correction paths, d = 64, bf16)
@@ -139,6 +140,7 @@ def _other(a, torch, workloads, gb):
         import time
         n = a.paths or (1 << 18)
         net = gb.Mlp(5, 256, 4, workloads.mlp_init())
+        net.set_train_mode("tf32x3" if a.prec == "tf32x3" else "fp32")
         g = torch.Generator("cuda").manual_seed(2)
         x = torch.rand((n, 5), device="cuda", generator=g) * 2 - 1
         t = torch.rand(n, device="cuda", generator=g)

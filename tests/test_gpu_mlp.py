@@ -290,16 +290,22 @@ def test_train_mode_checks(gb):
 S_SCALE, V_SCALE = 1.0 / 0.55, 1.0 / 0.15  # d input / d(S/K) and d input / d sigma of the surrogate's input map
 
 
+@pytest.mark.parametrize("mode", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("n", [131, 777])
-def test_derivative_loss_gradient_matches_oracle(gb, n):
+def test_derivative_loss_gradient_matches_oracle(gb, n, mode):
     """The derivative-label loss (mc_mlp_loss_grad_d: prices plus two input
     gradients, some labels missing) and its gradient against the FP64 oracle
-    (oracle/mlp.py dloss_and_grads, pinned by finite differences).  The
-    library compares scale_k dy/dx with g_k; the oracle's form is the same loss
-    with weight scale^2 and label g / scale."""
+    (oracle/mlp.py dloss_and_grads, pinned by finite differences), in both
+    training arithmetics (FP32 SIMT products; the width -> width products on
+    the tensor cores in three-pass TF32, stacked rows 393 and 2331: ragged
+    tiles and transposes).  The library compares scale_k dy/dx with g_k; the
+    oracle's form is the same loss with weight scale^2 and label g / scale."""
     import torch
     init = workloads.mlp_init(seed=9)
     net = gb.Mlp(5, 256, 4, init)
+    if mode == "tf32x3":
+        net.set_train_mode("tf32x3")
+    tol_parts = 1e-5 if mode == "fp32" else 5e-5
     x, t = _data(n, seed=4)
     rng = np.random.default_rng(5)
     g = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
@@ -314,15 +320,16 @@ def test_derivative_loss_gradient_matches_oracle(gb, n):
                                           dirs, list(np.array(weights) * sc * sc))
     g_ref = omlp.pack(G)
     for a, b in zip(parts, p_ref):
-        assert abs(a - b) <= 1e-5 * b + 1e-9, (parts, p_ref)
+        assert abs(a - b) <= tol_parts * b + 1e-9, (mode, parts, p_ref)
     scale = np.max(np.abs(g_ref))
-    print("derivative loss: parts", parts, "max grad err / max |grad| %.2e" % (np.max(np.abs(grad - g_ref)) / scale))
+    print("derivative loss (%s): parts" % mode, parts,
+          "max grad err / max |grad| %.2e" % (np.max(np.abs(grad - g_ref)) / scale))
     assert np.max(np.abs(grad - g_ref)) <= 1e-4 * scale
     # no directions: the plain loss and gradient
     parts0, grad0 = net.loss_grad_d(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), None, [], [], [])
     l_plain, g_plain = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
-    assert abs(parts0[0] - l_plain) <= 1e-6 * l_plain
-    assert np.max(np.abs(grad0 - g_plain)) <= 1e-5 * np.max(np.abs(g_plain))
+    assert abs(parts0[0] - l_plain) <= (1e-6 if mode == "fp32" else 1e-5) * l_plain
+    assert np.max(np.abs(grad0 - g_plain)) <= (1e-5 if mode == "fp32" else 1e-4) * np.max(np.abs(g_plain))
     net.close()
 
 

@@ -107,6 +107,8 @@ def test_network_kernels_time_out_and_recover(gb):
     r0 = gb.risk(pf, n_scen=2048, method="surrogate", surrogate=net, surrogate_precision="bf16")
     net.set_train_mode("tf32x3")
     l0, g0 = net.loss_grad(x[:2048], t[:2048])
+    gd = torch.from_numpy(np.random.default_rng(5).uniform(-1, 1, (3000, 2)).astype(np.float32)).cuda()
+    d0, gr0 = net.loss_grad_d(x[:2048], t[:2048], gd[:2048], [0, 1], [1.0, 1.0], [0.5, 0.5])
     with stalled():
         # inference: asynchronous, the failure shows as NaN rows ...
         y = net.forward(x, "bf16").cpu().numpy()
@@ -115,9 +117,13 @@ def test_network_kernels_time_out_and_recover(gb):
         with pytest.raises(gb.MCError) as ei:
             gb.risk(pf, n_scen=2048, method="surrogate", surrogate=net, surrogate_precision="bf16")
         assert ei.value.status == -5
-        # training products on the tensor cores (three-pass TF32)
+        # training products on the tensor cores (three-pass TF32), plain and
+        # with derivative labels
         with pytest.raises(gb.MCError) as ei:
             net.loss_grad(x[:2048], t[:2048])
+        assert ei.value.status == -5
+        with pytest.raises(gb.MCError) as ei:
+            net.loss_grad_d(x[:2048], t[:2048], gd[:2048], [0, 1], [1.0, 1.0], [0.5, 0.5])
         assert ei.value.status == -5
     assert np.array_equal(net.forward(x, "bf16").cpu().numpy(), y0)
     r1 = gb.risk(pf, n_scen=2048, method="surrogate", surrogate=net, surrogate_precision="bf16")
@@ -125,4 +131,7 @@ def test_network_kernels_time_out_and_recover(gb):
     l1, g1 = net.loss_grad(x[:2048], t[:2048])
     assert l1 == pytest.approx(l0, rel=1e-6)
     assert np.max(np.abs(g1 - g0)) <= 1e-5 * np.max(np.abs(g0))
+    d1, gr1 = net.loss_grad_d(x[:2048], t[:2048], gd[:2048], [0, 1], [1.0, 1.0], [0.5, 0.5])
+    assert np.allclose(d1, d0, rtol=1e-6, atol=0)
+    assert np.max(np.abs(gr1 - gr0)) <= 1e-5 * np.max(np.abs(gr0))
     net.close()
