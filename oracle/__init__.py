@@ -115,6 +115,8 @@ def _load():
     lib.orc_gbm_greeks.restype = i32
     lib.orc_gbm_corr_tangents.argtypes = [i32, d_p, d_p, d_p, dbl, dbl, i32, u64, i64, i64, d_p, d_p]
     lib.orc_gbm_corr_tangents.restype = i32
+    lib.orc_gbm_corr_asian_tangents.argtypes = [i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, u64, i64, i64, d_p, d_p]
+    lib.orc_gbm_corr_asian_tangents.restype = i32
     lib.orc_gbm1d_bridge_payoffs.argtypes = [dbl] * 5 + [i32, u64, i64, i64, i32, i_p, d_p, d_p, d_p]
     lib.orc_gbm1d_bridge_payoffs.restype = i32
     lib.orc_gbm_factor_payoffs.argtypes = [i32, i32, d_p, d_p, d_p, d_p, dbl, dbl, i32, i32, u64, i64, i64, i32, i_p,
@@ -372,6 +374,19 @@ def gbm_corr_tangents(s0, sigma, corr, r, T, steps, paths, seed=42, path_offset=
     return xT, tL
 
 
+def gbm_corr_asian_tangents(s0, sigma, corr, weights, r, T, steps, paths, seed=42, path_offset=0):
+    """The arithmetic average A = (1/M) sum_i U(t_i) of the basket U = w . S
+    over the steps, shape [paths], and its forward tangents dA / d Lrho[a][b]
+    (b <= a, drift held fixed), packed row by row, [d (d + 1) / 2, paths]."""
+    d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
+    A = np.empty(paths, dtype=np.float64)
+    tA = np.empty((d * (d + 1) // 2, paths), dtype=np.float64)
+    rc = _load().orc_gbm_corr_asian_tangents(d, _dptr(s0), _dptr(sigma), _dptr(corr), _dptr(w), r, T, steps, seed,
+                                             path_offset, paths, _dptr(A), _dptr(tA))
+    _check(rc, "orc_gbm_corr_asian_tangents")
+    return A, tA
+
+
 def cholesky_tangent(L, E) -> np.ndarray:
     """Forward derivative of the Cholesky factor: if A = L L^T moves by a
     symmetric E, L moves by L Phi(L^-1 E L^-T), Phi = the lower triangle with
@@ -385,9 +400,10 @@ def cholesky_tangent(L, E) -> np.ndarray:
 
 def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, seed=42, path_offset=0):
     """Per-path discounted pathwise correlation sensitivities of a European
-    basket call or put on U = sum_a w_a S_a(T) (log-Euler), forward mode:
+    basket call or put on U = sum_a w_a S_a(T), or of an Asian one on the
+    average A of U over the steps (log-Euler), forward mode:
       f     [paths]        discounted payoff
-      U     [paths]        the basket value at T
+      U     [paths]        the basket value at T (Asian: the average A)
       dl    [d, d, paths]  d/d Lrho[a][b] (b <= a; zero above the diagonal)
       drho  [d, d, paths]  d/d corr[a][b] for a != b, corr[a][b] and
                            corr[b][a] moved together; zero on the diagonal
@@ -398,8 +414,21 @@ def gbm_corr_greeks(s0, sigma, corr, r, T, steps, paths, payoff, weights=None, s
     d, s0, sigma, corr, w = _gbm_args(s0, sigma, corr, weights)
     corr = np.eye(d) if corr is None else corr
     kind, K = payoff["kind"], float(payoff["strike"])
+    if kind in ("asian_call", "asian_put"):
+        # the payoff on the average A of the basket over the steps
+        A, tA = gbm_corr_asian_tangents(s0, sigma, corr, w, r, T, steps, paths, seed, path_offset)
+        disc = np.exp(-r * T)
+        if kind == "asian_call":
+            f, slope = np.maximum(A - K, 0.0), (A > K).astype(np.float64)
+        else:
+            f, slope = np.maximum(K - A, 0.0), -(A < K).astype(np.float64)
+        dl = np.zeros((d, d, paths))
+        for a in range(d):
+            for b in range(a + 1):
+                dl[a, b] = disc * slope * tA[a * (a + 1) // 2 + b]
+        return dict(f=disc * f, U=A, dl=dl, drho=corr_chain(corr, dl))
     if kind not in ("call", "put"):
-        raise ValueError("European call or put only")
+        raise ValueError("European or Asian call or put only")
     xT, tL = gbm_corr_tangents(s0, sigma, corr, r, T, steps, paths, seed, path_offset)
     S = np.exp(xT)
     U = w @ S

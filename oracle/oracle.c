@@ -749,6 +749,55 @@ int orc_gbm_corr_tangents(int d, const double *s0, const double *sig, const doub
     return 0;
 }
 
+/* Arithmetic-average basket (Asian) version: the average                    */
+/*   A = (1/M) sum_{i=1..M} U(t_i),  U = sum_a w_a S_a,                        */
+/* and its tangents dA / d Lrho[a][b] = (1/M) sum_i w_a S_a(t_i) t_ab(t_i),   */
+/* t_ab(t_i) the running tangent of x_a above after step i.  Per path n:     */
+/*   A[n], tA[(a(a+1)/2 + b) * npaths + n].                                   */
+int orc_gbm_corr_asian_tangents(int d, const double *s0, const double *sig, const double *corr, const double *w,
+                                double r, double T, int steps, uint64_t seed, int64_t path0, int64_t npaths,
+                                double *A, double *tA)
+{
+    if (d < 1 || steps < 1 || npaths < 0 || !(T > 0.0)) return -1;
+    orc_gbm m;
+    int rc = gbm_setup(&m, d, s0, sig, corr, NULL, r, T, steps, 0, seed);
+    if (rc) return rc;
+    const double dt = T / steps, sdt = sqrt(dt);
+    const size_t nt = (size_t)d * (d + 1) / 2;
+#pragma omp parallel
+    {
+        double *x = (double *)malloc(sizeof(double) * (2 * (size_t)d + 2 * nt));
+        double *z = x + d, *t = z + d, *acc = t + nt;
+#pragma omp for schedule(static)
+        for (int64_t n = 0; n < npaths; ++n) {
+            orc_stream st;
+            stream_init(&st, seed, (uint64_t)(path0 + n));
+            for (int a = 0; a < d; ++a) x[a] = log(s0[a]);
+            for (size_t k = 0; k < nt; ++k) t[k] = acc[k] = 0.0;
+            double sumU = 0.0;
+            for (int i = 0; i < steps; ++i) {
+                for (int a = 0; a < d; ++a) z[a] = stream_normal(&st, (uint64_t)i * d + a);
+                for (int a = 0; a < d; ++a) {
+                    double y = 0.0;
+                    for (int b = 0; b <= a; ++b) y += m.Lrho[(size_t)a * d + b] * z[b];
+                    x[a] += (r - 0.5 * sig[a] * sig[a]) * dt + sdt * sig[a] * y;
+                    for (int b = 0; b <= a; ++b) t[(size_t)a * (a + 1) / 2 + b] += sdt * sig[a] * z[b];
+                }
+                for (int a = 0; a < d; ++a) {
+                    const double v = w[a] * exp(x[a]);
+                    sumU += v;
+                    for (int b = 0; b <= a; ++b) acc[(size_t)a * (a + 1) / 2 + b] += v * t[(size_t)a * (a + 1) / 2 + b];
+                }
+            }
+            A[n] = sumU / steps;
+            for (size_t k = 0; k < nt; ++k) tA[k * npaths + n] = acc[k] / steps;
+        }
+        free(x);
+    }
+    free(m.Lrho);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Heston stochastic volatility (Sec. II.A.1 names stochastic-volatility     */
 /* extensions of the scalar Euler scheme), full-truncation Euler on          */

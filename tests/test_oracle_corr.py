@@ -3,7 +3,9 @@ sensitivities to model parameters; Sec. VI.A.2 differentiates the basket
 simulation): the Cholesky tangent against LAPACK finite differences and its
 defining identity, per-path terminal tangents against bumped simulations on
 the same stream, the geometric-basket closed form within 3 SE, and common-
-random-number central differences of the arithmetic-basket price."""
+random-number central differences of the arithmetic-basket price; the
+Asian (time-averaged) basket against the same differences and, with one
+step, against the terminal basket."""
 import numpy as np
 import pytest
 
@@ -129,3 +131,37 @@ def test_factor_tangents_tie_to_delta_and_vega(orc):
     lhs = np.einsum("ab,abn->an", L, res["dl"])
     rhs = SIG[:, None] * g[d:2 * d] + (SIG ** 2 * T * S0)[:, None] * g[:d]
     assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("kind", ["asian_call", "asian_put"])
+def test_asian_basket_against_crn_differences(orc, kind):
+    """Pathwise d/d corr[a][b] of a call / put on the basket's average over
+    the steps against central differences of the per-path payoffs on the same
+    stream (corr +- h E_ab): within 3 SE of the per-path difference, and far
+    below the sensitivity itself."""
+    d, M, N = 4, 8, 1 << 13
+    pay = dict(kind=kind, strike=100.0 if kind == "asian_call" else 103.0)
+    res = orc.gbm_corr_greeks(S0, SIG, CORR, R, T, M, N, pay)
+    assert np.allclose(res["drho"], np.transpose(res["drho"], (1, 0, 2)))
+    h = 1e-6
+    for a, b in [(1, 0), (2, 0), (3, 1), (3, 2)]:
+        E = _unit(d, a, b)
+        up = orc.gbm_payoffs(S0, SIG, R, T, M, N, [pay], corr=CORR + h * E)[0]
+        dn = orc.gbm_payoffs(S0, SIG, R, T, M, N, [pay], corr=CORR - h * E)[0]
+        diff = (up - dn) / (2 * h) - res["drho"][a, b]
+        m, se = orc.mean_se(diff)
+        assert abs(m) <= 3 * se + 1e-9, (a, b, m, se)
+        assert abs(np.mean(res["drho"][a, b])) > 10 * abs(m)
+    base = orc.gbm_payoffs(S0, SIG, R, T, M, N, [pay], corr=CORR)[0]
+    assert np.allclose(res["f"], base, rtol=1e-13)
+
+
+def test_asian_with_one_step_is_the_terminal_basket(orc):
+    """With one step the average is the terminal basket: the Asian call's
+    sensitivities equal the European call's path by path."""
+    pay_a, pay_e = dict(kind="asian_call", strike=100.0), dict(kind="call", strike=100.0)
+    ra = orc.gbm_corr_greeks(S0, SIG, CORR, R, T, 1, 2000, pay_a)
+    re = orc.gbm_corr_greeks(S0, SIG, CORR, R, T, 1, 2000, pay_e)
+    scale = np.max(np.abs(re["dl"]))
+    assert np.max(np.abs(ra["dl"] - re["dl"])) <= 1e-12 * scale
+    assert np.max(np.abs(ra["f"] - re["f"])) <= 1e-12 * np.max(re["f"])
