@@ -257,7 +257,9 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
 
 /*
  * mc_corr_greeks -- pathwise sensitivities of a European basket call or put
- * on U = sum_a w_a S_a(T) to the correlation matrix (Sec. I.A.3:
+ * on U = sum_a w_a S_a(T), or (d <= 64) of an Asian one (MC_ASIAN_CALL /
+ * MC_ASIAN_PUT: on the average of U over the steps), to the correlation
+ * matrix (Sec. I.A.3:
  * sensitivities to model parameters; Sec. II.A.2: dW = sqrt(dt) diag(sigma)
  * Lrho z with Lrho the Cholesky factor of corr; Sec. VI.A.2 differentiates
  * the basket simulation), reverse mode, FP32 paths and FP64 post-processing.
@@ -266,7 +268,11 @@ int mc_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *pay
  *          the per-path vectors live in device scratch (8 d bytes per path;
  *          paths x d <= 2^31) and the path contractions run as FP32
  *          products.
- *   payoff: one MC_CALL or MC_PUT (weights from the model, 1/d if NULL).
+ *   payoff: one MC_CALL or MC_PUT, or for d <= 64 MC_ASIAN_CALL or
+ *          MC_ASIAN_PUT (weights from the model, 1/d if NULL).  The Asian
+ *          form runs every path twice: once to its average and payoff slope,
+ *          then again adding the slope-weighted outer products of every
+ *          step.
  *   price: host [1] or NULL: the discounted price and its standard error.
  *   dl:    host [d*d] or NULL, row-major: dP/dLrho[a][b] for b <= a (the
  *          entry's coefficient in dW_a, the drift (r - sigma_a^2/2) held

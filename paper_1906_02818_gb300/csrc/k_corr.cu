@@ -233,6 +233,138 @@ __global__ void corr_finish_kernel(int d, int B, const double *nb, const double 
     }
 }
 
+// ------------------------- Asian basket (d <= 64) --------------------------
+// Payoff on A = (1/M) sum_i U(t_i).  With x_a(t_i) = i drift_a + (Lhat W_i)_a
+// (log2 units, W_i the sum of the first i normal vectors), the slope of the
+// payoff in x_a(t_i) is u_{a,i} = f'(A) w_a S_a(t_i) / M, so
+//   dP/dLrho[a][b] = disc sqrt(dt) sigma_a E[sum_i u_{a,i} W_{i,b}],
+// a d x d outer product per path-step.  Per tile of 128 paths: pass 1 runs
+// the paths to their averages, payoffs and slopes f'(A); pass 2 runs them
+// again and, every step, stages u_i and W_i of all 128 paths in shared
+// memory and adds sum_p u_p W_p^T to H (each thread an 8 x 4 block, held
+// in registers across the launch).
+constexpr int kAsianStride = kD + 4;  // staged row stride (floats; 16-B aligned rows)
+
+__device__ __forceinline__ void asian_draw(bool exact, int i, int d, uint64_t n, const RoundKeys &rk,
+                                           NormalReader &rd, float (&W)[kD])
+{
+    if (exact) {
+        const int nb = d >> 2;
+#pragma unroll
+        for (int kb = 0; kb < kD / 4; ++kb) {
+            if (kb < nb) {
+                const float4 z = normals4(static_cast<uint64_t>(i) * nb + kb, n, rk);
+                W[4 * kb] += z.x;
+                W[4 * kb + 1] += z.y;
+                W[4 * kb + 2] += z.z;
+                W[4 * kb + 3] += z.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kD; ++k)
+            if (k < d) W[k] += rd.get(static_cast<uint64_t>(i) * d + k);
+    }
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(kThreads) corr_asian_kernel(const __grid_constant__ CorrArgs a, const CorrConst c)
+{
+    extern __shared__ __align__(16) float s_dyn[];
+    float *sv = s_dyn;                            // [kThreads][kAsianStride] u of the staged paths
+    float *sw = s_dyn + kThreads * kAsianStride;  // [kThreads][kAsianStride] W of the staged paths
+    __shared__ AccSlot s_acc[(kThreads / 32) * 2];
+    __shared__ double s_red[32];
+    const int t = threadIdx.x;
+    if (t < (kThreads / 32) * 2) s_acc[t] = 0.0f;
+    __syncthreads();
+
+    const int M = a.run.steps, d = a.d;
+    const float inv_m = 1.0f / static_cast<float>(M);
+    const int64_t ntiles = (a.run.paths + kThreads - 1) / kThreads;
+    const int rg = t >> 4, cg = t & 15;  // H rows 8 rg .. 8 rg + 7, columns 4 cg .. 4 cg + 3
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    int64_t cnt = 0;
+    const bool put = a.kind == MC_ASIAN_PUT;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t nl = tile * kThreads + t;
+        const bool valid = nl < a.run.paths;
+        const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
+        const int64_t left = a.run.paths - tile * kThreads;
+        cnt += left < kThreads ? left : kThreads;
+        // pass 1: the average, the payoff and its slope
+        float W[kD];
+#pragma unroll
+        for (int k = 0; k < kD; ++k) W[k] = 0.0f;
+        NormalReader rd;
+        rd.init(n, a.run.rk);
+        float sumU = 0.0f;
+        for (int i = 0; i < M; ++i) {
+            asian_draw(EXACT, i, d, n, a.run.rk, rd, W);
+            const float fi = static_cast<float>(i + 1);
+            float U = 0.0f;
+#pragma unroll
+            for (int ra = 0; ra < kD; ++ra) {
+                float y = fi * c.drift[ra];
+#pragma unroll
+                for (int k = 0; k <= ra; ++k) y = fmaf(c.L[ra * (ra + 1) / 2 + k], W[k], y);
+                U = fmaf(c.ws0[ra], ex2_approx(y), U);
+            }
+            sumU += U;
+        }
+        const float A = sumU * inv_m;
+        const float f = put ? fmaxf(a.strike - A, 0.0f) : fmaxf(A - a.strike, 0.0f);
+        const float slope = valid ? (put ? (A < a.strike ? -1.0f : 0.0f) : (A > a.strike ? 1.0f : 0.0f)) : 0.0f;
+        warp_accumulate(s_acc, 1, 0, valid ? f : 0.0f);
+        // pass 2: the same paths again, u_i W_i^T of all of them every step
+        const float su = slope * inv_m;
+        const bool any = __syncthreads_or(su != 0.0f);  // a tile without slopes adds nothing
+#pragma unroll
+        for (int k = 0; k < kD; ++k) W[k] = 0.0f;
+        rd.init(n, a.run.rk);
+        for (int i = 0; any && i < M; ++i) {
+            asian_draw(EXACT, i, d, n, a.run.rk, rd, W);
+            const float fi = static_cast<float>(i + 1);
+            float *vr = sv + t * kAsianStride, *wr = sw + t * kAsianStride;
+#pragma unroll
+            for (int ra = 0; ra < kD; ++ra) {
+                float y = fi * c.drift[ra];
+#pragma unroll
+                for (int k = 0; k <= ra; ++k) y = fmaf(c.L[ra * (ra + 1) / 2 + k], W[k], y);
+                vr[ra] = su * c.ws0[ra] * ex2_approx(y);
+                wr[ra] = W[ra];
+            }
+            __syncthreads();
+            for (int p = 0; p < kThreads; ++p) {
+                const float4 v0 = *reinterpret_cast<const float4 *>(sv + p * kAsianStride + 8 * rg);
+                const float4 v1 = *reinterpret_cast<const float4 *>(sv + p * kAsianStride + 8 * rg + 4);
+                const float4 w4 = *reinterpret_cast<const float4 *>(sw + p * kAsianStride + 4 * cg);
+                const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(vv[r], ww[q], acc[r][q]);
+            }
+            __syncthreads();  // the staged rows are read before the next step rewrites them
+        }
+    }
+    float *dst = a.partials + static_cast<size_t>(blockIdx.x) * kD * kD;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[(8 * rg + r) * kD + 4 * cg + q] = acc[r][q];
+    if (t == 0) a.counts[blockIdx.x] = static_cast<double>(cnt);
+    block_finish(s_acc, s_red, 1, a.red);
+}
+
+size_t corr_asian_smem() { return 2 * static_cast<size_t>(kThreads) * kAsianStride * sizeof(float); }
+
 // ------------------------- wide baskets (d > 64) ---------------------------
 // Same estimator, with the per-path vectors in global memory and the two
 // path-sized contractions as FP32 products:
@@ -399,18 +531,29 @@ __global__ void corr_sym_kernel(int d, const double *__restrict__ Sm, double *__
     }
 }
 
+bool corr_asian(const CorrArgs &a) { return a.kind == MC_ASIAN_CALL || a.kind == MC_ASIAN_PUT; }
+
 const void *corr_select(const CorrArgs &a)
 {
+    if (corr_asian(a))
+        return a.exact4 ? reinterpret_cast<const void *>(&corr_asian_kernel<true>)
+                        : reinterpret_cast<const void *>(&corr_asian_kernel<false>);
     return a.exact4 ? reinterpret_cast<const void *>(&corr_path_kernel<true>)
                     : reinterpret_cast<const void *>(&corr_path_kernel<false>);
 }
+
+size_t corr_dyn_smem(const CorrArgs &a) { return corr_asian(a) ? corr_asian_smem() : 0; }
 
 }  // namespace
 
 int corr_occupancy(const CorrArgs &a)
 {
+    const size_t smem = corr_dyn_smem(a);
+    if (smem > 0 && cudaFuncSetAttribute(corr_select(a), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)) != cudaSuccess)
+        return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, corr_select(a), kThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, corr_select(a), kThreads, smem) != cudaSuccess) return 0;
     return n;
 }
 
@@ -423,7 +566,13 @@ cudaError_t launch_corr(const CorrArgs &a, const CorrConst &c, int grid, int bat
                         mc_result *res_dl, mc_result *res_drho, cudaStream_t s)
 {
     void *args[] = {const_cast<CorrArgs *>(&a), const_cast<CorrConst *>(&c)};
-    cudaError_t e = cudaLaunchKernel(corr_select(a), dim3(grid), dim3(kThreads), args, 0, s);
+    const size_t dyn = corr_dyn_smem(a);
+    if (dyn > 0) {
+        const cudaError_t ea = cudaFuncSetAttribute(corr_select(a), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    static_cast<int>(dyn));
+        if (ea != cudaSuccess) return ea;
+    }
+    cudaError_t e = cudaLaunchKernel(corr_select(a), dim3(grid), dim3(kThreads), args, dyn, s);
     if (e != cudaSuccess) return e;
     corr_batch_kernel<<<batches, 256, 0, s>>>(a.partials, a.counts, grid, batches, Hb, nb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

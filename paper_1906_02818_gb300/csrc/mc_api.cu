@@ -1206,8 +1206,11 @@ int mc_corr_greeks(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pay,
     if (c->scheme != MC_LOG_EULER) return fail(MC_EUNSUPPORTED, "correlation sensitivities use the log-Euler scheme");
     if (c->precision != MC_FP32) return fail(MC_EUNSUPPORTED, "correlation sensitivities are computed in FP32");
     if (c->monitoring != MC_DISCRETE) return fail(MC_EUNSUPPORTED, "correlation sensitivities: European payoffs only");
-    if (pay->kind != MC_CALL && pay->kind != MC_PUT)
-        return fail(MC_EUNSUPPORTED, "correlation sensitivities: a European basket call or put");
+    const bool asian = pay->kind == MC_ASIAN_CALL || pay->kind == MC_ASIAN_PUT;
+    if (pay->kind != MC_CALL && pay->kind != MC_PUT && !asian)
+        return fail(MC_EUNSUPPORTED, "correlation sensitivities: a European or Asian basket call or put");
+    if (asian && m->d > kCorrMaxD)
+        return fail(MC_EUNSUPPORTED, "correlation sensitivities of Asian payoffs for d <= %d", kCorrMaxD);
     if (!std::isfinite(pay->strike)) return fail(MC_EINVAL, "strike not finite");
     DeviceInfo di;
     if ((rc = device_info(&di))) return rc;

@@ -262,7 +262,8 @@ struct CorrArgs {
     PathRun run;
     int d;
     int exact4;         // d % 4 == 0: every step is d/4 whole Philox blocks
-    int kind;           // MC_CALL or MC_PUT on U = sum_a w_a S_a(T)
+    int kind;           // MC_CALL or MC_PUT on U = sum_a w_a S_a(T); MC_ASIAN_CALL or
+                        // MC_ASIAN_PUT on the average of U over the steps (d <= 64)
     float strike;
     float *partials;    // [grid][64 x 64] per-CTA sums of u_a W_b (FP32)
     double *counts;     // [grid] paths simulated by each CTA

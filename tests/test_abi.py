@@ -168,7 +168,9 @@ def test_correlation_sensitivity_checks(lib):
             (dict(d=4, loadings=np.full((4, 2), 0.5)), native.MC_EUNSUPPORTED, "2 <= d <= 512"),
             (dict(d=4, scheme="euler"), native.MC_EUNSUPPORTED, "log-Euler"),
             (dict(d=4, precision="bf16"), native.MC_EUNSUPPORTED, "FP32"),
-            (dict(d=4, payoffs=[dict(kind="asian_call", strike=100.0)]), native.MC_EUNSUPPORTED, "European"),
+            (dict(d=65, payoffs=[dict(kind="asian_call", strike=100.0)]), native.MC_EUNSUPPORTED, "Asian"),
+            (dict(d=4, payoffs=[dict(kind="uo_put", strike=100.0, barrier=130.0)]), native.MC_EUNSUPPORTED,
+             "European"),
             (dict(d=4, payoffs=[dict(kind="uo_call", strike=100.0, barrier=130.0)]), native.MC_EUNSUPPORTED,
              "European"),
             (dict(d=2, corr=np.array([[1.0, 0.5], [0.4, 1.0]])), native.MC_EINVAL, "symmetric")]:
