@@ -293,6 +293,12 @@ def config_c2(torch, gb, orc, hw, flush, reps, headline):
             rec["roofline_tensor"] = hw.tensor(ps / t * d * (d + 1), "fp8" if prec == "fp8" else "bf16",
                                                f"{d * (d + 1)} flop per path-step (triangular contraction)")
         out["precisions"][prec] = rec
+    # correlation sensitivities of the ATM basket call on the same paths (FP32)
+    tc, _, (cp, _, _) = time_call(torch, lambda: gb.corr_greeks(model, dict(base), w["payoffs"][0]), 3)
+    out["corr_greeks"] = {"ms": tc * 1e3, "value": ps / tc, "unit": UNIT, "price": list(cp),
+                          "what": f"dP/dLrho and dP/dcorr ({d * (d - 1) // 2} pairs) of the ATM basket call, "
+                                  "one mc_corr_greeks call (set-up, path kernel, FP64 Cholesky adjoint per batch)",
+                          "roofline": hw.sfu(ps / tc, normals=d, ex2=0, what=f"{d} normals")}
     return out
 
 
@@ -452,6 +458,12 @@ def config_c5(torch, gb, orc, hw, flush, reps):
                              "what": "price + 512 deltas + 512 vegas + rho from the same paths",
                              "delta_sum": float(g[0, :d, 0].sum())}
         out["precisions"][prec] = rec
+    # correlation sensitivities (FP32 paths; the wide path's device buffers and products)
+    tc, _, (cp, _, _) = time_call(torch, lambda: gb.corr_greeks(model, dict(base), pays[0]), 1)
+    out["corr_greeks"] = {"ms": tc * 1e3, "value": ps / tc, "unit": UNIT, "price": list(cp),
+                          "what": f"dP/dLrho and dP/dcorr ({d * (d - 1) // 2} pairs) of the ATM basket call, one "
+                                  "mc_corr_greeks call (summed normals, two FP32 products, FP64 adjoint per batch)",
+                          "roofline": hw.sfu(ps / tc, normals=d, what=f"{d} normals")}
     return out
 
 
