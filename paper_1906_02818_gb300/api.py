@@ -135,8 +135,14 @@ def greeks(model: dict, cfg: dict, payoffs, stream=None):
     gr = (McResult * (mm.n_payoff * G))()
     check(L.mc_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, pr, gr,
                       _stream_handle(stream)))
-    g = np.array([[r.price, r.se] for r in gr]).reshape(mm.n_payoff, G, 2)
+    g = _results_np(gr, (mm.n_payoff, G, 2))
     return [(r.price, r.se) for r in pr], g
+
+
+def _results_np(arr, shape):
+    """A ctypes array of mc_result (two doubles each) as a float64 copy of
+    the given shape, without a Python loop over the entries."""
+    return np.frombuffer(arr, dtype=np.float64).reshape(shape).copy()
 
 
 def corr_greeks(model: dict, cfg: dict, payoff: dict, stream=None):
@@ -152,8 +158,8 @@ def corr_greeks(model: dict, cfg: dict, payoff: dict, stream=None):
     dr = (McResult * (d * d))()
     check(L.mc_corr_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, ctypes.byref(pr), dl, dr,
                            _stream_handle(stream)))
-    a = np.array([[r.price, r.se] for r in dl]).reshape(d, d, 2)
-    b = np.array([[r.price, r.se] for r in dr]).reshape(d, d, 2)
+    a = _results_np(dl, (d, d, 2))
+    b = _results_np(dr, (d, d, 2))
     return (pr.price, pr.se), a, b
 
 

@@ -490,32 +490,41 @@ __global__ void corr_adj_a_kernel(int d, const double *__restrict__ L, const dou
     }
 }
 
-// X_k = P_k Lrho^-1 in place, one thread per row: x_ij = (p_ij - sum_{q > j} x_iq L_qj) / L_jj, j = i .. 0.
-__global__ void corr_adj_x_kernel(int d, const double *__restrict__ L, double *__restrict__ Pm)
+// X_k = P_k Lrho^-1 in place, one warp per row: x_ij = (p_ij - sum_{q > j} x_iq L_qj) / L_jj,
+// j = i .. 0, the sum split over the lanes.
+__global__ void __launch_bounds__(256) corr_adj_x_kernel(int d, const double *__restrict__ L, double *__restrict__ Pm)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d) return;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= d) return;  // whole warps
     double *X = Pm + static_cast<int64_t>(blockIdx.y) * d * d + static_cast<int64_t>(i) * d;
     for (int j = i; j >= 0; --j) {
-        double s = X[j];
-        for (int q = j + 1; q <= i; ++q) s = fma(-X[q], L[static_cast<int64_t>(q) * d + j], s);
-        X[j] = s / L[static_cast<int64_t>(j) * d + j];
+        double s = 0.0;
+        for (int q = j + 1 + lane; q <= i; q += 32) s = fma(X[q], L[static_cast<int64_t>(q) * d + j], s);
+        s = warp_sum_d(s);
+        if (lane == 0) X[j] = (X[j] - s) / L[static_cast<int64_t>(j) * d + j];
+        __syncwarp();
     }
 }
 
-// S_k = Lrho^-T X_k, one thread per column: s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii, i = d-1 .. 0.
-__global__ void corr_adj_s_kernel(int d, const double *__restrict__ L, const double *__restrict__ Pm,
-                                  double *__restrict__ Sm)
+// S_k = Lrho^-T X_k, one warp per column: s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii,
+// i = d-1 .. 0, the sum split over the lanes.
+__global__ void __launch_bounds__(256) corr_adj_s_kernel(int d, const double *__restrict__ L,
+                                                         const double *__restrict__ Pm, double *__restrict__ Sm)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d) return;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= d) return;  // whole warps
     const int64_t off = static_cast<int64_t>(blockIdx.y) * d * d;
     const double *X = Pm + off;
     double *S = Sm + off;
     for (int i = d - 1; i >= 0; --i) {
-        double s = X[static_cast<int64_t>(i) * d + j];
-        for (int q = i + 1; q < d; ++q) s = fma(-L[static_cast<int64_t>(q) * d + i], S[static_cast<int64_t>(q) * d + j], s);
-        S[static_cast<int64_t>(i) * d + j] = s / L[static_cast<int64_t>(i) * d + i];
+        double s = 0.0;
+        for (int q = i + 1 + lane; q < d; q += 32)
+            s = fma(L[static_cast<int64_t>(q) * d + i], S[static_cast<int64_t>(q) * d + j], s);
+        s = warp_sum_d(s);
+        if (lane == 0) S[static_cast<int64_t>(i) * d + j] = (X[static_cast<int64_t>(i) * d + j] - s) / L[static_cast<int64_t>(i) * d + i];
+        __syncwarp();
     }
 }
 
@@ -612,10 +621,10 @@ cudaError_t launch_corr_wide(const CorrArgs &a, const CorrWide &w, int grid, cud
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     corr_adj_a_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, w.L, w.out_dl, w.Pm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const unsigned gr = static_cast<unsigned>((d + 63) / 64);
-    corr_adj_x_kernel<<<dim3(gr, B + 1), 64, 0, s>>>(d, w.L, w.Pm);
+    const unsigned gr = static_cast<unsigned>((d + 7) / 8);  // 8 rows (columns) per block of 256
+    corr_adj_x_kernel<<<dim3(gr, B + 1), 256, 0, s>>>(d, w.L, w.Pm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    corr_adj_s_kernel<<<dim3(gr, B + 1), 64, 0, s>>>(d, w.L, w.Pm, w.Sm);
+    corr_adj_s_kernel<<<dim3(gr, B + 1), 256, 0, s>>>(d, w.L, w.Pm, w.Sm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     corr_sym_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, w.Sm, w.out_drho);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
