@@ -689,9 +689,15 @@ int plan_setup(mc_plan *P, const mc_model *m, const mc_sim_cfg *c, const mc_payo
             resident = basket_tc_occupancy(P->prec, ta) * di.sms;
         } else {
             P->kk = K_BASKET_FP32;
-            // one block of 640 per SM when every SM gets at least two rounds
-            // of paths, else blocks of 128 (5 per SM) to spread small runs
-            P->block = (c->paths >= static_cast<int64_t>(2) * 640 * di.sms) ? 640 : 128;
+            // Large runs: one block per SM, as many rounds of paths as 640
+            // threads need, the block trimmed (to whole warps) so that those
+            // rounds cover the paths on every SM; small runs (or a trimmed
+            // block under 16 warps): blocks of 128, 5 per SM, to spread them.
+            const int64_t per_round = static_cast<int64_t>(640) * di.sms;
+            const int64_t rounds = (c->paths + per_round - 1) / per_round;
+            const int64_t per_sm = (c->paths + rounds * di.sms - 1) / (rounds * di.sms);
+            const int trimmed = static_cast<int>(std::min<int64_t>(640, (per_sm + 31) / 32 * 32));
+            P->block = (c->paths >= 2 * per_round || trimmed >= 512) && c->paths >= per_round ? trimmed : 128;
             MC_CUDA(launch_scale_factor(d, P->dL, P->dsig, cfac, sdt, m->r, dt, c->scheme, P->dLp, P->ddrift, s));
             std::vector<float> Lp(tri), drift(d);
             MC_CUDA(cudaMemcpyAsync(&status, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
