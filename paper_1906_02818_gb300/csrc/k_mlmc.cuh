@@ -5,7 +5,8 @@
 // the first term from many tensor-core paths (mc_plan_execute with BF16 /
 // FP16 / E4M3 operands), the second from fewer paths simulated twice on the
 // same normals by this kernel:
-//   pass 1: the FP32 contraction (dW = Lhat z, the FP32 basket kernel's step);
+//   pass 1: the FP32 contraction (dW = Lhat z, the FP32 basket kernel's step,
+//           in the same packed FP32x2 FMAs);
 //   pass 2: the tensor-core arithmetic with FP32 accumulation: normals rounded
 //           to the operand type (E4M3 scaled per step by 448 / max|z| of the
 //           path's row and dequantised by max|z| / 448), the factor rounded as
@@ -67,20 +68,26 @@ __device__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n)
                 deq = amax / 448.0f;
             }
         }
-        float acc[kD];
+        // dW = Lhat z column by column in packed FP32x2 FMAs over row pairs
+        // (each lane an ordinary fma, the columns in order per element)
+        f32x2 acc2[kD / 2];
 #pragma unroll
-        for (int j = 0; j < kD; ++j) acc[j] = 0.0f;
+        for (int q = 0; q < kD / 2; ++q) acc2[q] = pack2(0.0f, 0.0f);
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             float z = k < d ? rd.get(static_cast<uint64_t>(i) * d + k) : 0.0f;
             if (QUANT) z = round_operand<PREC>(PREC == MC_FP8E4M3 ? z * sz : z);
+            const f32x2 z2 = pack2(z, z);
 #pragma unroll
-            for (int j = k; j < kD; ++j) acc[j] = fmaf(QUANT ? c.Lq[j * (j + 1) / 2 + k] : c.L[j * (j + 1) / 2 + k], z, acc[j]);
+            for (int q = k / 2; q < kD / 2; ++q)
+                acc2[q] = ffma2(QUANT ? c.Lqp[basket_pair_base(kD, k) + q - k / 2] : c.Lp[basket_pair_base(kD, k) + q - k / 2],
+                                z2, acc2[q]);
         }
         float u = 0.0f;
 #pragma unroll
         for (int j = 0; j < kD; ++j) {
-            const float dw = QUANT ? c.csq[j] * (acc[j] * deq) : acc[j];
+            const float aj = (j & 1) ? hi_of(acc2[j >> 1]) : lo_of(acc2[j >> 1]);
+            const float dw = QUANT ? c.csq[j] * (aj * deq) : aj;
             if (SCHEME == MC_LOG_EULER) {
                 x[j] += c.drift[j] + dw;
                 if (STATS) u = fmaf(c.ws0[j], ex2_approx(x[j]), u);

@@ -1362,10 +1362,12 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     if (status) return fail(MC_ENOTPSD, "correlation matrix is not positive definite");
     MlmcConst k;
     std::memset(&k, 0, sizeof k);
+    float *kL = reinterpret_cast<float *>(k.Lp), *kLq = reinterpret_cast<float *>(k.Lqp);
     for (int a = 0; a < 64; ++a) {
-        for (int j = 0; j <= a; ++j) {
-            k.L[a * (a + 1) / 2 + j] = a < d ? Lp[static_cast<size_t>(a) * (a + 1) / 2 + j] : 0.0f;
-            k.Lq[a * (a + 1) / 2 + j] = Lq[a * (a + 1) / 2 + j];
+        for (int j = 0; j <= a; ++j) {  // row a of column j: pair a / 2 of the column's run, lane a & 1
+            const int e = 2 * (basket_pair_base(64, j) + a / 2 - j / 2) + (a & 1);
+            kL[e] = a < d ? Lp[static_cast<size_t>(a) * (a + 1) / 2 + j] : 0.0f;
+            kLq[e] = Lq[a * (a + 1) / 2 + j];
         }
         k.csq[a] = csq[a];
         if (a < d) {

@@ -172,8 +172,11 @@ int greeks_block();
 // Lq (packed lower triangles), Lq's column scales, drift and weights.
 constexpr int kMlmcMaxPayoffs = 10;  // 3 accumulated values per payoff
 struct MlmcConst {
-    float L[64 * 65 / 2];
-    float Lq[64 * 65 / 2];
+    // the FP32 factor and its tensor-core rounding as column pairs (the
+    // BasketConst<64> layout: column k's pairs q >= k/2 at basket_pair_base),
+    // 64-bit operands of the packed FMAs; zero above the diagonal and beyond d
+    unsigned long long Lp[basket_pair_count(64)];
+    unsigned long long Lqp[basket_pair_count(64)];
     float csq[64];
     float drift[64];
     float ws0[64];
