@@ -73,5 +73,6 @@ int mlmc_occupancy(int prec, const MlmcArgs &a)
 }
 
 int mlmc_block() { return kBlock; }
+int mlmc_paths_per_block() { return kHalf; }
 
 }  // namespace gbmc

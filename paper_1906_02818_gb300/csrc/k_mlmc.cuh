@@ -12,8 +12,11 @@
 //           path's row and dequantised by max|z| / 448), the factor rounded as
 //           the tensor-core factor tile (rows scaled by s_n, column scale
 //           cs_n = c sqrt(dt) sigma_n / s_n folded after the sum).
-// Per path and payoff it accumulates f_fp32 - f_q, f_fp32 and f_q.  One
-// thread per path, d <= 64 padded to 64.  The kernels are instantiated per
+// Per path and payoff it accumulates f_fp32 - f_q, f_fp32 and f_q.  A block
+// carries 64 paths at a time: its first two warps run them in FP32, the other
+// two in the rounded arithmetic (twice the warps for the few paths this
+// level takes), and the rounded payoffs pass through shared memory; d <= 64
+// padded to 64.  The kernels are instantiated per
 // operand type in k_mlmc_{bf16,fp16,fp8}.cu; k_mlmc.cu holds the dispatch,
 // the factor preparation and the launchers.
 #pragma once
@@ -28,6 +31,7 @@ namespace {
 
 constexpr int kD = 64;
 constexpr int kBlock = 128;
+constexpr int kHalf = kBlock / 2;  // paths a block carries at a time
 
 template <int PREC>
 __device__ __forceinline__ float round_operand(float v)
@@ -113,38 +117,41 @@ __global__ void __launch_bounds__(kBlock) mlmc_coupled_kernel(const __grid_const
 {
     __shared__ AccSlot s_acc[(kBlock / 32) * MC_MAX_PAYOFFS * 2];
     __shared__ double s_red[32];
+    __shared__ float s_fq[kMlmcMaxPayoffs][kHalf];
     const int np = a.pay.n, nv = 3 * np;
     for (int i = threadIdx.x; i < (kBlock / 32) * nv * 2; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();
-    const int64_t gthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int half = threadIdx.x / kHalf, lt = threadIdx.x % kHalf;  // half: warp-uniform
+    const int64_t gpaths = static_cast<int64_t>(gridDim.x) * kHalf;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * kHalf + lt;
     for (int it = 0; it < a.run.ppt; ++it) {
-        const int64_t nl = tid + it * gthreads;
+        const int64_t nl = tid + it * gpaths;
         const bool valid = nl < a.run.paths;
         const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
-        float fe[kMlmcMaxPayoffs], fq[kMlmcMaxPayoffs];
-        {
-            const PathOut o = simulate<PREC, SCHEME, STATS, false>(a, c, n);
+        const PathOut o = half ? simulate<PREC, SCHEME, STATS, true>(a, c, n) : simulate<PREC, SCHEME, STATS, false>(a, c, n);
+        float f[kMlmcMaxPayoffs];
+#pragma unroll
+        for (int p = 0; p < kMlmcMaxPayoffs; ++p)
+            f[p] = p < np ? payoff_eval(a.pay.kind[p], a.pay.strike[p], a.pay.barrier[p], o.uT, o.avg, o.umax, o.umin)
+                          : 0.0f;
+        if (half) {
 #pragma unroll
             for (int p = 0; p < kMlmcMaxPayoffs; ++p)
-                fe[p] = p < np ? payoff_eval(a.pay.kind[p], a.pay.strike[p], a.pay.barrier[p], o.uT, o.avg, o.umax, o.umin)
-                               : 0.0f;
+                if (p < np) s_fq[p][lt] = f[p];
         }
-        {
-            const PathOut o = simulate<PREC, SCHEME, STATS, true>(a, c, n);
+        __syncthreads();
+        if (!half) {
 #pragma unroll
-            for (int p = 0; p < kMlmcMaxPayoffs; ++p)
-                fq[p] = p < np ? payoff_eval(a.pay.kind[p], a.pay.strike[p], a.pay.barrier[p], o.uT, o.avg, o.umax, o.umin)
-                               : 0.0f;
-        }
-#pragma unroll
-        for (int p = 0; p < kMlmcMaxPayoffs; ++p) {
-            if (p < np) {
-                warp_accumulate(s_acc, nv, p, valid ? fe[p] - fq[p] : 0.0f);
-                warp_accumulate(s_acc, nv, np + p, valid ? fe[p] : 0.0f);
-                warp_accumulate(s_acc, nv, 2 * np + p, valid ? fq[p] : 0.0f);
+            for (int p = 0; p < kMlmcMaxPayoffs; ++p) {
+                if (p < np) {
+                    const float fe = f[p], fq = s_fq[p][lt];
+                    warp_accumulate(s_acc, nv, p, valid ? fe - fq : 0.0f);
+                    warp_accumulate(s_acc, nv, np + p, valid ? fe : 0.0f);
+                    warp_accumulate(s_acc, nv, 2 * np + p, valid ? fq : 0.0f);
+                }
             }
         }
+        __syncthreads();  // the rounded payoffs are read before the next paths write theirs
     }
     block_finish(s_acc, s_red, nv, a.red);
 }

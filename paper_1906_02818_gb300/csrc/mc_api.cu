@@ -1390,11 +1390,10 @@ int mc_price_mlmc(const mc_model *m, const mc_sim_cfg *c, const mc_payoff *pays,
     a.scheme = c->scheme;
     a.pay = ps;
     const int nv = 3 * np;
-    const int block = mlmc_block();
     const int occ = mlmc_occupancy(c->precision, a);
     if (occ <= 0) return fail(MC_ECUDA, "correction kernel cannot be resident");
     int grid = 0, ppt = 1;
-    size_grid(paths_ref, block, occ * di.sms, &grid, &ppt);
+    size_grid(paths_ref, mlmc_paths_per_block(), occ * di.sms, &grid, &ppt);
     a.run.ppt = ppt;
     MC_CUDA(dev_alloc(&P.partials, static_cast<size_t>(grid) * nv * 2 * sizeof(float)));
     MC_CUDA(dev_alloc(&P.ticket, sizeof(unsigned int)));

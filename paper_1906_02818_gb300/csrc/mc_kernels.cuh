@@ -195,6 +195,7 @@ cudaError_t launch_mlmc_prep(int prec, int d, const double *L, const double *sig
 cudaError_t launch_mlmc_coupled(int prec, const MlmcArgs &a, const MlmcConst &c, int grid, cudaStream_t s);
 int mlmc_occupancy(int prec, const MlmcArgs &a);
 int mlmc_block();
+int mlmc_paths_per_block();  // paths a block carries at a time (the grid's unit)
 
 // Randomised quasi-Monte Carlo (k_qmc.cu): Sobol direction words of up to
 // kQmcMaxDims dimensions, the FP32 factor Lhat (packed, rows of width
