@@ -49,10 +49,12 @@ struct PathOut {
     float uT, avg, umax, umin;
 };
 
-// One path of the correlated GBM basket; QUANT selects the tensor-core
-// operand arithmetic (pass 2) instead of the FP32 contraction (pass 1).
-template <int PREC, int SCHEME, bool STATS, bool QUANT>
-__device__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n)
+// One path of the correlated GBM basket; quant selects the tensor-core
+// operand arithmetic (pass 2) instead of the FP32 contraction (pass 1).  One
+// out-of-line copy serves both passes: the two fully unrolled copies did not
+// fit the instruction cache together (no_instruction stalls).
+template <int PREC, int SCHEME, bool STATS>
+__device__ __noinline__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n, bool quant)
 {
     const int M = a.run.steps, d = a.d;
     NormalReader rd;
@@ -64,7 +66,7 @@ __device__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n)
     for (int i = 0; i < M; ++i) {
         // E4M3: the row scale needs the step's largest |z| first
         float sz = 1.0f, deq = 1.0f;
-        if (QUANT && PREC == MC_FP8E4M3) {
+        if (quant && PREC == MC_FP8E4M3) {
             float amax = 0.0f;
             for (int k = 0; k < d; ++k) amax = fmaxf(amax, fabsf(rd.get(static_cast<uint64_t>(i) * d + k)));
             if (amax > 0.0f) {
@@ -80,18 +82,18 @@ __device__ PathOut simulate(const MlmcArgs &a, const MlmcConst &c, uint64_t n)
 #pragma unroll
         for (int k = 0; k < kD; ++k) {
             float z = k < d ? rd.get(static_cast<uint64_t>(i) * d + k) : 0.0f;
-            if (QUANT) z = round_operand<PREC>(PREC == MC_FP8E4M3 ? z * sz : z);
+            if (quant) z = round_operand<PREC>(PREC == MC_FP8E4M3 ? z * sz : z);
             const f32x2 z2 = pack2(z, z);
 #pragma unroll
             for (int q = k / 2; q < kD / 2; ++q)
-                acc2[q] = ffma2(QUANT ? c.Lqp[basket_pair_base(kD, k) + q - k / 2] : c.Lp[basket_pair_base(kD, k) + q - k / 2],
+                acc2[q] = ffma2(quant ? c.Lqp[basket_pair_base(kD, k) + q - k / 2] : c.Lp[basket_pair_base(kD, k) + q - k / 2],
                                 z2, acc2[q]);
         }
         float u = 0.0f;
 #pragma unroll
         for (int j = 0; j < kD; ++j) {
             const float aj = (j & 1) ? hi_of(acc2[j >> 1]) : lo_of(acc2[j >> 1]);
-            const float dw = QUANT ? c.csq[j] * (aj * deq) : aj;
+            const float dw = quant ? c.csq[j] * (aj * deq) : aj;
             if (SCHEME == MC_LOG_EULER) {
                 x[j] += c.drift[j] + dw;
                 if (STATS) u = fmaf(c.ws0[j], ex2_approx(x[j]), u);
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) mlmc_coupled_kernel(const __grid_const
         const int64_t nl = tid + it * gpaths;
         const bool valid = nl < a.run.paths;
         const uint64_t n = static_cast<uint64_t>(a.run.path_offset + (valid ? nl : 0));
-        const PathOut o = half ? simulate<PREC, SCHEME, STATS, true>(a, c, n) : simulate<PREC, SCHEME, STATS, false>(a, c, n);
+        const PathOut o = simulate<PREC, SCHEME, STATS>(a, c, n, half != 0);
         float f[kMlmcMaxPayoffs];
 #pragma unroll
         for (int p = 0; p < kMlmcMaxPayoffs; ++p)
