@@ -8,7 +8,8 @@
 // sustains a fraction of the FMA pipe's rate on this part; the 64-bit pair
 // operand carries two factor entries per instruction.
 //
-// Large runs launch one block of 640 threads per SM whose warps meet at a
+// Large runs launch one block per SM, of up to 640 threads (trimmed to whole
+// warps so that the rounds of paths fill every SM), whose warps meet at a
 // block barrier after every four columns of a step, so that all warps of an
 // SM read the same few hundred bytes of the factor at a time; small runs
 // launch blocks of 128 (more SMs busy).  Either way every thread runs every
@@ -31,7 +32,7 @@ const void *basket_select_scheme(const BasketArgs &a);
 namespace basket_detail {
 
 constexpr int kBlock = 640;        // slots of the reduction (at most 20 warps)
-constexpr int kLaunchBlock = 640;  // the largest launch block (mc_api: 640 or 128); 20 warps per SM
+constexpr int kLaunchBlock = 640;  // the largest launch block (mc_api: up to 640, or 128); 20 warps per SM
 
 __device__ __forceinline__ float elem(const f32x2 *v, int j) { return (j & 1) ? hi_of(v[j >> 1]) : lo_of(v[j >> 1]); }
 
