@@ -507,24 +507,39 @@ __global__ void __launch_bounds__(256) corr_adj_x_kernel(int d, const double *__
     }
 }
 
-// S_k = Lrho^-T X_k, one warp per column: s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii,
-// i = d-1 .. 0, the sum split over the lanes.
-__global__ void __launch_bounds__(256) corr_adj_s_kernel(int d, const double *__restrict__ L,
+// Lt = Lrho^T (row i of Lt = column i of Lrho, contiguous for the solve below).
+__global__ void corr_lt_kernel(int d, const double *__restrict__ L, double *__restrict__ Lt)
+{
+    const int64_t dd = static_cast<int64_t>(d) * d;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < dd;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        Lt[e] = L[(e % d) * d + e / d];
+}
+
+// S_k = Lrho^-T X_k, one thread per column (a warp's lanes on consecutive
+// columns: the reads of S coalesce, those of Lt broadcast):
+// s_ij = (x_ij - sum_{q > i} L_qi s_qj) / L_ii, i = d-1 .. 0, the sum in four
+// independent partial sums (shorter FP64 dependency chains).
+__global__ void __launch_bounds__(128) corr_adj_s_kernel(int d, const double *__restrict__ Lt,
                                                          const double *__restrict__ Pm, double *__restrict__ Sm)
 {
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= d) return;  // whole warps
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
     const int64_t off = static_cast<int64_t>(blockIdx.y) * d * d;
     const double *X = Pm + off;
     double *S = Sm + off;
     for (int i = d - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int q = i + 1 + lane; q < d; q += 32)
-            s = fma(L[static_cast<int64_t>(q) * d + i], S[static_cast<int64_t>(q) * d + j], s);
-        s = warp_sum_d(s);
-        if (lane == 0) S[static_cast<int64_t>(i) * d + j] = (X[static_cast<int64_t>(i) * d + j] - s) / L[static_cast<int64_t>(i) * d + i];
-        __syncwarp();
+        const double *li = Lt + static_cast<int64_t>(i) * d;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int q = i + 1;
+        for (; q + 3 < d; q += 4) {
+            s0 = fma(li[q], S[static_cast<int64_t>(q) * d + j], s0);
+            s1 = fma(li[q + 1], S[static_cast<int64_t>(q + 1) * d + j], s1);
+            s2 = fma(li[q + 2], S[static_cast<int64_t>(q + 2) * d + j], s2);
+            s3 = fma(li[q + 3], S[static_cast<int64_t>(q + 3) * d + j], s3);
+        }
+        for (; q < d; ++q) s0 = fma(li[q], S[static_cast<int64_t>(q) * d + j], s0);
+        S[static_cast<int64_t>(i) * d + j] = (X[static_cast<int64_t>(i) * d + j] - ((s0 + s1) + (s2 + s3))) / li[i];
     }
 }
 
@@ -624,7 +639,9 @@ cudaError_t launch_corr_wide(const CorrArgs &a, const CorrWide &w, int grid, cud
     const unsigned gr = static_cast<unsigned>((d + 7) / 8);  // 8 rows (columns) per block of 256
     corr_adj_x_kernel<<<dim3(gr, B + 1), 256, 0, s>>>(d, w.L, w.Pm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    corr_adj_s_kernel<<<dim3(gr, B + 1), 256, 0, s>>>(d, w.L, w.Pm, w.Sm);
+    corr_lt_kernel<<<ge, 256, 0, s>>>(d, w.L, w.Lt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    corr_adj_s_kernel<<<dim3(static_cast<unsigned>((d + 127) / 128), B + 1), 128, 0, s>>>(d, w.Lt, w.Pm, w.Sm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     corr_sym_kernel<<<dim3(ge, B + 1), 256, 0, s>>>(d, w.Sm, w.out_drho);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

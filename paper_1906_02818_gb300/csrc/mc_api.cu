@@ -1126,7 +1126,7 @@ static int corr_greeks_wide(const mc_model *m, const mc_sim_cfg *c, const mc_pay
     const size_t bytes = DeviceArena::up(dd * 8) * 2 + DeviceArena::up(d * 8) * 2 + DeviceArena::up(sizeof(int)) +
                          DeviceArena::up(tri * 4) + DeviceArena::up(d * 4) * 2 + DeviceArena::up(dd * 4) +
                          DeviceArena::up(static_cast<size_t>(P) * d * 4) * 2 + DeviceArena::up(B * dd * 4) +
-                         DeviceArena::up(B * 8) + 4 * DeviceArena::up((B + 1) * dd * 8) +
+                         DeviceArena::up(B * 8) + 4 * DeviceArena::up((B + 1) * dd * 8) + DeviceArena::up(dd * 8) +
                          2 * DeviceArena::up(dd * sizeof(mc_result)) + DeviceArena::up(static_cast<size_t>(ugrid) * 2 * 4) +
                          DeviceArena::up(4) + DeviceArena::up(sizeof(mc_result));
     MC_CUDA(dev_alloc(&ar.base, bytes));
@@ -1139,6 +1139,7 @@ static int corr_greeks_wide(const mc_model *m, const mc_sim_cfg *c, const mc_pay
     w.Ybuf = ar.take<float>(static_cast<size_t>(P) * d);
     w.part = ar.take<float>(B * dd);
     double *dnb = ar.take<double>(B);
+    w.Lt = ar.take<double>(dd);
     w.Pm = ar.take<double>((B + 1) * dd);
     w.Sm = ar.take<double>((B + 1) * dd);
     w.out_dl = ar.take<double>((B + 1) * dd);

@@ -310,6 +310,7 @@ struct CorrWide {
     int batches;
     int kchunk;           // paths per batch (a multiple of 16; the last batch may hold fewer)
     float *Wbuf, *Ybuf, *part;
+    double *Lt;           // [d x d] scratch: Lrho transposed
     double *Pm, *Sm, *out_dl, *out_drho;
     mc_result *res_dl, *res_drho;
 };
