@@ -65,6 +65,21 @@ def test_gbm1d_full_size_config(gb, orc):
     assert abs(got[0][0] - bs_call(100, 100, 0.05, 0.2, 1.0)) <= 3 * got[0][1]
 
 
+def test_gbm1d_2_28_paths_reduction_precision(gb):
+    """2^28 paths of the 1-D call (each warp's FP64 slot collects thousands of
+    FP32 warp sums before the FP64 cross-block finish): the price within 3 SE
+    of Black-Scholes (log-Euler is exact in law) at a standard error 16x below
+    the 2^20-path run's, and the standard error itself scaling as 1/sqrt(N)
+    within 1 % (an FP32-accumulated second moment would drift)."""
+    from closed_forms import bs_call
+    w = workloads.gbm_1d()
+    small = gb.price(gbm_model(w), cfg_of(w, paths=1 << 20), w["payoffs"])
+    big = gb.price(gbm_model(w), cfg_of(w, paths=1 << 28), w["payoffs"])
+    want = bs_call(100, 100, 0.05, 0.2, 1.0)
+    assert abs(big[0][0] - want) <= 3 * big[0][1], (big[0], want)
+    assert abs(big[0][1] * 16 / small[0][1] - 1.0) <= 0.01, (big[0][1], small[0][1])
+
+
 def test_plan_matches_price_and_repeats(gb):
     import torch
     w = workloads.gbm_1d(paths=1 << 16)
