@@ -159,6 +159,32 @@ def test_factor_model_checks(lib):
         assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
 
 
+def test_factor_model_greeks_checks(lib):
+    """mc_greeks on a factor model takes one European call or put under
+    log-Euler with every sigma > 0; the rest is refused before any device
+    work."""
+    from paper_1906_02818_gb300 import native
+    d = 4
+    pr, gr = (native.McResult * 2)(), (native.McResult * (2 * (2 * d + 1)))()
+    fm = dict(d=d, loadings=np.full((d, 2), 0.5))
+    call = [dict(kind="call", strike=100.0)]
+    for over, code, needle in [
+            (dict(fm, payoffs=[dict(kind="asian_call", strike=100.0)]), native.MC_EUNSUPPORTED, "European"),
+            (dict(fm, payoffs=[dict(kind="uo_call", strike=100.0, barrier=130.0)]), native.MC_EUNSUPPORTED,
+             "European"),
+            (dict(fm, payoffs=call * 2), native.MC_EUNSUPPORTED, "exactly one"),
+            (dict(fm, scheme="euler"), native.MC_EUNSUPPORTED, "log-Euler"),
+            (dict(fm, sigma=np.array([0.2, 0.0, 0.3, 0.25])), native.MC_EINVAL, "sigma > 0"),
+            (dict(fm, precision="bf16"), native.MC_EUNSUPPORTED, "FP32")]:
+        mm = _structs(**over)
+        rc = lib.mc_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, pr, gr, None)
+        assert rc == code, over
+        assert needle in lib.mc_last_error().decode(), (over, lib.mc_last_error())
+    mm = _structs(**fm)
+    assert lib.mc_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, 1, pr, None, None) == native.MC_EINVAL
+    assert lib.mc_greek_count(ctypes.byref(mm.model)) == 2 * d + 1
+
+
 def test_correlation_sensitivity_checks(lib):
     from paper_1906_02818_gb300 import native
     pr, dl, dr = native.McResult(), (native.McResult * 4096)(), (native.McResult * 4096)()
