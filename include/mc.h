@@ -45,7 +45,7 @@ typedef enum {
     MC_ENOMEM = -3,        /* device or host allocation failed */
     MC_ECUDA = -4,         /* a CUDA runtime call failed (message has the name) */
     MC_ETIMEOUT = -5,      /* a bounded device wait ran out */
-    MC_EUNSUPPORTED = -6   /* valid request this build cannot serve */
+    MC_EUNSUPPORTED = -6   /* valid request the library does not serve */
 } mc_status;
 
 typedef enum {

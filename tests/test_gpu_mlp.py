@@ -339,7 +339,7 @@ def test_training_on_greeks_gains_over_prices_alone(gb):
     2^14 European points of the surrogate's box, each labelled by 2^10 Monte
     Carlo paths, one on the prices alone and one on the prices plus the
     pathwise delta and vega labels of the same paths.  On 4096 fresh points
-    the Black-Scholes closed forms judge both: the Greek-trained network's
+    both are scored against the Black-Scholes closed forms: the Greek-trained network's
     delta error and its price error must be the smaller."""
     import math
     import torch
