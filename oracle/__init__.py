@@ -43,7 +43,11 @@ price against Black-Scholes and its error rate against plain Monte Carlo;
 the Cholesky tangent against LAPACK differences, per-path correlation
 tangents against bumped simulations, the geometric-basket correlation
 sensitivity against its closed form and the arithmetic basket's against
-common-random-number differences.
+common-random-number differences; the nested up-and-out value against the
+discretely monitored barrier of the GBM pricer; the random digital shift
+against the uniform law (Box-Muller normals of the shifted origin).  A
+mutation check (tests/test_oracle_mutants.py) plants one plausible mistake at
+a time in a copy of this package and requires a pin to fail for each.
 """
 from __future__ import annotations
 

@@ -6,6 +6,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# A copy of the oracle package with one planted mistake (test_oracle_mutants.py)
+# is imported in place of the repository's when GBMC_ORACLE_DIR names it.
+if os.environ.get("GBMC_ORACLE_DIR"):
+    sys.path.insert(0, os.environ["GBMC_ORACLE_DIR"])
 
 
 def pytest_configure(config):

@@ -1,0 +1,207 @@
+"""Mutation check of the oracle's pins.  Each case plants one plausible
+mistake in a copy of the oracle (a dropped term, a wrong sign, a wrong index
+or a transposed operand) and runs the pins named beside it against that copy:
+at least one of them must fail by an assertion (not by a build or import
+error).  A control copy without a mistake must pass the same pins, so a
+failure is the planted mistake's doing.
+
+The copy sits in a temporary directory; tests/conftest.py puts it ahead of
+the repository's oracle on the import path when GBMC_ORACLE_DIR names it, and
+the copy builds its own liboracle.so beside its oracle.c.  Nothing here runs
+on, or touches, the CUDA library."""
+import concurrent.futures as cf
+import os
+import re
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+pytestmark = pytest.mark.slow
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+T = "tests/"
+
+# (name, file under oracle/, text, replacement, pin tests that must catch it)
+MUTANTS = [
+    # Philox4x32-10 round function and key schedule (Sec. IV.A)
+    ("philox_high_word", "oracle.c", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;",
+     [T + "test_oracle_rng.py::test_philox_bit_exact_vs_torch_engine"]),
+    ("philox_weyl_swap", "oracle.c", "k0 += W0; k1 += W1;", "k0 += W1; k1 += W0;",
+     [T + "test_oracle_rng.py::test_philox_bit_exact_vs_torch_engine"]),
+    # uniform map and Box-Muller (Sec. VI.D)
+    ("uniform_offset", "oracle.c", "((double)(x >> 9) + 0.5)", "((double)(x >> 9) + 1.0)",
+     [T + "test_oracle_rng.py"]),
+    ("box_muller_radius", "oracle.c", "double rad = sqrt(-2.0 * log(u1));", "double rad = sqrt(-log(u1));",
+     [T + "test_oracle_rng.py"]),
+    ("box_muller_angle", "oracle.c", "rad * sin(2.0 * M_PI * u2)", "rad * sin(M_PI * u2)",
+     [T + "test_oracle_rng.py"]),
+    # Cholesky factor of the correlation (Sec. II.A.3)
+    ("cholesky_transposed_operand", "oracle.c", "s -= L[(size_t)i * d + k] * L[(size_t)j * d + k];",
+     "s -= L[(size_t)i * d + k] * L[(size_t)k * d + j];", [T + "test_oracle_gbm.py::test_cholesky_against_lapack"]),
+    # GBM step (Sec. II.A.1, II.A.2)
+    ("log_euler_drift_sign", "oracle.c", "x[a] += (m->r - 0.5 * m->sig[a] * m->sig[a]) * dt + dW;",
+     "x[a] += (m->r + 0.5 * m->sig[a] * m->sig[a]) * dt + dW;", [T + "test_oracle_gbm.py"]),
+    ("increment_scale", "oracle.c", "double dW = sdt * m->sig[a] * y[a];", "double dW = dt * m->sig[a] * y[a];",
+     [T + "test_oracle_gbm.py"]),
+    ("factor_transposed", "oracle.c", "for (int k = 0; k <= a; ++k) s += m->Lrho[(size_t)a * d + k] * z[k];",
+     "for (int k = 0; k <= a; ++k) s += m->Lrho[(size_t)k * d + a] * z[k];", [T + "test_oracle_gbm.py"]),
+    ("euler_drift_dropped", "oracle.c", "double g = 1.0 + m->r * dt + dW;", "double g = 1.0 + dW;",
+     [T + "test_oracle_gbm.py"]),
+    # payoffs and monitoring (Sec. I.A.2)
+    ("asian_average_count", "oracle.c", "stats->u_T = u; stats->avg = sum / M;",
+     "stats->u_T = u; stats->avg = sum / (M + 1);", [T + "test_oracle_gbm.py"]),
+    ("barrier_at_maturity_only", "oracle.c", "int up_hit = p->umax >= H,", "int up_hit = p->u_T >= H,",
+     [T + "test_oracle_gbm.py"]),
+    ("down_barrier_direction", "oracle.c", "down_hit = p->umin <= H;", "down_hit = p->umin >= H;",
+     [T + "test_oracle_gbm.py", T + "test_oracle_bridge.py"]),
+    ("up_in_put_pays_call", "oracle.c", "case ORC_UI_PUT: return up_hit ? put : 0.0;",
+     "case ORC_UI_PUT: return up_hit ? call : 0.0;", [T + "test_oracle_gbm.py"]),
+    ("discount_without_maturity", "oracle.c",
+     "    const double disc = exp(-r * T);\n#pragma omp parallel\n    {\n"
+     "        double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);",
+     "    const double disc = exp(-r);\n#pragma omp parallel\n    {\n"
+     "        double *work = (double *)malloc(sizeof(double) * 3 * (size_t)d);", [T + "test_oracle_gbm.py"]),
+    # Brownian-bridge extremes (Sec. VI.A.1)
+    ("bridge_variance_half", "oracle.c", "- 2.0 * dt * sig * sig * log(Ui)", "- dt * sig * sig * log(Ui)",
+     [T + "test_oracle_bridge.py"]),
+    ("bridge_minimum_sign", "oracle.c", "0.5 * (x + y - sqrt(", "0.5 * (x + y + sqrt(",
+     [T + "test_oracle_bridge.py"]),
+    # factor-model correlation
+    ("factor_idiosyncratic_variance", "oracle.c", "e[a] = sqrt(q < 1.0 ? 1.0 - q : 0.0);",
+     "e[a] = q < 1.0 ? 1.0 - q : 0.0;", [T + "test_oracle_factor.py"]),
+    ("factor_noise_reuses_factors", "oracle.c",
+     "eps[a] = stream_normal(&st, base + (uint64_t)k + (uint64_t)a);",
+     "eps[a] = stream_normal(&st, base + (uint64_t)a);", [T + "test_oracle_factor.py"]),
+    # Sobol directions and points (Sec. IV, VI.D)
+    ("sobol_recurrence_shift", "oracle.c", "uint32_t v = m[k - s] ^ (m[k - s] << s);",
+     "uint32_t v = m[k - s] ^ (m[k - s] << (s - 1));", [T + "test_oracle_qmc.py"]),
+    ("sobol_direction_scale", "oracle.c", "= m[k] << (32 - k);", "= m[k] << (31 - k);",
+     [T + "test_oracle_qmc.py"]),
+    ("qmc_shift_shared_by_a_pair", "oracle.c", "^ shift[2 * jn + 1]);", "^ shift[2 * jn]);",
+     [T + "test_oracle_qmc.py"]),
+    # forward-mode pathwise Greeks (Sec. I.A.3)
+    ("vega_tangent_sign", "oracle.c", "tg->tsig[a] += -m->sig[a] * dt + sdt * y[a];",
+     "tg->tsig[a] += m->sig[a] * dt + sdt * y[a];", [T + "test_oracle_greeks.py"]),
+    ("rho_discount_term_dropped", "oracle.c",
+     "g[((size_t)p * ng + 2 * d) * npaths + n] = disc * (slope * dr - T * f);",
+     "g[((size_t)p * ng + 2 * d) * npaths + n] = disc * slope * dr;", [T + "test_oracle_greeks.py"]),
+    ("asian_tangent_unaveraged", "oracle.c", "tg->aS0[a] += m->w[a] * f * tg->tS0[a] / M;",
+     "tg->aS0[a] += m->w[a] * f * tg->tS0[a];", [T + "test_oracle_greeks.py"]),
+    ("euler_vega_tangent_growth", "oracle.c", "tg->tsig[a] = tg->tsig[a] * g + x[a] * sdt * y[a];",
+     "tg->tsig[a] = tg->tsig[a] + x[a] * sdt * y[a];", [T + "test_oracle_greeks.py"]),
+    # correlation tangents (Sec. I.A.3, VI.A.2)
+    ("corr_tangent_wrong_normal", "oracle.c",
+     "t[(size_t)a * (a + 1) / 2 + b] += sdt * sig[a] * z[b];\n                }\n            }\n"
+     "            for (int a = 0; a < d; ++a) xT[",
+     "t[(size_t)a * (a + 1) / 2 + b] += sdt * sig[a] * z[a];\n                }\n            }\n"
+     "            for (int a = 0; a < d; ++a) xT[", [T + "test_oracle_corr.py"]),
+    ("corr_asian_tangent_unweighted", "oracle.c", "acc[(size_t)a * (a + 1) / 2 + b] += v * t[",
+     "acc[(size_t)a * (a + 1) / 2 + b] += t[", [T + "test_oracle_corr.py"]),
+    # Heston full-truncation Euler and its tangents
+    ("heston_correlation_root", "oracle.c", "const double rc = sqrt(1.0 - h->rho * h->rho);",
+     "const double rc = 1.0 - h->rho * h->rho;", [T + "test_oracle_heston.py"]),
+    ("heston_mean_reversion_sign", "oracle.c", "h->kappa * (h->theta - vp) * dt", "h->kappa * (vp - h->theta) * dt",
+     [T + "test_oracle_heston.py"]),
+    ("heston_rho_tangent_sign", "oracle.c", "(z1 - h->rho / rc * z2)", "(z1 + h->rho / rc * z2)",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_root_tangent_factor", "oracle.c", "dt * dvp / (2.0 * sq)", "dt * dvp / sq",
+     [T + "test_oracle_greeks.py"]),
+    # estimator (Eq. 3)
+    ("standard_error_divisor", "oracle.c", "/ (double)(n - 1)) : 0.0;", "/ (double)n) : 0.0;",
+     [T + "test_oracle_gbm.py::test_mean_se_definition"]),
+    # risk scenarios, nested values, labels (Sec. VI.B)
+    ("scenario_horizon_root", "oracle.c", "sqrt(h) * sig[u] * w", "h * sig[u] * w",
+     [T + "test_oracle_risk.py::test_scenario_moments"]),
+    ("nested_discount_one_step", "oracle.c", "return exp(-r * steps * dt) * sum / inner;",
+     "return exp(-r * dt) * sum / inner;", [T + "test_oracle_risk.py"]),
+    ("nested_barrier_at_maturity_only", "oracle.c", "if (kind == ORC_UO_CALL && exp(mx) >= H) f = 0.0;",
+     "if (kind == ORC_UO_CALL && ST >= H) f = 0.0;", [T + "test_oracle_risk.py"]),
+    ("label_vega_sign", "oracle.c", "(sqrt(dt) * zs - sig * tau)", "(sqrt(dt) * zs + sig * tau)",
+     [T + "test_oracle_risk.py::test_label_greeks_pins"]),
+    ("loss_sign", "risk.py", "l = np.sort(-np.asarray(pnl, dtype=np.float64))[::-1]",
+     "l = np.sort(np.asarray(pnl, dtype=np.float64))[::-1]",
+     [T + "test_oracle_risk.py::test_var_cvar_normal_closed_form"]),
+    # Cholesky tangent and the chain rule to correlation sensitivities (numpy)
+    ("cholesky_tangent_full_diagonal", "__init__.py", "np.tril(X, -1) + 0.5 * np.diag(np.diag(X))",
+     "np.tril(X, -1) + np.diag(np.diag(X))", [T + "test_oracle_corr.py"]),
+    ("cholesky_tangent_transposed", "__init__.py", "X = Li @ np.asarray(E, dtype=np.float64) @ Li.T",
+     "X = Li.T @ np.asarray(E, dtype=np.float64) @ Li", [T + "test_oracle_corr.py"]),
+    ("corr_chain_one_sided", "__init__.py", "drho[a, b] = drho[b, a] = vals[k]", "drho[a, b] = vals[k]",
+     [T + "test_oracle_corr.py"]),
+    ("corr_put_slope_sign", "__init__.py", "f, slope = np.maximum(K - U, 0.0), -(U < K).astype(np.float64)",
+     "f, slope = np.maximum(K - U, 0.0), (U < K).astype(np.float64)", [T + "test_oracle_corr.py"]),
+    ("factor_vega_drift_sign", "__init__.py", "((r + 0.5 * sigma ** 2) * T)", "((r - 0.5 * sigma ** 2) * T)",
+     [T + "test_oracle_factor.py"]),
+    ("factor_rho_discount_term_dropped", "__init__.py", "out[2 * d] = disc * slope * U * T - T * f[0]",
+     "out[2 * d] = disc * slope * U * T", [T + "test_oracle_factor.py"]),
+    # surrogate network, loss and optimiser
+    ("mlp_activation_derivative_dropped", "mlp.py", "dz = dh if l == len(params) - 1 else dh * silu_grad(z)",
+     "dz = dh", [T + "test_oracle_mlp.py"]),
+    ("mlp_bias_gradient_mean", "mlp.py", "grads[l] = (h.T @ dz, dz.sum(axis=0))",
+     "grads[l] = (h.T @ dz, dz.mean(axis=0))", [T + "test_oracle_mlp.py"]),
+    ("silu_derivative_sign", "mlp.py", "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 - z * (1.0 - s))",
+     [T + "test_oracle_mlp.py"]),
+    ("silu_second_derivative_term", "mlp.py", "(2.0 + z * (1.0 - 2.0 * s))", "(2.0 + z * (1.0 - s))",
+     [T + "test_oracle_mlp.py"]),
+    ("derivative_loss_second_order_dropped", "mlp.py",
+     "zbar = hbar * silu_grad(z) + sum(dhbar[k] * silu_grad2(z) * dzs[l - 1][k] for k in range(K))",
+     "zbar = hbar * silu_grad(z)", [T + "test_oracle_mlp.py"]),
+    ("adam_bias_correction_dropped", "mlp.py", "mh = m2 / (1 - beta1 ** step)", "mh = m2",
+     [T + "test_oracle_mlp.py"]),
+]
+
+
+def _copy(dst, mutant=None):
+    src = os.path.join(ROOT, "oracle")
+    out = os.path.join(dst, "oracle")
+    os.makedirs(out)
+    for name in ("__init__.py", "oracle.c", "mlp.py", "risk.py"):
+        shutil.copyfile(os.path.join(src, name), os.path.join(out, name))
+    if mutant is not None:
+        _, fname, old, new, _ = mutant
+        path = os.path.join(out, fname)
+        text = open(path).read()
+        assert text.count(old) == 1, f"{mutant[0]}: the text to change must occur once in {fname}"
+        open(path, "w").write(text.replace(old, new))
+    return out
+
+
+def _run_pins(alt_dir, targets):
+    env = dict(os.environ, GBMC_ORACLE_DIR=alt_dir, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", *targets, "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    out = r.stdout + r.stderr
+    summary = out.strip().splitlines()[-1] if out.strip() else ""
+    return r.returncode, summary, out
+
+
+def _case(mutant):
+    with tempfile.TemporaryDirectory(prefix="orc_mutant_") as tmp:
+        pkg = _copy(tmp, mutant)
+        rc, summary, out = _run_pins(tmp, mutant[4])
+        built = mutant[1] != "oracle.c" or os.path.exists(os.path.join(pkg, "liboracle.so"))
+        return mutant[0], rc, summary, built, out
+
+
+def test_every_planted_mistake_fails_a_pin():
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+    # control: the unchanged copy passes every pin the mutants use
+    targets = sorted({t.split("::")[0] for m in MUTANTS for t in m[4]})
+    with tempfile.TemporaryDirectory(prefix="orc_control_") as tmp:
+        _copy(tmp)
+        rc, summary, out = _run_pins(tmp, targets)
+        assert rc == 0, "control copy fails its pins:\n" + out[-3000:]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(4, (os.cpu_count() or 2) // 2))) as ex:
+        results = list(ex.map(_case, MUTANTS))
+    survivors = []
+    for name, rc, summary, built, out in results:
+        assert built, f"{name}: the planted copy did not build\n{out[-2000:]}"
+        caught = rc == 1 and re.search(r"\b\d+ failed\b", summary) and "error" not in summary
+        print(f"{name:40s} {'caught' if caught else 'SURVIVED'}: {summary}")
+        if not caught:
+            survivors.append((name, summary))
+    assert not survivors, survivors

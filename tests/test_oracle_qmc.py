@@ -9,7 +9,11 @@ fact that does not come from the oracle's code:
     numbers: m_k = 1 up to k = s, then m_{s+1} > 1) follows the count of
     primitive polynomials of degree s over GF(2), phi(2^s - 1) / s;
   * the randomised estimator is unbiased (Black-Scholes within 3 SE) and its
-    error falls faster than plain Monte Carlo's N^-1/2.
+    error falls faster than plain Monte Carlo's N^-1/2;
+  * the random digital shift makes every point uniform on the unit cube: the
+    first Sobol point is the origin, so across replications its shifted
+    coordinates are the shift itself, and the Box-Muller normals they yield
+    must be independent standard normals.
 """
 import math
 
@@ -91,3 +95,26 @@ def test_rqmc_basket_matches_monte_carlo(orc):
     mc = orc.gbm_payoffs(s0, sg, 0.05, 1.0, 1, 1 << 17, pays, corr=corr, weights=w)[0]
     se = math.sqrt(q.var(ddof=1) / 8 + mc.var(ddof=1) / mc.size)
     assert abs(q.mean() - mc.mean()) <= 3 * se
+
+
+def test_digital_shift_makes_the_origin_uniform(orc):
+    """At the first Sobol point (all words zero) replication rep's uniforms
+    are its shift words; with independent uniform shifts the normals of the
+    two Box-Muller pairs (dimensions 0-1 and 2-3) are i.i.d. N(0, 1) across
+    replications.  They are read back exactly from a one-asset, two-step
+    path: the strike-0 call gives S_2, the strike-0 Asian call (S_1 + S_2)/2."""
+    from scipy import stats
+    S, r, sg, T, R = 100.0, 0.05, 0.3, 1.0, 4096
+    dt = T / 2
+    pays = [dict(kind="call", strike=0.0), dict(kind="asian_call", strike=0.0)]
+    disc = math.exp(-r * T)
+    z = np.empty((2, R))
+    for rep in range(R):
+        f = orc.qmc_gbm_payoffs(S, sg, r, T, 2, 1, pays, rep=rep)[:, 0] / disc
+        s2, s1 = f[0], 2.0 * f[1] - f[0]
+        x1, x2 = math.log(s1 / S), math.log(s2 / s1)
+        z[:, rep] = [(x - (r - 0.5 * sg * sg) * dt) / (sg * math.sqrt(dt)) for x in (x1, x2)]
+    for k in range(2):
+        p = stats.kstest(z[k], "norm").pvalue
+        assert p > 1e-3, (k, p)
+    assert abs(np.corrcoef(z)[0, 1]) < 4.0 / math.sqrt(R)

@@ -62,6 +62,25 @@ def test_nested_value_is_black_scholes(orc):
     assert 0 < U[0] < van[0] and U[1] == 0.0
 
 
+def test_nested_up_and_out_monitors_every_step(orc):
+    """The nested revaluation's up-and-out call is knocked out when any of
+    its monitored prices reaches the barrier: its value equals the discretely
+    monitored up-and-out call of the GBM pricer (the same estimand, pinned by
+    the path-maximum test, on other streams) within 3 combined SE, while the
+    call knocked out on the terminal price alone lies far above both."""
+    S, sg, r, dt, steps, K, H = 100.0, 0.25, 0.05, 1 / 252, 60, 100.0, 112.0
+    inner, T = 1 << 16, steps / 252
+    V = risk.option_values([S], [sg], r, dt, 0, 0, [0], [4], [K], [H], [steps], inner)[0]
+    f = orc.gbm_payoffs(S, sg, r, T, steps, 1 << 17, [dict(kind="uo_call", strike=K, barrier=H)])[0]
+    m, se = orc.mean_se(f)
+    se_v = f.std(ddof=1) / math.sqrt(inner)  # the nested estimate's payoff law is the same
+    assert abs(V - m) <= 3 * math.hypot(se, se_v), (V, m, se, se_v)
+    # knocked out only at maturity: C(K) - C(H) - (H - K) * digital(H)
+    d2 = (math.log(S / H) + (r - 0.5 * sg * sg) * T) / (sg * math.sqrt(T))
+    terminal_only = cf.bs_call(S, K, r, sg, T) - cf.bs_call(S, H, r, sg, T) - (H - K) * math.exp(-r * T) * cf.ncdf(d2)
+    assert terminal_only - V > 20 * math.hypot(se, se_v), (terminal_only, V)
+
+
 def test_labels_european_are_black_scholes(orc):
     pts = np.array([[1.0, 0.2, 1.0, 0.05, 0.0], [1.2, 0.3, 0.5, 0.02, 0.0], [0.8, 0.15, 2.0, 0.07, 0.0]])
     lab = risk.labels(pts, 1 << 15)
