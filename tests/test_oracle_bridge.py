@@ -60,3 +60,16 @@ def test_bridge_knocks_more_often_than_the_grid(orc):
     van = orc.gbm1d_bridge_payoffs(100.0, 0.8, 0.03, 2.0, 25, 1 << 14, [dict(kind="put", strike=120.0)])[0]
     m, se = _mean_se(van)
     assert abs(m - bs_put(100.0, 120.0, 0.03, 0.8, 2.0)) <= 3 * se
+
+
+def test_unmonitored_payoffs_are_the_grid_pricers(orc):
+    """European and Asian payoffs do not look at the bridge extremes: on the
+    same normals they equal the grid pricer's path by path, for a monitored
+    underlying U = w S with w != 1 as well."""
+    pays = [dict(kind="call", strike=95.0), dict(kind="put", strike=110.0), dict(kind="asian_call", strike=100.0),
+            dict(kind="asian_put", strike=104.0)]
+    for w in (1.0, 1.7):
+        pw = [dict(p, strike=w * p["strike"]) for p in pays]
+        b = orc.gbm1d_bridge_payoffs(100.0, 0.4, 0.03, 1.5, 12, 4096, pw, weight=w)
+        g = orc.gbm_payoffs(np.array([100.0]), np.array([0.4]), 0.03, 1.5, 12, 4096, pw, weights=np.array([w]))
+        assert np.allclose(b, g, rtol=1e-12, atol=1e-10), w  # U ~ 200: rounding of U near the strike

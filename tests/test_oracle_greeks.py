@@ -69,11 +69,13 @@ def test_greeks_reject_barriers(orc):
         orc.gbm_greeks(100.0, 0.2, 0.05, 1.0, 4, 16, [dict(kind="uo_call", strike=100.0, barrier=120.0)])
 
 
+@pytest.mark.parametrize("T", [1.0, 0.75])
 @pytest.mark.parametrize("kind", ["call", "asian_call"])
-def test_heston_pathwise_equals_crn_finite_difference(orc, kind):
+def test_heston_pathwise_equals_crn_finite_difference(orc, kind, T):
     """Feller condition met (2 kappa theta = 0.16 > xi^2 = 0.04): the path map
-    is smooth on the sample and every Greek matches the CRN difference."""
-    N, M, T = 1 << 12, 32, 1.0
+    is smooth on the sample and every Greek matches the CRN difference (at a
+    maturity other than 1 as well, where d/dr's -T P term shows its T)."""
+    N, M = 1 << 12, 32
     base = dict(BASE, xi=0.2)
     pay = [dict(kind=kind, strike=100.0)]
     g = orc.heston_greeks(base, T, M, N, pay)[0].mean(axis=1)

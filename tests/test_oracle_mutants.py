@@ -137,6 +137,90 @@ MUTANTS = [
      [T + "test_oracle_factor.py"]),
     ("factor_rho_discount_term_dropped", "__init__.py", "out[2 * d] = disc * slope * U * T - T * f[0]",
      "out[2 * d] = disc * slope * U * T", [T + "test_oracle_factor.py"]),
+    # stream layout: both words of the key, the stream index and the counter
+    ("stream_counter_high_word", "oracle.c",
+     "uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)s->stream, (uint32_t)(s->stream >> 32)};",
+     "uint32_t ctr[4] = {(uint32_t)q, 0u, (uint32_t)s->stream, (uint32_t)(s->stream >> 32)};",
+     [T + "test_oracle_rng.py::test_box_muller_pairs"]),
+    ("stream_index_high_word", "oracle.c",
+     "uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)s->stream, (uint32_t)(s->stream >> 32)};",
+     "uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)s->stream, 0u};",
+     [T + "test_oracle_rng.py::test_box_muller_pairs"]),
+    ("key_high_word", "oracle.c", "uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};",
+     "uint32_t key[2] = {(uint32_t)s->seed, 0u};", [T + "test_oracle_rng.py::test_box_muller_pairs"]),
+    ("path_offset_ignored", "oracle.c",
+     "gbm_path(&m, path0 + n, NULL, 0, 0, 0, NULL, &ps, NULL, work);\n            for (int p = 0; p < npay; ++p)\n"
+     "                out",
+     "gbm_path(&m, n, NULL, 0, 0, 0, NULL, &ps, NULL, work);\n            for (int p = 0; p < npay; ++p)\n"
+     "                out", [T + "test_oracle_gbm.py"]),
+    ("saved_path_slot", "oracle.c",
+     "save[((size_t)slot * d + a) * ld + col] = (m->scheme == 0) ? exp(x[a]) : x[a];",
+     "save[((size_t)(slot - 1) * d + a) * ld + col] = (m->scheme == 0) ? exp(x[a]) : x[a];",
+     [T + "test_oracle_gbm.py"]),
+    ("estimator_compensation_sign", "oracle.c", "(a - t) + b : (b - t) + a;", "(a - t) - b : (b - t) + a;",
+     [T + "test_oracle_gbm.py::test_mean_se_definition"]),
+    # more of the bridge, factor model, Sobol and risk paths
+    ("bridge_uniform_lane", "oracle.c", "return orc_uniform(x[j & 3]);", "return orc_uniform(x[0]);",
+     [T + "test_oracle_bridge.py"]),
+    ("bridge_maximum_on_grid_only", "oracle.c", "if (hi > mmax) mmax = hi;", "if (y > mmax) mmax = y;",
+     [T + "test_oracle_bridge.py"]),
+    ("bridge_average_unweighted", "oracle.c", "sum += w * exp(x);", "sum += exp(x);", [T + "test_oracle_bridge.py"]),
+    ("factor_euler_drift_dropped", "oracle.c", "else x[a] *= 1.0 + r * dt + dW;\n                    u += w[a]",
+     "else x[a] *= 1.0 + dW;\n                    u += w[a]", [T + "test_oracle_factor.py"]),
+    ("factor_loadings_transposed", "oracle.c", "for (int j = 0; j < k; ++j) f += B[(size_t)a * k + j] * z[j];",
+     "for (int j = 0; j < k; ++j) f += B[(size_t)j * d + a] * z[j];", [T + "test_oracle_factor.py"]),
+    ("sobol_first_dimension_bits", "oracle.c", "for (int k = 0; k < 32; ++k) V[k] = (uint32_t)1 << (31 - k);",
+     "for (int k = 0; k < 32; ++k) V[k] = (uint32_t)1 << (31 - (k ^ 1));", [T + "test_oracle_qmc.py"]),
+    ("qmc_factor_wrong_normal", "oracle.c",
+     "for (int k = 0; k <= a; ++k) acc += m.Lrho[(size_t)a * d + k] * z[k];",
+     "for (int k = 0; k <= a; ++k) acc += m.Lrho[(size_t)a * d + k] * z[a];", [T + "test_oracle_qmc.py"]),
+    ("scenario_drift_sign", "oracle.c", "exp((mu - 0.5 * sig[u] * sig[u]) * h", "exp((mu + 0.5 * sig[u] * sig[u]) * h",
+     [T + "test_oracle_risk.py::test_scenario_moments"]),
+    ("scenario_factor_transposed", "oracle.c", "for (int k = 0; k <= u; ++k) w += L[(size_t)u * d + k] * z[k];",
+     "for (int k = 0; k <= u; ++k) w += L[(size_t)k * d + u] * z[k];",
+     [T + "test_oracle_risk.py::test_scenario_moments"]),
+    ("base_values_skip_the_horizon", "oracle.c", "rem[o] + hsteps, inner, seed, 5,", "rem[o], inner, seed, 5,",
+     [T + "test_oracle_risk.py"]),
+    ("label_delta_ratio_dropped", "oracle.c", "disc * in * ST / S,", "disc * in * ST,",
+     [T + "test_oracle_risk.py::test_label_greeks_pins"]),
+    ("label_greeks_undiscounted", "oracle.c",
+     "const double v[3] = {disc * (ST > 1.0 ? ST - 1.0 : 0.0), disc * in * ST / S,",
+     "const double v[3] = {disc * (ST > 1.0 ? ST - 1.0 : 0.0), in * ST / S,",
+     [T + "test_oracle_risk.py::test_label_greeks_pins"]),
+    # more Greeks: GBM, Heston, correlation
+    ("r_tangent_scaled", "oracle.c", "tg->tr[a] += dt;", "tg->tr[a] += dt * m->sig[a];", [T + "test_oracle_greeks.py"]),
+    ("euler_delta_tangent_init", "oracle.c", "tg->tS0[a] = (m->scheme == 0) ? 1.0 / m->s0[a] : 1.0;",
+     "tg->tS0[a] = 1.0 / m->s0[a];", [T + "test_oracle_greeks.py"]),
+    ("asian_rho_from_terminal", "oracle.c", "dr += asian ? tg.ar[a] : m.w[a] * tg.tr[a];", "dr += m.w[a] * tg.tr[a];",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_v0_tangent_seed", "oracle.c", "tv[1] = 1.0;", "tv[1] = 0.0;", [T + "test_oracle_greeks.py"]),
+    ("heston_rho_greek_maturity", "oracle.c", "if (k == 2) v -= T * disc * f;", "if (k == 2) v -= disc * f;",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_truncation_tangent", "oracle.c", "double dvp = v > 0.0 ? tv[k] : 0.0;", "double dvp = tv[k];",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_theta_tangent_sign", "oracle.c", "h->kappa * (dth - dvp)", "h->kappa * (dth + dvp)",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_kappa_tangent_sign", "oracle.c", "(dkap * (h->theta - vp)", "(dkap * (h->theta + vp)",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_xi_tangent_dropped", "oracle.c", "+ (dxi * sq + h->xi * dsq) * z1;", "+ (h->xi * dsq) * z1;",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_asian_tangent_unaveraged", "oracle.c", "ta[k] += S * tx[k] / M;", "ta[k] += S * tx[k];",
+     [T + "test_oracle_greeks.py"]),
+    ("heston_variance_noise_wrong_normal", "oracle.c", "+ h->xi * sq * z1;", "+ h->xi * sq * z2;",
+     [T + "test_oracle_heston.py"]),
+    ("heston_saved_variance_truncated", "oracle.c", "save[((size_t)slot * 2 + 1) * ld + col] = v;",
+     "save[((size_t)slot * 2 + 1) * ld + col] = vp;", [T + "test_oracle_heston.py"]),
+    ("corr_asian_average_count", "oracle.c", "A[n] = sumU / steps;", "A[n] = sumU / (steps + 1);",
+     [T + "test_oracle_corr.py"]),
+    ("corr_weight_dropped", "__init__.py", "g = disc * slope[None, :] * w[:, None] * S",
+     "g = disc * slope[None, :] * S", [T + "test_oracle_corr.py"]),
+    ("corr_asian_undiscounted", "__init__.py", "dl[a, b] = disc * slope * tA[a * (a + 1) // 2 + b]",
+     "dl[a, b] = slope * tA[a * (a + 1) // 2 + b]", [T + "test_oracle_corr.py"]),
+    ("corr_asian_put_slope_sign", "__init__.py",
+     "f, slope = np.maximum(K - A, 0.0), -(A < K).astype(np.float64)",
+     "f, slope = np.maximum(K - A, 0.0), (A < K).astype(np.float64)", [T + "test_oracle_corr.py"]),
+    ("factor_delta_ratio_dropped", "__init__.py", "out[:d] = disc * slope[None, :] * wS / s0[:, None]",
+     "out[:d] = disc * slope[None, :] * wS", [T + "test_oracle_factor.py"]),
     # surrogate network, loss and optimiser
     ("mlp_activation_derivative_dropped", "mlp.py", "dz = dh if l == len(params) - 1 else dh * silu_grad(z)",
      "dz = dh", [T + "test_oracle_mlp.py"]),
@@ -149,7 +233,18 @@ MUTANTS = [
     ("derivative_loss_second_order_dropped", "mlp.py",
      "zbar = hbar * silu_grad(z) + sum(dhbar[k] * silu_grad2(z) * dzs[l - 1][k] for k in range(K))",
      "zbar = hbar * silu_grad(z)", [T + "test_oracle_mlp.py"]),
+    ("derivative_loss_tangent_weight_gradient_dropped", "mlp.py",
+     "gW = hs[l].T @ zbar + sum(dhs[l][k].T @ dzbar[k] for k in range(K))", "gW = hs[l].T @ zbar",
+     [T + "test_oracle_mlp.py"]),
+    ("derivative_loss_seed_halved", "mlp.py",
+     "dzbar = np.stack([(2.0 * lams[k] / n) * rd[k][:, None] for k in range(K)]) if K else np.zeros((0, n, 1))",
+     "dzbar = np.stack([(lams[k] / n) * rd[k][:, None] for k in range(K)]) if K else np.zeros((0, n, 1))",
+     [T + "test_oracle_mlp.py"]),
+    ("input_tangent_activation_dropped", "mlp.py", "hh, dh = silu(z), silu_grad(z) * dz", "hh, dh = silu(z), dz",
+     [T + "test_oracle_mlp.py"]),
     ("adam_bias_correction_dropped", "mlp.py", "mh = m2 / (1 - beta1 ** step)", "mh = m2",
+     [T + "test_oracle_mlp.py"]),
+    ("adam_second_moment_correction_dropped", "mlp.py", "vh = v2 / (1 - beta2 ** step)", "vh = v2",
      [T + "test_oracle_mlp.py"]),
 ]
 

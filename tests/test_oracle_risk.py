@@ -62,6 +62,17 @@ def test_nested_value_is_black_scholes(orc):
     assert 0 < U[0] < van[0] and U[1] == 0.0
 
 
+def test_base_values_run_the_full_maturity(orc):
+    """Base-date values (scen < 0) price from s0 over the horizon plus the
+    remaining steps: Black-Scholes at (rem + hsteps) dt within 3 SE."""
+    rem, hsteps, inner = 230, 20, 1 << 16
+    V = risk.option_values([100.0], [0.25], 0.05, 1 / 252, hsteps, -1, [0, 0], [0, 1], [105.0, 95.0],
+                           [np.inf, np.inf], [rem, rem], inner)
+    tau = (rem + hsteps) / 252
+    for v, want in zip(V, [cf.bs_call(100, 105, 0.05, 0.25, tau), cf.bs_put(100, 95, 0.05, 0.25, tau)]):
+        assert abs(v - want) < 3 * 0.06, (v, want)  # SE of the 2^16-path estimate is below 0.06 here
+
+
 def test_nested_up_and_out_monitors_every_step(orc):
     """The nested revaluation's up-and-out call is knocked out when any of
     its monitored prices reaches the barrier: its value equals the discretely

@@ -80,10 +80,13 @@ def test_uniform_map_exact_and_open(orc):
         assert u == ((int(x) >> 9) + 0.5) / 2**23
 
 
-def test_box_muller_pairs(orc):
-    """Normals 4q..4q+3 come from block q: z0^2 + z1^2 = -2 ln u(x0) and
-    atan2(z1, z0) = 2 pi u(x1) (mod 2 pi); same for lanes 2, 3."""
-    seed, stream = 42, 12345
+@pytest.mark.parametrize("seed,stream", [(42, 12345), ((7 << 40) | 42, 12345), (42, (2 << 56) | 9),
+                                         ((1 << 63) | 5, (1 << 35) | 3)])
+def test_box_muller_pairs(orc, seed, stream):
+    """Normals 4q..4q+3 of stream s under key seed come from the block at
+    counter (q lo, q hi, s lo, s hi), key (seed lo, seed hi):
+    z0^2 + z1^2 = -2 ln u(x0) and atan2(z1, z0) = 2 pi u(x1) (mod 2 pi); same
+    for lanes 2, 3 (both words of the key, the stream and the counter used)."""
     for q in [0, 1, 7, 1000, 2**33 + 5]:
         x = orc.philox([q & 0xFFFFFFFF, q >> 32, stream & 0xFFFFFFFF, stream >> 32],
                        [seed & 0xFFFFFFFF, seed >> 32])
