@@ -509,7 +509,7 @@ const void *basket_tc_select(const TcArgs &a, int *smem)
 {
     const bool stats = a.pay.need_avg || a.pay.need_max || a.pay.need_min;
     const bool exact = a.d == tcb::kN;
-    if (PREC != MC_FP8E4M3 && SCHEME == MC_LOG_EULER) {
+    if constexpr (PREC != MC_FP8E4M3 && SCHEME == MC_LOG_EULER) {
         // TMEM running sum: Z tile + factor tile + barriers + payoff slots
         // (~27 KB with the static arrays and the per-block reservation: at
         // most 8 CTAs, 8 x 64 TMEM columns, share an SM)
