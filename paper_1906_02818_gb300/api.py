@@ -29,15 +29,21 @@ class _Marshalled:
         m.kind = native.MODEL[kind]
         s0 = self._arr(np.atleast_1d(model["s0"]))
         m.d = s0.size
+        self.model_d = m.d
         m.s0 = self._ptr(s0)
         if kind == "gbm":
-            m.sigma = self._ptr(self._arr(np.atleast_1d(model["sigma"])))
+            # the library reads d (sigma, weights), d x d (corr) and d x k
+            # (loadings) doubles through these pointers: the sizes are checked here
+            m.sigma = self._ptr(self._sized(model["sigma"], m.d, "sigma"))
             if model.get("corr") is not None:
-                m.corr = self._ptr(self._arr(model["corr"]))
+                m.corr = self._ptr(self._sized(model["corr"], m.d * m.d, "corr (d x d)"))
             if model.get("weights") is not None:
-                m.weights = self._ptr(self._arr(model["weights"]))
+                m.weights = self._ptr(self._sized(model["weights"], m.d, "weights"))
             if model.get("loadings") is not None:
-                B = self._arr(np.asarray(model["loadings"], dtype=np.float64).reshape(m.d, -1))
+                B = np.asarray(model["loadings"], dtype=np.float64)
+                if (B.ndim == 2 and B.shape[0] != m.d) or B.ndim > 2 or B.size % m.d:
+                    raise ValueError(f"loadings of shape {B.shape} are not [d, k] with d = {m.d}")
+                B = self._arr(B.reshape(m.d, -1))
                 m.n_factors = B.shape[1]
                 m.loadings = self._ptr(B) if B.size else self._ptr(self._arr(np.zeros(1)))
         else:
@@ -71,6 +77,12 @@ class _Marshalled:
     def _arr(self, a):
         a = np.ascontiguousarray(a, dtype=np.float64)
         self.arrays.append(a)
+        return a
+
+    def _sized(self, a, n, what):
+        a = self._arr(np.atleast_1d(a))
+        if a.size != n:
+            raise ValueError(f"{what} has {a.size} entries, {n} expected for d = {self.model_d}")
         return a
 
     @staticmethod
@@ -127,7 +139,8 @@ def price_qmc(model: dict, cfg: dict, payoffs, replications: int = 16, stream=No
 def greeks(model: dict, cfg: dict, payoffs, stream=None):
     """Pathwise Greeks: (prices, greeks) with prices a list of (price, se) and
     greeks an array [n_payoff, G, 2] of (mean, se); G = 7 for Heston
-    (S0, v0, r, kappa, theta, xi, rho), 3 for single-asset GBM (S0, sigma, r)."""
+    (S0, v0, r, kappa, theta, xi, rho), 2d + 1 for GBM with d assets
+    (d/dS0_a for every asset, then d/dsigma_a, then d/dr)."""
     L = native.lib()
     mm = _Marshalled(model, cfg, payoffs)
     G = L.mc_greek_count(ctypes.byref(mm.model))

@@ -124,6 +124,8 @@ def dp_train(net, x_local, t_local, epochs: int, batch: int, lr: float, group=No
     import torch.distributed as dist
     world = dist.get_world_size(group)
     b = batch // world
+    if b < 1:
+        raise ValueError(f"a global batch of {batch} leaves no sample for each of {world} ranks")
     steps = len(t_local) // b
     n_global = b * world
     last = 0.0

@@ -73,6 +73,22 @@ def test_price_rejects_bad_arguments_on_host(lib, over, needle):
     assert needle in lib.mc_last_error().decode()
 
 
+@pytest.mark.parametrize("over,needle", [
+    (dict(sigma=np.full(3, 0.2)), "sigma"),
+    (dict(corr=np.eye(3)), "corr"),
+    (dict(weights=np.full(5, 0.25)), "weights"),
+    (dict(loadings=np.full((2, 4), 0.3)), "loadings"),
+    (dict(loadings=np.full(6, 0.3)), "loadings"),
+])
+def test_binding_checks_array_sizes(over, needle):
+    """The library reads d, d x d or d x k doubles through the model's
+    pointers; the binding refuses arrays of other sizes before any call."""
+    with pytest.raises(ValueError, match=needle):
+        _structs(d=4, **over)
+    _structs(d=4, loadings=np.full((4, 2), 0.3))  # [d, k] passes
+    _structs(d=4, loadings=np.zeros((4, 0)))      # no factors passes
+
+
 def test_heston_argument_checks(lib):
     from paper_1906_02818_gb300 import native
     for over, needle in [(dict(rho=1.0), "rho"), (dict(xi=-0.1), ">= 0"), (dict(precision="bf16"), "precision")]:

@@ -82,3 +82,17 @@ def test_moments_and_combine_through_the_library(orc):
         api.moments([(float("nan"), 1.0)], 10)
     with pytest.raises(native.MCError):
         api.combine(np.array([[1.0, 2.0, 0.0]]))
+
+
+def test_data_parallel_training_needs_a_sample_per_rank():
+    """A global batch smaller than the world leaves a rank nothing to train
+    on: refused before any collective (one-rank gloo group)."""
+    import torch.distributed as dist
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised in this process")
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{_free_port()}", rank=0, world_size=1)
+    try:
+        with pytest.raises(ValueError, match="no sample"):
+            shard.dp_train(object(), np.zeros((4, 5)), np.zeros(4), epochs=1, batch=0, lr=1e-3)
+    finally:
+        dist.destroy_process_group()
