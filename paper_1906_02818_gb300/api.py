@@ -97,6 +97,38 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _cuda_f32(x, what):
+    """x as a contiguous CUDA float32 tensor: the library reads float32
+    device memory through the pointer, so any other tensor is refused."""
+    import torch
+    if not (torch.is_tensor(x) and x.is_cuda and x.dtype == torch.float32):
+        raise ValueError(f"{what} must be a CUDA float32 tensor")
+    return x.contiguous()
+
+
+def _rows(x, cols, what):
+    """A CUDA float32 [n, cols] tensor."""
+    x = _cuda_f32(x, what)
+    if x.dim() != 2 or x.shape[1] != cols:
+        raise ValueError(f"{what} must have shape [n, {cols}], not {tuple(x.shape)}")
+    return x
+
+
+def _count(x, n, what):
+    """A CUDA float32 tensor of exactly n values."""
+    x = _cuda_f32(x, what)
+    if x.numel() != n:
+        raise ValueError(f"{what} holds {x.numel()} values, {n} expected")
+    return x
+
+
+def _host_f32(a, n, what):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"{what} holds {a.size} values, {n} expected")
+    return a
+
+
 def price(model: dict, cfg: dict, payoffs, stream=None):
     """Discounted prices and standard errors: list of (price, se)."""
     L = native.lib()
@@ -306,7 +338,7 @@ class Mlp:
         return out
 
     def set_params(self, p):
-        p = np.ascontiguousarray(p, dtype=np.float32)
+        p = _host_f32(p, self.count, "params")
         check(self._lib.mc_mlp_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
 
     def set_train_mode(self, mode: str):
@@ -317,14 +349,15 @@ class Mlp:
 
     def forward(self, x, precision="fp32", stream=None):
         import torch
-        x = x.contiguous()
+        x = _rows(x, self.n_in, "x")
         y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         check(self._lib.mc_mlp_forward(self._h, ctypes.c_void_p(x.data_ptr()), x.shape[0], ctypes.c_void_p(y.data_ptr()),
                                        native.PRECISION[precision], _stream_handle(stream)))
         return y
 
     def loss_grad(self, x, t, stream=None):
-        x, t = x.contiguous(), t.contiguous()
+        x = _rows(x, self.n_in, "x")
+        t = _count(t, x.shape[0], "t")
         g = np.empty(self.count, dtype=np.float32)
         loss = ctypes.c_double()
         check(self._lib.mc_mlp_loss_grad(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
@@ -333,7 +366,8 @@ class Mlp:
         return loss.value, g
 
     def train(self, x, t, epochs, batch, lr, stream=None):
-        x, t = x.contiguous(), t.contiguous()
+        x = _rows(x, self.n_in, "x")
+        t = _count(t, x.shape[0], "t")
         loss = ctypes.c_double()
         check(self._lib.mc_mlp_train(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                      x.shape[0], epochs, batch, ctypes.c_float(lr), ctypes.byref(loss),
@@ -342,7 +376,7 @@ class Mlp:
 
     def apply_grad(self, g, lr, stream=None):
         """One Adam step with the given packed gradient (host array)."""
-        g = np.ascontiguousarray(g, dtype=np.float32)
+        g = _host_f32(g, self.count, "g")
         check(self._lib.mc_mlp_apply_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(lr),
                                           _stream_handle(stream)))
 
@@ -360,9 +394,10 @@ class Mlp:
         """Loss with derivative labels (mc_mlp_loss_grad_d): (loss parts
         [1 + K], packed gradient); g a CUDA float32 [n, K] tensor (NaN: no
         label)."""
-        x, t = x.contiguous(), t.contiguous()
+        x = _rows(x, self.n_in, "x")
+        t = _count(t, x.shape[0], "t")
         d = self._dloss(dirs, scales, weights)
-        gp = ctypes.c_void_p(g.contiguous().data_ptr()) if d.n_dir else None
+        gp = ctypes.c_void_p(_count(g, x.shape[0] * d.n_dir, "g").data_ptr()) if d.n_dir else None
         parts = (ctypes.c_double * (1 + d.n_dir))()
         grad = np.empty(self.count, dtype=np.float32)
         check(self._lib.mc_mlp_loss_grad_d(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), gp,
@@ -372,9 +407,10 @@ class Mlp:
 
     def train_d(self, x, t, g, dirs, scales, weights, epochs, batch, lr, stream=None):
         """Mini-batch Adam on the derivative-label loss (mc_mlp_train_d)."""
-        x, t = x.contiguous(), t.contiguous()
+        x = _rows(x, self.n_in, "x")
+        t = _count(t, x.shape[0], "t")
         d = self._dloss(dirs, scales, weights)
-        gp = ctypes.c_void_p(g.contiguous().data_ptr()) if d.n_dir else None
+        gp = ctypes.c_void_p(_count(g, x.shape[0] * d.n_dir, "g").data_ptr()) if d.n_dir else None
         loss = ctypes.c_double()
         check(self._lib.mc_mlp_train_d(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), gp,
                                        x.shape[0], ctypes.byref(d), epochs, batch, ctypes.c_float(lr),
@@ -385,7 +421,8 @@ class Mlp:
         """CUDA float32 [count + 1]: the gradient of the batch's summed
         squared error and that sum (mc_mlp_loss_grad_sums, asynchronous)."""
         import torch
-        x, t = x.contiguous(), t.contiguous()
+        x = _rows(x, self.n_in, "x")
+        t = _count(t, x.shape[0], "t")
         out = torch.empty(self.count + 1, dtype=torch.float32, device=x.device)
         check(self._lib.mc_mlp_loss_grad_sums(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                               x.shape[0], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
@@ -394,9 +431,9 @@ class Mlp:
     def apply_grad_sums(self, g, scale, lr, stream=None):
         """One Adam step with gradient scale * g[:count] (g a CUDA float32
         tensor; mc_mlp_apply_grad_sums, asynchronous)."""
-        g = g.contiguous()
-        if not g.is_cuda or g.numel() < self.count:
-            raise ValueError("g must be a CUDA float32 tensor of at least count entries")
+        g = _cuda_f32(g, "g")
+        if g.numel() < self.count:
+            raise ValueError(f"g holds {g.numel()} values, at least {self.count} expected")
         check(self._lib.mc_mlp_apply_grad_sums(self._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_float(scale),
                                                ctypes.c_float(lr), _stream_handle(stream)))
 
@@ -420,7 +457,7 @@ def surrogate_labels(points, paths, steps_per_year=252, seed=42, stream=None, wi
     (S/K, sigma, tau, r, K/H); with_inputs=True also returns the network
     inputs of the points."""
     import torch
-    pts = points.contiguous()
+    pts = _rows(points, 5, "points")
     out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
     inp = torch.empty_like(pts) if with_inputs else None
     check(native.lib().mc_surrogate_labels(pts.shape[0], ctypes.c_void_p(pts.data_ptr()), paths, steps_per_year, seed,
@@ -435,7 +472,7 @@ def surrogate_label_greeks(points, paths, steps_per_year=252, seed=42, stream=No
     [n], dlabels [n, 2] = (d/d(S/K), d/d sigma), NaN rows for barrier points
     [, inputs])."""
     import torch
-    pts = points.contiguous()
+    pts = _rows(points, 5, "points")
     out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
     dl = torch.empty((pts.shape[0], 2), dtype=torch.float32, device=pts.device)
     inp = torch.empty_like(pts) if with_inputs else None

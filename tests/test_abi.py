@@ -268,3 +268,20 @@ def test_rng_entry_points_check_arguments_on_host(lib):
     assert lib.mc_normals(42, 0, 0, 0, ctypes.c_void_p(16), None) == native.MC_OK
     assert lib.mc_normals(42, 0, (1 << 64) - 2, 4, ctypes.c_void_p(16), None) == native.MC_EINVAL
     assert lib.mc_normals(42, 0, 0, 1 << 41, ctypes.c_void_p(16), None) == native.MC_EINVAL
+
+
+def test_binding_checks_device_tensors():
+    """Network and label calls read float32 device memory through their
+    pointers: host tensors, other dtypes and other shapes are refused by the
+    binding before any library call (checked here on host tensors)."""
+    import torch
+    from paper_1906_02818_gb300 import api
+    with pytest.raises(ValueError, match="CUDA float32"):
+        api._rows(torch.zeros((4, 5)), 5, "x")
+    with pytest.raises(ValueError, match="CUDA float32"):
+        api._count(np.zeros(4, dtype=np.float32), 4, "t")
+    with pytest.raises(ValueError, match="CUDA float32"):
+        api.surrogate_labels(torch.zeros((4, 5), dtype=torch.float64), 16)
+    with pytest.raises(ValueError, match="holds 3 values, 4 expected"):
+        api._host_f32(np.zeros(3), 4, "params")
+    assert api._host_f32(np.zeros(4), 4, "params").dtype == np.float32
