@@ -490,25 +490,31 @@ def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_pat
     L = native.lib()
     keep = []
 
-    def dp(x):
-        a = np.ascontiguousarray(x, dtype=np.float64)
+    # the library reads n_under (s0, sigma), n_under^2 (corr) and n_opt (the
+    # option arrays) values through these pointers: the sizes are checked here
+    def sized(x, n, what, dtype):
+        a = np.ascontiguousarray(np.atleast_1d(x), dtype=dtype)
+        if a.size != n:
+            raise ValueError(f"portfolio {what} has {a.size} entries, {n} expected")
         keep.append(a)
-        return a.ctypes.data_as(native.c_double_p)
+        return a
 
-    def ip(x):
-        a = np.ascontiguousarray(x, dtype=np.int32)
-        keep.append(a)
-        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    def dp(x, n, what):
+        return sized(x, n, what, np.float64).ctypes.data_as(native.c_double_p)
+
+    def ip(x, n, what):
+        return sized(x, n, what, np.int32).ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
     pf = native.McPortfolio()
-    pf.n_under = len(portfolio["s0"])
-    pf.s0, pf.sigma = dp(portfolio["s0"]), dp(portfolio["sigma"])
-    pf.corr = dp(portfolio["corr"]) if portfolio.get("corr") is not None else None
+    d = pf.n_under = len(np.atleast_1d(portfolio["s0"]))
+    pf.s0, pf.sigma = dp(portfolio["s0"], d, "s0"), dp(portfolio["sigma"], d, "sigma")
+    pf.corr = dp(portfolio["corr"], d * d, "corr") if portfolio.get("corr") is not None else None
     pf.r, pf.mu = float(portfolio["r"]), float(portfolio["mu"])
-    pf.n_opt = len(portfolio["strike"])
-    pf.under, pf.kind = ip(portfolio["under"]), ip([PORTFOLIO_KIND[int(k)] for k in portfolio["kind"]])
-    pf.strike, pf.barrier = dp(portfolio["strike"]), dp(portfolio["barrier"])
-    pf.maturity, pf.position = dp(portfolio["maturity"]), dp(portfolio["position"])
+    no = pf.n_opt = len(np.atleast_1d(portfolio["strike"]))
+    pf.under = ip(portfolio["under"], no, "under")
+    pf.kind = ip([PORTFOLIO_KIND[int(k)] for k in np.atleast_1d(portfolio["kind"])], no, "kind")
+    pf.strike, pf.barrier = dp(portfolio["strike"], no, "strike"), dp(portfolio["barrier"], no, "barrier")
+    pf.maturity, pf.position = dp(portfolio["maturity"], no, "maturity"), dp(portfolio["position"], no, "position")
     cf = native.McRiskCfg()
     cf.alpha, cf.horizon, cf.n_scen = alpha, float(portfolio["horizon"]), int(n_scen)
     cf.steps_per_year = int(portfolio.get("steps_per_year", 252))

@@ -285,3 +285,16 @@ def test_binding_checks_device_tensors():
     with pytest.raises(ValueError, match="holds 3 values, 4 expected"):
         api._host_f32(np.zeros(3), 4, "params")
     assert api._host_f32(np.zeros(4), 4, "params").dtype == np.float32
+
+
+@pytest.mark.parametrize("key,value", [("sigma", np.full(3, 0.2)), ("corr", np.eye(3)), ("barrier", np.full(5, 1e300)),
+                                       ("under", np.zeros(7, dtype=np.int32)), ("position", np.ones(2))])
+def test_risk_binding_checks_portfolio_sizes(lib, key, value):
+    """mc_risk reads n_under, n_under^2 and n_opt values through the
+    portfolio's pointers: arrays of other sizes are refused by the binding."""
+    import workloads
+    from paper_1906_02818_gb300 import api
+    pf = workloads.risk_portfolio(n_under=4, per_under=2)
+    pf[key] = value
+    with pytest.raises(ValueError, match=key):
+        api.risk(pf, n_scen=16)
