@@ -10,7 +10,7 @@ float64 CPU tensors (the library returns host results).
 Both return the tensor [n_payoff] of discounted prices.
 
   BasketPricer.apply(s0, sigma, r, corr, cfg, payoff, weights=None)
-      s0, sigma: [d]; r: []; corr: [d, d] (2 <= d <= 64); one European
+      s0, sigma: [d]; r: []; corr: [d, d] (2 <= d <= 512); one European
       basket call or put, log-Euler, FP32.  Returns the price [].  Backward:
       d/ds0, d/dsigma, d/dr from mc_greeks and d/dcorr from mc_corr_greeks;
       the gradient of a correlation entry pair is split evenly between
@@ -73,7 +73,8 @@ class GbmPricer(torch.autograd.Function):
 def _basket_model(s0, sigma, r, corr, weights):
     def arr(t):
         return t.detach().cpu().double().numpy()
-    return dict(kind="gbm", s0=arr(s0), sigma=arr(sigma), r=float(r), corr=arr(corr), weights=weights)
+    w = arr(weights) if torch.is_tensor(weights) else weights
+    return dict(kind="gbm", s0=arr(s0), sigma=arr(sigma), r=float(r), corr=arr(corr), weights=w)
 
 
 class BasketPricer(torch.autograd.Function):
