@@ -764,9 +764,12 @@ size_t mlp_train_floats_d(const MlpLayout &L, int64_t n, int K)
     return f + 2 * static_cast<size_t>(K + 1) * n * maxw + static_cast<size_t>(kMaxSlices) * maxw * maxw;
 }
 
-// Loss with derivative labels and its gradient (the derivation is in the
-// oracle's dloss_and_grads): a forward sweep of the primal rows and, stacked
-// below them, one tangent per direction; a reverse sweep through both.
+// Loss with derivative labels and its gradient: a forward sweep of the
+// primal rows and, stacked below them, one tangent per direction
+// (dz = dh W, next dh = silu'(z) dz); a reverse sweep through both
+// (W-bar = h^T z-bar + sum_k dh_k^T dz_k-bar, h-bar = z-bar W^T,
+// dh_k-bar = dz_k-bar W^T, previous z-bar = h-bar silu'(z)
+// + sum_k dh_k-bar silu''(z) dz_k, previous dz_k-bar = dh_k-bar silu'(z)).
 // acts: mlp_train_floats_d floats; partial: (1 + K) npartial doubles.
 cudaError_t mlp_loss_grad_d(const MlpLayout &L, const float *params, const float *x, const float *t, const float *g,
                             int64_t n, int K, const int *dirs, const float *scale, const float *weight, float *acts,
