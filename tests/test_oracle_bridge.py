@@ -73,3 +73,18 @@ def test_unmonitored_payoffs_are_the_grid_pricers(orc):
         b = orc.gbm1d_bridge_payoffs(100.0, 0.4, 0.03, 1.5, 12, 4096, pw, weight=w)
         g = orc.gbm_payoffs(np.array([100.0]), np.array([0.4]), 0.03, 1.5, 12, 4096, pw, weights=np.array([w]))
         assert np.allclose(b, g, rtol=1e-12, atol=1e-10), w  # U ~ 200: rounding of U near the strike
+
+
+def test_weighted_barriers_scale(orc):
+    """With a monitored underlying U = w S the bridge payoffs (barrier ones
+    included) at strike w K and barrier w H are w times those of w = 1 at K
+    and H, path by path: the weight reaches the terminal value, the average
+    and both monitored extremes."""
+    pays = [dict(kind="ui_put", strike=120.0, barrier=140.0), dict(kind="uo_call", strike=95.0, barrier=130.0),
+            dict(kind="di_call", strike=90.0, barrier=80.0), dict(kind="do_put", strike=105.0, barrier=85.0)]
+    w = 0.6
+    scaled = [dict(p, strike=p["strike"] * w, barrier=p["barrier"] * w) for p in pays]
+    a = orc.gbm1d_bridge_payoffs(100.0, 0.5, 0.03, 1.0, 16, 4096, scaled, weight=w)
+    b = orc.gbm1d_bridge_payoffs(100.0, 0.5, 0.03, 1.0, 16, 4096, pays, weight=1.0)
+    assert np.allclose(a, w * b, rtol=1e-12, atol=1e-10)
+    assert all(0 < np.count_nonzero(row) < row.size for row in a)

@@ -50,6 +50,15 @@ def test_martingale_every_step(orc):
         assert abs(x.mean() - 100.0) <= 3 * x.std(ddof=1) / np.sqrt(N) + 1e-12
 
 
+def test_saved_paths_start_at_s0(orc):
+    """Slot 0 of the materialised paths is t_0: every asset's own S0."""
+    s0, sg = np.array([90.0, 100.0, 120.0]), np.array([0.2, 0.3, 0.25])
+    corr = np.array([[1.0, 0.3, 0.1], [0.3, 1.0, 0.2], [0.1, 0.2, 1.0]])
+    for scheme in ("log_euler", "euler"):
+        P = orc.gbm_paths(s0, sg, 0.05, 1.0, 4, 64, corr=corr, scheme=scheme, save_every=2)
+        assert np.array_equal(P[0], np.repeat(s0[:, None], 64, axis=1))
+
+
 def test_euler_scheme_moments(orc):
     """Arithmetic Euler (the formula of Sec. II.A.1 with mu = r S, sigma = s S):
     the factors (1 + r D + s sqrt(D) z) are independent, so

@@ -118,3 +118,21 @@ def test_heston_against_semi_closed_form(orc):
         print(f"K={p['strike']:.0f}: Monte Carlo {m:.4f} +- {se:.4f}, semi-closed form {cf:.4f}, "
               f"difference {m - cf:+.4f} ({(m - cf) / se:+.1f} SE)")
         assert abs(m - cf) <= 4 * se + 0.02 * cf
+
+
+def test_barriers_monitor_every_step(orc):
+    """Heston barrier payoffs look at every monitored price: in + out =
+    vanilla path by path, and the up-and-in call (down-and-in put) is alive
+    exactly on the in-the-money paths whose saved prices reach the barrier at
+    some step (the materialised paths of the same streams)."""
+    M, N, T = 32, 4096, 1.0
+    pays = [dict(kind="call", strike=100.0), dict(kind="ui_call", strike=100.0, barrier=125.0),
+            dict(kind="uo_call", strike=100.0, barrier=125.0), dict(kind="put", strike=100.0),
+            dict(kind="di_put", strike=100.0, barrier=85.0), dict(kind="do_put", strike=100.0, barrier=85.0)]
+    f = orc.heston_payoffs(BASE, T, M, N, pays)
+    assert np.array_equal(f[1] + f[2], f[0]) and np.array_equal(f[4] + f[5], f[3])
+    P = orc.heston_paths(BASE, T, M, N, save_every=1)[:, 0]
+    up, down = P[1:].max(axis=0) >= 125.0, P[1:].min(axis=0) <= 85.0
+    assert np.array_equal(f[1] > 0, up & (P[-1] > 100.0))
+    assert np.array_equal(f[4] > 0, down & (P[-1] < 100.0))
+    assert 0 < np.count_nonzero(f[1]) < np.count_nonzero(f[0])  # the barrier matters on this sample

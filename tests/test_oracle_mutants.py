@@ -116,9 +116,9 @@ MUTANTS = [
     ("scenario_horizon_root", "oracle.c", "sqrt(h) * sig[u] * w", "h * sig[u] * w",
      [T + "test_oracle_risk.py::test_scenario_moments"]),
     ("nested_discount_one_step", "oracle.c", "return exp(-r * steps * dt) * sum / inner;",
-     "return exp(-r * dt) * sum / inner;", [T + "test_oracle_risk.py"]),
+     "return exp(-r * dt) * sum / inner;", [T + "test_oracle_risk.py::test_nested_value_is_black_scholes"]),
     ("nested_barrier_at_maturity_only", "oracle.c", "if (kind == ORC_UO_CALL && exp(mx) >= H) f = 0.0;",
-     "if (kind == ORC_UO_CALL && ST >= H) f = 0.0;", [T + "test_oracle_risk.py"]),
+     "if (kind == ORC_UO_CALL && ST >= H) f = 0.0;", [T + "test_oracle_risk.py::test_nested_up_and_out_monitors_every_step"]),
     ("label_vega_sign", "oracle.c", "(sqrt(dt) * zs - sig * tau)", "(sqrt(dt) * zs + sig * tau)",
      [T + "test_oracle_risk.py::test_label_greeks_pins"]),
     ("loss_sign", "risk.py", "l = np.sort(-np.asarray(pnl, dtype=np.float64))[::-1]",
@@ -180,7 +180,7 @@ MUTANTS = [
      "for (int k = 0; k <= u; ++k) w += L[(size_t)k * d + u] * z[k];",
      [T + "test_oracle_risk.py::test_scenario_moments"]),
     ("base_values_skip_the_horizon", "oracle.c", "rem[o] + hsteps, inner, seed, 5,", "rem[o], inner, seed, 5,",
-     [T + "test_oracle_risk.py"]),
+     [T + "test_oracle_risk.py::test_base_values_run_the_full_maturity"]),
     ("label_delta_ratio_dropped", "oracle.c", "disc * in * ST / S,", "disc * in * ST,",
      [T + "test_oracle_risk.py::test_label_greeks_pins"]),
     ("label_greeks_undiscounted", "oracle.c",
@@ -219,8 +219,68 @@ MUTANTS = [
     ("corr_asian_put_slope_sign", "__init__.py",
      "f, slope = np.maximum(K - A, 0.0), -(A < K).astype(np.float64)",
      "f, slope = np.maximum(K - A, 0.0), (A < K).astype(np.float64)", [T + "test_oracle_corr.py"]),
+    ("cholesky_tangent_upper_triangle", "__init__.py", "return L @ (np.tril(X, -1) + 0.5 * np.diag(np.diag(X)))",
+     "return L @ (np.triu(X, 1) + 0.5 * np.diag(np.diag(X)))", [T + "test_oracle_corr.py"]),
+    ("factor_put_slope_sign", "__init__.py",
+     'slope = (U > K).astype(np.float64) if kind == "call" else -(U < K).astype(np.float64)\n    wS',
+     'slope = (U > K).astype(np.float64) if kind == "call" else (U < K).astype(np.float64)\n    wS',
+     [T + "test_oracle_factor.py"]),
     ("factor_delta_ratio_dropped", "__init__.py", "out[:d] = disc * slope[None, :] * wS / s0[:, None]",
      "out[:d] = disc * slope[None, :] * wS", [T + "test_oracle_factor.py"]),
+    # statistics, discounting and schemes of the other pricers
+    ("factor_average_count", "oracle.c",
+     "ps.u_T = u; ps.avg = sum / steps; ps.umax = umax; ps.umin = umin;\n"
+     "            for (int p = 0; p < npay; ++p) out[(size_t)p * npaths + n]",
+     "ps.u_T = u; ps.avg = sum / (steps + 1); ps.umax = umax; ps.umin = umin;\n"
+     "            for (int p = 0; p < npay; ++p) out[(size_t)p * npaths + n]", [T + "test_oracle_factor.py"]),
+    ("qmc_average_count", "oracle.c",
+     "ps.u_T = u; ps.avg = sum / steps; ps.umax = umax; ps.umin = umin;\n"
+     "        for (int p = 0; p < npay; ++p) out[(size_t)p * npts + i]",
+     "ps.u_T = u; ps.avg = sum / (steps + 1); ps.umax = umax; ps.umin = umin;\n"
+     "        for (int p = 0; p < npay; ++p) out[(size_t)p * npts + i]", [T + "test_oracle_qmc.py"]),
+    ("qmc_discount_without_maturity", "oracle.c",
+     "    const double dt = T / steps, sdt = sqrt(dt), disc = exp(-r * T);\n#pragma omp parallel for schedule(static)\n"
+     "    for (int64_t i = 0; i < npts; ++i) {",
+     "    const double dt = T / steps, sdt = sqrt(dt), disc = exp(-r);\n#pragma omp parallel for schedule(static)\n"
+     "    for (int64_t i = 0; i < npts; ++i) {", [T + "test_oracle_qmc.py"]),
+    ("qmc_euler_drift_dropped", "oracle.c",
+     "                else x[a] *= 1.0 + r * dt + dW;\n                u += w[a] * ((scheme == 0) ? exp(x[a]) : x[a]);\n"
+     "            }\n            sum += u;",
+     "                else x[a] *= 1.0 + dW;\n                u += w[a] * ((scheme == 0) ? exp(x[a]) : x[a]);\n"
+     "            }\n            sum += u;", [T + "test_oracle_qmc.py"]),
+    ("heston_average_count", "oracle.c", "if (stats) { stats->u_T = S; stats->avg = sum / M;",
+     "if (stats) { stats->u_T = S; stats->avg = sum / (M + 1);", [T + "test_oracle_heston.py", T + "test_oracle_greeks.py"]),
+    ("heston_drift_rate_dropped", "oracle.c", "double xn = x + (h->r - 0.5 * vp) * dt + sq * c;",
+     "double xn = x + (-0.5 * vp) * dt + sq * c;", [T + "test_oracle_heston.py"]),
+    ("heston_maximum_is_terminal", "oracle.c", "if (S > umax) umax = S;", "umax = S;", [T + "test_oracle_heston.py"]),
+    ("bridge_maximum_unweighted", "oracle.c", "ps.umax = w * exp(mmax);", "ps.umax = exp(mmax);",
+     [T + "test_oracle_bridge.py"]),
+    ("bridge_minimum_unweighted", "oracle.c", "ps.umin = w * exp(mmin);", "ps.umin = exp(mmin);",
+     [T + "test_oracle_bridge.py"]),
+    ("saved_start_first_asset", "oracle.c", "for (int a = 0; a < d; ++a) save[(size_t)a * ld + col] = m->s0[a];",
+     "for (int a = 0; a < d; ++a) save[(size_t)a * ld + col] = m->s0[0];", [T + "test_oracle_gbm.py"]),
+    ("estimator_single_sample_error", "oracle.c", "*se = n > 1 ? sqrt(", "*se = n > 0 ? sqrt(",
+     [T + "test_oracle_gbm.py"]),
+    ("rho_greek_payoff_kind", "oracle.c",
+     "double f = payoff_value(kind[p], strike[p], 0.0, &ps);\n                int asian",
+     "double f = payoff_value(ORC_CALL, strike[p], 0.0, &ps);\n                int asian", [T + "test_oracle_greeks.py"]),
+    ("corr_tangent_time_scale", "oracle.c",
+     "for (int b = 0; b <= a; ++b) t[(size_t)a * (a + 1) / 2 + b] += sdt * sig[a] * z[b];\n                }\n"
+     "            }\n            for",
+     "for (int b = 0; b <= a; ++b) t[(size_t)a * (a + 1) / 2 + b] += dt * sig[a] * z[b];\n                }\n"
+     "            }\n            for", [T + "test_oracle_corr.py"]),
+    # nested revaluation, scenarios and labels: streams and payoffs
+    ("nested_knock_at_start_dropped", "oracle.c", "if (kind == ORC_UO_CALL && S >= H) return 0.0;",
+     "if (kind == ORC_UO_CALL && S > 2 * H) return 0.0;", [T + "test_oracle_risk.py::test_nested_value_is_black_scholes"]),
+    ("nested_put_pays_call", "oracle.c", "if (kind == ORC_PUT) f = K > ST ? K - ST : 0.0;",
+     "if (kind == ORC_PUT) f = ST > K ? ST - K : 0.0;", [T + "test_oracle_risk.py::test_nested_value_is_black_scholes"]),
+    ("nested_paths_share_a_stream", "oracle.c", "stream_init(&st, seed, domain_tag(domain, base | (uint64_t)p));",
+     "stream_init(&st, seed, domain_tag(domain, base));", [T + "test_oracle_risk.py::test_nested_value_is_black_scholes"]),
+    ("scenarios_share_a_stream", "oracle.c", "stream_init(&st, seed, domain_tag(2, (uint64_t)s));",
+     "stream_init(&st, seed, domain_tag(2, 0));", [T + "test_oracle_risk.py::test_scenario_moments"]),
+    ("label_points_share_streams", "oracle.c", "4, (uint64_t)p << 16);", "4, 0);", [T + "test_oracle_risk.py"]),
+    ("label_vega_sums_squares", "oracle.c", "                zs += z;", "                zs += z * z;",
+     [T + "test_oracle_risk.py::test_label_greeks_pins"]),
     # surrogate network, loss and optimiser
     ("mlp_activation_derivative_dropped", "mlp.py", "dz = dh if l == len(params) - 1 else dh * silu_grad(z)",
      "dz = dh", [T + "test_oracle_mlp.py"]),
@@ -241,6 +301,15 @@ MUTANTS = [
      "dzbar = np.stack([(lams[k] / n) * rd[k][:, None] for k in range(K)]) if K else np.zeros((0, n, 1))",
      [T + "test_oracle_mlp.py"]),
     ("input_tangent_activation_dropped", "mlp.py", "hh, dh = silu(z), silu_grad(z) * dz", "hh, dh = silu(z), dz",
+     [T + "test_oracle_mlp.py"]),
+    ("output_layer_activated", "mlp.py", "        h = silu(z) if l < len(params) - 1 else z\n", "        h = silu(z)\n",
+     [T + "test_oracle_mlp.py"]),
+    ("input_tangent_takes_bias", "mlp.py", "            dz = dh @ W\n            if l < len(params) - 1:",
+     "            dz = dh @ W + b\n            if l < len(params) - 1:", [T + "test_oracle_mlp.py"]),
+    ("derivative_labels_unmasked", "mlp.py", "r, rd = y - t, m * (dy - gz)", "r, rd = y - t, (dy - gz)",
+     [T + "test_oracle_mlp.py"]),
+    ("bias_gradient_takes_tangents", "mlp.py", "        grads[l] = (gW, zbar.sum(axis=0))\n        if l == 0:",
+     "        grads[l] = (gW, zbar.sum(axis=0) + dzbar.sum(axis=(0, 1)))\n        if l == 0:",
      [T + "test_oracle_mlp.py"]),
     ("adam_bias_correction_dropped", "mlp.py", "mh = m2 / (1 - beta1 ** step)", "mh = m2",
      [T + "test_oracle_mlp.py"]),
@@ -265,7 +334,7 @@ def _copy(dst, mutant=None):
 
 
 def _run_pins(alt_dir, targets):
-    env = dict(os.environ, GBMC_ORACLE_DIR=alt_dir, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
+    env = dict(os.environ, GBMC_ORACLE_DIR=alt_dir, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
     r = subprocess.run([sys.executable, "-m", "pytest", *targets, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     out = r.stdout + r.stderr
@@ -284,14 +353,20 @@ def _case(mutant):
 def test_every_planted_mistake_fails_a_pin():
     names = [m[0] for m in MUTANTS]
     assert len(set(names)) == len(names)
-    # control: the unchanged copy passes every pin the mutants use
+    # control: the unchanged copy passes every pin the mutants use (run
+    # beside the planted copies)
     targets = sorted({t.split("::")[0] for m in MUTANTS for t in m[4]})
-    with tempfile.TemporaryDirectory(prefix="orc_control_") as tmp:
-        _copy(tmp)
-        rc, summary, out = _run_pins(tmp, targets)
-        assert rc == 0, "control copy fails its pins:\n" + out[-3000:]
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(4, (os.cpu_count() or 2) // 2))) as ex:
+
+    def control():
+        with tempfile.TemporaryDirectory(prefix="orc_control_") as tmp:
+            _copy(tmp)
+            return _run_pins(tmp, targets)
+
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2))) as ex:
+        ctl = ex.submit(control)
         results = list(ex.map(_case, MUTANTS))
+        rc, summary, out = ctl.result()
+    assert rc == 0, "control copy fails its pins:\n" + out[-3000:]
     survivors = []
     for name, rc, summary, built, out in results:
         assert built, f"{name}: the planted copy did not build\n{out[-2000:]}"

@@ -118,3 +118,19 @@ def test_digital_shift_makes_the_origin_uniform(orc):
         p = stats.kstest(z[k], "norm").pvalue
         assert p > 1e-3, (k, p)
     assert abs(np.corrcoef(z)[0, 1]) < 4.0 / math.sqrt(R)
+
+
+@pytest.mark.parametrize("scheme", ["log_euler", "euler"])
+def test_rqmc_forward_at_another_maturity(orc, scheme):
+    """The zero-strike call of the randomised-QMC pricer at T = 2.5 over 4
+    steps is the discounted mean terminal price: S0 under log-Euler (exact in
+    law) and S0 (1 + r T/M)^M e^{-rT} under Euler (each step's factor has
+    mean 1 + r dt), within 3 SE of the replication means."""
+    S, r, sg, T, M = 100.0, 0.04, 0.3, 2.5, 4
+    pays = [dict(kind="call", strike=0.0)]
+    means = np.array([orc.qmc_gbm_payoffs(S, sg, r, T, M, 1 << 10, pays, rep=rep, scheme=scheme)[0].mean()
+                      for rep in range(16)])
+    want = S if scheme == "log_euler" else S * (1 + r * T / M) ** M * math.exp(-r * T)
+    se = means.std(ddof=1) / 4.0
+    assert abs(means.mean() - want) <= 3 * se + 1e-9, (scheme, means.mean(), want, se)
+    assert abs(want - S * math.exp(-r * T)) > 50 * se  # the discount's T is resolved

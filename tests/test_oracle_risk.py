@@ -60,6 +60,12 @@ def test_nested_value_is_black_scholes(orc):
                            [60, 60], 4096)
     van = risk.option_values([100.0], [0.25], 0.05, 1 / 252, 1, 0, [0], [0], [100.0], [np.inf], [60], 4096)
     assert 0 < U[0] < van[0] and U[1] == 0.0
+    # at or above the barrier on the revaluation date the option is already
+    # knocked out, even where later prices would fall back and finish in
+    # the money (a low strike)
+    Z = risk.option_values([100.0], [0.25], 0.05, 1 / 252, 1, 0, [0, 0], [4, 0], [50.0, 50.0], [100.0, np.inf],
+                           [60, 60], 4096)
+    assert Z[0] == 0.0 and Z[1] > 40.0
 
 
 def test_base_values_run_the_full_maturity(orc):
