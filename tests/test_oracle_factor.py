@@ -27,9 +27,13 @@ def test_no_factors_equals_independent_cholesky_paths(orc):
     s0 = np.linspace(90, 110, d)
     sg = np.linspace(0.15, 0.35, d)
     for scheme in ("log_euler", "euler"):
-        f = orc.gbm_factor_payoffs(s0, sg, np.zeros((d, 0)), 0.04, 1.0, 8, 3000, PAYS, scheme=scheme)
+        f, ST = orc.gbm_factor_payoffs(s0, sg, np.zeros((d, 0)), 0.04, 1.0, 8, 3000, PAYS, scheme=scheme,
+                                       terminal=True)
         g = orc.gbm_payoffs(s0, sg, 0.04, 1.0, 8, 3000, PAYS, scheme=scheme)
         assert np.max(np.abs(f - g)) <= 1e-12 * np.max(np.abs(g))
+        # the terminal prices it reports are the prices, under either scheme
+        P = orc.gbm_paths(s0, sg, 0.04, 1.0, 8, 3000, scheme=scheme, save_every=8)[-1]
+        assert np.allclose(ST, P, rtol=1e-12)
 
 
 def test_market_loadings_reproduce_its_correlation():
@@ -63,8 +67,8 @@ def test_one_asset_partial_loading_is_black_scholes(orc):
     assert abs(f.mean() - bs_call(100.0, 100.0, 0.05, 0.3, 1.0)) <= 3 * f.std(ddof=1) / np.sqrt(f.size)
 
 
-@pytest.mark.parametrize("kind", ["call", "put"])
-def test_factor_greeks_against_crn_differences(orc, kind):
+@pytest.mark.parametrize("kind,T", [("call", 1.0), ("put", 1.0), ("call", 0.6)])
+def test_factor_greeks_against_crn_differences(orc, kind, T):
     """Pathwise d/dS0_a, d/dsigma_a, d/dr against central differences of the
     per-path payoffs simulated with the bumped parameter on the same stream
     (the loadings held fixed): per path they differ only where the basket
@@ -74,7 +78,7 @@ def test_factor_greeks_against_crn_differences(orc, kind):
     s0, sg, B = workloads.basket_market_factors(d, k, seed=5)
     w = np.linspace(1.0, 2.0, d)
     w /= w.sum()
-    r, T = 0.04, 1.0
+    r = 0.04
     K = float(w @ s0) * (1.0 if kind == "call" else 1.02)
     pay = dict(kind=kind, strike=K)
     g = orc.gbm_factor_greeks(s0, sg, B, r, T, M, N, pay, weights=w)

@@ -133,6 +133,22 @@ def test_cholesky_against_lapack(orc):
         orc.cholesky(bad)
 
 
+def test_cholesky_rejects_what_lapack_rejects(orc):
+    """An indefinite symmetric matrix with unit diagonal (every entry a valid
+    correlation) has no Cholesky factor: LAPACK refuses it, and so must the
+    oracle, directly and through the pricer."""
+    import pytest
+    for c in (0.9, 0.6, 0.51):  # last pivot -15.2, -0.8, -0.06
+        A = np.array([[1.0, c, c], [c, 1.0, -c], [c, -c, 1.0]])
+        with pytest.raises(np.linalg.LinAlgError):
+            np.linalg.cholesky(A)
+        with pytest.raises(Exception):
+            orc.cholesky(A)
+        with pytest.raises(Exception):
+            orc.gbm_payoffs(np.full(3, 100.0), np.full(3, 0.2), 0.05, 1.0, 4, 16, [dict(kind="call", strike=100.0)],
+                            corr=A)
+
+
 def test_basket_log_return_covariance(orc):
     """Empirical covariance of one-step log returns equals diag(s) rho diag(s) T
     (a transposed factor, L^T z, would give L^T L instead)."""
@@ -166,16 +182,18 @@ def test_geometric_basket_closed_form(orc):
 
 
 def test_identity_correlation_is_independent_assets(orc):
-    """With rho = I, asset a of a d-asset basket uses normals a, a+d, a+2d ...
-    of its path's stream: reconstruct its path from the raw normals."""
+    """With rho = I (given, or left out), asset a of a d-asset basket uses
+    normals a, a+d, a+2d ... of its path's stream: reconstruct its path from
+    the raw normals."""
     d, M, N, r, T = 3, 5, 64, 0.05, 1.0
     s0, sig = np.array([90.0, 100.0, 110.0]), np.array([0.1, 0.2, 0.3])
-    P = orc.gbm_paths(s0, sig, r, T, M, N, corr=np.eye(d), save_every=1, path_offset=1000)
     D = T / M
-    for n in range(N):
-        z = orc.normals(42, 1000 + n, 0, M * d).reshape(M, d)
-        x = np.log(s0) + np.cumsum((r - 0.5 * sig ** 2) * D + sig * np.sqrt(D) * z, axis=0)
-        assert np.allclose(P[1:, :, n], np.exp(x), rtol=1e-13)
+    for corr in (np.eye(d), None):
+        P = orc.gbm_paths(s0, sig, r, T, M, N, corr=corr, save_every=1, path_offset=1000)
+        for n in range(N):
+            z = orc.normals(42, 1000 + n, 0, M * d).reshape(M, d)
+            x = np.log(s0) + np.cumsum((r - 0.5 * sig ** 2) * D + sig * np.sqrt(D) * z, axis=0)
+            assert np.allclose(P[1:, :, n], np.exp(x), rtol=1e-13)
 
 
 def test_path_offset_selects_streams(orc):

@@ -281,6 +281,62 @@ MUTANTS = [
     ("label_points_share_streams", "oracle.c", "4, (uint64_t)p << 16);", "4, 0);", [T + "test_oracle_risk.py"]),
     ("label_vega_sums_squares", "oracle.c", "                zs += z;", "                zs += z * z;",
      [T + "test_oracle_risk.py::test_label_greeks_pins"]),
+    # payoff kinds, slopes and barrier conventions
+    ("down_out_call_watches_the_maximum", "oracle.c", "case ORC_DO_CALL: return down_hit ? 0.0 : call;",
+     "case ORC_DO_CALL: return up_hit ? 0.0 : call;", [T + "test_oracle_gbm.py", T + "test_oracle_bridge.py"]),
+    ("up_out_put_watches_the_minimum", "oracle.c", "case ORC_UO_PUT: return up_hit ? 0.0 : put;",
+     "case ORC_UO_PUT: return down_hit ? 0.0 : put;", [T + "test_oracle_gbm.py", T + "test_oracle_bridge.py"]),
+    ("down_in_put_pays_call", "oracle.c", "case ORC_DI_PUT: return down_hit ? put : 0.0;",
+     "case ORC_DI_PUT: return down_hit ? call : 0.0;", [T + "test_oracle_gbm.py", T + "test_oracle_bridge.py"]),
+    ("asian_put_on_terminal", "oracle.c", "case ORC_ASIAN_PUT: return K > p->avg ? K - p->avg : 0.0;",
+     "case ORC_ASIAN_PUT: return K > p->u_T ? K - p->u_T : 0.0;",
+     [T + "test_oracle_gbm.py", T + "test_oracle_greeks.py", T + "test_oracle_corr.py"]),
+    ("up_barrier_needs_a_margin", "oracle.c", "int up_hit = p->umax >= H,", "int up_hit = p->umax > H * (1 + 1e-3),",
+     [T + "test_oracle_gbm.py"]),
+    ("asian_slope_on_terminal", "oracle.c", "case ORC_ASIAN_CALL: return p->avg > K ? 1.0 : 0.0;",
+     "case ORC_ASIAN_CALL: return p->u_T > K ? 1.0 : 0.0;", [T + "test_oracle_greeks.py"]),
+    ("put_slope_sign", "oracle.c", "case ORC_PUT: return K > p->u_T ? -1.0 : 0.0;",
+     "case ORC_PUT: return K > p->u_T ? 1.0 : 0.0;", [T + "test_oracle_greeks.py"]),
+    # set-up, tangents, Sobol and Heston details
+    ("cholesky_accepts_indefinite", "oracle.c", "if (!(s > 0.0)) return -1;", "if (!(s > -1.0)) return -1;",
+     [T + "test_oracle_gbm.py::test_cholesky_rejects_what_lapack_rejects"]),
+    ("identity_factor_scaled", "oracle.c", "for (int a = 0; a < d; ++a) m->Lrho[(size_t)a * d + a] = 1.0;",
+     "for (int a = 0; a < d; ++a) m->Lrho[(size_t)a * d + a] = 1.0 + (a > 0);", [T + "test_oracle_gbm.py"]),
+    ("euler_delta_tangent_not_grown", "oracle.c", "tg->tS0[a] = tg->tS0[a] * g;", "tg->tS0[a] = tg->tS0[a];",
+     [T + "test_oracle_greeks.py"]),
+    ("euler_rho_tangent_not_grown", "oracle.c", "tg->tr[a] = tg->tr[a] * g + x[a] * dt;",
+     "tg->tr[a] = tg->tr[a] + x[a] * dt;", [T + "test_oracle_greeks.py"]),
+    ("factor_terminal_prices_as_logs", "oracle.c",
+     "for (int a = 0; a < d; ++a) ST[(size_t)a * npaths + n] = (scheme == 0) ? exp(x[a]) : x[a];",
+     "for (int a = 0; a < d; ++a) ST[(size_t)a * npaths + n] = exp(x[a]);", [T + "test_oracle_factor.py"]),
+    ("primitivity_test_incomplete", "oracle.c", "        if (gf2_xpow_mod(order / q, p, s) == 1) return 0;\n", "",
+     [T + "test_oracle_qmc.py"]),
+    ("qmc_shift_one_lane", "oracle.c",
+     "for (int l = 0; l < 4 && 4 * q + l < ndim; ++l) shift[4 * q + l] = x[l];",
+     "for (int l = 0; l < 4 && 4 * q + l < ndim; ++l) shift[4 * q + l] = x[0];", [T + "test_oracle_qmc.py"]),
+    ("qmc_second_uniform_dimension", "oracle.c",
+     "const double u2 = orc_uniform(sobol_word(V + (size_t)(2 * jn + 1) * 32, (uint64_t)(n0 + i))",
+     "const double u2 = orc_uniform(sobol_word(V + (size_t)(2 * jn) * 32, (uint64_t)(n0 + i))",
+     [T + "test_oracle_qmc.py"]),
+    ("qmc_point_offset_ignored", "oracle.c",
+     "sobol_word(V + (size_t)(2 * jn) * 32, (uint64_t)(n0 + i)) ^ shift[2 * jn]);",
+     "sobol_word(V + (size_t)(2 * jn) * 32, (uint64_t)(i)) ^ shift[2 * jn]);",
+     [T + "test_oracle_qmc.py::test_point_offset_selects_points"]),
+    ("heston_correlated_noise_swapped", "oracle.c", "double c = h->rho * z1 + rc * z2;",
+     "double c = h->rho * z2 + rc * z1;", [T + "test_oracle_heston.py"]),
+    ("heston_drift_untruncated_variance", "oracle.c",
+     "double vn = v + h->kappa * (h->theta - vp) * dt + h->xi * sq * z1;",
+     "double vn = v + h->kappa * (h->theta - v) * dt + h->xi * sq * z1;",
+     [T + "test_oracle_heston.py", T + "test_oracle_greeks.py"]),
+    ("nested_barrier_margin", "oracle.c", "if (kind == ORC_UO_CALL && exp(mx) >= H) f = 0.0;",
+     "if (kind == ORC_UO_CALL && exp(mx) > H * 1.01) f = 0.0;",
+     [T + "test_oracle_risk.py::test_nested_up_and_out_monitors_every_step"]),
+    ("corr_chain_includes_diagonal", "__init__.py", "pairs = [(a, b) for a in range(d) for b in range(a)]",
+     "pairs = [(a, b) for a in range(d) for b in range(a + 1)]", [T + "test_oracle_corr.py"]),
+    ("corr_asian_payoff_undiscounted", "__init__.py", "return dict(f=disc * f, U=A, dl=dl, drho=corr_chain(corr, dl))",
+     "return dict(f=f, U=A, dl=dl, drho=corr_chain(corr, dl))", [T + "test_oracle_corr.py"]),
+    ("factor_greeks_discount_maturity", "__init__.py", "    disc = np.exp(-r * T)\n    U = w @ ST",
+     "    disc = np.exp(-r)\n    U = w @ ST", [T + "test_oracle_factor.py"]),
     # surrogate network, loss and optimiser
     ("mlp_activation_derivative_dropped", "mlp.py", "dz = dh if l == len(params) - 1 else dh * silu_grad(z)",
      "dz = dh", [T + "test_oracle_mlp.py"]),
@@ -313,6 +369,10 @@ MUTANTS = [
      [T + "test_oracle_mlp.py"]),
     ("adam_bias_correction_dropped", "mlp.py", "mh = m2 / (1 - beta1 ** step)", "mh = m2",
      [T + "test_oracle_mlp.py"]),
+    ("adam_denominator_without_root", "mlp.py", "new.append((p_ - lr * mh / (np.sqrt(vh) + eps), m2, v2))",
+     "new.append((p_ - lr * mh / (vh + eps), m2, v2))", [T + "test_oracle_mlp.py"]),
+    ("unpack_bias_offset", "mlp.py", "        bb = np.asarray(flat[o:o + b], dtype=np.float64)\n        o += b",
+     "        bb = np.asarray(flat[o:o + b], dtype=np.float64)\n        o += 0", [T + "test_oracle_mlp.py"]),
     ("adam_second_moment_correction_dropped", "mlp.py", "vh = v2 / (1 - beta2 ** step)", "vh = v2",
      [T + "test_oracle_mlp.py"]),
 ]

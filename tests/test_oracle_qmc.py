@@ -134,3 +134,14 @@ def test_rqmc_forward_at_another_maturity(orc, scheme):
     se = means.std(ddof=1) / 4.0
     assert abs(means.mean() - want) <= 3 * se + 1e-9, (scheme, means.mean(), want, se)
     assert abs(want - S * math.exp(-r * T)) > 50 * se  # the discount's T is resolved
+
+
+def test_point_offset_selects_points(orc):
+    """Points [n0, n0 + m) of a replication are the tail of a run over
+    [0, n0 + m): each point depends only on its own index."""
+    import workloads
+    s0, sg, corr = workloads.basket_market(4, 2)
+    pays = [dict(kind="call", strike=100.0), dict(kind="asian_put", strike=105.0)]
+    a = orc.qmc_gbm_payoffs(s0, sg, 0.05, 1.0, 3, 300, pays, rep=5, corr=corr)
+    b = orc.qmc_gbm_payoffs(s0, sg, 0.05, 1.0, 3, 77, pays, rep=5, corr=corr, point_offset=223)
+    assert np.array_equal(a[:, 223:], b)
