@@ -339,7 +339,9 @@ int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *
 
 /*
  * Surrogate pricing network (mc_mlp): n_in -> width x hidden (SiLU) -> 1
- * (linear), the network that revalues the risk portfolio.  Parameters are
+ * (linear), the network that revalues the risk portfolio (Sec. VI.B; its
+ * layers are the DNN layer / simulation time step analogy of Sec. III.C,
+ * trained by back-propagation, Sec. I.A.3).  Parameters are
  * one packed FP32 vector: for each layer l, W_l [in x out] row-major, then
  * b_l [out].  All x / y / t buffers are DEVICE pointers, row-major [n x n_in]
  * and [n]; host pointers are noted.  The network lives on the device that
@@ -358,8 +360,13 @@ int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *
  *     products on the tensor cores with operands split hi + lo and
  *     accumulated as hi*hi + hi*lo + lo*hi in FP32 (FP32-like accuracy); needs
  *     >= 2 hidden layers of a width that is a multiple of 64
- *     (MC_EUNSUPPORTED otherwise).  A bounded wait that expires makes the
- *     call return MC_ETIMEOUT.
+ *     (MC_EUNSUPPORTED otherwise).  It also selects the arithmetic of
+ *     mc_mlp_loss_grad_d, mc_mlp_train_d and mc_mlp_loss_grad_sums.  A
+ *     bounded wait that expires makes the call return MC_ETIMEOUT.
+ * Errors: MC_EINVAL for a NULL network or buffer, n < 1, sizes outside the
+ * limits above, or a learning rate that is not > 0 (checked before any
+ * device work); MC_ECUDA when a CUDA call fails.  The caller owns every buffer; the
+ * network owns its parameters and Adam state until mc_mlp_destroy.
  */
 #define MC_MLP_TRAIN_FP32 0
 #define MC_MLP_TRAIN_TF32X3 1
@@ -387,7 +394,9 @@ int mc_mlp_apply_grad(mc_mlp *net, const float *host_grad, float lr, void *strea
  * the network's input gradient (forward-mode tangents through the layers) and
  * the loss is differentiated through it (a reverse sweep through the
  * tangents, with the activation's second derivative).  FP32 SIMT products,
- * whatever mc_mlp_set_train_mode selected; the network needs a hidden layer.
+ * or, in MC_MLP_TRAIN_TF32X3, the width -> width products of the stacked
+ * primal and tangent rows on the tensor cores as in mc_mlp_loss_grad; the
+ * network needs a hidden layer.
  *   dl: n_dir in [0, 4] directions; dir[k] an input index, scale[k] finite
  *     (scale_k = 1 / (the input map's slope) turns a network-input derivative
  *     into a derivative in the raw variable), weight[k] >= 0.
@@ -522,7 +531,8 @@ int mc_surrogate_label_greeks(int64_t n_points, const float *dev_points, int32_t
                               uint64_t seed, float *dev_labels, float *dev_dlabels, float *dev_inputs, void *stream);
 
 /*
- * Plans: the same computation as mc_price split into a set-up phase (argument
+ * Plans: the same computation as mc_price (the paths of Eq. 1, the estimator
+ * of Eq. 3) split into a set-up phase (argument
  * checks, upload of the model, FP64 Cholesky factorisation on the device,
  * scaled copies of the factor, device scratch for per-block partial sums)
  * and an asynchronous execution that launches only the path kernels and the
@@ -530,6 +540,10 @@ int mc_surrogate_label_greeks(int64_t n_points, const float *dev_points, int32_t
  * stream of the device it was created on, but executions of one plan must
  * not overlap in time (they share the plan's scratch).
  *   mc_plan_execute: dev_out is a DEVICE buffer of n_payoff mc_result.
+ * Errors: mc_plan_create returns mc_price's argument errors (MC_EINVAL,
+ * MC_EUNSUPPORTED, MC_ENOTPSD) before launching anything; mc_plan_execute
+ * returns MC_EINVAL for a NULL plan or buffer and MC_ECUDA when a launch
+ * fails.  The plan owns its device scratch until mc_plan_destroy.
  */
 typedef struct mc_plan mc_plan;
 int mc_plan_create(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs,
