@@ -303,7 +303,11 @@ int mc_corr_greeks(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff
  * paths, so se^2 = se_0^2 + se_1^2.
  *   Correlated GBM baskets with 2 <= d <= 64, discrete monitoring;
  *   1 <= n_payoff <= 10; paths_ref >= 2.  out: host [n_payoff].
- * Synchronises `stream`.
+ * Errors: MC_EINVAL for bad arguments (an FP32 cfg->precision, counts
+ * outside the limits), MC_EUNSUPPORTED outside the cases above, MC_ENOTPSD
+ * if corr is not positive definite, MC_ETIMEOUT if a bounded wait of the
+ * tensor-core level expires; out is untouched on error.  Synchronises
+ * `stream`.
  */
 typedef struct {
     double price, se;         /* the two-level estimate of the FP32 price */
@@ -332,7 +336,10 @@ int mc_price_mlmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff 
  *   out: host [n_payoff]: price = mean of the replication means, se = their
  *   standard deviation / sqrt(replications).  rep_means: optional host
  *   [replications][n_payoff].
- * Synchronises `stream`.
+ * Errors: MC_EINVAL for bad arguments (replications or the point range out
+ * of bounds), MC_EUNSUPPORTED outside the cases above (d, dimensions,
+ * precision), MC_ENOTPSD if corr is not positive definite; outputs are
+ * untouched on error.  Synchronises `stream`.
  */
 int mc_price_qmc(const mc_model *model, const mc_sim_cfg *cfg, const mc_payoff *payoffs, int32_t n_payoff,
                  int32_t replications, mc_result *out, double *rep_means, void *stream);
@@ -453,6 +460,13 @@ int mc_mlp_destroy(mc_mlp *net);
  *   Limits: n_under <= 64, 32 options per underlying, n_scen <= 2^24;
  *   option kinds MC_CALL, MC_PUT, MC_UO_CALL.
  *   host_pnl: host [n_scen] or NULL.  Synchronises `stream`.
+ * Errors (checked before any device work unless noted): MC_EINVAL for NULL
+ * arrays, counts or limits outside the above, non-positive s0 or strike,
+ * negative sigma, maturities or a horizon that are not whole steps, a
+ * missing surrogate or one without 5 inputs; MC_EUNSUPPORTED for another
+ * option kind; MC_ENOTPSD when corr is not positive definite (after the
+ * device Cholesky); MC_ETIMEOUT when a bounded wait of the surrogate's
+ * kernel expired.  res and host_pnl are untouched on error.
  */
 typedef struct {
     int32_t n_under;
