@@ -124,6 +124,13 @@ MUTANTS = [
     ("loss_sign", "risk.py", "l = np.sort(-np.asarray(pnl, dtype=np.float64))[::-1]",
      "l = np.sort(np.asarray(pnl, dtype=np.float64))[::-1]",
      [T + "test_oracle_risk.py::test_var_cvar_normal_closed_form"]),
+    ("var_rank_off_by_one", "risk.py", "    var = l[k - 1]", "    var = l[min(k, l.size - 1)]",
+     [T + "test_oracle_risk.py::test_var_is_the_upper_quantile_of_the_sample"]),
+    ("var_rank_rounded_down", "risk.py", "k = max(1, math.ceil((1.0 - alpha) * l.size - 1e-9))",
+     "k = max(1, math.floor((1.0 - alpha) * l.size))",
+     [T + "test_oracle_risk.py::test_var_is_the_upper_quantile_of_the_sample"]),
+    ("cvar_tail_includes_var", "risk.py", "tail = l[:k][l[:k] > var]", "tail = l[:k]",
+     [T + "test_oracle_risk.py::test_var_is_the_upper_quantile_of_the_sample"]),
     # Cholesky tangent and the chain rule to correlation sensitivities (numpy)
     ("cholesky_tangent_full_diagonal", "__init__.py", "np.tril(X, -1) + 0.5 * np.diag(np.diag(X))",
      "np.tril(X, -1) + np.diag(np.diag(X))", [T + "test_oracle_corr.py"]),

@@ -26,6 +26,32 @@ def test_var_cvar_definition_brute_force():
             assert cvar >= var
 
 
+def test_var_is_the_upper_quantile_of_the_sample():
+    """VaR_alpha read as the upper alpha-quantile of the empirical loss law,
+    inf{x : F_n(x) > alpha} (F_n(x) = #(losses <= x) / n, exact rational
+    comparison), found by scanning the candidate losses; CVaR_alpha as the
+    conditional mean of the losses above it, E_n[L | L > VaR] (VaR itself
+    when no loss is above).  Ties included."""
+    from fractions import Fraction
+    rng = np.random.default_rng(4)
+    for n in (1, 2, 3, 10, 99, 100, 101, 1000, 1001):
+        for alpha in (0.5, 0.9, 0.95, 0.99, 0.999):
+            for ties in (False, True):
+                pnl = rng.standard_normal(n)
+                if ties:
+                    pnl = np.round(pnl, 1)
+                losses = -pnl
+                a = Fraction(str(alpha))
+                cand = sorted(set(losses.tolist()))
+                want = next(x for x in cand if Fraction(int(np.sum(losses <= x)), n) > a) \
+                    if any(Fraction(int(np.sum(losses <= x)), n) > a for x in cand) else max(cand)
+                above = losses[losses > want]
+                var, cvar, nt = risk.var_cvar(pnl, alpha)
+                assert var == want, (n, alpha, ties, var, want)
+                assert nt == above.size
+                assert cvar == pytest.approx(above.mean() if above.size else want, rel=1e-12, abs=1e-12)
+
+
 def test_var_cvar_normal_closed_form():
     rng = np.random.default_rng(1)
     n, alpha = 1 << 20, 0.99
