@@ -136,3 +136,15 @@ def test_barriers_monitor_every_step(orc):
     assert np.array_equal(f[1] > 0, up & (P[-1] > 100.0))
     assert np.array_equal(f[4] > 0, down & (P[-1] < 100.0))
     assert 0 < np.count_nonzero(f[1]) < np.count_nonzero(f[0])  # the barrier matters on this sample
+
+
+def test_two_semi_closed_forms_agree():
+    """The two Fourier-inversion forms written for these pins (the
+    characteristic function of log S_T here, the P1 / P2 integrands in
+    closed_forms) agree, at the workload's Feller-violating parameters and
+    in a milder regime."""
+    for K, v0, kappa, theta, xi, rho in [(80.0, 0.04, 2.0, 0.04, 0.5, -0.7), (100.0, 0.04, 2.0, 0.04, 0.5, -0.7),
+                                         (120.0, 0.09, 1.5, 0.05, 0.3, 0.4)]:
+        a = heston_call_semi_closed(100.0, K, 0.05, 1.0, v0, kappa, theta, xi, rho)
+        b = cf.heston_call(100.0, K, 0.05, 1.0, v0, kappa, theta, xi, rho)
+        assert abs(a - b) <= 1e-6 * max(1.0, abs(a)), (K, a, b)
