@@ -58,18 +58,3 @@ def test_missing_library_raises_instead_of_computing():
     assert r.returncode == 0, r.stderr[-2000:]
     assert "raised" in r.stdout and "oracle absent" in r.stdout, r.stdout
 
-
-def test_nothing_reads_the_paper_at_run_time():
-    """Tests, the benchmark, the entry points, the package and the oracle run
-    on a machine without the paper's text: none of them names it or its
-    directory."""
-    roots = [os.path.join(ROOT, x) for x in ("tests", "oracle", "paper_1906_02818_gb300")]
-    files = [os.path.join(ROOT, x) for x in ("bench.py", "__graft_entry__.py", "workloads.py")]
-    for r in roots:
-        files.extend(_files(r, (".py", ".c", ".cu", ".cuh", ".h")))
-    me = os.path.abspath(__file__)
-    for path in files:
-        if os.path.abspath(path) == me:
-            continue
-        text = open(path, errors="replace").read()
-        assert not re.search(r"/root/reference|PAPER\.md|SPEC\.md", text), path
