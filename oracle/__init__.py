@@ -45,9 +45,13 @@ tangents against bumped simulations, the geometric-basket correlation
 sensitivity against its closed form and the arithmetic basket's against
 common-random-number differences; the nested up-and-out value against the
 discretely monitored barrier of the GBM pricer; the random digital shift
-against the uniform law (Box-Muller normals of the shifted origin).  A
-mutation check (tests/test_oracle_mutants.py) plants one plausible mistake at
-a time in a copy of this package and requires a pin to fail for each.
+against the uniform law (Box-Muller normals of the shifted origin); Heston
+barriers against the monitored maxima of its saved paths; Cholesky refusals
+against LAPACK's; VaR as the sample's upper quantile found by scanning the
+losses.  The closed forms themselves are pinned by quadrature, parity,
+differences and their limits (tests/test_closed_forms.py).  A mutation check
+(tests/test_oracle_mutants.py) plants one plausible mistake at a time in a
+copy of this package and requires a pin to fail for each.
 """
 from __future__ import annotations
 
