@@ -298,3 +298,84 @@ def test_risk_binding_checks_portfolio_sizes(lib, key, value):
     pf[key] = value
     with pytest.raises(ValueError, match=key):
         api.risk(pf, n_scen=16)
+
+
+def _payoff_kind(mm, kind):
+    mm.payoffs[0].kind = kind
+    return mm
+
+
+def _set(mm, **fields):
+    for obj, name, value in ((mm.model if k.startswith("m_") else mm.cfg, k[2:], v) for k, v in fields.items()):
+        setattr(obj, name, value)
+    return mm
+
+
+@pytest.mark.parametrize("make,needle", [
+    (lambda: _set(_structs(), m_kind=7), "unknown model kind"),
+    (lambda: _set(_structs(), m_d=0), "out of range [1, 4096]"),
+    (lambda: _set(_structs(), m_d=5000), "out of range [1, 4096]"),
+    (lambda: _set(_structs(), m_s0=None), "s0 is NULL"),
+    (lambda: _structs(r=float("inf")), "r is not finite"),
+    (lambda: _set(_structs(kind="heston"), m_d=2), "Heston requires d == 1"),
+    (lambda: _set(_structs(kind="heston"), m_kappa=float("nan")), "Heston parameters must be finite"),
+    (lambda: _set(_structs(), m_sigma=None), "sigma is NULL"),
+    (lambda: _structs(d=4, loadings=np.full((4, 2), np.nan)), "loadings must be finite"),
+    (lambda: _structs(d=2, corr=np.array([[1.0, np.nan], [np.nan, 1.0]])), "corr must be finite"),
+    (lambda: _structs(d=2, corr=np.array([[1.0, 1.5], [1.5, 1.0]])), "outside [-1, 1]"),
+    (lambda: _set(_structs(), c_scheme=5), "unknown scheme"),
+    (lambda: _set(_structs(), c_precision=9), "unknown precision"),
+    (lambda: _set(_structs(), c_ckpt_every=-1), "ckpt_every must be >= 0"),
+    (lambda: _payoff_kind(_structs(), 99), "unknown kind"),
+])
+def test_model_and_config_checks(lib, make, needle):
+    """Every model / configuration / payoff check of mc_price that runs before
+    any CUDA call: MC_EINVAL with its message, outputs untouched."""
+    from paper_1906_02818_gb300 import native
+    mm = make()
+    out = (native.McResult * 1)(native.McResult(12345.0, -1.0))
+    rc = lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, out, None)
+    assert rc == native.MC_EINVAL, (needle, rc, lib.mc_last_error())
+    assert needle in lib.mc_last_error().decode(), (needle, lib.mc_last_error())
+    assert out[0].price == 12345.0 and out[0].se == -1.0
+
+
+def test_null_pointer_checks(lib):
+    from paper_1906_02818_gb300 import native
+    mm = _structs()
+    out = (native.McResult * 1)()
+    assert lib.mc_price(ctypes.byref(mm.model), None, mm.payoffs, 1, out, None) == native.MC_EINVAL
+    assert "cfg is NULL" in lib.mc_last_error().decode()
+    assert lib.mc_price(ctypes.byref(mm.model), ctypes.byref(mm.cfg), None, 1, out, None) == native.MC_EINVAL
+    assert "payoffs is NULL" in lib.mc_last_error().decode()
+    hm = _structs(kind="heston")
+    hm.model.corr = hm._ptr(hm._arr(np.eye(1)))
+    assert lib.mc_price(ctypes.byref(hm.model), ctypes.byref(hm.cfg), hm.payoffs, 1, out, None) == native.MC_EINVAL
+    assert "no correlation" in lib.mc_last_error().decode()
+
+
+def test_greeks_checks(lib):
+    """mc_greeks' own host checks (single-asset, basket and Heston forms)."""
+    from paper_1906_02818_gb300 import native
+    pr, g = (native.McResult * 2)(), (native.McResult * 64)()
+    for mm, gp, code, needle in [
+            (_structs(payoffs=[dict(kind="uo_call", strike=100.0, barrier=130.0)]), g, native.MC_EUNSUPPORTED,
+             "no pathwise Greek"),
+            (_structs(d=3, payoffs=[dict(kind="call", strike=100.0)] * 2), g, native.MC_EINVAL, "exactly one payoff"),
+            (_structs(d=3, sigma=np.array([0.2, 0.0, 0.3])), g, native.MC_EINVAL, "sigma > 0"),
+            (_structs(scheme="euler"), g, native.MC_EUNSUPPORTED, "log-Euler"),
+            (_set(_structs(kind="heston"), c_ckpt_every=100), g, native.MC_EINVAL, "outside [1, 64]"),
+            (_structs(), None, native.MC_EINVAL, "greeks is NULL")]:
+        rc = lib.mc_greeks(ctypes.byref(mm.model), ctypes.byref(mm.cfg), mm.payoffs, mm.n_payoff, pr, gp, None)
+        assert rc == code, (needle, rc, lib.mc_last_error())
+        assert needle in lib.mc_last_error().decode(), (needle, lib.mc_last_error())
+
+
+def test_moments_and_combine_checks(lib):
+    from paper_1906_02818_gb300 import native
+    res = (native.McResult * 1)(native.McResult(float("nan"), 1.0))
+    mom = (ctypes.c_double * 3)()
+    assert lib.mc_moments(res, 1, 10, mom) == native.MC_EINVAL and "not finite" in lib.mc_last_error().decode()
+    bad = (ctypes.c_double * 3)(1.0, 1.0, 0.0)
+    out = (native.McResult * 1)()
+    assert lib.mc_combine(bad, 1, out) == native.MC_EINVAL and "path count" in lib.mc_last_error().decode()
