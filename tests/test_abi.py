@@ -317,7 +317,7 @@ def _set(mm, **fields):
     (lambda: _set(_structs(), m_d=5000), "out of range [1, 4096]"),
     (lambda: _set(_structs(), m_s0=None), "s0 is NULL"),
     (lambda: _structs(r=float("inf")), "r is not finite"),
-    (lambda: _set(_structs(kind="heston"), m_d=2), "Heston requires d == 1"),
+    (lambda: _structs(kind="heston", s0=np.array([100.0, 100.0])), "Heston requires d == 1"),
     (lambda: _set(_structs(kind="heston"), m_kappa=float("nan")), "Heston parameters must be finite"),
     (lambda: _set(_structs(), m_sigma=None), "sigma is NULL"),
     (lambda: _structs(d=4, loadings=np.full((4, 2), np.nan)), "loadings must be finite"),
