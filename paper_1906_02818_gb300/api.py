@@ -512,7 +512,10 @@ def risk(portfolio: dict, alpha=0.99, n_scen=1 << 16, method="nested", inner_pat
     pf.r, pf.mu = float(portfolio["r"]), float(portfolio["mu"])
     no = pf.n_opt = len(np.atleast_1d(portfolio["strike"]))
     pf.under = ip(portfolio["under"], no, "under")
-    pf.kind = ip([PORTFOLIO_KIND[int(k)] for k in np.atleast_1d(portfolio["kind"])], no, "kind")
+    kinds = [int(k) for k in np.atleast_1d(portfolio["kind"])]
+    if any(k not in PORTFOLIO_KIND for k in kinds):
+        raise ValueError("portfolio option kinds: 0 call, 1 put, 4 up-and-out call")
+    pf.kind = ip([PORTFOLIO_KIND[k] for k in kinds], no, "kind")
     pf.strike, pf.barrier = dp(portfolio["strike"], no, "strike"), dp(portfolio["barrier"], no, "barrier")
     pf.maturity, pf.position = dp(portfolio["maturity"], no, "maturity"), dp(portfolio["position"], no, "position")
     cf = native.McRiskCfg()

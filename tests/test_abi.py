@@ -379,3 +379,68 @@ def test_moments_and_combine_checks(lib):
     bad = (ctypes.c_double * 3)(1.0, 1.0, 0.0)
     out = (native.McResult * 1)()
     assert lib.mc_combine(bad, 1, out) == native.MC_EINVAL and "path count" in lib.mc_last_error().decode()
+
+
+def test_network_label_tail_and_stream_checks(lib):
+    """Host checks of the network, label, tail and random-stream entry points
+    (NULL handles and buffers, sizes, ranges), all before any CUDA call."""
+    from paper_1906_02818_gb300 import native
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below is refused first
+    res = native.McRiskResult()
+    for call, needle in [
+            (lambda: lib.mc_mlp_forward(None, p, 4, p, 0, None), "network is NULL"),
+            (lambda: lib.mc_mlp_loss_grad(None, p, p, 4, None, None, None), "network is NULL"),
+            (lambda: lib.mc_mlp_train(None, p, p, 4, 1, 1, ctypes.c_float(1e-3), None, None), "network is NULL"),
+            (lambda: lib.mc_mlp_apply_grad(None, None, ctypes.c_float(1e-3), None), "network is NULL"),
+            (lambda: lib.mc_mlp_create(0, 256, 4, None, ctypes.byref(ctypes.c_void_p())), "n_in in [1,64]"),
+            (lambda: lib.mc_mlp_create(5, 256, 4, None, None), "out is NULL"),
+            (lambda: lib.mc_surrogate_labels(0, p, 16, 252, 42, p, None, None), "n >= 1"),
+            (lambda: lib.mc_surrogate_labels(4, p, 0, 252, 42, p, None, None), "paths must lie in [1, 65536]"),
+            (lambda: lib.mc_surrogate_labels(4, p, 16, 0, 42, p, None, None), "steps_per_year"),
+            (lambda: lib.mc_surrogate_label_greeks(4, p, 16, 252, 42, p, None, None, None), "dev_dlabels"),
+            (lambda: lib.mc_tail(None, 4, ctypes.c_double(0.99), ctypes.byref(res), None), "dev_pnl and result"),
+            (lambda: lib.mc_tail(p, 0, ctypes.c_double(0.99), ctypes.byref(res), None), "n outside [1, 2^24]"),
+            (lambda: lib.mc_tail(p, 4, ctypes.c_double(1.0), ctypes.byref(res), None), "alpha must lie in (0, 1)"),
+            (lambda: lib.mc_philox_words(42, 0, 0, 1 << 41, p, None), "blocks outside [0, 2^40]"),
+            (lambda: lib.mc_philox_words(42, 0, (1 << 64) - 2, 4, p, None), "wraps past 2^64"),
+            (lambda: lib.mc_normals(42, 0, 0, 1 << 41, p, None), "count outside [0, 2^40]")]:
+        rc = call()
+        assert rc == native.MC_EINVAL, (needle, rc, lib.mc_last_error())
+        assert needle in lib.mc_last_error().decode(), (needle, lib.mc_last_error())
+    assert lib.mc_mlp_destroy(None) == 0  # destroying nothing is allowed
+
+
+class _NullStream:
+    cuda_stream = 0  # the default stream's handle, for calls refused before any CUDA work
+
+
+@pytest.mark.parametrize("over,kw,needle", [
+    ({}, dict(n_scen=0), "n_scen outside"),
+    ({}, dict(n_scen=16, alpha=1.5), "alpha must lie in (0, 1)"),
+    ({"horizon": 1.5 / 252}, dict(n_scen=16), "whole number of steps"),
+    ({}, dict(n_scen=16, method="surrogate"), "surrogate network not set"),
+    ({}, dict(n_scen=16, inner_paths=0), "inner_paths in [1, 65536]"),
+    ({"strike": "zero"}, dict(n_scen=16), "strike must be > 0"),
+    ({"maturity": "one day"}, dict(n_scen=16), "whole steps beyond the horizon"),
+    ({"s0": "negative"}, dict(n_scen=16), "s0 > 0 and sigma >= 0"),
+    ({}, dict(n_scen=16, scen_offset=-1), "scenario range"),
+])
+def test_risk_checks(lib, over, kw, needle):
+    import workloads
+    from paper_1906_02818_gb300 import api, native
+    pf = workloads.risk_portfolio(n_under=4, per_under=2)
+    fill = {"zero": 0.0, "one day": 1 / 252, "negative": -1.0}
+    for k, v in over.items():
+        pf[k] = np.full_like(pf[k], fill[v]) if isinstance(v, str) else v
+    with pytest.raises(native.MCError) as e:
+        api.risk(pf, stream=_NullStream(), **kw)
+    assert e.value.status == native.MC_EINVAL and needle in str(e.value), str(e.value)
+
+
+def test_risk_binding_refuses_unknown_kinds(lib):
+    import workloads
+    from paper_1906_02818_gb300 import api
+    pf = workloads.risk_portfolio(n_under=4, per_under=2)
+    pf["kind"] = np.full_like(pf["kind"], 2)
+    with pytest.raises(ValueError, match="option kinds"):
+        api.risk(pf, n_scen=16, stream=_NullStream())
